@@ -1,0 +1,356 @@
+"""The paper's circuits, step by step, over two oracle backends.
+
+TEST INFRASTRUCTURE ONLY (imported by tests/, __graft_entry__.smoke() and the
+CPU-baseline leg of bench.py).
+
+Backends:
+  * ``PlainSlots`` - the noiseless model: a ciphertext is a float64 vector of the
+    n/2 slots plus its level; a rotation is a cyclic shift, every polynomial is
+    evaluated exactly.  It gives the ideal value of every intermediate.
+  * ``OracleCkks`` - the same schedule on the plain RNS-CKKS of ``ckks.py``.
+
+Slot layout (Sec. 2.3, row-by-row encoding): slot q*N^2 + i*N + j holds row i,
+column j of the N x N matrix of query q (q = 0 .. Q-1 queries packed in one
+ciphertext, Q*N^2 <= n/2).  A rotation amount r > 0 is a left rotation
+(slot s <- slot s + r); r < 0 is a right rotation by -r.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import ckks
+
+# Cheon et al. composite sign polynomials (Sec. 2.2), coefficients of x, x^3, x^5, x^7.
+F_COEFFS = (35 / 16, -35 / 16, 21 / 16, -5 / 16)
+G_COEFFS = (4589 / 1024, -16577 / 1024, 25614 / 1024, -12860 / 1024)
+
+
+def log2_exact(N: int) -> int:
+    k = N.bit_length() - 1
+    assert N == 1 << k, f"N={N} is not a power of two"
+    return k
+
+
+# --------------------------------------------------------------------------
+# Plaintext masks (slot vectors)
+# --------------------------------------------------------------------------
+def mask_slots(kind: str, N: int, Q: int = 1, n_real: int | None = None, *, slots: int) -> np.ndarray:
+    """Slot vector of a named plaintext, tiled over Q packed queries.
+    n_real (<= N) is the unpadded length for the padding mask."""
+    block = np.zeros((N, N))
+    i, j = np.indices((N, N))
+    if kind == "row0":            # MaskR(X, 0): keep row 0
+        block[0, :] = 1.0
+    elif kind == "col0":          # MaskC(X, 0): keep column 0
+        block[:, 0] = 1.0
+    elif kind == "tie":           # 4*delta_{j>=i} - 2 on the block (Alg. 6 folded, see rank_tie_corrected)
+        block = np.where(j >= i, 2.0, -2.0)
+    elif kind == "tri":           # delta_{j>=i}: upper triangle with the diagonal (Alg. 6)
+        block = (j >= i).astype(float)
+    elif kind == "valid":         # rows and columns of the unpadded vector (Sec. 3.1, padding)
+        m = N if n_real is None else n_real
+        block = ((i < m) & (j < m)).astype(float)
+    else:
+        raise ValueError(kind)
+    v = np.zeros(slots)
+    flat = block.reshape(-1)
+    for q in range(Q):
+        v[q * N * N:(q + 1) * N * N] = flat
+    return v
+
+
+# --------------------------------------------------------------------------
+# Backends
+# --------------------------------------------------------------------------
+class PV:
+    __slots__ = ("v", "level")
+
+    def __init__(self, v, level):
+        self.v = v
+        self.level = level
+
+
+class PlainSlots:
+    """Noiseless slot model with level accounting (every product costs one level)."""
+
+    def __init__(self, slots: int, top_level: int):
+        self.slots = slots
+        self.top = top_level
+        self.counts = {"rot": 0, "mul": 0, "mul_scalar": 0, "mul_plain": 0}
+
+    def fresh(self, values) -> PV:
+        v = np.zeros(self.slots)
+        v[: len(values)] = values
+        return PV(v, self.top)
+
+    def level(self, x):
+        return x.level
+
+    def _lv(self, x, d=1):
+        assert x.level - d >= 0, "out of levels"
+        return x.level - d
+
+    def rot(self, x, r):
+        self.counts["rot"] += 1
+        return PV(np.roll(x.v, -(r % self.slots)), x.level)
+
+    def rot_many(self, x, rs):
+        return [self.rot(x, r) for r in rs]
+
+    def add(self, x, y):
+        assert x.level == y.level
+        return PV(x.v + y.v, x.level)
+
+    def sub(self, x, y):
+        assert x.level == y.level
+        return PV(x.v - y.v, x.level)
+
+    def neg(self, x):
+        return PV(-x.v, x.level)
+
+    def mul(self, x, y):
+        assert x.level == y.level
+        self.counts["mul"] += 1
+        return PV(x.v * y.v, self._lv(x))
+
+    def mul_scalar(self, x, c):
+        self.counts["mul_scalar"] += 1
+        return PV(x.v * c, self._lv(x))
+
+    def mul_plain(self, x, key):
+        self.counts["mul_plain"] += 1
+        return PV(x.v * mask_slots(*key, slots=self.slots), self._lv(x))
+
+    def add_const(self, x, c):
+        return PV(x.v + c, x.level)
+
+    def level_down(self, x, target):
+        while x.level > target:
+            x = self.mul_scalar(x, 1.0)
+        return x
+
+    def values(self, x):
+        return x.v
+
+
+class OracleCkks:
+    """The schedule on the plain RNS-CKKS oracle."""
+
+    def __init__(self, P: ckks.Params, keys: ckks.Keys):
+        self.P = P
+        self.keys = keys
+        self.slots = P.slots
+        self._enc = {}
+        self.counts = {"rot": 0, "mul": 0, "mul_scalar": 0, "mul_plain": 0}
+
+    def unscaled(self, key):
+        if key not in self._enc:
+            self._enc[key] = ckks.encode_unscaled(mask_slots(*key, slots=self.slots), self.P.n)
+        return self._enc[key]
+
+    def level(self, x):
+        return x.level
+
+    def rot(self, x, r):
+        self.counts["rot"] += 1
+        return ckks.rotate(self.P, self.keys, x, r)
+
+    def rot_many(self, x, rs):
+        return [self.rot(x, r) for r in rs]
+
+    def add(self, x, y):
+        return ckks.add(self.P, x, y)
+
+    def sub(self, x, y):
+        return ckks.sub(self.P, x, y)
+
+    def neg(self, x):
+        return ckks.neg(self.P, x)
+
+    def mul(self, x, y):
+        self.counts["mul"] += 1
+        return ckks.mul(self.P, self.keys, x, y)
+
+    def mul_scalar(self, x, c):
+        self.counts["mul_scalar"] += 1
+        return ckks.mul_scalar(self.P, x, c)
+
+    def mul_plain(self, x, key):
+        self.counts["mul_plain"] += 1
+        return ckks.mul_plain(self.P, x, self.unscaled(key))
+
+    def add_const(self, x, c):
+        return ckks.add_const(self.P, x, c)
+
+    def level_down(self, x, target):
+        return ckks.level_down(self.P, x, target)
+
+    def values(self, x):
+        return ckks.decrypt(self.P, self.keys, x)
+
+
+# --------------------------------------------------------------------------
+# Recursive matrix operations (App. A, Alg. 8-11; transpositions Alg. 1-2)
+# --------------------------------------------------------------------------
+def repl_r(B, x, N):
+    """Alg. 10: X <- X + (X >> N 2^i), i = 0 .. log N - 1."""
+    for i in range(log2_exact(N)):
+        x = B.add(x, B.rot(x, -(N << i)))
+    return x
+
+
+def repl_c(B, x, N):
+    """Alg. 11: X <- X + (X >> 2^i)."""
+    for i in range(log2_exact(N)):
+        x = B.add(x, B.rot(x, -(1 << i)))
+    return x
+
+
+def sum_r(B, x, N, Q=1):
+    """Alg. 8: X <- X + (X << N 2^i), then MaskR(X, 0)."""
+    for i in range(log2_exact(N)):
+        x = B.add(x, B.rot(x, N << i))
+    return B.mul_plain(x, ("row0", N, Q))
+
+
+def sum_c(B, x, N, Q=1):
+    """Alg. 9: X <- X + (X << 2^i), then MaskC(X, 0)."""
+    for i in range(log2_exact(N)):
+        x = B.add(x, B.rot(x, 1 << i))
+    return B.mul_plain(x, ("col0", N, Q))
+
+
+def trans_r(B, x, N, Q=1, trace=None):
+    """Alg. 1: X <- X + (X >> N(N-1)/2^i), i = 1 .. log N, then MaskC(X, 0)."""
+    for i in range(1, log2_exact(N) + 1):
+        r = (N * (N - 1)) >> i
+        x = B.add(x, B.rot(x, -r))
+        if trace is not None:
+            trace.append((r, x))
+    return B.mul_plain(x, ("col0", N, Q))
+
+
+def trans_c(B, x, N, Q=1, trace=None):
+    """Alg. 2: X <- X + (X << N(N-1)/2^i), i = 1 .. log N, then MaskR(X, 0)."""
+    for i in range(1, log2_exact(N) + 1):
+        r = (N * (N - 1)) >> i
+        x = B.add(x, B.rot(x, r))
+        if trace is not None:
+            trace.append((r, x))
+    return B.mul_plain(x, ("row0", N, Q))
+
+
+# --------------------------------------------------------------------------
+# Comparison (Sec. 2.2, composite f/g form)
+# --------------------------------------------------------------------------
+def poly7(B, x, c):
+    """Odd degree-7 polynomial c1 x + c3 x^3 + c5 x^5 + c7 x^7 in multiplicative depth 3
+    with four ciphertext products:  p = (c5 x + c7 x^3) x^4 + (c3/c7)(c7 x^3) + c1 x."""
+    c1, c3, c5, c7 = c
+    y = B.mul(x, x)                                        # x^2
+    z = B.mul(y, y)                                        # x^4
+    b7 = B.mul(B.mul_scalar(x, c7), y)                     # c7 x^3
+    a5 = B.mul_scalar(B.mul_scalar(x, c5), 1.0)            # c5 x
+    hz = B.mul(B.add(a5, b7), z)                           # c5 x^5 + c7 x^7
+    t3 = B.mul_scalar(b7, c3 / c7)                         # c3 x^3
+    t1 = B.mul_scalar(B.mul_scalar(B.mul_scalar(x, c1), 1.0), 1.0)   # c1 x
+    return B.add(B.add(hz, t3), t1)
+
+
+def cmp_stages(dg: int, df: int):
+    """g applied d_g times, then f applied d_f times; the last stage carries the 1/2 of
+    Cmp = (f^df(g^dg(x)) + 1) / 2."""
+    stages = [G_COEFFS] * dg + [F_COEFFS] * df
+    out = []
+    for idx, c in enumerate(stages):
+        if idx == len(stages) - 1:
+            c = tuple(ci / 2 for ci in c)
+        out.append(c)
+    return out
+
+
+def cmp(B, x, dg, df):
+    """Cmp(a, b) on x = a - b: 1 if a > b, 1/2 if equal, 0 if a < b (Eq. 1)."""
+    for c in cmp_stages(dg, df):
+        x = poly7(B, x, c)
+    return B.add_const(x, 0.5)
+
+
+# --------------------------------------------------------------------------
+# Ranking (Alg. 3) and tie correction (Alg. 6)
+# --------------------------------------------------------------------------
+def comparison_matrix(B, V, N, dg, df, Q=1):
+    """C = Cmp(ReplR(V), ReplC(TransR(V))): slot iN+j holds Cmp(v_j, v_i) (Alg. 3 lines 1-3).
+    The first rotations of ReplR and TransR both rotate V and share one ModUp (hoisting)."""
+    k = log2_exact(N)
+    if k == 0:
+        VR, VT = V, V
+    else:
+        r1, t1 = B.rot_many(V, [-N, -((N * (N - 1)) >> 1)])
+        VR = B.add(V, r1)
+        for i in range(1, k):
+            VR = B.add(VR, B.rot(VR, -(N << i)))
+        VT = B.add(V, t1)
+        for i in range(2, k + 1):
+            VT = B.add(VT, B.rot(VT, -((N * (N - 1)) >> i)))
+    T = B.mul_plain(VT, ("col0", N, Q))                     # TransR's MaskC
+    VC = repl_c(B, T, N)
+    X = B.sub(B.level_down(VR, B.level(VC)), VC)
+    return cmp(B, X, dg, df)
+
+
+def rank(B, V, N, dg, df, Q=1, n_real=None):
+    """Alg. 3: R = SumR(C) + 1/2 (fractional ranks in row 0).  With n_real < N the
+    vector was zero-padded to N = 2^k and the comparison matrix is masked to the
+    n_real x n_real block before summing (Sec. 3.1)."""
+    C = comparison_matrix(B, V, N, dg, df, Q)
+    if n_real is not None and n_real != N:
+        C = B.mul_plain(C, ("valid", N, Q, n_real))
+    return B.add_const(sum_r(B, C, N, Q), 0.5)
+
+
+def rank_tie_corrected(B, V, N, dg, df, Q=1):
+    """Alg. 3 + Alg. 6 in one SumR:  R + F = SumR(C + E (delta_{j>=i} - 1/2)) with
+    E = 4 C (1 - C);  the factor 4 and the -1/2 are folded into the 'tie' plaintext
+    (4 delta - 2) applied to K = C - C^2.  The +1/2 of Alg. 3 and the -1/2 of Alg. 6 cancel."""
+    C = comparison_matrix(B, V, N, dg, df, Q)
+    C2 = B.mul(C, C)
+    Cd = B.level_down(C, B.level(C2))
+    K = B.sub(Cd, C2)
+    KT = B.mul_plain(K, ("tie", N, Q))
+    W = B.add(B.level_down(Cd, B.level(KT)), KT)
+    return sum_r(B, W, N, Q)
+
+
+def tie_offset_unfolded(B, C, N, Q=1):
+    """Alg. 6 as printed: E = 4 C (1 - C); U = SumR(E . delta_{j>=i}); T = SumR(E);
+    F = U - T/2 - 1/2.  Used by the tests as the reference for the folded schedule."""
+    E = B.mul_scalar(B.mul(C, B.add_const(B.neg(C), 1.0)), 4.0)
+    U = sum_r(B, B.mul_plain(E, ("tri", N, Q)), N, Q)
+    T = sum_r(B, B.level_down(E, B.level(E) - 1), N, Q)
+    Th = B.mul_scalar(T, 0.5)
+    F = B.add_const(B.sub(B.level_down(U, B.level(Th)), Th), -0.5)
+    return E, U, T, F
+
+
+# --------------------------------------------------------------------------
+# Brute-force definitions (exact results the circuits approximate)
+# --------------------------------------------------------------------------
+def brute_fractional_rank(v):
+    """r_j = #{i: v_i < v_j} + (#{i: v_i = v_j} + 1) / 2 (Sec. 3.1)."""
+    v = np.asarray(v)
+    less = (v[None, :] < v[:, None]).sum(axis=1)
+    eq = (v[None, :] == v[:, None]).sum(axis=1)
+    return less + 0.5 * (eq + 1)
+
+
+def brute_tie_corrected_rank(v):
+    """k_j = #{i: v_i < v_j} + #{i <= j: v_i = v_j} (Sec. 4): a stable sort's positions."""
+    v = np.asarray(v)
+    N = len(v)
+    out = np.empty(N)
+    for j in range(N):
+        out[j] = np.sum(v < v[j]) + np.sum(v[: j + 1] == v[j])
+    return out

@@ -1,0 +1,162 @@
+"""Pins for the circuits in the noiseless slot model: the paper's worked examples
+(tests/golden/paper_examples.json), brute force over small N and the invariants
+of the correctness proofs (Sec. 3.1, Sec. 4, Eq. 3)."""
+import numpy as np
+import pytest
+
+from oracle import circuits as C
+
+
+def _mat(B, x, N, q=0):
+    return B.values(x)[q * N * N:(q + 1) * N * N].reshape(N, N)
+
+
+def test_fig1_transc_trace(golden):
+    g = golden["fig1_transc_n8"]
+    N = 8
+    B = C.PlainSlots(N * N, 5)                  # the figure rotates over exactly N^2 slots
+    start = np.array(g["start"], dtype=float)
+    x = C.PV(start.reshape(-1), 5)
+    trace = []
+    out = C.trans_c(B, x, N, trace=trace)
+    assert [r for r, _ in trace] == g["rotations"]
+    for (r, xi), key in zip(trace, ["after_28", "after_14", "after_7"]):
+        assert np.array_equal(_mat(B, xi, N), np.array(g[key], dtype=float)), key
+    assert np.array_equal(_mat(B, out, N), np.array(g["masked"], dtype=float))
+
+
+@pytest.mark.parametrize("N", [1, 2, 4, 8, 16])
+def test_matrix_ops_brute_force(N):
+    slots = 4 * N * N
+    B = C.PlainSlots(slots, 10)
+    rng = np.random.default_rng(N)
+    M = rng.uniform(-1, 1, (N, N))
+    X = np.zeros(slots)
+    X[: N * N] = M.reshape(-1)
+    x = C.PV(X, 10)
+    assert np.allclose(_mat(B, C.sum_r(B, x, N), N)[0], M.sum(axis=0))
+    assert np.allclose(_mat(B, C.sum_c(B, x, N), N)[:, 0], M.sum(axis=1))
+    row = np.zeros(slots)
+    row[:N] = M[0]
+    col = np.zeros(slots)
+    col[: N * N: N] = M[:, 0]
+    assert np.allclose(_mat(B, C.repl_r(B, C.PV(row, 10), N), N), np.tile(M[0], (N, 1)))
+    assert np.allclose(_mat(B, C.repl_c(B, C.PV(col, 10), N), N), np.tile(M[:, 0][:, None], (1, N)))
+    tr = _mat(B, C.trans_r(B, C.PV(row, 10), N), N)
+    expect = np.zeros((N, N))
+    expect[:, 0] = M[0]
+    assert np.allclose(tr, expect)
+    tc = _mat(B, C.trans_c(B, C.PV(col, 10), N), N)
+    expect = np.zeros((N, N))
+    expect[0] = M[:, 0]
+    assert np.allclose(tc, expect)
+
+
+def test_fig2_rank_example(golden):
+    g = golden["fig2_rank"]
+    v = np.array(g["input"]) / 64.0
+    B = C.PlainSlots(64, 40)
+    Cm = C.comparison_matrix(B, B.fresh(v), 4, 3, 2)
+    assert np.max(np.abs(_mat(B, Cm, 4) - np.array(g["C"]))) < 1e-6
+    assert np.all(_mat(B, Cm, 4)[np.eye(4, dtype=bool)] == 0.5)       # Cmp(x, x) = 1/2 exactly
+    S = C.sum_r(B, Cm, 4)
+    assert np.max(np.abs(B.values(S)[:4] - np.array(g["sumR"]))) < 1e-5
+    B2 = C.PlainSlots(64, 40)
+    R = C.rank(B2, B2.fresh(v), 4, 3, 2)
+    assert np.max(np.abs(B2.values(R)[:4] - np.array(g["rank"]))) < 1e-5
+
+
+def test_sec31_fractional_padded(golden):
+    g = golden["sec31_fractional"]
+    v = np.array(g["input"]) / 64.0
+    B = C.PlainSlots(256, 40)
+    R = C.rank(B, B.fresh(np.r_[v, np.zeros(3)]), 8, 3, 2, n_real=5)
+    assert np.max(np.abs(B.values(R)[:5] - np.array(g["rank"]))) < 1e-5
+    assert np.allclose(C.brute_fractional_rank(g["input"]), g["rank"])
+
+
+def test_fig4_tie_offset(golden):
+    g = golden["fig4_tie_offset"]
+    v = np.array(g["input"]) / 64.0
+    B = C.PlainSlots(64, 40)
+    Cm = C.comparison_matrix(B, B.fresh(v), 4, 3, 2)
+    E, U, T, F = C.tie_offset_unfolded(B, Cm, 4)
+    assert np.max(np.abs(_mat(B, E, 4) - np.array(g["E"]))) < 1e-5
+    assert np.max(np.abs(B.values(U)[:4] - np.array(g["U"]))) < 1e-5
+    assert np.max(np.abs(B.values(T)[:4] - np.array(g["T"]))) < 1e-5
+    assert np.max(np.abs(B.values(F)[:4] - np.array(g["F"]))) < 1e-5
+    B2 = C.PlainSlots(64, 40)
+    R = C.rank_tie_corrected(B2, B2.fresh(v), 4, 3, 2)
+    assert np.max(np.abs(B2.values(R)[:4] - np.array(g["corrected_rank"]))) < 1e-5
+    assert np.allclose(C.brute_tie_corrected_rank(g["input"]), g["corrected_rank"])
+
+
+def test_rotation_count_rank(golden):
+    # Sec. 3.1: 4 ceil(log N) rotations for ranking; 28 at N = 128 (Sec. 6 argmin count).
+    for N in (2, 8, 32, 128):
+        B = C.PlainSlots(max(2 * N * N, 64), 40)
+        C.rank(B, B.fresh(np.linspace(0, 0.9, N)), N, 4, 2)
+        assert B.counts["rot"] == 4 * int(np.log2(N))
+    assert golden["argmin_counts"]["rotations"] == 4 * 7
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_rank_brute_force_and_invariants(seed):
+    rng = np.random.default_rng(seed)
+    N = [4, 8, 16, 32, 64, 128][seed]
+    gap = 2.0 ** -9
+    v = np.sort(rng.uniform(0, 1 - (N - 1) * gap, N)) + np.arange(N) * gap
+    v = rng.permutation(v)
+    B = C.PlainSlots(max(2 * N * N, 64), 40)
+    R = B.values(C.rank(B, B.fresh(v), N, 4, 2))[:N]
+    assert np.max(np.abs(R - C.brute_fractional_rank(v))) < 0.25
+    assert abs(R.sum() - N * (N + 1) / 2) < 0.25
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_tie_corrected_is_permutation(seed):
+    rng = np.random.default_rng(100 + seed)
+    N = [8, 16, 32, 64][seed]
+    v = rng.integers(0, 64, N) / 64.0
+    B = C.PlainSlots(max(2 * N * N, 64), 40)
+    R = B.values(C.rank_tie_corrected(B, B.fresh(v), N, 3, 2))[:N]
+    k = C.brute_tie_corrected_rank(v)
+    assert np.max(np.abs(R - k)) < 0.25
+    assert sorted(np.rint(R).astype(int)) == list(range(1, N + 1))
+    # v_j is the k_j-th order statistic (Sec. 4, proof point 2)
+    s = np.sort(v)
+    assert all(s[int(kj) - 1] == vj for kj, vj in zip(np.rint(R), v))
+
+
+def test_block_complement_identity():
+    # Eq. 3: C_{i,j} = (1 - C_{j,i})^T for blocks of a longer vector
+    rng = np.random.default_rng(7)
+    Bsz = 8
+    vi = rng.uniform(0, 1, Bsz)
+    vj = rng.uniform(0, 1, Bsz)
+
+    def block_cmp(a, b):
+        B = C.PlainSlots(2 * Bsz * Bsz, 40)
+        VR = C.repl_r(B, B.fresh(a), Bsz)
+        VC = C.repl_c(B, C.trans_r(B, B.fresh(b), Bsz), Bsz)
+        X = B.sub(B.level_down(VR, B.level(VC)), VC)
+        return _mat(B, C.cmp(B, X, 4, 2), Bsz)
+
+    Cij = block_cmp(vi, vj)
+    Cji = block_cmp(vj, vi)
+    assert np.max(np.abs(Cij - (1 - Cji).T)) < 1e-5
+
+
+def test_packed_queries_do_not_leak():
+    # Q queries packed at stride N^2: each query's ranks equal its own brute force.
+    N, Q = 8, 4
+    rng = np.random.default_rng(11)
+    vs = [rng.permutation(np.linspace(0.05, 0.95, N)) for _ in range(Q)]
+    slots = Q * N * N * 2
+    B = C.PlainSlots(slots, 40)
+    X = np.zeros(slots)
+    for q, v in enumerate(vs):
+        X[q * N * N: q * N * N + N] = v
+    R = B.values(C.rank(B, C.PV(X, 40), N, 4, 2, Q=Q))
+    for q, v in enumerate(vs):
+        assert np.max(np.abs(R[q * N * N: q * N * N + N] - C.brute_fractional_rank(v))) < 1e-3
