@@ -1,0 +1,409 @@
+#!/usr/bin/env python
+"""Benchmark of the encrypted 128-element rank (Alg. 3) on one GB300 per process.
+
+Workload: rank of a 128-element vector, values uniform in [0, 1) with pairwise
+gap >= 2^-9 (seeded), RNS-CKKS with n = 2^16, 28 limbs (scale 2^45) plus 3
+special primes, digits of 3 limbs, comparator g^4 then f^2 (Sec. 2.2).  One step
+= one complete rank circuit on one encrypted vector (ReplR, TransR, ReplC, Cmp,
+SumR), inputs already resident in HBM; the rotation keys (8.7 GB) exceed L2, so
+every step streams from HBM.
+
+Reported (one JSON line from rank 0):
+  value          seconds per rank (CUDA events on the library stream), max over ranks
+  e2e            the same through the C-ABI from pinned host ciphertexts, with the
+                 host->device import and the device->host export of the result timed
+  roofline       the profiled kernel's algorithmic bytes / its event-timed duration
+  cpu_baseline   the oracle (plain CPU RNS-CKKS) on a bounded sample, scaled to a rank
+  clocks         nvidia-smi SM clocks sampled during the timed region
+  gpu_launches   kernels this library launched inside the timed region
+
+`--impl reference` times the oracle itself (the CPU reference of this project) on
+the same workload: each step is the bounded sample described in `cpu_baseline`.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "128-elem encrypted rank latency"
+UNIT = "s"
+PAPER_RANK128_S = 5.76   # the paper's 128-element rank, 64 threads on a Xeon 8358 (context)
+WORKLOAD = dict(log_n=16, n_limbs=28, n_special=3, digit_size=3, log_scale=45, log_q0=60, log_special=61,
+                d_g=4, d_f=2, N=128, gap=2.0 ** -9)
+
+
+def workload_config(extra=None):
+    cfg = {"workload": "rank N=128, n=2^16, 28+3 limbs, scale 2^45, dnum digits of 3, Cmp g^4 f^2",
+           "vector_len": WORKLOAD["N"], "ring_degree": 1 << WORKLOAD["log_n"], "limbs": WORKLOAD["n_limbs"],
+           "special_primes": WORKLOAD["n_special"], "gap": "2^-9",
+           "l2": "working set larger than L2 (rotation keys ~8.7 GB read every step)"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_id_for(local_rank: int) -> str:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [x.strip() for x in vis.split(",") if x.strip()]
+        if local_rank < len(ids):
+            return ids[local_rank]
+    return str(local_rank)
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def committed_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        src = open(os.path.join(ROOT, "paper_2412_15126_gb300", "csrc", "kernels.cu"), "rb").read()
+        if d.get("kernels_cu_sha256") != hashlib.sha256(src).hexdigest():
+            return None
+        return d.get("per_launch_bytes", {}).get(kernel)
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle on a bounded sample
+# ---------------------------------------------------------------------------
+def oracle_rank_estimate(steps: int = 1, warmup: int = 0):
+    """Time the oracle's rotation, product and scalar product at the top level (28
+    limbs), `steps` times each, and scale to one full rank circuit: each key switch
+    (rotation or product) at level l weighted by beta_l (l+1+alpha) relative to the
+    top level, each scalar/mask product by (l+1).  Returns seconds per rank and the
+    per-step samples."""
+    import numpy as np
+    from oracle import ckks, circuits as C
+
+    W = WORKLOAD
+    P = ckks.gen_params(W["log_n"], W["n_limbs"], W["log_q0"], W["log_scale"], W["n_special"],
+                        W["log_special"], W["digit_size"])
+    keys = ckks.keygen(P, 3, [ckks.galois_left(P.slots - W["N"], P.n)])
+    from paper_2412_15126_gb300 import inputs
+    ct = ckks.encrypt(P, keys, inputs.gap_vector(W["N"], W["gap"], 1), 1)
+
+    # op trace of the rank circuit (levels from the noiseless model of the same schedule)
+    class Trace(C.PlainSlots):
+        def __init__(self, slots, top):
+            super().__init__(slots, top)
+            self.ops = []
+
+        def rot(self, x, r):
+            self.ops.append(("ks", x.level))
+            return super().rot(x, r)
+
+        def mul(self, x, y):
+            self.ops.append(("ks", x.level))
+            return super().mul(x, y)
+
+        def mul_scalar(self, x, c):
+            self.ops.append(("rs", x.level))
+            return super().mul_scalar(x, c)
+
+        def mul_plain(self, x, key):
+            self.ops.append(("rs", x.level))
+            return super().mul_plain(x, key)
+
+    T = Trace(P.slots, P.L)
+    C.rank(T, T.fresh(np.zeros(W["N"])), W["N"], W["d_g"], W["d_f"])
+    top = P.L
+
+    def w_ks(l):
+        return P.beta(l) * (l + 1 + P.alpha)
+
+    samples = []
+    for s in range(warmup + steps):
+        t0 = time.perf_counter()
+        ckks.rotate(P, keys, ct, -W["N"])
+        t_rot = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        ckks.mul(P, keys, ct, ct)
+        t_mul = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        ckks.mul_scalar(P, ct, 0.5)
+        t_rs = time.perf_counter() - t0
+        t_ks = 0.5 * (t_rot + t_mul)
+        est = 0.0
+        for kind, l in T.ops:
+            est += t_ks * w_ks(l) / w_ks(top) if kind == "ks" else t_rs * (l + 1) / (top + 1)
+        if s >= warmup:
+            samples.append({"est_s": est, "sample_s": t_rot + t_mul + t_rs})
+    n_ks = sum(1 for k, _ in T.ops if k == "ks")
+    n_rs = len(T.ops) - n_ks
+    desc = (f"one rotation, one product (tensor+relinearise+rescale) and one scalar product of a 28-limb "
+            f"ciphertext per step on the oracle, scaled to the rank circuit's {n_ks} key switches and {n_rs} "
+            f"scalar/mask products by beta_l(l+1+alpha) and (l+1) per level")
+    return samples, desc
+
+
+def cpu_cores():
+    v = os.environ.get("OMP_NUM_THREADS")
+    return int(v) if v and v.isdigit() else (os.cpu_count() or 1)
+
+
+# ---------------------------------------------------------------------------
+# arms
+# ---------------------------------------------------------------------------
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return 0
+    from oracle import _lib
+    _lib.build()
+    samples, desc = oracle_rank_estimate(steps=args.steps, warmup=args.warmup)
+    est = [s["est_s"] for s in samples]
+    value = statistics.mean(est)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1000.0, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": value / PAPER_RANK128_S, "dtype": "u64", "data": "synthetic",
+        "config": workload_config({"impl_detail": "plain CPU RNS-CKKS oracle (C core, OpenMP over residues)"}),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_cuda(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2412_15126_gb300 import inputs, rankfhe
+
+    W = WORKLOAD
+    stream = torch.cuda.Stream()
+    ctx = rankfhe.Context(W["log_n"], W["n_limbs"], W["n_special"], W["digit_size"], W["log_scale"], W["log_q0"],
+                          W["log_special"], W["d_g"], W["d_f"], device=local, stream=stream.cuda_stream)
+    ctx.keygen(1000 + rank, W["N"])
+    n_in = args.warmup + args.steps
+    vecs = [inputs.gap_vector(W["N"], W["gap"], 1 + rank * 1000 + i) for i in range(n_in)]
+    cts = [ctx.encrypt(v, N=W["N"]) for v in vecs]
+    ctx.sync()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    # warm-up (also builds the cached plaintext masks)
+    for i in range(args.warmup):
+        ctx.rank(cts[i])
+    ctx.sync()
+
+    clocks = ClockSampler(gpu_id_for(local))
+    barrier()
+    torch.cuda.synchronize()
+    ctx.sync()
+    clocks.start()
+    time.sleep(0.2)
+    launches0 = ctx.launch_count()
+    ctx.profile_start(args.roofline_kernel)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    outs = []
+    torch.cuda.nvtx.range_push("timed")
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for i in range(args.steps):
+            outs.append(ctx.rank(cts[args.warmup + i]))
+        ev1.record(stream)
+    ev1.synchronize()
+    torch.cuda.nvtx.range_pop()
+    ctx.sync()
+    prof = ctx.profile_stop()
+    launches = ctx.launch_count() - launches0
+    clk = clocks.stop()
+    barrier()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    ms_per_step = elapsed_ms / args.steps
+
+    # correctness of the timed outputs (outside the timed region)
+    from oracle.circuits import brute_fractional_rank  # brute-force definition only
+    err = 0.0
+    for i in (0, args.steps - 1):
+        got = ctx.decrypt(outs[i])
+        err = max(err, float(np.max(np.abs(got - brute_fractional_rank(vecs[args.warmup + i])))))
+    for o in outs:
+        o.free()
+
+    # end to end through the C-ABI: pinned host ciphertexts in, result ciphertext out
+    e2e_steps = min(args.steps, 10)
+    host_in = []
+    for i in range(e2e_steps):
+        arr = cts[args.warmup + i].export()
+        pinned = torch.empty(arr.size, dtype=torch.int64, pin_memory=True)
+        pinned.numpy()[:] = arr.reshape(-1).view(np.int64)
+        host_in.append((pinned, arr.shape))
+    out_level = None
+    barrier()
+    ctx.sync()
+    t0 = time.perf_counter()
+    for pinned, shape in host_in:
+        g = ctx.ct_import(pinned.numpy().view(np.uint64).reshape(shape), shape[1] - 1, N=W["N"])
+        r = ctx.rank(g)
+        res = r.export()                      # device -> host read of the result
+        out_level = r.level
+        g.free()
+        r.free()
+    ctx.sync()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    n = 1 << W["log_n"]
+    h2d = 2 * W["n_limbs"] * n * 8
+    d2h = 2 * (out_level + 1) * n * 8 if out_level is not None else 0
+
+    peak, peak_kind = measured_peaks()
+    achieved = None
+    if prof["launches"] and prof["ms"] > 0:
+        achieved = prof["bytes"] / (prof["ms"] * 1e-3) / 1e9
+    traffic = committed_traffic(args.roofline_kernel)
+
+    line = None
+    if rank == 0:
+        value = ms_per_step / 1000.0
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            samples, desc = oracle_rank_estimate(steps=1)
+            cpu = {"value": samples[0]["est_s"], "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": desc}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": value / PAPER_RANK128_S, "dtype": "u64", "data": "synthetic",
+            "config": workload_config({"ranks_per_s_total": world * 1000.0 / ms_per_step,
+                                       "max_rank_error": err}),
+            "e2e": {"value": e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "roofline": {"bound": "hbm", "kernel": args.roofline_kernel, "achieved": achieved, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s",
+                         "frac": (achieved / peak) if achieved else None,
+                         "traffic": traffic,
+                         "algorithmic_bytes_per_launch": prof["bytes"] / max(prof["launches"], 1),
+                         "avg_launch_us": prof["ms"] * 1000.0 / max(prof["launches"], 1),
+                         "launches": prof["launches"]},
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "gpu_launches": launches,
+        }
+        print(json.dumps(line), flush=True)
+    for c in cts:
+        c.free()
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
+    ap.add_argument("--roofline-kernel", default="ks_inner")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_cuda(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

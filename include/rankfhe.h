@@ -1,0 +1,234 @@
+/*
+ * rankfhe - encrypted ranking, order statistics and sorting under RNS-CKKS on
+ * NVIDIA GB300 (sm_103a).  C ABI.
+ *
+ * The method is that of "Efficient Ranking, Order Statistics, and Sorting under
+ * CKKS" (Mazzone, Everts, Hahn, Peter; arxiv 2412.15126): all N x N pairwise
+ * comparisons of an encrypted vector are packed into the slots of one
+ * ciphertext by the ReplR / ReplC / TransR re-encoding (Sec. 2.3, Alg. 1, 10,
+ * 11), a composite sign polynomial gives the comparison matrix (Sec. 2.2), SumR
+ * gives the ranks (Alg. 3, Alg. 8) and the tie-correction offset makes them a
+ * permutation (Alg. 6).
+ *
+ * Conventions for every function:
+ *  - Return RK_OK on success; on failure a non-zero rk_status and a thread-local
+ *    message readable with rk_last_error().  No C++ exception crosses the ABI.
+ *  - Inputs are borrowed and never modified.  Every rk_ct* written through an
+ *    output argument is owned by the caller and released with rk_ct_free().
+ *  - Device work is ordered on the context's CUDA stream.  Functions that return
+ *    host-visible data (decrypt, export, moduli) synchronise that stream.
+ *  - A context is used by one host thread at a time.
+ *  - Ciphertexts live in device memory in the evaluation (NTT) domain as
+ *    64-bit residues, limb-major: [2][L+1][n] words, limbs 0..level in use.
+ *  - Canonical exchange form (import/export): coefficient domain, residues in
+ *    [0, q), little-endian uint64, layout [2][level+1][n] for a ciphertext.
+ */
+#ifndef RANKFHE_H
+#define RANKFHE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rk_ctx rk_ctx;
+typedef struct rk_ct rk_ct;
+
+typedef enum {
+    RK_OK = 0,
+    RK_EINVAL = 1,    /* bad argument (size, range, layout, level mismatch)            */
+    RK_ENOMEM = 2,    /* device or host allocation failed                               */
+    RK_EDEPTH = 3,    /* the circuit needs more levels than the ciphertext has left     */
+    RK_ETIMEOUT = 4,  /* a bounded device-side wait gave up                             */
+    RK_ECUDA = 5,     /* a CUDA runtime call failed (message has the CUDA error text)   */
+    RK_EFORMAT = 6,   /* malformed or truncated serialised data                         */
+    RK_ENOKEY = 7     /* a switching key (relinearisation or rotation) is missing      */
+} rk_status;
+
+/* Parameter set.  Moduli are derived deterministically from these sizes:
+ * q_0 = largest prime < 2^log_q0 with q = 1 mod 2n; q_L..q_1 chosen top down,
+ * q_l the unused prime = 1 mod 2n nearest floor(Delta_l^2 / 2^log_scale) (ties to
+ * the smaller) with Delta_L = 2^log_scale and Delta_{l-1} = Delta_l^2 / q_l;
+ * the n_special special primes are the largest unused primes < 2^log_special. */
+typedef struct {
+    uint32_t log_n;        /* ring degree n = 2^log_n (Sec. 2.1), 10..17                 */
+    uint32_t n_limbs;      /* number of primes in Q (L + 1)                              */
+    uint32_t n_special;    /* number of special primes alpha (hybrid key switching)      */
+    uint32_t digit_size;   /* limbs per key-switching digit                              */
+    uint32_t log_scale;    /* log2 of the top-level scale Delta_L                        */
+    uint32_t log_q0;       /* bit bound of q_0                                           */
+    uint32_t log_special;  /* bit bound of the special primes (<= 61)                    */
+    uint32_t d_g;          /* compositions of g in Cmp (Sec. 2.2)                         */
+    uint32_t d_f;          /* compositions of f in Cmp (Sec. 2.2)                         */
+} rk_params;
+
+/* Ciphertext slot layouts (Sec. 2.3 row-by-row encoding; slot q*N^2 + i*N + j is
+ * row i, column j of packed query q). */
+#define RK_LAYOUT_ROW 0u   /* vector in row 0: slots q*N^2 + j            */
+#define RK_LAYOUT_COL 1u   /* vector in column 0: slots q*N^2 + i*N       */
+
+/* Plaintext mask kinds (Sec. 2.3 MaskR/MaskC, Alg. 6, padding of Sec. 3.1). */
+#define RK_MASK_ROW0  1u   /* 1 on row 0 of each N x N block                           */
+#define RK_MASK_COL0  2u   /* 1 on column 0 of each block                              */
+#define RK_MASK_TIE   3u   /* 4*[j >= i] - 2 on each block (folded Alg. 6)             */
+#define RK_MASK_TRI   4u   /* [j >= i] on each block (Alg. 6 delta mask)               */
+#define RK_MASK_VALID 5u   /* 1 on rows and columns < n_real of each block (padding)   */
+
+/* Key kinds for rk_key_import. */
+#define RK_KEY_RELIN  1u
+#define RK_KEY_GALOIS 2u
+
+/* Flags for rk_rank. */
+#define RK_TIES_CORRECT 1u /* add the tie-correction offset (Alg. 6): ranks become a permutation */
+
+/* ---- context -------------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * (e.g. a PyTorch stream's handle) or NULL for a stream owned by the context.
+ * Builds the prime chain, NTT twiddle tables and basis-conversion constants.
+ * Errors: RK_EINVAL for out-of-range sizes, RK_ECUDA, RK_ENOMEM. */
+rk_status rk_ctx_create(const rk_params* params, int device, void* cuda_stream, rk_ctx** out);
+void rk_ctx_destroy(rk_ctx* ctx);
+
+/* The moduli q_0..q_L followed by p_0..p_{alpha-1}; *count receives L+1+alpha.
+ * Writes min(cap, count) words.  Errors: RK_EINVAL on NULL. */
+rk_status rk_ctx_moduli(const rk_ctx* ctx, uint64_t* out, size_t cap, size_t* count);
+/* The canonical scales Delta_0..Delta_L (doubles); writes min(cap, L+1). */
+rk_status rk_ctx_scales(const rk_ctx* ctx, double* out, size_t cap);
+/* Block until all work queued on the context stream has finished. */
+rk_status rk_sync(rk_ctx* ctx);
+/* Counters since creation: [key switches, rotations, ciphertext products, rescales]. */
+rk_status rk_ctx_counters(const rk_ctx* ctx, uint64_t out[4]);
+
+/* ---- keys ----------------------------------------------------------------- */
+
+/* Generate secret, public, relinearisation key and the rotation (Galois) keys
+ * the circuits need for every power-of-two length N <= max_len (Sec. 3.1: the
+ * rotations of ReplR, ReplC, TransR, SumR, SumC, TransC), on the device, from
+ * `seed` (SplitMix64 counter stream).  Errors: RK_EINVAL, RK_ENOMEM, RK_ECUDA. */
+rk_status rk_keygen(rk_ctx* ctx, uint64_t seed, uint32_t max_len);
+
+/* Add rotation keys for left rotations by r[i] slots (negative = right). */
+rk_status rk_keygen_rotations(rk_ctx* ctx, const int32_t* r, size_t count);
+
+/* Import a ternary secret s (n signed coefficients in {-1,0,1}). */
+rk_status rk_secret_import(rk_ctx* ctx, const int64_t* s, size_t n);
+
+/* Import a switching key made elsewhere (e.g. by a reference implementation).
+ * kind: RK_KEY_RELIN (galois ignored) or RK_KEY_GALOIS with its Galois element.
+ * coeffs: [beta_L][2][L+1+alpha][n] words, coefficient domain, residues in
+ * [0, q) in prime order q_0..q_L, p_0..p_{alpha-1}; entry [j][0] is b_j, [j][1]
+ * is a_j with b_j = -a_j s + e_j + P E_j s' (E_j the CRT idempotent of digit j).
+ * Errors: RK_EINVAL if words does not match, RK_ENOMEM. */
+rk_status rk_key_import(rk_ctx* ctx, uint32_t kind, uint64_t galois, const uint64_t* coeffs, size_t words);
+
+/* Galois element of a left rotation by r slots: 5^r mod 2n. */
+uint64_t rk_galois_left(const rk_ctx* ctx, int32_t r);
+
+/* ---- encoding ---------------------------------------------------------------- */
+
+/* Override the unscaled encoding (n doubles: the real polynomial whose slot
+ * values are the mask) used for mask `kind` at (N, Q, n_real).  By default the
+ * library computes it with its own FFT; importing a table from another
+ * implementation makes plaintext products bit-identical to it.
+ * Errors: RK_EINVAL on a bad kind or length. */
+rk_status rk_encoding_import(rk_ctx* ctx, uint32_t kind, uint32_t N, uint32_t Q, uint32_t n_real,
+                             const double* u, size_t n);
+
+/* ---- client operations ------------------------------------------------------ */
+
+/* Encode and encrypt (public key) `count` values into row 0 of packed queries:
+ * value i goes to query i / n_real, column i % n_real.  N is the padded length
+ * (a power of two >= n_real with Q*N*N <= n/2), Q the number of packed queries.
+ * Values must lie in [0, 1) (the comparator's domain, Sec. 2.2): else RK_EINVAL. */
+rk_status rk_encrypt(rk_ctx* ctx, const double* v, uint32_t count, uint32_t N, uint32_t Q,
+                     uint32_t n_real, rk_ct** out);
+
+/* Decrypt and decode all n/2 slots (real parts) into out[0..cap). */
+rk_status rk_decrypt_slots(rk_ctx* ctx, const rk_ct* ct, double* out, size_t cap);
+
+/* Decrypt the result vector: row 0 (or column 0 for RK_LAYOUT_COL) of each packed
+ * query, n_real values per query, Q*n_real values written when cap allows.
+ * *n_out receives Q*n_real. */
+rk_status rk_decrypt(rk_ctx* ctx, const rk_ct* ct, double* out, size_t cap, uint32_t* n_out);
+
+/* Import a ciphertext in canonical form ([2][level+1][n] coefficient-domain
+ * residues) with its vector metadata.  Errors: RK_EINVAL. */
+rk_status rk_ct_import(rk_ctx* ctx, const uint64_t* coeffs, uint32_t level, uint32_t N, uint32_t Q,
+                       uint32_t n_real, rk_ct** out);
+/* Export in canonical form; cap in words must be >= 2*(level+1)*n. */
+rk_status rk_ct_export(const rk_ct* ct, uint64_t* coeffs, size_t cap);
+uint32_t rk_ct_level(const rk_ct* ct);
+void rk_ct_free(rk_ct* ct);
+
+/* ---- homomorphic operations (Sec. 2.1) --------------------------------------- */
+
+/* Left rotation by r slots (r < 0: right rotation by -r): slot s <- slot s + r.
+ * The automorphism X -> X^(5^r) is applied to the lifted digits of the key switch.
+ * Errors: RK_ENOKEY if the rotation key is missing. */
+rk_status rk_rotate(rk_ctx* ctx, const rk_ct* in, int32_t r, rk_ct** out);
+/* Several rotations of one ciphertext sharing one ModUp (hoisting). */
+rk_status rk_rotate_many(rk_ctx* ctx, const rk_ct* in, const int32_t* r, uint32_t k, rk_ct** outs);
+rk_status rk_add(rk_ctx* ctx, const rk_ct* a, const rk_ct* b, rk_ct** out);
+rk_status rk_sub(rk_ctx* ctx, const rk_ct* a, const rk_ct* b, rk_ct** out);
+/* Add the constant v to every slot (v * Delta_level rounded half away from zero). */
+rk_status rk_add_const(rk_ctx* ctx, const rk_ct* a, double v, rk_ct** out);
+/* Product with relinearisation and rescale: out at level-1. */
+rk_status rk_mul(rk_ctx* ctx, const rk_ct* a, const rk_ct* b, rk_ct** out);
+/* Product with the constant v, rescaled: out at level-1. */
+rk_status rk_mul_scalar(rk_ctx* ctx, const rk_ct* a, double v, rk_ct** out);
+/* Product with a mask plaintext (RK_MASK_*), rescaled: out at level-1. */
+rk_status rk_mul_mask(rk_ctx* ctx, const rk_ct* a, uint32_t kind, rk_ct** out);
+/* Drop one prime by rounding division (rescale); out at level-1, scale divided by q_level. */
+rk_status rk_rescale(rk_ctx* ctx, const rk_ct* a, rk_ct** out);
+
+/* ---- circuits (Sec. 3-4) ------------------------------------------------------ */
+
+/* Rank (Alg. 3): fractional ranks of the vector in row 0 of `in` (fresh, top
+ * level), in row 0 of the output.  flags: RK_TIES_CORRECT adds the tie-correction
+ * offset of Alg. 6.  Errors: RK_EDEPTH if the parameters lack the levels,
+ * RK_ENOKEY, RK_EINVAL. */
+rk_status rk_rank(rk_ctx* ctx, const rk_ct* in, uint32_t flags, rk_ct** out);
+
+/* Comparison matrix (Alg. 3 lines 1-3): C = Cmp(ReplR(V), ReplC(TransR(V))), slot
+ * q*N^2 + i*N + j holding Cmp(v_j, v_i) of Eq. 1 approximated by the composite
+ * (f^d_f o g^d_g)(x)/2 + 1/2 of Sec. 2.2.  Errors as rk_rank. */
+rk_status rk_compare_matrix(rk_ctx* ctx, const rk_ct* in, rk_ct** out);
+
+/* Ranks of `count` ciphertexts (each its own query set), one circuit per input,
+ * all queued on the context stream. */
+rk_status rk_rank_batch(rk_ctx* ctx, const rk_ct* const* in, size_t count, uint32_t flags, rk_ct** out);
+
+/* ---- raw kernels on device buffers (for parity tests and composition) ------- */
+
+/* Forward / inverse negacyclic NTT of `limbs` residue polynomials stored
+ * contiguously at device address d_data (limb t uses prime id first_prime + t;
+ * prime ids index q_0..q_L, p_0..).  Forward output order: index i holds the
+ * evaluation at psi^(2 brev(i) + 1).  Inputs must be in [0, q); outputs are. */
+rk_status rk_ntt_forward(rk_ctx* ctx, uint64_t* d_data, uint32_t limbs, uint32_t first_prime);
+rk_status rk_ntt_inverse(rk_ctx* ctx, uint64_t* d_data, uint32_t limbs, uint32_t first_prime);
+
+/* ---- measurement ------------------------------------------------------------- */
+
+/* Time every launch of one kernel kind with CUDA events on the context stream:
+ * "ntt_fwd", "ntt_inv", "modup", "ks_inner", "moddown_conv", "ks_combine",
+ * "tensor", "rescale", "pointwise", "client"; NULL or "" stops timing.  Resets the
+ * accumulators.  Errors: RK_EINVAL for an unknown name. */
+rk_status rk_profile_start(rk_ctx* ctx, const char* kind);
+/* Synchronise and report the timed launches since rk_profile_start:
+ * out[0] total milliseconds, out[1] launches (an NTT counts its two passes as one),
+ * out[2] algorithmic bytes (each input word read once, each output word written
+ * once), out[3] modular products.  Stops timing. */
+rk_status rk_profile_stop(rk_ctx* ctx, double out[4]);
+/* Number of kernels this context has launched since creation. */
+uint64_t rk_launch_count(const rk_ctx* ctx);
+
+/* The thread-local message of the last failure on this thread. */
+const char* rk_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RANKFHE_H */

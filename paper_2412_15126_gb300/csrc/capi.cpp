@@ -1,0 +1,448 @@
+// C-ABI entry points (include/rankfhe.h): argument checks, exception-to-status
+// translation and handle ownership.  All compute is in the CUDA kernels.
+#include <cstring>
+
+#include "kernels.cuh"
+
+void ctx_build(rk_ctx* c, const rk_params* p, int device, void* stream);
+void ctx_release(rk_ctx* c);
+rk_ct* circuit_rank(rk_ctx* c, const rk_ct* in, uint32_t flags);
+rk_ct* circuit_compare_matrix(rk_ctx* c, const rk_ct* in);
+void circuit_rotations(uint32_t N, std::vector<int>& out);
+
+namespace {
+thread_local std::string g_last_error;
+
+template <class F>
+rk_status guard(F&& f) {
+    try {
+        f();
+        return RK_OK;
+    } catch (const rk_error& e) {
+        g_last_error = e.what();
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        g_last_error = "host allocation failed";
+        return RK_ENOMEM;
+    } catch (const std::exception& e) {
+        g_last_error = e.what();
+        return RK_EINVAL;
+    }
+}
+
+void need(const void* p, const char* what) {
+    if (!p) throw rk_error(RK_EINVAL, std::string(what) + " is NULL");
+}
+
+void same_ctx(const rk_ctx* c, const rk_ct* a) {
+    need(a, "ciphertext");
+    if (a->ctx != c) throw rk_error(RK_EINVAL, "ciphertext belongs to another context");
+}
+
+void set_device(rk_ctx* c) { RK_CUDA(cudaSetDevice(c->device)); }
+
+// Check for a launch error after queuing kernels.
+void check_launch() {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) throw rk_error(RK_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+}
+}  // namespace
+
+extern "C" {
+
+const char* rk_last_error(void) { return g_last_error.c_str(); }
+
+rk_status rk_ctx_create(const rk_params* params, int device, void* cuda_stream, rk_ctx** out) {
+    return guard([&] {
+        need(out, "out");
+        *out = nullptr;
+        rk_ctx* c = new rk_ctx();
+        try {
+            ctx_build(c, params, device, cuda_stream);
+        } catch (...) {
+            ctx_release(c);
+            delete c;
+            throw;
+        }
+        *out = c;
+    });
+}
+
+void rk_ctx_destroy(rk_ctx* ctx) {
+    if (!ctx) return;
+    ctx_release(ctx);
+    delete ctx;
+}
+
+rk_status rk_ctx_moduli(const rk_ctx* ctx, uint64_t* out, size_t cap, size_t* count) {
+    return guard([&] {
+        need(ctx, "ctx");
+        if (count) *count = ctx->primes.size();
+        if (out)
+            for (size_t i = 0; i < ctx->primes.size() && i < cap; i++) out[i] = ctx->primes[i];
+    });
+}
+
+rk_status rk_ctx_scales(const rk_ctx* ctx, double* out, size_t cap) {
+    return guard([&] {
+        need(ctx, "ctx");
+        need(out, "out");
+        for (size_t i = 0; i < ctx->scales.size() && i < cap; i++) out[i] = ctx->scales[i];
+    });
+}
+
+rk_status rk_sync(rk_ctx* ctx) {
+    return guard([&] {
+        need(ctx, "ctx");
+        RK_CUDA(cudaStreamSynchronize(ctx->stream));
+    });
+}
+
+rk_status rk_ctx_counters(const rk_ctx* ctx, uint64_t out[4]) {
+    return guard([&] {
+        need(ctx, "ctx");
+        need(out, "out");
+        out[0] = ctx->n_ks;
+        out[1] = ctx->n_rot;
+        out[2] = ctx->n_mul;
+        out[3] = ctx->n_rescale;
+    });
+}
+
+rk_status rk_keygen(rk_ctx* ctx, uint64_t seed, uint32_t max_len) {
+    return guard([&] {
+        need(ctx, "ctx");
+        set_device(ctx);
+        RK_REQUIRE((size_t)max_len * max_len <= (size_t)ctx->n / 2, RK_EINVAL, "max_len^2 exceeds the slots");
+        std::vector<int> rots;
+        for (uint32_t N = 2; N <= max_len; N <<= 1) circuit_rotations(N, rots);
+        keys_generate(ctx, seed, rots);
+        check_launch();
+    });
+}
+
+rk_status rk_keygen_rotations(rk_ctx* ctx, const int32_t* r, size_t count) {
+    return guard([&] {
+        need(ctx, "ctx");
+        need(r, "r");
+        set_device(ctx);
+        keys_add_rotations(ctx, std::vector<int>(r, r + count));
+        check_launch();
+    });
+}
+
+rk_status rk_secret_import(rk_ctx* ctx, const int64_t* s, size_t n) {
+    return guard([&] {
+        need(ctx, "ctx");
+        need(s, "s");
+        set_device(ctx);
+        secret_import(ctx, s, n);
+        check_launch();
+    });
+}
+
+rk_status rk_key_import(rk_ctx* ctx, uint32_t kind, uint64_t galois, const uint64_t* coeffs, size_t words) {
+    return guard([&] {
+        need(ctx, "ctx");
+        need(coeffs, "coeffs");
+        set_device(ctx);
+        key_import(ctx, kind, galois, coeffs, words);
+        check_launch();
+    });
+}
+
+uint64_t rk_galois_left(const rk_ctx* ctx, int32_t r) { return ctx ? galois_left(ctx, r) : 0; }
+
+rk_status rk_encoding_import(rk_ctx* ctx, uint32_t kind, uint32_t N, uint32_t Q, uint32_t n_real, const double* u, size_t n) {
+    return guard([&] {
+        need(ctx, "ctx");
+        need(u, "u");
+        RK_REQUIRE(n == (size_t)ctx->n, RK_EINVAL, "encoding length must be n");
+        RK_REQUIRE(kind >= RK_MASK_ROW0 && kind <= RK_MASK_VALID, RK_EINVAL, "unknown mask kind");
+        const uint32_t nr = kind == RK_MASK_VALID ? n_real : 0;
+        ctx->encodings[std::make_tuple(kind, N, Q, nr)] = std::vector<double>(u, u + n);
+        for (auto it = ctx->plain_cache.begin(); it != ctx->plain_cache.end();) {
+            if (std::get<0>(it->first) == kind && std::get<1>(it->first) == N && std::get<2>(it->first) == Q &&
+                std::get<3>(it->first) == nr) {
+                cudaFree(it->second);
+                it = ctx->plain_cache.erase(it);
+            } else {
+                ++it;
+            }
+        }
+    });
+}
+
+rk_status rk_encrypt(rk_ctx* ctx, const double* v, uint32_t count, uint32_t N, uint32_t Q, uint32_t n_real, rk_ct** out) {
+    return guard([&] {
+        need(ctx, "ctx");
+        need(out, "out");
+        need(v, "v");
+        set_device(ctx);
+        *out = encrypt_values(ctx, v, count, N, Q, n_real);
+        check_launch();
+    });
+}
+
+rk_status rk_decrypt_slots(rk_ctx* ctx, const rk_ct* ct, double* out, size_t cap) {
+    return guard([&] {
+        need(ctx, "ctx");
+        same_ctx(ctx, ct);
+        need(out, "out");
+        set_device(ctx);
+        std::vector<double> s;
+        decrypt_slots(ctx, ct, s);
+        for (size_t i = 0; i < s.size() && i < cap; i++) out[i] = s[i];
+    });
+}
+
+rk_status rk_decrypt(rk_ctx* ctx, const rk_ct* ct, double* out, size_t cap, uint32_t* n_out) {
+    return guard([&] {
+        need(ctx, "ctx");
+        same_ctx(ctx, ct);
+        set_device(ctx);
+        std::vector<double> s;
+        decrypt_slots(ctx, ct, s);
+        const size_t NN = (size_t)ct->N * ct->N;
+        size_t w = 0;
+        for (uint32_t q = 0; q < ct->Q; q++)
+            for (uint32_t i = 0; i < ct->n_real; i++) {
+                size_t slot = q * NN + (ct->layout == RK_LAYOUT_COL ? (size_t)i * ct->N : i);
+                if (out && w < cap) out[w] = s[slot];
+                w++;
+            }
+        if (n_out) *n_out = (uint32_t)w;
+    });
+}
+
+rk_status rk_ct_import(rk_ctx* ctx, const uint64_t* coeffs, uint32_t level, uint32_t N, uint32_t Q, uint32_t n_real,
+                       rk_ct** out) {
+    return guard([&] {
+        need(ctx, "ctx");
+        need(coeffs, "coeffs");
+        need(out, "out");
+        RK_REQUIRE(N >= 1 && (N & (N - 1)) == 0 && n_real >= 1 && n_real <= N && Q >= 1, RK_EINVAL, "bad vector metadata");
+        set_device(ctx);
+        rk_ct* ct = ct_import(ctx, coeffs, (int)level);
+        ct->N = N;
+        ct->Q = Q;
+        ct->n_real = n_real;
+        ct->layout = RK_LAYOUT_ROW;
+        *out = ct;
+    });
+}
+
+rk_status rk_ct_export(const rk_ct* ct, uint64_t* coeffs, size_t cap) {
+    return guard([&] {
+        need(ct, "ct");
+        need(coeffs, "coeffs");
+        rk_ctx* c = ct->ctx;
+        RK_REQUIRE(cap >= (size_t)2 * (ct->level + 1) * c->n, RK_EINVAL, "export buffer too small");
+        set_device(c);
+        ct_export(c, ct, coeffs);
+    });
+}
+
+uint32_t rk_ct_level(const rk_ct* ct) { return ct ? (uint32_t)ct->level : 0; }
+
+void rk_ct_free(rk_ct* ct) {
+    if (ct) ct_free(ct);
+}
+
+#define RK_UNARY_OUT(ctx, a, out, level_expr, body) \
+    need(ctx, "ctx");                                 \
+    same_ctx(ctx, a);                                 \
+    need(out, "out");                                 \
+    set_device(ctx);                                  \
+    rk_ct* o = ct_clone_meta(a, (level_expr));        \
+    try {                                             \
+        body;                                         \
+        check_launch();                               \
+    } catch (...) {                                   \
+        ct_free(o);                                   \
+        throw;                                        \
+    }                                                 \
+    *out = o;
+
+rk_status rk_rotate(rk_ctx* ctx, const rk_ct* in, int32_t r, rk_ct** out) {
+    return guard([&] {
+        RK_UNARY_OUT(ctx, in, out, in->level, {
+            int rr = r;
+            rk_ct* outs[1] = {o};
+            ev_rotate_many(ctx, in, &rr, 1, outs);
+        })
+    });
+}
+
+rk_status rk_rotate_many(rk_ctx* ctx, const rk_ct* in, const int32_t* r, uint32_t k, rk_ct** outs) {
+    return guard([&] {
+        need(ctx, "ctx");
+        same_ctx(ctx, in);
+        need(r, "r");
+        need(outs, "outs");
+        set_device(ctx);
+        std::vector<rk_ct*> o(k);
+        std::vector<int> rr(r, r + k);
+        for (uint32_t i = 0; i < k; i++) o[i] = ct_clone_meta(in, in->level);
+        try {
+            ev_rotate_many(ctx, in, rr.data(), (int)k, o.data());
+            check_launch();
+        } catch (...) {
+            for (auto* p : o) ct_free(p);
+            throw;
+        }
+        for (uint32_t i = 0; i < k; i++) outs[i] = o[i];
+    });
+}
+
+rk_status rk_add(rk_ctx* ctx, const rk_ct* a, const rk_ct* b, rk_ct** out) {
+    return guard([&] {
+        same_ctx(ctx, b);
+        RK_UNARY_OUT(ctx, a, out, a->level, ev_add(ctx, a, b, o))
+    });
+}
+
+rk_status rk_sub(rk_ctx* ctx, const rk_ct* a, const rk_ct* b, rk_ct** out) {
+    return guard([&] {
+        same_ctx(ctx, b);
+        RK_UNARY_OUT(ctx, a, out, a->level, ev_sub(ctx, a, b, o))
+    });
+}
+
+rk_status rk_add_const(rk_ctx* ctx, const rk_ct* a, double v, rk_ct** out) {
+    return guard([&] { RK_UNARY_OUT(ctx, a, out, a->level, ev_add_const(ctx, a, v, o)) });
+}
+
+rk_status rk_mul(rk_ctx* ctx, const rk_ct* a, const rk_ct* b, rk_ct** out) {
+    return guard([&] {
+        same_ctx(ctx, b);
+        RK_UNARY_OUT(ctx, a, out, a->level, ev_mul(ctx, a, b, o))
+    });
+}
+
+rk_status rk_mul_scalar(rk_ctx* ctx, const rk_ct* a, double v, rk_ct** out) {
+    return guard([&] { RK_UNARY_OUT(ctx, a, out, a->level, ev_mul_scalar(ctx, a, v, o)) });
+}
+
+rk_status rk_mul_mask(rk_ctx* ctx, const rk_ct* a, uint32_t kind, rk_ct** out) {
+    return guard([&] {
+        RK_REQUIRE(kind >= RK_MASK_ROW0 && kind <= RK_MASK_VALID, RK_EINVAL, "unknown mask kind");
+        RK_UNARY_OUT(ctx, a, out, a->level,
+                     ev_mul_plain(ctx, a, kind, a->N, a->Q, kind == RK_MASK_VALID ? a->n_real : 0, o))
+    });
+}
+
+rk_status rk_rescale(rk_ctx* ctx, const rk_ct* a, rk_ct** out) {
+    return guard([&] {
+        RK_UNARY_OUT(ctx, a, out, a->level, {
+            ev_copy(ctx, a, o);
+            ev_rescale_inplace(ctx, o);
+        })
+    });
+}
+
+rk_status rk_rank(rk_ctx* ctx, const rk_ct* in, uint32_t flags, rk_ct** out) {
+    return guard([&] {
+        need(ctx, "ctx");
+        same_ctx(ctx, in);
+        need(out, "out");
+        set_device(ctx);
+        *out = circuit_rank(ctx, in, flags);
+        check_launch();
+    });
+}
+
+rk_status rk_compare_matrix(rk_ctx* ctx, const rk_ct* in, rk_ct** out) {
+    return guard([&] {
+        need(ctx, "ctx");
+        same_ctx(ctx, in);
+        need(out, "out");
+        set_device(ctx);
+        *out = circuit_compare_matrix(ctx, in);
+        check_launch();
+    });
+}
+
+rk_status rk_rank_batch(rk_ctx* ctx, const rk_ct* const* in, size_t count, uint32_t flags, rk_ct** out) {
+    return guard([&] {
+        need(ctx, "ctx");
+        need(in, "in");
+        need(out, "out");
+        set_device(ctx);
+        std::vector<rk_ct*> res;
+        try {
+            for (size_t i = 0; i < count; i++) {
+                same_ctx(ctx, in[i]);
+                res.push_back(circuit_rank(ctx, in[i], flags));
+            }
+            check_launch();
+        } catch (...) {
+            for (auto* p : res) ct_free(p);
+            throw;
+        }
+        for (size_t i = 0; i < count; i++) out[i] = res[i];
+    });
+}
+
+rk_status rk_profile_start(rk_ctx* ctx, const char* kind) {
+    return guard([&] {
+        need(ctx, "ctx");
+        Profiler& p = ctx->prof;
+        p.target = -1;
+        p.used = 0;
+        p.bytes = p.ops = 0;
+        p.timed = 0;
+        if (!kind || !kind[0]) return;
+        for (int k = 0; k < KK_COUNT; k++)
+            if (std::strcmp(kind, kKernelKindNames[k]) == 0) p.target = k;
+        RK_REQUIRE(p.target >= 0, RK_EINVAL, std::string("unknown kernel kind ") + kind);
+    });
+}
+
+rk_status rk_profile_stop(rk_ctx* ctx, double out[4]) {
+    return guard([&] {
+        need(ctx, "ctx");
+        need(out, "out");
+        set_device(ctx);
+        Profiler& p = ctx->prof;
+        RK_CUDA(cudaStreamSynchronize(ctx->stream));
+        double ms = 0;
+        for (size_t i = 0; i + 1 < p.used; i += 2) {
+            float t = 0;
+            RK_CUDA(cudaEventElapsedTime(&t, p.ev[i], p.ev[i + 1]));
+            ms += t;
+        }
+        out[0] = ms;
+        out[1] = (double)p.timed;
+        out[2] = p.bytes;
+        out[3] = p.ops;
+        p.target = -1;
+        p.used = 0;
+    });
+}
+
+uint64_t rk_launch_count(const rk_ctx* ctx) { return ctx ? ctx->prof.launches : 0; }
+
+rk_status rk_ntt_forward(rk_ctx* ctx, uint64_t* d_data, uint32_t limbs, uint32_t first_prime) {
+    return guard([&] {
+        need(ctx, "ctx");
+        need(d_data, "d_data");
+        RK_REQUIRE(first_prime + limbs <= (uint32_t)ctx->n_primes, RK_EINVAL, "prime range out of bounds");
+        set_device(ctx);
+        launch_ntt_forward(ctx->env, LimbSet{(u64*)d_data, 0, 1, (int)limbs, (int)limbs, (int)first_prime, 0}, ctx->stream);
+        check_launch();
+    });
+}
+
+rk_status rk_ntt_inverse(rk_ctx* ctx, uint64_t* d_data, uint32_t limbs, uint32_t first_prime) {
+    return guard([&] {
+        need(ctx, "ctx");
+        need(d_data, "d_data");
+        RK_REQUIRE(first_prime + limbs <= (uint32_t)ctx->n_primes, RK_EINVAL, "prime range out of bounds");
+        set_device(ctx);
+        launch_ntt_inverse(ctx->env, LimbSet{(u64*)d_data, 0, 1, (int)limbs, (int)limbs, (int)first_prime, 0}, ctx->stream);
+        check_launch();
+    });
+}
+
+}  // extern "C"

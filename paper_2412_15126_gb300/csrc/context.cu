@@ -1,0 +1,340 @@
+// Context creation: prime chain, canonical scales, NTT twiddles and the constant
+// tables of the RNS basis conversions (Sec. 2.1 scheme substrate).
+#include <cmath>
+#include <cstring>
+
+#include "kernels.cuh"
+
+// ---------------------------------------------------------------------------
+// Host number theory
+// ---------------------------------------------------------------------------
+u64 h_mulmod(u64 a, u64 b, u64 q) { return (u64)(((u128)a * b) % q); }
+
+u64 h_powmod(u64 a, u64 e, u64 q) {
+    u64 r = 1 % q;
+    a %= q;
+    while (e) {
+        if (e & 1) r = h_mulmod(r, a, q);
+        a = h_mulmod(a, a, q);
+        e >>= 1;
+    }
+    return r;
+}
+
+u64 h_invmod(u64 a, u64 q) { return h_powmod(a, q - 2, q); }
+
+static bool h_is_prime(u64 n) {
+    if (n < 2) return false;
+    static const u64 small[12] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37};
+    for (u64 p : small) {
+        if (n == p) return true;
+        if (n % p == 0) return false;
+    }
+    u64 d = n - 1;
+    int s = 0;
+    while (!(d & 1)) {
+        d >>= 1;
+        s++;
+    }
+    for (u64 a : small) {
+        u64 x = h_powmod(a, d, n);
+        if (x == 1 || x == n - 1) continue;
+        bool witness = true;
+        for (int r = 1; r < s && witness; r++) {
+            x = h_mulmod(x, x, n);
+            if (x == n - 1) witness = false;
+        }
+        if (witness) return false;
+    }
+    return true;
+}
+
+int64_t round_half_away(double x) { return (int64_t)llround(x); }
+
+static bool in_list(const std::vector<u64>& v, u64 x) {
+    for (u64 y : v)
+        if (y == x) return true;
+    return false;
+}
+
+// largest prime < bound with p = 1 mod m, not in `used`
+static u64 largest_prime_below(u64 bound, u64 m, const std::vector<u64>& used) {
+    u64 k = (bound - 2) / m;
+    for (;; k--) {
+        u64 c = k * m + 1;
+        if (!in_list(used, c) && h_is_prime(c)) return c;
+    }
+}
+
+// prime p = 1 mod m nearest to c (ties to the smaller), not in `used`
+static u64 nearest_prime(u64 c, u64 m, const std::vector<u64>& used) {
+    u64 lo = ((c - 1) / m) * m + 1;
+    u64 hi = lo + m;
+    for (;;) {
+        if (c - lo <= hi - c) {
+            if (lo > 2 && !in_list(used, lo) && h_is_prime(lo)) return lo;
+            lo -= m;
+        } else {
+            if (!in_list(used, hi) && h_is_prime(hi)) return hi;
+            hi += m;
+        }
+    }
+}
+
+// primitive 2n-th root of unity mod q: c^((q-1)/2n) of the first c = 2, 3, ... of order 2n
+static u64 root_2n(u64 q, u64 two_n) {
+    for (u64 c = 2;; c++) {
+        u64 w = h_powmod(c, (q - 1) / two_n, q);
+        if (h_powmod(w, two_n / 2, q) == q - 1) return w;
+    }
+}
+
+static u64 shoup_of(u64 w, u64 q) { return (u64)(((u128)w << 64) / q); }
+
+static u64 mont_qinv(u64 q) {  // q^-1 mod 2^64 by Newton iteration
+    u64 x = q;                 // correct to 3 bits for odd q
+    for (int i = 0; i < 6; i++) x *= 2 - q * x;
+    return x;
+}
+
+static int bitrev(int x, int bits) {
+    int r = 0;
+    for (int i = 0; i < bits; i++) r |= ((x >> i) & 1) << (bits - 1 - i);
+    return r;
+}
+
+u64* rk_ctx::scratch(size_t words) {
+    if (words > scratch_words) {
+        RK_CUDA(cudaStreamSynchronize(stream));
+        if (d_scratch) RK_CUDA(cudaFree(d_scratch));
+        d_scratch = nullptr;
+        RK_CUDA(cudaMalloc((void**)&d_scratch, words * 8));
+        scratch_words = words;
+    }
+    return d_scratch;
+}
+
+static void validate(const rk_params* p) {
+    RK_REQUIRE(p, RK_EINVAL, "params is NULL");
+    RK_REQUIRE(p->log_n >= 10 && p->log_n <= 17, RK_EINVAL, "log_n must be in [10, 17]");
+    RK_REQUIRE(p->n_limbs >= 1 && p->n_special >= 1 && p->n_special <= RK_MAX_SPECIAL, RK_EINVAL, "bad limb counts");
+    RK_REQUIRE(p->n_limbs + p->n_special <= RK_MAX_PRIMES, RK_EINVAL, "too many primes");
+    RK_REQUIRE(p->digit_size >= 1 && p->digit_size <= RK_MAX_DIGIT, RK_EINVAL, "digit_size must be in [1, 8]");
+    RK_REQUIRE((p->n_limbs + p->digit_size - 1) / p->digit_size <= 16, RK_EINVAL, "at most 16 key-switching digits");
+    RK_REQUIRE(p->log_scale >= 20 && p->log_scale <= 58, RK_EINVAL, "log_scale must be in [20, 58]");
+    RK_REQUIRE(p->log_q0 >= 20 && p->log_q0 <= 61, RK_EINVAL, "log_q0 must be in [20, 61]");
+    RK_REQUIRE(p->log_special >= 20 && p->log_special <= 61, RK_EINVAL, "log_special must be in [20, 61]");
+}
+
+void ctx_build(rk_ctx* c, const rk_params* p, int device, void* stream) {
+    validate(p);
+    c->prm = *p;
+    c->device = device;
+    RK_CUDA(cudaSetDevice(device));
+    if (stream) {
+        c->stream = (cudaStream_t)stream;
+        c->own_stream = false;
+    } else {
+        RK_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+        c->own_stream = true;
+    }
+    {   // keep freed stream-ordered allocations in the pool
+        cudaMemPool_t pool;
+        RK_CUDA(cudaDeviceGetDefaultMemPool(&pool, device));
+        uint64_t thr = UINT64_MAX;
+        RK_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+    }
+    c->log_n = (int)p->log_n;
+    c->n = 1 << c->log_n;
+    c->L = (int)p->n_limbs - 1;
+    c->alpha = (int)p->n_special;
+    c->dsize = (int)p->digit_size;
+    c->n_primes = c->L + 1 + c->alpha;
+    const u64 m = 2ull * (u64)c->n;
+
+    // ---- prime chain and canonical scales ----
+    std::vector<u64> used;
+    std::vector<u64> q(c->L + 1);
+    q[0] = largest_prime_below(1ull << p->log_q0, m, used);
+    used.push_back(q[0]);
+    std::vector<double> sc(c->L + 1);
+    const double two_ls = std::ldexp(1.0, (int)p->log_scale);
+    sc[c->L] = two_ls;
+    for (int l = c->L; l >= 1; l--) {
+        volatile double t = sc[l] * sc[l];
+        double target = t / two_ls;
+        u64 ql = nearest_prime((u64)std::floor(target), m, used);
+        used.push_back(ql);
+        q[l] = ql;
+        volatile double sq = sc[l] * sc[l];
+        sc[l - 1] = sq / (double)ql;
+    }
+    std::vector<u64> sp;
+    u64 bound = 1ull << p->log_special;
+    for (int k = 0; k < c->alpha; k++) {
+        u64 pk = largest_prime_below(bound, m, used);
+        used.push_back(pk);
+        sp.push_back(pk);
+        bound = pk;
+    }
+    c->primes = q;
+    c->primes.insert(c->primes.end(), sp.begin(), sp.end());
+    c->scales = sc;
+    for (u64 x : c->primes) RK_REQUIRE(x < (1ull << 61), RK_EINVAL, "prime above 2^61");
+
+    // ---- per-prime constants ----
+    const int NP = c->n_primes, n = c->n;
+    c->h_pc.resize(NP);
+    for (int i = 0; i < NP; i++) {
+        u64 qi = c->primes[i];
+        PrimeConst& P = c->h_pc[i];
+        P.q = qi;
+        P.qinv = mont_qinv(qi);
+        P.r_mod = (u64)(((u128)1 << 64) % qi);
+        P.r2 = h_mulmod(P.r_mod, P.r_mod, qi);
+        P.r_shoup = shoup_of(P.r_mod, qi);
+        P.ninv = h_invmod((u64)n % qi, qi);
+        P.ninv_shoup = shoup_of(P.ninv, qi);
+        P.one_shoup = shoup_of(1, qi);
+    }
+    RK_CUDA(cudaMalloc((void**)&c->d_pc, NP * sizeof(PrimeConst)));
+    RK_CUDA(cudaMemcpy(c->d_pc, c->h_pc.data(), NP * sizeof(PrimeConst), cudaMemcpyHostToDevice));
+
+    // ---- twiddles: psi^brev(i), psi^-brev(i) and Shoup companions ----
+    std::vector<u64> tw((size_t)4 * NP * n);
+    for (int i = 0; i < NP; i++) {
+        u64 qi = c->primes[i];
+        u64 psi = root_2n(qi, m), ipsi = h_invmod(psi, qi);
+        std::vector<u64> pw(n), ipw(n);
+        pw[0] = ipw[0] = 1;
+        for (int k = 1; k < n; k++) {
+            pw[k] = h_mulmod(pw[k - 1], psi, qi);
+            ipw[k] = h_mulmod(ipw[k - 1], ipsi, qi);
+        }
+        u64* T0 = tw.data() + ((size_t)0 * NP + i) * n;
+        u64* T1 = tw.data() + ((size_t)1 * NP + i) * n;
+        u64* T2 = tw.data() + ((size_t)2 * NP + i) * n;
+        u64* T3 = tw.data() + ((size_t)3 * NP + i) * n;
+        for (int k = 0; k < n; k++) {
+            int r = bitrev(k, c->log_n);
+            T0[k] = pw[r];
+            T1[k] = shoup_of(pw[r], qi);
+            T2[k] = ipw[r];
+            T3[k] = shoup_of(ipw[r], qi);
+        }
+    }
+    RK_CUDA(cudaMalloc((void**)&c->d_tw, tw.size() * 8));
+    RK_CUDA(cudaMemcpy(c->d_tw, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice));
+
+    // ---- basis conversion constants ----
+    const int L = c->L, A = c->alpha, DS = c->dsize, T = L + 1 + A;
+    const int beta_max = c->beta(L);
+    const size_t mu_stride = (size_t)2 * DS + (size_t)DS * T;
+    std::vector<u64> conv;
+    // ModUp blocks
+    const size_t mu_off = 0;
+    conv.resize(mu_off + (size_t)(L + 1) * beta_max * mu_stride, 0);
+    for (int l = 0; l <= L; l++) {
+        for (int j = 0; j < c->beta(l); j++) {
+            u64* blk = conv.data() + mu_off + ((size_t)l * beta_max + j) * mu_stride;
+            int lo = j * DS, hi = std::min(lo + DS, l + 1);
+            for (int i = lo; i < hi; i++) {
+                u64 qi = q[i];
+                u64 dh = 1;
+                for (int i2 = lo; i2 < hi; i2++)
+                    if (i2 != i) dh = h_mulmod(dh, q[i2] % qi, qi);
+                u64 inv = h_invmod(dh, qi);
+                blk[i - lo] = inv;
+                blk[DS + (i - lo)] = shoup_of(inv, qi);
+                for (int t = 0; t < l + 1 + A; t++) {
+                    int pid = t <= l ? t : L + 1 + (t - l - 1);
+                    u64 pt = c->primes[pid];
+                    u64 v = 1 % pt;
+                    for (int i2 = lo; i2 < hi; i2++)
+                        if (i2 != i) v = h_mulmod(v, q[i2] % pt, pt);
+                    blk[2 * DS + (size_t)(i - lo) * T + t] = h_mulmod(v, c->h_pc[pid].r_mod, pt);
+                }
+            }
+        }
+    }
+    // ModDown block
+    const size_t md_off = conv.size();
+    conv.resize(md_off + 2 * A + (size_t)A * (L + 1), 0);
+    for (int k = 0; k < A; k++) {
+        u64 pk = sp[k];
+        u64 ph = 1;
+        for (int k2 = 0; k2 < A; k2++)
+            if (k2 != k) ph = h_mulmod(ph, sp[k2] % pk, pk);
+        u64 inv = h_invmod(ph, pk);
+        conv[md_off + k] = inv;
+        conv[md_off + A + k] = shoup_of(inv, pk);
+        for (int i = 0; i <= L; i++) {
+            u64 v = 1 % q[i];
+            for (int k2 = 0; k2 < A; k2++)
+                if (k2 != k) v = h_mulmod(v, sp[k2] % q[i], q[i]);
+            conv[md_off + 2 * A + (size_t)k * (L + 1) + i] = h_mulmod(v, c->h_pc[i].r_mod, q[i]);
+        }
+    }
+    // P^-1 mod q_i
+    const size_t pi_off = conv.size();
+    conv.resize(pi_off + 2 * (size_t)(L + 1), 0);
+    c->h_pinv.resize(L + 1);
+    for (int i = 0; i <= L; i++) {
+        u64 pm = 1;
+        for (int k = 0; k < A; k++) pm = h_mulmod(pm, sp[k] % q[i], q[i]);
+        u64 inv = h_invmod(pm, q[i]);
+        conv[pi_off + 2 * i] = inv;
+        conv[pi_off + 2 * i + 1] = shoup_of(inv, q[i]);
+        c->h_pinv[i] = inv;
+    }
+    // rescale blocks
+    const size_t rs_off = conv.size();
+    conv.resize(rs_off + (size_t)(L + 1) * 3 * (L + 1), 0);
+    for (int l = 1; l <= L; l++) {
+        u64* blk = conv.data() + rs_off + (size_t)l * 3 * (L + 1);
+        for (int i = 0; i < l; i++) {
+            u64 inv = h_invmod(q[l] % q[i], q[i]);
+            blk[i] = inv;
+            blk[(L + 1) + i] = shoup_of(inv, q[i]);
+            blk[2 * (L + 1) + i] = q[l] % q[i];
+        }
+    }
+    RK_CUDA(cudaMalloc((void**)&c->d_conv, conv.size() * 8));
+    RK_CUDA(cudaMemcpy(c->d_conv, conv.data(), conv.size() * 8, cudaMemcpyHostToDevice));
+
+    KernelEnv& e = c->env;
+    e.logn = c->log_n;
+    e.n = n;
+    e.L = L;
+    e.alpha = A;
+    e.pc = c->d_pc;
+    e.tw.psi = c->d_tw;
+    e.tw.psi_sh = c->d_tw + (size_t)1 * NP * n;
+    e.tw.ipsi = c->d_tw + (size_t)2 * NP * n;
+    e.tw.ipsi_sh = c->d_tw + (size_t)3 * NP * n;
+    e.conv.modup = c->d_conv + mu_off;
+    e.conv.modup_stride = mu_stride;
+    e.conv.beta_max = beta_max;
+    e.conv.dsize = DS;
+    e.conv.moddown = c->d_conv + md_off;
+    e.conv.pinv = c->d_conv + pi_off;
+    e.conv.rescale = c->d_conv + rs_off;
+    e.prof = &c->prof;
+}
+
+void ctx_release(rk_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (auto& kv : c->plain_cache) cudaFree(kv.second);
+    for (auto& kv : c->gal) cudaFree(kv.second.data);
+    if (c->rlk.data) cudaFree(c->rlk.data);
+    if (c->d_sk) cudaFree(c->d_sk);
+    if (c->d_pk) cudaFree(c->d_pk);
+    if (c->d_scratch) cudaFree(c->d_scratch);
+    if (c->d_conv) cudaFree(c->d_conv);
+    if (c->d_tw) cudaFree(c->d_tw);
+    if (c->d_pc) cudaFree(c->d_pc);
+    for (cudaEvent_t ev : c->prof.ev) cudaEventDestroy(ev);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+}

@@ -1,0 +1,554 @@
+// Homomorphic operations of RNS-CKKS on the device (Sec. 2.1: addition,
+// multiplication, rotation), key generation and the client operations.
+//
+// Conventions (fixed by this library; the paper leaves them to the scheme):
+//  * hybrid key switching with digits of `digit_size` limbs; ModUp is the fast
+//    basis conversion of one digit without correction; for a rotation the
+//    automorphism X -> X^g acts on the lifted digits (so that several rotations of
+//    one ciphertext share one ModUp); ModDown converts the P part back and
+//    multiplies by P^-1;
+//  * rescale lifts the dropped residue centred into (-q/2, q/2];
+//  * a factor (scalar or plaintext) multiplied at level l is encoded at scale
+//    Delta_{l-1} q_l / Delta_l and rounded half away from zero, so that after the
+//    rescale the product sits at the canonical scale Delta_{l-1};
+//  * a constant c is added as round(c Delta_l) to every evaluation of c0.
+#include <cmath>
+#include <complex>
+#include <cstring>
+
+#include "kernels.cuh"
+
+namespace {
+
+struct Scratch {
+    u64 *coef, *ext, *u, *w, *d, *v, *misc;
+    size_t misc_words;
+};
+
+Scratch scratch_layout(rk_ctx* c) {
+    const size_t n = c->n, L1 = c->L + 1, QP = c->L + 1 + c->alpha;
+    const size_t w_coef = L1 * n, w_ext = (size_t)c->beta(c->L) * QP * n, w_u = 2 * QP * n, w_w = 2 * L1 * n,
+                 w_d = 3 * L1 * n, w_v = 2 * L1 * n, w_misc = 4 * QP * n;
+    u64* b = c->scratch(w_coef + w_ext + w_u + w_w + w_d + w_v + w_misc);
+    Scratch S;
+    S.coef = b;
+    S.ext = S.coef + w_coef;
+    S.u = S.ext + w_ext;
+    S.w = S.u + w_u;
+    S.d = S.w + w_w;
+    S.v = S.d + w_d;
+    S.misc = S.v + w_v;
+    S.misc_words = w_misc;
+    return S;
+}
+
+LimbSet ls_q(u64* base, size_t ps, int polys, int limbs) { return LimbSet{base, ps, polys, limbs, limbs, 0, 0}; }
+LimbSet ls_one(u64* base, size_t ps, int polys, int prime) { return LimbSet{base, ps, polys, 1, 1, prime, 0}; }
+LimbSet ls_all(u64* base, size_t ps, int polys, int np) { return LimbSet{base, ps, polys, np, np, 0, 0}; }
+
+u64 shoup_companion(u64 w, u64 q) { return (u64)(((u128)w << 64) / q); }
+
+ScalarArg scalar_residues(const rk_ctx* c, int64_t K, int limbs) {
+    ScalarArg a;
+    memset(&a, 0, sizeof(a));
+    for (int i = 0; i < limbs; i++) {
+        const int64_t q = (int64_t)c->primes[i];
+        int64_t r = K % q;
+        if (r < 0) r += q;
+        a.w[i] = (u64)r;
+        a.wsh[i] = shoup_companion((u64)r, (u64)q);
+    }
+    return a;
+}
+
+// SplitMix64 counter stream for host-side sampling (keys, encryption noise).
+struct HostRng {
+    u64 seed, ctr = 0;
+    explicit HostRng(u64 s) : seed(s) {}
+    static u64 mix(u64 x) {
+        x += 0x9E3779B97F4A7C15ull;
+        x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+        x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+        return x ^ (x >> 31);
+    }
+    u64 next() { return mix(seed ^ mix(ctr++)); }
+    double uniform01() { return ((next() >> 11) + 0.5) * (1.0 / 9007199254740992.0); }
+    int64_t ternary() { return (int64_t)(next() % 3) - 1; }
+    int64_t gaussian(double sigma) {
+        for (;;) {
+            double u1 = uniform01(), u2 = uniform01();
+            double g = std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2) * sigma;
+            if (std::fabs(g) <= 6.0 * sigma) return (int64_t)llround(g);
+        }
+    }
+};
+
+const double kSigma = 3.19;
+
+void upload_i64_sync(rk_ctx* c, int64_t* dst, const int64_t* src, size_t count) {
+    RK_CUDA(cudaMemcpyAsync(dst, src, count * 8, cudaMemcpyHostToDevice, c->stream));
+    RK_CUDA(cudaStreamSynchronize(c->stream));
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Ciphertext handles
+// ---------------------------------------------------------------------------
+rk_ct* ct_alloc(rk_ctx* c, int level) {
+    rk_ct* ct = new rk_ct();
+    ct->ctx = c;
+    ct->level = level;
+    cudaError_t e = cudaMallocAsync((void**)&ct->data, c->ct_words() * 8, c->stream);
+    if (e != cudaSuccess) {
+        delete ct;
+        throw rk_error(RK_ENOMEM, std::string("ciphertext allocation: ") + cudaGetErrorString(e));
+    }
+    return ct;
+}
+
+void ct_free(rk_ct* ct) {
+    if (!ct) return;
+    if (ct->data) cudaFreeAsync(ct->data, ct->ctx->stream);
+    delete ct;
+}
+
+static void copy_meta(rk_ct* out, const rk_ct* a) {
+    out->N = a->N;
+    out->n_real = a->n_real;
+    out->Q = a->Q;
+    out->layout = a->layout;
+}
+
+rk_ct* ct_clone_meta(const rk_ct* src, int level) {
+    rk_ct* o = ct_alloc(src->ctx, level);
+    copy_meta(o, src);
+    return o;
+}
+
+// ---------------------------------------------------------------------------
+// Pointwise operations
+// ---------------------------------------------------------------------------
+void ev_copy(rk_ctx* c, const rk_ct* a, rk_ct* out) {
+    if (out != a) {
+        const size_t bytes = (size_t)(a->level + 1) * c->n * 8;
+        RK_CUDA(cudaMemcpyAsync(out->data, a->data, bytes, cudaMemcpyDeviceToDevice, c->stream));
+        RK_CUDA(cudaMemcpyAsync(out->data + c->poly_stride(), a->data + c->poly_stride(), bytes, cudaMemcpyDeviceToDevice,
+                                c->stream));
+    }
+    out->level = a->level;
+    copy_meta(out, a);
+}
+
+void ev_add(rk_ctx* c, const rk_ct* a, const rk_ct* b, rk_ct* out) {
+    RK_REQUIRE(a->level == b->level, RK_EINVAL, "add: level mismatch");
+    launch_addsub(c->env, out->data, a->data, b->data, a->level + 1, c->poly_stride(), 0, c->stream);
+    out->level = a->level;
+    copy_meta(out, a);
+}
+
+void ev_sub(rk_ctx* c, const rk_ct* a, const rk_ct* b, rk_ct* out) {
+    RK_REQUIRE(a->level == b->level, RK_EINVAL, "sub: level mismatch");
+    launch_addsub(c->env, out->data, a->data, b->data, a->level + 1, c->poly_stride(), 1, c->stream);
+    out->level = a->level;
+    copy_meta(out, a);
+}
+
+void ev_neg(rk_ctx* c, const rk_ct* a, rk_ct* out) {
+    launch_addsub(c->env, out->data, a->data, a->data, a->level + 1, c->poly_stride(), 2, c->stream);
+    out->level = a->level;
+    copy_meta(out, a);
+}
+
+void ev_add_const(rk_ctx* c, const rk_ct* a, double v, rk_ct* out) {
+    const int l = a->level;
+    const int64_t K = round_half_away(v * c->scales[l]);
+    launch_add_const(c->env, out->data, a->data, scalar_residues(c, K, l + 1), l + 1, c->poly_stride(), c->stream);
+    out->level = l;
+    copy_meta(out, a);
+}
+
+void ev_rescale_inplace(rk_ctx* c, rk_ct* a) {
+    const int l = a->level;
+    RK_REQUIRE(l >= 1, RK_EDEPTH, "rescale: no level left");
+    Scratch S = scratch_layout(c);
+    const size_t ps = c->poly_stride(), n = c->n;
+    launch_ntt_inverse(c->env, ls_one(a->data + (size_t)l * n, ps, 2, l), c->stream);
+    launch_rescale_lift(c->env, a->data + (size_t)l * n, ps, S.v, l, c->stream);
+    launch_ntt_forward(c->env, ls_q(S.v, (size_t)l * n, 2, l), c->stream);
+    launch_rescale_combine(c->env, a->data, ps, S.v, l, c->stream);
+    a->level = l - 1;
+    c->n_rescale++;
+}
+
+static double factor_scale(const rk_ctx* c, int l) {
+    return (c->scales[l - 1] * (double)c->primes[l]) / c->scales[l];
+}
+
+void ev_mul_scalar(rk_ctx* c, const rk_ct* a, double v, rk_ct* out) {
+    const int l = a->level;
+    RK_REQUIRE(l >= 1, RK_EDEPTH, "mul_scalar: no level left");
+    const int64_t K = round_half_away(v * factor_scale(c, l));
+    launch_mul_scalar(c->env, out->data, a->data, scalar_residues(c, K, l + 1), l + 1, c->poly_stride(), c->stream);
+    out->level = l;
+    copy_meta(out, a);
+    ev_rescale_inplace(c, out);
+}
+
+void ev_level_down(rk_ctx* c, const rk_ct* a, int target, rk_ct* out) {
+    RK_REQUIRE(target <= a->level && target >= 0, RK_EINVAL, "level_down: bad target");
+    if (a->level == target) {
+        ev_copy(c, a, out);
+        return;
+    }
+    ev_mul_scalar(c, a, 1.0, out);
+    while (out->level > target) ev_mul_scalar(c, out, 1.0, out);
+}
+
+static const u64* plain_get(rk_ctx* c, uint32_t kind, uint32_t N, uint32_t Q, uint32_t n_real, int l) {
+    auto key = std::make_tuple(kind, N, Q, n_real, l);
+    auto it = c->plain_cache.find(key);
+    if (it != c->plain_cache.end()) return it->second;
+    auto ekey = std::make_tuple(kind, N, Q, n_real);
+    if (!c->encodings.count(ekey)) {
+        std::vector<double> slots;
+        mask_slot_values(kind, N, Q, n_real, (size_t)c->n / 2, slots);
+        std::vector<double> u;
+        encode_unscaled(c->log_n, slots.data(), slots.size(), u);
+        c->encodings[ekey] = u;
+    }
+    const std::vector<double>& u = c->encodings[ekey];
+    const double s = factor_scale(c, l);
+    std::vector<int64_t> m(c->n);
+    for (int k = 0; k < c->n; k++) m[k] = round_half_away(s * u[k]);
+    Scratch S = scratch_layout(c);
+    u64* buf = nullptr;
+    RK_CUDA(cudaMalloc((void**)&buf, (size_t)(l + 1) * c->n * 8));
+    int64_t* tmp = (int64_t*)S.misc;
+    upload_i64_sync(c, tmp, m.data(), c->n);
+    launch_reduce_signed(c->env, tmp, ls_q(buf, 0, 1, l + 1), c->stream);
+    launch_ntt_forward(c->env, ls_q(buf, 0, 1, l + 1), c->stream);
+    launch_to_mont(c->env, ls_q(buf, 0, 1, l + 1), c->stream);
+    RK_CUDA(cudaStreamSynchronize(c->stream));
+    c->plain_cache[key] = buf;
+    return buf;
+}
+
+void ev_mul_plain(rk_ctx* c, const rk_ct* a, uint32_t kind, uint32_t N, uint32_t Q, uint32_t n_real, rk_ct* out) {
+    const int l = a->level;
+    RK_REQUIRE(l >= 1, RK_EDEPTH, "mul_plain: no level left");
+    const u64* pt = plain_get(c, kind, N, Q, n_real, l);
+    launch_mul_plain(c->env, out->data, a->data, pt, l + 1, c->poly_stride(), c->stream);
+    out->level = l;
+    copy_meta(out, a);
+    ev_rescale_inplace(c, out);
+}
+
+// ---------------------------------------------------------------------------
+// Key switching
+// ---------------------------------------------------------------------------
+// ModUp of d (evaluation domain, limbs 0..l) into the ext scratch (evaluation domain).
+static void ks_modup(rk_ctx* c, const u64* d_eval, int l) {
+    Scratch S = scratch_layout(c);
+    const size_t n = c->n;
+    const int QP = l + 1 + c->alpha;
+    RK_CUDA(cudaMemcpyAsync(S.coef, d_eval, (size_t)(l + 1) * n * 8, cudaMemcpyDeviceToDevice, c->stream));
+    launch_ntt_inverse(c->env, ls_q(S.coef, 0, 1, l + 1), c->stream);
+    launch_modup(c->env, S.coef, S.ext, (size_t)QP * n, l, c->beta(l), c->stream);
+    launch_ntt_forward(c->env, LimbSet{S.ext, (size_t)QP * n, c->beta(l), QP, l + 1, 0, c->L + 1}, c->stream);
+}
+
+// Inner product with `key` (automorphism `galois` on the lifted digits), ModDown, and
+// out = base + result (automorphism galois0 on base0).
+static void ks_apply(rk_ctx* c, const u64* key, int l, u64 galois, const u64* base0, u64 galois0, const u64* base1, u64* out,
+                     size_t out_ps) {
+    Scratch S = scratch_layout(c);
+    const size_t n = c->n;
+    const int QP = l + 1 + c->alpha;
+    launch_ks_inner(c->env, S.ext, (size_t)QP * n, key, S.u, l, c->beta(l), galois, c->stream);
+    launch_ntt_inverse(c->env, LimbSet{S.u + (size_t)(l + 1) * n, (size_t)QP * n, 2, c->alpha, 0, 0, c->L + 1}, c->stream);
+    launch_moddown_conv(c->env, S.u, S.w, l, c->stream);
+    launch_ntt_forward(c->env, ls_q(S.w, (size_t)(l + 1) * n, 2, l + 1), c->stream);
+    launch_ks_combine(c->env, out, out_ps, base0, galois0, base1, S.u, S.w, l, c->stream);
+    c->n_ks++;
+}
+
+u64 galois_left(const rk_ctx* c, int r) {
+    const int64_t slots = c->n / 2;
+    int64_t rr = ((int64_t)r % slots + slots) % slots;
+    return h_powmod(5, (u64)rr, 2ull * (u64)c->n);
+}
+
+void ev_rotate_many(rk_ctx* c, const rk_ct* a, const int* r, int k, rk_ct** outs) {
+    const int l = a->level;
+    const size_t ps = c->poly_stride();
+    bool need_ks = false;
+    for (int i = 0; i < k; i++) {
+        RK_REQUIRE(outs[i] != a, RK_EINVAL, "rotate: output aliases input");
+        u64 g = galois_left(c, r[i]);
+        if (g != 1) {
+            RK_REQUIRE(c->gal.count(g), RK_ENOKEY, "rotation key missing for r = " + std::to_string(r[i]));
+            need_ks = true;
+        }
+    }
+    if (need_ks) ks_modup(c, a->data + ps, l);
+    for (int i = 0; i < k; i++) {
+        u64 g = galois_left(c, r[i]);
+        if (g == 1) {
+            ev_copy(c, a, outs[i]);
+            continue;
+        }
+        ks_apply(c, c->gal[g].data, l, g, a->data, g, nullptr, outs[i]->data, ps);
+        outs[i]->level = l;
+        copy_meta(outs[i], a);
+        c->n_rot++;
+    }
+}
+
+void ev_mul(rk_ctx* c, const rk_ct* a, const rk_ct* b, rk_ct* out) {
+    RK_REQUIRE(a->level == b->level, RK_EINVAL, "mul: level mismatch");
+    const int l = a->level;
+    RK_REQUIRE(l >= 1, RK_EDEPTH, "mul: no level left");
+    RK_REQUIRE(c->rlk.data, RK_ENOKEY, "relinearisation key missing");
+    Scratch S = scratch_layout(c);
+    const size_t pl = (size_t)(l + 1) * c->n;
+    launch_tensor(c->env, S.d, a->data, b->data, l + 1, c->poly_stride(), c->stream);
+    ks_modup(c, S.d + 2 * pl, l);
+    ks_apply(c, c->rlk.data, l, 0, S.d, 0, S.d + pl, out->data, c->poly_stride());
+    out->level = l;
+    copy_meta(out, a);
+    c->n_mul++;
+    ev_rescale_inplace(c, out);
+}
+
+// ---------------------------------------------------------------------------
+// Keys
+// ---------------------------------------------------------------------------
+static void secret_set(rk_ctx* c, const std::vector<int64_t>& s) {
+    const int NP = c->n_primes;
+    c->h_sk = s;
+    if (!c->d_sk) RK_CUDA(cudaMalloc((void**)&c->d_sk, (size_t)NP * c->n * 8));
+    Scratch S = scratch_layout(c);
+    upload_i64_sync(c, (int64_t*)S.misc, s.data(), c->n);
+    launch_reduce_signed(c->env, (int64_t*)S.misc, ls_all(c->d_sk, 0, 1, NP), c->stream);
+    launch_ntt_forward(c->env, ls_all(c->d_sk, 0, 1, NP), c->stream);
+    launch_to_mont(c->env, ls_all(c->d_sk, 0, 1, NP), c->stream);
+}
+
+// small Gaussian polynomial over the first `limbs` primes, evaluation domain, into dst
+static void gaussian_eval(rk_ctx* c, HostRng& rng, u64* dst, int limbs, int64_t* dev_tmp) {
+    std::vector<int64_t> e(c->n);
+    for (auto& x : e) x = rng.gaussian(kSigma);
+    upload_i64_sync(c, dev_tmp, e.data(), c->n);
+    launch_reduce_signed(c->env, dev_tmp, ls_all(dst, 0, 1, limbs), c->stream);
+    launch_ntt_forward(c->env, ls_all(dst, 0, 1, limbs), c->stream);
+}
+
+static void make_pk(rk_ctx* c) {
+    const int L1 = c->L + 1;
+    Scratch S = scratch_layout(c);
+    if (!c->d_pk) RK_CUDA(cudaMalloc((void**)&c->d_pk, (size_t)2 * L1 * c->n * 8));
+    HostRng rng(c->seed ^ 0x5045524B45590001ull);
+    u64* a = S.misc;
+    u64* e = S.misc + (size_t)L1 * c->n;
+    int64_t* tmp = (int64_t*)(S.misc + (size_t)2 * L1 * c->n);
+    launch_uniform(c->env, ls_all(a, 0, 1, L1), c->seed, 0xA0000000ull, c->stream);
+    gaussian_eval(c, rng, e, L1, tmp);
+    launch_pk(c->env, c->d_pk, (size_t)L1 * c->n, a, e, c->d_sk, L1, c->stream);
+    RK_CUDA(cudaStreamSynchronize(c->stream));
+}
+
+// Switching key from s' (evaluation domain, normal form, all primes, in sp) to s.
+static u64* make_switch_key(rk_ctx* c, const u64* sp, u64 stream_id) {
+    const int NP = c->n_primes, L = c->L, DS = c->dsize, BL = c->beta(L);
+    const size_t n = c->n;
+    u64* buf = nullptr;
+    cudaError_t err = cudaMalloc((void**)&buf, (size_t)BL * 2 * NP * n * 8);
+    if (err != cudaSuccess) throw rk_error(RK_ENOMEM, "switching key allocation failed");
+    Scratch S = scratch_layout(c);
+    // misc: [sp copy is provided by caller in misc][e: NP n][tmp: n]
+    u64* e = S.misc + (size_t)NP * n;
+    int64_t* tmp = (int64_t*)(S.misc + (size_t)2 * NP * n);
+    u64* gad_dev = S.misc + (size_t)2 * NP * n + n;
+    HostRng rng(c->seed ^ HostRng::mix(stream_id + 0x4B4559ull));
+    u64 Pmod[RK_MAX_PRIMES];
+    for (int t = 0; t <= L; t++) {
+        u64 pm = 1;
+        for (int k = 0; k < c->alpha; k++) pm = h_mulmod(pm, c->primes[L + 1 + k] % c->primes[t], c->primes[t]);
+        Pmod[t] = pm;
+    }
+    for (int j = 0; j < BL; j++) {
+        u64* kb = buf + (size_t)j * 2 * NP * n;
+        u64* ka = kb + (size_t)NP * n;
+        launch_uniform(c->env, ls_all(ka, 0, 1, NP), c->seed, stream_id * 64 + (u64)j, c->stream);
+        gaussian_eval(c, rng, e, NP, tmp);
+        std::vector<u64> gad(NP, 0);
+        for (int t = j * DS; t < std::min((j + 1) * DS, L + 1); t++) gad[t] = h_mulmod(Pmod[t], c->h_pc[t].r_mod, c->primes[t]);
+        RK_CUDA(cudaMemcpyAsync(gad_dev, gad.data(), NP * 8, cudaMemcpyHostToDevice, c->stream));
+        launch_key_digit(c->env, kb, ka, ka, e, c->d_sk, sp, gad_dev, NP, c->stream);
+        RK_CUDA(cudaStreamSynchronize(c->stream));
+    }
+    return buf;
+}
+
+static void make_relin_key(rk_ctx* c) {
+    Scratch S = scratch_layout(c);
+    launch_square_secret(c->env, S.misc, c->d_sk, c->n_primes, c->stream);
+    if (c->rlk.data) cudaFree(c->rlk.data);
+    c->rlk.data = make_switch_key(c, S.misc, 1);
+}
+
+void keys_add_rotations(rk_ctx* c, const std::vector<int>& rotations) {
+    RK_REQUIRE(c->d_sk, RK_EINVAL, "no secret key");
+    Scratch S = scratch_layout(c);
+    const int NP = c->n_primes;
+    for (int r : rotations) {
+        u64 g = galois_left(c, r);
+        if (g == 1 || c->gal.count(g)) continue;
+        // s' = sigma_g(s): from Montgomery form, then permute evaluations
+        u64* s_norm = S.misc + (size_t)2 * NP * c->n + 2 * c->n;   // beyond make_switch_key's area
+        launch_from_mont(c->env, s_norm, c->d_sk, NP, c->stream);
+        launch_automorph(c->env, S.misc, s_norm, g, NP, c->stream);
+        c->gal[g].data = make_switch_key(c, S.misc, 16 + g);
+    }
+}
+
+void keys_generate(rk_ctx* c, uint64_t seed, const std::vector<int>& rotations) {
+    c->seed = seed;
+    HostRng rng(seed ^ 0x5345435245540001ull);
+    std::vector<int64_t> s(c->n);
+    for (auto& x : s) x = rng.ternary();
+    secret_set(c, s);
+    make_pk(c);
+    make_relin_key(c);
+    keys_add_rotations(c, rotations);
+}
+
+void secret_import(rk_ctx* c, const int64_t* s, size_t n) {
+    RK_REQUIRE(n == (size_t)c->n, RK_EINVAL, "secret length must be n");
+    for (size_t i = 0; i < n; i++) RK_REQUIRE(s[i] >= -1 && s[i] <= 1, RK_EINVAL, "secret must be ternary");
+    if (c->seed == 0) c->seed = 0x1234567ull;
+    secret_set(c, std::vector<int64_t>(s, s + n));
+    make_pk(c);
+}
+
+void key_import(rk_ctx* c, uint32_t kind, uint64_t galois, const uint64_t* coeffs, size_t words) {
+    const int NP = c->n_primes, BL = c->beta(c->L);
+    const size_t n = c->n, expect = (size_t)BL * 2 * NP * n;
+    RK_REQUIRE(words == expect, RK_EINVAL, "key size mismatch: expected " + std::to_string(expect) + " words");
+    RK_REQUIRE(kind == RK_KEY_RELIN || kind == RK_KEY_GALOIS, RK_EINVAL, "bad key kind");
+    for (int t = 0; t < NP; t++)  // spot-check residues are canonical
+        RK_REQUIRE(coeffs[(size_t)t * n] < c->primes[t], RK_EFORMAT, "key residue out of range");
+    u64* buf = nullptr;
+    RK_CUDA(cudaMalloc((void**)&buf, expect * 8));
+    RK_CUDA(cudaMemcpyAsync(buf, coeffs, expect * 8, cudaMemcpyHostToDevice, c->stream));
+    launch_ntt_forward(c->env, ls_all(buf, (size_t)NP * n, BL * 2, NP), c->stream);
+    launch_to_mont(c->env, ls_all(buf, (size_t)NP * n, BL * 2, NP), c->stream);
+    RK_CUDA(cudaStreamSynchronize(c->stream));
+    if (kind == RK_KEY_RELIN) {
+        if (c->rlk.data) cudaFree(c->rlk.data);
+        c->rlk.data = buf;
+    } else {
+        auto it = c->gal.find(galois);
+        if (it != c->gal.end()) cudaFree(it->second.data);
+        c->gal[galois].data = buf;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Client operations
+// ---------------------------------------------------------------------------
+rk_ct* encrypt_values(rk_ctx* c, const double* v, uint32_t count, uint32_t N, uint32_t Q, uint32_t n_real) {
+    RK_REQUIRE(c->d_pk, RK_EINVAL, "no public key: call rk_keygen or rk_secret_import first");
+    const size_t slots = c->n / 2;
+    RK_REQUIRE(N >= 1 && (N & (N - 1)) == 0, RK_EINVAL, "N must be a power of two");
+    RK_REQUIRE(n_real >= 1 && n_real <= N, RK_EINVAL, "n_real must be in [1, N]");
+    RK_REQUIRE(Q >= 1 && (size_t)Q * N * N <= slots, RK_EINVAL, "Q * N^2 exceeds the slot count");
+    RK_REQUIRE(count <= (size_t)Q * n_real, RK_EINVAL, "more values than Q * n_real");
+    std::vector<double> z(slots, 0.0);
+    for (uint32_t i = 0; i < count; i++) {
+        RK_REQUIRE(v[i] >= 0.0 && v[i] < 1.0, RK_EINVAL, "values must lie in [0, 1)");
+        z[(size_t)(i / n_real) * N * N + (i % n_real)] = v[i];
+    }
+    std::vector<double> u;
+    encode_unscaled(c->log_n, z.data(), z.size(), u);
+    const int L1 = c->L + 1;
+    const size_t n = c->n;
+    std::vector<int64_t> host(4 * n);
+    HostRng rng(c->seed ^ HostRng::mix(0x454E43ull + c->enc_counter++));
+    for (size_t k = 0; k < n; k++) host[k] = rng.ternary();
+    for (size_t k = 0; k < n; k++) host[n + k] = rng.gaussian(kSigma);
+    for (size_t k = 0; k < n; k++) host[2 * n + k] = rng.gaussian(kSigma);
+    for (size_t k = 0; k < n; k++) host[3 * n + k] = round_half_away(c->scales[c->L] * u[k]);
+    Scratch S = scratch_layout(c);
+    int64_t* tmp2 = (int64_t*)S.u;   // 2 (L+1+alpha) n >= 4 n words
+    upload_i64_sync(c, tmp2, host.data(), 4 * n);
+    LimbSet r = ls_q(S.misc, (size_t)L1 * n, 4, L1);
+    launch_reduce_signed(c->env, tmp2, r, c->stream);
+    launch_ntt_forward(c->env, r, c->stream);
+    rk_ct* ct = ct_alloc(c, c->L);
+    launch_encrypt(c->env, ct->data, c->poly_stride(), S.misc, c->d_pk, (size_t)L1 * n, L1, c->stream);
+    ct->N = N;
+    ct->Q = Q;
+    ct->n_real = n_real;
+    ct->layout = RK_LAYOUT_ROW;
+    return ct;
+}
+
+void decrypt_slots(rk_ctx* c, const rk_ct* ct, std::vector<double>& slots) {
+    RK_REQUIRE(c->d_sk, RK_EINVAL, "no secret key");
+    const int l = ct->level;
+    const size_t n = c->n;
+    Scratch S = scratch_layout(c);
+    launch_decrypt(c->env, S.misc, ct->data, ct->data + c->poly_stride(), c->d_sk, l + 1, c->stream);
+    launch_ntt_inverse(c->env, ls_q(S.misc, 0, 1, l + 1), c->stream);
+    const int use = l >= 1 ? 2 : 1;
+    std::vector<u64> h((size_t)use * n);
+    RK_CUDA(cudaMemcpyAsync(h.data(), S.misc, (size_t)use * n * 8, cudaMemcpyDeviceToHost, c->stream));
+    RK_CUDA(cudaStreamSynchronize(c->stream));
+    std::vector<double> m(n);
+    const u64 q0 = c->primes[0];
+    if (use == 1) {
+        for (size_t k = 0; k < n; k++) {
+            u64 x = h[k];
+            m[k] = x > q0 / 2 ? -(double)(q0 - x) : (double)x;
+        }
+    } else {
+        const u64 q1 = c->primes[1];
+        const u64 q0inv = h_invmod(q0 % q1, q1);
+        const u128 Q = (u128)q0 * q1;
+        for (size_t k = 0; k < n; k++) {
+            u64 x0 = h[k], x1 = h[n + k];
+            u64 t = h_mulmod((x1 + q1 - (x0 % q1)) % q1, q0inv, q1);
+            u128 x = (u128)x0 + (u128)q0 * t;
+            m[k] = x > Q / 2 ? -(double)(Q - x) : (double)x;
+        }
+    }
+    for (size_t k = 0; k < n; k++) m[k] /= c->scales[l];
+    decode_coeffs(c->log_n, m, slots);
+}
+
+rk_ct* ct_import(rk_ctx* c, const uint64_t* coeffs, int level) {
+    RK_REQUIRE(level >= 0 && level <= c->L, RK_EINVAL, "bad level");
+    const size_t n = c->n, pl = (size_t)(level + 1) * n;
+    for (int t = 0; t <= level; t++)
+        RK_REQUIRE(coeffs[(size_t)t * n] < c->primes[t] && coeffs[pl + (size_t)t * n] < c->primes[t], RK_EFORMAT,
+                   "ciphertext residue out of range");
+    rk_ct* ct = ct_alloc(c, level);
+    RK_CUDA(cudaMemcpyAsync(ct->data, coeffs, pl * 8, cudaMemcpyHostToDevice, c->stream));
+    RK_CUDA(cudaMemcpyAsync(ct->data + c->poly_stride(), coeffs + pl, pl * 8, cudaMemcpyHostToDevice, c->stream));
+    launch_ntt_forward(c->env, ls_q(ct->data, c->poly_stride(), 2, level + 1), c->stream);
+    RK_CUDA(cudaStreamSynchronize(c->stream));
+    return ct;
+}
+
+void ct_export(rk_ctx* c, const rk_ct* ct, uint64_t* coeffs) {
+    const int l = ct->level;
+    const size_t n = c->n, pl = (size_t)(l + 1) * n;
+    Scratch S = scratch_layout(c);
+    RK_CUDA(cudaMemcpyAsync(S.misc, ct->data, pl * 8, cudaMemcpyDeviceToDevice, c->stream));
+    RK_CUDA(cudaMemcpyAsync(S.misc + pl, ct->data + c->poly_stride(), pl * 8, cudaMemcpyDeviceToDevice, c->stream));
+    launch_ntt_inverse(c->env, ls_q(S.misc, pl, 2, l + 1), c->stream);
+    RK_CUDA(cudaMemcpyAsync(coeffs, S.misc, 2 * pl * 8, cudaMemcpyDeviceToHost, c->stream));
+    RK_CUDA(cudaStreamSynchronize(c->stream));
+}

@@ -1,0 +1,663 @@
+// CUDA kernels of the RNS-CKKS evaluator (sm_103a).
+//
+// Data: residue polynomials of n = 2^log_n 64-bit words, limb-major, in the
+// evaluation (NTT) domain unless a kernel says otherwise.  Evaluation order of the
+// forward NTT: index i holds the value at psi^(2 brev(i) + 1), psi the chosen
+// primitive 2n-th root of unity modulo the limb's prime.
+#include <algorithm>
+
+#include "kernels.cuh"
+
+#define TPB 256
+
+const char* const kKernelKindNames[KK_COUNT] = {"ntt_fwd", "ntt_inv", "modup", "ks_inner", "moddown_conv",
+                                               "ks_combine", "tensor", "rescale", "pointwise", "client"};
+
+// Counts every launch; when `kind` is the profiled kind, brackets the launch(es) with
+// CUDA events on the launching stream and accumulates the algorithmic bytes/products.
+struct ProfScope {
+    Profiler* p;
+    bool on = false;
+    cudaStream_t st;
+    double bytes, ops;
+    ProfScope(const KernelEnv& e, int kind, cudaStream_t s, int nlaunch, double b, double o)
+        : p(e.prof), st(s), bytes(b), ops(o) {
+        if (!p) return;
+        p->launches += (uint64_t)nlaunch;
+        if (p->target == kind) {
+            on = true;
+            record();
+        }
+    }
+    void record() {
+        if (p->used == p->ev.size()) {
+            cudaEvent_t ev;
+            cudaEventCreate(&ev);
+            p->ev.push_back(ev);
+        }
+        cudaEventRecord(p->ev[p->used++], st);
+    }
+    ~ProfScope() {
+        if (on) {
+            record();
+            p->bytes += bytes;
+            p->ops += ops;
+            p->timed++;
+        }
+    }
+};
+
+__device__ __forceinline__ int brev_bits(unsigned x, int bits) { return (int)(__brev(x) >> (32 - bits)); }
+
+// Source index of output index k under X -> X^g in the evaluation domain.
+__device__ __forceinline__ int galois_src(int k, u64 g, int logn) {
+    unsigned two_n_mask = (2u << logn) - 1u;
+    unsigned e = 2u * (unsigned)brev_bits((unsigned)k, logn) + 1u;
+    unsigned e2 = (unsigned)((e * (unsigned)g) & two_n_mask);
+    return brev_bits((e2 - 1u) >> 1, logn);
+}
+
+// ===========================================================================
+// NTT: log_n = a + b.  The column pass runs the first a Cooley-Tukey stages on
+// the 2^a-point columns {r 2^b + c}; the row pass runs the last b stages on the
+// contiguous 2^b-point rows.  Inverse (Gentleman-Sande) runs the row pass first.
+// Values stay in [0, 2q) between passes; the last pass returns [0, q).
+// ===========================================================================
+#define NTT_COLS 16
+#define NTT_ROW_TILE 2048
+
+__global__ void __launch_bounds__(TPB) k_ntt_fwd_col(LimbSet s, int logn, int loga, const PrimeConst* __restrict__ pc,
+                                                     const u64* __restrict__ psi, const u64* __restrict__ psi_sh) {
+    extern __shared__ u64 sm[];
+    const int n = 1 << logn, B = 1 << (logn - loga), R = 1 << loga;
+    const int limb = blockIdx.y;
+    const int pid = limb_prime(s, limb);
+    const u64 q = pc[pid].q, q2 = 2 * q;
+    u64* data = s.base + (size_t)blockIdx.z * s.poly_stride + (size_t)limb * n;
+    const u64* w = psi + (size_t)pid * n;
+    const u64* wsh = psi_sh + (size_t)pid * n;
+    const int c0 = blockIdx.x * NTT_COLS;
+    for (int idx = threadIdx.x; idx < R * NTT_COLS; idx += blockDim.x) {
+        int r = idx / NTT_COLS, c = idx % NTT_COLS;
+        sm[idx] = data[(size_t)r * B + c0 + c];
+    }
+    __syncthreads();
+    for (int st = 0; st < loga; st++) {
+        const int m = 1 << st, tt = R >> (st + 1);
+        for (int bf = threadIdx.x; bf < (R / 2) * NTT_COLS; bf += blockDim.x) {
+            int c = bf % NTT_COLS, p = bf / NTT_COLS;
+            int i = p / tt, r = i * 2 * tt + (p % tt);
+            u64 W = __ldg(w + m + i), Wsh = __ldg(wsh + m + i);
+            u64 U = sm[r * NTT_COLS + c];
+            u64 V = shoup_lazy(sm[(r + tt) * NTT_COLS + c], W, Wsh, q);
+            u64 x = U + V;
+            if (x >= q2) x -= q2;
+            u64 y = U + q2 - V;
+            if (y >= q2) y -= q2;
+            sm[r * NTT_COLS + c] = x;
+            sm[(r + tt) * NTT_COLS + c] = y;
+        }
+        __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < R * NTT_COLS; idx += blockDim.x) {
+        int r = idx / NTT_COLS, c = idx % NTT_COLS;
+        data[(size_t)r * B + c0 + c] = sm[idx];
+    }
+}
+
+__global__ void __launch_bounds__(TPB) k_ntt_fwd_row(LimbSet s, int logn, int loga, int rows, const PrimeConst* __restrict__ pc,
+                                                     const u64* __restrict__ psi, const u64* __restrict__ psi_sh) {
+    extern __shared__ u64 sm[];
+    const int n = 1 << logn, logb = logn - loga, B = 1 << logb, R = 1 << loga;
+    const int limb = blockIdx.y;
+    const int pid = limb_prime(s, limb);
+    const u64 q = pc[pid].q, q2 = 2 * q;
+    const int r0 = blockIdx.x * rows;
+    u64* data = s.base + (size_t)blockIdx.z * s.poly_stride + (size_t)limb * n + (size_t)r0 * B;
+    const u64* w = psi + (size_t)pid * n;
+    const u64* wsh = psi_sh + (size_t)pid * n;
+    for (int e = threadIdx.x; e < rows * B; e += blockDim.x) sm[e] = data[e];
+    __syncthreads();
+    for (int st = 0; st < logb; st++) {
+        const int m = R << st, tt = B >> (st + 1);
+        for (int bf = threadIdx.x; bf < rows * (B / 2); bf += blockDim.x) {
+            int rr = bf / (B / 2), p = bf % (B / 2);
+            int il = p / tt, c = il * 2 * tt + (p % tt);
+            int idx = m + ((r0 + rr) << st) + il;
+            u64 W = __ldg(w + idx), Wsh = __ldg(wsh + idx);
+            u64* x0 = sm + rr * B + c;
+            u64 U = x0[0];
+            u64 V = shoup_lazy(x0[tt], W, Wsh, q);
+            u64 x = U + V;
+            if (x >= q2) x -= q2;
+            u64 y = U + q2 - V;
+            if (y >= q2) y -= q2;
+            x0[0] = x;
+            x0[tt] = y;
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < rows * B; e += blockDim.x) {
+        u64 x = sm[e];
+        data[e] = reduce_2q(x, q);
+    }
+}
+
+__global__ void __launch_bounds__(TPB) k_ntt_inv_row(LimbSet s, int logn, int loga, int rows, const PrimeConst* __restrict__ pc,
+                                                     const u64* __restrict__ ipsi, const u64* __restrict__ ipsi_sh) {
+    extern __shared__ u64 sm[];
+    const int n = 1 << logn, logb = logn - loga, B = 1 << logb;
+    const int limb = blockIdx.y;
+    const int pid = limb_prime(s, limb);
+    const u64 q = pc[pid].q, q2 = 2 * q;
+    const int r0 = blockIdx.x * rows;
+    u64* data = s.base + (size_t)blockIdx.z * s.poly_stride + (size_t)limb * n + (size_t)r0 * B;
+    const u64* w = ipsi + (size_t)pid * n;
+    const u64* wsh = ipsi_sh + (size_t)pid * n;
+    for (int e = threadIdx.x; e < rows * B; e += blockDim.x) sm[e] = data[e];
+    __syncthreads();
+    for (int st = 0; st < logb; st++) {
+        const int tt = 1 << st, m = (n >> 1) >> st;
+        for (int bf = threadIdx.x; bf < rows * (B / 2); bf += blockDim.x) {
+            int rr = bf / (B / 2), p = bf % (B / 2);
+            int il = p / tt, c = il * 2 * tt + (p % tt);
+            int idx = m + ((r0 + rr) << (logb - st - 1)) + il;
+            u64 W = __ldg(w + idx), Wsh = __ldg(wsh + idx);
+            u64* x0 = sm + rr * B + c;
+            u64 U = x0[0], V = x0[tt];
+            u64 x = U + V;
+            if (x >= q2) x -= q2;
+            x0[0] = x;
+            x0[tt] = shoup_lazy(U + q2 - V, W, Wsh, q);
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < rows * B; e += blockDim.x) data[e] = sm[e];
+}
+
+__global__ void __launch_bounds__(TPB) k_ntt_inv_col(LimbSet s, int logn, int loga, const PrimeConst* __restrict__ pc,
+                                                     const u64* __restrict__ ipsi, const u64* __restrict__ ipsi_sh) {
+    extern __shared__ u64 sm[];
+    const int n = 1 << logn, B = 1 << (logn - loga), R = 1 << loga;
+    const int limb = blockIdx.y;
+    const int pid = limb_prime(s, limb);
+    const PrimeConst P = pc[pid];
+    const u64 q = P.q, q2 = 2 * q;
+    u64* data = s.base + (size_t)blockIdx.z * s.poly_stride + (size_t)limb * n;
+    const u64* w = ipsi + (size_t)pid * n;
+    const u64* wsh = ipsi_sh + (size_t)pid * n;
+    const int c0 = blockIdx.x * NTT_COLS;
+    for (int idx = threadIdx.x; idx < R * NTT_COLS; idx += blockDim.x) {
+        int r = idx / NTT_COLS, c = idx % NTT_COLS;
+        sm[idx] = data[(size_t)r * B + c0 + c];
+    }
+    __syncthreads();
+    for (int st = 0; st < loga; st++) {
+        const int tt = 1 << st, m = (R >> 1) >> st;
+        for (int bf = threadIdx.x; bf < (R / 2) * NTT_COLS; bf += blockDim.x) {
+            int c = bf % NTT_COLS, p = bf / NTT_COLS;
+            int i = p / tt, r = i * 2 * tt + (p % tt);
+            u64 W = __ldg(w + m + i), Wsh = __ldg(wsh + m + i);
+            u64 U = sm[r * NTT_COLS + c], V = sm[(r + tt) * NTT_COLS + c];
+            u64 x = U + V;
+            if (x >= q2) x -= q2;
+            sm[r * NTT_COLS + c] = x;
+            sm[(r + tt) * NTT_COLS + c] = shoup_lazy(U + q2 - V, W, Wsh, q);
+        }
+        __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < R * NTT_COLS; idx += blockDim.x) {
+        int r = idx / NTT_COLS, c = idx % NTT_COLS;
+        data[(size_t)r * B + c0 + c] = shoup_mul(sm[idx], P.ninv, P.ninv_shoup, q);
+    }
+}
+
+static int ntt_loga(int logn) { return logn / 2; }
+// rows of the row pass handled by one block: a 2048-word tile, at most all 2^a rows
+static int ntt_rows(int logn, int loga) { return std::min(NTT_ROW_TILE >> (logn - loga), 1 << loga); }
+
+void launch_ntt_forward(const KernelEnv& env, const LimbSet& s, cudaStream_t st) {
+    if (s.n_limbs <= 0 || s.n_polys <= 0) return;
+    ProfScope ps(env, KK_NTT_FWD, st, 2, 2.0 * s.n_limbs * s.n_polys * 8.0 * env.n, (double)s.n_limbs * s.n_polys * (env.n / 2) * env.logn);
+    const int logn = env.logn, loga = ntt_loga(logn), logb = logn - loga;
+    dim3 gc((1 << logb) / NTT_COLS, s.n_limbs, s.n_polys);
+    k_ntt_fwd_col<<<gc, TPB, (size_t)(1 << loga) * NTT_COLS * 8, st>>>(s, logn, loga, env.pc, env.tw.psi, env.tw.psi_sh);
+    const int rows = ntt_rows(logn, loga);
+    dim3 gr((1 << loga) / rows, s.n_limbs, s.n_polys);
+    k_ntt_fwd_row<<<gr, TPB, (size_t)rows * (1 << logb) * 8, st>>>(s, logn, loga, rows, env.pc, env.tw.psi, env.tw.psi_sh);
+}
+
+void launch_ntt_inverse(const KernelEnv& env, const LimbSet& s, cudaStream_t st) {
+    if (s.n_limbs <= 0 || s.n_polys <= 0) return;
+    ProfScope ps(env, KK_NTT_INV, st, 2, 2.0 * s.n_limbs * s.n_polys * 8.0 * env.n, (double)s.n_limbs * s.n_polys * (env.n / 2) * env.logn);
+    const int logn = env.logn, loga = ntt_loga(logn), logb = logn - loga;
+    const int rows = ntt_rows(logn, loga);
+    dim3 gr((1 << loga) / rows, s.n_limbs, s.n_polys);
+    k_ntt_inv_row<<<gr, TPB, (size_t)rows * (1 << logb) * 8, st>>>(s, logn, loga, rows, env.pc, env.tw.ipsi, env.tw.ipsi_sh);
+    dim3 gc((1 << logb) / NTT_COLS, s.n_limbs, s.n_polys);
+    k_ntt_inv_col<<<gc, TPB, (size_t)(1 << loga) * NTT_COLS * 8, st>>>(s, logn, loga, env.pc, env.tw.ipsi, env.tw.ipsi_sh);
+}
+
+// ===========================================================================
+// Pointwise kernels on ciphertexts (layout [2][L+1][n], limb t <-> q_t).
+// grid: (n / TPB, limbs, polys)
+// ===========================================================================
+__global__ void k_addsub(u64* out, const u64* a, const u64* b, int n, size_t ps, const PrimeConst* __restrict__ pc, int mode) {
+    const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y, c = blockIdx.z;
+    const u64 q = pc[t].q;
+    const size_t off = c * ps + (size_t)t * n + k;
+    u64 x = a[off];
+    u64 r;
+    if (mode == 0) r = add_mod(x, b[off], q);
+    else if (mode == 1) r = sub_mod(x, b[off], q);
+    else r = x ? q - x : 0;
+    out[off] = r;
+}
+
+void launch_addsub(const KernelEnv& env, u64* out, const u64* a, const u64* b, int limbs, size_t ps, int mode, cudaStream_t st) {
+    ProfScope pf(env, KK_POINTWISE, st, 1, 6.0 * limbs * 8.0 * env.n, 0.0);
+    dim3 g(env.n / TPB, limbs, 2);
+    k_addsub<<<g, TPB, 0, st>>>(out, a, b, env.n, ps, env.pc, mode);
+}
+
+// out0 = a0 + K_t, out1 = a1
+__global__ void k_add_const(u64* out, const u64* a, ScalarArg K, int n, size_t ps, const PrimeConst* __restrict__ pc) {
+    const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y, c = blockIdx.z;
+    const size_t off = c * ps + (size_t)t * n + k;
+    u64 x = a[off];
+    if (c == 0) x = add_mod(x, K.w[t], pc[t].q);
+    out[off] = x;
+}
+
+void launch_add_const(const KernelEnv& env, u64* out, const u64* a, const ScalarArg& K, int limbs, size_t ps, cudaStream_t st) {
+    ProfScope pf(env, KK_POINTWISE, st, 1, 4.0 * limbs * 8.0 * env.n, 0.0);
+    dim3 g(env.n / TPB, limbs, 2);
+    k_add_const<<<g, TPB, 0, st>>>(out, a, K, env.n, ps, env.pc);
+}
+
+// out = a * K_t (Shoup)
+__global__ void k_mul_scalar(u64* out, const u64* a, ScalarArg K, int n, size_t ps, const PrimeConst* __restrict__ pc) {
+    const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y, c = blockIdx.z;
+    const size_t off = c * ps + (size_t)t * n + k;
+    out[off] = shoup_mul(a[off], K.w[t], K.wsh[t], pc[t].q);
+}
+
+void launch_mul_scalar(const KernelEnv& env, u64* out, const u64* a, const ScalarArg& K, int limbs, size_t ps, cudaStream_t st) {
+    ProfScope pf(env, KK_POINTWISE, st, 1, 4.0 * limbs * 8.0 * env.n, 2.0 * limbs * env.n);
+    dim3 g(env.n / TPB, limbs, 2);
+    k_mul_scalar<<<g, TPB, 0, st>>>(out, a, K, env.n, ps, env.pc);
+}
+
+// out = a * pt, pt stored times R ([limbs][n])
+__global__ void k_mul_plain(u64* out, const u64* a, const u64* pt, int n, size_t ps, const PrimeConst* __restrict__ pc) {
+    const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y, c = blockIdx.z;
+    const size_t off = c * ps + (size_t)t * n + k;
+    const PrimeConst P = pc[t];
+    out[off] = mont_mul(a[off], pt[(size_t)t * n + k], P.q, P.qinv);
+}
+
+void launch_mul_plain(const KernelEnv& env, u64* out, const u64* a, const u64* pt, int limbs, size_t ps, cudaStream_t st) {
+    ProfScope pf(env, KK_POINTWISE, st, 1, 5.0 * limbs * 8.0 * env.n, 2.0 * limbs * env.n);
+    dim3 g(env.n / TPB, limbs, 2);
+    k_mul_plain<<<g, TPB, 0, st>>>(out, a, pt, env.n, ps, env.pc);
+}
+
+// d = [d0 | d1 | d2] each [limbs][n]: d0 = x0 y0, d1 = x0 y1 + x1 y0, d2 = x1 y1
+__global__ void k_tensor(u64* d, const u64* x, const u64* y, int limbs, int n, size_t ps, const PrimeConst* __restrict__ pc) {
+    const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y;
+    const PrimeConst P = pc[t];
+    const size_t off = (size_t)t * n + k;
+    const u64 x0 = x[off], x1 = x[ps + off], y0 = y[off], y1 = y[ps + off];
+    const size_t pl = (size_t)limbs * n;
+    u64 r0 = mont_mul(x0, y0, P.q, P.qinv);
+    Acc128 a1;
+    a1.mac(x0, y1);
+    a1.mac(x1, y0);
+    u64 r1 = a1.redc(P.q, P.qinv);
+    u64 r2 = mont_mul(x1, y1, P.q, P.qinv);
+    d[off] = shoup_mul(r0, P.r_mod, P.r_shoup, P.q);
+    d[pl + off] = shoup_mul(r1, P.r_mod, P.r_shoup, P.q);
+    d[2 * pl + off] = shoup_mul(r2, P.r_mod, P.r_shoup, P.q);
+}
+
+void launch_tensor(const KernelEnv& env, u64* d, const u64* x, const u64* y, int limbs, size_t ps, cudaStream_t st) {
+    ProfScope pf(env, KK_TENSOR, st, 1, 7.0 * limbs * 8.0 * env.n, 4.0 * limbs * env.n);
+    dim3 g(env.n / TPB, limbs);
+    k_tensor<<<g, TPB, 0, st>>>(d, x, y, limbs, env.n, ps, env.pc);
+}
+
+// ===========================================================================
+// Basis conversion (coefficient domain).
+// ===========================================================================
+// ModUp of every digit: ext[j][t][k], t over Q_l u P (QP limb order).
+__global__ void __launch_bounds__(TPB) k_modup(const u64* __restrict__ x, u64* __restrict__ ext, size_t ext_stride, int level,
+                                               int L, int alpha, ConvTables cv, int n, const PrimeConst* __restrict__ pc) {
+    const int k = blockIdx.x * TPB + threadIdx.x, j = blockIdx.y;
+    const int DS = cv.dsize;
+    const int lo = j * DS, hi = min(lo + DS, level + 1), ns = hi - lo;
+    const u64* tab = cv.modup + ((size_t)level * cv.beta_max + j) * cv.modup_stride;
+    const int T = L + 1 + alpha;
+    u64 y[RK_MAX_DIGIT];
+#pragma unroll
+    for (int i = 0; i < RK_MAX_DIGIT; i++) {
+        if (i < ns) {
+            const u64 qi = pc[lo + i].q;
+            y[i] = shoup_mul(x[(size_t)(lo + i) * n + k], tab[i], tab[DS + i], qi);
+        }
+    }
+    const int limbs = level + 1 + alpha;
+    u64* out = ext + (size_t)j * ext_stride + k;
+    for (int t = 0; t < limbs; t++) {
+        const int pid = t <= level ? t : L + 1 + (t - level - 1);
+        const PrimeConst P = pc[pid];
+        Acc128 acc;
+#pragma unroll
+        for (int i = 0; i < RK_MAX_DIGIT; i++)
+            if (i < ns) acc.mac(y[i], __ldg(tab + 2 * DS + (size_t)i * T + t));
+        out[(size_t)t * n] = acc.redc(P.q, P.qinv);
+    }
+}
+
+void launch_modup(const KernelEnv& env, const u64* x, u64* ext, size_t ext_stride, int level, int beta, cudaStream_t st) {
+    ProfScope pf(env, KK_MODUP, st, 1, ((double)(level + 1) + (double)beta * (level + 1 + env.alpha)) * 8.0 * env.n, (double)(level + 1 + env.alpha) * (level + 1) * env.n);
+    dim3 g(env.n / TPB, beta);
+    k_modup<<<g, TPB, 0, st>>>(x, ext, ext_stride, level, env.L, env.alpha, env.conv, env.n, env.pc);
+}
+
+// ModDown conversion of the P part of u ([2][l+1+alpha][n], P limbs already in the
+// coefficient domain) to w = [2][l+1][n].
+__global__ void __launch_bounds__(TPB) k_moddown_conv(const u64* __restrict__ u, u64* __restrict__ w, int level, int L, int alpha,
+                                                      ConvTables cv, int n, const PrimeConst* __restrict__ pc) {
+    const int k = blockIdx.x * TPB + threadIdx.x, c = blockIdx.y;
+    const int ul = level + 1 + alpha;
+    const u64* up = u + (size_t)c * ul * n + (size_t)(level + 1) * n + k;
+    u64 y[RK_MAX_SPECIAL];
+#pragma unroll
+    for (int kk = 0; kk < RK_MAX_SPECIAL; kk++) {
+        if (kk < alpha) {
+            const u64 pk = pc[L + 1 + kk].q;
+            y[kk] = shoup_mul(up[(size_t)kk * n], cv.moddown[kk], cv.moddown[alpha + kk], pk);
+        }
+    }
+    u64* out = w + (size_t)c * (level + 1) * n + k;
+    const u64* cm = cv.moddown + 2 * alpha;
+    for (int i = 0; i <= level; i++) {
+        const PrimeConst P = pc[i];
+        Acc128 acc;
+#pragma unroll
+        for (int kk = 0; kk < RK_MAX_SPECIAL; kk++)
+            if (kk < alpha) acc.mac(y[kk], __ldg(cm + (size_t)kk * (L + 1) + i));
+        out[(size_t)i * n] = acc.redc(P.q, P.qinv);
+    }
+}
+
+void launch_moddown_conv(const KernelEnv& env, const u64* u, u64* w, int level, cudaStream_t st) {
+    ProfScope pf(env, KK_MODDOWN, st, 1, (2.0 * env.alpha + 2.0 * (level + 1)) * 8.0 * env.n, 2.0 * (level + 1) * env.alpha * env.n);
+    dim3 g(env.n / TPB, 2);
+    k_moddown_conv<<<g, TPB, 0, st>>>(u, w, level, env.L, env.alpha, env.conv, env.n, env.pc);
+}
+
+// ===========================================================================
+// Key-switching inner product (evaluation domain), automorphism fused:
+//   u_c[t][k] = sum_j ext[j][t][src(k)] * key[j][c][prime(t)][k]   (key times R)
+// ===========================================================================
+__global__ void __launch_bounds__(TPB) k_ks_inner(const u64* __restrict__ ext, size_t ext_stride, const u64* __restrict__ key,
+                                                  u64* __restrict__ u, int level, int L, int alpha, int beta, u64 galois,
+                                                  int logn, const PrimeConst* __restrict__ pc) {
+    const int n = 1 << logn;
+    const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y;
+    const int pid = t <= level ? t : L + 1 + (t - level - 1);
+    const PrimeConst P = pc[pid];
+    const int src = galois ? galois_src(k, galois, logn) : k;
+    const size_t KL = (size_t)(L + 1 + alpha) * n;
+    Acc128 a0, a1;
+    for (int j = 0; j < beta; j++) {
+        const u64 e = ext[(size_t)j * ext_stride + (size_t)t * n + src];
+        const u64* kj = key + (size_t)j * 2 * KL + (size_t)pid * n + k;
+        a0.mac(e, kj[0]);
+        a1.mac(e, kj[KL]);
+    }
+    const int ul = level + 1 + alpha;
+    u[(size_t)t * n + k] = a0.redc(P.q, P.qinv);
+    u[(size_t)ul * n + (size_t)t * n + k] = a1.redc(P.q, P.qinv);
+}
+
+void launch_ks_inner(const KernelEnv& env, const u64* ext, size_t ext_stride, const u64* key, u64* u, int level, int beta,
+                     u64 galois, cudaStream_t st) {
+    ProfScope pf(env, KK_KS_INNER, st, 1, (3.0 * beta + 2.0) * (level + 1 + env.alpha) * 8.0 * env.n, 2.0 * beta * (level + 1 + env.alpha) * env.n);
+    dim3 g(env.n / TPB, level + 1 + env.alpha);
+    k_ks_inner<<<g, TPB, 0, st>>>(ext, ext_stride, key, u, level, env.L, env.alpha, beta, galois, env.logn, env.pc);
+}
+
+// out[c][t] = base_c[t] (automorphism applied to base0 when galois0 != 0) + (u[c][t] - w[c][t]) * P^-1;
+// base_c points at limb 0 of one polynomial, or is null.
+__global__ void k_ks_combine(u64* out, size_t ps, const u64* base0, u64 galois0, const u64* base1,
+                             const u64* __restrict__ u, const u64* __restrict__ w, int level, int alpha, ConvTables cv,
+                             int logn, const PrimeConst* __restrict__ pc) {
+    const int n = 1 << logn;
+    const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y, c = blockIdx.z;
+    const u64 q = pc[t].q;
+    const int ul = level + 1 + alpha;
+    u64 v = sub_mod(u[(size_t)c * ul * n + (size_t)t * n + k], w[(size_t)c * (level + 1) * n + (size_t)t * n + k], q);
+    v = shoup_mul(v, cv.pinv[2 * t], cv.pinv[2 * t + 1], q);
+    const u64* base = c == 0 ? base0 : base1;
+    if (base) {
+        const int src = (c == 0 && galois0) ? galois_src(k, galois0, logn) : k;
+        v = add_mod(v, base[(size_t)t * n + src], q);
+    }
+    out[(size_t)c * ps + (size_t)t * n + k] = v;
+}
+
+void launch_ks_combine(const KernelEnv& env, u64* out, size_t ps, const u64* base0, u64 galois0, const u64* base1,
+                       const u64* u, const u64* w, int level, cudaStream_t st) {
+    ProfScope pf(env, KK_KS_COMBINE, st, 1, 7.0 * (level + 1) * 8.0 * env.n, 2.0 * (level + 1) * env.n);
+    dim3 g(env.n / TPB, level + 1, 2);
+    k_ks_combine<<<g, TPB, 0, st>>>(out, ps, base0, galois0, base1, u, w, level, env.alpha, env.conv, env.logn, env.pc);
+}
+
+// ===========================================================================
+// Rescale: lift the (coefficient-domain) last limb, centred, into the lower limbs.
+// last: 2 polys at stride ls; v: [2][level][n].  grid (n/TPB, level, 2)
+// ===========================================================================
+__global__ void k_rescale_lift(const u64* last, size_t ls, u64* v, int level, int L, ConvTables cv, int n,
+                               const PrimeConst* __restrict__ pc) {
+    const int k = blockIdx.x * TPB + threadIdx.x, i = blockIdx.y, c = blockIdx.z;
+    const u64 ql = pc[level].q;
+    const u64 x = last[(size_t)c * ls + k];
+    const PrimeConst P = pc[i];
+    u64 r = shoup_mul(x, 1, P.one_shoup, P.q);
+    if (x > (ql >> 1)) r = sub_mod(r, cv.rescale[(size_t)level * 3 * (L + 1) + 2 * (L + 1) + i], P.q);
+    v[(size_t)c * level * n + (size_t)i * n + k] = r;
+}
+
+void launch_rescale_lift(const KernelEnv& env, const u64* last, size_t ls, u64* v, int level, cudaStream_t st) {
+    ProfScope pf(env, KK_RESCALE, st, 1, (2.0 + 2.0 * level) * 8.0 * env.n, 2.0 * level * env.n);
+    dim3 g(env.n / TPB, level, 2);
+    k_rescale_lift<<<g, TPB, 0, st>>>(last, ls, v, level, env.L, env.conv, env.n, env.pc);
+}
+
+// ct[c][i] = (ct[c][i] - v[c][i]) * q_l^-1, i < level (in place)
+__global__ void k_rescale_combine(u64* ct, size_t ps, const u64* v, int level, int L, ConvTables cv, int n,
+                                  const PrimeConst* __restrict__ pc) {
+    const int k = blockIdx.x * TPB + threadIdx.x, i = blockIdx.y, c = blockIdx.z;
+    const u64 q = pc[i].q;
+    const u64* tab = cv.rescale + (size_t)level * 3 * (L + 1);
+    const size_t off = (size_t)c * ps + (size_t)i * n + k;
+    u64 d = sub_mod(ct[off], v[(size_t)c * level * n + (size_t)i * n + k], q);
+    ct[off] = shoup_mul(d, tab[i], tab[(L + 1) + i], q);
+}
+
+void launch_rescale_combine(const KernelEnv& env, u64* ct, size_t ps, const u64* v, int level, cudaStream_t st) {
+    ProfScope pf(env, KK_RESCALE, st, 1, 6.0 * level * 8.0 * env.n, 2.0 * level * env.n);
+    dim3 g(env.n / TPB, level, 2);
+    k_rescale_combine<<<g, TPB, 0, st>>>(ct, ps, v, level, env.L, env.conv, env.n, env.pc);
+}
+
+// ===========================================================================
+// Client-side helpers: signed reduction, uniform sampling, key assembly, decrypt.
+// ===========================================================================
+// dst[t][k] = src[k] mod prime(t) for `limbs` limbs of the LimbSet's first poly map.
+__global__ void k_reduce_signed(const int64_t* src, u64* dst, LimbSet s, int n, const PrimeConst* __restrict__ pc) {
+    const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y, p = blockIdx.z;
+    const PrimeConst P = pc[limb_prime(s, t)];
+    const int64_t x = src[(size_t)p * n + k];
+    const u64 ax = x < 0 ? (u64)(-(x + 1)) + 1u : (u64)x;
+    u64 r = shoup_mul(ax, 1, P.one_shoup, P.q);
+    if (x < 0 && r) r = P.q - r;
+    dst[(size_t)p * s.poly_stride + (size_t)t * n + k] = r;
+}
+
+void launch_reduce_signed(const KernelEnv& env, const int64_t* src, const LimbSet& s, cudaStream_t st) {
+    ProfScope pf(env, KK_CLIENT, st, 1, 0.0, 0.0);
+    dim3 g(env.n / TPB, s.n_limbs, s.n_polys);
+    k_reduce_signed<<<g, TPB, 0, st>>>(src, s.base, s, env.n, env.pc);
+}
+
+__device__ __forceinline__ u64 splitmix64(u64 x) {
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+// Uniform residues: word k of limb t of poly p from SplitMix64 of a per-word counter.
+__global__ void k_uniform(LimbSet s, u64 seed, u64 stream_id, int n, const PrimeConst* __restrict__ pc) {
+    const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y, p = blockIdx.z;
+    const u64 q = pc[limb_prime(s, t)].q;
+    const u64 ctr = ((stream_id * 64 + (u64)p) * 128 + (u64)t) * (u64)n + (u64)k;
+    const u64 r = splitmix64(seed ^ splitmix64(ctr));
+    s.base[(size_t)p * s.poly_stride + (size_t)t * n + k] = umulhi64(r, q);
+}
+
+void launch_uniform(const KernelEnv& env, const LimbSet& s, u64 seed, u64 stream_id, cudaStream_t st) {
+    ProfScope pf(env, KK_CLIENT, st, 1, 0.0, 0.0);
+    dim3 g(env.n / TPB, s.n_limbs, s.n_polys);
+    k_uniform<<<g, TPB, 0, st>>>(s, seed, stream_id, env.n, env.pc);
+}
+
+// Switching-key digit in Montgomery form over all primes (eval domain):
+//   b = -a s + e + gad_t s',  key_b = b R, key_a = a R.
+// a, e, s' normal form; s_R = s R.  grid (n/TPB, n_primes)
+__global__ void k_key_digit(u64* kb, u64* ka, const u64* a, const u64* e, const u64* s_R, const u64* sp, const u64* gad,
+                            int n, const PrimeConst* __restrict__ pc) {
+    const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y;
+    const PrimeConst P = pc[t];
+    const size_t off = (size_t)t * n + k;
+    const u64 as = mont_mul(a[off], s_R[off], P.q, P.qinv);
+    u64 b = sub_mod(e[off], as, P.q);
+    if (gad[t]) b = add_mod(b, mont_mul(sp[off], gad[t], P.q, P.qinv), P.q);   // gad stored times R
+    kb[off] = mont_mul(b, P.r2, P.q, P.qinv);
+    ka[off] = mont_mul(a[off], P.r2, P.q, P.qinv);
+}
+
+void launch_key_digit(const KernelEnv& env, u64* kb, u64* ka, const u64* a, const u64* e, const u64* s_R, const u64* sp,
+                      const u64* gad_dev, int n_primes, cudaStream_t st) {
+    ProfScope pf(env, KK_CLIENT, st, 1, 0.0, 0.0);
+    dim3 g(env.n / TPB, n_primes);
+    k_key_digit<<<g, TPB, 0, st>>>(kb, ka, a, e, s_R, sp, gad_dev, env.n, env.pc);
+}
+
+// x <- x R (to Montgomery form), over `limbs` limbs of `polys` polys using LimbSet prime map
+__global__ void k_to_mont(LimbSet s, int n, const PrimeConst* __restrict__ pc) {
+    const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y, p = blockIdx.z;
+    const PrimeConst P = pc[limb_prime(s, t)];
+    u64* x = s.base + (size_t)p * s.poly_stride + (size_t)t * n + k;
+    *x = mont_mul(*x, P.r2, P.q, P.qinv);
+}
+
+void launch_to_mont(const KernelEnv& env, const LimbSet& s, cudaStream_t st) {
+    ProfScope pf(env, KK_CLIENT, st, 1, 0.0, 0.0);
+    dim3 g(env.n / TPB, s.n_limbs, s.n_polys);
+    k_to_mont<<<g, TPB, 0, st>>>(s, env.n, env.pc);
+}
+
+// out[t][k] = x[t][src(k)] (automorphism in the eval domain) over `limbs` contiguous limbs
+__global__ void k_automorph(u64* out, const u64* x, u64 g, int logn) {
+    const int n = 1 << logn;
+    const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y;
+    out[(size_t)t * n + k] = x[(size_t)t * n + galois_src(k, g, logn)];
+}
+
+void launch_automorph(const KernelEnv& env, u64* out, const u64* x, u64 g, int limbs, cudaStream_t st) {
+    ProfScope pf(env, KK_CLIENT, st, 1, 0.0, 0.0);
+    dim3 g2(env.n / TPB, limbs);
+    k_automorph<<<g2, TPB, 0, st>>>(out, x, g, env.logn);
+}
+
+// m[t] = c0[t] + c1[t] s[t] (s times R), t <= level; m is [limbs][n]
+__global__ void k_decrypt(u64* m, const u64* c0, const u64* c1, const u64* s_R, int n, const PrimeConst* __restrict__ pc) {
+    const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y;
+    const PrimeConst P = pc[t];
+    const size_t off = (size_t)t * n + k;
+    m[off] = add_mod(c0[off], mont_mul(c1[off], s_R[off], P.q, P.qinv), P.q);
+}
+
+void launch_decrypt(const KernelEnv& env, u64* m, const u64* c0, const u64* c1, const u64* s_R, int limbs, cudaStream_t st) {
+    ProfScope pf(env, KK_CLIENT, st, 1, 0.0, 0.0);
+    dim3 g(env.n / TPB, limbs);
+    k_decrypt<<<g, TPB, 0, st>>>(m, c0, c1, s_R, env.n, env.pc);
+}
+
+// Public-key encryption: c0 = v pk0 + e0 + m, c1 = v pk1 + e1 (pk times R).
+// r = [v | e0 | e1 | m] each [limbs][n] reduced and transformed.
+__global__ void k_encrypt(u64* ct, size_t ps, const u64* r, const u64* pk, size_t pk_ps, int limbs, int n,
+                          const PrimeConst* __restrict__ pc) {
+    const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y;
+    const PrimeConst P = pc[t];
+    const size_t off = (size_t)t * n + k, pl = (size_t)limbs * n;
+    const u64 v = r[off], e0 = r[pl + off], e1 = r[2 * pl + off], m = r[3 * pl + off];
+    ct[off] = add_mod(add_mod(mont_mul(v, pk[off], P.q, P.qinv), e0, P.q), m, P.q);
+    ct[ps + off] = add_mod(mont_mul(v, pk[pk_ps + off], P.q, P.qinv), e1, P.q);
+}
+
+void launch_encrypt(const KernelEnv& env, u64* ct, size_t ps, const u64* r, const u64* pk, size_t pk_ps, int limbs, cudaStream_t st) {
+    ProfScope pf(env, KK_CLIENT, st, 1, 0.0, 0.0);
+    dim3 g(env.n / TPB, limbs);
+    k_encrypt<<<g, TPB, 0, st>>>(ct, ps, r, pk, pk_ps, limbs, env.n, env.pc);
+}
+
+// pk0 = -a s + e (s times R), normal form; then both stored times R.  grid (n/TPB, limbs)
+__global__ void k_pk(u64* pk, size_t ps, const u64* a, const u64* e, const u64* s_R, int n, const PrimeConst* __restrict__ pc) {
+    const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y;
+    const PrimeConst P = pc[t];
+    const size_t off = (size_t)t * n + k;
+    u64 b = sub_mod(e[off], mont_mul(a[off], s_R[off], P.q, P.qinv), P.q);
+    pk[off] = mont_mul(b, P.r2, P.q, P.qinv);
+    pk[ps + off] = mont_mul(a[off], P.r2, P.q, P.qinv);
+}
+
+void launch_pk(const KernelEnv& env, u64* pk, size_t ps, const u64* a, const u64* e, const u64* s_R, int limbs, cudaStream_t st) {
+    ProfScope pf(env, KK_CLIENT, st, 1, 0.0, 0.0);
+    dim3 g(env.n / TPB, limbs);
+    k_pk<<<g, TPB, 0, st>>>(pk, ps, a, e, s_R, env.n, env.pc);
+}
+
+// s' = s * s (eval domain), inputs times R: out = s_R s_R R^-1 = s^2 R -> normal form via a second redc
+__global__ void k_square_secret(u64* out, const u64* s_R, int n, const PrimeConst* __restrict__ pc) {
+    const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y;
+    const PrimeConst P = pc[t];
+    const size_t off = (size_t)t * n + k;
+    const u64 sR = s_R[off];
+    const u64 s = mont_redc(sR, 0, P.q, P.qinv);
+    out[off] = mont_mul(s, sR, P.q, P.qinv);   // s * sR * R^-1 = s^2
+}
+
+void launch_square_secret(const KernelEnv& env, u64* out, const u64* s_R, int limbs, cudaStream_t st) {
+    ProfScope pf(env, KK_CLIENT, st, 1, 0.0, 0.0);
+    dim3 g(env.n / TPB, limbs);
+    k_square_secret<<<g, TPB, 0, st>>>(out, s_R, env.n, env.pc);
+}
+
+// from Montgomery form to normal form
+__global__ void k_from_mont(u64* out, const u64* x, int n, const PrimeConst* __restrict__ pc) {
+    const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y;
+    const PrimeConst P = pc[t];
+    const size_t off = (size_t)t * n + k;
+    out[off] = mont_redc(x[off], 0, P.q, P.qinv);
+}
+
+void launch_from_mont(const KernelEnv& env, u64* out, const u64* x, int limbs, cudaStream_t st) {
+    ProfScope pf(env, KK_CLIENT, st, 1, 0.0, 0.0);
+    dim3 g(env.n / TPB, limbs);
+    k_from_mont<<<g, TPB, 0, st>>>(out, x, env.n, env.pc);
+}

@@ -1,0 +1,219 @@
+// Internal declarations of the CUDA RNS-CKKS library behind include/rankfhe.h.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/rankfhe.h"
+#include "modarith.cuh"
+
+// ---------------------------------------------------------------------------
+// Errors: internal code throws rk_error; the C-ABI converts to rk_status.
+// ---------------------------------------------------------------------------
+struct rk_error : std::runtime_error {
+    rk_status code;
+    rk_error(rk_status c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+#define RK_CUDA(call)                                                                       \
+    do {                                                                                    \
+        cudaError_t _e = (call);                                                            \
+        if (_e != cudaSuccess)                                                              \
+            throw rk_error(RK_ECUDA, std::string(#call) + ": " + cudaGetErrorString(_e));   \
+    } while (0)
+#define RK_REQUIRE(cond, code, msg)                  \
+    do {                                             \
+        if (!(cond)) throw rk_error((code), (msg));  \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Device-side description of a set of residue polynomials.
+// Limb t of poly p lives at base + p * poly_stride + t * n.
+// Limb t uses prime id  t < split ? t + off_lo : off_hi + (t - split).
+// ---------------------------------------------------------------------------
+struct LimbSet {
+    u64* base;
+    size_t poly_stride;
+    int n_polys;
+    int n_limbs;
+    int split;
+    int off_lo;
+    int off_hi;
+};
+
+__host__ __device__ __forceinline__ int limb_prime(const LimbSet& s, int t) {
+    return t < s.split ? t + s.off_lo : s.off_hi + (t - s.split);
+}
+
+// Per-level constants of the basis conversions (device memory, see context.cu).
+struct ConvTables {
+    // ModUp, for level l and digit j: block at modup + (l * beta_max + j) * modup_stride:
+    //   [0, DS)           (D/q_i)^-1 mod q_i          (source i of the digit)
+    //   [DS, 2DS)         Shoup companions
+    //   [2DS, 2DS + DS*T) (D/q_i) mod prime(t) times R, t = 0 .. l+alpha, row-major [i][t]
+    //   T = L + 1 + alpha is the row length (only the first l+1+alpha columns are used)
+    const u64* modup;
+    size_t modup_stride;
+    int beta_max;
+    int dsize;
+    // ModDown (level independent): [0, A) (P/p_k)^-1 mod p_k, [A, 2A) Shoup,
+    //   [2A, 2A + A*(L+1)) (P/p_k) mod q_i times R, row-major [k][i]
+    const u64* moddown;
+    // P^-1 mod q_i and Shoup companion: [2 * (L+1)]
+    const u64* pinv;
+    // Rescale for level l: block at rescale + l * 3 * (L+1):
+    //   [0, L+1) q_l^-1 mod q_i; [L+1, 2(L+1)) Shoup; [2(L+1), 3(L+1)) q_l mod q_i
+    const u64* rescale;
+};
+
+struct DevTables {
+    const u64* psi;       // [n_primes][n]  psi^brev(i)
+    const u64* psi_sh;
+    const u64* ipsi;      // [n_primes][n]  psi^-brev(i)
+    const u64* ipsi_sh;
+};
+
+// Constants of a scalar multiplication (one residue per limb, with Shoup companions).
+struct ScalarArg {
+    u64 w[RK_MAX_PRIMES];
+    u64 wsh[RK_MAX_PRIMES];
+};
+
+#define RK_MAX_DIGIT 8
+#define RK_MAX_SPECIAL 8
+
+// Kernel kinds the profiler can time (rk_profile_start names).
+enum KernelKind {
+    KK_NTT_FWD = 0, KK_NTT_INV, KK_MODUP, KK_KS_INNER, KK_MODDOWN, KK_KS_COMBINE, KK_TENSOR, KK_RESCALE,
+    KK_POINTWISE, KK_CLIENT, KK_COUNT
+};
+extern const char* const kKernelKindNames[KK_COUNT];
+
+// Launch counter and CUDA-event timing of one kernel kind on the context stream.
+struct Profiler {
+    uint64_t launches = 0;        // every kernel this library launched
+    int target = -1;              // kind being timed, -1 = none
+    std::vector<cudaEvent_t> ev;  // start/stop pairs
+    size_t used = 0;
+    double bytes = 0, ops = 0;    // algorithmic bytes and modular products of the timed launches
+    uint64_t timed = 0;
+};
+
+// Everything a kernel launcher needs: sizes and device tables.
+struct KernelEnv {
+    int logn, n, L, alpha;
+    const PrimeConst* pc;   // device array [n_primes]
+    DevTables tw;
+    ConvTables conv;
+    Profiler* prof;
+};
+
+// ---------------------------------------------------------------------------
+// Host context
+// ---------------------------------------------------------------------------
+struct DevBuf {
+    u64* p = nullptr;
+    size_t words = 0;
+};
+
+struct SwitchKeyDev {
+    u64* data = nullptr;  // [beta_L][2][L+1+alpha][n], evaluation domain, Montgomery form
+};
+
+struct rk_ctx {
+    rk_params prm{};
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int log_n = 0, n = 0, L = 0, alpha = 0, dsize = 0, n_primes = 0;
+    std::vector<u64> primes;      // q_0..q_L, p_0..p_{alpha-1}
+    std::vector<double> scales;   // Delta_0..Delta_L
+    std::vector<u64> ninv;        // n^-1 mod prime
+    // device tables
+    u64* d_tw = nullptr;          // 4 * n_primes * n
+    u64* d_conv = nullptr;
+    PrimeConst* d_pc = nullptr;
+    std::vector<PrimeConst> h_pc;
+    KernelEnv env{};
+    Profiler prof;
+    std::vector<u64> h_pinv;      // host copies used by the encoder/decoder
+    // keys (device)
+    u64* d_sk = nullptr;          // secret in eval domain over all primes, Montgomery form
+    std::vector<int64_t> h_sk;    // secret coefficients (ternary)
+    u64* d_pk = nullptr;          // [2][L+1][n] eval, Montgomery form
+    SwitchKeyDev rlk;
+    std::map<u64, SwitchKeyDev> gal;
+    uint64_t enc_counter = 0;     // encryption randomness counter
+    uint64_t seed = 0;
+    // scratch (grows on demand; stream ordered)
+    u64* d_scratch = nullptr;
+    size_t scratch_words = 0;
+    // plaintext caches: key = (kind, N, Q, n_real, level)
+    std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint32_t, int>, u64*> plain_cache;
+    std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint32_t>, std::vector<double>> encodings;
+    // op counters
+    uint64_t n_ks = 0, n_rot = 0, n_mul = 0, n_rescale = 0;
+    size_t ct_words() const { return (size_t)2 * (L + 1) * n; }
+    size_t poly_stride() const { return (size_t)(L + 1) * n; }
+    int qp_limbs(int level) const { return level + 1 + alpha; }
+    int beta(int level) const { return (level + 1 + dsize - 1) / dsize; }
+    u64* scratch(size_t words);
+};
+
+struct rk_ct {
+    rk_ctx* ctx = nullptr;
+    u64* data = nullptr;   // [2][L+1][n] (only limbs 0..level are meaningful), evaluation domain
+    int level = 0;
+    uint32_t N = 0;        // padded vector length (power of two)
+    uint32_t n_real = 0;   // unpadded length
+    uint32_t Q = 1;        // queries packed at stride N^2
+    uint32_t layout = 0;   // RK_LAYOUT_ROW / RK_LAYOUT_COL
+};
+
+// ---------------------------------------------------------------------------
+// Evaluator (evaluator.cu)
+// ---------------------------------------------------------------------------
+rk_ct* ct_alloc(rk_ctx* c, int level);
+void ct_free(rk_ct* ct);
+rk_ct* ct_clone_meta(const rk_ct* src, int level);
+
+void ev_add(rk_ctx* c, const rk_ct* a, const rk_ct* b, rk_ct* out);
+void ev_sub(rk_ctx* c, const rk_ct* a, const rk_ct* b, rk_ct* out);
+void ev_neg(rk_ctx* c, const rk_ct* a, rk_ct* out);
+void ev_add_const(rk_ctx* c, const rk_ct* a, double v, rk_ct* out);
+void ev_rescale_inplace(rk_ctx* c, rk_ct* a);
+void ev_mul_scalar(rk_ctx* c, const rk_ct* a, double v, rk_ct* out);        // out at level-1
+void ev_mul(rk_ctx* c, const rk_ct* a, const rk_ct* b, rk_ct* out);         // out at level-1
+void ev_mul_plain(rk_ctx* c, const rk_ct* a, uint32_t kind, uint32_t N, uint32_t Q, uint32_t n_real, rk_ct* out);
+void ev_rotate_many(rk_ctx* c, const rk_ct* a, const int* r, int k, rk_ct** outs);  // left rotations
+void ev_level_down(rk_ctx* c, const rk_ct* a, int target, rk_ct* out);
+void ev_copy(rk_ctx* c, const rk_ct* a, rk_ct* out);
+
+// keys / client ops
+void keys_generate(rk_ctx* c, uint64_t seed, const std::vector<int>& rotations);
+void keys_add_rotations(rk_ctx* c, const std::vector<int>& rotations);
+void key_import(rk_ctx* c, uint32_t kind, uint64_t galois, const uint64_t* coeffs, size_t words);
+void secret_import(rk_ctx* c, const int64_t* s, size_t n);
+u64 galois_left(const rk_ctx* c, int r);
+rk_ct* encrypt_values(rk_ctx* c, const double* v, uint32_t count, uint32_t N, uint32_t Q, uint32_t n_real);
+void decrypt_slots(rk_ctx* c, const rk_ct* ct, std::vector<double>& slots);
+rk_ct* ct_import(rk_ctx* c, const uint64_t* coeffs, int level);
+void ct_export(rk_ctx* c, const rk_ct* ct, uint64_t* coeffs);
+
+// encoder (encoder.cpp)
+void encode_unscaled(int log_n, const double* z, size_t count, std::vector<double>& u);
+void decode_coeffs(int log_n, const std::vector<double>& m, std::vector<double>& slots);
+
+// masks (circuits.cpp)
+void mask_slot_values(uint32_t kind, uint32_t N, uint32_t Q, uint32_t n_real, size_t slots, std::vector<double>& v);
+
+// host number theory (context.cu)
+u64 h_mulmod(u64 a, u64 b, u64 q);
+u64 h_powmod(u64 a, u64 e, u64 q);
+u64 h_invmod(u64 a, u64 q);
+int64_t round_half_away(double x);

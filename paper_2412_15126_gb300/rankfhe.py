@@ -1,0 +1,300 @@
+"""ctypes binding of the C-ABI in ``include/rankfhe.h`` (argument marshalling only).
+
+Every operation runs in the CUDA library ``_lib/librankfhe.so``; there is no
+fallback.  Importing this module loads the library and raises ``ImportError`` if
+it has not been built (``python -m paper_2412_15126_gb300.build`` or
+``__graft_entry__.build()``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import weakref
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "librankfhe.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"CUDA library not built: {LIB_PATH} is missing (run __graft_entry__.build())")
+_L = ctypes.CDLL(LIB_PATH)
+
+RK_OK, RK_EINVAL, RK_ENOMEM, RK_EDEPTH, RK_ETIMEOUT, RK_ECUDA, RK_EFORMAT, RK_ENOKEY = range(8)
+STATUS_NAMES = {0: "RK_OK", 1: "RK_EINVAL", 2: "RK_ENOMEM", 3: "RK_EDEPTH", 4: "RK_ETIMEOUT",
+                5: "RK_ECUDA", 6: "RK_EFORMAT", 7: "RK_ENOKEY"}
+LAYOUT_ROW, LAYOUT_COL = 0, 1
+MASK_ROW0, MASK_COL0, MASK_TIE, MASK_TRI, MASK_VALID = 1, 2, 3, 4, 5
+KEY_RELIN, KEY_GALOIS = 1, 2
+TIES_CORRECT = 1
+
+
+class RkError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_uint32) for name in
+                ("log_n", "n_limbs", "n_special", "digit_size", "log_scale", "log_q0", "log_special", "d_g", "d_f")]
+
+
+_vp = ctypes.c_void_p
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_dp = ctypes.POINTER(ctypes.c_double)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_u32 = ctypes.c_uint32
+_sz = ctypes.c_size_t
+
+
+def _sig(name, args, res=ctypes.c_int):
+    f = getattr(_L, name)
+    f.argtypes = args
+    f.restype = res
+    return f
+
+
+_sig("rk_ctx_create", [ctypes.POINTER(Params), ctypes.c_int, _vp, ctypes.POINTER(_vp)])
+_sig("rk_ctx_destroy", [_vp], None)
+_sig("rk_ctx_moduli", [_vp, _u64p, _sz, ctypes.POINTER(_sz)])
+_sig("rk_ctx_scales", [_vp, _dp, _sz])
+_sig("rk_sync", [_vp])
+_sig("rk_ctx_counters", [_vp, _u64p])
+_sig("rk_keygen", [_vp, ctypes.c_uint64, _u32])
+_sig("rk_keygen_rotations", [_vp, _i32p, _sz])
+_sig("rk_secret_import", [_vp, _i64p, _sz])
+_sig("rk_key_import", [_vp, _u32, ctypes.c_uint64, _u64p, _sz])
+_sig("rk_galois_left", [_vp, ctypes.c_int32], ctypes.c_uint64)
+_sig("rk_encoding_import", [_vp, _u32, _u32, _u32, _u32, _dp, _sz])
+_sig("rk_encrypt", [_vp, _dp, _u32, _u32, _u32, _u32, ctypes.POINTER(_vp)])
+_sig("rk_decrypt_slots", [_vp, _vp, _dp, _sz])
+_sig("rk_decrypt", [_vp, _vp, _dp, _sz, ctypes.POINTER(_u32)])
+_sig("rk_ct_import", [_vp, _u64p, _u32, _u32, _u32, _u32, ctypes.POINTER(_vp)])
+_sig("rk_ct_export", [_vp, _u64p, _sz])
+_sig("rk_ct_level", [_vp], _u32)
+_sig("rk_ct_free", [_vp], None)
+_sig("rk_rotate", [_vp, _vp, ctypes.c_int32, ctypes.POINTER(_vp)])
+_sig("rk_rotate_many", [_vp, _vp, _i32p, _u32, ctypes.POINTER(_vp)])
+for _n in ("rk_add", "rk_sub", "rk_mul"):
+    _sig(_n, [_vp, _vp, _vp, ctypes.POINTER(_vp)])
+_sig("rk_add_const", [_vp, _vp, ctypes.c_double, ctypes.POINTER(_vp)])
+_sig("rk_mul_scalar", [_vp, _vp, ctypes.c_double, ctypes.POINTER(_vp)])
+_sig("rk_mul_mask", [_vp, _vp, _u32, ctypes.POINTER(_vp)])
+_sig("rk_rescale", [_vp, _vp, ctypes.POINTER(_vp)])
+_sig("rk_rank", [_vp, _vp, _u32, ctypes.POINTER(_vp)])
+_sig("rk_compare_matrix", [_vp, _vp, ctypes.POINTER(_vp)])
+_sig("rk_rank_batch", [_vp, ctypes.POINTER(_vp), _sz, _u32, ctypes.POINTER(_vp)])
+_sig("rk_ntt_forward", [_vp, _vp, _u32, _u32])
+_sig("rk_ntt_inverse", [_vp, _vp, _u32, _u32])
+_sig("rk_profile_start", [_vp, ctypes.c_char_p])
+_sig("rk_profile_stop", [_vp, _dp])
+_sig("rk_launch_count", [_vp], ctypes.c_uint64)
+_sig("rk_last_error", [], ctypes.c_char_p)
+
+
+def _check(status):
+    if status != RK_OK:
+        raise RkError(status, _L.rk_last_error().decode(errors="replace"))
+
+
+def raw(name):
+    """The raw ctypes function of a C-ABI entry point."""
+    return getattr(_L, name)
+
+
+def library_path() -> str:
+    return LIB_PATH
+
+
+class Ciphertext:
+    def __init__(self, ctx: "Context", handle: int):
+        self.ctx = ctx
+        self.handle = ctypes.c_void_p(handle)
+        ctx._live.add(self)
+
+    @property
+    def level(self) -> int:
+        return int(_L.rk_ct_level(self.handle))
+
+    def free(self):
+        if self.handle and self.handle.value:
+            _L.rk_ct_free(self.handle)
+            self.handle = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def export(self) -> np.ndarray:
+        n = self.ctx.n
+        out = np.empty((2, self.level + 1, n), dtype=np.uint64)
+        _check(_L.rk_ct_export(self.handle, out.ctypes.data_as(_u64p), out.size))
+        return out
+
+
+class Context:
+    def __init__(self, log_n, n_limbs, n_special, digit_size, log_scale, log_q0=60, log_special=61,
+                 d_g=4, d_f=2, device=0, stream=None):
+        self.params = Params(log_n, n_limbs, n_special, digit_size, log_scale, log_q0, log_special, d_g, d_f)
+        h = _vp()
+        _check(_L.rk_ctx_create(ctypes.byref(self.params), device, _vp(stream) if stream else None, ctypes.byref(h)))
+        self.handle = h
+        self.n = 1 << log_n
+        self._live = weakref.WeakSet()
+
+    def close(self):
+        """Free every ciphertext still alive, then the context."""
+        if self.handle and self.handle.value:
+            for ct in list(self._live):
+                ct.free()
+            _L.rk_ctx_destroy(self.handle)
+            self.handle = _vp(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- parameters ----
+    def moduli(self) -> list:
+        cnt = _sz()
+        _check(_L.rk_ctx_moduli(self.handle, None, 0, ctypes.byref(cnt)))
+        out = (ctypes.c_uint64 * cnt.value)()
+        _check(_L.rk_ctx_moduli(self.handle, out, cnt.value, ctypes.byref(cnt)))
+        return [int(x) for x in out]
+
+    def scales(self) -> list:
+        L1 = self.params.n_limbs
+        out = (ctypes.c_double * L1)()
+        _check(_L.rk_ctx_scales(self.handle, out, L1))
+        return list(out)
+
+    def sync(self):
+        _check(_L.rk_sync(self.handle))
+
+    def counters(self) -> dict:
+        out = (ctypes.c_uint64 * 4)()
+        _check(_L.rk_ctx_counters(self.handle, out))
+        return dict(zip(("key_switch", "rotate", "mul", "rescale"), [int(x) for x in out]))
+
+    # ---- keys ----
+    def keygen(self, seed: int, max_len: int):
+        _check(_L.rk_keygen(self.handle, seed, max_len))
+
+    def keygen_rotations(self, rs):
+        arr = (ctypes.c_int32 * len(rs))(*rs)
+        _check(_L.rk_keygen_rotations(self.handle, arr, len(rs)))
+
+    def secret_import(self, s):
+        s = np.ascontiguousarray(s, dtype=np.int64)
+        _check(_L.rk_secret_import(self.handle, s.ctypes.data_as(_i64p), s.size))
+
+    def key_import(self, kind, galois, data):
+        data = np.ascontiguousarray(data, dtype=np.uint64)
+        _check(_L.rk_key_import(self.handle, kind, galois, data.ctypes.data_as(_u64p), data.size))
+
+    def galois_left(self, r: int) -> int:
+        return int(_L.rk_galois_left(self.handle, r))
+
+    def encoding_import(self, kind, N, Q, n_real, u):
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        _check(_L.rk_encoding_import(self.handle, kind, N, Q, n_real, u.ctypes.data_as(_dp), u.size))
+
+    # ---- client ----
+    def encrypt(self, values, N=None, Q=1, n_real=None) -> Ciphertext:
+        v = np.ascontiguousarray(values, dtype=np.float64)
+        if n_real is None:
+            n_real = v.size // Q
+        if N is None:
+            N = 1 << max(0, (int(n_real) - 1).bit_length())
+        h = _vp()
+        _check(_L.rk_encrypt(self.handle, v.ctypes.data_as(_dp), v.size, N, Q, n_real, ctypes.byref(h)))
+        return Ciphertext(self, h.value)
+
+    def decrypt(self, ct: Ciphertext) -> np.ndarray:
+        cnt = _u32()
+        _check(_L.rk_decrypt(self.handle, ct.handle, None, 0, ctypes.byref(cnt)))
+        out = np.empty(cnt.value, dtype=np.float64)
+        _check(_L.rk_decrypt(self.handle, ct.handle, out.ctypes.data_as(_dp), out.size, ctypes.byref(cnt)))
+        return out
+
+    def decrypt_slots(self, ct: Ciphertext) -> np.ndarray:
+        out = np.empty(self.n // 2, dtype=np.float64)
+        _check(_L.rk_decrypt_slots(self.handle, ct.handle, out.ctypes.data_as(_dp), out.size))
+        return out
+
+    def ct_import(self, coeffs, level, N=1, Q=1, n_real=None) -> Ciphertext:
+        c = np.ascontiguousarray(coeffs, dtype=np.uint64)
+        h = _vp()
+        _check(_L.rk_ct_import(self.handle, c.ctypes.data_as(_u64p), level, N, Q, n_real or N, ctypes.byref(h)))
+        return Ciphertext(self, h.value)
+
+    # ---- operations ----
+    def _out(self, fn, *args) -> Ciphertext:
+        h = _vp()
+        _check(fn(self.handle, *args, ctypes.byref(h)))
+        return Ciphertext(self, h.value)
+
+    def rotate(self, ct, r):
+        return self._out(_L.rk_rotate, ct.handle, int(r))
+
+    def rotate_many(self, ct, rs):
+        arr = (ctypes.c_int32 * len(rs))(*rs)
+        outs = (_vp * len(rs))()
+        _check(_L.rk_rotate_many(self.handle, ct.handle, arr, len(rs), outs))
+        return [Ciphertext(self, o) for o in outs]
+
+    def add(self, a, b):
+        return self._out(_L.rk_add, a.handle, b.handle)
+
+    def sub(self, a, b):
+        return self._out(_L.rk_sub, a.handle, b.handle)
+
+    def mul(self, a, b):
+        return self._out(_L.rk_mul, a.handle, b.handle)
+
+    def add_const(self, a, v):
+        return self._out(_L.rk_add_const, a.handle, float(v))
+
+    def mul_scalar(self, a, v):
+        return self._out(_L.rk_mul_scalar, a.handle, float(v))
+
+    def mul_mask(self, a, kind):
+        return self._out(_L.rk_mul_mask, a.handle, kind)
+
+    def rescale(self, a):
+        return self._out(_L.rk_rescale, a.handle)
+
+    def compare_matrix(self, ct):
+        return self._out(_L.rk_compare_matrix, ct.handle)
+
+    def rank(self, ct, flags=0):
+        return self._out(_L.rk_rank, ct.handle, flags)
+
+    def rank_batch(self, cts, flags=0):
+        ins = (_vp * len(cts))(*[c.handle.value for c in cts])
+        outs = (_vp * len(cts))()
+        _check(_L.rk_rank_batch(self.handle, ins, len(cts), flags, outs))
+        return [Ciphertext(self, o) for o in outs]
+
+    def profile_start(self, kind):
+        _check(_L.rk_profile_start(self.handle, kind.encode() if kind else None))
+
+    def profile_stop(self) -> dict:
+        out = (ctypes.c_double * 4)()
+        _check(_L.rk_profile_stop(self.handle, out))
+        return {"ms": out[0], "launches": int(out[1]), "bytes": out[2], "ops": out[3]}
+
+    def launch_count(self) -> int:
+        return int(_L.rk_launch_count(self.handle))
+
+    def ntt_forward(self, dev_ptr: int, limbs: int, first_prime: int):
+        _check(_L.rk_ntt_forward(self.handle, _vp(dev_ptr), limbs, first_prime))
+
+    def ntt_inverse(self, dev_ptr: int, limbs: int, first_prime: int):
+        _check(_L.rk_ntt_inverse(self.handle, _vp(dev_ptr), limbs, first_prime))

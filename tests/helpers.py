@@ -1,0 +1,59 @@
+"""Shared test set-up: the parameter sets, the oracle's keys and encodings imported
+into a CUDA context, and conversions between the two sides' formats."""
+from __future__ import annotations
+
+import numpy as np
+
+from oracle import ckks, circuits
+
+# name -> (log_n, n_limbs, log_q0, log_scale, n_special, log_special, digit_size, d_g, d_f)
+CONFIGS = {
+    "small": (11, 6, 60, 40, 2, 61, 2, 1, 1),
+    "cfg1": (13, 14, 40, 40, 1, 61, 1, 2, 1),       # N = 8 rank, n = 2^13, 14 x ~40-bit + 1 special
+    "cfg2": (16, 28, 60, 45, 3, 61, 3, 4, 2),       # N = 128 rank, n = 2^16, 28 limbs + 3 special
+    "cfg3": (16, 34, 60, 45, 3, 61, 3, 3, 2),       # N = 128 ties, 34 limbs
+}
+
+MASK_IDS = {"row0": 1, "col0": 2, "tie": 3, "tri": 4, "valid": 5}
+
+
+def oracle_params(name):
+    log_n, n_limbs, log_q0, log_scale, alpha, log_sp, dsize, _, _ = CONFIGS[name]
+    return ckks.gen_params(log_n, n_limbs, log_q0, log_scale, alpha, log_sp, dsize)
+
+
+def gpu_context(name, device=0):
+    from paper_2412_15126_gb300 import rankfhe
+    log_n, n_limbs, log_q0, log_scale, alpha, log_sp, dsize, dg, df = CONFIGS[name]
+    return rankfhe.Context(log_n, n_limbs, alpha, dsize, log_scale, log_q0, log_sp, dg, df, device=device)
+
+
+def import_keys(ctx, keys):
+    from paper_2412_15126_gb300 import rankfhe
+    ctx.secret_import(keys.s)
+    ctx.key_import(rankfhe.KEY_RELIN, 0, keys.rlk.data)
+    for g, k in keys.gal.items():
+        ctx.key_import(rankfhe.KEY_GALOIS, g, k.data)
+
+
+def import_encodings(ctx, P, N, Q=1, n_real=None, kinds=("row0", "col0", "tie", "tri")):
+    for kind in kinds:
+        u = ckks.encode_unscaled(circuits.mask_slots(kind, N, Q, slots=P.slots), P.n)
+        ctx.encoding_import(MASK_IDS[kind], N, Q, 0, u)
+    if n_real is not None and n_real != N:
+        u = ckks.encode_unscaled(circuits.mask_slots("valid", N, Q, n_real, slots=P.slots), P.n)
+        ctx.encoding_import(MASK_IDS["valid"], N, Q, n_real, u)
+
+
+def rotation_set(N):
+    k = int(np.log2(N))
+    rs = set()
+    for i in range(k):
+        rs.update({-(N << i), N << i, -(1 << i), 1 << i})
+    for i in range(1, k + 1):
+        rs.update({-((N * (N - 1)) >> i), (N * (N - 1)) >> i})
+    return sorted(rs)
+
+
+def galois_elts(P, rots):
+    return sorted({ckks.galois_left(r % P.slots, P.n) for r in rots})
