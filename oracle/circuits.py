@@ -49,6 +49,14 @@ def mask_slots(kind: str, N: int, Q: int = 1, n_real: int | None = None, *, slot
         block = np.where(j >= i, 2.0, -2.0)
     elif kind == "tri":           # delta_{j>=i}: upper triangle with the diagonal (Alg. 6)
         block = (j >= i).astype(float)
+    elif kind == "row0s":         # MaskR(X, 0) scaled by 1/N: ranks leave SumR already divided by N
+        block[0, :] = 1.0 / N
+    elif kind == "col0s":         # MaskC(X, 0) scaled by 1/N
+        block[:, 0] = 1.0 / N
+    elif kind == "tiec":          # column form of "tie": 4*delta_{j<=i} - 2
+        block = np.where(j <= i, 2.0, -2.0)
+    elif kind == "sortidx":       # -(j+1)/N: column j of the sorting mask selects rank j+1 (Alg. 5)
+        block = -(j + 1.0) / N
     elif kind == "valid":         # rows and columns of the unpadded vector (Sec. 3.1, padding)
         m = N if n_real is None else n_real
         block = ((i < m) & (j < m)).astype(float)
@@ -126,6 +134,14 @@ class PlainSlots:
     def add_const(self, x, c):
         return PV(x.v + c, x.level)
 
+    def add_plain(self, x, key):
+        return PV(x.v + mask_slots(*key, slots=self.slots), x.level)
+
+    def lincomb(self, xs, cs):
+        assert all(x.level == xs[0].level for x in xs)
+        self.counts["mul_scalar"] += 1
+        return PV(sum(c * x.v for x, c in zip(xs, cs)), self._lv(xs[0]))
+
     def level_down(self, x, target):
         while x.level > target:
             x = self.mul_scalar(x, 1.0)
@@ -183,6 +199,13 @@ class OracleCkks:
 
     def add_const(self, x, c):
         return ckks.add_const(self.P, x, c)
+
+    def add_plain(self, x, key):
+        return ckks.add_plain(self.P, x, self.unscaled(key))
+
+    def lincomb(self, xs, cs):
+        self.counts["mul_scalar"] += 1
+        return ckks.lincomb(self.P, xs, cs)
 
     def level_down(self, x, target):
         return ckks.level_down(self.P, x, target)
@@ -282,8 +305,15 @@ def cmp(B, x, dg, df):
 # Ranking (Alg. 3) and tie correction (Alg. 6)
 # --------------------------------------------------------------------------
 def comparison_matrix(B, V, N, dg, df, Q=1):
-    """C = Cmp(ReplR(V), ReplC(TransR(V))): slot iN+j holds Cmp(v_j, v_i) (Alg. 3 lines 1-3).
-    The first rotations of ReplR and TransR both rotate V and share one ModUp (hoisting)."""
+    """C = Cmp(ReplR(V), ReplC(TransR(V))): slot iN+j holds Cmp(v_j, v_i) (Alg. 3 lines 1-3)."""
+    VR, VC = row_col_forms(B, V, N, Q)
+    return cmp(B, B.sub(VR, VC), dg, df)
+
+
+def row_col_forms(B, V, N, Q=1):
+    """V_R = ReplR(V) and V_C = ReplC(TransR(V)) (Alg. 3 lines 1-2), V_R brought down to
+    V_C's level.  The first rotations of ReplR and TransR both rotate V and share one
+    ModUp (hoisting)."""
     k = log2_exact(N)
     if k == 0:
         VR, VT = V, V
@@ -297,8 +327,7 @@ def comparison_matrix(B, V, N, dg, df, Q=1):
             VT = B.add(VT, B.rot(VT, -((N * (N - 1)) >> i)))
     T = B.mul_plain(VT, ("col0", N, Q))                     # TransR's MaskC
     VC = repl_c(B, T, N)
-    X = B.sub(B.level_down(VR, B.level(VC)), VC)
-    return cmp(B, X, dg, df)
+    return B.level_down(VR, B.level(VC)), VC
 
 
 def rank(B, V, N, dg, df, Q=1, n_real=None):
@@ -311,17 +340,156 @@ def rank(B, V, N, dg, df, Q=1, n_real=None):
     return B.add_const(sum_r(B, C, N, Q), 0.5)
 
 
+def tie_fold(B, C, N, Q=1, kind="tie"):
+    """C + E (delta - 1/2) with E = 4 C (1 - C) = 4 K, K = C - C^2 (Alg. 6 before its
+    SumR): the plaintext `kind` carries 4 delta - 2 (row form: delta_{j>=i}; column
+    form 'tiec': delta_{j<=i})."""
+    C2 = B.mul(C, C)
+    Cd = B.level_down(C, B.level(C2))
+    K = B.sub(Cd, C2)
+    KT = B.mul_plain(K, (kind, N, Q))
+    return B.add(B.level_down(Cd, B.level(KT)), KT)
+
+
 def rank_tie_corrected(B, V, N, dg, df, Q=1):
     """Alg. 3 + Alg. 6 in one SumR:  R + F = SumR(C + E (delta_{j>=i} - 1/2)) with
     E = 4 C (1 - C);  the factor 4 and the -1/2 are folded into the 'tie' plaintext
     (4 delta - 2) applied to K = C - C^2.  The +1/2 of Alg. 3 and the -1/2 of Alg. 6 cancel."""
     C = comparison_matrix(B, V, N, dg, df, Q)
-    C2 = B.mul(C, C)
-    Cd = B.level_down(C, B.level(C2))
-    K = B.sub(Cd, C2)
-    KT = B.mul_plain(K, ("tie", N, Q))
-    W = B.add(B.level_down(Cd, B.level(KT)), KT)
-    return sum_r(B, W, N, Q)
+    return sum_r(B, tie_fold(B, C, N, Q, "tie"), N, Q)
+
+
+# --------------------------------------------------------------------------
+# Indicator: Chebyshev approximation evaluated by Paterson-Stockmeyer (Sec. 2.2)
+# --------------------------------------------------------------------------
+def sinc2_window_coeffs(N: int, degree: int | None = None) -> np.ndarray:
+    """Chebyshev coefficients of the interpolant (first-kind nodes) on [-1, 1] of
+    sinc^2(N t), degree 8N - 1: 1 at t = 0 and 0 at every t = k/N, k != 0, so that
+    p((r - k)/N) is the indicator Ind_k of Alg. 4 at integer ranks r."""
+    d = 8 * N - 1 if degree is None else degree
+    return np.polynomial.chebyshev.chebinterpolate(lambda t: np.sinc(N * t) ** 2, d)
+
+
+def baby_steps(length: int) -> int:
+    """Number of baby steps k = 2^ceil(log2 sqrt(length)) for `length` coefficients."""
+    k = 1 << math.ceil(math.log2(math.sqrt(length)))
+    return min(k, length)
+
+
+def cheb_ps(B, t, coeffs):
+    """p(t) = sum_i c_i T_i(t) by Paterson-Stockmeyer in the Chebyshev basis.
+
+    Baby steps T_1..T_k (T_2i = 2 T_i^2 - 1, T_2i+1 = 2 T_i T_i+1 - T_1), giant steps
+    T_2m = 2 T_m^2 - 1 for m = k, 2k, ...; the coefficient vector (length a power of two,
+    k * 2^j) is split recursively as p = q T_m + r with m half its length,
+    q = c_m + sum_{j>=1} 2 c_{m+j} T_j and r = c_0 + sum_{i=1}^{m-1} (c_i - c_{2m-i}) T_i;
+    a part of length k is a linear combination of T_1..T_{k-1} plus c_0.  Products
+    bring both operands to the lower level first."""
+    c = np.asarray(coeffs, dtype=np.float64)
+    length = len(c)
+    assert length >= 2 and length & (length - 1) == 0, "coefficient count must be a power of two"
+    k = baby_steps(length)
+
+    def prod2(a, b):  # 2 a b
+        lo = min(B.level(a), B.level(b))
+        y = B.mul(B.level_down(a, lo), B.level_down(b, lo))
+        return B.add(y, y)
+
+    T = {1: t}
+    for i in range(2, k + 1):
+        if i % 2 == 0:
+            T[i] = B.add_const(prod2(T[i // 2], T[i // 2]), -1.0)
+        else:
+            y = prod2(T[i // 2], T[i // 2 + 1])
+            T[i] = B.sub(y, B.level_down(T[1], B.level(y)))
+    G = {k: T[k]}
+    m = k
+    while 2 * m < length:
+        G[2 * m] = B.add_const(prod2(G[m], G[m]), -1.0)
+        m *= 2
+    leaf_level = min(B.level(T[i]) for i in range(1, k))
+    TL = [B.level_down(T[i], leaf_level) for i in range(1, k)]
+
+    def leaf(cc):
+        return B.add_const(B.lincomb(TL, list(cc[1:])), float(cc[0]))
+
+    def rec(cc):
+        if len(cc) == k:
+            return leaf(cc)
+        m = len(cc) // 2
+        q = np.empty(m)
+        r = np.empty(m)
+        q[0] = cc[m]
+        q[1:] = 2.0 * cc[m + 1:]
+        r[0] = cc[0]
+        r[1:] = cc[1:m] - cc[2 * m - np.arange(1, m)]
+        Qc = rec(q)
+        Rc = rec(r)
+        lo = min(B.level(Qc), B.level(G[m]))
+        Pm = B.mul(B.level_down(Qc, lo), B.level_down(G[m], lo))
+        return B.add(Pm, B.level_down(Rc, B.level(Pm)))
+
+    return rec(c)
+
+
+def cheb_depth(length: int) -> int:
+    """Levels used by cheb_ps on `length` coefficients: log2(length) + 1."""
+    return int(math.log2(length)) + 1
+
+
+# --------------------------------------------------------------------------
+# Order statistics (Alg. 4) and sorting (Alg. 5, column form)
+# --------------------------------------------------------------------------
+def sum_rows_masked(B, x, N, Q, kind):
+    for i in range(log2_exact(N)):
+        x = B.add(x, B.rot(x, N << i))
+    return B.mul_plain(x, (kind, N, Q))
+
+
+def sum_cols_masked(B, x, N, Q, kind):
+    for i in range(log2_exact(N)):
+        x = B.add(x, B.rot(x, 1 << i))
+    return B.mul_plain(x, (kind, N, Q))
+
+
+def order_statistic(B, V, N, k, dg, df, Q=1, ties="first", coeffs=None):
+    """O = Ind_k(R) (Alg. 4): a 0/1 row marking the element(s) of rank k.
+
+    ties = "first": tie-corrected ranks (Alg. 6), one-hot at the first of equal
+    elements.  ties = "all": k = 1 uses Cmp_G = 2C^2 - C (all minima rank 1),
+    k = N uses Cmp_GE = 3C - 2C^2 (all maxima rank N) (Sec. 3.2, Min and Max);
+    other k use the fractional ranks of Alg. 3.  The ranks leave SumR divided by N
+    (mask 'row0s') and Ind_k(r) = p((r - k)/N) with p the sinc^2 window."""
+    coeffs = sinc2_window_coeffs(N) if coeffs is None else coeffs
+    C = comparison_matrix(B, V, N, dg, df, Q)
+    if ties == "first":
+        t = B.add_const(sum_rows_masked(B, tie_fold(B, C, N, Q, "tie"), N, Q, "row0s"), -k / N)
+    elif k == 1 or k == N:
+        C2 = B.mul(C, C)
+        Cd = B.level_down(C, B.level(C2))
+        if k == 1:
+            CG = B.sub(B.add(C2, C2), Cd)
+            t = B.add_const(sum_rows_masked(B, CG, N, Q, "row0s"), (1.0 - k) / N)
+        else:
+            CG = B.sub(B.add(B.add(Cd, Cd), Cd), B.add(C2, C2))
+            t = B.add_const(sum_rows_masked(B, CG, N, Q, "row0s"), -k / N)
+    else:
+        t = B.add_const(sum_rows_masked(B, C, N, Q, "row0s"), (0.5 - k) / N)
+    return cheb_ps(B, t, coeffs)
+
+
+def sort(B, V, N, dg, df, Q=1, coeffs=None):
+    """Alg. 5 in column form (Sec. 3.3): ranks as a column, C' = Cmp(V_C, V_R),
+    tie-corrected with 'tiec', SumC (scaled by 1/N), ReplC, minus (j+1)/N, the
+    indicator around 0 gives M_ij = [r_i = j+1]; SumR(M . V_C) is the sorted row."""
+    coeffs = sinc2_window_coeffs(N) if coeffs is None else coeffs
+    VR, VC = row_col_forms(B, V, N, Q)
+    Cc = cmp(B, B.sub(VC, VR), dg, df)
+    S = sum_cols_masked(B, tie_fold(B, Cc, N, Q, "tiec"), N, Q, "col0s")
+    D = B.add_plain(repl_c(B, S, N), ("sortidx", N, Q))
+    M = cheb_ps(B, D, coeffs)
+    Pm = B.mul(M, B.level_down(VC, B.level(M)))
+    return sum_r(B, Pm, N, Q)
 
 
 def tie_offset_unfolded(B, C, N, Q=1):

@@ -517,6 +517,32 @@ def mul_plain(P: Params, x: Ct, u: np.ndarray) -> Ct:
     return rescale(P, Ct(out, lvl))
 
 
+def add_plain(P: Params, x: Ct, u: np.ndarray) -> Ct:
+    """Add the plaintext with unscaled coefficients u, encoded at the ciphertext's
+    canonical scale Delta_l (rounded half away from zero), to c0.  No level is used."""
+    lvl = x.level
+    q = P.q[: lvl + 1]
+    m = to_residues(rha(P.scales[lvl] * np.asarray(u, dtype=np.float64)), q)
+    return Ct(np.stack([add_mod(x.c[0], m, q), x.c[1].copy()]), lvl)
+
+
+def lincomb(P: Params, xs, cs) -> Ct:
+    """sum_i c_i x_i for ciphertexts at one level l: each x_i is multiplied by the
+    integer rha(c_i * s_l) (s_l as for a scalar product), the products are summed
+    exactly, and the sum is rescaled once (result at level l-1)."""
+    lvl = xs[0].level
+    assert all(x.level == lvl for x in xs)
+    q = P.q[: lvl + 1]
+    s = scalar_scale(P, lvl)
+    acc = np.zeros((2, lvl + 1, P.n), dtype=np.uint64)
+    for x, c in zip(xs, cs):
+        K = rha_scalar(float(c) * s)
+        consts = [K % qi for qi in q]
+        for i in range(2):
+            acc[i] = add_mod(acc[i], mul_scalar_mod(x.c[i], consts, q), q)
+    return rescale(P, Ct(acc, lvl))
+
+
 def add_const(P: Params, x: Ct, c: float) -> Ct:
     lvl = x.level
     q = P.q[: lvl + 1]
