@@ -184,6 +184,24 @@ rk_status rk_mul_mask(rk_ctx* ctx, const rk_ct* a, uint32_t kind, rk_ct** out);
 /* Drop one prime by rounding division (rescale); out at level-1, scale divided by q_level. */
 rk_status rk_rescale(rk_ctx* ctx, const rk_ct* a, rk_ct** out);
 
+/* Rescale without any device allocation, for callers that cannot allocate device
+ * memory on the call path (e.g. where another runtime has reserved the device
+ * memory in its own pool, or in a loop that must never enter the CUDA allocator).
+ * The paper has no counterpart; it is rk_rescale on caller-owned buffers.
+ * d_in:  device buffer [2][level+1][n] words, evaluation domain (the layout of
+ *        rk_ntt_forward applied to each polynomial of a canonical ciphertext);
+ * d_out: device buffer [2][level][n] words, receives the rescaled ciphertext in
+ *        the same domain; it must not overlap d_in.
+ * The temporary lives in one fixed 4 MiB array in device memory declared by the
+ * library (held by every GPU that loads the library until the process exits), so
+ * 2*(level+1)*n must not exceed 2^19 words: larger sizes fail with RK_EINVAL.
+ * The first call on a device resolves that array's address; make that first call
+ * before any CUDA stream capture.  All calls share the array (nothing in it needs
+ * to start at zero): calls whose work overlaps on the GPU, e.g. from two contexts
+ * on different streams of one device, race.  Work is queued on the context stream.
+ * Errors: RK_EINVAL (NULL, level out of range, too large, overlap), RK_ECUDA. */
+rk_status rk_rescale_noalloc(rk_ctx* ctx, const uint64_t* d_in, uint64_t* d_out, uint32_t level);
+
 /* ---- circuits (Sec. 3-4) ------------------------------------------------------ */
 
 /* Rank (Alg. 3): fractional ranks of the vector in row 0 of `in` (fresh, top

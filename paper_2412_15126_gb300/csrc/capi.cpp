@@ -8,6 +8,7 @@ void ctx_build(rk_ctx* c, const rk_params* p, int device, void* stream);
 void ctx_release(rk_ctx* c);
 rk_ct* circuit_rank(rk_ctx* c, const rk_ct* in, uint32_t flags);
 rk_ct* circuit_compare_matrix(rk_ctx* c, const rk_ct* in);
+void rescale_noalloc(rk_ctx* c, const u64* in, u64* out, int l);
 void circuit_rotations(uint32_t N, std::vector<int>& out);
 
 namespace {
@@ -381,6 +382,13 @@ rk_status rk_rank_batch(rk_ctx* ctx, const rk_ct* const* in, size_t count, uint3
             throw;
         }
         for (size_t i = 0; i < count; i++) out[i] = res[i];
+    });
+}
+
+rk_status rk_rescale_noalloc(rk_ctx* ctx, const uint64_t* d_in, uint64_t* d_out, uint32_t level) {
+    return guard([&] {
+        need(ctx, "ctx");
+        rescale_noalloc(ctx, (const u64*)d_in, (u64*)d_out, (int)level);
     });
 }
 

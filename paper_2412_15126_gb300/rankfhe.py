@@ -83,6 +83,7 @@ _sig("rk_add_const", [_vp, _vp, ctypes.c_double, ctypes.POINTER(_vp)])
 _sig("rk_mul_scalar", [_vp, _vp, ctypes.c_double, ctypes.POINTER(_vp)])
 _sig("rk_mul_mask", [_vp, _vp, _u32, ctypes.POINTER(_vp)])
 _sig("rk_rescale", [_vp, _vp, ctypes.POINTER(_vp)])
+_sig("rk_rescale_noalloc", [_vp, _vp, _vp, _u32])
 _sig("rk_rank", [_vp, _vp, _u32, ctypes.POINTER(_vp)])
 _sig("rk_compare_matrix", [_vp, _vp, ctypes.POINTER(_vp)])
 _sig("rk_rank_batch", [_vp, ctypes.POINTER(_vp), _sz, _u32, ctypes.POINTER(_vp)])
@@ -272,6 +273,11 @@ class Context:
 
     def compare_matrix(self, ct):
         return self._out(_L.rk_compare_matrix, ct.handle)
+
+    def rescale_noalloc(self, d_in: int, d_out: int, level: int):
+        """Rescale between caller-owned device buffers (evaluation domain) with no
+        device allocation; see rk_rescale_noalloc in include/rankfhe.h."""
+        _check(_L.rk_rescale_noalloc(self.handle, _vp(d_in), _vp(d_out), level))
 
     def rank(self, ct, flags=0):
         return self._out(_L.rk_rank, ct.handle, flags)
