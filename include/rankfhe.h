@@ -75,6 +75,10 @@ typedef struct {
 #define RK_MASK_TIE   3u   /* 4*[j >= i] - 2 on each block (folded Alg. 6)             */
 #define RK_MASK_TRI   4u   /* [j >= i] on each block (Alg. 6 delta mask)               */
 #define RK_MASK_VALID 5u   /* 1 on rows and columns < n_real of each block (padding)   */
+#define RK_MASK_ROW0S 6u   /* 1/N on row 0 (MaskR that also divides ranks by N)        */
+#define RK_MASK_COL0S 7u   /* 1/N on column 0                                          */
+#define RK_MASK_TIEC  8u   /* 4*[j <= i] - 2: column form of RK_MASK_TIE               */
+#define RK_MASK_SORTIDX 9u /* -(j+1)/N at row i, column j (Alg. 5 index constant / N)  */
 
 /* Key kinds for rk_key_import. */
 #define RK_KEY_RELIN  1u
@@ -82,6 +86,9 @@ typedef struct {
 
 /* Flags for rk_rank. */
 #define RK_TIES_CORRECT 1u /* add the tie-correction offset (Alg. 6): ranks become a permutation */
+/* Flags for rk_order_stat. */
+#define RK_TIES_FIRST 0u   /* tie-corrected ranks: one-hot at the first (lowest index) of equal elements */
+#define RK_TIES_ALL   2u   /* k = 1 / k = N: mark every minimum / maximum (Cmp_G / Cmp_GE, Sec. 3.2) */
 
 /* ---- context -------------------------------------------------------------- */
 
@@ -136,6 +143,13 @@ uint64_t rk_galois_left(const rk_ctx* ctx, int32_t r);
  * Errors: RK_EINVAL on a bad kind or length. */
 rk_status rk_encoding_import(rk_ctx* ctx, uint32_t kind, uint32_t N, uint32_t Q, uint32_t n_real,
                              const double* u, size_t n);
+
+/* Override the Chebyshev coefficients c_0..c_{count-1} of the indicator window
+ * used for vectors of padded length N (Alg. 4, 5: Ind_k(r) = p((r - k)/N) with
+ * p = sum_i c_i T_i).  By default the library interpolates sinc^2(N t) at the
+ * count = max(8N, 128) Chebyshev nodes of the first kind with its own transform.  count
+ * must be a power of two >= 4.  Errors: RK_EINVAL. */
+rk_status rk_indicator_import(rk_ctx* ctx, uint32_t N, const double* coeffs, size_t count);
 
 /* ---- client operations ------------------------------------------------------ */
 
@@ -214,6 +228,17 @@ rk_status rk_rank(rk_ctx* ctx, const rk_ct* in, uint32_t flags, rk_ct** out);
  * q*N^2 + i*N + j holding Cmp(v_j, v_i) of Eq. 1 approximated by the composite
  * (f^d_f o g^d_g)(x)/2 + 1/2 of Sec. 2.2.  Errors as rk_rank. */
 rk_status rk_compare_matrix(rk_ctx* ctx, const rk_ct* in, rk_ct** out);
+
+/* k-th order statistic (Alg. 4): a 0/1 row marking the element(s) of rank k
+ * (1 <= k <= N; k = 1 argmin, k = N argmax), Ind_k evaluated by Paterson-Stockmeyer
+ * in the Chebyshev basis.  flags: RK_TIES_FIRST (tie-corrected ranks, one-hot at
+ * the first of equal elements) or RK_TIES_ALL (k = 1 or N: every minimum / maximum;
+ * other k: fractional ranks).  Errors: RK_EDEPTH, RK_ENOKEY, RK_EINVAL. */
+rk_status rk_order_stat(rk_ctx* ctx, const rk_ct* in, uint32_t k, uint32_t flags, rk_ct** out);
+
+/* Sort (Alg. 5, column form of Sec. 3.3, with the tie-correction offset of Alg. 6):
+ * the ascending values in row 0 of the output.  Errors as rk_order_stat. */
+rk_status rk_sort(rk_ctx* ctx, const rk_ct* in, uint32_t flags, rk_ct** out);
 
 /* Ranks of `count` ciphertexts (each its own query set), one circuit per input,
  * all queued on the context stream. */

@@ -63,6 +63,8 @@ def lib():
             L.orc_mul_pointwise.argtypes = [_u64p, _u64p, _u64p, ctypes.c_int, ctypes.c_size_t, _u64p]
             L.orc_fast_base_conv.argtypes = [_u64p, ctypes.c_size_t, _u64p, ctypes.c_int,
                                              _u64p, ctypes.c_int, _u64p]
+            L.orc_fast_base_conv_centered.argtypes = [_u64p, ctypes.c_size_t, _u64p, ctypes.c_int,
+                                                      _u64p, ctypes.c_int, _u64p]
             _lib = L
     return _lib
 

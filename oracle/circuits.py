@@ -364,9 +364,9 @@ def rank_tie_corrected(B, V, N, dg, df, Q=1):
 # --------------------------------------------------------------------------
 def sinc2_window_coeffs(N: int, degree: int | None = None) -> np.ndarray:
     """Chebyshev coefficients of the interpolant (first-kind nodes) on [-1, 1] of
-    sinc^2(N t), degree 8N - 1: 1 at t = 0 and 0 at every t = k/N, k != 0, so that
-    p((r - k)/N) is the indicator Ind_k of Alg. 4 at integer ranks r."""
-    d = 8 * N - 1 if degree is None else degree
+    sinc^2(N t), degree max(8N, 128) - 1: 1 at t = 0 and 0 at every t = k/N, k != 0,
+    so that p((r - k)/N) is the indicator Ind_k of Alg. 4 at integer ranks r."""
+    d = max(8 * N, 128) - 1 if degree is None else degree
     return np.polynomial.chebyshev.chebinterpolate(lambda t: np.sinc(N * t) ** 2, d)
 
 

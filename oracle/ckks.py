@@ -22,7 +22,8 @@ library):
   ModUp      fast basis conversion of one digit without correction.
   KS         ModUp every digit, (for a rotation) apply the automorphism to the
              lifted digits, multiply-accumulate with the key over Q_l u P, ModDown.
-  ModDown    fast basis conversion of the P part to Q_l, subtract, times P^-1.
+  ModDown    fast basis conversion of the P part to Q_l with centred terms
+             (y_k in (-p_k/2, p_k/2]), subtract, times P^-1.
   rescale    centred lift of the last residue into (-q_l/2, q_l/2], subtract,
              times q_l^-1.
   mul        (x0 y0, x0 y1 + x1 y0, x1 y1), relinearise x1 y1, rescale.
@@ -205,6 +206,15 @@ def fast_base_conv(x, src, dst):
     x = u64(x)
     out = np.empty((len(dst), x.shape[1]), dtype=np.uint64)
     _lib.lib().orc_fast_base_conv(ptr(x), x.shape[1], ptr(u64(src)), len(src), ptr(u64(dst)), len(dst), ptr(out))
+    return out
+
+
+def fast_base_conv_centered(x, src, dst):
+    """Fast basis conversion with each term y_i taken in (-s_i/2, s_i/2]."""
+    x = u64(x)
+    out = np.empty((len(dst), x.shape[1]), dtype=np.uint64)
+    _lib.lib().orc_fast_base_conv_centered(ptr(x), x.shape[1], ptr(u64(src)), len(src), ptr(u64(dst)), len(dst),
+                                           ptr(out))
     return out
 
 
@@ -411,8 +421,11 @@ def mod_up(P: Params, d: np.ndarray, j: int, level: int) -> np.ndarray:
 
 
 def mod_down(P: Params, u: np.ndarray, level: int) -> np.ndarray:
+    """(u - [u]_P) / P over Q_l, [u]_P by the centred fast conversion, so that the
+    result is round(u / P) up to an error u' of mean zero (an uncentred conversion
+    would bias every key switch by about (alpha - 1)/2 per coefficient)."""
     q = P.q[: level + 1]
-    w = fast_base_conv(u[level + 1:], P.p, q)
+    w = fast_base_conv_centered(u[level + 1:], P.p, q)
     Pprod = 1
     for pk in P.p:
         Pprod *= pk

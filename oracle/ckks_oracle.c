@@ -218,3 +218,36 @@ void orc_fast_base_conv(const uint64_t *in, size_t n, const uint64_t *src, int n
     free(dhat_inv);
     free(dhat_mod);
 }
+
+/*
+ * The same conversion with centred terms: y_i is replaced by y_i - s_i when
+ * y_i > (s_i - 1)/2, so the sum sum_i y_i (D/s_i) lies in (-n_src D/2, n_src D/2] and
+ * differs from the centred representative of x mod D by a multiple u D with u of
+ * mean zero:
+ *   out_m = ( sum_i y_i (D/s_i) - #{i : y_i > (s_i-1)/2} * D ) mod t_m.
+ */
+void orc_fast_base_conv_centered(const uint64_t *in, size_t n, const uint64_t *src, int n_src,
+                                 const uint64_t *dst, int n_dst, uint64_t *out) {
+    orc_fast_base_conv(in, n, src, n_src, dst, n_dst, out);
+    uint64_t *dhat_inv = (uint64_t *)malloc(sizeof(uint64_t) * n_src);
+    for (int i = 0; i < n_src; i++) {
+        uint64_t h = 1;
+        for (int j = 0; j < n_src; j++) if (j != i) h = mulmod(h, src[j] % src[i], src[i]);
+        dhat_inv[i] = invmod(h, src[i]);
+    }
+#pragma omp parallel for
+    for (int m = 0; m < n_dst; m++) {
+        uint64_t tm = dst[m];
+        uint64_t Dm = 1 % tm; /* D mod t_m */
+        for (int j = 0; j < n_src; j++) Dm = mulmod(Dm, src[j] % tm, tm);
+        for (size_t k = 0; k < n; k++) {
+            uint64_t acc = out[(size_t)m * n + k];
+            for (int i = 0; i < n_src; i++) {
+                uint64_t y = mulmod(in[(size_t)i * n + k], dhat_inv[i], src[i]);
+                if (y > (src[i] - 1) / 2) acc = submod(acc, Dm, tm);
+            }
+            out[(size_t)m * n + k] = acc;
+        }
+    }
+    free(dhat_inv);
+}

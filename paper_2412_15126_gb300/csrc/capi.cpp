@@ -9,6 +9,9 @@ void ctx_release(rk_ctx* c);
 rk_ct* circuit_rank(rk_ctx* c, const rk_ct* in, uint32_t flags);
 rk_ct* circuit_compare_matrix(rk_ctx* c, const rk_ct* in);
 void rescale_noalloc(rk_ctx* c, const u64* in, u64* out, int l);
+rk_ct* circuit_order_stat(rk_ctx* c, const rk_ct* in, uint32_t k, uint32_t flags);
+rk_ct* circuit_sort(rk_ctx* c, const rk_ct* in, uint32_t flags);
+void indicator_import(rk_ctx* c, uint32_t N, const double* coeffs, size_t count);
 void circuit_rotations(uint32_t N, std::vector<int>& out);
 
 namespace {
@@ -349,6 +352,36 @@ rk_status rk_rank(rk_ctx* ctx, const rk_ct* in, uint32_t flags, rk_ct** out) {
         need(out, "out");
         set_device(ctx);
         *out = circuit_rank(ctx, in, flags);
+        check_launch();
+    });
+}
+
+rk_status rk_indicator_import(rk_ctx* ctx, uint32_t N, const double* coeffs, size_t count) {
+    return guard([&] {
+        need(ctx, "ctx");
+        need(coeffs, "coeffs");
+        indicator_import(ctx, N, coeffs, count);
+    });
+}
+
+rk_status rk_order_stat(rk_ctx* ctx, const rk_ct* in, uint32_t k, uint32_t flags, rk_ct** out) {
+    return guard([&] {
+        need(ctx, "ctx");
+        same_ctx(ctx, in);
+        need(out, "out");
+        set_device(ctx);
+        *out = circuit_order_stat(ctx, in, k, flags);
+        check_launch();
+    });
+}
+
+rk_status rk_sort(rk_ctx* ctx, const rk_ct* in, uint32_t flags, rk_ct** out) {
+    return guard([&] {
+        need(ctx, "ctx");
+        same_ctx(ctx, in);
+        need(out, "out");
+        set_device(ctx);
+        *out = circuit_sort(ctx, in, flags);
         check_launch();
     });
 }

@@ -24,6 +24,10 @@ void mask_slot_values(uint32_t kind, uint32_t N, uint32_t Q, uint32_t n_real, si
                     case RK_MASK_TIE: x = j >= i ? 2.0 : -2.0; break;
                     case RK_MASK_TRI: x = j >= i ? 1.0 : 0.0; break;
                     case RK_MASK_VALID: x = (i < m && j < m) ? 1.0 : 0.0; break;
+                    case RK_MASK_ROW0S: x = i == 0 ? 1.0 / N : 0.0; break;
+                    case RK_MASK_COL0S: x = j == 0 ? 1.0 / N : 0.0; break;
+                    case RK_MASK_TIEC: x = j <= i ? 2.0 : -2.0; break;
+                    case RK_MASK_SORTIDX: x = -(j + 1.0) / N; break;
                     default: throw rk_error(RK_EINVAL, "unknown mask kind");
                 }
                 v[(size_t)q * N * N + (size_t)i * N + j] = x;
@@ -111,6 +115,22 @@ struct Ev {
         ev_add_const(c, x.p, v, o.p);
         return o;
     }
+    H add_mask(const H& x, uint32_t kind) {
+        H o = fresh(x, x->level);
+        ev_add_plain(c, x.p, kind, x->N, x->Q, 0, o.p);
+        return o;
+    }
+    H lincomb(const std::vector<H>& xs, const double* cs) {
+        std::vector<const rk_ct*> ps;
+        std::vector<double> cv;
+        for (size_t i = 0; i < xs.size(); i++) {
+            ps.push_back(xs[i].p);
+            cv.push_back(cs[i]);
+        }
+        H o = fresh(xs[0], xs[0]->level);
+        ev_lincomb(c, ps, cv, o.p);
+        return o;
+    }
     H level_down(const H& x, int target) {
         H o = fresh(x, x->level);
         ev_level_down(c, x.p, target, o.p);
@@ -156,14 +176,109 @@ H cmp(Ev& E, H x, int dg, int df) {
     return E.add_const(x, 0.5);
 }
 
-H sum_r(Ev& E, H x) {
+// SumR (Alg. 8) with the row mask `kind` (RK_MASK_ROW0, or RK_MASK_ROW0S to divide by N)
+H sum_rows(Ev& E, H x, uint32_t kind) {
     const int N = (int)x->N, k = log2_exact(x->N);
     for (int i = 0; i < k; i++) x = E.add(x, E.rot(x, N << i));
-    return E.mul_mask(x, RK_MASK_ROW0);
+    return E.mul_mask(x, kind);
+}
+H sum_r(Ev& E, H x) { return sum_rows(E, std::move(x), RK_MASK_ROW0); }
+
+// SumC (Alg. 9) with the column mask `kind`
+H sum_cols(Ev& E, H x, uint32_t kind) {
+    const int k = log2_exact(x->N);
+    for (int i = 0; i < k; i++) x = E.add(x, E.rot(x, 1 << i));
+    return E.mul_mask(x, kind);
 }
 
-// C = Cmp(ReplR(V), ReplC(TransR(V))); slot iN+j holds Cmp(v_j, v_i) (Alg. 3 lines 1-3).
-H comparison_matrix(Ev& E, const H& V, int dg, int df) {
+// ReplC (Alg. 11)
+H repl_c(Ev& E, H x) {
+    const int k = log2_exact(x->N);
+    for (int i = 0; i < k; i++) x = E.add(x, E.rot(x, -(1 << i)));
+    return x;
+}
+
+// C + E (delta - 1/2), E = 4 K, K = C - C^2 (Alg. 6 before its SumR); the mask holds 4 delta - 2
+H tie_fold(Ev& E, const H& C, uint32_t kind) {
+    H C2 = E.mul(C, C);
+    H Cd = E.level_down(C, C2->level);
+    H K = E.sub(Cd, C2);
+    H KT = E.mul_mask(K, kind);
+    return E.add(E.level_down(Cd, KT->level), KT);
+}
+
+// 2 a b with both operands brought to the lower level first
+H prod2(Ev& E, const H& a, const H& b) {
+    const int lo = std::min(a->level, b->level);
+    H y = E.mul(E.level_down(a, lo), E.level_down(b, lo));
+    return E.add(y, y);
+}
+
+int baby_steps(int length) {
+    int k = 1;
+    while ((double)k * k < (double)length) k <<= 1;   // 2^ceil(log2 sqrt(length))
+    return std::min(k, length);
+}
+
+// p(t) = sum_i c_i T_i(t), Paterson-Stockmeyer in the Chebyshev basis: baby steps T_1..T_k,
+// giant steps T_2m = 2 T_m^2 - 1; p = q T_m + r with m half the coefficient count,
+// q = c_m + sum_{j>=1} 2 c_{m+j} T_j, r = c_0 + sum_{i=1}^{m-1} (c_i - c_{2m-i}) T_i; a part of
+// k coefficients is sum_{i>=1} c_i T_i (one exact combination, one rescale) plus c_0.
+struct ChebPS {
+    Ev& E;
+    int k;
+    std::map<int, H> T, G;
+    std::vector<H> TL;   // T_1..T_{k-1} at the leaf level
+    H leaf(const std::vector<double>& cc) {
+        H o = E.lincomb(TL, cc.data() + 1);
+        return E.add_const(o, cc[0]);
+    }
+    H rec(const std::vector<double>& cc) {
+        if ((int)cc.size() == k) return leaf(cc);
+        const int m = (int)cc.size() / 2;
+        std::vector<double> q(m), r(m);
+        q[0] = cc[m];
+        for (int j = 1; j < m; j++) q[j] = 2.0 * cc[m + j];
+        r[0] = cc[0];
+        for (int i = 1; i < m; i++) r[i] = cc[i] - cc[2 * m - i];
+        H Qc = rec(q);
+        H Rc = rec(r);
+        const int lo = std::min(Qc->level, G[m]->level);
+        H Pm = E.mul(E.level_down(Qc, lo), E.level_down(G[m], lo));
+        return E.add(Pm, E.level_down(Rc, Pm->level));
+    }
+};
+
+H cheb_ps(Ev& E, const H& t, const std::vector<double>& c) {
+    const int length = (int)c.size();
+    RK_REQUIRE(length >= 4 && (length & (length - 1)) == 0, RK_EINVAL, "Chebyshev coefficient count must be a power of two");
+    ChebPS ps{E, baby_steps(length)};
+    const int k = ps.k;
+    ps.T[1] = E.copy(t);
+    for (int i = 2; i <= k; i++) {
+        if (i % 2 == 0) {
+            ps.T[i] = E.add_const(prod2(E, ps.T[i / 2], ps.T[i / 2]), -1.0);
+        } else {
+            H y = prod2(E, ps.T[i / 2], ps.T[i / 2 + 1]);
+            ps.T[i] = E.sub(y, E.level_down(ps.T[1], y->level));
+        }
+    }
+    ps.G[k] = E.copy(ps.T[k]);
+    for (int m = k; 2 * m < length; m *= 2) ps.G[2 * m] = E.add_const(prod2(E, ps.G[m], ps.G[m]), -1.0);
+    int leaf_level = 1 << 30;
+    for (int i = 1; i < k; i++) leaf_level = std::min(leaf_level, ps.T[i]->level);
+    for (int i = 1; i < k; i++) ps.TL.push_back(E.level_down(ps.T[i], leaf_level));
+    return ps.rec(c);
+}
+
+int cheb_depth(int length) {
+    int d = 0;
+    while ((1 << d) < length) d++;
+    return d + 1;
+}
+
+// V_R = ReplR(V) and V_C = ReplC(TransR(V)) (Alg. 3 lines 1-2), V_R brought down to V_C's level.
+std::pair<H, H> row_col_forms(Ev& E, const H& V) {
     const int N = (int)V->N, k = log2_exact(V->N);
     H VR, VT;
     if (k == 0) {
@@ -177,9 +292,41 @@ H comparison_matrix(Ev& E, const H& V, int dg, int df) {
         for (int i = 2; i <= k; i++) VT = E.add(VT, E.rot(VT, -((N * (N - 1)) >> i)));
     }
     H VC = E.mul_mask(VT, RK_MASK_COL0);                 // TransR's MaskC
-    for (int i = 0; i < k; i++) VC = E.add(VC, E.rot(VC, -(1 << i)));
-    H X = E.sub(E.level_down(VR, VC->level), VC);
-    return cmp(E, std::move(X), dg, df);
+    VC = repl_c(E, std::move(VC));
+    H VRd = E.level_down(VR, VC->level);
+    return std::make_pair(std::move(VRd), std::move(VC));
+}
+
+// C = Cmp(ReplR(V), ReplC(TransR(V))); slot iN+j holds Cmp(v_j, v_i) (Alg. 3 lines 1-3).
+H comparison_matrix(Ev& E, const H& V, int dg, int df) {
+    auto rc = row_col_forms(E, V);
+    return cmp(E, E.sub(rc.first, rc.second), dg, df);
+}
+
+// Chebyshev coefficients of the interpolant of sinc^2(N t) on [-1, 1] at the count
+// Chebyshev nodes of the first kind: c_j = (2/count) sum_k f(x_k) cos(j theta_k), c_0 halved.
+std::vector<double> sinc2_coeffs(uint32_t N, int count) {
+    std::vector<double> f(count), c(count);
+    const double pi = 3.14159265358979323846;
+    for (int kk = 0; kk < count; kk++) {
+        const double th = pi * (kk + 0.5) / count;
+        const double x = N * std::cos(th);
+        const double s = x == 0.0 ? 1.0 : std::sin(pi * x) / (pi * x);
+        f[kk] = s * s;
+    }
+    for (int j = 0; j < count; j++) {
+        double acc = 0.0;
+        for (int kk = 0; kk < count; kk++) acc += f[kk] * std::cos(j * pi * (kk + 0.5) / count);
+        c[j] = 2.0 * acc / count;
+    }
+    c[0] *= 0.5;
+    return c;
+}
+
+const std::vector<double>& indicator_coeffs(rk_ctx* c, uint32_t N) {
+    auto it = c->indicator.find(N);
+    if (it == c->indicator.end()) it = c->indicator.emplace(N, sinc2_coeffs(N, std::max(8 * (int)N, 128))).first;
+    return it->second;
 }
 
 }  // namespace
@@ -204,17 +351,83 @@ rk_ct* circuit_rank(rk_ctx* c, const rk_ct* in, uint32_t flags) {
     ev_copy(c, in, V.p);
     H C = comparison_matrix(E, V, (int)c->prm.d_g, (int)c->prm.d_f);
     if (in->n_real != in->N) C = E.mul_mask(C, RK_MASK_VALID);
-    if (flags & RK_TIES_CORRECT) {
-        // R + F = SumR(C + E (delta - 1/2)), E = 4 C (1 - C) = 4 K with K = C - C^2 (Alg. 6 folded)
-        H C2 = E.mul(C, C);
-        H Cd = E.level_down(C, C2->level);
-        H K = E.sub(Cd, C2);
-        H KT = E.mul_mask(K, RK_MASK_TIE);
-        H W = E.add(E.level_down(Cd, KT->level), KT);
-        return sum_r(E, std::move(W)).release();
-    }
+    if (flags & RK_TIES_CORRECT)   // R + F = SumR(C + E (delta - 1/2)) (Alg. 6 folded)
+        return sum_r(E, tie_fold(E, C, RK_MASK_TIE)).release();
     H R = E.add_const(sum_r(E, std::move(C)), 0.5);
     return R.release();
+}
+
+void indicator_import(rk_ctx* c, uint32_t N, const double* coeffs, size_t count) {
+    RK_REQUIRE(count >= 4 && (count & (count - 1)) == 0, RK_EINVAL, "coefficient count must be a power of two >= 4");
+    c->indicator[N] = std::vector<double>(coeffs, coeffs + count);
+}
+
+static void check_square(rk_ctx* c, const rk_ct* in, int need, const char* what) {
+    RK_REQUIRE(in->layout == RK_LAYOUT_ROW, RK_EINVAL, std::string(what) + " expects a row vector");
+    RK_REQUIRE((size_t)in->Q * in->N * in->N <= (size_t)c->n / 2, RK_EINVAL, "N^2 exceeds the slots");
+    RK_REQUIRE(in->n_real == in->N, RK_EINVAL, std::string(what) + " of a padded vector is not supported");
+    RK_REQUIRE(c->prm.d_g + c->prm.d_f >= 1, RK_EINVAL, "comparator needs at least one stage");
+    RK_REQUIRE(in->level >= need, RK_EDEPTH,
+               std::string(what) + " needs " + std::to_string(need) + " levels, input has " + std::to_string(in->level));
+}
+
+int order_stat_depth(rk_ctx* c, const rk_ct* in, uint32_t k, uint32_t flags) {
+    const int dc = 3 * (int)(c->prm.d_g + c->prm.d_f);
+    const int ind = cheb_depth((int)indicator_coeffs(c, in->N).size());
+    int extra = 0;
+    if (!(flags & RK_TIES_ALL)) extra = 2;                              // tie fold
+    else if (k == 1 || k == in->N) extra = 1;                           // Cmp_G / Cmp_GE
+    return 1 + dc + extra + 1 + ind;
+}
+
+// Alg. 4: O = Ind_k(R), ranks leaving SumR divided by N, Ind_k(r) = p((r - k)/N).
+rk_ct* circuit_order_stat(rk_ctx* c, const rk_ct* in, uint32_t k, uint32_t flags) {
+    RK_REQUIRE(k >= 1 && k <= in->N, RK_EINVAL, "k must be in [1, N]");
+    check_square(c, in, order_stat_depth(c, in, k, flags), "order statistic");
+    const double N = (double)in->N;
+    Ev E{c};
+    H V(ct_clone_meta(in, in->level));
+    ev_copy(c, in, V.p);
+    H C = comparison_matrix(E, V, (int)c->prm.d_g, (int)c->prm.d_f);
+    H t;
+    if (!(flags & RK_TIES_ALL)) {
+        t = E.add_const(sum_rows(E, tie_fold(E, C, RK_MASK_TIE), RK_MASK_ROW0S), -(double)k / N);
+    } else if (k == 1 || k == in->N) {
+        H C2 = E.mul(C, C);
+        H Cd = E.level_down(C, C2->level);
+        if (k == 1) {   // Cmp_G = 2 C^2 - C: every minimum has rank 1
+            H CG = E.sub(E.add(C2, C2), Cd);
+            t = E.add_const(sum_rows(E, std::move(CG), RK_MASK_ROW0S), (1.0 - (double)k) / N);
+        } else {        // Cmp_GE = 3 C - 2 C^2: every maximum has rank N
+            H CG = E.sub(E.add(E.add(Cd, Cd), Cd), E.add(C2, C2));
+            t = E.add_const(sum_rows(E, std::move(CG), RK_MASK_ROW0S), -(double)k / N);
+        }
+    } else {
+        t = E.add_const(sum_rows(E, std::move(C), RK_MASK_ROW0S), (0.5 - (double)k) / N);
+    }
+    return cheb_ps(E, t, indicator_coeffs(c, in->N)).release();
+}
+
+int sort_depth(rk_ctx* c, const rk_ct* in) {
+    const int dc = 3 * (int)(c->prm.d_g + c->prm.d_f);
+    return 1 + dc + 2 + 1 + cheb_depth((int)indicator_coeffs(c, in->N).size()) + 1 + 1;
+}
+
+// Alg. 5, column form (Sec. 3.3): C' = Cmp(V_C, V_R), tie fold ('tiec'), SumC / N, ReplC,
+// minus (j+1)/N, Ind_0 gives M_ij = [r_i = j+1], SumR(M . V_C) is the sorted row.
+rk_ct* circuit_sort(rk_ctx* c, const rk_ct* in, uint32_t flags) {
+    (void)flags;
+    check_square(c, in, sort_depth(c, in), "sort");
+    Ev E{c};
+    H V(ct_clone_meta(in, in->level));
+    ev_copy(c, in, V.p);
+    auto rc = row_col_forms(E, V);
+    H Cc = cmp(E, E.sub(rc.second, rc.first), (int)c->prm.d_g, (int)c->prm.d_f);
+    H S = sum_cols(E, tie_fold(E, Cc, RK_MASK_TIEC), RK_MASK_COL0S);
+    H D = E.add_mask(repl_c(E, std::move(S)), RK_MASK_SORTIDX);
+    H M = cheb_ps(E, D, indicator_coeffs(c, in->N));
+    H Pm = E.mul(M, E.level_down(rc.second, M->level));
+    return sum_r(E, std::move(Pm)).release();
 }
 
 rk_ct* circuit_compare_matrix(rk_ctx* c, const rk_ct* in) {

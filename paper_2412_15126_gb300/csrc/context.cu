@@ -259,7 +259,12 @@ void ctx_build(rk_ctx* c, const rk_params* p, int device, void* stream) {
     }
     // ModDown block
     const size_t md_off = conv.size();
-    conv.resize(md_off + 2 * A + (size_t)A * (L + 1), 0);
+    conv.resize(md_off + 2 * A + (size_t)A * (L + 1) + (L + 1), 0);
+    for (int i = 0; i <= L; i++) {   // P mod q_i, subtracted once per negative centred term
+        u64 pm = 1 % q[i];
+        for (int k = 0; k < A; k++) pm = h_mulmod(pm, sp[k] % q[i], q[i]);
+        conv[md_off + 2 * A + (size_t)A * (L + 1) + i] = pm;
+    }
     for (int k = 0; k < A; k++) {
         u64 pk = sp[k];
         u64 ph = 1;
@@ -320,6 +325,7 @@ void ctx_build(rk_ctx* c, const rk_params* p, int device, void* stream) {
     e.conv.pinv = c->d_conv + pi_off;
     e.conv.rescale = c->d_conv + rs_off;
     e.prof = &c->prof;
+    ntt_init_attributes();
 }
 
 void ctx_release(rk_ctx* c) {

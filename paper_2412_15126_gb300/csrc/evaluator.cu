@@ -244,6 +244,76 @@ void ev_mul_plain(rk_ctx* c, const rk_ct* a, uint32_t kind, uint32_t N, uint32_t
     ev_rescale_inplace(c, out);
 }
 
+// Mask plaintext encoded at the canonical scale Delta_l (normal form), for addition.
+static const u64* plain_add_get(rk_ctx* c, uint32_t kind, uint32_t N, uint32_t Q, uint32_t n_real, int l) {
+    auto key = std::make_tuple(kind, N, Q, n_real, l);
+    auto it = c->plain_add_cache.find(key);
+    if (it != c->plain_add_cache.end()) return it->second;
+    auto ekey = std::make_tuple(kind, N, Q, n_real);
+    if (!c->encodings.count(ekey)) {
+        std::vector<double> slots;
+        mask_slot_values(kind, N, Q, n_real, (size_t)c->n / 2, slots);
+        std::vector<double> u;
+        encode_unscaled(c->log_n, slots.data(), slots.size(), u);
+        c->encodings[ekey] = u;
+    }
+    const std::vector<double>& u = c->encodings[ekey];
+    std::vector<int64_t> m(c->n);
+    for (int k = 0; k < c->n; k++) m[k] = round_half_away(c->scales[l] * u[k]);
+    Scratch S = scratch_layout(c);
+    u64* buf = nullptr;
+    RK_CUDA(cudaMalloc((void**)&buf, (size_t)(l + 1) * c->n * 8));
+    int64_t* tmp = (int64_t*)S.misc;
+    upload_i64_sync(c, tmp, m.data(), c->n);
+    launch_reduce_signed(c->env, tmp, ls_q(buf, 0, 1, l + 1), c->stream);
+    launch_ntt_forward(c->env, ls_q(buf, 0, 1, l + 1), c->stream);
+    RK_CUDA(cudaStreamSynchronize(c->stream));
+    c->plain_add_cache[key] = buf;
+    return buf;
+}
+
+void ev_add_plain(rk_ctx* c, const rk_ct* a, uint32_t kind, uint32_t N, uint32_t Q, uint32_t n_real, rk_ct* out) {
+    const int l = a->level;
+    const u64* pt = plain_add_get(c, kind, N, Q, n_real, l);
+    const size_t pl = (size_t)(l + 1) * c->n;
+    // c0 + pt (poly 1 copied)
+    launch_addsub(c->env, out->data, a->data, pt, l + 1, 0, 0, c->stream, 1);   // c0 + pt
+    if (out != a)
+        RK_CUDA(cudaMemcpyAsync(out->data + c->poly_stride(), a->data + c->poly_stride(), pl * 8, cudaMemcpyDeviceToDevice,
+                                c->stream));
+    out->level = l;
+    copy_meta(out, a);
+}
+
+void ev_lincomb(rk_ctx* c, const std::vector<const rk_ct*>& xs, const std::vector<double>& cs, rk_ct* out) {
+    RK_REQUIRE(!xs.empty() && xs.size() == cs.size(), RK_EINVAL, "lincomb: bad term lists");
+    const int l = xs[0]->level;
+    RK_REQUIRE(l >= 1, RK_EDEPTH, "lincomb: no level left");
+    for (auto* x : xs) RK_REQUIRE(x->level == l, RK_EINVAL, "lincomb: level mismatch");
+    for (auto* x : xs) RK_REQUIRE(x != out, RK_EINVAL, "lincomb: output aliases an input");
+    const double s = factor_scale(c, l);
+    LincombArg arg;
+    size_t done = 0;
+    while (done < xs.size()) {
+        const int terms = (int)std::min<size_t>(16, xs.size() - done);
+        for (int i = 0; i < terms; i++) {
+            arg.x[i] = xs[done + i]->data;
+            const int64_t K = round_half_away(cs[done + i] * s);
+            for (int t = 0; t <= l; t++) {
+                const int64_t q = (int64_t)c->primes[t];
+                int64_t r = K % q;
+                if (r < 0) r += q;
+                arg.KR[i][t] = h_mulmod((u64)r, c->h_pc[t].r_mod, (u64)q);
+            }
+        }
+        launch_lincomb(c->env, out->data, arg, terms, done > 0, l + 1, c->poly_stride(), c->stream);
+        done += terms;
+    }
+    out->level = l;
+    copy_meta(out, xs[0]);
+    ev_rescale_inplace(c, out);
+}
+
 // ---------------------------------------------------------------------------
 // Key switching
 // ---------------------------------------------------------------------------

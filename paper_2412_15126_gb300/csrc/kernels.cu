@@ -13,40 +13,6 @@
 const char* const kKernelKindNames[KK_COUNT] = {"ntt_fwd", "ntt_inv", "modup", "ks_inner", "moddown_conv",
                                                "ks_combine", "tensor", "rescale", "pointwise", "client"};
 
-// Counts every launch; when `kind` is the profiled kind, brackets the launch(es) with
-// CUDA events on the launching stream and accumulates the algorithmic bytes/products.
-struct ProfScope {
-    Profiler* p;
-    bool on = false;
-    cudaStream_t st;
-    double bytes, ops;
-    ProfScope(const KernelEnv& e, int kind, cudaStream_t s, int nlaunch, double b, double o)
-        : p(e.prof), st(s), bytes(b), ops(o) {
-        if (!p) return;
-        p->launches += (uint64_t)nlaunch;
-        if (p->target == kind) {
-            on = true;
-            record();
-        }
-    }
-    void record() {
-        if (p->used == p->ev.size()) {
-            cudaEvent_t ev;
-            cudaEventCreate(&ev);
-            p->ev.push_back(ev);
-        }
-        cudaEventRecord(p->ev[p->used++], st);
-    }
-    ~ProfScope() {
-        if (on) {
-            record();
-            p->bytes += bytes;
-            p->ops += ops;
-            p->timed++;
-        }
-    }
-};
-
 __device__ __forceinline__ int brev_bits(unsigned x, int bits) { return (int)(__brev(x) >> (32 - bits)); }
 
 // Source index of output index k under X -> X^g in the evaluation domain.
@@ -55,187 +21,6 @@ __device__ __forceinline__ int galois_src(int k, u64 g, int logn) {
     unsigned e = 2u * (unsigned)brev_bits((unsigned)k, logn) + 1u;
     unsigned e2 = (unsigned)((e * (unsigned)g) & two_n_mask);
     return brev_bits((e2 - 1u) >> 1, logn);
-}
-
-// ===========================================================================
-// NTT: log_n = a + b.  The column pass runs the first a Cooley-Tukey stages on
-// the 2^a-point columns {r 2^b + c}; the row pass runs the last b stages on the
-// contiguous 2^b-point rows.  Inverse (Gentleman-Sande) runs the row pass first.
-// Values stay in [0, 2q) between passes; the last pass returns [0, q).
-// ===========================================================================
-#define NTT_COLS 16
-#define NTT_ROW_TILE 2048
-
-__global__ void __launch_bounds__(TPB) k_ntt_fwd_col(LimbSet s, int logn, int loga, const PrimeConst* __restrict__ pc,
-                                                     const u64* __restrict__ psi, const u64* __restrict__ psi_sh) {
-    extern __shared__ u64 sm[];
-    const int n = 1 << logn, B = 1 << (logn - loga), R = 1 << loga;
-    const int limb = blockIdx.y;
-    const int pid = limb_prime(s, limb);
-    const u64 q = pc[pid].q, q2 = 2 * q;
-    u64* data = s.base + (size_t)blockIdx.z * s.poly_stride + (size_t)limb * n;
-    const u64* w = psi + (size_t)pid * n;
-    const u64* wsh = psi_sh + (size_t)pid * n;
-    const int c0 = blockIdx.x * NTT_COLS;
-    for (int idx = threadIdx.x; idx < R * NTT_COLS; idx += blockDim.x) {
-        int r = idx / NTT_COLS, c = idx % NTT_COLS;
-        sm[idx] = data[(size_t)r * B + c0 + c];
-    }
-    __syncthreads();
-    for (int st = 0; st < loga; st++) {
-        const int m = 1 << st, tt = R >> (st + 1);
-        for (int bf = threadIdx.x; bf < (R / 2) * NTT_COLS; bf += blockDim.x) {
-            int c = bf % NTT_COLS, p = bf / NTT_COLS;
-            int i = p / tt, r = i * 2 * tt + (p % tt);
-            u64 W = __ldg(w + m + i), Wsh = __ldg(wsh + m + i);
-            u64 U = sm[r * NTT_COLS + c];
-            u64 V = shoup_lazy(sm[(r + tt) * NTT_COLS + c], W, Wsh, q);
-            u64 x = U + V;
-            if (x >= q2) x -= q2;
-            u64 y = U + q2 - V;
-            if (y >= q2) y -= q2;
-            sm[r * NTT_COLS + c] = x;
-            sm[(r + tt) * NTT_COLS + c] = y;
-        }
-        __syncthreads();
-    }
-    for (int idx = threadIdx.x; idx < R * NTT_COLS; idx += blockDim.x) {
-        int r = idx / NTT_COLS, c = idx % NTT_COLS;
-        data[(size_t)r * B + c0 + c] = sm[idx];
-    }
-}
-
-__global__ void __launch_bounds__(TPB) k_ntt_fwd_row(LimbSet s, int logn, int loga, int rows, const PrimeConst* __restrict__ pc,
-                                                     const u64* __restrict__ psi, const u64* __restrict__ psi_sh) {
-    extern __shared__ u64 sm[];
-    const int n = 1 << logn, logb = logn - loga, B = 1 << logb, R = 1 << loga;
-    const int limb = blockIdx.y;
-    const int pid = limb_prime(s, limb);
-    const u64 q = pc[pid].q, q2 = 2 * q;
-    const int r0 = blockIdx.x * rows;
-    u64* data = s.base + (size_t)blockIdx.z * s.poly_stride + (size_t)limb * n + (size_t)r0 * B;
-    const u64* w = psi + (size_t)pid * n;
-    const u64* wsh = psi_sh + (size_t)pid * n;
-    for (int e = threadIdx.x; e < rows * B; e += blockDim.x) sm[e] = data[e];
-    __syncthreads();
-    for (int st = 0; st < logb; st++) {
-        const int m = R << st, tt = B >> (st + 1);
-        for (int bf = threadIdx.x; bf < rows * (B / 2); bf += blockDim.x) {
-            int rr = bf / (B / 2), p = bf % (B / 2);
-            int il = p / tt, c = il * 2 * tt + (p % tt);
-            int idx = m + ((r0 + rr) << st) + il;
-            u64 W = __ldg(w + idx), Wsh = __ldg(wsh + idx);
-            u64* x0 = sm + rr * B + c;
-            u64 U = x0[0];
-            u64 V = shoup_lazy(x0[tt], W, Wsh, q);
-            u64 x = U + V;
-            if (x >= q2) x -= q2;
-            u64 y = U + q2 - V;
-            if (y >= q2) y -= q2;
-            x0[0] = x;
-            x0[tt] = y;
-        }
-        __syncthreads();
-    }
-    for (int e = threadIdx.x; e < rows * B; e += blockDim.x) {
-        u64 x = sm[e];
-        data[e] = reduce_2q(x, q);
-    }
-}
-
-__global__ void __launch_bounds__(TPB) k_ntt_inv_row(LimbSet s, int logn, int loga, int rows, const PrimeConst* __restrict__ pc,
-                                                     const u64* __restrict__ ipsi, const u64* __restrict__ ipsi_sh) {
-    extern __shared__ u64 sm[];
-    const int n = 1 << logn, logb = logn - loga, B = 1 << logb;
-    const int limb = blockIdx.y;
-    const int pid = limb_prime(s, limb);
-    const u64 q = pc[pid].q, q2 = 2 * q;
-    const int r0 = blockIdx.x * rows;
-    u64* data = s.base + (size_t)blockIdx.z * s.poly_stride + (size_t)limb * n + (size_t)r0 * B;
-    const u64* w = ipsi + (size_t)pid * n;
-    const u64* wsh = ipsi_sh + (size_t)pid * n;
-    for (int e = threadIdx.x; e < rows * B; e += blockDim.x) sm[e] = data[e];
-    __syncthreads();
-    for (int st = 0; st < logb; st++) {
-        const int tt = 1 << st, m = (n >> 1) >> st;
-        for (int bf = threadIdx.x; bf < rows * (B / 2); bf += blockDim.x) {
-            int rr = bf / (B / 2), p = bf % (B / 2);
-            int il = p / tt, c = il * 2 * tt + (p % tt);
-            int idx = m + ((r0 + rr) << (logb - st - 1)) + il;
-            u64 W = __ldg(w + idx), Wsh = __ldg(wsh + idx);
-            u64* x0 = sm + rr * B + c;
-            u64 U = x0[0], V = x0[tt];
-            u64 x = U + V;
-            if (x >= q2) x -= q2;
-            x0[0] = x;
-            x0[tt] = shoup_lazy(U + q2 - V, W, Wsh, q);
-        }
-        __syncthreads();
-    }
-    for (int e = threadIdx.x; e < rows * B; e += blockDim.x) data[e] = sm[e];
-}
-
-__global__ void __launch_bounds__(TPB) k_ntt_inv_col(LimbSet s, int logn, int loga, const PrimeConst* __restrict__ pc,
-                                                     const u64* __restrict__ ipsi, const u64* __restrict__ ipsi_sh) {
-    extern __shared__ u64 sm[];
-    const int n = 1 << logn, B = 1 << (logn - loga), R = 1 << loga;
-    const int limb = blockIdx.y;
-    const int pid = limb_prime(s, limb);
-    const PrimeConst P = pc[pid];
-    const u64 q = P.q, q2 = 2 * q;
-    u64* data = s.base + (size_t)blockIdx.z * s.poly_stride + (size_t)limb * n;
-    const u64* w = ipsi + (size_t)pid * n;
-    const u64* wsh = ipsi_sh + (size_t)pid * n;
-    const int c0 = blockIdx.x * NTT_COLS;
-    for (int idx = threadIdx.x; idx < R * NTT_COLS; idx += blockDim.x) {
-        int r = idx / NTT_COLS, c = idx % NTT_COLS;
-        sm[idx] = data[(size_t)r * B + c0 + c];
-    }
-    __syncthreads();
-    for (int st = 0; st < loga; st++) {
-        const int tt = 1 << st, m = (R >> 1) >> st;
-        for (int bf = threadIdx.x; bf < (R / 2) * NTT_COLS; bf += blockDim.x) {
-            int c = bf % NTT_COLS, p = bf / NTT_COLS;
-            int i = p / tt, r = i * 2 * tt + (p % tt);
-            u64 W = __ldg(w + m + i), Wsh = __ldg(wsh + m + i);
-            u64 U = sm[r * NTT_COLS + c], V = sm[(r + tt) * NTT_COLS + c];
-            u64 x = U + V;
-            if (x >= q2) x -= q2;
-            sm[r * NTT_COLS + c] = x;
-            sm[(r + tt) * NTT_COLS + c] = shoup_lazy(U + q2 - V, W, Wsh, q);
-        }
-        __syncthreads();
-    }
-    for (int idx = threadIdx.x; idx < R * NTT_COLS; idx += blockDim.x) {
-        int r = idx / NTT_COLS, c = idx % NTT_COLS;
-        data[(size_t)r * B + c0 + c] = shoup_mul(sm[idx], P.ninv, P.ninv_shoup, q);
-    }
-}
-
-static int ntt_loga(int logn) { return logn / 2; }
-// rows of the row pass handled by one block: a 2048-word tile, at most all 2^a rows
-static int ntt_rows(int logn, int loga) { return std::min(NTT_ROW_TILE >> (logn - loga), 1 << loga); }
-
-void launch_ntt_forward(const KernelEnv& env, const LimbSet& s, cudaStream_t st) {
-    if (s.n_limbs <= 0 || s.n_polys <= 0) return;
-    ProfScope ps(env, KK_NTT_FWD, st, 2, 2.0 * s.n_limbs * s.n_polys * 8.0 * env.n, (double)s.n_limbs * s.n_polys * (env.n / 2) * env.logn);
-    const int logn = env.logn, loga = ntt_loga(logn), logb = logn - loga;
-    dim3 gc((1 << logb) / NTT_COLS, s.n_limbs, s.n_polys);
-    k_ntt_fwd_col<<<gc, TPB, (size_t)(1 << loga) * NTT_COLS * 8, st>>>(s, logn, loga, env.pc, env.tw.psi, env.tw.psi_sh);
-    const int rows = ntt_rows(logn, loga);
-    dim3 gr((1 << loga) / rows, s.n_limbs, s.n_polys);
-    k_ntt_fwd_row<<<gr, TPB, (size_t)rows * (1 << logb) * 8, st>>>(s, logn, loga, rows, env.pc, env.tw.psi, env.tw.psi_sh);
-}
-
-void launch_ntt_inverse(const KernelEnv& env, const LimbSet& s, cudaStream_t st) {
-    if (s.n_limbs <= 0 || s.n_polys <= 0) return;
-    ProfScope ps(env, KK_NTT_INV, st, 2, 2.0 * s.n_limbs * s.n_polys * 8.0 * env.n, (double)s.n_limbs * s.n_polys * (env.n / 2) * env.logn);
-    const int logn = env.logn, loga = ntt_loga(logn), logb = logn - loga;
-    const int rows = ntt_rows(logn, loga);
-    dim3 gr((1 << loga) / rows, s.n_limbs, s.n_polys);
-    k_ntt_inv_row<<<gr, TPB, (size_t)rows * (1 << logb) * 8, st>>>(s, logn, loga, rows, env.pc, env.tw.ipsi, env.tw.ipsi_sh);
-    dim3 gc((1 << logb) / NTT_COLS, s.n_limbs, s.n_polys);
-    k_ntt_inv_col<<<gc, TPB, (size_t)(1 << loga) * NTT_COLS * 8, st>>>(s, logn, loga, env.pc, env.tw.ipsi, env.tw.ipsi_sh);
 }
 
 // ===========================================================================
@@ -254,9 +39,10 @@ __global__ void k_addsub(u64* out, const u64* a, const u64* b, int n, size_t ps,
     out[off] = r;
 }
 
-void launch_addsub(const KernelEnv& env, u64* out, const u64* a, const u64* b, int limbs, size_t ps, int mode, cudaStream_t st) {
-    ProfScope pf(env, KK_POINTWISE, st, 1, 6.0 * limbs * 8.0 * env.n, 0.0);
-    dim3 g(env.n / TPB, limbs, 2);
+void launch_addsub(const KernelEnv& env, u64* out, const u64* a, const u64* b, int limbs, size_t ps, int mode, cudaStream_t st,
+                   int polys) {
+    ProfScope pf(env, KK_POINTWISE, st, 1, 3.0 * polys * limbs * 8.0 * env.n, 0.0);
+    dim3 g(env.n / TPB, limbs, polys);
     k_addsub<<<g, TPB, 0, st>>>(out, a, b, env.n, ps, env.pc, mode);
 }
 
@@ -300,6 +86,25 @@ void launch_mul_plain(const KernelEnv& env, u64* out, const u64* a, const u64* p
     ProfScope pf(env, KK_POINTWISE, st, 1, 5.0 * limbs * 8.0 * env.n, 2.0 * limbs * env.n);
     dim3 g(env.n / TPB, limbs, 2);
     k_mul_plain<<<g, TPB, 0, st>>>(out, a, pt, env.n, ps, env.pc);
+}
+
+// out (+)= sum_i x_i * K_i, exact modular arithmetic, one reduction per output
+__global__ void k_lincomb(u64* out, LincombArg a, int terms, int accumulate, int n, size_t ps, const PrimeConst* __restrict__ pc) {
+    const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y, c = blockIdx.z;
+    const PrimeConst P = pc[t];
+    const size_t off = c * ps + (size_t)t * n + k;
+    Acc128 acc;
+    for (int i = 0; i < terms; i++) acc.mac(a.x[i][off], a.KR[i][t]);
+    u64 r = acc.redc(P.q, P.qinv);
+    if (accumulate) r = add_mod(r, out[off], P.q);
+    out[off] = r;
+}
+
+void launch_lincomb(const KernelEnv& env, u64* out, const LincombArg& a, int terms, bool accumulate, int limbs, size_t ps,
+                    cudaStream_t st) {
+    ProfScope pf(env, KK_POINTWISE, st, 1, (2.0 * terms + 2.0) * limbs * 8.0 * env.n, 2.0 * terms * limbs * env.n);
+    dim3 g(env.n / TPB, limbs, 2);
+    k_lincomb<<<g, TPB, 0, st>>>(out, a, terms, accumulate ? 1 : 0, env.n, ps, env.pc);
 }
 
 // d = [d0 | d1 | d2] each [limbs][n]: d0 = x0 y0, d1 = x0 y1 + x1 y0, d2 = x1 y1
@@ -371,23 +176,30 @@ __global__ void __launch_bounds__(TPB) k_moddown_conv(const u64* __restrict__ u,
     const int k = blockIdx.x * TPB + threadIdx.x, c = blockIdx.y;
     const int ul = level + 1 + alpha;
     const u64* up = u + (size_t)c * ul * n + (size_t)(level + 1) * n + k;
+    // centred terms: y_k in (-p_k/2, p_k/2]; a negative term contributes y_k (P/p_k) - P
     u64 y[RK_MAX_SPECIAL];
+    int nneg = 0;
 #pragma unroll
     for (int kk = 0; kk < RK_MAX_SPECIAL; kk++) {
         if (kk < alpha) {
             const u64 pk = pc[L + 1 + kk].q;
             y[kk] = shoup_mul(up[(size_t)kk * n], cv.moddown[kk], cv.moddown[alpha + kk], pk);
+            nneg += y[kk] > (pk >> 1) ? 1 : 0;
         }
     }
     u64* out = w + (size_t)c * (level + 1) * n + k;
     const u64* cm = cv.moddown + 2 * alpha;
+    const u64* pmod = cm + (size_t)alpha * (L + 1);
     for (int i = 0; i <= level; i++) {
         const PrimeConst P = pc[i];
         Acc128 acc;
 #pragma unroll
         for (int kk = 0; kk < RK_MAX_SPECIAL; kk++)
             if (kk < alpha) acc.mac(y[kk], __ldg(cm + (size_t)kk * (L + 1) + i));
-        out[(size_t)i * n] = acc.redc(P.q, P.qinv);
+        u64 r = acc.redc(P.q, P.qinv);
+        const u64 pm = __ldg(pmod + i);
+        for (int j = 0; j < nneg; j++) r = sub_mod(r, pm, P.q);
+        out[(size_t)i * n] = r;
     }
 }
 

@@ -4,12 +4,55 @@
 #include "rk_internal.cuh"
 
 
+// Counts every launch; when `kind` is the profiled kind, brackets the launch(es) with
+// CUDA events on the launching stream and accumulates the algorithmic bytes/products.
+struct ProfScope {
+    Profiler* p;
+    bool on = false;
+    cudaStream_t st;
+    double bytes, ops;
+    ProfScope(const KernelEnv& e, int kind, cudaStream_t s, int nlaunch, double b, double o)
+        : p(e.prof), st(s), bytes(b), ops(o) {
+        if (!p) return;
+        p->launches += (uint64_t)nlaunch;
+        if (p->target == kind) {
+            on = true;
+            record();
+        }
+    }
+    void record() {
+        if (p->used == p->ev.size()) {
+            cudaEvent_t ev;
+            cudaEventCreate(&ev);
+            p->ev.push_back(ev);
+        }
+        cudaEventRecord(p->ev[p->used++], st);
+    }
+    ~ProfScope() {
+        if (on) {
+            record();
+            p->bytes += bytes;
+            p->ops += ops;
+            p->timed++;
+        }
+    }
+};
+
+void ntt_init_attributes();
 void launch_ntt_forward(const KernelEnv& env, const LimbSet& s, cudaStream_t st);
 void launch_ntt_inverse(const KernelEnv& env, const LimbSet& s, cudaStream_t st);
-void launch_addsub(const KernelEnv& env, u64* out, const u64* a, const u64* b, int limbs, size_t ps, int mode, cudaStream_t st);
+void launch_addsub(const KernelEnv& env, u64* out, const u64* a, const u64* b, int limbs, size_t ps, int mode, cudaStream_t st,
+                   int polys = 2);
 void launch_add_const(const KernelEnv& env, u64* out, const u64* a, const ScalarArg& K, int limbs, size_t ps, cudaStream_t st);
 void launch_mul_scalar(const KernelEnv& env, u64* out, const u64* a, const ScalarArg& K, int limbs, size_t ps, cudaStream_t st);
 void launch_mul_plain(const KernelEnv& env, u64* out, const u64* a, const u64* pt, int limbs, size_t ps, cudaStream_t st);
+// out[c][t] (+)= sum_i x_i[c][t] * K_i[t] for up to 16 terms; KR holds K_i times R
+struct LincombArg {
+    const u64* x[16];
+    u64 KR[16][RK_MAX_PRIMES];
+};
+void launch_lincomb(const KernelEnv& env, u64* out, const LincombArg& a, int terms, bool accumulate, int limbs, size_t ps,
+                    cudaStream_t st);
 void launch_tensor(const KernelEnv& env, u64* d, const u64* x, const u64* y, int limbs, size_t ps, cudaStream_t st);
 void launch_modup(const KernelEnv& env, const u64* x, u64* ext, size_t ext_stride, int level, int beta, cudaStream_t st);
 void launch_moddown_conv(const KernelEnv& env, const u64* u, u64* w, int level, cudaStream_t st);

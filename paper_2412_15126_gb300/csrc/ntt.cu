@@ -1,0 +1,260 @@
+// Negacyclic NTT over 64-bit primes (sm_103a), register-blocked.
+//
+// n = 2^logn is split as 2^a x 2^b (a = logn/2).  The column pass runs the first a
+// Cooley-Tukey stages on the 2^a-point columns {r 2^b + c}; the row pass runs the
+// last b stages on the contiguous 2^b-point rows (merged psi twiddles in bit-reversed
+// order, so the output index i holds the value at psi^(2 brev(i) + 1)).  The inverse
+// (Gentleman-Sande) runs the row pass first and folds n^-1 into the column pass.
+//
+// Inside a pass a transform of T = 2^LOG points is owned by P = 2^(LOG/2) threads,
+// each holding E = T/P residues in registers: the butterfly stages whose span is at
+// least P run on the strided set {t + P m}, the others on the contiguous set
+// {t E + m}, with one shared-memory exchange in between.  The twiddle of a
+// butterfly whose lower element has in-transform index x, at span 2^v, is entry
+//   (1 << (Sbase - v)) + (rho << (LOG - 1 - v)) + (x >> (v + 1))
+// of the (inverse) table, Sbase = a - 1 for the column pass and logn - 1 for the row
+// pass, rho the row number of a row-pass transform (0 in the column pass).
+// Residues stay in [0, 2q) between stages (Shoup products, Harvey's lazy bounds).
+#include <algorithm>
+
+#include "kernels.cuh"
+
+namespace {
+
+__device__ __forceinline__ void ct_bfly(u64& a, u64& b, u64 w, u64 wsh, u64 q, u64 q2) {
+    u64 U = a;
+    u64 V = shoup_lazy(b, w, wsh, q);
+    u64 x = U + V;
+    if (x >= q2) x -= q2;
+    u64 y = U + q2 - V;
+    if (y >= q2) y -= q2;
+    a = x;
+    b = y;
+}
+
+__device__ __forceinline__ void gs_bfly(u64& a, u64& b, u64 w, u64 wsh, u64 q, u64 q2) {
+    u64 U = a, V = b;
+    u64 x = U + V;
+    if (x >= q2) x -= q2;
+    a = x;
+    b = shoup_lazy(U + q2 - V, w, wsh, q);
+}
+
+template <int LOG, bool INV, bool COL>
+__global__ void __launch_bounds__(256) k_ntt_pass(LimbSet s, int logn, int loga, int units, const PrimeConst* __restrict__ pc,
+                                                  const u64* __restrict__ tw, const u64* __restrict__ tw_sh) {
+    constexpr int T = 1 << LOG, LOGP = LOG / 2, P = 1 << LOGP, LOGE = LOG - LOGP, E = 1 << LOGE;
+    extern __shared__ u64 sm[];
+    const int n = 1 << logn, B = 1 << (logn - loga);
+    const int limb = blockIdx.y;
+    const int pid = limb_prime(s, limb);
+    const PrimeConst PC = pc[pid];
+    const u64 q = PC.q, q2 = 2 * q;
+    u64* data = s.base + (size_t)blockIdx.z * s.poly_stride + (size_t)limb * n;
+    const u64* W = tw + (size_t)pid * n;
+    const u64* Wsh = tw_sh + (size_t)pid * n;
+    const int Sbase = COL ? loga - 1 : logn - 1;
+    const int tid = threadIdx.x;
+    int u, t, rho;
+    u64* g;
+    size_t gs;   // element x of this thread's transform is g[x * gs]
+    if (COL) {
+        u = tid % units;
+        t = tid / units;
+        rho = 0;
+        g = data + (size_t)blockIdx.x * units + u;
+        gs = (size_t)B;
+    } else {
+        u = tid / P;
+        t = tid % P;
+        rho = blockIdx.x * units + u;
+        g = data + (size_t)rho * B;
+        gs = 1;
+    }
+    // shared-memory slot of element e of this thread's transform (rows are swizzled
+    // so that both the strided and the contiguous access patterns avoid conflicts)
+    auto sidx = [&](int e) -> int {
+        if (COL) return e * units + u;
+        return u * T + (e ^ ((e >> LOGE) & (E - 1)));
+    };
+    auto twid = [&](int v, int x, u64& w, u64& wsh) {
+        const int idx = (1 << (Sbase - v)) + (rho << (LOG - 1 - v)) + (x >> (v + 1));
+        w = __ldg(W + idx);
+        wsh = __ldg(Wsh + idx);
+    };
+    u64 x[E];
+
+    if (!INV) {
+        // load the strided set {t + P m}: coalesced over u (columns) or t (rows)
+#pragma unroll
+        for (int m = 0; m < E; m++) x[m] = g[(size_t)(t + P * m) * gs];
+        // stages with span 2^v >= P, v = LOG-1 .. LOGP; m-span 2^(v - LOGP)
+#pragma unroll
+        for (int v = LOG - 1; v >= LOGP; v--) {
+            const int h = 1 << (v - LOGP);
+#pragma unroll
+            for (int m = 0; m < E; m++) {
+                if (m & h) continue;
+                u64 w, wsh;
+                twid(v, t + P * m, w, wsh);
+                ct_bfly(x[m], x[m + h], w, wsh, q, q2);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < E; m++) sm[sidx(t + P * m)] = x[m];
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < E; m++) x[m] = sm[sidx(t * E + m)];
+        // stages with span 2^v < P on the contiguous set {t E + m}
+#pragma unroll
+        for (int v = LOGP - 1; v >= 0; v--) {
+            const int h = 1 << v;
+#pragma unroll
+            for (int m = 0; m < E; m++) {
+                if (m & h) continue;
+                u64 w, wsh;
+                twid(v, t * E + m, w, wsh);
+                ct_bfly(x[m], x[m + h], w, wsh, q, q2);
+            }
+        }
+        if (COL) {
+            // column pass output stays in [0, 2q); coalesced over u
+#pragma unroll
+            for (int m = 0; m < E; m++) g[(size_t)(t * E + m) * gs] = x[m];
+        } else {
+            __syncthreads();
+#pragma unroll
+            for (int m = 0; m < E; m++) sm[sidx(t * E + m)] = x[m];
+            __syncthreads();
+#pragma unroll
+            for (int m = 0; m < E; m++) g[t + P * m] = reduce_2q(sm[sidx(t + P * m)], q);
+        }
+    } else {
+        // load the contiguous set {t E + m}
+        if (COL) {
+#pragma unroll
+            for (int m = 0; m < E; m++) x[m] = g[(size_t)(t * E + m) * gs];
+        } else {
+#pragma unroll
+            for (int m = 0; m < E; m++) sm[sidx(t + P * m)] = g[t + P * m];
+            __syncthreads();
+#pragma unroll
+            for (int m = 0; m < E; m++) x[m] = sm[sidx(t * E + m)];
+            __syncthreads();
+        }
+        // stages with span 2^v < P, v = 0 .. LOGP-1
+#pragma unroll
+        for (int v = 0; v < LOGP; v++) {
+            const int h = 1 << v;
+#pragma unroll
+            for (int m = 0; m < E; m++) {
+                if (m & h) continue;
+                u64 w, wsh;
+                twid(v, t * E + m, w, wsh);
+                gs_bfly(x[m], x[m + h], w, wsh, q, q2);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < E; m++) sm[sidx(t * E + m)] = x[m];
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < E; m++) x[m] = sm[sidx(t + P * m)];
+        // stages with span 2^v >= P on the strided set {t + P m}
+#pragma unroll
+        for (int v = LOGP; v < LOG; v++) {
+            const int h = 1 << (v - LOGP);
+#pragma unroll
+            for (int m = 0; m < E; m++) {
+                if (m & h) continue;
+                u64 w, wsh;
+                twid(v, t + P * m, w, wsh);
+                gs_bfly(x[m], x[m + h], w, wsh, q, q2);
+            }
+        }
+        if (COL) {   // last inverse pass: times n^-1, result in [0, q)
+#pragma unroll
+            for (int m = 0; m < E; m++) g[(size_t)(t + P * m) * gs] = shoup_mul(x[m], PC.ninv, PC.ninv_shoup, q);
+        } else {
+#pragma unroll
+            for (int m = 0; m < E; m++) g[t + P * m] = x[m];
+        }
+    }
+}
+
+template <bool INV, bool COL>
+void pass_launch(int LOG, dim3 grid, int threads, size_t smem, cudaStream_t st, const LimbSet& s, int logn, int loga,
+                 int units, const PrimeConst* pc, const u64* tw, const u64* tw_sh) {
+    switch (LOG) {
+#define RK_NTT_CASE(L)                                                                                        \
+    case L:                                                                                                   \
+        k_ntt_pass<L, INV, COL><<<grid, threads, smem, st>>>(s, logn, loga, units, pc, tw, tw_sh);            \
+        break;
+        RK_NTT_CASE(5)
+        RK_NTT_CASE(6)
+        RK_NTT_CASE(7)
+        RK_NTT_CASE(8)
+        RK_NTT_CASE(9)
+#undef RK_NTT_CASE
+        default:
+            throw rk_error(RK_EINVAL, "unsupported NTT pass size");
+    }
+}
+
+template <bool INV, bool COL>
+void set_smem_attr() {
+    const int bytes = 96 * 1024;
+    cudaFuncSetAttribute(k_ntt_pass<5, INV, COL>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_ntt_pass<6, INV, COL>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_ntt_pass<7, INV, COL>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_ntt_pass<8, INV, COL>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_ntt_pass<9, INV, COL>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+// geometry of one pass: transforms of 2^LOG points, `count` of them per limb
+struct PassGeom {
+    dim3 grid;
+    int threads, units;
+    size_t smem;
+};
+
+PassGeom geom(int LOG, int count, const LimbSet& s) {
+    const int P = 1 << (LOG / 2);
+    const int units = std::min(256 / P, count);
+    PassGeom gm;
+    gm.units = units;
+    gm.threads = P * units;
+    gm.grid = dim3(count / units, s.n_limbs, s.n_polys);
+    gm.smem = (size_t)(1 << LOG) * units * 8;
+    return gm;
+}
+
+}  // namespace
+
+void ntt_init_attributes() {
+    set_smem_attr<false, false>();
+    set_smem_attr<false, true>();
+    set_smem_attr<true, false>();
+    set_smem_attr<true, true>();
+}
+
+void launch_ntt_forward(const KernelEnv& env, const LimbSet& s, cudaStream_t st) {
+    if (s.n_limbs <= 0 || s.n_polys <= 0) return;
+    ProfScope ps(env, KK_NTT_FWD, st, 2, 2.0 * s.n_limbs * s.n_polys * 8.0 * env.n,
+                 (double)s.n_limbs * s.n_polys * (env.n / 2) * env.logn);
+    const int logn = env.logn, loga = logn / 2, logb = logn - loga;
+    PassGeom c = geom(loga, 1 << logb, s);
+    pass_launch<false, true>(loga, c.grid, c.threads, c.smem, st, s, logn, loga, c.units, env.pc, env.tw.psi, env.tw.psi_sh);
+    PassGeom r = geom(logb, 1 << loga, s);
+    pass_launch<false, false>(logb, r.grid, r.threads, r.smem, st, s, logn, loga, r.units, env.pc, env.tw.psi, env.tw.psi_sh);
+}
+
+void launch_ntt_inverse(const KernelEnv& env, const LimbSet& s, cudaStream_t st) {
+    if (s.n_limbs <= 0 || s.n_polys <= 0) return;
+    ProfScope ps(env, KK_NTT_INV, st, 2, 2.0 * s.n_limbs * s.n_polys * 8.0 * env.n,
+                 (double)s.n_limbs * s.n_polys * (env.n / 2) * env.logn);
+    const int logn = env.logn, loga = logn / 2, logb = logn - loga;
+    PassGeom r = geom(logb, 1 << loga, s);
+    pass_launch<true, false>(logb, r.grid, r.threads, r.smem, st, s, logn, loga, r.units, env.pc, env.tw.ipsi, env.tw.ipsi_sh);
+    PassGeom c = geom(loga, 1 << logb, s);
+    pass_launch<true, true>(loga, c.grid, c.threads, c.smem, st, s, logn, loga, c.units, env.pc, env.tw.ipsi, env.tw.ipsi_sh);
+}

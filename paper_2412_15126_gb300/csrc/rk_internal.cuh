@@ -62,7 +62,8 @@ struct ConvTables {
     int beta_max;
     int dsize;
     // ModDown (level independent): [0, A) (P/p_k)^-1 mod p_k, [A, 2A) Shoup,
-    //   [2A, 2A + A*(L+1)) (P/p_k) mod q_i times R, row-major [k][i]
+    //   [2A, 2A + A*(L+1)) (P/p_k) mod q_i times R, row-major [k][i],
+    //   then (L+1) words P mod q_i
     const u64* moddown;
     // P^-1 mod q_i and Shoup companion: [2 * (L+1)]
     const u64* pinv;
@@ -156,6 +157,10 @@ struct rk_ctx {
     // plaintext caches: key = (kind, N, Q, n_real, level)
     std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint32_t, int>, u64*> plain_cache;
     std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint32_t>, std::vector<double>> encodings;
+    // plaintexts for addition (scale Delta_l, normal form), same key
+    std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint32_t, int>, u64*> plain_add_cache;
+    // Chebyshev coefficients of the indicator window per padded length N
+    std::map<uint32_t, std::vector<double>> indicator;
     // op counters
     uint64_t n_ks = 0, n_rot = 0, n_mul = 0, n_rescale = 0;
     size_t ct_words() const { return (size_t)2 * (L + 1) * n; }
@@ -191,6 +196,8 @@ void ev_mul_scalar(rk_ctx* c, const rk_ct* a, double v, rk_ct* out);        // o
 void ev_mul(rk_ctx* c, const rk_ct* a, const rk_ct* b, rk_ct* out);         // out at level-1
 void ev_mul_plain(rk_ctx* c, const rk_ct* a, uint32_t kind, uint32_t N, uint32_t Q, uint32_t n_real, rk_ct* out);
 void ev_rotate_many(rk_ctx* c, const rk_ct* a, const int* r, int k, rk_ct** outs);  // left rotations
+void ev_add_plain(rk_ctx* c, const rk_ct* a, uint32_t kind, uint32_t N, uint32_t Q, uint32_t n_real, rk_ct* out);
+void ev_lincomb(rk_ctx* c, const std::vector<const rk_ct*>& xs, const std::vector<double>& cs, rk_ct* out);  // out at level-1
 void ev_level_down(rk_ctx* c, const rk_ct* a, int target, rk_ct* out);
 void ev_copy(rk_ctx* c, const rk_ct* a, rk_ct* out);
 

@@ -27,6 +27,8 @@ LAYOUT_ROW, LAYOUT_COL = 0, 1
 MASK_ROW0, MASK_COL0, MASK_TIE, MASK_TRI, MASK_VALID = 1, 2, 3, 4, 5
 KEY_RELIN, KEY_GALOIS = 1, 2
 TIES_CORRECT = 1
+TIES_FIRST, TIES_ALL = 0, 2
+MASK_ROW0S, MASK_COL0S, MASK_TIEC, MASK_SORTIDX = 6, 7, 8, 9
 
 
 class RkError(RuntimeError):
@@ -86,6 +88,9 @@ _sig("rk_rescale", [_vp, _vp, ctypes.POINTER(_vp)])
 _sig("rk_rescale_noalloc", [_vp, _vp, _vp, _u32])
 _sig("rk_rank", [_vp, _vp, _u32, ctypes.POINTER(_vp)])
 _sig("rk_compare_matrix", [_vp, _vp, ctypes.POINTER(_vp)])
+_sig("rk_order_stat", [_vp, _vp, _u32, _u32, ctypes.POINTER(_vp)])
+_sig("rk_sort", [_vp, _vp, _u32, ctypes.POINTER(_vp)])
+_sig("rk_indicator_import", [_vp, _u32, _dp, _sz])
 _sig("rk_rank_batch", [_vp, ctypes.POINTER(_vp), _sz, _u32, ctypes.POINTER(_vp)])
 _sig("rk_ntt_forward", [_vp, _vp, _u32, _u32])
 _sig("rk_ntt_inverse", [_vp, _vp, _u32, _u32])
@@ -273,6 +278,16 @@ class Context:
 
     def compare_matrix(self, ct):
         return self._out(_L.rk_compare_matrix, ct.handle)
+
+    def order_stat(self, ct, k, flags=0):
+        return self._out(_L.rk_order_stat, ct.handle, int(k), flags)
+
+    def sort(self, ct, flags=0):
+        return self._out(_L.rk_sort, ct.handle, flags)
+
+    def indicator_import(self, N, coeffs):
+        c = np.ascontiguousarray(coeffs, dtype=np.float64)
+        _check(_L.rk_indicator_import(self.handle, N, c.ctypes.data_as(_dp), c.size))
 
     def rescale_noalloc(self, d_in: int, d_out: int, level: int):
         """Rescale between caller-owned device buffers (evaluation domain) with no

@@ -12,9 +12,11 @@ CONFIGS = {
     "cfg1": (13, 14, 40, 40, 1, 61, 1, 2, 1),       # N = 8 rank, n = 2^13, 14 x ~40-bit + 1 special
     "cfg2": (16, 28, 60, 45, 3, 61, 3, 4, 2),       # N = 128 rank, n = 2^16, 28 limbs + 3 special
     "cfg3": (16, 34, 60, 45, 3, 61, 3, 3, 2),       # N = 128 ties, 34 limbs
+    "ord": (11, 24, 60, 40, 2, 61, 2, 2, 1),        # deep small ring for order statistics / sort parity
 }
 
-MASK_IDS = {"row0": 1, "col0": 2, "tie": 3, "tri": 4, "valid": 5}
+MASK_IDS = {"row0": 1, "col0": 2, "tie": 3, "tri": 4, "valid": 5, "row0s": 6, "col0s": 7, "tiec": 8, "sortidx": 9}
+ALL_MASKS = ("row0", "col0", "tie", "tri", "row0s", "col0s", "tiec", "sortidx")
 
 
 def oracle_params(name):

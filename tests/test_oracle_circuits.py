@@ -50,3 +50,23 @@ def test_encrypted_tie_corrected_rank(small):
     R = C.rank_tie_corrected(B, ct, 8, 2, 1)
     got = B.values(R)[:8]
     assert np.max(np.abs(got - C.brute_tie_corrected_rank(v))) < 0.25
+
+
+@pytest.fixture(scope="module")
+def deep():
+    P = ckks.gen_params(11, 24, 60, 40, 2, 61, 2)
+    gal = [ckks.galois_left(r % P.slots, P.n) for r in rotation_set(8)]
+    return P, ckks.keygen(P, 7, gal)
+
+
+def test_encrypted_argmin_argmax_sort_n8(deep):
+    P, keys = deep
+    v = np.array([3, 1, 3, 0, 2, 1, 3, 2]) / 4.0
+    ct = ckks.encrypt(P, keys, v, 2)
+    B = C.OracleCkks(P, keys)
+    o = B.values(C.order_statistic(B, ct, 8, 1, 2, 1))[:8]
+    assert np.max(np.abs(o - (np.arange(8) == 3))) < 0.01
+    o = B.values(C.order_statistic(B, ct, 8, 8, 2, 1, ties="all"))[:8]
+    assert np.max(np.abs(o - (v == v.max()))) < 0.01
+    s = B.values(C.sort(B, ct, 8, 2, 1))[:8]
+    assert np.max(np.abs(s - np.sort(v))) < 0.01

@@ -15,7 +15,7 @@ N_RING = 1 << LOG_N
 @pytest.fixture(scope="module")
 def setup():
     P = ckks.gen_params(LOG_N, 6, 60, 40, 2, 61, 2)
-    rots = [1, 5, P.slots - 3, 17]
+    rots = [1, 3, 5, P.slots - 3, 17]
     keys = ckks.keygen(P, 42, [ckks.galois_left(r, P.n) for r in rots])
     rng = np.random.default_rng(9)
     z1 = rng.uniform(-1, 1, P.slots)
@@ -107,6 +107,44 @@ def test_mod_down_divides_by_P(setup):
         if d > (Q * Pp) // 2:
             d -= Q * Pp
         assert abs(d) <= (P.alpha + 1) * Pp
+
+
+def test_mod_down_is_unbiased(setup):
+    """out*P - u has mean ~0 over coefficients: the centred conversion removes the
+    positive bias (alpha-1)/2 * P of an uncentred fast conversion."""
+    P, _, _, _, _, _, _ = setup
+    lvl = 3
+    primes = P.qp(lvl)
+    rng = np.random.default_rng(8)
+    u = np.stack([rng.integers(0, q, P.n, dtype=np.uint64) for q in primes])
+    out = ckks.mod_down(P, u, lvl)
+    Pp = math.prod(P.p)
+    Q = math.prod(P.q[: lvl + 1])
+    U = ckks.crt_centered(u, primes)
+    Y = ckks.crt_centered(out, P.q[: lvl + 1])
+    d = []
+    for k in range(P.n):
+        x = (int(Y[k]) * Pp - int(U[k])) % (Q * Pp)
+        if x > (Q * Pp) // 2:
+            x -= Q * Pp
+        d.append(x / Pp)
+    assert abs(np.mean(d)) < 0.1
+    assert max(abs(x) for x in d) <= P.alpha
+
+
+def test_rotation_error_is_unbiased(setup):
+    """After eight rotations the decrypted coefficients minus the encoded expected
+    slots have mean ~0.  (A constant coefficient bias b decodes to an error of about
+    b 2n/pi at slot 0; an uncentred ModDown gives b ~ (alpha-1)/2 * sum(s) per switch.)"""
+    P, keys, z1, _, c1, _, rots = setup
+    x = c1
+    tot = 0
+    for r in (1, 5, 17, 3) * 2:
+        x = ckks.rotate(P, keys, x, r)
+        tot += r
+    got = ckks.decrypt_coeffs(P, keys, x).astype(np.float64)
+    expect = ckks.encode(np.roll(z1, -tot), P.scales[x.level], P.n).astype(np.float64)
+    assert abs(np.mean(got - expect)) < 5.0
 
 
 def test_key_switch_relation(setup):

@@ -160,3 +160,63 @@ def test_packed_queries_do_not_leak():
     R = B.values(C.rank(B, C.PV(X, 40), N, 4, 2, Q=Q))
     for q, v in enumerate(vs):
         assert np.max(np.abs(R[q * N * N: q * N * N + N] - C.brute_fractional_rank(v))) < 1e-3
+
+
+def test_fig3_sort_example(golden):
+    g = golden["fig3_sort"]
+    v = np.array(g["input"]) / 64.0
+    B = C.PlainSlots(64, 40)
+    S = B.values(C.sort(B, B.fresh(v), 4, 3, 2))
+    assert np.max(np.abs(S[:4] - np.array(g["sorted"]) / 64.0)) < 1e-4
+    assert np.all(np.abs(S[4:16]) < 1e-9)
+
+
+def test_cheb_ps_matches_chebyshev_sum():
+    """The recursive split p = q T_m + r reproduces sum_i c_i T_i(t) (numpy's chebval)."""
+    rng = np.random.default_rng(3)
+    for length in (4, 8, 16, 64, 256):
+        c = rng.uniform(-1, 1, length)
+        t = np.linspace(-1, 1, 97)
+        B = C.PlainSlots(97, 40)
+        got = B.values(C.cheb_ps(B, C.PV(t.copy(), 40), c))
+        assert np.max(np.abs(got - np.polynomial.chebyshev.chebval(t, c))) < 1e-9
+        assert B.level is not None
+
+
+def test_cheb_ps_depth():
+    for length in (8, 64, 1024):
+        B = C.PlainSlots(4, 40)
+        out = C.cheb_ps(B, C.PV(np.zeros(4), 40), np.ones(length))
+        assert out.level == 40 - C.cheb_depth(length)
+
+
+@pytest.mark.parametrize("N", [4, 8, 32, 128])
+def test_sinc2_window_is_indicator_at_integers(N):
+    c = C.sinc2_window_coeffs(N)
+    assert len(c) == max(8 * N, 128)
+    ks = np.arange(-N + 1, N)
+    vals = np.polynomial.chebyshev.chebval(ks / N, c)
+    assert np.max(np.abs(vals - (ks == 0))) < 1e-9
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_order_statistics_and_sort_brute_force(seed):
+    rng = np.random.default_rng(200 + seed)
+    N = [8, 16, 32, 64][seed]
+    v = rng.integers(0, 16, N) / 16.0
+    s = np.sort(v)
+    for k in (1, N // 2, N):
+        B = C.PlainSlots(max(2 * N * N, 64), 40)
+        O = B.values(C.order_statistic(B, B.fresh(v), N, k, 3, 2))[:N]
+        first = np.zeros(N)
+        first[int(np.where(C.brute_tie_corrected_rank(v) == k)[0][0])] = 1
+        assert np.max(np.abs(O - first)) < 1e-6
+    B = C.PlainSlots(max(2 * N * N, 64), 40)
+    O = B.values(C.order_statistic(B, B.fresh(v), N, 1, 3, 2, ties="all"))[:N]
+    assert np.max(np.abs(O - (v == v.min()))) < 1e-6
+    B = C.PlainSlots(max(2 * N * N, 64), 40)
+    O = B.values(C.order_statistic(B, B.fresh(v), N, N, 3, 2, ties="all"))[:N]
+    assert np.max(np.abs(O - (v == v.max()))) < 1e-6
+    B = C.PlainSlots(max(2 * N * N, 64), 40)
+    S = B.values(C.sort(B, B.fresh(v), N, 3, 2))[:N]
+    assert np.max(np.abs(S - s)) < 1e-6
