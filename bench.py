@@ -220,6 +220,69 @@ def cpu_cores():
 
 
 # ---------------------------------------------------------------------------
+# batched form: 96 queries of N in {16, 32, 64, 128} + 8 queries of N = 512 (4 blocks)
+# ---------------------------------------------------------------------------
+def batched_workload(ctx, seed=4):
+    """Per-query form (one ciphertext and one circuit per query, blocked queries one
+    Alg. 7 each) against the batched form (queries of one length slot-packed Q =
+    (n/2)/N^2 per ciphertext, ciphertexts of one shape stacked into one circuit,
+    N = 512 queries packed two per block ciphertext).  Inputs resident; both timed
+    end of queue to end of queue with CUDA events on the library stream."""
+    import numpy as np
+    import torch
+    from paper_2412_15126_gb300 import inputs
+    from oracle.circuits import brute_fractional_rank
+
+    slots = 1 << (WORKLOAD["log_n"] - 1)
+    lens = inputs.batch_lengths(96, seed=seed)
+    vecs = [inputs.gap_vector(N, WORKLOAD["gap"], 10_000 + i) for i, N in enumerate(lens)]
+    big = [inputs.gap_vector(512, WORKLOAD["gap"], 20_000 + i) for i in range(8)]
+    pq = [ctx.encrypt(v, N=N) for v, N in zip(vecs, lens)]
+    pq_blocks = [[ctx.encrypt(v[128 * b:128 * (b + 1)], N=128) for b in range(4)] for v in big]
+    packed, packed_ids = [], []
+    for N in sorted(set(lens)):
+        ids = [i for i, x in enumerate(lens) if x == N]
+        qmax = slots // (N * N)
+        for s in range(0, len(ids), qmax):
+            chunk = ids[s:s + qmax]
+            packed.append(ctx.encrypt(np.concatenate([vecs[i] for i in chunk]), N=N, Q=len(chunk), n_real=N))
+            packed_ids.append(chunk)
+    pk_blocks = []
+    for a in range(0, 8, 2):
+        pk_blocks.append([ctx.encrypt(np.concatenate([big[a][128 * b:128 * (b + 1)], big[a + 1][128 * b:128 * (b + 1)]]),
+                                      N=128, Q=2, n_real=128) for b in range(4)])
+    def timed(fn):
+        ctx.sync()
+        t0 = time.perf_counter()
+        out = fn()
+        ctx.sync()
+        return time.perf_counter() - t0, out
+
+    per_query = lambda: ([ctx.rank(c) for c in pq], [ctx.rank_blocked(b) for b in pq_blocks])
+    batched = lambda: (ctx.rank_batch(packed), [ctx.rank_blocked(b) for b in pk_blocks])
+    timed(batched)          # warm-up: plaintext masks and stack scratch
+    timed(per_query)
+    t_pq, out_pq = timed(per_query)
+    t_b, out_b = timed(batched)
+    # correctness of the batched outputs
+    err = 0.0
+    for ct, chunk in zip(out_b[0], packed_ids):
+        got = ctx.decrypt(ct).reshape(len(chunk), -1)
+        for row, i in zip(got, chunk):
+            err = max(err, float(np.max(np.abs(row - brute_fractional_rank(vecs[i])))))
+    for pair, blocks in zip(range(0, 8, 2), out_b[1]):
+        got = np.stack([ctx.decrypt(b).reshape(2, 128) for b in blocks], axis=1).reshape(2, 512)
+        for q in range(2):
+            err = max(err, float(np.max(np.abs(got[q] - brute_fractional_rank(big[pair + q])))))
+    n_q = len(vecs) + len(big)
+    elems = sum(lens) + 512 * len(big)
+    return {"queries": n_q, "elements": elems, "per_query_s": t_pq, "batched_s": t_b,
+            "ranks_per_s": n_q / t_b, "per_query_ranks_per_s": n_q / t_pq, "elements_per_s": elems / t_b,
+            "speedup": t_pq / t_b, "ciphertexts_batched": len(packed) + 4 * len(pk_blocks),
+            "ciphertexts_per_query": len(pq) + 4 * len(pq_blocks), "max_rank_error": err}
+
+
+# ---------------------------------------------------------------------------
 # arms
 # ---------------------------------------------------------------------------
 def dist_info():
@@ -349,6 +412,32 @@ def run_cuda(args):
     h2d = 2 * W["n_limbs"] * n * 8
     d2h = 2 * (out_level + 1) * n * 8 if out_level is not None else 0
 
+    # the same steps replayed from one CUDA graph of the rank circuit
+    graph = None
+    if not args.no_graph:
+        g = ctx.graph_rank(cts[0])
+        for i in range(args.warmup):
+            g.run(cts[i]).free()
+        ctx.sync()
+        gev0 = torch.cuda.Event(enable_timing=True)
+        gev1 = torch.cuda.Event(enable_timing=True)
+        gouts = []
+        with torch.cuda.stream(stream):
+            gev0.record(stream)
+            for i in range(args.steps):
+                gouts.append(g.run(cts[args.warmup + i]))
+            gev1.record(stream)
+        gev1.synchronize()
+        same = bool(np.array_equal(gouts[-1].export(), ctx.rank(cts[args.warmup + args.steps - 1]).export()))
+        graph = {"ms_per_step": gev0.elapsed_time(gev1) / args.steps, "bit_identical_to_direct": same}
+        for o in gouts:
+            o.free()
+        g.free()
+
+    batched = None
+    if not args.no_batched:
+        batched = batched_workload(ctx)
+
     peak, peak_kind = measured_peaks()
     achieved = None
     if prof["launches"] and prof["ms"] > 0:
@@ -377,6 +466,8 @@ def run_cuda(args):
                          "avg_launch_us": prof["ms"] * 1000.0 / max(prof["launches"], 1),
                          "launches": prof["launches"]},
             "cpu_baseline": cpu,
+            "batched": batched,
+            "graph": graph,
             "clocks": clk,
             "gpu_launches": launches,
         }
@@ -397,6 +488,8 @@ def main():
     ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
     ap.add_argument("--roofline-kernel", default="ks_inner")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 104-query batched workload")
+    ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay of the rank steps")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

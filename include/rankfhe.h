@@ -172,6 +172,16 @@ rk_status rk_decrypt(rk_ctx* ctx, const rk_ct* ct, double* out, size_t cap, uint
  * residues) with its vector metadata.  Errors: RK_EINVAL. */
 rk_status rk_ct_import(rk_ctx* ctx, const uint64_t* coeffs, uint32_t level, uint32_t N, uint32_t Q,
                        uint32_t n_real, rk_ct** out);
+/* Stack `count` ciphertexts of the same level and vector shape into one handle
+ * ([count][2][L+1][n] in device memory, copied): every operation and circuit on a
+ * stacked handle runs all of them with one launch per kernel, each switching key
+ * read once per 8 ciphertexts.  Errors: RK_EINVAL on a shape mismatch. */
+rk_status rk_ct_stack(rk_ctx* ctx, const rk_ct* const* in, uint32_t count, rk_ct** out);
+/* Split a stacked handle into rk_ct_count(in) single ciphertexts (copied). */
+rk_status rk_ct_unstack(rk_ctx* ctx, const rk_ct* in, rk_ct** outs);
+/* Number of ciphertexts in a handle (1 unless stacked). */
+uint32_t rk_ct_count(const rk_ct* ct);
+
 /* Export in canonical form; cap in words must be >= 2*(level+1)*n. */
 rk_status rk_ct_export(const rk_ct* ct, uint64_t* coeffs, size_t cap);
 uint32_t rk_ct_level(const rk_ct* ct);
@@ -240,9 +250,33 @@ rk_status rk_order_stat(rk_ctx* ctx, const rk_ct* in, uint32_t k, uint32_t flags
  * the ascending values in row 0 of the output.  Errors as rk_order_stat. */
 rk_status rk_sort(rk_ctx* ctx, const rk_ct* in, uint32_t flags, rk_ct** out);
 
-/* Ranks of `count` ciphertexts (each its own query set), one circuit per input,
- * all queued on the context stream. */
+/* Multi-ciphertext ranking (Alg. 7, Sec. 5): a vector of L*B values split into L
+ * blocks of B (a power of two with B^2 <= n/2), block i encrypted in row 0 of
+ * blocks[i] (all at one level, unpadded).  outs[i] receives the fractional ranks of
+ * block i's values among all L*B values, in row 0.  Only the L(L+1)/2 comparisons
+ * C_{i,j}, j >= i, are evaluated (Eq. 3), as one stacked circuit.  flags must be 0.
+ * Errors: RK_EDEPTH, RK_ENOKEY, RK_EINVAL. */
+rk_status rk_rank_blocked(rk_ctx* ctx, const rk_ct* const* blocks, uint32_t L, uint32_t flags, rk_ct** outs);
+
+/* Ranks of `count` ciphertexts (each its own query set).  Inputs of the same level
+ * and vector shape are stacked and run as one circuit (one launch per kernel for
+ * the group); out[i] is the rank ciphertext of in[i]. */
 rk_status rk_rank_batch(rk_ctx* ctx, const rk_ct* const* in, size_t count, uint32_t flags, rk_ct** out);
+
+/* ---- CUDA graphs -------------------------------------------------------------- */
+
+typedef struct rk_graph rk_graph;
+
+/* Capture the whole rank circuit (rk_rank with `flags`) for inputs shaped like
+ * `tmpl` (level, N, Q, n_real, stack size) as one CUDA graph on the context stream.
+ * Runs the circuit once first (to build cached plaintexts and size the scratch).
+ * Must not be called while the context stream is being captured elsewhere.
+ * Errors: as rk_rank, RK_ECUDA if capture or instantiation fails. */
+rk_status rk_graph_rank(rk_ctx* ctx, const rk_ct* tmpl, uint32_t flags, rk_graph** out);
+/* Replay: copy `in` (same shape as the template) into the captured input, launch
+ * the graph and return the result in a new handle (owned by the caller). */
+rk_status rk_graph_run(rk_graph* g, const rk_ct* in, rk_ct** out);
+void rk_graph_free(rk_graph* g);
 
 /* ---- raw kernels on device buffers (for parity tests and composition) ------- */
 

@@ -340,6 +340,36 @@ def rank(B, V, N, dg, df, Q=1, n_real=None):
     return B.add_const(sum_r(B, C, N, Q), 0.5)
 
 
+def rank_blocked(B, Vs, Bsz, dg, df, Q=1):
+    """Alg. 7, multi-ciphertext ranking of a vector split into L blocks of Bsz values
+    (block i in row 0 of Vs[i]).  C_{i,j} = Cmp(ReplR(V_i), ReplC(TransR(V_j))) for
+    j >= i only; by Eq. 3 the blocks j < i enter as 1 - C_{j,i}, summed column-wise
+    and transposed:  R_i = TransC(SumC(sum_{j<i} (1 - C_{j,i}))) + SumR(sum_{j>=i} C_{i,j}) + 1/2.
+    All R_i leave at the level of the TransC branch (SumR's branch is brought down)."""
+    L = len(Vs)
+    forms = [row_col_forms(B, V, Bsz, Q) for V in Vs]
+    Cs = {}
+    for i in range(L):
+        for j in range(i, L):
+            Cs[(i, j)] = cmp(B, B.sub(forms[i][0], forms[j][1]), dg, df)
+    out = []
+    for i in range(L):
+        A = Cs[(i, i)]
+        for j in range(i + 1, L):
+            A = B.add(A, Cs[(i, j)])
+        S = sum_r(B, A, Bsz, Q)
+        if i > 0:
+            Bs = Cs[(0, i)]
+            for j in range(1, i):
+                Bs = B.add(Bs, Cs[(j, i)])
+            T = trans_c(B, sum_c(B, B.add_const(B.neg(Bs), float(i)), Bsz, Q), Bsz, Q)
+            R = B.add(B.level_down(S, B.level(T)), T)
+        else:
+            R = B.level_down(S, B.level(S) - 1)
+        out.append(B.add_const(R, 0.5))
+    return out
+
+
 def tie_fold(B, C, N, Q=1, kind="tie"):
     """C + E (delta - 1/2) with E = 4 C (1 - C) = 4 K, K = C - C^2 (Alg. 6 before its
     SumR): the plaintext `kind` carries 4 delta - 2 (row form: delta_{j>=i}; column

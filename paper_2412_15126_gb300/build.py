@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "librankfhe.so")
-SOURCES = ["kernels.cu", "context.cu", "evaluator.cu", "encoder.cpp", "circuits.cpp", "capi.cpp", "noalloc.cu", "ntt.cu"]
+SOURCES = ["kernels.cu", "context.cu", "evaluator.cu", "encoder.cpp", "circuits.cpp", "capi.cpp", "noalloc.cu", "ntt.cu", "graph.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off", "-I", INCLUDE]
 

@@ -12,6 +12,11 @@ void rescale_noalloc(rk_ctx* c, const u64* in, u64* out, int l);
 rk_ct* circuit_order_stat(rk_ctx* c, const rk_ct* in, uint32_t k, uint32_t flags);
 rk_ct* circuit_sort(rk_ctx* c, const rk_ct* in, uint32_t flags);
 void indicator_import(rk_ctx* c, uint32_t N, const double* coeffs, size_t count);
+void circuit_rank_blocked(rk_ctx* c, const rk_ct* const* blocks, int L, rk_ct** outs);
+rk_graph* graph_rank_capture(rk_ctx* c, const rk_ct* tmpl, uint32_t flags);
+rk_ct* graph_rank_run(rk_graph* g, const rk_ct* in);
+void graph_free(rk_graph* g);
+rk_ctx* graph_context(const rk_graph* g);
 void circuit_rotations(uint32_t N, std::vector<int>& out);
 
 namespace {
@@ -162,7 +167,7 @@ rk_status rk_encoding_import(rk_ctx* ctx, uint32_t kind, uint32_t N, uint32_t Q,
         need(ctx, "ctx");
         need(u, "u");
         RK_REQUIRE(n == (size_t)ctx->n, RK_EINVAL, "encoding length must be n");
-        RK_REQUIRE(kind >= RK_MASK_ROW0 && kind <= RK_MASK_VALID, RK_EINVAL, "unknown mask kind");
+        RK_REQUIRE(kind >= RK_MASK_ROW0 && kind <= RK_MASK_SORTIDX, RK_EINVAL, "unknown mask kind");
         const uint32_t nr = kind == RK_MASK_VALID ? n_real : 0;
         ctx->encodings[std::make_tuple(kind, N, Q, nr)] = std::vector<double>(u, u + n);
         for (auto it = ctx->plain_cache.begin(); it != ctx->plain_cache.end();) {
@@ -330,7 +335,7 @@ rk_status rk_mul_scalar(rk_ctx* ctx, const rk_ct* a, double v, rk_ct** out) {
 
 rk_status rk_mul_mask(rk_ctx* ctx, const rk_ct* a, uint32_t kind, rk_ct** out) {
     return guard([&] {
-        RK_REQUIRE(kind >= RK_MASK_ROW0 && kind <= RK_MASK_VALID, RK_EINVAL, "unknown mask kind");
+        RK_REQUIRE(kind >= RK_MASK_ROW0 && kind <= RK_MASK_SORTIDX, RK_EINVAL, "unknown mask kind");
         RK_UNARY_OUT(ctx, a, out, a->level,
                      ev_mul_plain(ctx, a, kind, a->N, a->Q, kind == RK_MASK_VALID ? a->n_real : 0, o))
     });
@@ -403,11 +408,31 @@ rk_status rk_rank_batch(rk_ctx* ctx, const rk_ct* const* in, size_t count, uint3
         need(in, "in");
         need(out, "out");
         set_device(ctx);
-        std::vector<rk_ct*> res;
+        // group single ciphertexts of one level and vector shape; each group is one stacked circuit
+        std::map<std::tuple<int, uint32_t, uint32_t, uint32_t, uint32_t>, std::vector<size_t>> groups;
+        for (size_t i = 0; i < count; i++) {
+            same_ctx(ctx, in[i]);
+            RK_REQUIRE(in[i]->B == 1, RK_EINVAL, "rk_rank_batch takes single ciphertexts");
+            groups[std::make_tuple(in[i]->level, in[i]->N, in[i]->Q, in[i]->n_real, in[i]->layout)].push_back(i);
+        }
+        std::vector<rk_ct*> res(count, nullptr);
         try {
-            for (size_t i = 0; i < count; i++) {
-                same_ctx(ctx, in[i]);
-                res.push_back(circuit_rank(ctx, in[i], flags));
+            for (auto& g : groups) {
+                std::vector<const rk_ct*> members;
+                for (size_t i : g.second) members.push_back(in[i]);
+                rk_ct* st = ct_stack(ctx, members.data(), (int)members.size());
+                rk_ct* r = nullptr;
+                try {
+                    r = circuit_rank(ctx, st, flags);
+                } catch (...) {
+                    ct_free(st);
+                    throw;
+                }
+                ct_free(st);
+                std::vector<rk_ct*> parts(members.size());
+                ct_unstack(ctx, r, parts.data());
+                ct_free(r);
+                for (size_t k = 0; k < g.second.size(); k++) res[g.second[k]] = parts[k];
             }
             check_launch();
         } catch (...) {
@@ -417,6 +442,65 @@ rk_status rk_rank_batch(rk_ctx* ctx, const rk_ct* const* in, size_t count, uint3
         for (size_t i = 0; i < count; i++) out[i] = res[i];
     });
 }
+
+rk_status rk_rank_blocked(rk_ctx* ctx, const rk_ct* const* blocks, uint32_t L, uint32_t flags, rk_ct** outs) {
+    return guard([&] {
+        need(ctx, "ctx");
+        need(blocks, "blocks");
+        need(outs, "outs");
+        RK_REQUIRE(flags == 0, RK_EINVAL, "blocked rank takes no flags");
+        for (uint32_t i = 0; i < L; i++) same_ctx(ctx, blocks[i]);
+        set_device(ctx);
+        circuit_rank_blocked(ctx, blocks, (int)L, outs);
+        check_launch();
+    });
+}
+
+rk_status rk_graph_rank(rk_ctx* ctx, const rk_ct* tmpl, uint32_t flags, rk_graph** out) {
+    return guard([&] {
+        need(ctx, "ctx");
+        same_ctx(ctx, tmpl);
+        need(out, "out");
+        set_device(ctx);
+        *out = graph_rank_capture(ctx, tmpl, flags);
+    });
+}
+
+rk_status rk_graph_run(rk_graph* g, const rk_ct* in, rk_ct** out) {
+    return guard([&] {
+        need(g, "graph");
+        need(out, "out");
+        rk_ctx* ctx = graph_context(g);
+        same_ctx(ctx, in);
+        set_device(ctx);
+        *out = graph_rank_run(g, in);
+    });
+}
+
+void rk_graph_free(rk_graph* g) { graph_free(g); }
+
+rk_status rk_ct_stack(rk_ctx* ctx, const rk_ct* const* in, uint32_t count, rk_ct** out) {
+    return guard([&] {
+        need(ctx, "ctx");
+        need(in, "in");
+        need(out, "out");
+        for (uint32_t i = 0; i < count; i++) same_ctx(ctx, in[i]);
+        set_device(ctx);
+        *out = ct_stack(ctx, in, (int)count);
+    });
+}
+
+rk_status rk_ct_unstack(rk_ctx* ctx, const rk_ct* in, rk_ct** outs) {
+    return guard([&] {
+        need(ctx, "ctx");
+        same_ctx(ctx, in);
+        need(outs, "outs");
+        set_device(ctx);
+        ct_unstack(ctx, in, outs);
+    });
+}
+
+uint32_t rk_ct_count(const rk_ct* ct) { return ct ? (uint32_t)ct->B : 0; }
 
 rk_status rk_rescale_noalloc(rk_ctx* ctx, const uint64_t* d_in, uint64_t* d_out, uint32_t level) {
     return guard([&] {

@@ -191,6 +191,12 @@ H sum_cols(Ev& E, H x, uint32_t kind) {
     return E.mul_mask(x, kind);
 }
 
+// TransC (Alg. 2): X <- X + (X << N(N-1)/2^i), i = 1 .. log N, then MaskR(X, 0)
+H trans_c(Ev& E, H x) {
+    const int N = (int)x->N, k = log2_exact(x->N);
+    for (int i = 1; i <= k; i++) x = E.add(x, E.rot(x, (N * (N - 1)) >> i));
+    return E.mul_mask(x, RK_MASK_ROW0);
+}
 // ReplC (Alg. 11)
 H repl_c(Ev& E, H x) {
     const int k = log2_exact(x->N);
@@ -428,6 +434,89 @@ rk_ct* circuit_sort(rk_ctx* c, const rk_ct* in, uint32_t flags) {
     H M = cheb_ps(E, D, indicator_coeffs(c, in->N));
     H Pm = E.mul(M, E.level_down(rc.second, M->level));
     return sum_r(E, std::move(Pm)).release();
+}
+
+// Stack of handles (copied) from a list of single ciphertexts or views.
+static H stack_of(rk_ctx* c, const std::vector<rk_ct*>& xs) {
+    std::vector<const rk_ct*> p(xs.begin(), xs.end());
+    return H(ct_stack(c, p.data(), (int)p.size()));
+}
+
+// Alg. 7: ranks of a vector split into L blocks (one ciphertext each, same shape).
+// The L blocks run as one stack through ReplR/TransR/ReplC, the L(L+1)/2 block
+// comparisons C_{i,j} (j >= i) as one stack through Cmp; then
+// R_i = TransC(SumC(sum_{j<i} (1 - C_{j,i}))) + SumR(sum_{j>=i} C_{i,j}) + 1/2 (Eq. 3).
+void circuit_rank_blocked(rk_ctx* c, const rk_ct* const* blocks, int L, rk_ct** outs) {
+    RK_REQUIRE(L >= 1, RK_EINVAL, "no blocks");
+    const rk_ct* b0 = blocks[0];
+    for (int i = 0; i < L; i++) {
+        RK_REQUIRE(blocks[i]->B == 1 && blocks[i]->level == b0->level && blocks[i]->N == b0->N &&
+                       blocks[i]->Q == b0->Q && blocks[i]->n_real == b0->N,
+                   RK_EINVAL, "blocks must be single, unpadded ciphertexts of one level and length");
+    }
+    const int need = 3 + 3 * (int)(c->prm.d_g + c->prm.d_f);
+    check_square(c, b0, need, "blocked rank");
+    Ev E{c};
+    H V(ct_stack(c, blocks, L));
+    auto rc = row_col_forms(E, V);   // stacks of L
+    std::vector<std::pair<int, int>> pairs;
+    std::map<std::pair<int, int>, int> pidx;
+    for (int i = 0; i < L; i++)
+        for (int j = i; j < L; j++) {
+            pidx[{i, j}] = (int)pairs.size();
+            pairs.push_back({i, j});
+        }
+    std::vector<H> vr_views, vc_views;
+    std::vector<rk_ct*> vr, vc;
+    for (auto& pr : pairs) {
+        vr_views.emplace_back(ct_view(rc.first.p, pr.first));
+        vc_views.emplace_back(ct_view(rc.second.p, pr.second));
+        vr.push_back(vr_views.back().p);
+        vc.push_back(vc_views.back().p);
+    }
+    H Cst = cmp(E, E.sub(stack_of(c, vr), stack_of(c, vc)), (int)c->prm.d_g, (int)c->prm.d_f);
+    auto Cv = [&](int i, int j) { return H(ct_view(Cst.p, pidx[{i, j}])); };
+    // A_i = sum_{j>=i} C_{i,j}, B_i = sum_{j<i} (1 - C_{j,i}) = i - sum_{j<i} C_{j,i}
+    std::vector<H> A, Bm;
+    for (int i = 0; i < L; i++) {
+        H a = E.copy(Cv(i, i));
+        for (int j = i + 1; j < L; j++) a = E.add(a, Cv(i, j));
+        A.push_back(std::move(a));
+        if (i > 0) {
+            H s = E.copy(Cv(0, i));
+            for (int j = 1; j < i; j++) s = E.add(s, Cv(j, i));
+            H ng = E.fresh(s, s->level);
+            ev_neg(c, s.p, ng.p);
+            Bm.push_back(E.add_const(ng, (double)i));
+        }
+    }
+    std::vector<rk_ct*> ap;
+    for (auto& a : A) ap.push_back(a.p);
+    H S = sum_r(E, stack_of(c, ap));   // stack of L
+    H T;
+    if (L > 1) {
+        std::vector<rk_ct*> bp;
+        for (auto& b : Bm) bp.push_back(b.p);
+        T = trans_c(E, sum_cols(E, stack_of(c, bp), RK_MASK_COL0));   // stack of L-1
+    }
+    std::vector<rk_ct*> res(L, nullptr);
+    try {
+        for (int i = 0; i < L; i++) {
+            H s(ct_view(S.p, i));
+            H R;
+            if (i > 0) {
+                H t(ct_view(T.p, i - 1));
+                R = E.add(E.level_down(s, t->level), t);
+            } else {
+                R = E.level_down(s, s->level - 1);
+            }
+            res[i] = E.add_const(R, 0.5).release();
+        }
+    } catch (...) {
+        for (auto* p : res) ct_free(p);
+        throw;
+    }
+    for (int i = 0; i < L; i++) outs[i] = res[i];
 }
 
 rk_ct* circuit_compare_matrix(rk_ctx* c, const rk_ct* in) {

@@ -5,13 +5,16 @@
 //  * hybrid key switching with digits of `digit_size` limbs; ModUp is the fast
 //    basis conversion of one digit without correction; for a rotation the
 //    automorphism X -> X^g acts on the lifted digits (so that several rotations of
-//    one ciphertext share one ModUp); ModDown converts the P part back and
-//    multiplies by P^-1;
+//    one ciphertext share one ModUp); ModDown converts the P part back with centred
+//    terms (zero-mean error) and multiplies by P^-1;
 //  * rescale lifts the dropped residue centred into (-q/2, q/2];
 //  * a factor (scalar or plaintext) multiplied at level l is encoded at scale
 //    Delta_{l-1} q_l / Delta_l and rounded half away from zero, so that after the
 //    rescale the product sits at the canonical scale Delta_{l-1};
 //  * a constant c is added as round(c Delta_l) to every evaluation of c0.
+//
+// A handle may hold a stack of B ciphertexts ([B][2][L+1][n]); every operation
+// then runs on all of them with the same launches (same constants, same keys).
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -25,10 +28,11 @@ struct Scratch {
     size_t misc_words;
 };
 
+// Regions sized for stacks of up to c->batch_cap ciphertexts at the top level.
 Scratch scratch_layout(rk_ctx* c) {
-    const size_t n = c->n, L1 = c->L + 1, QP = c->L + 1 + c->alpha;
-    const size_t w_coef = L1 * n, w_ext = (size_t)c->beta(c->L) * QP * n, w_u = 2 * QP * n, w_w = 2 * L1 * n,
-                 w_d = 3 * L1 * n, w_v = 2 * L1 * n, w_misc = 4 * QP * n;
+    const size_t n = c->n, L1 = c->L + 1, QP = c->L + 1 + c->alpha, Bc = (size_t)c->batch_cap;
+    const size_t w_coef = Bc * L1 * n, w_ext = Bc * (size_t)c->beta(c->L) * QP * n, w_u = Bc * 2 * QP * n,
+                 w_w = Bc * 2 * L1 * n, w_d = Bc * 3 * L1 * n, w_v = Bc * 2 * L1 * n, w_misc = 4 * QP * n;
     u64* b = c->scratch(w_coef + w_ext + w_u + w_w + w_d + w_v + w_misc);
     Scratch S;
     S.coef = b;
@@ -90,16 +94,30 @@ void upload_i64_sync(rk_ctx* c, int64_t* dst, const int64_t* src, size_t count) 
     RK_CUDA(cudaStreamSynchronize(c->stream));
 }
 
+// copy limbs 0..l of `polys` polynomials between two buffers with poly stride ps
+void copy_polys(rk_ctx* c, u64* dst, const u64* src, int polys, int l) {
+    const size_t pitch = c->poly_stride() * 8, width = (size_t)(l + 1) * c->n * 8;
+    RK_CUDA(cudaMemcpy2DAsync(dst, pitch, src, pitch, width, polys, cudaMemcpyDeviceToDevice, c->stream));
+}
+
 }  // namespace
+
+void ensure_batch(rk_ctx* c, int B) {
+    if (B > c->batch_cap) {
+        c->batch_cap = B;
+        scratch_layout(c);   // grows the allocation (synchronises once)
+    }
+}
 
 // ---------------------------------------------------------------------------
 // Ciphertext handles
 // ---------------------------------------------------------------------------
-rk_ct* ct_alloc(rk_ctx* c, int level) {
+rk_ct* ct_alloc(rk_ctx* c, int level, int B) {
     rk_ct* ct = new rk_ct();
     ct->ctx = c;
     ct->level = level;
-    cudaError_t e = cudaMallocAsync((void**)&ct->data, c->ct_words() * 8, c->stream);
+    ct->B = B;
+    cudaError_t e = cudaMallocAsync((void**)&ct->data, (size_t)B * c->ct_words() * 8, c->stream);
     if (e != cudaSuccess) {
         delete ct;
         throw rk_error(RK_ENOMEM, std::string("ciphertext allocation: ") + cudaGetErrorString(e));
@@ -109,8 +127,17 @@ rk_ct* ct_alloc(rk_ctx* c, int level) {
 
 void ct_free(rk_ct* ct) {
     if (!ct) return;
-    if (ct->data) cudaFreeAsync(ct->data, ct->ctx->stream);
+    if (ct->data && !ct->view) cudaFreeAsync(ct->data, ct->ctx->stream);
     delete ct;
+}
+
+rk_ct* ct_view(const rk_ct* stack, int b) {
+    RK_REQUIRE(b >= 0 && b < stack->B, RK_EINVAL, "view index out of range");
+    rk_ct* v = new rk_ct(*stack);
+    v->data = stack->data + (size_t)b * stack->ctx->ct_words();
+    v->B = 1;
+    v->view = true;
+    return v;
 }
 
 static void copy_meta(rk_ct* out, const rk_ct* a) {
@@ -121,41 +148,60 @@ static void copy_meta(rk_ct* out, const rk_ct* a) {
 }
 
 rk_ct* ct_clone_meta(const rk_ct* src, int level) {
-    rk_ct* o = ct_alloc(src->ctx, level);
+    rk_ct* o = ct_alloc(src->ctx, level, src->B);
     copy_meta(o, src);
     return o;
+}
+rk_ct* ct_stack(rk_ctx* c, const rk_ct* const* in, int count) {
+    RK_REQUIRE(count >= 1, RK_EINVAL, "stack of no ciphertexts");
+    const rk_ct* a = in[0];
+    for (int i = 0; i < count; i++)
+        RK_REQUIRE(in[i]->B == 1 && in[i]->level == a->level && in[i]->N == a->N && in[i]->Q == a->Q &&
+                       in[i]->n_real == a->n_real && in[i]->layout == a->layout,
+                   RK_EINVAL, "stacked ciphertexts must share level and vector shape");
+    rk_ct* o = ct_alloc(c, a->level, count);
+    copy_meta(o, a);
+    for (int i = 0; i < count; i++) copy_polys(c, o->data + (size_t)i * c->ct_words(), in[i]->data, 2, a->level);
+    return o;
+}
+
+void ct_unstack(rk_ctx* c, const rk_ct* in, rk_ct** outs) {
+    for (int i = 0; i < in->B; i++) {
+        rk_ct* o = ct_alloc(c, in->level, 1);
+        copy_meta(o, in);
+        copy_polys(c, o->data, in->data + (size_t)i * c->ct_words(), 2, in->level);
+        outs[i] = o;
+    }
 }
 
 // ---------------------------------------------------------------------------
 // Pointwise operations
 // ---------------------------------------------------------------------------
 void ev_copy(rk_ctx* c, const rk_ct* a, rk_ct* out) {
-    if (out != a) {
-        const size_t bytes = (size_t)(a->level + 1) * c->n * 8;
-        RK_CUDA(cudaMemcpyAsync(out->data, a->data, bytes, cudaMemcpyDeviceToDevice, c->stream));
-        RK_CUDA(cudaMemcpyAsync(out->data + c->poly_stride(), a->data + c->poly_stride(), bytes, cudaMemcpyDeviceToDevice,
-                                c->stream));
-    }
+    RK_REQUIRE(out->B == a->B, RK_EINVAL, "copy: stack size mismatch");
+    if (out != a) copy_polys(c, out->data, a->data, 2 * a->B, a->level);
     out->level = a->level;
     copy_meta(out, a);
 }
 
 void ev_add(rk_ctx* c, const rk_ct* a, const rk_ct* b, rk_ct* out) {
     RK_REQUIRE(a->level == b->level, RK_EINVAL, "add: level mismatch");
-    launch_addsub(c->env, out->data, a->data, b->data, a->level + 1, c->poly_stride(), 0, c->stream);
+    RK_REQUIRE(a->B == b->B && out->B == a->B, RK_EINVAL, "add: stack size mismatch");
+    launch_addsub(c->env, out->data, a->data, b->data, a->level + 1, c->poly_stride(), 0, c->stream, 2 * a->B);
     out->level = a->level;
     copy_meta(out, a);
 }
 
 void ev_sub(rk_ctx* c, const rk_ct* a, const rk_ct* b, rk_ct* out) {
     RK_REQUIRE(a->level == b->level, RK_EINVAL, "sub: level mismatch");
-    launch_addsub(c->env, out->data, a->data, b->data, a->level + 1, c->poly_stride(), 1, c->stream);
+    RK_REQUIRE(a->B == b->B && out->B == a->B, RK_EINVAL, "sub: stack size mismatch");
+    launch_addsub(c->env, out->data, a->data, b->data, a->level + 1, c->poly_stride(), 1, c->stream, 2 * a->B);
     out->level = a->level;
     copy_meta(out, a);
 }
 
 void ev_neg(rk_ctx* c, const rk_ct* a, rk_ct* out) {
-    launch_addsub(c->env, out->data, a->data, a->data, a->level + 1, c->poly_stride(), 2, c->stream);
+    launch_addsub(c->env, out->data, a->data, a->data, a->level + 1, c->poly_stride(), 2, c->stream, 2 * a->B);
     out->level = a->level;
     copy_meta(out, a);
 }
@@ -163,7 +209,7 @@ void ev_neg(rk_ctx* c, const rk_ct* a, rk_ct* out) {
 void ev_add_const(rk_ctx* c, const rk_ct* a, double v, rk_ct* out) {
     const int l = a->level;
     const int64_t K = round_half_away(v * c->scales[l]);
-    launch_add_const(c->env, out->data, a->data, scalar_residues(c, K, l + 1), l + 1, c->poly_stride(), c->stream);
+    launch_add_const(c->env, out->data, a->data, scalar_residues(c, K, l + 1), l + 1, c->poly_stride(), c->stream, 2 * a->B);
     out->level = l;
     copy_meta(out, a);
 }
@@ -171,12 +217,14 @@ void ev_add_const(rk_ctx* c, const rk_ct* a, double v, rk_ct* out) {
 void ev_rescale_inplace(rk_ctx* c, rk_ct* a) {
     const int l = a->level;
     RK_REQUIRE(l >= 1, RK_EDEPTH, "rescale: no level left");
+    ensure_batch(c, a->B);
     Scratch S = scratch_layout(c);
     const size_t ps = c->poly_stride(), n = c->n;
-    launch_ntt_inverse(c->env, ls_one(a->data + (size_t)l * n, ps, 2, l), c->stream);
-    launch_rescale_lift(c->env, a->data + (size_t)l * n, ps, S.v, l, c->stream);
-    launch_ntt_forward(c->env, ls_q(S.v, (size_t)l * n, 2, l), c->stream);
-    launch_rescale_combine(c->env, a->data, ps, S.v, l, c->stream);
+    const int polys = 2 * a->B;
+    launch_ntt_inverse(c->env, ls_one(a->data + (size_t)l * n, ps, polys, l), c->stream);
+    launch_rescale_lift(c->env, a->data + (size_t)l * n, ps, S.v, l, c->stream, polys);
+    launch_ntt_forward(c->env, ls_q(S.v, (size_t)l * n, polys, l), c->stream);
+    launch_rescale_combine(c->env, a->data, ps, S.v, l, c->stream, polys);
     a->level = l - 1;
     c->n_rescale++;
 }
@@ -189,7 +237,7 @@ void ev_mul_scalar(rk_ctx* c, const rk_ct* a, double v, rk_ct* out) {
     const int l = a->level;
     RK_REQUIRE(l >= 1, RK_EDEPTH, "mul_scalar: no level left");
     const int64_t K = round_half_away(v * factor_scale(c, l));
-    launch_mul_scalar(c->env, out->data, a->data, scalar_residues(c, K, l + 1), l + 1, c->poly_stride(), c->stream);
+    launch_mul_scalar(c->env, out->data, a->data, scalar_residues(c, K, l + 1), l + 1, c->poly_stride(), c->stream, 2 * a->B);
     out->level = l;
     copy_meta(out, a);
     ev_rescale_inplace(c, out);
@@ -205,10 +253,7 @@ void ev_level_down(rk_ctx* c, const rk_ct* a, int target, rk_ct* out) {
     while (out->level > target) ev_mul_scalar(c, out, 1.0, out);
 }
 
-static const u64* plain_get(rk_ctx* c, uint32_t kind, uint32_t N, uint32_t Q, uint32_t n_real, int l) {
-    auto key = std::make_tuple(kind, N, Q, n_real, l);
-    auto it = c->plain_cache.find(key);
-    if (it != c->plain_cache.end()) return it->second;
+static const std::vector<double>& encoding_of(rk_ctx* c, uint32_t kind, uint32_t N, uint32_t Q, uint32_t n_real) {
     auto ekey = std::make_tuple(kind, N, Q, n_real);
     if (!c->encodings.count(ekey)) {
         std::vector<double> slots;
@@ -217,8 +262,11 @@ static const u64* plain_get(rk_ctx* c, uint32_t kind, uint32_t N, uint32_t Q, ui
         encode_unscaled(c->log_n, slots.data(), slots.size(), u);
         c->encodings[ekey] = u;
     }
-    const std::vector<double>& u = c->encodings[ekey];
-    const double s = factor_scale(c, l);
+    return c->encodings[ekey];
+}
+
+// Residues of round(s u) over limbs 0..l in the evaluation domain (Montgomery form if mont).
+static u64* plain_make(rk_ctx* c, const std::vector<double>& u, double s, int l, bool mont) {
     std::vector<int64_t> m(c->n);
     for (int k = 0; k < c->n; k++) m[k] = round_half_away(s * u[k]);
     Scratch S = scratch_layout(c);
@@ -228,20 +276,18 @@ static const u64* plain_get(rk_ctx* c, uint32_t kind, uint32_t N, uint32_t Q, ui
     upload_i64_sync(c, tmp, m.data(), c->n);
     launch_reduce_signed(c->env, tmp, ls_q(buf, 0, 1, l + 1), c->stream);
     launch_ntt_forward(c->env, ls_q(buf, 0, 1, l + 1), c->stream);
-    launch_to_mont(c->env, ls_q(buf, 0, 1, l + 1), c->stream);
+    if (mont) launch_to_mont(c->env, ls_q(buf, 0, 1, l + 1), c->stream);
     RK_CUDA(cudaStreamSynchronize(c->stream));
-    c->plain_cache[key] = buf;
     return buf;
 }
 
-void ev_mul_plain(rk_ctx* c, const rk_ct* a, uint32_t kind, uint32_t N, uint32_t Q, uint32_t n_real, rk_ct* out) {
-    const int l = a->level;
-    RK_REQUIRE(l >= 1, RK_EDEPTH, "mul_plain: no level left");
-    const u64* pt = plain_get(c, kind, N, Q, n_real, l);
-    launch_mul_plain(c->env, out->data, a->data, pt, l + 1, c->poly_stride(), c->stream);
-    out->level = l;
-    copy_meta(out, a);
-    ev_rescale_inplace(c, out);
+static const u64* plain_get(rk_ctx* c, uint32_t kind, uint32_t N, uint32_t Q, uint32_t n_real, int l) {
+    auto key = std::make_tuple(kind, N, Q, n_real, l);
+    auto it = c->plain_cache.find(key);
+    if (it != c->plain_cache.end()) return it->second;
+    u64* buf = plain_make(c, encoding_of(c, kind, N, Q, n_real), factor_scale(c, l), l, true);
+    c->plain_cache[key] = buf;
+    return buf;
 }
 
 // Mask plaintext encoded at the canonical scale Delta_l (normal form), for addition.
@@ -249,38 +295,29 @@ static const u64* plain_add_get(rk_ctx* c, uint32_t kind, uint32_t N, uint32_t Q
     auto key = std::make_tuple(kind, N, Q, n_real, l);
     auto it = c->plain_add_cache.find(key);
     if (it != c->plain_add_cache.end()) return it->second;
-    auto ekey = std::make_tuple(kind, N, Q, n_real);
-    if (!c->encodings.count(ekey)) {
-        std::vector<double> slots;
-        mask_slot_values(kind, N, Q, n_real, (size_t)c->n / 2, slots);
-        std::vector<double> u;
-        encode_unscaled(c->log_n, slots.data(), slots.size(), u);
-        c->encodings[ekey] = u;
-    }
-    const std::vector<double>& u = c->encodings[ekey];
-    std::vector<int64_t> m(c->n);
-    for (int k = 0; k < c->n; k++) m[k] = round_half_away(c->scales[l] * u[k]);
-    Scratch S = scratch_layout(c);
-    u64* buf = nullptr;
-    RK_CUDA(cudaMalloc((void**)&buf, (size_t)(l + 1) * c->n * 8));
-    int64_t* tmp = (int64_t*)S.misc;
-    upload_i64_sync(c, tmp, m.data(), c->n);
-    launch_reduce_signed(c->env, tmp, ls_q(buf, 0, 1, l + 1), c->stream);
-    launch_ntt_forward(c->env, ls_q(buf, 0, 1, l + 1), c->stream);
-    RK_CUDA(cudaStreamSynchronize(c->stream));
+    u64* buf = plain_make(c, encoding_of(c, kind, N, Q, n_real), c->scales[l], l, false);
     c->plain_add_cache[key] = buf;
     return buf;
+}
+
+void ev_mul_plain(rk_ctx* c, const rk_ct* a, uint32_t kind, uint32_t N, uint32_t Q, uint32_t n_real, rk_ct* out) {
+    const int l = a->level;
+    RK_REQUIRE(l >= 1, RK_EDEPTH, "mul_plain: no level left");
+    const u64* pt = plain_get(c, kind, N, Q, n_real, l);
+    launch_mul_plain(c->env, out->data, a->data, pt, l + 1, c->poly_stride(), c->stream, 2 * a->B);
+    out->level = l;
+    copy_meta(out, a);
+    ev_rescale_inplace(c, out);
 }
 
 void ev_add_plain(rk_ctx* c, const rk_ct* a, uint32_t kind, uint32_t N, uint32_t Q, uint32_t n_real, rk_ct* out) {
     const int l = a->level;
     const u64* pt = plain_add_get(c, kind, N, Q, n_real, l);
-    const size_t pl = (size_t)(l + 1) * c->n;
-    // c0 + pt (poly 1 copied)
-    launch_addsub(c->env, out->data, a->data, pt, l + 1, 0, 0, c->stream, 1);   // c0 + pt
+    const size_t cw = c->ct_words();
+    for (int b = 0; b < a->B; b++)   // c0 + pt for every stacked ciphertext
+        launch_addsub(c->env, out->data + b * cw, a->data + b * cw, pt, l + 1, 0, 0, c->stream, 1);
     if (out != a)
-        RK_CUDA(cudaMemcpyAsync(out->data + c->poly_stride(), a->data + c->poly_stride(), pl * 8, cudaMemcpyDeviceToDevice,
-                                c->stream));
+        for (int b = 0; b < a->B; b++) copy_polys(c, out->data + b * cw + c->poly_stride(), a->data + b * cw + c->poly_stride(), 1, l);
     out->level = l;
     copy_meta(out, a);
 }
@@ -289,7 +326,7 @@ void ev_lincomb(rk_ctx* c, const std::vector<const rk_ct*>& xs, const std::vecto
     RK_REQUIRE(!xs.empty() && xs.size() == cs.size(), RK_EINVAL, "lincomb: bad term lists");
     const int l = xs[0]->level;
     RK_REQUIRE(l >= 1, RK_EDEPTH, "lincomb: no level left");
-    for (auto* x : xs) RK_REQUIRE(x->level == l, RK_EINVAL, "lincomb: level mismatch");
+    for (auto* x : xs) RK_REQUIRE(x->level == l && x->B == out->B, RK_EINVAL, "lincomb: level or stack mismatch");
     for (auto* x : xs) RK_REQUIRE(x != out, RK_EINVAL, "lincomb: output aliases an input");
     const double s = factor_scale(c, l);
     LincombArg arg;
@@ -306,7 +343,7 @@ void ev_lincomb(rk_ctx* c, const std::vector<const rk_ct*>& xs, const std::vecto
                 arg.KR[i][t] = h_mulmod((u64)r, c->h_pc[t].r_mod, (u64)q);
             }
         }
-        launch_lincomb(c->env, out->data, arg, terms, done > 0, l + 1, c->poly_stride(), c->stream);
+        launch_lincomb(c->env, out->data, arg, terms, done > 0, l + 1, c->poly_stride(), c->stream, 2 * out->B);
         done += terms;
     }
     out->level = l;
@@ -317,30 +354,36 @@ void ev_lincomb(rk_ctx* c, const std::vector<const rk_ct*>& xs, const std::vecto
 // ---------------------------------------------------------------------------
 // Key switching
 // ---------------------------------------------------------------------------
-// ModUp of d (evaluation domain, limbs 0..l) into the ext scratch (evaluation domain).
-static void ks_modup(rk_ctx* c, const u64* d_eval, int l) {
+// ModUp of B polynomials d_b = d_eval + b * d_stride (evaluation domain, limbs 0..l)
+// into the ext scratch [B][beta][l+1+alpha][n] (evaluation domain).
+static void ks_modup(rk_ctx* c, const u64* d_eval, size_t d_stride, int l, int B) {
+    ensure_batch(c, B);
     Scratch S = scratch_layout(c);
     const size_t n = c->n;
     const int QP = l + 1 + c->alpha;
-    RK_CUDA(cudaMemcpyAsync(S.coef, d_eval, (size_t)(l + 1) * n * 8, cudaMemcpyDeviceToDevice, c->stream));
-    launch_ntt_inverse(c->env, ls_q(S.coef, 0, 1, l + 1), c->stream);
-    launch_modup(c->env, S.coef, S.ext, (size_t)QP * n, l, c->beta(l), c->stream);
-    launch_ntt_forward(c->env, LimbSet{S.ext, (size_t)QP * n, c->beta(l), QP, l + 1, 0, c->L + 1}, c->stream);
+    const size_t width = (size_t)(l + 1) * n * 8;
+    RK_CUDA(cudaMemcpy2DAsync(S.coef, width, d_eval, d_stride * 8, width, B, cudaMemcpyDeviceToDevice, c->stream));
+    launch_ntt_inverse(c->env, ls_q(S.coef, (size_t)(l + 1) * n, B, l + 1), c->stream);
+    launch_modup(c->env, S.coef, d_eval, d_stride, S.ext, (size_t)QP * n, l, c->beta(l), c->stream, B);
+    LimbSet ext{S.ext, (size_t)QP * n, B * c->beta(l), QP, l + 1, 0, c->L + 1};
+    ext.skip_ds = c->dsize;   // each digit's own limbs are already in the evaluation domain
+    ext.skip_beta = c->beta(l);
+    launch_ntt_forward(c->env, ext, c->stream);
 }
 
 // Inner product with `key` (automorphism `galois` on the lifted digits), ModDown, and
-// out = base + result (automorphism galois0 on base0).
-static void ks_apply(rk_ctx* c, const u64* key, int l, u64 galois, const u64* base0, u64 galois0, const u64* base1, u64* out,
-                     size_t out_ps) {
+// out_b = base_b + result_b (automorphism galois0 on base0), for B stacked inputs.
+static void ks_apply(rk_ctx* c, const u64* key, int l, u64 galois, const u64* base0, u64 galois0, const u64* base1,
+                     size_t bstride, u64* out, size_t out_ps, int B) {
     Scratch S = scratch_layout(c);
     const size_t n = c->n;
     const int QP = l + 1 + c->alpha;
-    launch_ks_inner(c->env, S.ext, (size_t)QP * n, key, S.u, l, c->beta(l), galois, c->stream);
-    launch_ntt_inverse(c->env, LimbSet{S.u + (size_t)(l + 1) * n, (size_t)QP * n, 2, c->alpha, 0, 0, c->L + 1}, c->stream);
-    launch_moddown_conv(c->env, S.u, S.w, l, c->stream);
-    launch_ntt_forward(c->env, ls_q(S.w, (size_t)(l + 1) * n, 2, l + 1), c->stream);
-    launch_ks_combine(c->env, out, out_ps, base0, galois0, base1, S.u, S.w, l, c->stream);
-    c->n_ks++;
+    launch_ks_inner(c->env, S.ext, (size_t)QP * n, key, S.u, l, c->beta(l), galois, c->stream, B);
+    launch_ntt_inverse(c->env, LimbSet{S.u + (size_t)(l + 1) * n, (size_t)QP * n, 2 * B, c->alpha, 0, 0, c->L + 1}, c->stream);
+    launch_moddown_conv(c->env, S.u, S.w, l, c->stream, 2 * B);
+    launch_ntt_forward(c->env, ls_q(S.w, (size_t)(l + 1) * n, 2 * B, l + 1), c->stream);
+    launch_ks_combine(c->env, out, out_ps, base0, galois0, base1, bstride, S.u, S.w, l, c->stream, B);
+    c->n_ks += (uint64_t)B;
 }
 
 u64 galois_left(const rk_ctx* c, int r) {
@@ -355,39 +398,42 @@ void ev_rotate_many(rk_ctx* c, const rk_ct* a, const int* r, int k, rk_ct** outs
     bool need_ks = false;
     for (int i = 0; i < k; i++) {
         RK_REQUIRE(outs[i] != a, RK_EINVAL, "rotate: output aliases input");
+        RK_REQUIRE(outs[i]->B == a->B, RK_EINVAL, "rotate: stack size mismatch");
         u64 g = galois_left(c, r[i]);
         if (g != 1) {
             RK_REQUIRE(c->gal.count(g), RK_ENOKEY, "rotation key missing for r = " + std::to_string(r[i]));
             need_ks = true;
         }
     }
-    if (need_ks) ks_modup(c, a->data + ps, l);
+    if (need_ks) ks_modup(c, a->data + ps, 2 * ps, l, a->B);
     for (int i = 0; i < k; i++) {
         u64 g = galois_left(c, r[i]);
         if (g == 1) {
             ev_copy(c, a, outs[i]);
             continue;
         }
-        ks_apply(c, c->gal[g].data, l, g, a->data, g, nullptr, outs[i]->data, ps);
+        ks_apply(c, c->gal[g].data, l, g, a->data, g, nullptr, 2 * ps, outs[i]->data, ps, a->B);
         outs[i]->level = l;
         copy_meta(outs[i], a);
-        c->n_rot++;
+        c->n_rot += (uint64_t)a->B;
     }
 }
 
 void ev_mul(rk_ctx* c, const rk_ct* a, const rk_ct* b, rk_ct* out) {
     RK_REQUIRE(a->level == b->level, RK_EINVAL, "mul: level mismatch");
-    const int l = a->level;
+    RK_REQUIRE(a->B == b->B && out->B == a->B, RK_EINVAL, "mul: stack size mismatch");
+    const int l = a->level, B = a->B;
     RK_REQUIRE(l >= 1, RK_EDEPTH, "mul: no level left");
     RK_REQUIRE(c->rlk.data, RK_ENOKEY, "relinearisation key missing");
+    ensure_batch(c, B);
     Scratch S = scratch_layout(c);
     const size_t pl = (size_t)(l + 1) * c->n;
-    launch_tensor(c->env, S.d, a->data, b->data, l + 1, c->poly_stride(), c->stream);
-    ks_modup(c, S.d + 2 * pl, l);
-    ks_apply(c, c->rlk.data, l, 0, S.d, 0, S.d + pl, out->data, c->poly_stride());
+    launch_tensor(c->env, S.d, a->data, b->data, l + 1, c->poly_stride(), c->stream, B);
+    ks_modup(c, S.d + 2 * pl, 3 * pl, l, B);
+    ks_apply(c, c->rlk.data, l, 0, S.d, 0, S.d + pl, 3 * pl, out->data, c->poly_stride(), B);
     out->level = l;
     copy_meta(out, a);
-    c->n_mul++;
+    c->n_mul += (uint64_t)B;
     ev_rescale_inplace(c, out);
 }
 
@@ -567,6 +613,7 @@ rk_ct* encrypt_values(rk_ctx* c, const double* v, uint32_t count, uint32_t N, ui
 
 void decrypt_slots(rk_ctx* c, const rk_ct* ct, std::vector<double>& slots) {
     RK_REQUIRE(c->d_sk, RK_EINVAL, "no secret key");
+    RK_REQUIRE(ct->B == 1, RK_EINVAL, "decrypt a stacked handle after rk_ct_unstack");
     const int l = ct->level;
     const size_t n = c->n;
     Scratch S = scratch_layout(c);
@@ -613,6 +660,7 @@ rk_ct* ct_import(rk_ctx* c, const uint64_t* coeffs, int level) {
 }
 
 void ct_export(rk_ctx* c, const rk_ct* ct, uint64_t* coeffs) {
+    RK_REQUIRE(ct->B == 1, RK_EINVAL, "export a stacked handle after rk_ct_unstack");
     const int l = ct->level;
     const size_t n = c->n, pl = (size_t)(l + 1) * n;
     Scratch S = scratch_layout(c);

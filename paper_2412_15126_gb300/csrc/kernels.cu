@@ -51,13 +51,14 @@ __global__ void k_add_const(u64* out, const u64* a, ScalarArg K, int n, size_t p
     const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y, c = blockIdx.z;
     const size_t off = c * ps + (size_t)t * n + k;
     u64 x = a[off];
-    if (c == 0) x = add_mod(x, K.w[t], pc[t].q);
+    if ((c & 1) == 0) x = add_mod(x, K.w[t], pc[t].q);
     out[off] = x;
 }
 
-void launch_add_const(const KernelEnv& env, u64* out, const u64* a, const ScalarArg& K, int limbs, size_t ps, cudaStream_t st) {
-    ProfScope pf(env, KK_POINTWISE, st, 1, 4.0 * limbs * 8.0 * env.n, 0.0);
-    dim3 g(env.n / TPB, limbs, 2);
+void launch_add_const(const KernelEnv& env, u64* out, const u64* a, const ScalarArg& K, int limbs, size_t ps, cudaStream_t st,
+                      int polys) {
+    ProfScope pf(env, KK_POINTWISE, st, 1, 2.0 * polys * limbs * 8.0 * env.n, 0.0);
+    dim3 g(env.n / TPB, limbs, polys);
     k_add_const<<<g, TPB, 0, st>>>(out, a, K, env.n, ps, env.pc);
 }
 
@@ -68,9 +69,10 @@ __global__ void k_mul_scalar(u64* out, const u64* a, ScalarArg K, int n, size_t 
     out[off] = shoup_mul(a[off], K.w[t], K.wsh[t], pc[t].q);
 }
 
-void launch_mul_scalar(const KernelEnv& env, u64* out, const u64* a, const ScalarArg& K, int limbs, size_t ps, cudaStream_t st) {
-    ProfScope pf(env, KK_POINTWISE, st, 1, 4.0 * limbs * 8.0 * env.n, 2.0 * limbs * env.n);
-    dim3 g(env.n / TPB, limbs, 2);
+void launch_mul_scalar(const KernelEnv& env, u64* out, const u64* a, const ScalarArg& K, int limbs, size_t ps, cudaStream_t st,
+                       int polys) {
+    ProfScope pf(env, KK_POINTWISE, st, 1, 2.0 * polys * limbs * 8.0 * env.n, 1.0 * polys * limbs * env.n);
+    dim3 g(env.n / TPB, limbs, polys);
     k_mul_scalar<<<g, TPB, 0, st>>>(out, a, K, env.n, ps, env.pc);
 }
 
@@ -82,9 +84,10 @@ __global__ void k_mul_plain(u64* out, const u64* a, const u64* pt, int n, size_t
     out[off] = mont_mul(a[off], pt[(size_t)t * n + k], P.q, P.qinv);
 }
 
-void launch_mul_plain(const KernelEnv& env, u64* out, const u64* a, const u64* pt, int limbs, size_t ps, cudaStream_t st) {
-    ProfScope pf(env, KK_POINTWISE, st, 1, 5.0 * limbs * 8.0 * env.n, 2.0 * limbs * env.n);
-    dim3 g(env.n / TPB, limbs, 2);
+void launch_mul_plain(const KernelEnv& env, u64* out, const u64* a, const u64* pt, int limbs, size_t ps, cudaStream_t st,
+                      int polys) {
+    ProfScope pf(env, KK_POINTWISE, st, 1, (2.0 * polys + 1.0) * limbs * 8.0 * env.n, 1.0 * polys * limbs * env.n);
+    dim3 g(env.n / TPB, limbs, polys);
     k_mul_plain<<<g, TPB, 0, st>>>(out, a, pt, env.n, ps, env.pc);
 }
 
@@ -101,19 +104,23 @@ __global__ void k_lincomb(u64* out, LincombArg a, int terms, int accumulate, int
 }
 
 void launch_lincomb(const KernelEnv& env, u64* out, const LincombArg& a, int terms, bool accumulate, int limbs, size_t ps,
-                    cudaStream_t st) {
-    ProfScope pf(env, KK_POINTWISE, st, 1, (2.0 * terms + 2.0) * limbs * 8.0 * env.n, 2.0 * terms * limbs * env.n);
-    dim3 g(env.n / TPB, limbs, 2);
+                    cudaStream_t st, int polys) {
+    ProfScope pf(env, KK_POINTWISE, st, 1, (terms + 1.0) * polys * limbs * 8.0 * env.n, 1.0 * terms * polys * limbs * env.n);
+    dim3 g(env.n / TPB, limbs, polys);
     k_lincomb<<<g, TPB, 0, st>>>(out, a, terms, accumulate ? 1 : 0, env.n, ps, env.pc);
 }
 
 // d = [d0 | d1 | d2] each [limbs][n]: d0 = x0 y0, d1 = x0 y1 + x1 y0, d2 = x1 y1
+// one ciphertext pair per blockIdx.z (stacked layout [B][2][L+1][n]); d is [B][3][limbs][n]
 __global__ void k_tensor(u64* d, const u64* x, const u64* y, int limbs, int n, size_t ps, const PrimeConst* __restrict__ pc) {
-    const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y;
+    const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y, b = blockIdx.z;
     const PrimeConst P = pc[t];
+    const size_t pl = (size_t)limbs * n;
+    x += (size_t)b * 2 * ps;
+    y += (size_t)b * 2 * ps;
+    d += (size_t)b * 3 * pl;
     const size_t off = (size_t)t * n + k;
     const u64 x0 = x[off], x1 = x[ps + off], y0 = y[off], y1 = y[ps + off];
-    const size_t pl = (size_t)limbs * n;
     u64 r0 = mont_mul(x0, y0, P.q, P.qinv);
     Acc128 a1;
     a1.mac(x0, y1);
@@ -125,9 +132,9 @@ __global__ void k_tensor(u64* d, const u64* x, const u64* y, int limbs, int n, s
     d[2 * pl + off] = shoup_mul(r2, P.r_mod, P.r_shoup, P.q);
 }
 
-void launch_tensor(const KernelEnv& env, u64* d, const u64* x, const u64* y, int limbs, size_t ps, cudaStream_t st) {
-    ProfScope pf(env, KK_TENSOR, st, 1, 7.0 * limbs * 8.0 * env.n, 4.0 * limbs * env.n);
-    dim3 g(env.n / TPB, limbs);
+void launch_tensor(const KernelEnv& env, u64* d, const u64* x, const u64* y, int limbs, size_t ps, cudaStream_t st, int B) {
+    ProfScope pf(env, KK_TENSOR, st, 1, 7.0 * B * limbs * 8.0 * env.n, 4.0 * B * limbs * env.n);
+    dim3 g(env.n / TPB, limbs, B);
     k_tensor<<<g, TPB, 0, st>>>(d, x, y, limbs, env.n, ps, env.pc);
 }
 
@@ -135,8 +142,11 @@ void launch_tensor(const KernelEnv& env, u64* d, const u64* x, const u64* y, int
 // Basis conversion (coefficient domain).
 // ===========================================================================
 // ModUp of every digit: ext[j][t][k], t over Q_l u P (QP limb order).
-__global__ void __launch_bounds__(TPB) k_modup(const u64* __restrict__ x, u64* __restrict__ ext, size_t ext_stride, int level,
-                                               int L, int alpha, ConvTables cv, int n, const PrimeConst* __restrict__ pc) {
+// The digit's own limbs are copied from the evaluation-domain input x_eval (the
+// conversion reproduces them exactly), so the following NTT can skip them.
+__global__ void __launch_bounds__(TPB) k_modup(const u64* __restrict__ x, const u64* __restrict__ x_eval, u64* __restrict__ ext,
+                                               size_t ext_stride, int level, int L, int alpha, ConvTables cv, int n,
+                                               const PrimeConst* __restrict__ pc) {
     const int k = blockIdx.x * TPB + threadIdx.x, j = blockIdx.y;
     const int DS = cv.dsize;
     const int lo = j * DS, hi = min(lo + DS, level + 1), ns = hi - lo;
@@ -153,6 +163,10 @@ __global__ void __launch_bounds__(TPB) k_modup(const u64* __restrict__ x, u64* _
     const int limbs = level + 1 + alpha;
     u64* out = ext + (size_t)j * ext_stride + k;
     for (int t = 0; t < limbs; t++) {
+        if (t >= lo && t < hi) {
+            out[(size_t)t * n] = x_eval[(size_t)t * n + k];
+            continue;
+        }
         const int pid = t <= level ? t : L + 1 + (t - level - 1);
         const PrimeConst P = pc[pid];
         Acc128 acc;
@@ -163,10 +177,16 @@ __global__ void __launch_bounds__(TPB) k_modup(const u64* __restrict__ x, u64* _
     }
 }
 
-void launch_modup(const KernelEnv& env, const u64* x, u64* ext, size_t ext_stride, int level, int beta, cudaStream_t st) {
-    ProfScope pf(env, KK_MODUP, st, 1, ((double)(level + 1) + (double)beta * (level + 1 + env.alpha)) * 8.0 * env.n, (double)(level + 1 + env.alpha) * (level + 1) * env.n);
+// B stacked inputs: x is [B][l+1][n] (coefficient domain), x_eval_b = x_eval + b * eval_stride
+// (evaluation domain), ext is [B][beta][l+1+alpha][n] (ext_stride per digit)
+void launch_modup(const KernelEnv& env, const u64* x, const u64* x_eval, size_t eval_stride, u64* ext, size_t ext_stride,
+                  int level, int beta, cudaStream_t st, int B) {
+    ProfScope pf(env, KK_MODUP, st, B, B * (2.0 * (level + 1) + (double)beta * (level + 1 + env.alpha)) * 8.0 * env.n,
+                 (double)B * (level + 1 + env.alpha) * (level + 1) * env.n);
     dim3 g(env.n / TPB, beta);
-    k_modup<<<g, TPB, 0, st>>>(x, ext, ext_stride, level, env.L, env.alpha, env.conv, env.n, env.pc);
+    for (int b = 0; b < B; b++)
+        k_modup<<<g, TPB, 0, st>>>(x + (size_t)b * (level + 1) * env.n, x_eval + (size_t)b * eval_stride,
+                                   ext + (size_t)b * beta * ext_stride, ext_stride, level, env.L, env.alpha, env.conv, env.n, env.pc);
 }
 
 // ModDown conversion of the P part of u ([2][l+1+alpha][n], P limbs already in the
@@ -203,9 +223,9 @@ __global__ void __launch_bounds__(TPB) k_moddown_conv(const u64* __restrict__ u,
     }
 }
 
-void launch_moddown_conv(const KernelEnv& env, const u64* u, u64* w, int level, cudaStream_t st) {
-    ProfScope pf(env, KK_MODDOWN, st, 1, (2.0 * env.alpha + 2.0 * (level + 1)) * 8.0 * env.n, 2.0 * (level + 1) * env.alpha * env.n);
-    dim3 g(env.n / TPB, 2);
+void launch_moddown_conv(const KernelEnv& env, const u64* u, u64* w, int level, cudaStream_t st, int polys) {
+    ProfScope pf(env, KK_MODDOWN, st, 1, polys * (1.0 * env.alpha + (level + 1)) * 8.0 * env.n, 1.0 * polys * (level + 1) * env.alpha * env.n);
+    dim3 g(env.n / TPB, polys);
     k_moddown_conv<<<g, TPB, 0, st>>>(u, w, level, env.L, env.alpha, env.conv, env.n, env.pc);
 }
 
@@ -213,58 +233,93 @@ void launch_moddown_conv(const KernelEnv& env, const u64* u, u64* w, int level, 
 // Key-switching inner product (evaluation domain), automorphism fused:
 //   u_c[t][k] = sum_j ext[j][t][src(k)] * key[j][c][prime(t)][k]   (key times R)
 // ===========================================================================
+// Up to CH stacked ciphertexts per thread: each key word is read once per chunk.
+// CH is the smallest of 1, 2, 4, 8 that covers the stack (chunks of 8 beyond), so a
+// single ciphertext keeps two accumulators and the digit loop stays unrolled.
+template <int CH>
 __global__ void __launch_bounds__(TPB) k_ks_inner(const u64* __restrict__ ext, size_t ext_stride, const u64* __restrict__ key,
                                                   u64* __restrict__ u, int level, int L, int alpha, int beta, u64 galois,
-                                                  int logn, const PrimeConst* __restrict__ pc) {
+                                                  int logn, int B, const PrimeConst* __restrict__ pc) {
     const int n = 1 << logn;
     const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y;
+    const int b0 = blockIdx.z * CH;
+    const int nb = min(CH, B - b0);
     const int pid = t <= level ? t : L + 1 + (t - level - 1);
     const PrimeConst P = pc[pid];
     const int src = galois ? galois_src(k, galois, logn) : k;
     const size_t KL = (size_t)(L + 1 + alpha) * n;
-    Acc128 a0, a1;
+    const size_t estride = (size_t)beta * ext_stride;   // between stacked ciphertexts
+    Acc128 a0[CH], a1[CH];
+    const u64* kj = key + (size_t)pid * n + k;
+    const u64* ej = ext + (size_t)b0 * estride + (size_t)t * n + src;
+#pragma unroll 4
     for (int j = 0; j < beta; j++) {
-        const u64 e = ext[(size_t)j * ext_stride + (size_t)t * n + src];
-        const u64* kj = key + (size_t)j * 2 * KL + (size_t)pid * n + k;
-        a0.mac(e, kj[0]);
-        a1.mac(e, kj[KL]);
+        const u64 kb = __ldg(kj), ka = __ldg(kj + KL);
+#pragma unroll
+        for (int b = 0; b < CH; b++) {
+            if (CH == 1 || b < nb) {
+                const u64 e = ej[(size_t)b * estride];
+                a0[b].mac(e, kb);
+                a1[b].mac(e, ka);
+            }
+        }
+        kj += 2 * KL;
+        ej += ext_stride;
     }
     const int ul = level + 1 + alpha;
-    u[(size_t)t * n + k] = a0.redc(P.q, P.qinv);
-    u[(size_t)ul * n + (size_t)t * n + k] = a1.redc(P.q, P.qinv);
+#pragma unroll
+    for (int b = 0; b < CH; b++) {
+        if (CH == 1 || b < nb) {
+            u64* ub = u + (size_t)(b0 + b) * 2 * ul * n;
+            ub[(size_t)t * n + k] = a0[b].redc(P.q, P.qinv);
+            ub[(size_t)ul * n + (size_t)t * n + k] = a1[b].redc(P.q, P.qinv);
+        }
+    }
 }
 
 void launch_ks_inner(const KernelEnv& env, const u64* ext, size_t ext_stride, const u64* key, u64* u, int level, int beta,
-                     u64 galois, cudaStream_t st) {
-    ProfScope pf(env, KK_KS_INNER, st, 1, (3.0 * beta + 2.0) * (level + 1 + env.alpha) * 8.0 * env.n, 2.0 * beta * (level + 1 + env.alpha) * env.n);
-    dim3 g(env.n / TPB, level + 1 + env.alpha);
-    k_ks_inner<<<g, TPB, 0, st>>>(ext, ext_stride, key, u, level, env.L, env.alpha, beta, galois, env.logn, env.pc);
+                     u64 galois, cudaStream_t st, int B) {
+    // algorithmic bytes: B lifted inputs read, the key read once per chunk, B outputs written
+    const double QP = level + 1 + env.alpha;
+    const int ch = B <= 1 ? 1 : B <= 2 ? 2 : B <= 4 ? 4 : 8;
+    const int chunks = (B + ch - 1) / ch;
+    ProfScope pf(env, KK_KS_INNER, st, 1, ((double)B * beta + 2.0 * beta * chunks + 2.0 * B) * QP * 8.0 * env.n,
+                 2.0 * B * beta * QP * env.n);
+    dim3 g(env.n / TPB, level + 1 + env.alpha, chunks);
+    switch (ch) {
+        case 1: k_ks_inner<1><<<g, TPB, 0, st>>>(ext, ext_stride, key, u, level, env.L, env.alpha, beta, galois, env.logn, B, env.pc); break;
+        case 2: k_ks_inner<2><<<g, TPB, 0, st>>>(ext, ext_stride, key, u, level, env.L, env.alpha, beta, galois, env.logn, B, env.pc); break;
+        case 4: k_ks_inner<4><<<g, TPB, 0, st>>>(ext, ext_stride, key, u, level, env.L, env.alpha, beta, galois, env.logn, B, env.pc); break;
+        default: k_ks_inner<8><<<g, TPB, 0, st>>>(ext, ext_stride, key, u, level, env.L, env.alpha, beta, galois, env.logn, B, env.pc); break;
+    }
 }
 
 // out[c][t] = base_c[t] (automorphism applied to base0 when galois0 != 0) + (u[c][t] - w[c][t]) * P^-1;
 // base_c points at limb 0 of one polynomial, or is null.
-__global__ void k_ks_combine(u64* out, size_t ps, const u64* base0, u64 galois0, const u64* base1,
+// z = 2b + p over B stacked ciphertexts; base_p of ciphertext b at base_p + b * bstride
+__global__ void k_ks_combine(u64* out, size_t ps, const u64* base0, u64 galois0, const u64* base1, size_t bstride,
                              const u64* __restrict__ u, const u64* __restrict__ w, int level, int alpha, ConvTables cv,
                              int logn, const PrimeConst* __restrict__ pc) {
     const int n = 1 << logn;
     const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y, c = blockIdx.z;
+    const int b = c >> 1, p = c & 1;
     const u64 q = pc[t].q;
     const int ul = level + 1 + alpha;
     u64 v = sub_mod(u[(size_t)c * ul * n + (size_t)t * n + k], w[(size_t)c * (level + 1) * n + (size_t)t * n + k], q);
     v = shoup_mul(v, cv.pinv[2 * t], cv.pinv[2 * t + 1], q);
-    const u64* base = c == 0 ? base0 : base1;
+    const u64* base = p == 0 ? base0 : base1;
     if (base) {
-        const int src = (c == 0 && galois0) ? galois_src(k, galois0, logn) : k;
-        v = add_mod(v, base[(size_t)t * n + src], q);
+        const int src = (p == 0 && galois0) ? galois_src(k, galois0, logn) : k;
+        v = add_mod(v, base[(size_t)b * bstride + (size_t)t * n + src], q);
     }
     out[(size_t)c * ps + (size_t)t * n + k] = v;
 }
 
-void launch_ks_combine(const KernelEnv& env, u64* out, size_t ps, const u64* base0, u64 galois0, const u64* base1,
-                       const u64* u, const u64* w, int level, cudaStream_t st) {
-    ProfScope pf(env, KK_KS_COMBINE, st, 1, 7.0 * (level + 1) * 8.0 * env.n, 2.0 * (level + 1) * env.n);
-    dim3 g(env.n / TPB, level + 1, 2);
-    k_ks_combine<<<g, TPB, 0, st>>>(out, ps, base0, galois0, base1, u, w, level, env.alpha, env.conv, env.logn, env.pc);
+void launch_ks_combine(const KernelEnv& env, u64* out, size_t ps, const u64* base0, u64 galois0, const u64* base1, size_t bstride,
+                       const u64* u, const u64* w, int level, cudaStream_t st, int B) {
+    ProfScope pf(env, KK_KS_COMBINE, st, 1, 7.0 * B * (level + 1) * 8.0 * env.n, 2.0 * B * (level + 1) * env.n);
+    dim3 g(env.n / TPB, level + 1, 2 * B);
+    k_ks_combine<<<g, TPB, 0, st>>>(out, ps, base0, galois0, base1, bstride, u, w, level, env.alpha, env.conv, env.logn, env.pc);
 }
 
 // ===========================================================================
@@ -282,9 +337,9 @@ __global__ void k_rescale_lift(const u64* last, size_t ls, u64* v, int level, in
     v[(size_t)c * level * n + (size_t)i * n + k] = r;
 }
 
-void launch_rescale_lift(const KernelEnv& env, const u64* last, size_t ls, u64* v, int level, cudaStream_t st) {
-    ProfScope pf(env, KK_RESCALE, st, 1, (2.0 + 2.0 * level) * 8.0 * env.n, 2.0 * level * env.n);
-    dim3 g(env.n / TPB, level, 2);
+void launch_rescale_lift(const KernelEnv& env, const u64* last, size_t ls, u64* v, int level, cudaStream_t st, int polys) {
+    ProfScope pf(env, KK_RESCALE, st, 1, polys * (1.0 + level) * 8.0 * env.n, 1.0 * polys * level * env.n);
+    dim3 g(env.n / TPB, level, polys);
     k_rescale_lift<<<g, TPB, 0, st>>>(last, ls, v, level, env.L, env.conv, env.n, env.pc);
 }
 
@@ -299,9 +354,9 @@ __global__ void k_rescale_combine(u64* ct, size_t ps, const u64* v, int level, i
     ct[off] = shoup_mul(d, tab[i], tab[(L + 1) + i], q);
 }
 
-void launch_rescale_combine(const KernelEnv& env, u64* ct, size_t ps, const u64* v, int level, cudaStream_t st) {
-    ProfScope pf(env, KK_RESCALE, st, 1, 6.0 * level * 8.0 * env.n, 2.0 * level * env.n);
-    dim3 g(env.n / TPB, level, 2);
+void launch_rescale_combine(const KernelEnv& env, u64* ct, size_t ps, const u64* v, int level, cudaStream_t st, int polys) {
+    ProfScope pf(env, KK_RESCALE, st, 1, 3.0 * polys * level * 8.0 * env.n, 1.0 * polys * level * env.n);
+    dim3 g(env.n / TPB, level, polys);
     k_rescale_combine<<<g, TPB, 0, st>>>(ct, ps, v, level, env.L, env.conv, env.n, env.pc);
 }
 

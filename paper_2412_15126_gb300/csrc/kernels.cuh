@@ -43,25 +43,29 @@ void launch_ntt_forward(const KernelEnv& env, const LimbSet& s, cudaStream_t st)
 void launch_ntt_inverse(const KernelEnv& env, const LimbSet& s, cudaStream_t st);
 void launch_addsub(const KernelEnv& env, u64* out, const u64* a, const u64* b, int limbs, size_t ps, int mode, cudaStream_t st,
                    int polys = 2);
-void launch_add_const(const KernelEnv& env, u64* out, const u64* a, const ScalarArg& K, int limbs, size_t ps, cudaStream_t st);
-void launch_mul_scalar(const KernelEnv& env, u64* out, const u64* a, const ScalarArg& K, int limbs, size_t ps, cudaStream_t st);
-void launch_mul_plain(const KernelEnv& env, u64* out, const u64* a, const u64* pt, int limbs, size_t ps, cudaStream_t st);
+void launch_add_const(const KernelEnv& env, u64* out, const u64* a, const ScalarArg& K, int limbs, size_t ps, cudaStream_t st,
+                      int polys = 2);
+void launch_mul_scalar(const KernelEnv& env, u64* out, const u64* a, const ScalarArg& K, int limbs, size_t ps, cudaStream_t st,
+                       int polys = 2);
+void launch_mul_plain(const KernelEnv& env, u64* out, const u64* a, const u64* pt, int limbs, size_t ps, cudaStream_t st,
+                      int polys = 2);
 // out[c][t] (+)= sum_i x_i[c][t] * K_i[t] for up to 16 terms; KR holds K_i times R
 struct LincombArg {
     const u64* x[16];
     u64 KR[16][RK_MAX_PRIMES];
 };
 void launch_lincomb(const KernelEnv& env, u64* out, const LincombArg& a, int terms, bool accumulate, int limbs, size_t ps,
-                    cudaStream_t st);
-void launch_tensor(const KernelEnv& env, u64* d, const u64* x, const u64* y, int limbs, size_t ps, cudaStream_t st);
-void launch_modup(const KernelEnv& env, const u64* x, u64* ext, size_t ext_stride, int level, int beta, cudaStream_t st);
-void launch_moddown_conv(const KernelEnv& env, const u64* u, u64* w, int level, cudaStream_t st);
+                    cudaStream_t st, int polys = 2);
+void launch_tensor(const KernelEnv& env, u64* d, const u64* x, const u64* y, int limbs, size_t ps, cudaStream_t st, int B = 1);
+void launch_modup(const KernelEnv& env, const u64* x, const u64* x_eval, size_t eval_stride, u64* ext, size_t ext_stride,
+                  int level, int beta, cudaStream_t st, int B = 1);
+void launch_moddown_conv(const KernelEnv& env, const u64* u, u64* w, int level, cudaStream_t st, int polys = 2);
 void launch_ks_inner(const KernelEnv& env, const u64* ext, size_t ext_stride, const u64* key, u64* u, int level, int beta,
-                     u64 galois, cudaStream_t st);
-void launch_ks_combine(const KernelEnv& env, u64* out, size_t ps, const u64* base0, u64 galois0, const u64* base1,
-                       const u64* u, const u64* w, int level, cudaStream_t st);
-void launch_rescale_lift(const KernelEnv& env, const u64* last, size_t ls, u64* v, int level, cudaStream_t st);
-void launch_rescale_combine(const KernelEnv& env, u64* ct, size_t ps, const u64* v, int level, cudaStream_t st);
+                     u64 galois, cudaStream_t st, int B = 1);
+void launch_ks_combine(const KernelEnv& env, u64* out, size_t ps, const u64* base0, u64 galois0, const u64* base1, size_t bstride,
+                       const u64* u, const u64* w, int level, cudaStream_t st, int B = 1);
+void launch_rescale_lift(const KernelEnv& env, const u64* last, size_t ls, u64* v, int level, cudaStream_t st, int polys = 2);
+void launch_rescale_combine(const KernelEnv& env, u64* ct, size_t ps, const u64* v, int level, cudaStream_t st, int polys = 2);
 void launch_reduce_signed(const KernelEnv& env, const int64_t* src, const LimbSet& s, cudaStream_t st);
 void launch_uniform(const KernelEnv& env, const LimbSet& s, u64 seed, u64 stream_id, cudaStream_t st);
 void launch_key_digit(const KernelEnv& env, u64* kb, u64* ka, const u64* a, const u64* e, const u64* s_R, const u64* sp,

@@ -14,22 +14,26 @@
 //   (1 << (Sbase - v)) + (rho << (LOG - 1 - v)) + (x >> (v + 1))
 // of the (inverse) table, Sbase = a - 1 for the column pass and logn - 1 for the row
 // pass, rho the row number of a row-pass transform (0 in the column pass).
-// Residues stay in [0, 2q) between stages (Shoup products, Harvey's lazy bounds).
+// Forward residues stay in [0, 4q) between stages, inverse ones in [0, 2q) (Shoup
+// products, Harvey's lazy bounds); each transform returns [0, q).
 #include <algorithm>
 
 #include "kernels.cuh"
 
 namespace {
 
+// Cooley-Tukey butterfly on values in [0, 4q) (Harvey): one conditional subtraction.
 __device__ __forceinline__ void ct_bfly(u64& a, u64& b, u64 w, u64 wsh, u64 q, u64 q2) {
     u64 U = a;
-    u64 V = shoup_lazy(b, w, wsh, q);
-    u64 x = U + V;
+    if (U >= q2) U -= q2;
+    const u64 V = shoup_lazy(b, w, wsh, q);   // [0, 2q) for any 64-bit input
+    a = U + V;
+    b = U + q2 - V;
+}
+
+__device__ __forceinline__ u64 reduce_4q(u64 x, u64 q, u64 q2) {
     if (x >= q2) x -= q2;
-    u64 y = U + q2 - V;
-    if (y >= q2) y -= q2;
-    a = x;
-    b = y;
+    return x >= q ? x - q : x;
 }
 
 __device__ __forceinline__ void gs_bfly(u64& a, u64& b, u64 w, u64 wsh, u64 q, u64 q2) {
@@ -41,12 +45,13 @@ __device__ __forceinline__ void gs_bfly(u64& a, u64& b, u64 w, u64 wsh, u64 q, u
 }
 
 template <int LOG, bool INV, bool COL>
-__global__ void __launch_bounds__(256) k_ntt_pass(LimbSet s, int logn, int loga, int units, const PrimeConst* __restrict__ pc,
+__global__ void __launch_bounds__(256, (LOG <= 8 && COL ? 3 : 2)) k_ntt_pass(LimbSet s, int logn, int loga, int units, const PrimeConst* __restrict__ pc,
                                                   const u64* __restrict__ tw, const u64* __restrict__ tw_sh) {
     constexpr int T = 1 << LOG, LOGP = LOG / 2, P = 1 << LOGP, LOGE = LOG - LOGP, E = 1 << LOGE;
     extern __shared__ u64 sm[];
     const int n = 1 << logn, B = 1 << (logn - loga);
     const int limb = blockIdx.y;
+    if (s.skip_ds && limb < s.split && limb / s.skip_ds == (int)(blockIdx.z % s.skip_beta)) return;   // block-uniform
     const int pid = limb_prime(s, limb);
     const PrimeConst PC = pc[pid];
     const u64 q = PC.q, q2 = 2 * q;
@@ -118,7 +123,7 @@ __global__ void __launch_bounds__(256) k_ntt_pass(LimbSet s, int logn, int loga,
             }
         }
         if (COL) {
-            // column pass output stays in [0, 2q); coalesced over u
+            // column pass output stays in [0, 4q); coalesced over u
 #pragma unroll
             for (int m = 0; m < E; m++) g[(size_t)(t * E + m) * gs] = x[m];
         } else {
@@ -127,7 +132,7 @@ __global__ void __launch_bounds__(256) k_ntt_pass(LimbSet s, int logn, int loga,
             for (int m = 0; m < E; m++) sm[sidx(t * E + m)] = x[m];
             __syncthreads();
 #pragma unroll
-            for (int m = 0; m < E; m++) g[t + P * m] = reduce_2q(sm[sidx(t + P * m)], q);
+            for (int m = 0; m < E; m++) g[t + P * m] = reduce_4q(sm[sidx(t + P * m)], q, q2);
         }
     } else {
         // load the contiguous set {t E + m}
@@ -239,8 +244,8 @@ void ntt_init_attributes() {
 
 void launch_ntt_forward(const KernelEnv& env, const LimbSet& s, cudaStream_t st) {
     if (s.n_limbs <= 0 || s.n_polys <= 0) return;
-    ProfScope ps(env, KK_NTT_FWD, st, 2, 2.0 * s.n_limbs * s.n_polys * 8.0 * env.n,
-                 (double)s.n_limbs * s.n_polys * (env.n / 2) * env.logn);
+    const double limbs = (double)s.n_limbs * s.n_polys - (s.skip_ds ? (double)(s.n_polys / s.skip_beta) * s.split : 0.0);
+    ProfScope ps(env, KK_NTT_FWD, st, 2, 2.0 * limbs * 8.0 * env.n, limbs * (env.n / 2) * env.logn);
     const int logn = env.logn, loga = logn / 2, logb = logn - loga;
     PassGeom c = geom(loga, 1 << logb, s);
     pass_launch<false, true>(loga, c.grid, c.threads, c.smem, st, s, logn, loga, c.units, env.pc, env.tw.psi, env.tw.psi_sh);

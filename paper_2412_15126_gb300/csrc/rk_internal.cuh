@@ -44,6 +44,10 @@ struct LimbSet {
     int split;
     int off_lo;
     int off_hi;
+    // optional: skip limbs t < split with t / skip_ds == poly % skip_beta (the lifted
+    // digits of a ModUp already hold their own limbs in the evaluation domain)
+    int skip_ds = 0;
+    int skip_beta = 1;
 };
 
 __host__ __device__ __forceinline__ int limb_prime(const LimbSet& s, int t) {
@@ -154,6 +158,7 @@ struct rk_ctx {
     // scratch (grows on demand; stream ordered)
     u64* d_scratch = nullptr;
     size_t scratch_words = 0;
+    int batch_cap = 1;            // largest stack B the scratch layout is sized for
     // plaintext caches: key = (kind, N, Q, n_real, level)
     std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint32_t, int>, u64*> plain_cache;
     std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint32_t>, std::vector<double>> encodings;
@@ -172,8 +177,10 @@ struct rk_ctx {
 
 struct rk_ct {
     rk_ctx* ctx = nullptr;
-    u64* data = nullptr;   // [2][L+1][n] (only limbs 0..level are meaningful), evaluation domain
+    u64* data = nullptr;   // [B][2][L+1][n] (only limbs 0..level are meaningful), evaluation domain
     int level = 0;
+    int B = 1;             // ciphertexts stacked in this handle (one launch per operation for all)
+    bool view = false;     // borrows `data` from another handle (never freed through this one)
     uint32_t N = 0;        // padded vector length (power of two)
     uint32_t n_real = 0;   // unpadded length
     uint32_t Q = 1;        // queries packed at stride N^2
@@ -183,9 +190,13 @@ struct rk_ct {
 // ---------------------------------------------------------------------------
 // Evaluator (evaluator.cu)
 // ---------------------------------------------------------------------------
-rk_ct* ct_alloc(rk_ctx* c, int level);
+rk_ct* ct_alloc(rk_ctx* c, int level, int B = 1);
 void ct_free(rk_ct* ct);
 rk_ct* ct_clone_meta(const rk_ct* src, int level);
+void ensure_batch(rk_ctx* c, int B);   // size the scratch for stacks of B ciphertexts
+rk_ct* ct_stack(rk_ctx* c, const rk_ct* const* in, int count);        // B = count, copies
+void ct_unstack(rk_ctx* c, const rk_ct* in, rk_ct** outs);            // B outputs of B = 1
+rk_ct* ct_view(const rk_ct* stack, int b);                            // member b, no copy
 
 void ev_add(rk_ctx* c, const rk_ct* a, const rk_ct* b, rk_ct* out);
 void ev_sub(rk_ctx* c, const rk_ct* a, const rk_ct* b, rk_ct* out);

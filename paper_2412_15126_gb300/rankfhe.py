@@ -77,6 +77,10 @@ _sig("rk_ct_import", [_vp, _u64p, _u32, _u32, _u32, _u32, ctypes.POINTER(_vp)])
 _sig("rk_ct_export", [_vp, _u64p, _sz])
 _sig("rk_ct_level", [_vp], _u32)
 _sig("rk_ct_free", [_vp], None)
+_sig("rk_ct_stack", [_vp, ctypes.POINTER(_vp), _u32, ctypes.POINTER(_vp)])
+_sig("rk_rank_blocked", [_vp, ctypes.POINTER(_vp), _u32, _u32, ctypes.POINTER(_vp)])
+_sig("rk_ct_unstack", [_vp, _vp, ctypes.POINTER(_vp)])
+_sig("rk_ct_count", [_vp], _u32)
 _sig("rk_rotate", [_vp, _vp, ctypes.c_int32, ctypes.POINTER(_vp)])
 _sig("rk_rotate_many", [_vp, _vp, _i32p, _u32, ctypes.POINTER(_vp)])
 for _n in ("rk_add", "rk_sub", "rk_mul"):
@@ -92,6 +96,9 @@ _sig("rk_order_stat", [_vp, _vp, _u32, _u32, ctypes.POINTER(_vp)])
 _sig("rk_sort", [_vp, _vp, _u32, ctypes.POINTER(_vp)])
 _sig("rk_indicator_import", [_vp, _u32, _dp, _sz])
 _sig("rk_rank_batch", [_vp, ctypes.POINTER(_vp), _sz, _u32, ctypes.POINTER(_vp)])
+_sig("rk_graph_rank", [_vp, _vp, _u32, ctypes.POINTER(_vp)])
+_sig("rk_graph_run", [_vp, _vp, ctypes.POINTER(_vp)])
+_sig("rk_graph_free", [_vp], None)
 _sig("rk_ntt_forward", [_vp, _vp, _u32, _u32])
 _sig("rk_ntt_inverse", [_vp, _vp, _u32, _u32])
 _sig("rk_profile_start", [_vp, ctypes.c_char_p])
@@ -142,6 +149,31 @@ class Ciphertext:
         return out
 
 
+class RankGraph:
+    """The rank circuit captured as one CUDA graph for one input shape."""
+
+    def __init__(self, ctx: "Context", handle: int):
+        self.ctx = ctx
+        self.handle = ctypes.c_void_p(handle)
+        ctx._live.add(self)
+
+    def run(self, ct: Ciphertext) -> Ciphertext:
+        h = _vp()
+        _check(_L.rk_graph_run(self.handle, ct.handle, ctypes.byref(h)))
+        return Ciphertext(self.ctx, h.value)
+
+    def free(self):
+        if self.handle and self.handle.value:
+            _L.rk_graph_free(self.handle)
+            self.handle = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
 class Context:
     def __init__(self, log_n, n_limbs, n_special, digit_size, log_scale, log_q0=60, log_special=61,
                  d_g=4, d_f=2, device=0, stream=None):
@@ -155,8 +187,12 @@ class Context:
     def close(self):
         """Free every ciphertext still alive, then the context."""
         if self.handle and self.handle.value:
-            for ct in list(self._live):
-                ct.free()
+            live = list(self._live)
+            for obj in live:                 # graphs first: they hold captured buffers
+                if isinstance(obj, RankGraph):
+                    obj.free()
+            for obj in live:
+                obj.free()
             _L.rk_ctx_destroy(self.handle)
             self.handle = _vp(0)
 
@@ -246,6 +282,24 @@ class Context:
         _check(fn(self.handle, *args, ctypes.byref(h)))
         return Ciphertext(self, h.value)
 
+    def rank_blocked(self, blocks):
+        ins = (_vp * len(blocks))(*[c.handle.value for c in blocks])
+        outs = (_vp * len(blocks))()
+        _check(_L.rk_rank_blocked(self.handle, ins, len(blocks), 0, outs))
+        return [Ciphertext(self, o) for o in outs]
+
+    def stack(self, cts):
+        ins = (_vp * len(cts))(*[c.handle.value for c in cts])
+        h = _vp()
+        _check(_L.rk_ct_stack(self.handle, ins, len(cts), ctypes.byref(h)))
+        return Ciphertext(self, h.value)
+
+    def unstack(self, ct):
+        k = int(_L.rk_ct_count(ct.handle))
+        outs = (_vp * k)()
+        _check(_L.rk_ct_unstack(self.handle, ct.handle, outs))
+        return [Ciphertext(self, o) for o in outs]
+
     def rotate(self, ct, r):
         return self._out(_L.rk_rotate, ct.handle, int(r))
 
@@ -296,6 +350,12 @@ class Context:
 
     def rank(self, ct, flags=0):
         return self._out(_L.rk_rank, ct.handle, flags)
+
+    def graph_rank(self, template: Ciphertext, flags=0) -> RankGraph:
+        """Capture rank(template-shaped input, flags) as one CUDA graph."""
+        h = _vp()
+        _check(_L.rk_graph_rank(self.handle, template.handle, flags, ctypes.byref(h)))
+        return RankGraph(self, h.value)
 
     def rank_batch(self, cts, flags=0):
         ins = (_vp * len(cts))(*[c.handle.value for c in cts])

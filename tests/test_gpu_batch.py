@@ -1,0 +1,117 @@
+"""GPU parity of the batched forms: stacked ciphertexts (one launch per kernel for
+the stack) and slot packing (Q queries per ciphertext, masks tiled per query).
+
+* Each member of a stacked rank is the oracle's rank of that input, bit for bit.
+* rk_rank_batch on a mix of lengths returns, for every query, exactly the
+  ciphertext its own rank returns alone.
+* Slot-packed queries decrypt to their own brute-force ranks (no leakage).
+"""
+import numpy as np
+import pytest
+
+from oracle import ckks, circuits as C
+from paper_2412_15126_gb300 import inputs
+from tests import helpers
+
+pytestmark = pytest.mark.gpu
+
+
+def test_stacked_rank_bit_exact_per_member():
+    P = helpers.oracle_params("cfg1")
+    keys = ckks.keygen(P, 11, helpers.galois_elts(P, helpers.rotation_set(8)))
+    ctx = helpers.gpu_context("cfg1")
+    try:
+        helpers.import_keys(ctx, keys)
+        helpers.import_encodings(ctx, P, 8)
+        vs = [inputs.gap_vector(8, 0.05, s) for s in (21, 22, 23)]
+        cts = [ckks.encrypt(P, keys, v, s) for v, s in zip(vs, (21, 22, 23))]
+        st = ctx.stack([ctx.ct_import(c.c, c.level, N=8) for c in cts])
+        parts = ctx.unstack(ctx.rank(st))
+        B = C.OracleCkks(P, keys)
+        for ct, part, v in zip(cts, parts, vs):
+            assert np.array_equal(part.export(), C.rank(B, ct, 8, 2, 1).c)
+            assert np.max(np.abs(ctx.decrypt(part) - C.brute_fractional_rank(v))) < 0.25
+    finally:
+        ctx.close()
+
+
+@pytest.fixture(scope="module")
+def cfg2():
+    ctx = helpers.gpu_context("cfg2")
+    ctx.keygen(4242, 128)
+    yield ctx
+    ctx.close()
+
+
+def test_rank_batch_identical_alone_and_in_mix(cfg2):
+    ctx = cfg2
+    lens = [16, 32, 16, 128, 64, 32, 128]
+    vs = [inputs.gap_vector(N, 2.0 ** -9, 300 + i) for i, N in enumerate(lens)]
+    cts = [ctx.encrypt(v, N=N) for v, N in zip(vs, lens)]
+    mixed = ctx.rank_batch(cts)
+    for ct, out, v in zip(cts, mixed, vs):
+        alone = ctx.rank(ct)
+        assert np.array_equal(out.export(), alone.export())
+        assert np.max(np.abs(ctx.decrypt(out) - C.brute_fractional_rank(v))) < 0.25
+
+
+def test_blocked_rank_bit_exact_n8x3():
+    P = helpers.oracle_params("cfg1")
+    keys = ckks.keygen(P, 12, helpers.galois_elts(P, helpers.rotation_set(8)))
+    ctx = helpers.gpu_context("cfg1")
+    try:
+        helpers.import_keys(ctx, keys)
+        helpers.import_encodings(ctx, P, 8)
+        v = inputs.gap_vector(24, 0.04, 9)
+        cts = [ckks.encrypt(P, keys, v[8 * i: 8 * i + 8], 40 + i) for i in range(3)]
+        ref = C.rank_blocked(C.OracleCkks(P, keys), cts, 8, 2, 1)
+        got = ctx.rank_blocked([ctx.ct_import(c.c, c.level, N=8) for c in cts])
+        for g, r in zip(got, ref):
+            assert np.array_equal(g.export(), r.c)
+        ranks = np.concatenate([ctx.decrypt(g) for g in got])
+        assert np.max(np.abs(ranks - C.brute_fractional_rank(v))) < 0.5
+    finally:
+        ctx.close()
+
+
+def test_blocked_rank_n512(cfg2):
+    ctx = cfg2
+    v = inputs.gap_vector(512, 2.0 ** -9, 77)
+    blocks = [ctx.encrypt(v[128 * i: 128 * (i + 1)], N=128) for i in range(4)]
+    ranks = np.concatenate([ctx.decrypt(r) for r in ctx.rank_blocked(blocks)])
+    assert np.max(np.abs(ranks - C.brute_fractional_rank(v))) < 0.25
+
+
+@pytest.mark.parametrize("N,Q", [(16, 8), (32, 4), (64, 2)])
+def test_slot_packed_queries(cfg2, N, Q):
+    ctx = cfg2
+    vs = [inputs.gap_vector(N, 2.0 ** -9, 500 + q) for q in range(Q)]
+    ct = ctx.encrypt(np.concatenate(vs), N=N, Q=Q, n_real=N)
+    got = ctx.decrypt(ctx.rank(ct)).reshape(Q, N)
+    for q in range(Q):
+        assert np.max(np.abs(got[q] - C.brute_fractional_rank(vs[q]))) < 0.25
+
+
+@pytest.mark.parametrize("flags", [0, 1])
+def test_graph_rank_bit_identical_to_direct(cfg2, flags):
+    """The rank circuit captured as one CUDA graph replays to exactly the ciphertext
+    the direct call returns, for fresh inputs of the captured shape (single and stacked)."""
+    ctx = cfg2
+    N = 32
+    vs = [inputs.gap_vector(N, 2.0 ** -9, 500 + i) for i in range(5)]
+    cts = [ctx.encrypt(v, N=N) for v in vs]
+    g = ctx.graph_rank(cts[0], flags)
+    try:
+        for ct in cts[1:3]:                       # inputs other than the template
+            assert np.array_equal(g.run(ct).export(), ctx.rank(ct, flags).export())
+    finally:
+        g.free()
+    st = ctx.stack(cts[2:5])
+    gs = ctx.graph_rank(st, flags)
+    try:
+        st2 = ctx.stack(cts[0:3])
+        got = ctx.unstack(gs.run(st2))
+        for ct, part in zip(cts[0:3], got):
+            assert np.array_equal(part.export(), ctx.rank(ct, flags).export())
+    finally:
+        gs.free()

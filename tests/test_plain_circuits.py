@@ -162,6 +162,45 @@ def test_packed_queries_do_not_leak():
         assert np.max(np.abs(R[q * N * N: q * N * N + N] - C.brute_fractional_rank(v))) < 1e-3
 
 
+@pytest.mark.parametrize("Bsz,L", [(4, 2), (4, 3), (8, 4), (64, 2)])
+def test_blocked_rank_equals_whole_vector_rank(Bsz, L):
+    """Alg. 7 on L blocks gives the ranks of the whole vector (for Bsz = 64, L = 2 the
+    single-ciphertext N = 128 ranks)."""
+    rng = np.random.default_rng(Bsz * 10 + L)
+    N = Bsz * L
+    v = rng.permutation(np.linspace(0.01, 0.98, N))
+    slots = max(2 * Bsz * Bsz, 64)
+    B = C.PlainSlots(slots, 40)
+    Rs = C.rank_blocked(B, [B.fresh(v[i * Bsz:(i + 1) * Bsz]) for i in range(L)], Bsz, 4, 2)
+    got = np.concatenate([B.values(R)[:Bsz] for R in Rs])
+    assert np.max(np.abs(got - C.brute_fractional_rank(v))) < 1e-3
+    assert len({R.level for R in Rs}) == 1 and Rs[0].level == 40 - 3 - 3 * 6
+    if N <= 128 and N & (N - 1) == 0:
+        B1 = C.PlainSlots(2 * N * N, 40)
+        single = B1.values(C.rank(B1, B1.fresh(v), N, 4, 2))[:N]
+        assert np.max(np.abs(got - single)) < 1e-3
+
+
+def test_blocked_rank_two_packed_queries():
+    """Two blocked queries packed at stride Bsz^2 in the same block ciphertexts keep
+    their own ranks (Q = 2, as the batched form packs N = 512 queries)."""
+    Bsz, L, Q = 8, 3, 2
+    rng = np.random.default_rng(5)
+    vs = [rng.permutation(np.linspace(0.02, 0.97, Bsz * L)) for _ in range(Q)]
+    slots = Q * Bsz * Bsz * 2
+    B = C.PlainSlots(slots, 40)
+    blocks = []
+    for i in range(L):
+        x = np.zeros(slots)
+        for q in range(Q):
+            x[q * Bsz * Bsz: q * Bsz * Bsz + Bsz] = vs[q][i * Bsz:(i + 1) * Bsz]
+        blocks.append(C.PV(x, 40))
+    Rs = C.rank_blocked(B, blocks, Bsz, 4, 2, Q=Q)
+    for q in range(Q):
+        got = np.concatenate([B.values(R)[q * Bsz * Bsz: q * Bsz * Bsz + Bsz] for R in Rs])
+        assert np.max(np.abs(got - C.brute_fractional_rank(vs[q]))) < 1e-3
+
+
 def test_fig3_sort_example(golden):
     g = golden["fig3_sort"]
     v = np.array(g["input"]) / 64.0
