@@ -53,6 +53,59 @@ def workload_config(extra=None):
     return cfg
 
 
+ORDER_WORKLOAD = dict(log_n=16, n_limbs=34, n_special=3, digit_size=3, log_scale=45, log_q0=60, log_special=61,
+                      d_g=3, d_f=2, N=128, levels=64)
+
+
+def order_sort_workload(stream, device, reps=3, seed=3):
+    """Tie-corrected argmin (Alg. 4, one-hot at the first minimum), argmax with every
+    tied maximum (Cmp_G route) and the column-form sort (Alg. 5) of N = 128 values
+    on a 64-level grid, n = 2^16 with 34 limbs; inputs resident, each op timed with
+    CUDA events on the library stream over `reps` fresh inputs."""
+    import numpy as np
+    import torch
+    from paper_2412_15126_gb300 import inputs, rankfhe
+
+    W = ORDER_WORKLOAD
+    ctx = rankfhe.Context(W["log_n"], W["n_limbs"], W["n_special"], W["digit_size"], W["log_scale"], W["log_q0"],
+                          W["log_special"], W["d_g"], W["d_f"], device=device, stream=stream.cuda_stream)
+    try:
+        ctx.keygen(5000 + seed, W["N"])
+        vecs = [inputs.grid_vector(W["N"], W["levels"], 100 + seed * 10 + i) for i in range(reps + 1)]
+        cts = [ctx.encrypt(v, N=W["N"]) for v in vecs]
+        ops = {
+            "argmin_first": lambda ct: ctx.order_stat(ct, 1, rankfhe.TIES_FIRST),
+            "argmax_all": lambda ct: ctx.order_stat(ct, W["N"], rankfhe.TIES_ALL),
+            "sort": lambda ct: ctx.sort(ct),
+        }
+        exact = {
+            "argmin_first": lambda v: np.eye(len(v))[int(np.argmin(v))],
+            "argmax_all": lambda v: (v == v.max()).astype(float),
+            "sort": lambda v: np.sort(v),
+        }
+        out = {"workload": "N=128 on a 64-level grid (ties), n=2^16, 34+3 limbs, scale 2^45, Cmp g^3 f^2, "
+                           "indicator degree 1023"}
+        for name, fn in ops.items():
+            fn(cts[0]).free()          # warm-up: masks, indicator coefficients
+            ctx.sync()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            res = []
+            with torch.cuda.stream(stream):
+                ev0.record(stream)
+                for ct in cts[1:]:
+                    res.append(fn(ct))
+                ev1.record(stream)
+            ev1.synchronize()
+            err = max(float(np.max(np.abs(ctx.decrypt(r) - exact[name](v)))) for r, v in zip(res, vecs[1:]))
+            out[name] = {"ms": ev0.elapsed_time(ev1) / reps, "max_error": err}
+            for r in res:
+                r.free()
+        return out
+    finally:
+        ctx.close()
+
+
 # ---------------------------------------------------------------------------
 # clocks
 # ---------------------------------------------------------------------------
@@ -412,6 +465,22 @@ def run_cuda(args):
     h2d = 2 * W["n_limbs"] * n * 8
     d2h = 2 * (out_level + 1) * n * 8 if out_level is not None else 0
 
+    # per kernel kind: algorithmic bytes over event-timed duration, one rank step each
+    kinds = None
+    if not args.no_kernel_table:
+        kinds = {}
+        for kind in ("ntt_fwd", "ntt_inv", "modup", "ks_inner", "moddown_conv", "ks_combine", "tensor", "rescale",
+                     "pointwise"):
+            ctx.sync()
+            ctx.profile_start(kind)
+            ctx.rank(cts[args.warmup]).free()
+            ctx.sync()
+            pr = ctx.profile_stop()
+            if pr["launches"]:
+                gbs = pr["bytes"] / (pr["ms"] * 1e-3) / 1e9
+                kinds[kind] = {"launches": pr["launches"], "ms_per_step": pr["ms"], "gb": pr["bytes"] / 1e9,
+                               "gbs": gbs, "frac_hbm": gbs / measured_peaks()[0]}
+
     # the same steps replayed from one CUDA graph of the rank circuit
     graph = None
     if not args.no_graph:
@@ -437,6 +506,10 @@ def run_cuda(args):
     batched = None
     if not args.no_batched:
         batched = batched_workload(ctx)
+
+    order_sort = None
+    if not args.no_order_sort and world == 1:
+        order_sort = order_sort_workload(stream, local)
 
     peak, peak_kind = measured_peaks()
     achieved = None
@@ -468,6 +541,8 @@ def run_cuda(args):
             "cpu_baseline": cpu,
             "batched": batched,
             "graph": graph,
+            "order_sort": order_sort,
+            "kernels": kinds,
             "clocks": clk,
             "gpu_launches": launches,
         }
@@ -490,6 +565,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 104-query batched workload")
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay of the rank steps")
+    ap.add_argument("--no-kernel-table", action="store_true", help="skip the per-kernel-kind roofline table")
+    ap.add_argument("--no-order-sort", action="store_true", help="skip the 34-limb argmin/argmax/sort latencies")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -109,6 +109,20 @@ rk_status rk_sync(rk_ctx* ctx);
 /* Counters since creation: [key switches, rotations, ciphertext products, rescales]. */
 rk_status rk_ctx_counters(const rk_ctx* ctx, uint64_t out[4]);
 
+/* Execution options (the paper has no counterpart; results do not depend on them).
+ * RK_OPT_KS_FUSED: 0 (default) runs hybrid key switching as staged kernels, which
+ *   materialise every lifted digit in device memory; 1 fuses the ModUp and ModDown
+ *   conversions into the NTT column passes and the key inner product and the final
+ *   combine into the row passes (fewer device-memory passes, less parallelism:
+ *   slower on GB300 at n = 2^16).  Both produce identical ciphertexts bit for bit.
+ * RK_OPT_KS_GROUP_BYTES: bytes of lifted digits the fused path keeps in flight
+ *   between its column and row kernels (default 48 MiB, sized for the 129 MB L2);
+ *   values below one limb group run one target limb at a time.
+ * Errors: RK_EINVAL for an unknown option or a negative value. */
+#define RK_OPT_KS_FUSED 1
+#define RK_OPT_KS_GROUP_BYTES 2
+rk_status rk_ctx_set_option(rk_ctx* ctx, uint32_t option, int64_t value);
+
 /* ---- keys ----------------------------------------------------------------- */
 
 /* Generate secret, public, relinearisation key and the rotation (Galois) keys
@@ -262,6 +276,39 @@ rk_status rk_rank_blocked(rk_ctx* ctx, const rk_ct* const* blocks, uint32_t L, u
  * and vector shape are stacked and run as one circuit (one launch per kernel for
  * the group); out[i] is the rank ciphertext of in[i]. */
 rk_status rk_rank_batch(rk_ctx* ctx, const rk_ct* const* in, size_t count, uint32_t flags, rk_ct** out);
+
+/* ---- serving loop ------------------------------------------------------------ */
+
+/* A worker thread per context with continuous batching (the paper has no serving
+ * layer; this is the batched form of Alg. 3-5 and 7 under a request stream).
+ * Requests are queued from any thread; whenever the worker is free it takes the
+ * oldest request and every queued request of the same operation, arguments and
+ * ciphertext shape (level, N, Q, n_real, layout), up to `max_stack` and to as many
+ * as fit `mem_budget_bytes` of working set, and evaluates them as one stacked
+ * circuit.  Each result is bit-identical to the result of its request alone.
+ * While a server runs, the worker owns the context: other threads may call only
+ * rk_server_* and rk_ct_free on collected results until rk_server_stop returns.
+ * Inputs are borrowed: keep each submitted ciphertext alive and unchanged until its
+ * result has been collected.  Results are owned by the caller once collected. */
+#define RK_OP_RANK 1          /* rk_rank(in, flags) */
+#define RK_OP_ORDER_STAT 2    /* rk_order_stat(in, arg = k, flags) */
+#define RK_OP_SORT 3          /* rk_sort(in, flags) */
+#define RK_OP_RANK_BLOCKED 4  /* rk_rank_blocked on the blocks of a stack (rk_ct_stack);
+                                 the result is the stack of the rank blocks */
+rk_status rk_server_start(rk_ctx* ctx, size_t mem_budget_bytes, uint32_t max_stack);
+/* Queue a request; *ticket identifies it.  Errors: RK_EINVAL (no server, unknown op,
+ * a stack where one ciphertext is expected, server stopping). */
+rk_status rk_server_submit(rk_ctx* ctx, uint32_t op, uint32_t arg, uint32_t flags, const rk_ct* in, uint64_t* ticket);
+/* Collect a finished request: *out = its result, or NULL while it is pending.  Waits
+ * up to timeout_s seconds (0: poll, negative: no limit).  A failed request returns its
+ * error status.  Each ticket is collected once; RK_EINVAL for unknown tickets. */
+rk_status rk_server_wait(rk_ctx* ctx, uint64_t ticket, double timeout_s, rk_ct** out);
+/* out[8]: requests finished, p50 and p99 and max latency (s, submit to result on the
+ * device), batches run, mean batch size, peak device memory in use above the level at
+ * rk_server_start (bytes), requests queued. */
+rk_status rk_server_stats(rk_ctx* ctx, double out[8]);
+/* Finish every queued request, stop the worker, free uncollected results. */
+rk_status rk_server_stop(rk_ctx* ctx);
 
 /* ---- CUDA graphs -------------------------------------------------------------- */
 

@@ -14,6 +14,11 @@ rk_ct* circuit_sort(rk_ctx* c, const rk_ct* in, uint32_t flags);
 void indicator_import(rk_ctx* c, uint32_t N, const double* coeffs, size_t count);
 void circuit_rank_blocked(rk_ctx* c, const rk_ct* const* blocks, int L, rk_ct** outs);
 rk_graph* graph_rank_capture(rk_ctx* c, const rk_ct* tmpl, uint32_t flags);
+rk_server* server_start(rk_ctx* c, size_t budget, int max_stack);
+uint64_t server_submit(rk_ctx* c, uint32_t op, uint32_t arg, uint32_t flags, const rk_ct* in);
+rk_ct* server_collect(rk_ctx* c, uint64_t ticket, double timeout_s);
+void server_stats(rk_ctx* c, double out[8]);
+void server_stop(rk_ctx* c);
 rk_ct* graph_rank_run(rk_graph* g, const rk_ct* in);
 void graph_free(rk_graph* g);
 rk_ctx* graph_context(const rk_graph* g);
@@ -115,6 +120,19 @@ rk_status rk_ctx_counters(const rk_ctx* ctx, uint64_t out[4]) {
         out[1] = ctx->n_rot;
         out[2] = ctx->n_mul;
         out[3] = ctx->n_rescale;
+    });
+}
+
+rk_status rk_ctx_set_option(rk_ctx* ctx, uint32_t option, int64_t value) {
+    return guard([&] {
+        need(ctx, "ctx");
+        RK_REQUIRE(value >= 0, RK_EINVAL, "option value must be non-negative");
+        RK_CUDA(cudaStreamSynchronize(ctx->stream));
+        switch (option) {
+            case RK_OPT_KS_FUSED: ctx->ks_fused = value != 0; break;
+            case RK_OPT_KS_GROUP_BYTES: ctx->ks_group_bytes = (double)value; break;
+            default: throw rk_error(RK_EINVAL, "unknown option " + std::to_string(option));
+        }
     });
 }
 
@@ -453,6 +471,48 @@ rk_status rk_rank_blocked(rk_ctx* ctx, const rk_ct* const* blocks, uint32_t L, u
         set_device(ctx);
         circuit_rank_blocked(ctx, blocks, (int)L, outs);
         check_launch();
+    });
+}
+
+rk_status rk_server_start(rk_ctx* ctx, size_t mem_budget_bytes, uint32_t max_stack) {
+    return guard([&] {
+        need(ctx, "ctx");
+        set_device(ctx);
+        server_start(ctx, mem_budget_bytes, (int)max_stack);
+    });
+}
+
+rk_status rk_server_submit(rk_ctx* ctx, uint32_t op, uint32_t arg, uint32_t flags, const rk_ct* in, uint64_t* ticket) {
+    return guard([&] {
+        need(ctx, "ctx");
+        same_ctx(ctx, in);
+        need(ticket, "ticket");
+        *ticket = server_submit(ctx, op, arg, flags, in);
+    });
+}
+
+rk_status rk_server_wait(rk_ctx* ctx, uint64_t ticket, double timeout_s, rk_ct** out) {
+    return guard([&] {
+        need(ctx, "ctx");
+        need(out, "out");
+        *out = nullptr;
+        *out = server_collect(ctx, ticket, timeout_s);
+    });
+}
+
+rk_status rk_server_stats(rk_ctx* ctx, double out[8]) {
+    return guard([&] {
+        need(ctx, "ctx");
+        need(out, "out");
+        server_stats(ctx, out);
+    });
+}
+
+rk_status rk_server_stop(rk_ctx* ctx) {
+    return guard([&] {
+        need(ctx, "ctx");
+        set_device(ctx);
+        server_stop(ctx);
     });
 }
 

@@ -326,10 +326,14 @@ void ctx_build(rk_ctx* c, const rk_params* p, int device, void* stream) {
     e.conv.rescale = c->d_conv + rs_off;
     e.prof = &c->prof;
     ntt_init_attributes();
+    ks_fused_init_attributes();
 }
+
+void server_stop(rk_ctx* c);
 
 void ctx_release(rk_ctx* c) {
     if (!c) return;
+    server_stop(c);
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     for (auto& kv : c->plain_cache) cudaFree(kv.second);

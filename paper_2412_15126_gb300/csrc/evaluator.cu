@@ -354,16 +354,23 @@ void ev_lincomb(rk_ctx* c, const std::vector<const rk_ct*>& xs, const std::vecto
 // ---------------------------------------------------------------------------
 // Key switching
 // ---------------------------------------------------------------------------
-// ModUp of B polynomials d_b = d_eval + b * d_stride (evaluation domain, limbs 0..l)
-// into the ext scratch [B][beta][l+1+alpha][n] (evaluation domain).
-static void ks_modup(rk_ctx* c, const u64* d_eval, size_t d_stride, int l, int B) {
+// ModUp, first half: B polynomials d_b = d_eval + b * d_stride (evaluation domain,
+// limbs 0..l) to the coefficient domain in S.coef [B][l+1][n].
+static void ks_lift(rk_ctx* c, const u64* d_eval, size_t d_stride, int l, int B) {
     ensure_batch(c, B);
     Scratch S = scratch_layout(c);
     const size_t n = c->n;
-    const int QP = l + 1 + c->alpha;
     const size_t width = (size_t)(l + 1) * n * 8;
     RK_CUDA(cudaMemcpy2DAsync(S.coef, width, d_eval, d_stride * 8, width, B, cudaMemcpyDeviceToDevice, c->stream));
     launch_ntt_inverse(c->env, ls_q(S.coef, (size_t)(l + 1) * n, B, l + 1), c->stream);
+}
+
+// Staged ModUp, second half: every digit lifted to the ext scratch
+// [B][beta][l+1+alpha][n] and taken to the evaluation domain in place.
+static void ks_lift_ext(rk_ctx* c, const u64* d_eval, size_t d_stride, int l, int B) {
+    Scratch S = scratch_layout(c);
+    const size_t n = c->n;
+    const int QP = l + 1 + c->alpha;
     launch_modup(c->env, S.coef, d_eval, d_stride, S.ext, (size_t)QP * n, l, c->beta(l), c->stream, B);
     LimbSet ext{S.ext, (size_t)QP * n, B * c->beta(l), QP, l + 1, 0, c->L + 1};
     ext.skip_ds = c->dsize;   // each digit's own limbs are already in the evaluation domain
@@ -371,18 +378,53 @@ static void ks_modup(rk_ctx* c, const u64* d_eval, size_t d_stride, int l, int B
     launch_ntt_forward(c->env, ext, c->stream);
 }
 
-// Inner product with `key` (automorphism `galois` on the lifted digits), ModDown, and
-// out_b = base_b + result_b (automorphism galois0 on base0), for B stacked inputs.
-static void ks_apply(rk_ctx* c, const u64* key, int l, u64 galois, const u64* base0, u64 galois0, const u64* base1,
-                     size_t bstride, u64* out, size_t out_ps, int B) {
+// Target limbs per fused ModUp group: the group's lifted digits stay resident in L2
+// between the column kernel that writes them and the row kernel that reads them.
+static int ks_group(const rk_ctx* c, int l, int B) {
+    const double per_limb = (double)c->n * 8.0 * B * c->beta(l);
+    const int g = (int)(c->ks_group_bytes / per_limb);
+    return std::max(1, std::min(g, l + 1 + c->alpha));
+}
+
+// Inner product of the lifted input with `key` (automorphism `galois` on the lifted
+// digits) into S.u [B][2][l+1+alpha][n].  `lifted` says whether S.ext already holds
+// every lifted digit (hoisted rotations); otherwise the fused path lifts group by group.
+static void ks_inner(rk_ctx* c, const u64* key, int l, u64 galois, const u64* d_eval, size_t d_stride, int B, bool lifted) {
+    Scratch S = scratch_layout(c);
+    const int QP = l + 1 + c->alpha, beta = c->beta(l);
+    const size_t es = (size_t)QP * c->n;
+    if (!c->ks_fused) {
+        launch_ks_inner(c->env, S.ext, es, key, S.u, l, beta, galois, c->stream, B);
+        return;
+    }
+    if (lifted) {
+        launch_ks_row(c->env, S.ext, es, d_eval, d_stride, key, S.u, l, beta, 0, QP, galois, c->stream, B);
+        return;
+    }
+    const int G = ks_group(c, l, B);
+    for (int t0 = 0; t0 < QP; t0 += G) {
+        const int g = std::min(G, QP - t0);
+        launch_modup_col(c->env, S.coef, S.ext, es, l, beta, t0, g, c->stream, B);
+        launch_ks_row(c->env, S.ext, es, d_eval, d_stride, key, S.u, l, beta, t0, g, galois, c->stream, B);
+    }
+}
+
+// ModDown of S.u and out_b = base_b + result_b (automorphism galois0 on base0), for B
+// stacked inputs (base_p of member b at base_p + b * bstride).
+static void ks_moddown(rk_ctx* c, int l, const u64* base0, u64 galois0, const u64* base1, size_t bstride, u64* out, size_t out_ps,
+                       int B) {
     Scratch S = scratch_layout(c);
     const size_t n = c->n;
     const int QP = l + 1 + c->alpha;
-    launch_ks_inner(c->env, S.ext, (size_t)QP * n, key, S.u, l, c->beta(l), galois, c->stream, B);
     launch_ntt_inverse(c->env, LimbSet{S.u + (size_t)(l + 1) * n, (size_t)QP * n, 2 * B, c->alpha, 0, 0, c->L + 1}, c->stream);
-    launch_moddown_conv(c->env, S.u, S.w, l, c->stream, 2 * B);
-    launch_ntt_forward(c->env, ls_q(S.w, (size_t)(l + 1) * n, 2 * B, l + 1), c->stream);
-    launch_ks_combine(c->env, out, out_ps, base0, galois0, base1, bstride, S.u, S.w, l, c->stream, B);
+    if (c->ks_fused) {
+        launch_moddown_col(c->env, S.u, S.w, l, c->stream, 2 * B);
+        launch_moddown_row(c->env, out, out_ps, base0, galois0, base1, bstride, S.u, S.w, l, c->stream, B);
+    } else {
+        launch_moddown_conv(c->env, S.u, S.w, l, c->stream, 2 * B);
+        launch_ntt_forward(c->env, ls_q(S.w, (size_t)(l + 1) * n, 2 * B, l + 1), c->stream);
+        launch_ks_combine(c->env, out, out_ps, base0, galois0, base1, bstride, S.u, S.w, l, c->stream, B);
+    }
     c->n_ks += (uint64_t)B;
 }
 
@@ -395,24 +437,38 @@ u64 galois_left(const rk_ctx* c, int r) {
 void ev_rotate_many(rk_ctx* c, const rk_ct* a, const int* r, int k, rk_ct** outs) {
     const int l = a->level;
     const size_t ps = c->poly_stride();
-    bool need_ks = false;
+    int nks = 0;
     for (int i = 0; i < k; i++) {
         RK_REQUIRE(outs[i] != a, RK_EINVAL, "rotate: output aliases input");
         RK_REQUIRE(outs[i]->B == a->B, RK_EINVAL, "rotate: stack size mismatch");
         u64 g = galois_left(c, r[i]);
         if (g != 1) {
             RK_REQUIRE(c->gal.count(g), RK_ENOKEY, "rotation key missing for r = " + std::to_string(r[i]));
-            need_ks = true;
+            nks++;
         }
     }
-    if (need_ks) ks_modup(c, a->data + ps, 2 * ps, l, a->B);
+    // hoisting: one ModUp serves every rotation of the list
+    const u64* d = a->data + ps;
+    bool lifted = false;
+    if (nks > 0) {
+        ks_lift(c, d, 2 * ps, l, a->B);
+        if (!c->ks_fused) {
+            ks_lift_ext(c, d, 2 * ps, l, a->B);
+            lifted = true;
+        } else if (nks > 1) {
+            launch_modup_col(c->env, scratch_layout(c).coef, scratch_layout(c).ext, (size_t)(l + 1 + c->alpha) * c->n, l,
+                             c->beta(l), 0, l + 1 + c->alpha, c->stream, a->B);
+            lifted = true;
+        }
+    }
     for (int i = 0; i < k; i++) {
         u64 g = galois_left(c, r[i]);
         if (g == 1) {
             ev_copy(c, a, outs[i]);
             continue;
         }
-        ks_apply(c, c->gal[g].data, l, g, a->data, g, nullptr, 2 * ps, outs[i]->data, ps, a->B);
+        ks_inner(c, c->gal[g].data, l, g, d, 2 * ps, a->B, lifted);
+        ks_moddown(c, l, a->data, g, nullptr, 2 * ps, outs[i]->data, ps, a->B);
         outs[i]->level = l;
         copy_meta(outs[i], a);
         c->n_rot += (uint64_t)a->B;
@@ -429,8 +485,10 @@ void ev_mul(rk_ctx* c, const rk_ct* a, const rk_ct* b, rk_ct* out) {
     Scratch S = scratch_layout(c);
     const size_t pl = (size_t)(l + 1) * c->n;
     launch_tensor(c->env, S.d, a->data, b->data, l + 1, c->poly_stride(), c->stream, B);
-    ks_modup(c, S.d + 2 * pl, 3 * pl, l, B);
-    ks_apply(c, c->rlk.data, l, 0, S.d, 0, S.d + pl, 3 * pl, out->data, c->poly_stride(), B);
+    ks_lift(c, S.d + 2 * pl, 3 * pl, l, B);
+    if (!c->ks_fused) ks_lift_ext(c, S.d + 2 * pl, 3 * pl, l, B);
+    ks_inner(c, c->rlk.data, l, 0, S.d + 2 * pl, 3 * pl, B, !c->ks_fused);
+    ks_moddown(c, l, S.d, 0, S.d + pl, 3 * pl, out->data, c->poly_stride(), B);
     out->level = l;
     copy_meta(out, a);
     c->n_mul += (uint64_t)B;

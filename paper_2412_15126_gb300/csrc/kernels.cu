@@ -6,22 +6,12 @@
 // primitive 2n-th root of unity modulo the limb's prime.
 #include <algorithm>
 
-#include "kernels.cuh"
+#include "ntt_core.cuh"
 
 #define TPB 256
 
 const char* const kKernelKindNames[KK_COUNT] = {"ntt_fwd", "ntt_inv", "modup", "ks_inner", "moddown_conv",
                                                "ks_combine", "tensor", "rescale", "pointwise", "client"};
-
-__device__ __forceinline__ int brev_bits(unsigned x, int bits) { return (int)(__brev(x) >> (32 - bits)); }
-
-// Source index of output index k under X -> X^g in the evaluation domain.
-__device__ __forceinline__ int galois_src(int k, u64 g, int logn) {
-    unsigned two_n_mask = (2u << logn) - 1u;
-    unsigned e = 2u * (unsigned)brev_bits((unsigned)k, logn) + 1u;
-    unsigned e2 = (unsigned)((e * (unsigned)g) & two_n_mask);
-    return brev_bits((e2 - 1u) >> 1, logn);
-}
 
 // ===========================================================================
 // Pointwise kernels on ciphertexts (layout [2][L+1][n], limb t <-> q_t).

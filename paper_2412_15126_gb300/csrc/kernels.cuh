@@ -64,6 +64,15 @@ void launch_ks_inner(const KernelEnv& env, const u64* ext, size_t ext_stride, co
                      u64 galois, cudaStream_t st, int B = 1);
 void launch_ks_combine(const KernelEnv& env, u64* out, size_t ps, const u64* base0, u64 galois0, const u64* base1, size_t bstride,
                        const u64* u, const u64* w, int level, cudaStream_t st, int B = 1);
+// fused key switching (ks_fused.cu)
+void ks_fused_init_attributes();
+void launch_modup_col(const KernelEnv& env, const u64* coef, u64* ext, size_t ext_stride, int level, int beta, int t0, int limbs,
+                      cudaStream_t st, int B = 1);
+void launch_ks_row(const KernelEnv& env, const u64* ext, size_t ext_stride, const u64* x_eval, size_t eval_stride, const u64* key,
+                   u64* u, int level, int beta, int t0, int limbs, u64 galois, cudaStream_t st, int B = 1);
+void launch_moddown_col(const KernelEnv& env, const u64* u, u64* w, int level, cudaStream_t st, int polys = 2);
+void launch_moddown_row(const KernelEnv& env, u64* out, size_t ps, const u64* base0, u64 galois0, const u64* base1, size_t bstride,
+                        const u64* u, const u64* w, int level, cudaStream_t st, int B = 1);
 void launch_rescale_lift(const KernelEnv& env, const u64* last, size_t ls, u64* v, int level, cudaStream_t st, int polys = 2);
 void launch_rescale_combine(const KernelEnv& env, u64* ct, size_t ps, const u64* v, int level, cudaStream_t st, int polys = 2);
 void launch_reduce_signed(const KernelEnv& env, const int64_t* src, const LimbSet& s, cudaStream_t st);

@@ -18,36 +18,16 @@
 // products, Harvey's lazy bounds); each transform returns [0, q).
 #include <algorithm>
 
-#include "kernels.cuh"
+#include "ntt_core.cuh"
 
 namespace {
-
-// Cooley-Tukey butterfly on values in [0, 4q) (Harvey): one conditional subtraction.
-__device__ __forceinline__ void ct_bfly(u64& a, u64& b, u64 w, u64 wsh, u64 q, u64 q2) {
-    u64 U = a;
-    if (U >= q2) U -= q2;
-    const u64 V = shoup_lazy(b, w, wsh, q);   // [0, 2q) for any 64-bit input
-    a = U + V;
-    b = U + q2 - V;
-}
-
-__device__ __forceinline__ u64 reduce_4q(u64 x, u64 q, u64 q2) {
-    if (x >= q2) x -= q2;
-    return x >= q ? x - q : x;
-}
-
-__device__ __forceinline__ void gs_bfly(u64& a, u64& b, u64 w, u64 wsh, u64 q, u64 q2) {
-    u64 U = a, V = b;
-    u64 x = U + V;
-    if (x >= q2) x -= q2;
-    a = x;
-    b = shoup_lazy(U + q2 - V, w, wsh, q);
-}
+using namespace nttc;
 
 template <int LOG, bool INV, bool COL>
 __global__ void __launch_bounds__(256, (LOG <= 8 && COL ? 3 : 2)) k_ntt_pass(LimbSet s, int logn, int loga, int units, const PrimeConst* __restrict__ pc,
                                                   const u64* __restrict__ tw, const u64* __restrict__ tw_sh) {
-    constexpr int T = 1 << LOG, LOGP = LOG / 2, P = 1 << LOGP, LOGE = LOG - LOGP, E = 1 << LOGE;
+    using S = Shape<LOG>;
+    constexpr int P = S::P, E = S::E;
     extern __shared__ u64 sm[];
     const int n = 1 << logn, B = 1 << (logn - loga);
     const int limb = blockIdx.y;
@@ -56,9 +36,6 @@ __global__ void __launch_bounds__(256, (LOG <= 8 && COL ? 3 : 2)) k_ntt_pass(Lim
     const PrimeConst PC = pc[pid];
     const u64 q = PC.q, q2 = 2 * q;
     u64* data = s.base + (size_t)blockIdx.z * s.poly_stride + (size_t)limb * n;
-    const u64* W = tw + (size_t)pid * n;
-    const u64* Wsh = tw_sh + (size_t)pid * n;
-    const int Sbase = COL ? loga - 1 : logn - 1;
     const int tid = threadIdx.x;
     int u, t, rho;
     u64* g;
@@ -76,58 +53,27 @@ __global__ void __launch_bounds__(256, (LOG <= 8 && COL ? 3 : 2)) k_ntt_pass(Lim
         g = data + (size_t)rho * B;
         gs = 1;
     }
-    // shared-memory slot of element e of this thread's transform (rows are swizzled
-    // so that both the strided and the contiguous access patterns avoid conflicts)
-    auto sidx = [&](int e) -> int {
-        if (COL) return e * units + u;
-        return u * T + (e ^ ((e >> LOGE) & (E - 1)));
-    };
-    auto twid = [&](int v, int x, u64& w, u64& wsh) {
-        const int idx = (1 << (Sbase - v)) + (rho << (LOG - 1 - v)) + (x >> (v + 1));
-        w = __ldg(W + idx);
-        wsh = __ldg(Wsh + idx);
-    };
+    const Twid tw_{tw + (size_t)pid * n, tw_sh + (size_t)pid * n, COL ? loga - 1 : logn - 1, rho};
+    auto sidx = [&](int e) -> int { return COL ? e * units + u : row_slot<LOG>(u, e); };
     u64 x[E];
 
     if (!INV) {
         // load the strided set {t + P m}: coalesced over u (columns) or t (rows)
 #pragma unroll
         for (int m = 0; m < E; m++) x[m] = g[(size_t)(t + P * m) * gs];
-        // stages with span 2^v >= P, v = LOG-1 .. LOGP; m-span 2^(v - LOGP)
-#pragma unroll
-        for (int v = LOG - 1; v >= LOGP; v--) {
-            const int h = 1 << (v - LOGP);
-#pragma unroll
-            for (int m = 0; m < E; m++) {
-                if (m & h) continue;
-                u64 w, wsh;
-                twid(v, t + P * m, w, wsh);
-                ct_bfly(x[m], x[m + h], w, wsh, q, q2);
-            }
-        }
+        fwd_strided<LOG>(x, t, tw_, q, q2);
 #pragma unroll
         for (int m = 0; m < E; m++) sm[sidx(t + P * m)] = x[m];
         __syncthreads();
 #pragma unroll
         for (int m = 0; m < E; m++) x[m] = sm[sidx(t * E + m)];
-        // stages with span 2^v < P on the contiguous set {t E + m}
-#pragma unroll
-        for (int v = LOGP - 1; v >= 0; v--) {
-            const int h = 1 << v;
-#pragma unroll
-            for (int m = 0; m < E; m++) {
-                if (m & h) continue;
-                u64 w, wsh;
-                twid(v, t * E + m, w, wsh);
-                ct_bfly(x[m], x[m + h], w, wsh, q, q2);
-            }
-        }
+        fwd_contig<LOG>(x, t, tw_, q, q2);
         if (COL) {
             // column pass output stays in [0, 4q); coalesced over u
 #pragma unroll
             for (int m = 0; m < E; m++) g[(size_t)(t * E + m) * gs] = x[m];
         } else {
-            __syncthreads();
+            // each thread rewrites the slots it read, then the row leaves in the strided set
 #pragma unroll
             for (int m = 0; m < E; m++) sm[sidx(t * E + m)] = x[m];
             __syncthreads();
@@ -147,35 +93,13 @@ __global__ void __launch_bounds__(256, (LOG <= 8 && COL ? 3 : 2)) k_ntt_pass(Lim
             for (int m = 0; m < E; m++) x[m] = sm[sidx(t * E + m)];
             __syncthreads();
         }
-        // stages with span 2^v < P, v = 0 .. LOGP-1
-#pragma unroll
-        for (int v = 0; v < LOGP; v++) {
-            const int h = 1 << v;
-#pragma unroll
-            for (int m = 0; m < E; m++) {
-                if (m & h) continue;
-                u64 w, wsh;
-                twid(v, t * E + m, w, wsh);
-                gs_bfly(x[m], x[m + h], w, wsh, q, q2);
-            }
-        }
+        inv_contig<LOG>(x, t, tw_, q, q2);
 #pragma unroll
         for (int m = 0; m < E; m++) sm[sidx(t * E + m)] = x[m];
         __syncthreads();
 #pragma unroll
         for (int m = 0; m < E; m++) x[m] = sm[sidx(t + P * m)];
-        // stages with span 2^v >= P on the strided set {t + P m}
-#pragma unroll
-        for (int v = LOGP; v < LOG; v++) {
-            const int h = 1 << (v - LOGP);
-#pragma unroll
-            for (int m = 0; m < E; m++) {
-                if (m & h) continue;
-                u64 w, wsh;
-                twid(v, t + P * m, w, wsh);
-                gs_bfly(x[m], x[m + h], w, wsh, q, q2);
-            }
-        }
+        inv_strided<LOG>(x, t, tw_, q, q2);
         if (COL) {   // last inverse pass: times n^-1, result in [0, q)
 #pragma unroll
             for (int m = 0; m < E; m++) g[(size_t)(t + P * m) * gs] = shoup_mul(x[m], PC.ninv, PC.ninv_shoup, q);

@@ -130,6 +130,8 @@ struct SwitchKeyDev {
     u64* data = nullptr;  // [beta_L][2][L+1+alpha][n], evaluation domain, Montgomery form
 };
 
+struct rk_server;
+
 struct rk_ctx {
     rk_params prm{};
     int device = 0;
@@ -159,6 +161,9 @@ struct rk_ctx {
     u64* d_scratch = nullptr;
     size_t scratch_words = 0;
     int batch_cap = 1;            // largest stack B the scratch layout is sized for
+    rk_server* server = nullptr;  // serving loop, when one runs (it owns the stream meanwhile)
+    bool ks_fused = false;        // key switching with conversions fused into the NTT passes
+    double ks_group_bytes = 48.0 * (1 << 20);   // lifted digits kept in L2 between the fused kernels
     // plaintext caches: key = (kind, N, Q, n_real, level)
     std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint32_t, int>, u64*> plain_cache;
     std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint32_t>, std::vector<double>> encodings;

@@ -29,6 +29,8 @@ KEY_RELIN, KEY_GALOIS = 1, 2
 TIES_CORRECT = 1
 TIES_FIRST, TIES_ALL = 0, 2
 MASK_ROW0S, MASK_COL0S, MASK_TIEC, MASK_SORTIDX = 6, 7, 8, 9
+OPT_KS_FUSED, OPT_KS_GROUP_BYTES = 1, 2
+OP_RANK, OP_ORDER_STAT, OP_SORT, OP_RANK_BLOCKED = 1, 2, 3, 4
 
 
 class RkError(RuntimeError):
@@ -64,6 +66,7 @@ _sig("rk_ctx_moduli", [_vp, _u64p, _sz, ctypes.POINTER(_sz)])
 _sig("rk_ctx_scales", [_vp, _dp, _sz])
 _sig("rk_sync", [_vp])
 _sig("rk_ctx_counters", [_vp, _u64p])
+_sig("rk_ctx_set_option", [_vp, _u32, ctypes.c_int64])
 _sig("rk_keygen", [_vp, ctypes.c_uint64, _u32])
 _sig("rk_keygen_rotations", [_vp, _i32p, _sz])
 _sig("rk_secret_import", [_vp, _i64p, _sz])
@@ -96,6 +99,11 @@ _sig("rk_order_stat", [_vp, _vp, _u32, _u32, ctypes.POINTER(_vp)])
 _sig("rk_sort", [_vp, _vp, _u32, ctypes.POINTER(_vp)])
 _sig("rk_indicator_import", [_vp, _u32, _dp, _sz])
 _sig("rk_rank_batch", [_vp, ctypes.POINTER(_vp), _sz, _u32, ctypes.POINTER(_vp)])
+_sig("rk_server_start", [_vp, _sz, _u32])
+_sig("rk_server_submit", [_vp, _u32, _u32, _u32, _vp, ctypes.POINTER(ctypes.c_uint64)])
+_sig("rk_server_wait", [_vp, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(_vp)])
+_sig("rk_server_stats", [_vp, _dp])
+_sig("rk_server_stop", [_vp])
 _sig("rk_graph_rank", [_vp, _vp, _u32, ctypes.POINTER(_vp)])
 _sig("rk_graph_run", [_vp, _vp, ctypes.POINTER(_vp)])
 _sig("rk_graph_free", [_vp], None)
@@ -183,10 +191,13 @@ class Context:
         self.handle = h
         self.n = 1 << log_n
         self._live = weakref.WeakSet()
+        self._server_inputs = {}
 
     def close(self):
         """Free every ciphertext still alive, then the context."""
         if self.handle and self.handle.value:
+            _L.rk_server_stop(self.handle)   # a running server still reads its inputs
+            self._server_inputs = {}
             live = list(self._live)
             for obj in live:                 # graphs first: they hold captured buffers
                 if isinstance(obj, RankGraph):
@@ -223,6 +234,9 @@ class Context:
         out = (ctypes.c_uint64 * 4)()
         _check(_L.rk_ctx_counters(self.handle, out))
         return dict(zip(("key_switch", "rotate", "mul", "rescale"), [int(x) for x in out]))
+
+    def set_option(self, option: int, value: int):
+        _check(_L.rk_ctx_set_option(self.handle, option, int(value)))
 
     # ---- keys ----
     def keygen(self, seed: int, max_len: int):
@@ -350,6 +364,39 @@ class Context:
 
     def rank(self, ct, flags=0):
         return self._out(_L.rk_rank, ct.handle, flags)
+
+    # ---- serving loop ----
+    def server_start(self, mem_budget_bytes: int, max_stack: int = 32):
+        _check(_L.rk_server_start(self.handle, int(mem_budget_bytes), int(max_stack)))
+
+    def server_submit(self, op: int, ct: Ciphertext, arg: int = 0, flags: int = 0) -> int:
+        t = ctypes.c_uint64()
+        _check(_L.rk_server_submit(self.handle, op, int(arg), flags, ct.handle, ctypes.byref(t)))
+        self._server_inputs[int(t.value)] = ct       # borrowed until the result is collected
+        return int(t.value)
+
+    def server_wait(self, ticket: int, timeout_s: float = -1.0):
+        """The finished request's result, or None while it is pending after timeout_s."""
+        h = _vp()
+        try:
+            _check(_L.rk_server_wait(self.handle, ticket, float(timeout_s), ctypes.byref(h)))
+        except RkError:
+            self._server_inputs.pop(ticket, None)
+            raise
+        if not h.value:
+            return None
+        self._server_inputs.pop(ticket, None)
+        return Ciphertext(self, h.value)
+
+    def server_stats(self) -> dict:
+        out = (ctypes.c_double * 8)()
+        _check(_L.rk_server_stats(self.handle, out))
+        keys = ("finished", "p50_s", "p99_s", "max_s", "batches", "mean_batch", "peak_bytes", "queued")
+        return dict(zip(keys, list(out)))
+
+    def server_stop(self):
+        _check(_L.rk_server_stop(self.handle))
+        self._server_inputs = {}
 
     def graph_rank(self, template: Ciphertext, flags=0) -> RankGraph:
         """Capture rank(template-shaped input, flags) as one CUDA graph."""

@@ -1,0 +1,59 @@
+"""GPU: the fused key-switching path (conversions inside the NTT passes, inner
+product inside the row pass) against the staged one (lifted digits materialised),
+bit for bit, for rotations (single and hoisted), products, stacked ciphertexts and
+every L2 grouping of the lifted limbs.  Parity of either path with the oracle is
+covered by the rotation / product tests, which run the default (fused) path."""
+import numpy as np
+import pytest
+
+from paper_2412_15126_gb300 import inputs, rankfhe
+from tests import helpers
+
+pytestmark = pytest.mark.gpu
+
+
+def _run_ops(ctx, cts, rots):
+    outs = []
+    for ct in cts:
+        outs += [ctx.rotate(ct, r).export() for r in rots]
+        outs += [c.export() for c in ctx.rotate_many(ct, rots)]
+        outs.append(ctx.mul(ct, ct).export())
+    st = ctx.stack(cts)
+    for part in ctx.unstack(ctx.rotate(st, rots[0])):
+        outs.append(part.export())
+    for part in ctx.unstack(ctx.mul(st, st)):
+        outs.append(part.export())
+    return outs
+
+
+@pytest.mark.parametrize("name", ["small", "cfg1", "cfg2"])
+def test_fused_equals_staged(name):
+    ctx = helpers.gpu_context(name)
+    try:
+        N = 8
+        ctx.keygen(77, N)
+        rots = [1, 2, N, -1]
+        ctx.keygen_rotations(rots)
+        cts = [ctx.encrypt(inputs.gap_vector(N, 0.05, s), N=N) for s in (1, 2, 3)]
+        ctx.set_option(rankfhe.OPT_KS_FUSED, 0)
+        staged = _run_ops(ctx, cts, rots)
+        ctx.set_option(rankfhe.OPT_KS_FUSED, 1)
+        for group in (1, 3 << 20, 1 << 40):          # one limb a group .. every limb at once
+            ctx.set_option(rankfhe.OPT_KS_GROUP_BYTES, group)
+            fused = _run_ops(ctx, cts, rots)
+            assert len(fused) == len(staged)
+            for a, b in zip(fused, staged):
+                assert np.array_equal(a, b)
+    finally:
+        ctx.close()
+
+
+def test_set_option_rejects_unknown():
+    ctx = helpers.gpu_context("small")
+    try:
+        with pytest.raises(rankfhe.RkError):
+            ctx.set_option(99, 1)
+        with pytest.raises(rankfhe.RkError):
+            ctx.set_option(rankfhe.OPT_KS_GROUP_BYTES, -1)
+    finally:
+        ctx.close()
