@@ -75,10 +75,13 @@ typedef struct {
 #define RK_MASK_TIE   3u   /* 4*[j >= i] - 2 on each block (folded Alg. 6)             */
 #define RK_MASK_TRI   4u   /* [j >= i] on each block (Alg. 6 delta mask)               */
 #define RK_MASK_VALID 5u   /* 1 on rows and columns < n_real of each block (padding)   */
-#define RK_MASK_ROW0S 6u   /* 1/N on row 0 (MaskR that also divides ranks by N)        */
-#define RK_MASK_COL0S 7u   /* 1/N on column 0                                          */
+#define RK_MASK_ROW0S 6u   /* 1/D on row 0 (MaskR that also divides ranks by D); D is the
+                              n_real argument where one is given, else N              */
+#define RK_MASK_COL0S 7u   /* 1/D on column 0 (D as for RK_MASK_ROW0S)                 */
 #define RK_MASK_TIEC  8u   /* 4*[j <= i] - 2: column form of RK_MASK_TIE               */
 #define RK_MASK_SORTIDX 9u /* -(j+1)/N at row i, column j (Alg. 5 index constant / N)  */
+#define RK_MASK_ROWIDX 10u /* -(i+1)/D at row i (Alg. 8 offset less its block constant;
+                              D = n_real where given, else N)                          */
 
 /* Key kinds for rk_key_import. */
 #define RK_KEY_RELIN  1u
@@ -268,9 +271,26 @@ rk_status rk_sort(rk_ctx* ctx, const rk_ct* in, uint32_t flags, rk_ct** out);
  * blocks of B (a power of two with B^2 <= n/2), block i encrypted in row 0 of
  * blocks[i] (all at one level, unpadded).  outs[i] receives the fractional ranks of
  * block i's values among all L*B values, in row 0.  Only the L(L+1)/2 comparisons
- * C_{i,j}, j >= i, are evaluated (Eq. 3), as one stacked circuit.  flags must be 0.
- * Errors: RK_EDEPTH, RK_ENOKEY, RK_EINVAL. */
+ * C_{i,j}, j >= i, are evaluated (Eq. 3), as one stacked circuit.  flags: 0, or
+ * RK_TIES_CORRECT for the stable ranks (Alg. 6 across blocks: equal values count
+ * when they sit in an earlier block or at an earlier position of the same block;
+ * per block pair, the diagonal pair takes the folded offset, the others
+ * Cmp_G = 2C^2 - C or its complement).  Errors: RK_EDEPTH, RK_ENOKEY, RK_EINVAL. */
 rk_status rk_rank_blocked(rk_ctx* ctx, const rk_ct* const* blocks, uint32_t L, uint32_t flags, rk_ct** outs);
+
+/* Order statistic over a multi-ciphertext vector (Alg. 4 on the tie-corrected
+ * blocked ranks of rk_rank_blocked): outs[i] marks, in row 0, the element of block i
+ * whose stable rank is k (1 <= k <= L*B), one-hot over the whole vector.  The
+ * indicator is the sinc^2 window for the length L*B.  flags must be RK_TIES_FIRST.
+ * Errors as rk_rank_blocked. */
+rk_status rk_order_stat_blocked(rk_ctx* ctx, const rk_ct* const* blocks, uint32_t L, uint32_t k, uint32_t flags,
+                                rk_ct** outs);
+
+/* Multi-ciphertext sorting (Alg. 8) on the tie-corrected blocked ranks: outs[i]
+ * holds, in row 0, the values of ranks B i + 1 .. B (i + 1) in ascending order.
+ * The L^2 indicators run as stacked circuits, in chunks that bound the working
+ * set.  flags must be 0.  Errors as rk_rank_blocked. */
+rk_status rk_sort_blocked(rk_ctx* ctx, const rk_ct* const* blocks, uint32_t L, uint32_t flags, rk_ct** outs);
 
 /* Ranks of `count` ciphertexts (each its own query set).  Inputs of the same level
  * and vector shape are stacked and run as one circuit (one launch per kernel for
@@ -293,8 +313,10 @@ rk_status rk_rank_batch(rk_ctx* ctx, const rk_ct* const* in, size_t count, uint3
 #define RK_OP_RANK 1          /* rk_rank(in, flags) */
 #define RK_OP_ORDER_STAT 2    /* rk_order_stat(in, arg = k, flags) */
 #define RK_OP_SORT 3          /* rk_sort(in, flags) */
-#define RK_OP_RANK_BLOCKED 4  /* rk_rank_blocked on the blocks of a stack (rk_ct_stack);
+#define RK_OP_RANK_BLOCKED 4  /* rk_rank_blocked(blocks of a stack (rk_ct_stack), flags);
                                  the result is the stack of the rank blocks */
+#define RK_OP_ORDER_STAT_BLOCKED 5   /* rk_order_stat_blocked(blocks of a stack, arg = k) */
+#define RK_OP_SORT_BLOCKED 6  /* rk_sort_blocked(blocks of a stack) */
 rk_status rk_server_start(rk_ctx* ctx, size_t mem_budget_bytes, uint32_t max_stack);
 /* Queue a request; *ticket identifies it.  Errors: RK_EINVAL (no server, unknown op,
  * a stack where one ciphertext is expected, server stopping). */

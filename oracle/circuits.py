@@ -49,10 +49,12 @@ def mask_slots(kind: str, N: int, Q: int = 1, n_real: int | None = None, *, slot
         block = np.where(j >= i, 2.0, -2.0)
     elif kind == "tri":           # delta_{j>=i}: upper triangle with the diagonal (Alg. 6)
         block = (j >= i).astype(float)
-    elif kind == "row0s":         # MaskR(X, 0) scaled by 1/N: ranks leave SumR already divided by N
-        block[0, :] = 1.0 / N
-    elif kind == "col0s":         # MaskC(X, 0) scaled by 1/N
-        block[:, 0] = 1.0 / N
+    elif kind == "row0s":         # MaskR(X, 0) scaled by 1/D: ranks leave SumR already divided by D
+        block[0, :] = 1.0 / (N if n_real is None else n_real)     # D = the length ranks count
+    elif kind == "col0s":         # MaskC(X, 0) scaled by 1/D
+        block[:, 0] = 1.0 / (N if n_real is None else n_real)
+    elif kind == "rowidx":        # -(a+1)/D in row a: Alg. 8's offset, less its block's constant
+        block = -(i + 1.0) / (N if n_real is None else n_real)
     elif kind == "tiec":          # column form of "tie": 4*delta_{j<=i} - 2
         block = np.where(j <= i, 2.0, -2.0)
     elif kind == "sortidx":       # -(j+1)/N: column j of the sorting mask selects rank j+1 (Alg. 5)
@@ -367,6 +369,82 @@ def rank_blocked(B, Vs, Bsz, dg, df, Q=1):
         else:
             R = B.level_down(S, B.level(S) - 1)
         out.append(B.add_const(R, 0.5))
+    return out
+
+
+def cmp_strict(B, C):
+    """Cmp_G = 2 C^2 - C: 1 where v_j > v_i, 0 at ties (Sec. 3.2, Min and Max)."""
+    C2 = B.mul(C, C)
+    return B.sub(B.add(C2, C2), B.level_down(C, B.level(C2)))
+
+
+def rank_blocked_tc(B, Vs, Bsz, dg, df, Q=1, scaled=False):
+    """Tie-corrected multi-ciphertext ranking (Alg. 7 with Alg. 6): the rank of element
+    b of block i counts the smaller elements and the equal ones at or before it in the
+    global order (block i, position b).  Per block pair (Eq. 3 for j < i):
+        j = i:  SumR(C_ii + E_ii (delta_{a<=b} - 1/2))  (the single-ciphertext fold)
+        j > i:  SumR(G_ij)                 G = 2C^2 - C, strictly smaller elements of block j
+        j < i:  TransC(SumC(1 - G_ji))     elements of block j not larger (all earlier ties count)
+    scaled: every rank leaves divided by the total length D = L Bsz (masks 'row0s' with
+    denominator D), the form the indicator of Alg. 4 and 8 takes.
+    Returns the rank blocks (all at one level) and the ReplR forms of the blocks."""
+    L = len(Vs)
+    D = L * Bsz
+    forms = [row_col_forms(B, V, Bsz, Q) for V in Vs]
+    Cs = {}
+    for i in range(L):
+        for j in range(i, L):
+            Cs[(i, j)] = cmp(B, B.sub(forms[i][0], forms[j][1]), dg, df)
+    Gs = {(i, j): cmp_strict(B, Cs[(i, j)]) for i in range(L) for j in range(i + 1, L)}
+    rmask = ("row0s", Bsz, Q, D) if scaled else ("row0", Bsz, Q)
+    out = []
+    for i in range(L):
+        A = tie_fold(B, Cs[(i, i)], Bsz, Q, "tie")
+        for j in range(i + 1, L):
+            A = B.add(A, B.level_down(Gs[(i, j)], B.level(A)))
+        for r in range(log2_exact(Bsz)):
+            A = B.add(A, B.rot(A, Bsz << r))
+        S = B.mul_plain(A, rmask)
+        if i > 0:
+            Bs = Gs[(0, i)]
+            for j in range(1, i):
+                Bs = B.add(Bs, Gs[(j, i)])
+            T = sum_c(B, B.add_const(B.neg(Bs), float(i)), Bsz, Q)
+            for r in range(1, log2_exact(Bsz) + 1):
+                T = B.add(T, B.rot(T, (Bsz * (Bsz - 1)) >> r))
+            T = B.mul_plain(T, rmask)
+            S = B.add(S, B.level_down(T, B.level(S)))
+        out.append(S)
+    return out, [f[0] for f in forms]
+
+
+def order_statistic_blocked(B, Vs, Bsz, k, dg, df, Q=1, coeffs=None):
+    """Alg. 4 over a multi-ciphertext vector: O_i = Ind_k(R_i) on the tie-corrected
+    block ranks, one-hot at the first element of global rank k."""
+    D = len(Vs) * Bsz
+    coeffs = sinc2_window_coeffs(D) if coeffs is None else coeffs
+    Rs, _ = rank_blocked_tc(B, Vs, Bsz, dg, df, Q, scaled=True)
+    return [cheb_ps(B, B.add_const(R, -k / D), coeffs) for R in Rs]
+
+
+def sort_blocked(B, Vs, Bsz, dg, df, Q=1, coeffs=None):
+    """Alg. 8 (multi-ciphertext sorting) on tie-corrected ranks:
+        S_i = TransC(SumC(sum_j Ind_0(ReplR(R_j) - offset_i) . ReplR(V_j)))
+    offset_i holds B i + a + 1 in row a (0-based block i): mask 'rowidx' plus the
+    constant -B i / D, with ranks and offsets divided by D = L B."""
+    L = len(Vs)
+    D = L * Bsz
+    coeffs = sinc2_window_coeffs(D) if coeffs is None else coeffs
+    Rs, VRs = rank_blocked_tc(B, Vs, Bsz, dg, df, Q, scaled=True)
+    RR = [B.add_plain(repl_r(B, R, Bsz), ("rowidx", Bsz, Q, D)) for R in Rs]
+    out = []
+    for i in range(L):
+        acc = None
+        for j in range(L):
+            M = cheb_ps(B, B.add_const(RR[j], -Bsz * i / D), coeffs)
+            P = B.mul(M, B.level_down(VRs[j], B.level(M)))
+            acc = P if acc is None else B.add(acc, P)
+        out.append(trans_c(B, sum_c(B, acc, Bsz, Q), Bsz, Q))
     return out
 
 

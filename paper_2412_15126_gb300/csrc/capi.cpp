@@ -13,6 +13,9 @@ rk_ct* circuit_order_stat(rk_ctx* c, const rk_ct* in, uint32_t k, uint32_t flags
 rk_ct* circuit_sort(rk_ctx* c, const rk_ct* in, uint32_t flags);
 void indicator_import(rk_ctx* c, uint32_t N, const double* coeffs, size_t count);
 void circuit_rank_blocked(rk_ctx* c, const rk_ct* const* blocks, int L, rk_ct** outs);
+void circuit_rank_blocked_tc(rk_ctx* c, const rk_ct* const* blocks, int L, rk_ct** outs);
+void circuit_order_stat_blocked(rk_ctx* c, const rk_ct* const* blocks, int L, uint32_t k, rk_ct** outs);
+void circuit_sort_blocked(rk_ctx* c, const rk_ct* const* blocks, int L, rk_ct** outs);
 rk_graph* graph_rank_capture(rk_ctx* c, const rk_ct* tmpl, uint32_t flags);
 rk_server* server_start(rk_ctx* c, size_t budget, int max_stack);
 uint64_t server_submit(rk_ctx* c, uint32_t op, uint32_t arg, uint32_t flags, const rk_ct* in);
@@ -185,7 +188,7 @@ rk_status rk_encoding_import(rk_ctx* ctx, uint32_t kind, uint32_t N, uint32_t Q,
         need(ctx, "ctx");
         need(u, "u");
         RK_REQUIRE(n == (size_t)ctx->n, RK_EINVAL, "encoding length must be n");
-        RK_REQUIRE(kind >= RK_MASK_ROW0 && kind <= RK_MASK_SORTIDX, RK_EINVAL, "unknown mask kind");
+        RK_REQUIRE(kind >= RK_MASK_ROW0 && kind <= RK_MASK_ROWIDX, RK_EINVAL, "unknown mask kind");
         const uint32_t nr = kind == RK_MASK_VALID ? n_real : 0;
         ctx->encodings[std::make_tuple(kind, N, Q, nr)] = std::vector<double>(u, u + n);
         for (auto it = ctx->plain_cache.begin(); it != ctx->plain_cache.end();) {
@@ -353,7 +356,7 @@ rk_status rk_mul_scalar(rk_ctx* ctx, const rk_ct* a, double v, rk_ct** out) {
 
 rk_status rk_mul_mask(rk_ctx* ctx, const rk_ct* a, uint32_t kind, rk_ct** out) {
     return guard([&] {
-        RK_REQUIRE(kind >= RK_MASK_ROW0 && kind <= RK_MASK_SORTIDX, RK_EINVAL, "unknown mask kind");
+        RK_REQUIRE(kind >= RK_MASK_ROW0 && kind <= RK_MASK_ROWIDX, RK_EINVAL, "unknown mask kind");
         RK_UNARY_OUT(ctx, a, out, a->level,
                      ev_mul_plain(ctx, a, kind, a->N, a->Q, kind == RK_MASK_VALID ? a->n_real : 0, o))
     });
@@ -466,10 +469,40 @@ rk_status rk_rank_blocked(rk_ctx* ctx, const rk_ct* const* blocks, uint32_t L, u
         need(ctx, "ctx");
         need(blocks, "blocks");
         need(outs, "outs");
-        RK_REQUIRE(flags == 0, RK_EINVAL, "blocked rank takes no flags");
+        RK_REQUIRE(flags == 0 || flags == RK_TIES_CORRECT, RK_EINVAL, "blocked rank flags: 0 or RK_TIES_CORRECT");
         for (uint32_t i = 0; i < L; i++) same_ctx(ctx, blocks[i]);
         set_device(ctx);
-        circuit_rank_blocked(ctx, blocks, (int)L, outs);
+        if (flags & RK_TIES_CORRECT)
+            circuit_rank_blocked_tc(ctx, blocks, (int)L, outs);
+        else
+            circuit_rank_blocked(ctx, blocks, (int)L, outs);
+        check_launch();
+    });
+}
+
+rk_status rk_order_stat_blocked(rk_ctx* ctx, const rk_ct* const* blocks, uint32_t L, uint32_t k, uint32_t flags,
+                                rk_ct** outs) {
+    return guard([&] {
+        need(ctx, "ctx");
+        need(blocks, "blocks");
+        need(outs, "outs");
+        RK_REQUIRE(flags == RK_TIES_FIRST, RK_EINVAL, "blocked order statistic takes RK_TIES_FIRST only");
+        for (uint32_t i = 0; i < L; i++) same_ctx(ctx, blocks[i]);
+        set_device(ctx);
+        circuit_order_stat_blocked(ctx, blocks, (int)L, k, outs);
+        check_launch();
+    });
+}
+
+rk_status rk_sort_blocked(rk_ctx* ctx, const rk_ct* const* blocks, uint32_t L, uint32_t flags, rk_ct** outs) {
+    return guard([&] {
+        need(ctx, "ctx");
+        need(blocks, "blocks");
+        need(outs, "outs");
+        RK_REQUIRE(flags == 0, RK_EINVAL, "blocked sort takes no flags");
+        for (uint32_t i = 0; i < L; i++) same_ctx(ctx, blocks[i]);
+        set_device(ctx);
+        circuit_sort_blocked(ctx, blocks, (int)L, outs);
         check_launch();
     });
 }

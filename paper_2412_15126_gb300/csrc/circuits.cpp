@@ -14,6 +14,7 @@ void mask_slot_values(uint32_t kind, uint32_t N, uint32_t Q, uint32_t n_real, si
     RK_REQUIRE((size_t)Q * N * N <= slots, RK_EINVAL, "mask does not fit the slots");
     v.assign(slots, 0.0);
     const uint32_t m = (kind == RK_MASK_VALID && n_real) ? n_real : N;
+    const double D = n_real ? (double)n_real : (double)N;   // denominator of the scaled kinds
     for (uint32_t q = 0; q < Q; q++)
         for (uint32_t i = 0; i < N; i++)
             for (uint32_t j = 0; j < N; j++) {
@@ -24,10 +25,11 @@ void mask_slot_values(uint32_t kind, uint32_t N, uint32_t Q, uint32_t n_real, si
                     case RK_MASK_TIE: x = j >= i ? 2.0 : -2.0; break;
                     case RK_MASK_TRI: x = j >= i ? 1.0 : 0.0; break;
                     case RK_MASK_VALID: x = (i < m && j < m) ? 1.0 : 0.0; break;
-                    case RK_MASK_ROW0S: x = i == 0 ? 1.0 / N : 0.0; break;
-                    case RK_MASK_COL0S: x = j == 0 ? 1.0 / N : 0.0; break;
+                    case RK_MASK_ROW0S: x = i == 0 ? 1.0 / D : 0.0; break;
+                    case RK_MASK_COL0S: x = j == 0 ? 1.0 / D : 0.0; break;
                     case RK_MASK_TIEC: x = j <= i ? 2.0 : -2.0; break;
                     case RK_MASK_SORTIDX: x = -(j + 1.0) / N; break;
+                    case RK_MASK_ROWIDX: x = -(i + 1.0) / D; break;
                     default: throw rk_error(RK_EINVAL, "unknown mask kind");
                 }
                 v[(size_t)q * N * N + (size_t)i * N + j] = x;
@@ -108,6 +110,21 @@ struct Ev {
         H o = fresh(x, x->level);
         const uint32_t nr = kind == RK_MASK_VALID ? x->n_real : 0;
         ev_mul_plain(c, x.p, kind, x->N, x->Q, nr, o.p);
+        return o;
+    }
+    H mul_mask_d(const H& x, uint32_t kind, uint32_t D) {   // scaled kinds with denominator D
+        H o = fresh(x, x->level);
+        ev_mul_plain(c, x.p, kind, x->N, x->Q, D, o.p);
+        return o;
+    }
+    H add_mask_d(const H& x, uint32_t kind, uint32_t D) {
+        H o = fresh(x, x->level);
+        ev_add_plain(c, x.p, kind, x->N, x->Q, D, o.p);
+        return o;
+    }
+    H neg(const H& x) {
+        H o = fresh(x, x->level);
+        ev_neg(c, x.p, o.p);
         return o;
     }
     H add_const(const H& x, double v) {
@@ -517,6 +534,187 @@ void circuit_rank_blocked(rk_ctx* c, const rk_ct* const* blocks, int L, rk_ct** 
         throw;
     }
     for (int i = 0; i < L; i++) outs[i] = res[i];
+}
+
+// 2 C^2 - C: 1 where the row-form value exceeds the column-form value, 0 at ties
+// (Cmp_G of Sec. 3.2).
+static H cmp_strict(Ev& E, const H& C) {
+    H C2 = E.mul(C, C);
+    return E.sub(E.add(C2, C2), E.level_down(C, C2->level));
+}
+
+// ReplR (Alg. 10): X <- X + (X >> N 2^i)
+static H repl_r(Ev& E, H x) {
+    const int N = (int)x->N, k = log2_exact(x->N);
+    for (int i = 0; i < k; i++) x = E.add(x, E.rot(x, -(N << i)));
+    return x;
+}
+
+static void check_blocks(rk_ctx* c, const rk_ct* const* blocks, int L, int need, const char* what) {
+    RK_REQUIRE(L >= 1, RK_EINVAL, "no blocks");
+    const rk_ct* b0 = blocks[0];
+    for (int i = 0; i < L; i++)
+        RK_REQUIRE(blocks[i]->B == 1 && blocks[i]->level == b0->level && blocks[i]->N == b0->N && blocks[i]->Q == b0->Q &&
+                       blocks[i]->n_real == b0->N,
+                   RK_EINVAL, "blocks must be single, unpadded ciphertexts of one level and length");
+    check_square(c, b0, need, what);
+}
+
+static int blocked_rank_tc_depth(const rk_ctx* c) { return 1 + 3 * (int)(c->prm.d_g + c->prm.d_f) + 3; }
+
+// Tie-corrected ranks of a multi-ciphertext vector (Alg. 7 with Alg. 6 across blocks).
+// The rank of element b of block i counts the smaller values and the equal values at
+// an earlier global position (earlier block, or same block and position <= b):
+//   pair j = i:  SumR(C_ii + E_ii (delta - 1/2))   (the folded single-block offset)
+//   pair j > i:  SumR(G_ij),  G = 2C^2 - C        (strictly smaller values of block j)
+//   pair j < i:  TransC(SumC(1 - G_ji))           (values of block j not larger, Eq. 3)
+// The diagonal and the upper pairs each run as one stack.  `scaled` divides every rank
+// by D = L B in the row masks.  Returns the stack of the L rank blocks and the stack
+// of the blocks' ReplR forms.
+static std::pair<H, H> blocked_ranks_tc(rk_ctx* c, const rk_ct* const* blocks, int L, bool scaled) {
+    Ev E{c};
+    const int Bsz = (int)blocks[0]->N, dg = (int)c->prm.d_g, df = (int)c->prm.d_f;
+    const uint32_t Dn = scaled ? (uint32_t)(L * Bsz) : 0u;
+    const uint32_t rmask = scaled ? RK_MASK_ROW0S : RK_MASK_ROW0;
+    H V(ct_stack(c, blocks, L));
+    auto rc = row_col_forms(E, V);   // stacks of L
+    std::vector<H> views;
+    std::vector<rk_ct*> dr, dcol, ur, uc;
+    std::map<std::pair<int, int>, int> uidx;
+    for (int i = 0; i < L; i++) {
+        views.emplace_back(ct_view(rc.first.p, i));
+        dr.push_back(views.back().p);
+        views.emplace_back(ct_view(rc.second.p, i));
+        dcol.push_back(views.back().p);
+    }
+    for (int i = 0; i < L; i++)
+        for (int j = i + 1; j < L; j++) {
+            uidx[{i, j}] = (int)ur.size();
+            ur.push_back(dr[i]);
+            uc.push_back(dcol[j]);
+        }
+    H F = tie_fold(E, cmp(E, E.sub(stack_of(c, dr), stack_of(c, dcol)), dg, df), RK_MASK_TIE);
+    H G, Gd;
+    if (L > 1) {
+        G = cmp_strict(E, cmp(E, E.sub(stack_of(c, ur), stack_of(c, uc)), dg, df));
+        Gd = E.level_down(G, F->level);
+    }
+    std::vector<H> A, Bm;
+    for (int i = 0; i < L; i++) {
+        H a = E.copy(H(ct_view(F.p, i)));
+        for (int j = i + 1; j < L; j++) a = E.add(a, H(ct_view(Gd.p, uidx[{i, j}])));
+        A.push_back(std::move(a));
+        if (i > 0) {
+            H s = E.copy(H(ct_view(G.p, uidx[{0, i}])));
+            for (int j = 1; j < i; j++) s = E.add(s, H(ct_view(G.p, uidx[{j, i}])));
+            Bm.push_back(E.add_const(E.neg(s), (double)i));
+        }
+    }
+    std::vector<rk_ct*> ap;
+    for (auto& a : A) ap.push_back(a.p);
+    H S = stack_of(c, ap);
+    {
+        const int k = log2_exact((uint32_t)Bsz);
+        for (int r = 0; r < k; r++) S = E.add(S, E.rot(S, Bsz << r));
+        S = E.mul_mask_d(S, rmask, Dn);
+    }
+    if (L == 1) return std::make_pair(std::move(S), std::move(rc.first));
+    std::vector<rk_ct*> bp;
+    for (auto& b : Bm) bp.push_back(b.p);
+    H T = sum_cols(E, stack_of(c, bp), RK_MASK_COL0);   // stack of L - 1
+    {
+        const int k = log2_exact((uint32_t)Bsz);
+        for (int r = 1; r <= k; r++) T = E.add(T, E.rot(T, (Bsz * (Bsz - 1)) >> r));
+        T = E.mul_mask_d(T, rmask, Dn);
+    }
+    std::vector<H> R;
+    std::vector<rk_ct*> rp;
+    for (int i = 0; i < L; i++) {
+        H si(ct_view(S.p, i));
+        if (i == 0) {
+            R.push_back(E.copy(si));
+        } else {
+            H ti(ct_view(T.p, i - 1));
+            R.push_back(E.add(si, E.level_down(ti, si->level)));
+        }
+        rp.push_back(R.back().p);
+    }
+    return std::make_pair(stack_of(c, rp), std::move(rc.first));
+}
+
+static void unstack_to(rk_ctx* c, const H& st, rk_ct** outs) {
+    std::vector<rk_ct*> parts(st->B, nullptr);
+    ct_unstack(c, st.p, parts.data());
+    for (int i = 0; i < st->B; i++) outs[i] = parts[i];
+}
+
+void circuit_rank_blocked_tc(rk_ctx* c, const rk_ct* const* blocks, int L, rk_ct** outs) {
+    check_blocks(c, blocks, L, blocked_rank_tc_depth(c), "blocked rank");
+    auto rr = blocked_ranks_tc(c, blocks, L, false);
+    unstack_to(c, rr.first, outs);
+}
+
+// Alg. 4 on the tie-corrected blocked ranks: O_i = Ind_k(R_i), the indicator the
+// sinc^2 window for the whole length D = L B; the L blocks run as one stack.
+void circuit_order_stat_blocked(rk_ctx* c, const rk_ct* const* blocks, int L, uint32_t k, rk_ct** outs) {
+    RK_REQUIRE(L >= 1, RK_EINVAL, "no blocks");
+    const uint32_t D = (uint32_t)L * blocks[0]->N;
+    RK_REQUIRE(k >= 1 && k <= D, RK_EINVAL, "k must be in [1, L B]");
+    const auto& co = indicator_coeffs(c, D);
+    check_blocks(c, blocks, L, blocked_rank_tc_depth(c) + cheb_depth((int)co.size()), "blocked order statistic");
+    auto rr = blocked_ranks_tc(c, blocks, L, true);
+    Ev E{c};
+    H O = cheb_ps(E, E.add_const(rr.first, -(double)k / D), co);
+    unstack_to(c, O, outs);
+}
+
+// Alg. 8 on the tie-corrected blocked ranks:
+//   S_i = TransC(SumC(sum_j Ind_0(ReplR(R_j) - offset_i) . ReplR(V_j)))
+// offset_i holds B i + a + 1 in row a: the mask RK_MASK_ROWIDX plus the constant
+// -B i / D (ranks and offsets divided by D = L B).  The L^2 indicators run as stacks of
+// at most `chunk` members so that the Paterson-Stockmeyer working set stays bounded.
+void circuit_sort_blocked(rk_ctx* c, const rk_ct* const* blocks, int L, rk_ct** outs) {
+    RK_REQUIRE(L >= 1, RK_EINVAL, "no blocks");
+    const int Bsz = (int)blocks[0]->N;
+    const uint32_t D = (uint32_t)(L * Bsz);
+    const auto& co = indicator_coeffs(c, D);
+    check_blocks(c, blocks, L, blocked_rank_tc_depth(c) + cheb_depth((int)co.size()) + 3, "blocked sort");
+    auto rr = blocked_ranks_tc(c, blocks, L, true);
+    Ev E{c};
+    H RR = E.add_mask_d(repl_r(E, std::move(rr.first)), RK_MASK_ROWIDX, D);   // stack of L
+    const size_t ct_bytes = (size_t)2 * (RR->level + 1) * c->n * 8;
+    const size_t live = (size_t)baby_steps((int)co.size()) + 2 * (size_t)cheb_depth((int)co.size()) + 8;
+    const int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)L * L, c->ind_stack_bytes / (live * ct_bytes)));
+    std::vector<H> acc(L);
+    std::vector<std::pair<int, int>> pairs;
+    for (int i = 0; i < L; i++)
+        for (int j = 0; j < L; j++) pairs.push_back({i, j});
+    for (size_t p0 = 0; p0 < pairs.size(); p0 += chunk) {
+        const size_t p1 = std::min(pairs.size(), p0 + chunk);
+        std::vector<H> in, vr;
+        std::vector<rk_ct*> ip;
+        for (size_t p = p0; p < p1; p++) {
+            in.push_back(E.add_const(H(ct_view(RR.p, pairs[p].second)), -(double)Bsz * pairs[p].first / D));
+            ip.push_back(in.back().p);
+        }
+        H M = cheb_ps(E, stack_of(c, ip), co);
+        in.clear();
+        std::vector<rk_ct*> vp;
+        for (size_t p = p0; p < p1; p++) {
+            vr.push_back(E.level_down(H(ct_view(rr.second.p, pairs[p].second)), M->level));
+            vp.push_back(vr.back().p);
+        }
+        H P = E.mul(M, stack_of(c, vp));
+        for (size_t p = p0; p < p1; p++) {
+            H pm(ct_view(P.p, (int)(p - p0)));
+            const int i = pairs[p].first;
+            acc[i] = acc[i].p ? E.add(acc[i], pm) : E.copy(pm);
+        }
+    }
+    std::vector<rk_ct*> ap;
+    for (auto& a : acc) ap.push_back(a.p);
+    H S = trans_c(E, sum_cols(E, stack_of(c, ap), RK_MASK_COL0));
+    unstack_to(c, S, outs);
 }
 
 rk_ct* circuit_compare_matrix(rk_ctx* c, const rk_ct* in) {

@@ -200,7 +200,7 @@ void ctx_build(rk_ctx* c, const rk_params* p, int device, void* stream) {
     RK_CUDA(cudaMalloc((void**)&c->d_pc, NP * sizeof(PrimeConst)));
     RK_CUDA(cudaMemcpy(c->d_pc, c->h_pc.data(), NP * sizeof(PrimeConst), cudaMemcpyHostToDevice));
 
-    // ---- twiddles: psi^brev(i), psi^-brev(i) and Shoup companions ----
+    // ---- twiddles: (psi^brev(i), Shoup companion) and (psi^-brev(i), companion) pairs ----
     std::vector<u64> tw((size_t)4 * NP * n);
     for (int i = 0; i < NP; i++) {
         u64 qi = c->primes[i];
@@ -211,16 +211,14 @@ void ctx_build(rk_ctx* c, const rk_params* p, int device, void* stream) {
             pw[k] = h_mulmod(pw[k - 1], psi, qi);
             ipw[k] = h_mulmod(ipw[k - 1], ipsi, qi);
         }
-        u64* T0 = tw.data() + ((size_t)0 * NP + i) * n;
-        u64* T1 = tw.data() + ((size_t)1 * NP + i) * n;
-        u64* T2 = tw.data() + ((size_t)2 * NP + i) * n;
-        u64* T3 = tw.data() + ((size_t)3 * NP + i) * n;
+        u64* F = tw.data() + (size_t)i * 2 * n;              // forward pairs
+        u64* I = tw.data() + ((size_t)NP + i) * 2 * n;       // inverse pairs
         for (int k = 0; k < n; k++) {
             int r = bitrev(k, c->log_n);
-            T0[k] = pw[r];
-            T1[k] = shoup_of(pw[r], qi);
-            T2[k] = ipw[r];
-            T3[k] = shoup_of(ipw[r], qi);
+            F[2 * k] = pw[r];
+            F[2 * k + 1] = shoup_of(pw[r], qi);
+            I[2 * k] = ipw[r];
+            I[2 * k + 1] = shoup_of(ipw[r], qi);
         }
     }
     RK_CUDA(cudaMalloc((void**)&c->d_tw, tw.size() * 8));
@@ -314,9 +312,7 @@ void ctx_build(rk_ctx* c, const rk_params* p, int device, void* stream) {
     e.alpha = A;
     e.pc = c->d_pc;
     e.tw.psi = c->d_tw;
-    e.tw.psi_sh = c->d_tw + (size_t)1 * NP * n;
     e.tw.ipsi = c->d_tw + (size_t)2 * NP * n;
-    e.tw.ipsi_sh = c->d_tw + (size_t)3 * NP * n;
     e.conv.modup = c->d_conv + mu_off;
     e.conv.modup_stride = mu_stride;
     e.conv.beta_max = beta_max;
@@ -325,6 +321,8 @@ void ctx_build(rk_ctx* c, const rk_params* p, int device, void* stream) {
     e.conv.pinv = c->d_conv + pi_off;
     e.conv.rescale = c->d_conv + rs_off;
     e.prof = &c->prof;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) == cudaSuccess && sms > 0) e.sms = sms;
     ntt_init_attributes();
     ks_fused_init_attributes();
 }

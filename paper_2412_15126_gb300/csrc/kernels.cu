@@ -134,36 +134,61 @@ void launch_tensor(const KernelEnv& env, u64* d, const u64* x, const u64* y, int
 // ModUp of every digit: ext[j][t][k], t over Q_l u P (QP limb order).
 // The digit's own limbs are copied from the evaluation-domain input x_eval (the
 // conversion reproduces them exactly), so the following NTT can skip them.
+// Each thread converts CONV_EL coefficients (k0 + e TPB) so that every conversion
+// constant, staged in shared memory, serves CONV_EL products.
+#define CONV_EL 4
+template <int DS>
 __global__ void __launch_bounds__(TPB) k_modup(const u64* __restrict__ x, const u64* __restrict__ x_eval, u64* __restrict__ ext,
                                                size_t ext_stride, int level, int L, int alpha, ConvTables cv, int n,
                                                const PrimeConst* __restrict__ pc) {
-    const int k = blockIdx.x * TPB + threadIdx.x, j = blockIdx.y;
-    const int DS = cv.dsize;
+    __shared__ u64 s_c[DS * RK_MAX_PRIMES];             // (D/q_i) R mod prime(t), [i][t]
+    __shared__ u64 s_q[RK_MAX_PRIMES], s_qinv[RK_MAX_PRIMES];
+    const int j = blockIdx.y;
     const int lo = j * DS, hi = min(lo + DS, level + 1), ns = hi - lo;
     const u64* tab = cv.modup + ((size_t)level * cv.beta_max + j) * cv.modup_stride;
     const int T = L + 1 + alpha;
-    u64 y[RK_MAX_DIGIT];
+    const int limbs = level + 1 + alpha;
+    for (int idx = threadIdx.x; idx < ns * limbs; idx += TPB) {
+        const int i = idx / limbs, t = idx - i * limbs;
+        s_c[i * RK_MAX_PRIMES + t] = tab[2 * DS + (size_t)i * T + t];
+    }
+    for (int t = threadIdx.x; t < limbs; t += TPB) {
+        const int pid = t <= level ? t : L + 1 + (t - level - 1);
+        s_q[t] = pc[pid].q;
+        s_qinv[t] = pc[pid].qinv;
+    }
+    __syncthreads();
+    const int k0 = blockIdx.x * (TPB * CONV_EL) + threadIdx.x;
+    u64 y[CONV_EL][DS];
 #pragma unroll
-    for (int i = 0; i < RK_MAX_DIGIT; i++) {
+    for (int i = 0; i < DS; i++) {
         if (i < ns) {
-            const u64 qi = pc[lo + i].q;
-            y[i] = shoup_mul(x[(size_t)(lo + i) * n + k], tab[i], tab[DS + i], qi);
+            const u64 qi = pc[lo + i].q, w = tab[i], wsh = tab[DS + i];
+            const u64* xi = x + (size_t)(lo + i) * n + k0;
+#pragma unroll
+            for (int e = 0; e < CONV_EL; e++) y[e][i] = shoup_mul(xi[e * TPB], w, wsh, qi);
         }
     }
-    const int limbs = level + 1 + alpha;
-    u64* out = ext + (size_t)j * ext_stride + k;
     for (int t = 0; t < limbs; t++) {
+        u64* out = ext + (size_t)j * ext_stride + (size_t)t * n + k0;
         if (t >= lo && t < hi) {
-            out[(size_t)t * n] = x_eval[(size_t)t * n + k];
+            const u64* xe = x_eval + (size_t)t * n + k0;
+#pragma unroll
+            for (int e = 0; e < CONV_EL; e++) out[e * TPB] = xe[e * TPB];
             continue;
         }
-        const int pid = t <= level ? t : L + 1 + (t - level - 1);
-        const PrimeConst P = pc[pid];
-        Acc128 acc;
+        Acc128 acc[CONV_EL];
 #pragma unroll
-        for (int i = 0; i < RK_MAX_DIGIT; i++)
-            if (i < ns) acc.mac(y[i], __ldg(tab + 2 * DS + (size_t)i * T + t));
-        out[(size_t)t * n] = acc.redc(P.q, P.qinv);
+        for (int i = 0; i < DS; i++) {
+            if (i < ns) {
+                const u64 cst = s_c[i * RK_MAX_PRIMES + t];
+#pragma unroll
+                for (int e = 0; e < CONV_EL; e++) acc[e].mac(y[e][i], cst);
+            }
+        }
+        const u64 q = s_q[t], qinv = s_qinv[t];
+#pragma unroll
+        for (int e = 0; e < CONV_EL; e++) out[e * TPB] = acc[e].redc(q, qinv);
     }
 }
 
@@ -173,50 +198,92 @@ void launch_modup(const KernelEnv& env, const u64* x, const u64* x_eval, size_t 
                   int level, int beta, cudaStream_t st, int B) {
     ProfScope pf(env, KK_MODUP, st, B, B * (2.0 * (level + 1) + (double)beta * (level + 1 + env.alpha)) * 8.0 * env.n,
                  (double)B * (level + 1 + env.alpha) * (level + 1) * env.n);
-    dim3 g(env.n / TPB, beta);
-    for (int b = 0; b < B; b++)
-        k_modup<<<g, TPB, 0, st>>>(x + (size_t)b * (level + 1) * env.n, x_eval + (size_t)b * eval_stride,
-                                   ext + (size_t)b * beta * ext_stride, ext_stride, level, env.L, env.alpha, env.conv, env.n, env.pc);
+    dim3 g(env.n / (TPB * CONV_EL), beta);
+    for (int b = 0; b < B; b++) {
+        const u64* xb = x + (size_t)b * (level + 1) * env.n;
+        const u64* eb = x_eval + (size_t)b * eval_stride;
+        u64* ob = ext + (size_t)b * beta * ext_stride;
+        switch (env.conv.dsize) {
+#define RK_MODUP_CASE(D)                                                                                                 \
+    case D:                                                                                                              \
+        k_modup<D><<<g, TPB, 0, st>>>(xb, eb, ob, ext_stride, level, env.L, env.alpha, env.conv, env.n, env.pc);        \
+        break;
+            RK_MODUP_CASE(1) RK_MODUP_CASE(2) RK_MODUP_CASE(3) RK_MODUP_CASE(4)
+            RK_MODUP_CASE(5) RK_MODUP_CASE(6) RK_MODUP_CASE(7) RK_MODUP_CASE(8)
+#undef RK_MODUP_CASE
+            default: throw rk_error(RK_EINVAL, "digit size out of range");
+        }
+    }
 }
 
 // ModDown conversion of the P part of u ([2][l+1+alpha][n], P limbs already in the
-// coefficient domain) to w = [2][l+1][n].
-__global__ void __launch_bounds__(TPB) k_moddown_conv(const u64* __restrict__ u, u64* __restrict__ w, int level, int L, int alpha,
+// coefficient domain) to w = [2][l+1][n]; CONV_EL coefficients a thread.
+template <int A>
+__global__ void __launch_bounds__(TPB) k_moddown_conv(const u64* __restrict__ u, u64* __restrict__ w, int level, int L,
                                                       ConvTables cv, int n, const PrimeConst* __restrict__ pc) {
-    const int k = blockIdx.x * TPB + threadIdx.x, c = blockIdx.y;
-    const int ul = level + 1 + alpha;
-    const u64* up = u + (size_t)c * ul * n + (size_t)(level + 1) * n + k;
+    __shared__ u64 s_c[A * RK_MAX_PRIMES];      // (P/p_k) R mod q_i, [k][i]
+    __shared__ u64 s_q[RK_MAX_PRIMES], s_qinv[RK_MAX_PRIMES], s_pm[RK_MAX_PRIMES];
+    const int c = blockIdx.y;
+    const u64* cm = cv.moddown + 2 * A;
+    const u64* pmod = cm + (size_t)A * (L + 1);
+    for (int idx = threadIdx.x; idx < A * (level + 1); idx += TPB) {
+        const int kk = idx / (level + 1), i = idx - kk * (level + 1);
+        s_c[kk * RK_MAX_PRIMES + i] = cm[(size_t)kk * (L + 1) + i];
+    }
+    for (int i = threadIdx.x; i <= level; i += TPB) {
+        s_q[i] = pc[i].q;
+        s_qinv[i] = pc[i].qinv;
+        s_pm[i] = pmod[i];
+    }
+    __syncthreads();
+    const int ul = level + 1 + A;
+    const int k0 = blockIdx.x * (TPB * CONV_EL) + threadIdx.x;
+    const u64* up = u + (size_t)c * ul * n + (size_t)(level + 1) * n + k0;
     // centred terms: y_k in (-p_k/2, p_k/2]; a negative term contributes y_k (P/p_k) - P
-    u64 y[RK_MAX_SPECIAL];
-    int nneg = 0;
+    u64 y[CONV_EL][A];
+    int nneg[CONV_EL];
 #pragma unroll
-    for (int kk = 0; kk < RK_MAX_SPECIAL; kk++) {
-        if (kk < alpha) {
-            const u64 pk = pc[L + 1 + kk].q;
-            y[kk] = shoup_mul(up[(size_t)kk * n], cv.moddown[kk], cv.moddown[alpha + kk], pk);
-            nneg += y[kk] > (pk >> 1) ? 1 : 0;
+    for (int e = 0; e < CONV_EL; e++) nneg[e] = 0;
+#pragma unroll
+    for (int kk = 0; kk < A; kk++) {
+        const u64 pk = pc[L + 1 + kk].q, iv = cv.moddown[kk], ivsh = cv.moddown[A + kk];
+#pragma unroll
+        for (int e = 0; e < CONV_EL; e++) {
+            y[e][kk] = shoup_mul(up[(size_t)kk * n + e * TPB], iv, ivsh, pk);
+            nneg[e] += y[e][kk] > (pk >> 1) ? 1 : 0;
         }
     }
-    u64* out = w + (size_t)c * (level + 1) * n + k;
-    const u64* cm = cv.moddown + 2 * alpha;
-    const u64* pmod = cm + (size_t)alpha * (L + 1);
+    u64* out = w + (size_t)c * (level + 1) * n + k0;
     for (int i = 0; i <= level; i++) {
-        const PrimeConst P = pc[i];
-        Acc128 acc;
+        const u64 q = s_q[i], qinv = s_qinv[i], pm = s_pm[i];
+        Acc128 acc[CONV_EL];
 #pragma unroll
-        for (int kk = 0; kk < RK_MAX_SPECIAL; kk++)
-            if (kk < alpha) acc.mac(y[kk], __ldg(cm + (size_t)kk * (L + 1) + i));
-        u64 r = acc.redc(P.q, P.qinv);
-        const u64 pm = __ldg(pmod + i);
-        for (int j = 0; j < nneg; j++) r = sub_mod(r, pm, P.q);
-        out[(size_t)i * n] = r;
+        for (int kk = 0; kk < A; kk++) {
+            const u64 cst = s_c[kk * RK_MAX_PRIMES + i];
+#pragma unroll
+            for (int e = 0; e < CONV_EL; e++) acc[e].mac(y[e][kk], cst);
+        }
+#pragma unroll
+        for (int e = 0; e < CONV_EL; e++) {
+            u64 r = acc[e].redc(q, qinv);
+            for (int z = 0; z < nneg[e]; z++) r = sub_mod(r, pm, q);
+            out[(size_t)i * n + e * TPB] = r;
+        }
     }
 }
 
 void launch_moddown_conv(const KernelEnv& env, const u64* u, u64* w, int level, cudaStream_t st, int polys) {
     ProfScope pf(env, KK_MODDOWN, st, 1, polys * (1.0 * env.alpha + (level + 1)) * 8.0 * env.n, 1.0 * polys * (level + 1) * env.alpha * env.n);
-    dim3 g(env.n / TPB, polys);
-    k_moddown_conv<<<g, TPB, 0, st>>>(u, w, level, env.L, env.alpha, env.conv, env.n, env.pc);
+    dim3 g(env.n / (TPB * CONV_EL), polys);
+    switch (env.alpha) {
+#define RK_MD_CASE(A)                                                                               \
+    case A:                                                                                         \
+        k_moddown_conv<A><<<g, TPB, 0, st>>>(u, w, level, env.L, env.conv, env.n, env.pc);          \
+        break;
+        RK_MD_CASE(1) RK_MD_CASE(2) RK_MD_CASE(3) RK_MD_CASE(4) RK_MD_CASE(5) RK_MD_CASE(6) RK_MD_CASE(7) RK_MD_CASE(8)
+#undef RK_MD_CASE
+        default: throw rk_error(RK_EINVAL, "special prime count out of range");
+    }
 }
 
 // ===========================================================================

@@ -34,7 +34,7 @@ template <int LOG>
 __global__ void __launch_bounds__(256) k_modup_col(const u64* __restrict__ coef, u64* __restrict__ ext, size_t ext_stride,
                                                    int level, int L, int alpha, int beta, int t0, ConvTables cv, int logn,
                                                    int loga, int units, const PrimeConst* __restrict__ pc,
-                                                   const u64* __restrict__ tw, const u64* __restrict__ tw_sh) {
+                                                   const u64* __restrict__ tw) {
     using S = Shape<LOG>;
     constexpr int P = S::P, E = S::E;
     extern __shared__ u64 sm[];
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(256) k_modup_col(const u64* __restrict__ coef,
         }
         x[m] = acc.redc(q, PC.qinv);
     }
-    const Twid tw_{tw + (size_t)pid * n, tw_sh + (size_t)pid * n, loga - 1, 0};
+    const Twid tw_{tw + (size_t)pid * 2 * n, loga - 1, 0};
     fwd_strided<LOG>(x, t, tw_, q, q2);
 #pragma unroll
     for (int m = 0; m < E; m++) sm[(t + P * m) * units + u] = x[m];
@@ -99,8 +99,7 @@ template <int LOG>
 __global__ void __launch_bounds__(2048 / Shape<LOG>::E, (LOG >= 7 ? 3 : 2)) k_ks_row(const u64* __restrict__ ext, size_t ext_stride, const u64* __restrict__ x_eval,
                                                 size_t eval_stride, const u64* __restrict__ key, u64* __restrict__ uo, int level,
                                                 int L, int alpha, int beta, int dsize, int t0, u64 galois, int logn, int units,
-                                                const PrimeConst* __restrict__ pc, const u64* __restrict__ tw,
-                                                const u64* __restrict__ tw_sh) {
+                                                const PrimeConst* __restrict__ pc, const u64* __restrict__ tw) {
     using S = Shape<LOG>;
     constexpr int P = S::P, E = S::E, T = S::T;
     extern __shared__ u64 sm[];
@@ -124,7 +123,7 @@ __global__ void __launch_bounds__(2048 / Shape<LOG>::E, (LOG >= 7 ? 3 : 2)) k_ks
         acc[(size_t)u * T + xo] = 0;
         acc[(size_t)(units + u) * T + xo] = 0;
     }
-    const Twid tw_{tw + (size_t)pid * n, tw_sh + (size_t)pid * n, logn - 1, rho};
+    const Twid tw_{tw + (size_t)pid * 2 * n, logn - 1, rho};
     const size_t KL = (size_t)(L + 1 + alpha) * n;
     const u64* krow = key + (size_t)pid * n + ((size_t)rr << logb);
     const u64* erow = ext + (size_t)b * beta * ext_stride + (size_t)tt * n + ((size_t)rho << logb);
@@ -181,8 +180,7 @@ __global__ void __launch_bounds__(2048 / Shape<LOG>::E, (LOG >= 7 ? 3 : 2)) k_ks
 template <int LOG>
 __global__ void __launch_bounds__(256) k_moddown_col(const u64* __restrict__ uin, u64* __restrict__ w, int level, int L,
                                                      int alpha, ConvTables cv, int logn, int loga, int units,
-                                                     const PrimeConst* __restrict__ pc, const u64* __restrict__ tw,
-                                                     const u64* __restrict__ tw_sh) {
+                                                     const PrimeConst* __restrict__ pc, const u64* __restrict__ tw) {
     using S = Shape<LOG>;
     constexpr int P = S::P, E = S::E;
     extern __shared__ u64 sm[];
@@ -224,7 +222,7 @@ __global__ void __launch_bounds__(256) k_moddown_col(const u64* __restrict__ uin
         for (int z = 0; z < nneg; z++) r = sub_mod(r, pm, q);
         x[m] = r;
     }
-    const Twid tw_{tw + (size_t)i * n, tw_sh + (size_t)i * n, loga - 1, 0};
+    const Twid tw_{tw + (size_t)i * 2 * n, loga - 1, 0};
     fwd_strided<LOG>(x, t, tw_, q, q2);
 #pragma unroll
     for (int m = 0; m < E; m++) sm[(t + P * m) * units + u] = x[m];
@@ -248,7 +246,7 @@ __global__ void __launch_bounds__(256) k_moddown_row(u64* __restrict__ out, size
                                                      const u64* base1, size_t bstride, const u64* __restrict__ uin,
                                                      const u64* __restrict__ w, int level, int alpha, ConvTables cv, int logn,
                                                      int units, const PrimeConst* __restrict__ pc,
-                                                     const u64* __restrict__ tw, const u64* __restrict__ tw_sh) {
+                                                     const u64* __restrict__ tw) {
     using S = Shape<LOG>;
     constexpr int P = S::P, E = S::E;
     extern __shared__ u64 sm[];
@@ -263,7 +261,7 @@ __global__ void __launch_bounds__(256) k_moddown_row(u64* __restrict__ out, size
     u64 x[E];
 #pragma unroll
     for (int m = 0; m < E; m++) x[m] = wr[t + P * m];
-    const Twid tw_{tw + (size_t)i * n, tw_sh + (size_t)i * n, logn - 1, rho};
+    const Twid tw_{tw + (size_t)i * 2 * n, logn - 1, rho};
     fwd_strided<LOG>(x, t, tw_, q, q2);
 #pragma unroll
     for (int m = 0; m < E; m++) sm[row_slot<LOG>(u, t + P * m)] = x[m];
@@ -341,8 +339,7 @@ void launch_modup_col(const KernelEnv& env, const u64* coef, u64* ext, size_t ex
     const dim3 grid(g.blocks, limbs, B * beta);
     const size_t smem = (size_t)(1 << loga) * g.units * 8;
     RK_LOG_SWITCH(loga, (k_modup_col<LG><<<grid, g.threads, smem, st>>>(coef, ext, ext_stride, level, env.L, env.alpha, beta, t0,
-                                                                        env.conv, logn, loga, g.units, env.pc, env.tw.psi,
-                                                                        env.tw.psi_sh)));
+                                                                        env.conv, logn, loga, g.units, env.pc, env.tw.psi)));
 }
 
 void launch_ks_row(const KernelEnv& env, const u64* ext, size_t ext_stride, const u64* x_eval, size_t eval_stride, const u64* key,
@@ -362,7 +359,7 @@ void launch_ks_row(const KernelEnv& env, const u64* ext, size_t ext_stride, cons
     const size_t smem = (size_t)(1 << logb) * g.units * 26;
     RK_LOG_SWITCH(logb, (k_ks_row<LG><<<grid, g.threads, smem, st>>>(ext, ext_stride, x_eval, eval_stride, key, u, level, env.L,
                                                                      env.alpha, beta, env.conv.dsize, t0, galois, logn, g.units,
-                                                                     env.pc, env.tw.psi, env.tw.psi_sh)));
+                                                                     env.pc, env.tw.psi)));
 }
 
 void launch_moddown_col(const KernelEnv& env, const u64* u, u64* w, int level, cudaStream_t st, int polys) {
@@ -373,7 +370,7 @@ void launch_moddown_col(const KernelEnv& env, const u64* u, u64* w, int level, c
     const dim3 grid(g.blocks, level + 1, polys);
     const size_t smem = (size_t)(1 << loga) * g.units * 8;
     RK_LOG_SWITCH(loga, (k_moddown_col<LG><<<grid, g.threads, smem, st>>>(u, w, level, env.L, env.alpha, env.conv, logn, loga,
-                                                                          g.units, env.pc, env.tw.psi, env.tw.psi_sh)));
+                                                                          g.units, env.pc, env.tw.psi)));
 }
 
 void launch_moddown_row(const KernelEnv& env, u64* out, size_t ps, const u64* base0, u64 galois0, const u64* base1, size_t bstride,
@@ -384,6 +381,5 @@ void launch_moddown_row(const KernelEnv& env, u64* out, size_t ps, const u64* ba
     const dim3 grid(g.blocks, level + 1, 2 * B);
     const size_t smem = (size_t)(1 << logb) * g.units * 8;
     RK_LOG_SWITCH(logb, (k_moddown_row<LG><<<grid, g.threads, smem, st>>>(out, ps, base0, galois0, base1, bstride, u, w, level,
-                                                                          env.alpha, env.conv, logn, g.units, env.pc, env.tw.psi,
-                                                                          env.tw.psi_sh)));
+                                                                          env.alpha, env.conv, logn, g.units, env.pc, env.tw.psi)));
 }

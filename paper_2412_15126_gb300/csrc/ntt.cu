@@ -20,12 +20,18 @@
 
 #include "ntt_core.cuh"
 
+// Resident blocks of 256 threads per SM the column passes are compiled for (the
+// row passes keep two): three caps them at 80 registers a thread.
+#ifndef RK_NTT_COL_BLOCKS
+#define RK_NTT_COL_BLOCKS 3
+#endif
+
 namespace {
 using namespace nttc;
 
 template <int LOG, bool INV, bool COL>
-__global__ void __launch_bounds__(256, (LOG <= 8 && COL ? 3 : 2)) k_ntt_pass(LimbSet s, int logn, int loga, int units, const PrimeConst* __restrict__ pc,
-                                                  const u64* __restrict__ tw, const u64* __restrict__ tw_sh) {
+__global__ void __launch_bounds__(256, (LOG <= 8 && COL ? RK_NTT_COL_BLOCKS : 2)) k_ntt_pass(LimbSet s, int logn, int loga, int units, const PrimeConst* __restrict__ pc,
+                                                  const u64* __restrict__ tw) {
     using S = Shape<LOG>;
     constexpr int P = S::P, E = S::E;
     extern __shared__ u64 sm[];
@@ -53,7 +59,7 @@ __global__ void __launch_bounds__(256, (LOG <= 8 && COL ? 3 : 2)) k_ntt_pass(Lim
         g = data + (size_t)rho * B;
         gs = 1;
     }
-    const Twid tw_{tw + (size_t)pid * n, tw_sh + (size_t)pid * n, COL ? loga - 1 : logn - 1, rho};
+    const Twid tw_{tw + (size_t)pid * 2 * n, COL ? loga - 1 : logn - 1, rho};
     auto sidx = [&](int e) -> int { return COL ? e * units + u : row_slot<LOG>(u, e); };
     u64 x[E];
 
@@ -112,11 +118,11 @@ __global__ void __launch_bounds__(256, (LOG <= 8 && COL ? 3 : 2)) k_ntt_pass(Lim
 
 template <bool INV, bool COL>
 void pass_launch(int LOG, dim3 grid, int threads, size_t smem, cudaStream_t st, const LimbSet& s, int logn, int loga,
-                 int units, const PrimeConst* pc, const u64* tw, const u64* tw_sh) {
+                 int units, const PrimeConst* pc, const u64* tw) {
     switch (LOG) {
 #define RK_NTT_CASE(L)                                                                                        \
     case L:                                                                                                   \
-        k_ntt_pass<L, INV, COL><<<grid, threads, smem, st>>>(s, logn, loga, units, pc, tw, tw_sh);            \
+        k_ntt_pass<L, INV, COL><<<grid, threads, smem, st>>>(s, logn, loga, units, pc, tw);                   \
         break;
         RK_NTT_CASE(5)
         RK_NTT_CASE(6)
@@ -146,9 +152,13 @@ struct PassGeom {
     size_t smem;
 };
 
-PassGeom geom(int LOG, int count, const LimbSet& s) {
+PassGeom geom(int LOG, int count, const LimbSet& s, int sms) {
     const int P = 1 << (LOG / 2);
-    const int units = std::min(256 / P, count);
+    int units = std::min(256 / P, count);
+    // small transforms (few limbs): narrower blocks until the grid covers two waves,
+    // keeping two warps a block (column passes: 32-byte row segments)
+    const long limbs = (long)s.n_limbs * s.n_polys;
+    while (units > 1 && P * units > 64 && (long)(count / units) * limbs < 2L * sms) units >>= 1;
     PassGeom gm;
     gm.units = units;
     gm.threads = P * units;
@@ -171,10 +181,10 @@ void launch_ntt_forward(const KernelEnv& env, const LimbSet& s, cudaStream_t st)
     const double limbs = (double)s.n_limbs * s.n_polys - (s.skip_ds ? (double)(s.n_polys / s.skip_beta) * s.split : 0.0);
     ProfScope ps(env, KK_NTT_FWD, st, 2, 2.0 * limbs * 8.0 * env.n, limbs * (env.n / 2) * env.logn);
     const int logn = env.logn, loga = logn / 2, logb = logn - loga;
-    PassGeom c = geom(loga, 1 << logb, s);
-    pass_launch<false, true>(loga, c.grid, c.threads, c.smem, st, s, logn, loga, c.units, env.pc, env.tw.psi, env.tw.psi_sh);
-    PassGeom r = geom(logb, 1 << loga, s);
-    pass_launch<false, false>(logb, r.grid, r.threads, r.smem, st, s, logn, loga, r.units, env.pc, env.tw.psi, env.tw.psi_sh);
+    PassGeom c = geom(loga, 1 << logb, s, env.sms);
+    pass_launch<false, true>(loga, c.grid, c.threads, c.smem, st, s, logn, loga, c.units, env.pc, env.tw.psi);
+    PassGeom r = geom(logb, 1 << loga, s, env.sms);
+    pass_launch<false, false>(logb, r.grid, r.threads, r.smem, st, s, logn, loga, r.units, env.pc, env.tw.psi);
 }
 
 void launch_ntt_inverse(const KernelEnv& env, const LimbSet& s, cudaStream_t st) {
@@ -182,8 +192,8 @@ void launch_ntt_inverse(const KernelEnv& env, const LimbSet& s, cudaStream_t st)
     ProfScope ps(env, KK_NTT_INV, st, 2, 2.0 * s.n_limbs * s.n_polys * 8.0 * env.n,
                  (double)s.n_limbs * s.n_polys * (env.n / 2) * env.logn);
     const int logn = env.logn, loga = logn / 2, logb = logn - loga;
-    PassGeom r = geom(logb, 1 << loga, s);
-    pass_launch<true, false>(logb, r.grid, r.threads, r.smem, st, s, logn, loga, r.units, env.pc, env.tw.ipsi, env.tw.ipsi_sh);
-    PassGeom c = geom(loga, 1 << logb, s);
-    pass_launch<true, true>(loga, c.grid, c.threads, c.smem, st, s, logn, loga, c.units, env.pc, env.tw.ipsi, env.tw.ipsi_sh);
+    PassGeom r = geom(logb, 1 << loga, s, env.sms);
+    pass_launch<true, false>(logb, r.grid, r.threads, r.smem, st, s, logn, loga, r.units, env.pc, env.tw.ipsi);
+    PassGeom c = geom(loga, 1 << logb, s, env.sms);
+    pass_launch<true, true>(loga, c.grid, c.threads, c.smem, st, s, logn, loga, c.units, env.pc, env.tw.ipsi);
 }

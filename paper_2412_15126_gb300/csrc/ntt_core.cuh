@@ -43,18 +43,21 @@ struct Shape {
     static constexpr int T = 1 << LOG, LOGP = LOG / 2, P = 1 << LOGP, LOGE = LOG - LOGP, E = 1 << LOGE;
 };
 
-// twiddle table of one prime and the position of the transform in the pass
+// twiddle table of one prime ((w, Shoup companion) pairs) and the position of the
+// transform in the pass
 struct Twid {
     const u64* W;
-    const u64* Wsh;
     int Sbase, rho;
 };
 
+// Twiddle of the butterflies at span 2^v whose lower element has in-transform index
+// x, given g = x >> (v + 1): one 16-byte load of the pair.
 template <int LOG>
-__device__ __forceinline__ void twid_at(const Twid& tw, int v, int x, u64& w, u64& wsh) {
-    const int idx = (1 << (tw.Sbase - v)) + (tw.rho << (LOG - 1 - v)) + (x >> (v + 1));
-    w = __ldg(tw.W + idx);
-    wsh = __ldg(tw.Wsh + idx);
+__device__ __forceinline__ void twid_at(const Twid& tw, int v, int g, u64& w, u64& wsh) {
+    const int idx = (1 << (tw.Sbase - v)) + (tw.rho << (LOG - 1 - v)) + g;
+    const ulonglong2 p = __ldg(reinterpret_cast<const ulonglong2*>(tw.W) + idx);
+    w = p.x;
+    wsh = p.y;
 }
 
 // forward stages with span 2^v >= P (v = LOG-1 .. LOGP) on the strided set
@@ -67,8 +70,8 @@ __device__ __forceinline__ void fwd_strided(u64 (&x)[Shape<LOG>::E], int t, cons
 #pragma unroll
         for (int m = 0; m < S::E; m++) {
             if (m & h) continue;
-            u64 w, wsh;
-            twid_at<LOG>(tw, v, t + S::P * m, w, wsh);
+            u64 w, wsh;   // (t + P m) >> (v + 1) = m >> (v + 1 - LOGP): shared by the whole transform
+            twid_at<LOG>(tw, v, m >> (v + 1 - S::LOGP), w, wsh);
             ct_bfly(x[m], x[m + h], w, wsh, q, q2);
         }
     }
@@ -84,8 +87,8 @@ __device__ __forceinline__ void fwd_contig(u64 (&x)[Shape<LOG>::E], int t, const
 #pragma unroll
         for (int m = 0; m < S::E; m++) {
             if (m & h) continue;
-            u64 w, wsh;
-            twid_at<LOG>(tw, v, t * S::E + m, w, wsh);
+            u64 w, wsh;   // (t E + m) >> (v + 1) = t E / 2^(v+1) + (m >> (v + 1))
+            twid_at<LOG>(tw, v, (t << (S::LOGE - v - 1)) + (m >> (v + 1)), w, wsh);
             ct_bfly(x[m], x[m + h], w, wsh, q, q2);
         }
     }
@@ -102,7 +105,7 @@ __device__ __forceinline__ void inv_contig(u64 (&x)[Shape<LOG>::E], int t, const
         for (int m = 0; m < S::E; m++) {
             if (m & h) continue;
             u64 w, wsh;
-            twid_at<LOG>(tw, v, t * S::E + m, w, wsh);
+            twid_at<LOG>(tw, v, (t << (S::LOGE - v - 1)) + (m >> (v + 1)), w, wsh);
             gs_bfly(x[m], x[m + h], w, wsh, q, q2);
         }
     }
@@ -119,7 +122,7 @@ __device__ __forceinline__ void inv_strided(u64 (&x)[Shape<LOG>::E], int t, cons
         for (int m = 0; m < S::E; m++) {
             if (m & h) continue;
             u64 w, wsh;
-            twid_at<LOG>(tw, v, t + S::P * m, w, wsh);
+            twid_at<LOG>(tw, v, m >> (v + 1 - S::LOGP), w, wsh);
             gs_bfly(x[m], x[m + h], w, wsh, q, q2);
         }
     }

@@ -77,10 +77,8 @@ struct ConvTables {
 };
 
 struct DevTables {
-    const u64* psi;       // [n_primes][n]  psi^brev(i)
-    const u64* psi_sh;
-    const u64* ipsi;      // [n_primes][n]  psi^-brev(i)
-    const u64* ipsi_sh;
+    const u64* psi;       // [n_primes][n][2]  (psi^brev(i), its Shoup companion)
+    const u64* ipsi;      // [n_primes][n][2]  (psi^-brev(i), its Shoup companion)
 };
 
 // Constants of a scalar multiplication (one residue per limb, with Shoup companions).
@@ -112,6 +110,7 @@ struct Profiler {
 // Everything a kernel launcher needs: sizes and device tables.
 struct KernelEnv {
     int logn, n, L, alpha;
+    int sms = 152;          // multiprocessors of the device (grid sizing)
     const PrimeConst* pc;   // device array [n_primes]
     DevTables tw;
     ConvTables conv;
@@ -164,6 +163,7 @@ struct rk_ctx {
     rk_server* server = nullptr;  // serving loop, when one runs (it owns the stream meanwhile)
     bool ks_fused = false;        // key switching with conversions fused into the NTT passes
     double ks_group_bytes = 48.0 * (1 << 20);   // lifted digits kept in L2 between the fused kernels
+    size_t ind_stack_bytes = (size_t)16 << 30;  // working set of one stacked indicator evaluation
     // plaintext caches: key = (kind, N, Q, n_real, level)
     std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint32_t, int>, u64*> plain_cache;
     std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint32_t>, std::vector<double>> encodings;

@@ -1,7 +1,7 @@
 // Serving loop: one worker thread per context with continuous batching.
 //
-// Requests (rank, order statistic, sort on one ciphertext; blocked rank on a stack of
-// blocks) are queued by any thread.  Whenever the worker is free it takes the oldest
+// Requests (rank, order statistic, sort on one ciphertext; their blocked forms on a
+// stack of blocks) are queued by any thread.  Whenever the worker is free it takes the oldest
 // request together with every queued request of the same operation, arguments and
 // ciphertext shape, stacks them into one ciphertext (one launch per kernel for the
 // stack), runs the circuit once and splits the result.  The stack is capped so that
@@ -23,6 +23,9 @@ rk_ct* circuit_rank(rk_ctx* c, const rk_ct* in, uint32_t flags);
 rk_ct* circuit_order_stat(rk_ctx* c, const rk_ct* in, uint32_t k, uint32_t flags);
 rk_ct* circuit_sort(rk_ctx* c, const rk_ct* in, uint32_t flags);
 void circuit_rank_blocked(rk_ctx* c, const rk_ct* const* blocks, int L, rk_ct** outs);
+void circuit_rank_blocked_tc(rk_ctx* c, const rk_ct* const* blocks, int L, rk_ct** outs);
+void circuit_order_stat_blocked(rk_ctx* c, const rk_ct* const* blocks, int L, uint32_t k, rk_ct** outs);
+void circuit_sort_blocked(rk_ctx* c, const rk_ct* const* blocks, int L, rk_ct** outs);
 
 namespace {
 
@@ -44,7 +47,7 @@ struct Result {
 };
 
 bool same_batch(const Request& a, const Request& b) {
-    return a.op == b.op && a.arg == b.arg && a.flags == b.flags && a.op != RK_OP_RANK_BLOCKED && a.in->level == b.in->level &&
+    return a.op == b.op && a.arg == b.arg && a.flags == b.flags && a.op < RK_OP_RANK_BLOCKED && a.in->level == b.in->level &&
            a.in->N == b.in->N && a.in->Q == b.in->Q && a.in->n_real == b.in->n_real && a.in->layout == b.in->layout &&
            a.in->B == 1 && b.in->B == 1;
 }
@@ -87,12 +90,19 @@ size_t member_bytes(const rk_ctx* c, int level) {
 void run_batch(rk_server* s, std::vector<Request>& batch, std::vector<Result>& res) {
     rk_ctx* c = s->ctx;
     const Request& r0 = batch[0];
-    if (r0.op == RK_OP_RANK_BLOCKED) {
+    if (r0.op >= RK_OP_RANK_BLOCKED) {
         const int L = r0.in->B;
         std::vector<rk_ct*> views(L), outs(L, nullptr);
         for (int i = 0; i < L; i++) views[i] = ct_view(r0.in, i);
         try {
-            circuit_rank_blocked(c, views.data(), L, outs.data());
+            if (r0.op == RK_OP_RANK_BLOCKED && (r0.flags & RK_TIES_CORRECT))
+                circuit_rank_blocked_tc(c, views.data(), L, outs.data());
+            else if (r0.op == RK_OP_RANK_BLOCKED)
+                circuit_rank_blocked(c, views.data(), L, outs.data());
+            else if (r0.op == RK_OP_ORDER_STAT_BLOCKED)
+                circuit_order_stat_blocked(c, views.data(), L, r0.arg, outs.data());
+            else
+                circuit_sort_blocked(c, views.data(), L, outs.data());
         } catch (...) {
             for (auto* v : views) ct_free(v);
             for (auto* o : outs) ct_free(o);
@@ -213,8 +223,8 @@ rk_server* server_start(rk_ctx* c, size_t budget, int max_stack) {
 uint64_t server_submit(rk_ctx* c, uint32_t op, uint32_t arg, uint32_t flags, const rk_ct* in) {
     rk_server* s = c->server;
     RK_REQUIRE(s, RK_EINVAL, "no server running on this context");
-    RK_REQUIRE(op >= RK_OP_RANK && op <= RK_OP_RANK_BLOCKED, RK_EINVAL, "unknown server operation");
-    RK_REQUIRE(op == RK_OP_RANK_BLOCKED ? in->B >= 1 : in->B == 1, RK_EINVAL,
+    RK_REQUIRE(op >= RK_OP_RANK && op <= RK_OP_SORT_BLOCKED, RK_EINVAL, "unknown server operation");
+    RK_REQUIRE(op >= RK_OP_RANK_BLOCKED ? in->B >= 1 : in->B == 1, RK_EINVAL,
                "server requests take one ciphertext (blocked rank: a stack of blocks)");
     std::lock_guard<std::mutex> lk(s->mu);
     RK_REQUIRE(!s->stopping, RK_EINVAL, "server is stopping");

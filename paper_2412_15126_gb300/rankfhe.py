@@ -28,9 +28,9 @@ MASK_ROW0, MASK_COL0, MASK_TIE, MASK_TRI, MASK_VALID = 1, 2, 3, 4, 5
 KEY_RELIN, KEY_GALOIS = 1, 2
 TIES_CORRECT = 1
 TIES_FIRST, TIES_ALL = 0, 2
-MASK_ROW0S, MASK_COL0S, MASK_TIEC, MASK_SORTIDX = 6, 7, 8, 9
+MASK_ROW0S, MASK_COL0S, MASK_TIEC, MASK_SORTIDX, MASK_ROWIDX = 6, 7, 8, 9, 10
 OPT_KS_FUSED, OPT_KS_GROUP_BYTES = 1, 2
-OP_RANK, OP_ORDER_STAT, OP_SORT, OP_RANK_BLOCKED = 1, 2, 3, 4
+OP_RANK, OP_ORDER_STAT, OP_SORT, OP_RANK_BLOCKED, OP_ORDER_STAT_BLOCKED, OP_SORT_BLOCKED = 1, 2, 3, 4, 5, 6
 
 
 class RkError(RuntimeError):
@@ -83,6 +83,8 @@ _sig("rk_ct_free", [_vp], None)
 _sig("rk_ct_stack", [_vp, ctypes.POINTER(_vp), _u32, ctypes.POINTER(_vp)])
 _sig("rk_rank_blocked", [_vp, ctypes.POINTER(_vp), _u32, _u32, ctypes.POINTER(_vp)])
 _sig("rk_ct_unstack", [_vp, _vp, ctypes.POINTER(_vp)])
+_sig("rk_order_stat_blocked", [_vp, ctypes.POINTER(_vp), _u32, _u32, _u32, ctypes.POINTER(_vp)])
+_sig("rk_sort_blocked", [_vp, ctypes.POINTER(_vp), _u32, _u32, ctypes.POINTER(_vp)])
 _sig("rk_ct_count", [_vp], _u32)
 _sig("rk_rotate", [_vp, _vp, ctypes.c_int32, ctypes.POINTER(_vp)])
 _sig("rk_rotate_many", [_vp, _vp, _i32p, _u32, ctypes.POINTER(_vp)])
@@ -296,10 +298,22 @@ class Context:
         _check(fn(self.handle, *args, ctypes.byref(h)))
         return Ciphertext(self, h.value)
 
-    def rank_blocked(self, blocks):
+    def rank_blocked(self, blocks, flags=0):
         ins = (_vp * len(blocks))(*[c.handle.value for c in blocks])
         outs = (_vp * len(blocks))()
-        _check(_L.rk_rank_blocked(self.handle, ins, len(blocks), 0, outs))
+        _check(_L.rk_rank_blocked(self.handle, ins, len(blocks), flags, outs))
+        return [Ciphertext(self, o) for o in outs]
+
+    def order_stat_blocked(self, blocks, k, flags=0):
+        ins = (_vp * len(blocks))(*[c.handle.value for c in blocks])
+        outs = (_vp * len(blocks))()
+        _check(_L.rk_order_stat_blocked(self.handle, ins, len(blocks), int(k), flags, outs))
+        return [Ciphertext(self, o) for o in outs]
+
+    def sort_blocked(self, blocks, flags=0):
+        ins = (_vp * len(blocks))(*[c.handle.value for c in blocks])
+        outs = (_vp * len(blocks))()
+        _check(_L.rk_sort_blocked(self.handle, ins, len(blocks), flags, outs))
         return [Ciphertext(self, o) for o in outs]
 
     def stack(self, cts):

@@ -13,9 +13,11 @@ CONFIGS = {
     "cfg2": (16, 28, 60, 45, 3, 61, 3, 4, 2),       # N = 128 rank, n = 2^16, 28 limbs + 3 special
     "cfg3": (16, 34, 60, 45, 3, 61, 3, 3, 2),       # N = 128 ties, 34 limbs
     "ord": (11, 24, 60, 40, 2, 61, 2, 2, 1),        # deep small ring for order statistics / sort parity
+    "ordb": (11, 24, 60, 40, 2, 61, 2, 1, 1),       # the same ring, shallower comparator: blocked sort parity
 }
 
-MASK_IDS = {"row0": 1, "col0": 2, "tie": 3, "tri": 4, "valid": 5, "row0s": 6, "col0s": 7, "tiec": 8, "sortidx": 9}
+MASK_IDS = {"row0": 1, "col0": 2, "tie": 3, "tri": 4, "valid": 5, "row0s": 6, "col0s": 7, "tiec": 8, "sortidx": 9,
+            "rowidx": 10}
 ALL_MASKS = ("row0", "col0", "tie", "tri", "row0s", "col0s", "tiec", "sortidx")
 
 

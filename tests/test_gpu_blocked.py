@@ -1,0 +1,98 @@
+"""GPU parity of the multi-ciphertext circuits with tie correction: blocked ranks
+(Alg. 7 with Alg. 6 across blocks), the blocked order statistic (Alg. 4) and the
+blocked sort (Alg. 8).
+
+* n = 2^11, 24 limbs, blocks of 4 (a ring the oracle runs in seconds): with the
+  oracle's keys, blocks, mask encodings and indicator imported, every output block
+  equals the oracle's ciphertext bit for bit.
+* n = 2^16, 34 limbs, N = 128 as two blocks of 64 on a 64-level grid (ties): the
+  library's own keys, decrypted against the brute-force answers.
+"""
+import numpy as np
+import pytest
+
+from oracle import ckks, circuits as C
+from paper_2412_15126_gb300 import inputs
+from tests import helpers
+
+pytestmark = pytest.mark.gpu
+
+BSZ = 4
+
+
+@pytest.fixture(scope="module")
+def ordb():
+    P = helpers.oracle_params("ordb")
+    keys = ckks.keygen(P, 41, helpers.galois_elts(P, helpers.rotation_set(BSZ)))
+    ctx = helpers.gpu_context("ordb")
+    helpers.import_keys(ctx, keys)
+    helpers.import_encodings(ctx, P, BSZ, kinds=("row0", "col0", "tie"))
+    for L in (2, 3):
+        D = L * BSZ
+        for kind in ("row0s", "rowidx"):
+            u = ckks.encode_unscaled(C.mask_slots(kind, BSZ, 1, D, slots=P.slots), P.n)
+            ctx.encoding_import(helpers.MASK_IDS[kind], BSZ, 1, D, u)
+        ctx.indicator_import(D, C.sinc2_window_coeffs(D))
+    yield P, keys, ctx
+    ctx.close()
+
+
+def _encrypt_blocks(P, keys, ctx, v, seed):
+    cts = [ckks.encrypt(P, keys, v[i * BSZ:(i + 1) * BSZ], seed + i) for i in range(len(v) // BSZ)]
+    return cts, [ctx.ct_import(c.c, c.level, N=BSZ) for c in cts]
+
+
+def test_blocked_tie_corrected_rank_bit_exact(ordb):
+    from paper_2412_15126_gb300 import rankfhe
+    P, keys, ctx = ordb
+    v = np.array([3, 1, 3, 0, 2, 1, 3, 2, 0, 1, 2, 3]) / 8.0
+    cts, g = _encrypt_blocks(P, keys, ctx, v, 10)
+    ref, _ = C.rank_blocked_tc(C.OracleCkks(P, keys), cts, BSZ, 1, 1)
+    got = ctx.rank_blocked(g, rankfhe.TIES_CORRECT)
+    for a, b in zip(got, ref):
+        assert a.level == b.level
+        assert np.array_equal(a.export(), b.c)
+
+
+def test_blocked_order_statistic_bit_exact(ordb):
+    P, keys, ctx = ordb
+    v = np.array([3, 1, 3, 0, 2, 0, 3, 2]) / 8.0
+    cts, g = _encrypt_blocks(P, keys, ctx, v, 20)
+    ref = C.order_statistic_blocked(C.OracleCkks(P, keys), cts, BSZ, 2, 1, 1)
+    got = ctx.order_stat_blocked(g, 2)
+    for a, b in zip(got, ref):
+        assert np.array_equal(a.export(), b.c)
+
+
+def test_blocked_sort_bit_exact(ordb):
+    P, keys, ctx = ordb
+    v = np.array([0.75, 0.125, 0.5, 0.0, 0.625, 0.25, 0.875, 0.375])
+    cts, g = _encrypt_blocks(P, keys, ctx, v, 30)
+    ref = C.sort_blocked(C.OracleCkks(P, keys), cts, BSZ, 1, 1)
+    got = ctx.sort_blocked(g)
+    for a, b in zip(got, ref):
+        assert a.level == b.level
+        assert np.array_equal(a.export(), b.c)
+
+
+@pytest.fixture(scope="module")
+def cfg3():
+    ctx = helpers.gpu_context("cfg3")
+    ctx.keygen(78, 64)
+    yield ctx
+    ctx.close()
+
+
+def test_cfg3_blocked_two_by_64_with_ties(cfg3):
+    from paper_2412_15126_gb300 import rankfhe
+    ctx = cfg3
+    v = inputs.grid_vector(128, 64, 9)
+    blocks = [ctx.encrypt(v[:64], N=64), ctx.encrypt(v[64:], N=64)]
+    R = np.concatenate([ctx.decrypt(r) for r in ctx.rank_blocked(blocks, rankfhe.TIES_CORRECT)])
+    assert np.max(np.abs(R - C.brute_tie_corrected_rank(v))) < 0.05
+    O = np.concatenate([ctx.decrypt(o) for o in ctx.order_stat_blocked(blocks, 1)])
+    first = np.zeros(128)
+    first[int(np.argmin(v))] = 1
+    assert np.max(np.abs(O - first)) < 0.01
+    S = np.concatenate([ctx.decrypt(s) for s in ctx.sort_blocked(blocks)])
+    assert np.max(np.abs(S - np.sort(v))) < 0.01

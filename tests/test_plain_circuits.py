@@ -259,3 +259,61 @@ def test_order_statistics_and_sort_brute_force(seed):
     B = C.PlainSlots(max(2 * N * N, 64), 40)
     S = B.values(C.sort(B, B.fresh(v), N, 3, 2))[:N]
     assert np.max(np.abs(S - s)) < 1e-6
+
+
+def _blocks(B, v, Bsz):
+    return [B.fresh(v[i * Bsz:(i + 1) * Bsz]) for i in range(len(v) // Bsz)]
+
+
+@pytest.mark.parametrize("Bsz,L", [(4, 2), (4, 3), (8, 2), (2, 4)])
+def test_blocked_tie_corrected_rank_is_the_stable_rank(Bsz, L):
+    """Alg. 7 with Alg. 6 over blocks: the global stable rank (equal values ordered by
+    block, then position), also when divided by the total length."""
+    rng = np.random.default_rng(100 + Bsz * L)
+    N = Bsz * L
+    v = rng.integers(0, max(N // 2, 2), N) / (2.0 * N)      # ties across and within blocks
+    B = C.PlainSlots(max(2 * Bsz * Bsz, 64), 60)
+    Rs, _ = C.rank_blocked_tc(B, _blocks(B, v, Bsz), Bsz, 4, 2)
+    got = np.concatenate([B.values(R)[:Bsz] for R in Rs])
+    assert np.max(np.abs(got - C.brute_tie_corrected_rank(v))) < 1e-3
+    assert len({R.level for R in Rs}) == 1 and Rs[0].level == 60 - 1 - 18 - 3
+    Bs = C.PlainSlots(max(2 * Bsz * Bsz, 64), 60)
+    Rs2, _ = C.rank_blocked_tc(Bs, _blocks(Bs, v, Bsz), Bsz, 4, 2, scaled=True)
+    got2 = np.concatenate([Bs.values(R)[:Bsz] for R in Rs2])
+    assert np.max(np.abs(got2 * N - C.brute_tie_corrected_rank(v))) < 1e-3
+
+
+def test_blocked_tie_corrected_rank_one_block_is_alg6():
+    """With one block the blocked schedule is the single-ciphertext fold of Alg. 6."""
+    v = np.array([3, 1, 3, 0, 2, 1, 3, 2]) / 8.0
+    B = C.PlainSlots(128, 60)
+    Rs, _ = C.rank_blocked_tc(B, [B.fresh(v)], 8, 4, 2)
+    ref = C.rank_tie_corrected(B, B.fresh(v), 8, 4, 2)
+    assert np.array_equal(B.values(Rs[0]), B.values(ref))
+
+
+@pytest.mark.parametrize("k", [1, 5, 12])
+def test_blocked_order_statistic_one_hot(k):
+    """Alg. 4 on blocked tie-corrected ranks: one 1 at the first element of rank k."""
+    Bsz, L = 4, 3
+    v = np.array([5, 2, 9, 2, 7, 0, 5, 11, 0, 3, 9, 6]) / 24.0
+    B = C.PlainSlots(64, 60)
+    Os = C.order_statistic_blocked(B, _blocks(B, v, Bsz), Bsz, k, 4, 2)
+    got = np.concatenate([B.values(O)[:Bsz] for O in Os])
+    want = (C.brute_tie_corrected_rank(v) == k).astype(float)
+    assert want.sum() == 1
+    assert np.max(np.abs(got - want)) < 1e-3
+
+
+@pytest.mark.parametrize("Bsz,L", [(4, 3), (2, 4), (8, 2)])
+def test_blocked_sort_is_sorted_vector(Bsz, L):
+    """Alg. 8 on tie-corrected ranks returns the sorted vector block by block (ties kept)."""
+    rng = np.random.default_rng(7 + Bsz * L)
+    N = Bsz * L
+    v = rng.integers(0, N, N) / (2.0 * N)
+    B = C.PlainSlots(max(2 * Bsz * Bsz, 64), 80)
+    Ss = C.sort_blocked(B, _blocks(B, v, Bsz), Bsz, 4, 2)
+    got = np.concatenate([B.values(S)[:Bsz] for S in Ss])
+    assert np.max(np.abs(got - np.sort(v))) < 1e-3
+    for S in Ss:   # nothing outside row 0 of each block
+        assert np.all(np.abs(B.values(S)[Bsz:Bsz * Bsz]) < 1e-6)
