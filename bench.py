@@ -107,6 +107,145 @@ def order_sort_workload(stream, device, reps=3, seed=3):
 
 
 # ---------------------------------------------------------------------------
+# serving: Poisson arrivals of mixed rank / argmin / sort requests
+# ---------------------------------------------------------------------------
+SERVE_RANK = dict(log_n=16, n_limbs=34, n_special=3, digit_size=3, log_scale=45, log_q0=60, log_special=61, d_g=4, d_f=2)
+SERVE_SORT = dict(log_n=16, n_limbs=39, n_special=3, digit_size=3, log_scale=40, log_q0=60, log_special=61, d_g=4, d_f=2)
+
+
+def serving_requests(count, rate, seed=5, sort_cap=512):
+    """Seeded request stream: exponential inter-arrival gaps (mean 1/rate), the op
+    uniform over {rank, argmin, sort}, N = round(exp(U(ln 8, ln 1024))) padded to
+    2^k (blocks of 128 above 128), values on a 256-level grid.  Padding slots hold
+    1 - 1/512, above every grid value, so no real element changes rank.  Sorts are
+    capped at sort_cap elements (deeper ones do not fit the 128-bit-secure ring)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    t, out = 0.0, []
+    for i in range(count):
+        t += rng.exponential(1.0 / rate)
+        op = ("rank", "argmin", "sort")[int(rng.integers(0, 3))]
+        N = int(round(float(np.exp(rng.uniform(np.log(8), np.log(1024))))))
+        if op == "sort":
+            N = min(N, sort_cap)
+        Np = 1 << max(3, (N - 1).bit_length())
+        v = rng.integers(0, 256, N) / 256.0
+        out.append({"t": t, "op": op, "N": N, "Np": Np, "v": v})
+    return out
+
+
+def serving_workload(stream_a, stream_b, device, count=120, rate=20.0):
+    """Two contexts, each with its serving loop (worker thread, continuous batching):
+    34 limbs at 2^45 for ranks and argmins up to 128 elements, 39 limbs at 2^40 for
+    sorts and blocked argmins.  Inputs are
+    encrypted before the clock starts; a client thread submits each request at its
+    arrival time.  Latency is submit to result on the device (server side)."""
+    import threading
+    import numpy as np
+    from paper_2412_15126_gb300 import rankfhe
+    from oracle.circuits import brute_fractional_rank   # brute-force definitions only
+
+    def make(P, stream):
+        return rankfhe.Context(P["log_n"], P["n_limbs"], P["n_special"], P["digit_size"], P["log_scale"], P["log_q0"],
+                               P["log_special"], P["d_g"], P["d_f"], device=device, stream=stream.cuda_stream)
+
+    reqs = serving_requests(count, rate)
+    ca, cs = make(SERVE_RANK, stream_a), make(SERVE_SORT, stream_b)
+    try:
+        ca.keygen(501, 128)
+        cs.keygen(502, 128)
+        pad = 1.0 - 1.0 / 512
+        for r in reqs:   # sorts and blocked argmins need the deeper chain
+            ctx = cs if (r["op"] == "sort" or (r["op"] == "argmin" and r["Np"] > 128)) else ca
+            x = np.full(r["Np"], pad)
+            x[:r["N"]] = r["v"]
+            r["ctx"] = ctx
+            if r["Np"] <= 128:
+                r["ct"] = ctx.encrypt(x, N=r["Np"])
+            else:
+                r["ct"] = ctx.stack([ctx.encrypt(x[b * 128:(b + 1) * 128], N=128) for b in range(r["Np"] // 128)])
+        for ctx in (ca, cs):
+            ctx.sync()
+            ctx.server_start(64 << 30, 16)
+        tickets = [None] * len(reqs)
+
+        def client():
+            t0 = time.perf_counter()
+            for i, r in enumerate(reqs):
+                d = r["t"] - (time.perf_counter() - t0)
+                if d > 0:
+                    time.sleep(d)
+                blocked = r["Np"] > 128
+                if r["op"] == "rank":
+                    op = rankfhe.OP_RANK_BLOCKED if blocked else rankfhe.OP_RANK
+                    tickets[i] = r["ctx"].server_submit(op, r["ct"])
+                elif r["op"] == "argmin":
+                    op = rankfhe.OP_ORDER_STAT_BLOCKED if blocked else rankfhe.OP_ORDER_STAT
+                    tickets[i] = r["ctx"].server_submit(op, r["ct"], arg=1, flags=rankfhe.TIES_FIRST)
+                else:
+                    op = rankfhe.OP_SORT_BLOCKED if blocked else rankfhe.OP_SORT
+                    tickets[i] = r["ctx"].server_submit(op, r["ct"])
+
+        t_start = time.perf_counter()
+        th = threading.Thread(target=client)
+        th.start()
+        th.join()
+        outs = [r["ctx"].server_wait(tk) for r, tk in zip(reqs, tickets)]
+        wall = time.perf_counter() - t_start
+        stats = {"rank_argmin": ca.server_stats(), "sort_deep": cs.server_stats()}
+        lat = sorted(ca.server_latencies() + cs.server_latencies())
+        ca.server_stop()
+        cs.server_stop()
+        # accuracy of every result against the brute-force answer
+        err = {"rank": 0.0, "argmin": 0.0, "sort": 0.0}
+        for r, o in zip(reqs, outs):
+            ctx = r["ctx"]
+            if r["Np"] <= 128:
+                got = ctx.decrypt(o)
+            else:
+                got = np.concatenate([ctx.decrypt(part) for part in ctx.unstack(o)])
+            got = got[:r["N"]]
+            v = r["v"]
+            if r["op"] == "rank":
+                want = brute_fractional_rank(v)
+            elif r["op"] == "argmin":
+                want = np.eye(r["N"])[int(np.argmin(v))]
+            else:
+                want = np.sort(v)
+            err[r["op"]] = max(err[r["op"]], float(np.max(np.abs(got - want))))
+        # identical alone and in the mix: three requests re-run directly
+        same = True
+        for r, o in list(zip(reqs, outs))[:3]:
+            ctx, blocked = r["ctx"], r["Np"] > 128
+            parts = ctx.unstack(r["ct"]) if blocked else None
+            if r["op"] == "rank":
+                ref = ctx.rank_blocked(parts) if blocked else [ctx.rank(r["ct"])]
+            elif r["op"] == "argmin":
+                ref = ctx.order_stat_blocked(parts, 1) if blocked else [ctx.order_stat(r["ct"], 1, rankfhe.TIES_FIRST)]
+            else:
+                ref = ctx.sort_blocked(parts) if blocked else [ctx.sort(r["ct"])]
+            got = ctx.unstack(o) if blocked else [o]
+            same = same and all(np.array_equal(a.export(), b.export()) for a, b in zip(got, ref))
+        sizes = [r["N"] for r in reqs]
+        return {
+            "requests": len(reqs), "rate_per_s": rate, "wall_s": wall, "requests_per_s": len(reqs) / wall,
+            "elements_per_s": sum(sizes) / wall,
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)), "max_s": float(lat[-1]),
+            "peak_device_bytes": stats["rank_argmin"]["peak_bytes"] + stats["sort_deep"]["peak_bytes"],
+            "rank_argmin_server": stats["rank_argmin"], "deep_server": stats["sort_deep"],
+            "max_abs_error": err, "identical_alone_vs_mix": same,
+            "ops": {op: sum(1 for r in reqs if r["op"] == op) for op in ("rank", "argmin", "sort")},
+            "blocked": sum(1 for r in reqs if r["Np"] > 128),
+            "workload": "Poisson 20 req/s, op uniform {rank, argmin, sort}, N log-uniform 8..1024 padded to 2^k "
+                        "(blocks of 128 above 128, sorts capped at 512), 256-level grid; ranks and argmins <= 128 "
+                        "n=2^16 34+3 limbs 2^45, sorts and blocked argmins 39+3 limbs 2^40, Cmp g^4 f^2",
+        }
+    finally:
+        ca.close()
+        cs.close()
+
+
+# ---------------------------------------------------------------------------
 # clocks
 # ---------------------------------------------------------------------------
 class ClockSampler:
@@ -180,16 +319,29 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def committed_traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
+KERNEL_SOURCE = {   # kernel -> (file, first line of its source, text after its launcher)
+    "ks_inner": ("kernels.cu", "// Up to CH stacked ciphertexts per thread", "// out[c][t] = base_c[t]"),
+}
+
+
+def kernel_source_sha256(kernel: str):
+    f, a, b = KERNEL_SOURCE[kernel]
+    src = open(os.path.join(ROOT, "paper_2412_15126_gb300", "csrc", f)).read()
+    i = src.index(a)
+    return hashlib.sha256(src[i:src.index(b, i)].encode()).hexdigest()
+
+
+def committed_traffic(kernel: str, algorithmic_per_launch: float):
+    """DRAM bytes per launch from the committed ncu capture (profiles/traffic.json),
+    scaled from the captured launch to the timed launches' average by algorithmic
+    bytes; None if the kernel's source changed since the capture."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
-            d = json.load(f)
-        src = open(os.path.join(ROOT, "paper_2412_15126_gb300", "csrc", "kernels.cu"), "rb").read()
-        if d.get("kernels_cu_sha256") != hashlib.sha256(src).hexdigest():
+            d = json.load(f)[kernel]
+        if d["source_sha256"] != kernel_source_sha256(kernel):
             return None
-        return d.get("per_launch_bytes", {}).get(kernel)
+        return d["dram_bytes"] / d["algorithmic_bytes"] * algorithmic_per_launch
     except Exception:
         return None
 
@@ -382,6 +534,7 @@ def run_cuda(args):
     ctx = rankfhe.Context(W["log_n"], W["n_limbs"], W["n_special"], W["digit_size"], W["log_scale"], W["log_q0"],
                           W["log_special"], W["d_g"], W["d_f"], device=local, stream=stream.cuda_stream)
     ctx.keygen(1000 + rank, W["N"])
+    tuned = ctx.autotune() if not args.no_autotune else None
     n_in = args.warmup + args.steps
     vecs = [inputs.gap_vector(W["N"], W["gap"], 1 + rank * 1000 + i) for i in range(n_in)]
     cts = [ctx.encrypt(v, N=W["N"]) for v in vecs]
@@ -511,11 +664,15 @@ def run_cuda(args):
     if not args.no_order_sort and world == 1:
         order_sort = order_sort_workload(stream, local)
 
+    serving = None
+    if args.serve and world == 1:
+        serving = serving_workload(stream, torch.cuda.Stream(), local, count=args.serve)
+
     peak, peak_kind = measured_peaks()
     achieved = None
     if prof["launches"] and prof["ms"] > 0:
         achieved = prof["bytes"] / (prof["ms"] * 1e-3) / 1e9
-    traffic = committed_traffic(args.roofline_kernel)
+    traffic = committed_traffic(args.roofline_kernel, prof["bytes"] / max(prof["launches"], 1))
 
     line = None
     if rank == 0:
@@ -542,6 +699,8 @@ def run_cuda(args):
             "batched": batched,
             "graph": graph,
             "order_sort": order_sort,
+            "serving": serving,
+            "autotune": tuned,
             "kernels": kinds,
             "clocks": clk,
             "gpu_launches": launches,
@@ -552,6 +711,30 @@ def run_cuda(args):
     ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+    return 0
+
+
+def profile_case():
+    """Small case for ncu captures: the rank workload's parameters (n = 2^16, 28 + 3
+    limbs) but only the keys of one rotation (about 1.3 GB on the device); two top-level
+    rotations and one product inside the NVTX range "prof"."""
+    import numpy as np
+    import torch
+    from paper_2412_15126_gb300 import rankfhe
+    W = WORKLOAD
+    ctx = rankfhe.Context(W["log_n"], W["n_limbs"], W["n_special"], W["digit_size"], W["log_scale"], W["log_q0"],
+                          W["log_special"], W["d_g"], W["d_f"], device=0)
+    ctx.keygen(5, 2)
+    ct = ctx.encrypt(np.linspace(0.0, 0.9, 2), N=2)
+    ctx.sync()
+    torch.cuda.nvtx.range_push("prof")
+    for _ in range(2):
+        r = ctx.rotate(ct, -2)
+    m = ctx.mul(ct, ct)
+    ctx.sync()
+    torch.cuda.nvtx.range_pop()
+    print(json.dumps({"profile_case": "ok", "levels": [r.level, m.level]}))
+    ctx.close()
     return 0
 
 
@@ -567,7 +750,12 @@ def main():
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay of the rank steps")
     ap.add_argument("--no-kernel-table", action="store_true", help="skip the per-kernel-kind roofline table")
     ap.add_argument("--no-order-sort", action="store_true", help="skip the 34-limb argmin/argmax/sort latencies")
+    ap.add_argument("--serve", type=int, default=0, help="requests of the serving sample (0: skip)")
+    ap.add_argument("--profile-case", action="store_true", help="run the small ncu capture case and exit")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the built-in launch shapes")
     args = ap.parse_args()
+    if args.profile_case:
+        return profile_case()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

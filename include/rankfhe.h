@@ -126,6 +126,16 @@ rk_status rk_ctx_counters(const rk_ctx* ctx, uint64_t out[4]);
 #define RK_OPT_KS_GROUP_BYTES 2
 rk_status rk_ctx_set_option(rk_ctx* ctx, uint32_t option, int64_t value);
 
+/* Autotune the launch shapes on this device (the paper has no counterpart): times
+ * every candidate block width of the four NTT passes for large (224 limbs) and small
+ * (2 x 3 limbs) limb sets, and, when a rotation key exists, one top-level rotation
+ * with staged and with fused key switching (three L2 group sizes); keeps the fastest
+ * of each.  Results never depend on the choice.  report (may be NULL) receives, for
+ * the NTT slots [small][inverse][column] in that nesting order, (width, us) pairs,
+ * then, with a rotation key, staged us, fused us at 24/48/96 MiB and the choice
+ * (0 staged, else the group MiB); *count receives the number of values. */
+rk_status rk_autotune(rk_ctx* ctx, double* report, size_t cap, size_t* count);
+
 /* ---- keys ----------------------------------------------------------------- */
 
 /* Generate secret, public, relinearisation key and the rotation (Galois) keys
@@ -329,6 +339,9 @@ rk_status rk_server_wait(rk_ctx* ctx, uint64_t ticket, double timeout_s, rk_ct**
  * device), batches run, mean batch size, peak device memory in use above the level at
  * rk_server_start (bytes), requests queued. */
 rk_status rk_server_stats(rk_ctx* ctx, double out[8]);
+/* Latencies (s) of the finished requests in completion order: writes min(cap, count)
+ * values; *count receives the number finished. */
+rk_status rk_server_latencies(rk_ctx* ctx, double* out, size_t cap, size_t* count);
 /* Finish every queued request, stop the worker, free uncollected results. */
 rk_status rk_server_stop(rk_ctx* ctx);
 

@@ -21,6 +21,9 @@ rk_server* server_start(rk_ctx* c, size_t budget, int max_stack);
 uint64_t server_submit(rk_ctx* c, uint32_t op, uint32_t arg, uint32_t flags, const rk_ct* in);
 rk_ct* server_collect(rk_ctx* c, uint64_t ticket, double timeout_s);
 void server_stats(rk_ctx* c, double out[8]);
+void ntt_autotune(rk_ctx* c, std::vector<double>& report);
+void ks_autotune(rk_ctx* c, std::vector<double>& report);
+size_t server_latencies(rk_ctx* c, double* out, size_t cap);
 void server_stop(rk_ctx* c);
 rk_ct* graph_rank_run(rk_graph* g, const rk_ct* in);
 void graph_free(rk_graph* g);
@@ -136,6 +139,20 @@ rk_status rk_ctx_set_option(rk_ctx* ctx, uint32_t option, int64_t value) {
             case RK_OPT_KS_GROUP_BYTES: ctx->ks_group_bytes = (double)value; break;
             default: throw rk_error(RK_EINVAL, "unknown option " + std::to_string(option));
         }
+    });
+}
+
+rk_status rk_autotune(rk_ctx* ctx, double* report, size_t cap, size_t* count) {
+    return guard([&] {
+        need(ctx, "ctx");
+        RK_REQUIRE(!ctx->server, RK_EINVAL, "autotune while a server runs");
+        set_device(ctx);
+        std::vector<double> rep;
+        ntt_autotune(ctx, rep);
+        ks_autotune(ctx, rep);
+        if (report)
+            for (size_t i = 0; i < std::min(cap, rep.size()); i++) report[i] = rep[i];
+        if (count) *count = rep.size();
     });
 }
 
@@ -538,6 +555,15 @@ rk_status rk_server_stats(rk_ctx* ctx, double out[8]) {
         need(ctx, "ctx");
         need(out, "out");
         server_stats(ctx, out);
+    });
+}
+
+rk_status rk_server_latencies(rk_ctx* ctx, double* out, size_t cap, size_t* count) {
+    return guard([&] {
+        need(ctx, "ctx");
+        need(count, "count");
+        RK_REQUIRE(out || cap == 0, RK_EINVAL, "out is NULL");
+        *count = server_latencies(ctx, out, cap);
     });
 }
 

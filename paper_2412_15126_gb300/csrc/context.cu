@@ -321,6 +321,7 @@ void ctx_build(rk_ctx* c, const rk_params* p, int device, void* stream) {
     e.conv.pinv = c->d_conv + pi_off;
     e.conv.rescale = c->d_conv + rs_off;
     e.prof = &c->prof;
+    e.tune = &c->tune;
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) == cudaSuccess && sms > 0) e.sms = sms;
     ntt_init_attributes();

@@ -131,11 +131,13 @@ void ct_free(rk_ct* ct) {
     delete ct;
 }
 
-rk_ct* ct_view(const rk_ct* stack, int b) {
-    RK_REQUIRE(b >= 0 && b < stack->B, RK_EINVAL, "view index out of range");
+rk_ct* ct_view(const rk_ct* stack, int b) { return ct_view_range(stack, b, 1); }
+
+rk_ct* ct_view_range(const rk_ct* stack, int first, int count) {
+    RK_REQUIRE(first >= 0 && count >= 1 && first + count <= stack->B, RK_EINVAL, "view range out of range");
     rk_ct* v = new rk_ct(*stack);
-    v->data = stack->data + (size_t)b * stack->ctx->ct_words();
-    v->B = 1;
+    v->data = stack->data + (size_t)first * stack->ctx->ct_words();
+    v->B = count;
     v->view = true;
     return v;
 }
@@ -155,13 +157,20 @@ rk_ct* ct_clone_meta(const rk_ct* src, int level) {
 rk_ct* ct_stack(rk_ctx* c, const rk_ct* const* in, int count) {
     RK_REQUIRE(count >= 1, RK_EINVAL, "stack of no ciphertexts");
     const rk_ct* a = in[0];
-    for (int i = 0; i < count; i++)
-        RK_REQUIRE(in[i]->B == 1 && in[i]->level == a->level && in[i]->N == a->N && in[i]->Q == a->Q &&
-                       in[i]->n_real == a->n_real && in[i]->layout == a->layout,
+    int total = 0;
+    for (int i = 0; i < count; i++) {
+        RK_REQUIRE(in[i]->level == a->level && in[i]->N == a->N && in[i]->Q == a->Q && in[i]->n_real == a->n_real &&
+                       in[i]->layout == a->layout,
                    RK_EINVAL, "stacked ciphertexts must share level and vector shape");
-    rk_ct* o = ct_alloc(c, a->level, count);
+        total += in[i]->B;
+    }
+    rk_ct* o = ct_alloc(c, a->level, total);
     copy_meta(o, a);
-    for (int i = 0; i < count; i++) copy_polys(c, o->data + (size_t)i * c->ct_words(), in[i]->data, 2, a->level);
+    int at = 0;
+    for (int i = 0; i < count; i++) {   // members of a stacked input keep their order
+        copy_polys(c, o->data + (size_t)at * c->ct_words(), in[i]->data, 2 * in[i]->B, a->level);
+        at += in[i]->B;
+    }
     return o;
 }
 
@@ -493,6 +502,71 @@ void ev_mul(rk_ctx* c, const rk_ct* a, const rk_ct* b, rk_ct* out) {
     copy_meta(out, a);
     c->n_mul += (uint64_t)B;
     ev_rescale_inplace(c, out);
+}
+
+// Times one top-level rotation with the staged key switching and with the fused
+// path at three L2 group sizes (CUDA events on the context stream, zero ciphertext,
+// the first rotation key) and keeps the fastest.  report: staged us, fused us at
+// 24 / 48 / 96 MiB, then the choice (0 staged, else the group MiB).
+void ks_autotune(rk_ctx* c, std::vector<double>& report) {
+    if (c->gal.empty()) return;
+    const u64 g = c->gal.begin()->first;
+    int r = -1;   // a rotation amount with that Galois element
+    for (int k = 1; k < c->n / 2 && r < 0; k++)
+        if (galois_left(c, k) == g) r = k;
+    if (r < 0) return;
+    rk_ct* x = ct_alloc(c, c->L, 1);
+    rk_ct* y = ct_alloc(c, c->L, 1);
+    RK_CUDA(cudaMemsetAsync(x->data, 0, c->ct_words() * 8, c->stream));
+    cudaEvent_t e0, e1;
+    RK_CUDA(cudaEventCreate(&e0));
+    RK_CUDA(cudaEventCreate(&e1));
+    const bool fused0 = c->ks_fused;
+    const double group0 = c->ks_group_bytes;
+    auto time_rot = [&](bool fused, double group) {
+        c->ks_fused = fused;
+        c->ks_group_bytes = group;
+        rk_ct* outs[1] = {y};
+        ev_rotate_many(c, x, &r, 1, outs);   // warm
+        RK_CUDA(cudaEventRecord(e0, c->stream));
+        for (int i = 0; i < 3; i++) ev_rotate_many(c, x, &r, 1, outs);
+        RK_CUDA(cudaEventRecord(e1, c->stream));
+        RK_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        RK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        return 1000.0 * ms / 3;
+    };
+    try {
+        const double mib = 1 << 20;
+        double best = time_rot(false, group0), choice = 0;
+        report.push_back(best);
+        for (double gm : {24.0, 48.0, 96.0}) {
+            const double t = time_rot(true, gm * mib);
+            report.push_back(t);
+            if (t < best) {
+                best = t;
+                choice = gm;
+            }
+        }
+        report.push_back(choice);
+        c->ks_fused = choice > 0;
+        c->ks_group_bytes = choice > 0 ? choice * mib : group0;
+    } catch (...) {
+        c->ks_fused = fused0;
+        c->ks_group_bytes = group0;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        ct_free(x);
+        ct_free(y);
+        throw;
+    }
+    c->n_ks -= 16;   // the timing rotations are not the caller's
+    c->n_rot -= 16;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ct_free(x);
+    ct_free(y);
+    RK_CUDA(cudaStreamSynchronize(c->stream));
 }
 
 // ---------------------------------------------------------------------------

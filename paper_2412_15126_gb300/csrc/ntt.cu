@@ -152,13 +152,20 @@ struct PassGeom {
     size_t smem;
 };
 
-PassGeom geom(int LOG, int count, const LimbSet& s, int sms) {
+bool small_set(const LimbSet& s) { return (long)s.n_limbs * s.n_polys < 16; }
+
+// forced > 0: that many transforms a block (autotuned), clamped to the valid range
+PassGeom geom(int LOG, int count, const LimbSet& s, int sms, int forced = 0) {
     const int P = 1 << (LOG / 2);
     int units = std::min(256 / P, count);
-    // small transforms (few limbs): narrower blocks until the grid covers two waves,
-    // keeping two warps a block (column passes: 32-byte row segments)
     const long limbs = (long)s.n_limbs * s.n_polys;
-    while (units > 1 && P * units > 64 && (long)(count / units) * limbs < 2L * sms) units >>= 1;
+    if (forced > 0) {
+        while (units > forced && units > 1) units >>= 1;
+    } else {
+        // small transforms (few limbs): narrower blocks until the grid covers two
+        // waves, keeping two warps a block (column passes: 32-byte row segments)
+        while (units > 1 && P * units > 64 && (long)(count / units) * limbs < 2L * sms) units >>= 1;
+    }
     PassGeom gm;
     gm.units = units;
     gm.threads = P * units;
@@ -181,9 +188,10 @@ void launch_ntt_forward(const KernelEnv& env, const LimbSet& s, cudaStream_t st)
     const double limbs = (double)s.n_limbs * s.n_polys - (s.skip_ds ? (double)(s.n_polys / s.skip_beta) * s.split : 0.0);
     ProfScope ps(env, KK_NTT_FWD, st, 2, 2.0 * limbs * 8.0 * env.n, limbs * (env.n / 2) * env.logn);
     const int logn = env.logn, loga = logn / 2, logb = logn - loga;
-    PassGeom c = geom(loga, 1 << logb, s, env.sms);
+    const int sm = small_set(s);
+    PassGeom c = geom(loga, 1 << logb, s, env.sms, env.tune ? env.tune->ntt_units[0][1][sm] : 0);
     pass_launch<false, true>(loga, c.grid, c.threads, c.smem, st, s, logn, loga, c.units, env.pc, env.tw.psi);
-    PassGeom r = geom(logb, 1 << loga, s, env.sms);
+    PassGeom r = geom(logb, 1 << loga, s, env.sms, env.tune ? env.tune->ntt_units[0][0][sm] : 0);
     pass_launch<false, false>(logb, r.grid, r.threads, r.smem, st, s, logn, loga, r.units, env.pc, env.tw.psi);
 }
 
@@ -192,8 +200,86 @@ void launch_ntt_inverse(const KernelEnv& env, const LimbSet& s, cudaStream_t st)
     ProfScope ps(env, KK_NTT_INV, st, 2, 2.0 * s.n_limbs * s.n_polys * 8.0 * env.n,
                  (double)s.n_limbs * s.n_polys * (env.n / 2) * env.logn);
     const int logn = env.logn, loga = logn / 2, logb = logn - loga;
-    PassGeom r = geom(logb, 1 << loga, s, env.sms);
+    const int sm = small_set(s);
+    PassGeom r = geom(logb, 1 << loga, s, env.sms, env.tune ? env.tune->ntt_units[1][0][sm] : 0);
     pass_launch<true, false>(logb, r.grid, r.threads, r.smem, st, s, logn, loga, r.units, env.pc, env.tw.ipsi);
-    PassGeom c = geom(loga, 1 << logb, s, env.sms);
+    PassGeom c = geom(loga, 1 << logb, s, env.sms, env.tune ? env.tune->ntt_units[1][1][sm] : 0);
     pass_launch<true, true>(loga, c.grid, c.threads, c.smem, st, s, logn, loga, c.units, env.pc, env.tw.ipsi);
+}
+
+// ---------------------------------------------------------------------------
+// Autotuning of the pass block widths: every candidate width of each pass is timed
+// with CUDA events on the context stream over a representative limb set (28+
+// limbs for the large class, 2 x 3 limbs for the small one); the fastest is kept.
+// The width changes only the launch shape, never a result.
+// ---------------------------------------------------------------------------
+namespace {
+template <bool INV, bool COL>
+float time_pass(const KernelEnv& env, const LimbSet& s, int LOG, int count, int units, cudaStream_t st, cudaEvent_t e0,
+                cudaEvent_t e1, int reps) {
+    const int logn = env.logn, loga = logn / 2;
+    PassGeom g = geom(LOG, count, s, env.sms, units);
+    const u64* tw = INV ? env.tw.ipsi : env.tw.psi;
+    pass_launch<INV, COL>(LOG, g.grid, g.threads, g.smem, st, s, logn, loga, g.units, env.pc, tw);   // warm
+    RK_CUDA(cudaEventRecord(e0, st));
+    for (int r = 0; r < reps; r++) pass_launch<INV, COL>(LOG, g.grid, g.threads, g.smem, st, s, logn, loga, g.units, env.pc, tw);
+    RK_CUDA(cudaEventRecord(e1, st));
+    RK_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    RK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    return ms / reps;
+}
+}  // namespace
+
+// report: per [inverse][column][small] slot the chosen width and its microseconds
+void ntt_autotune(rk_ctx* c, std::vector<double>& report) {
+    const KernelEnv& env = c->env;
+    const int logn = env.logn, loga = logn / 2, logb = logn - loga, n = env.n;
+    const int L1 = c->L + 1;
+    const int polys_large = std::max(1, 224 / L1);
+    u64* buf = nullptr;
+    RK_CUDA(cudaMallocAsync((void**)&buf, (size_t)polys_large * L1 * n * 8, c->stream));
+    RK_CUDA(cudaMemsetAsync(buf, 0, (size_t)polys_large * L1 * n * 8, c->stream));
+    cudaEvent_t e0, e1;
+    RK_CUDA(cudaEventCreate(&e0));
+    RK_CUDA(cudaEventCreate(&e1));
+    TuneTable t;
+    try {
+        for (int sm = 0; sm < 2; sm++) {
+            const LimbSet s = sm ? LimbSet{buf, (size_t)L1 * n, 2, std::min(3, L1), std::min(3, L1), 0, 0}
+                                 : LimbSet{buf, (size_t)L1 * n, polys_large, L1, L1, 0, 0};
+            const int reps = sm ? 20 : 5;
+            for (int inv = 0; inv < 2; inv++)
+                for (int col = 0; col < 2; col++) {
+                    const int LOG = col ? loga : logb, count = 1 << (col ? logb : loga);
+                    const int P = 1 << (LOG / 2);
+                    float best = 1e30f;
+                    int best_u = 0;
+                    for (int u = std::min(256 / P, count); u >= 1 && P * u >= 32; u >>= 1) {
+                        float ms;
+                        if (inv && col) ms = time_pass<true, true>(env, s, LOG, count, u, c->stream, e0, e1, reps);
+                        else if (inv) ms = time_pass<true, false>(env, s, LOG, count, u, c->stream, e0, e1, reps);
+                        else if (col) ms = time_pass<false, true>(env, s, LOG, count, u, c->stream, e0, e1, reps);
+                        else ms = time_pass<false, false>(env, s, LOG, count, u, c->stream, e0, e1, reps);
+                        if (ms < best) {
+                            best = ms;
+                            best_u = u;
+                        }
+                    }
+                    t.ntt_units[inv][col][sm] = best_u;
+                    report.push_back((double)best_u);
+                    report.push_back(1000.0 * best);
+                }
+        }
+    } catch (...) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaFreeAsync(buf, c->stream);
+        throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    RK_CUDA(cudaFreeAsync(buf, c->stream));
+    RK_CUDA(cudaStreamSynchronize(c->stream));
+    c->tune = t;
 }

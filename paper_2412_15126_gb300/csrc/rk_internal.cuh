@@ -108,9 +108,16 @@ struct Profiler {
 };
 
 // Everything a kernel launcher needs: sizes and device tables.
+// Launch shapes chosen by rk_autotune (0 keeps the built-in rule).  NTT block widths
+// (transforms per block) indexed [inverse][column pass][small: fewer than 16 limbs].
+struct TuneTable {
+    int ntt_units[2][2][2] = {};
+};
+
 struct KernelEnv {
     int logn, n, L, alpha;
     int sms = 152;          // multiprocessors of the device (grid sizing)
+    const TuneTable* tune = nullptr;
     const PrimeConst* pc;   // device array [n_primes]
     DevTables tw;
     ConvTables conv;
@@ -161,6 +168,7 @@ struct rk_ctx {
     size_t scratch_words = 0;
     int batch_cap = 1;            // largest stack B the scratch layout is sized for
     rk_server* server = nullptr;  // serving loop, when one runs (it owns the stream meanwhile)
+    TuneTable tune;
     bool ks_fused = false;        // key switching with conversions fused into the NTT passes
     double ks_group_bytes = 48.0 * (1 << 20);   // lifted digits kept in L2 between the fused kernels
     size_t ind_stack_bytes = (size_t)16 << 30;  // working set of one stacked indicator evaluation
@@ -202,6 +210,7 @@ void ensure_batch(rk_ctx* c, int B);   // size the scratch for stacks of B ciphe
 rk_ct* ct_stack(rk_ctx* c, const rk_ct* const* in, int count);        // B = count, copies
 void ct_unstack(rk_ctx* c, const rk_ct* in, rk_ct** outs);            // B outputs of B = 1
 rk_ct* ct_view(const rk_ct* stack, int b);                            // member b, no copy
+rk_ct* ct_view_range(const rk_ct* stack, int first, int count);      // members [first, first+count), no copy
 
 void ev_add(rk_ctx* c, const rk_ct* a, const rk_ct* b, rk_ct* out);
 void ev_sub(rk_ctx* c, const rk_ct* a, const rk_ct* b, rk_ct* out);

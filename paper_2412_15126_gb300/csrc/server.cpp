@@ -271,6 +271,15 @@ void server_stats(rk_ctx* c, double out[8]) {
     out[7] = (double)s->queue.size();
 }
 
+size_t server_latencies(rk_ctx* c, double* out, size_t cap) {
+    rk_server* s = c->server;
+    RK_REQUIRE(s, RK_EINVAL, "no server running on this context");
+    std::lock_guard<std::mutex> lk(s->mu);
+    const size_t m = std::min(cap, s->latency.size());
+    for (size_t i = 0; i < m; i++) out[i] = s->latency[i];
+    return s->latency.size();
+}
+
 // Drains the queue, joins the worker and frees every result nobody collected.
 void server_stop(rk_ctx* c) {
     rk_server* s = c->server;

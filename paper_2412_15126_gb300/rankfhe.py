@@ -67,6 +67,7 @@ _sig("rk_ctx_scales", [_vp, _dp, _sz])
 _sig("rk_sync", [_vp])
 _sig("rk_ctx_counters", [_vp, _u64p])
 _sig("rk_ctx_set_option", [_vp, _u32, ctypes.c_int64])
+_sig("rk_autotune", [_vp, _dp, _sz, ctypes.POINTER(_sz)])
 _sig("rk_keygen", [_vp, ctypes.c_uint64, _u32])
 _sig("rk_keygen_rotations", [_vp, _i32p, _sz])
 _sig("rk_secret_import", [_vp, _i64p, _sz])
@@ -106,6 +107,7 @@ _sig("rk_server_submit", [_vp, _u32, _u32, _u32, _vp, ctypes.POINTER(ctypes.c_ui
 _sig("rk_server_wait", [_vp, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(_vp)])
 _sig("rk_server_stats", [_vp, _dp])
 _sig("rk_server_stop", [_vp])
+_sig("rk_server_latencies", [_vp, _dp, _sz, ctypes.POINTER(_sz)])
 _sig("rk_graph_rank", [_vp, _vp, _u32, ctypes.POINTER(_vp)])
 _sig("rk_graph_run", [_vp, _vp, ctypes.POINTER(_vp)])
 _sig("rk_graph_free", [_vp], None)
@@ -239,6 +241,20 @@ class Context:
 
     def set_option(self, option: int, value: int):
         _check(_L.rk_ctx_set_option(self.handle, option, int(value)))
+
+    def autotune(self) -> dict:
+        """Time candidate launch shapes on this device and keep the fastest (results unchanged)."""
+        out = (ctypes.c_double * 64)()
+        cnt = _sz()
+        _check(_L.rk_autotune(self.handle, out, 64, ctypes.byref(cnt)))
+        v = list(out[:cnt.value])
+        rep = {}
+        for i, slot in enumerate([(s, d, p) for s in ("large", "small") for d in ("fwd", "inv") for p in ("row", "col")]):
+            rep["ntt_%s_%s_%s" % slot] = {"units": int(v[2 * i]), "us": v[2 * i + 1]}
+        if len(v) > 16:
+            rep["ks"] = {"staged_us": v[16], "fused_us": dict(zip(("24MiB", "48MiB", "96MiB"), v[17:20])),
+                         "choice": "staged" if v[20] == 0 else "fused %d MiB" % v[20]}
+        return rep
 
     # ---- keys ----
     def keygen(self, seed: int, max_len: int):
@@ -407,6 +423,13 @@ class Context:
         _check(_L.rk_server_stats(self.handle, out))
         keys = ("finished", "p50_s", "p99_s", "max_s", "batches", "mean_batch", "peak_bytes", "queued")
         return dict(zip(keys, list(out)))
+
+    def server_latencies(self) -> list:
+        cnt = _sz()
+        _check(_L.rk_server_latencies(self.handle, None, 0, ctypes.byref(cnt)))
+        out = (ctypes.c_double * max(cnt.value, 1))()
+        _check(_L.rk_server_latencies(self.handle, out, cnt.value, ctypes.byref(cnt)))
+        return list(out[:cnt.value])
 
     def server_stop(self):
         _check(_L.rk_server_stop(self.handle))

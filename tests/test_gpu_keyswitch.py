@@ -57,3 +57,19 @@ def test_set_option_rejects_unknown():
             ctx.set_option(rankfhe.OPT_KS_GROUP_BYTES, -1)
     finally:
         ctx.close()
+
+
+def test_autotune_keeps_results():
+    """The autotuner changes launch shapes only: a rank is bit-identical before and after."""
+    ctx = helpers.gpu_context("cfg1")
+    try:
+        ctx.keygen(3, 8)
+        ct = ctx.encrypt(inputs.gap_vector(8, 0.05, 9), N=8)
+        before = ctx.rank(ct).export()
+        rep = ctx.autotune()
+        assert rep["ntt_large_fwd_col"]["units"] >= 1 and rep["ntt_small_inv_row"]["us"] > 0
+        assert "ks" in rep
+        after = ctx.rank(ct).export()
+        assert np.array_equal(before, after)
+    finally:
+        ctx.close()

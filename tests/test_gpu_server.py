@@ -35,7 +35,9 @@ def test_server_mix_identical_to_alone():
         tickets = [ctx.server_submit(op, ct, arg, flags) for op, ct, arg, flags in reqs]
         outs = [ctx.server_wait(t) for t in tickets]
         stats = ctx.server_stats()
+        lat = ctx.server_latencies()
         ctx.server_stop()
+        assert len(lat) == len(reqs) and min(lat) > 0
         assert stats["finished"] == len(reqs)
         assert stats["p99_s"] >= stats["p50_s"] > 0
         for (op, ct, arg, flags), got in zip(reqs, outs):
