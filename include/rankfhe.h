@@ -121,9 +121,13 @@ rk_status rk_ctx_counters(const rk_ctx* ctx, uint64_t out[4]);
  * RK_OPT_KS_GROUP_BYTES: bytes of lifted digits the fused path keeps in flight
  *   between its column and row kernels (default 48 MiB, sized for the 129 MB L2);
  *   values below one limb group run one target limb at a time.
+ * RK_OPT_BLOCK_STACKING: 1 (default) runs the blocks and block pairs of
+ *   rk_rank_blocked (flags 0) as stacks; 0 runs every block and pair ciphertext with
+ *   its own launches (the plain per-query form, for comparison).  Same results.
  * Errors: RK_EINVAL for an unknown option or a negative value. */
 #define RK_OPT_KS_FUSED 1
 #define RK_OPT_KS_GROUP_BYTES 2
+#define RK_OPT_BLOCK_STACKING 3
 rk_status rk_ctx_set_option(rk_ctx* ctx, uint32_t option, int64_t value);
 
 /* Autotune the launch shapes on this device (the paper has no counterpart): times
@@ -336,8 +340,9 @@ rk_status rk_server_submit(rk_ctx* ctx, uint32_t op, uint32_t arg, uint32_t flag
  * error status.  Each ticket is collected once; RK_EINVAL for unknown tickets. */
 rk_status rk_server_wait(rk_ctx* ctx, uint64_t ticket, double timeout_s, rk_ct** out);
 /* out[8]: requests finished, p50 and p99 and max latency (s, submit to result on the
- * device), batches run, mean batch size, peak device memory in use above the level at
- * rk_server_start (bytes), requests queued. */
+ * device), batches run, mean batch size, peak device memory in use on the whole device
+ * above the level at rk_server_start (bytes; includes other users of the device),
+ * requests queued. */
 rk_status rk_server_stats(rk_ctx* ctx, double out[8]);
 /* Latencies (s) of the finished requests in completion order: writes min(cap, count)
  * values; *count receives the number finished. */

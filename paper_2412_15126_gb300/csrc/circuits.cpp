@@ -459,23 +459,76 @@ static H stack_of(rk_ctx* c, const std::vector<rk_ct*>& xs) {
     return H(ct_stack(c, p.data(), (int)p.size()));
 }
 
-// Alg. 7: ranks of a vector split into L blocks (one ciphertext each, same shape).
-// The L blocks run as one stack through ReplR/TransR/ReplC, the L(L+1)/2 block
-// comparisons C_{i,j} (j >= i) as one stack through Cmp; then
-// R_i = TransC(SumC(sum_{j<i} (1 - C_{j,i}))) + SumR(sum_{j>=i} C_{i,j}) + 1/2 (Eq. 3).
-void circuit_rank_blocked(rk_ctx* c, const rk_ct* const* blocks, int L, rk_ct** outs) {
+// f on the whole stack, or, when the context runs blocked circuits one ciphertext at
+// a time (the plain per-query form), on each member with its own launches.
+template <class F>
+static H each(rk_ctx* c, Ev& E, H x, F f) {
+    if (c->stack_blocks || x->B == 1) return f(std::move(x));
+    std::vector<H> parts;
+    std::vector<rk_ct*> ps;
+    for (int b = 0; b < x->B; b++) {
+        parts.push_back(f(E.copy(H(ct_view(x.p, b)))));
+        ps.push_back(parts.back().p);
+    }
+    return stack_of(c, ps);
+}
+
+// Members [i Bq, (i+1) Bq) of a stack built from L inputs of Bq members each.
+static H range(const H& st, int i, int Bq) { return H(ct_view_range(st.p, i * Bq, Bq)); }
+
+// outs[i] = a copy of members [i Bq, (i+1) Bq) (block i of every query)
+static void split_blocks(rk_ctx* c, const H& st, int L, rk_ct** outs) {
+    const int Bq = st->B / L;
+    std::vector<rk_ct*> res(L, nullptr);
+    try {
+        for (int i = 0; i < L; i++) {
+            H v = range(st, i, Bq);
+            const rk_ct* one[1] = {v.p};
+            res[i] = ct_stack(c, one, 1);
+        }
+    } catch (...) {
+        for (auto* p : res) ct_free(p);
+        throw;
+    }
+    for (int i = 0; i < L; i++) outs[i] = res[i];
+}
+
+static void check_blocks(rk_ctx* c, const rk_ct* const* blocks, int L, int need, const char* what) {
     RK_REQUIRE(L >= 1, RK_EINVAL, "no blocks");
     const rk_ct* b0 = blocks[0];
-    for (int i = 0; i < L; i++) {
-        RK_REQUIRE(blocks[i]->B == 1 && blocks[i]->level == b0->level && blocks[i]->N == b0->N &&
+    for (int i = 0; i < L; i++)
+        RK_REQUIRE(blocks[i]->B == b0->B && blocks[i]->level == b0->level && blocks[i]->N == b0->N &&
                        blocks[i]->Q == b0->Q && blocks[i]->n_real == b0->N,
-                   RK_EINVAL, "blocks must be single, unpadded ciphertexts of one level and length");
-    }
+                   RK_EINVAL, "blocks must be unpadded ciphertexts (or stacks of one size) of one level and length");
+    check_square(c, b0, need, what);
+}
+
+// Alg. 7: ranks of a vector split into L blocks (one ciphertext each, same shape;
+// each block may be a stack of Bq members, block i of Bq queries).  The L blocks run
+// as one stack through ReplR/TransR/ReplC, the L(L+1)/2 block comparisons C_{i,j}
+// (j >= i) as one stack through Cmp; then
+// R_i = TransC(SumC(sum_{j<i} (1 - C_{j,i}))) + SumR(sum_{j>=i} C_{i,j}) + 1/2 (Eq. 3).
+void circuit_rank_blocked(rk_ctx* c, const rk_ct* const* blocks, int L, rk_ct** outs) {
     const int need = 3 + 3 * (int)(c->prm.d_g + c->prm.d_f);
-    check_square(c, b0, need, "blocked rank");
+    check_blocks(c, blocks, L, need, "blocked rank");
+    const int Bq = blocks[0]->B;
     Ev E{c};
     H V(ct_stack(c, blocks, L));
-    auto rc = row_col_forms(E, V);   // stacks of L
+    std::pair<H, H> rc;   // stacks of L Bq
+    if (c->stack_blocks || V->B == 1) {
+        rc = row_col_forms(E, V);
+    } else {
+        std::vector<H> fr, fc;
+        std::vector<rk_ct*> pr, pc;
+        for (int b = 0; b < V->B; b++) {
+            auto f = row_col_forms(E, E.copy(H(ct_view(V.p, b))));
+            fr.push_back(std::move(f.first));
+            fc.push_back(std::move(f.second));
+            pr.push_back(fr.back().p);
+            pc.push_back(fc.back().p);
+        }
+        rc = std::make_pair(stack_of(c, pr), stack_of(c, pc));
+    }
     std::vector<std::pair<int, int>> pairs;
     std::map<std::pair<int, int>, int> pidx;
     for (int i = 0; i < L; i++)
@@ -486,13 +539,14 @@ void circuit_rank_blocked(rk_ctx* c, const rk_ct* const* blocks, int L, rk_ct** 
     std::vector<H> vr_views, vc_views;
     std::vector<rk_ct*> vr, vc;
     for (auto& pr : pairs) {
-        vr_views.emplace_back(ct_view(rc.first.p, pr.first));
-        vc_views.emplace_back(ct_view(rc.second.p, pr.second));
+        vr_views.push_back(range(rc.first, pr.first, Bq));
+        vc_views.push_back(range(rc.second, pr.second, Bq));
         vr.push_back(vr_views.back().p);
         vc.push_back(vc_views.back().p);
     }
-    H Cst = cmp(E, E.sub(stack_of(c, vr), stack_of(c, vc)), (int)c->prm.d_g, (int)c->prm.d_f);
-    auto Cv = [&](int i, int j) { return H(ct_view(Cst.p, pidx[{i, j}])); };
+    H Cst = each(c, E, E.sub(stack_of(c, vr), stack_of(c, vc)),
+                 [&](H x) { return cmp(E, std::move(x), (int)c->prm.d_g, (int)c->prm.d_f); });
+    auto Cv = [&](int i, int j) { return range(Cst, pidx[{i, j}], Bq); };
     // A_i = sum_{j>=i} C_{i,j}, B_i = sum_{j<i} (1 - C_{j,i}) = i - sum_{j<i} C_{j,i}
     std::vector<H> A, Bm;
     for (int i = 0; i < L; i++) {
@@ -502,38 +556,33 @@ void circuit_rank_blocked(rk_ctx* c, const rk_ct* const* blocks, int L, rk_ct** 
         if (i > 0) {
             H s = E.copy(Cv(0, i));
             for (int j = 1; j < i; j++) s = E.add(s, Cv(j, i));
-            H ng = E.fresh(s, s->level);
-            ev_neg(c, s.p, ng.p);
-            Bm.push_back(E.add_const(ng, (double)i));
+            Bm.push_back(E.add_const(E.neg(s), (double)i));
         }
     }
     std::vector<rk_ct*> ap;
     for (auto& a : A) ap.push_back(a.p);
-    H S = sum_r(E, stack_of(c, ap));   // stack of L
+    H S = each(c, E, stack_of(c, ap), [&](H x) { return sum_r(E, std::move(x)); });   // stack of L Bq
     H T;
     if (L > 1) {
         std::vector<rk_ct*> bp;
         for (auto& b : Bm) bp.push_back(b.p);
-        T = trans_c(E, sum_cols(E, stack_of(c, bp), RK_MASK_COL0));   // stack of L-1
+        T = each(c, E, stack_of(c, bp), [&](H x) { return trans_c(E, sum_cols(E, std::move(x), RK_MASK_COL0)); });
     }
-    std::vector<rk_ct*> res(L, nullptr);
-    try {
-        for (int i = 0; i < L; i++) {
-            H s(ct_view(S.p, i));
-            H R;
-            if (i > 0) {
-                H t(ct_view(T.p, i - 1));
-                R = E.add(E.level_down(s, t->level), t);
-            } else {
-                R = E.level_down(s, s->level - 1);
-            }
-            res[i] = E.add_const(R, 0.5).release();
+    std::vector<H> R;
+    std::vector<rk_ct*> rp;
+    for (int i = 0; i < L; i++) {
+        H si = range(S, i, Bq);
+        H r;
+        if (i > 0) {
+            H ti = range(T, i - 1, Bq);
+            r = E.add(E.level_down(si, ti->level), ti);
+        } else {
+            r = E.level_down(si, si->level - 1);
         }
-    } catch (...) {
-        for (auto* p : res) ct_free(p);
-        throw;
+        R.push_back(E.add_const(r, 0.5));
+        rp.push_back(R.back().p);
     }
-    for (int i = 0; i < L; i++) outs[i] = res[i];
+    split_blocks(c, stack_of(c, rp), L, outs);
 }
 
 // 2 C^2 - C: 1 where the row-form value exceeds the column-form value, 0 at ties
@@ -550,16 +599,6 @@ static H repl_r(Ev& E, H x) {
     return x;
 }
 
-static void check_blocks(rk_ctx* c, const rk_ct* const* blocks, int L, int need, const char* what) {
-    RK_REQUIRE(L >= 1, RK_EINVAL, "no blocks");
-    const rk_ct* b0 = blocks[0];
-    for (int i = 0; i < L; i++)
-        RK_REQUIRE(blocks[i]->B == 1 && blocks[i]->level == b0->level && blocks[i]->N == b0->N && blocks[i]->Q == b0->Q &&
-                       blocks[i]->n_real == b0->N,
-                   RK_EINVAL, "blocks must be single, unpadded ciphertexts of one level and length");
-    check_square(c, b0, need, what);
-}
-
 static int blocked_rank_tc_depth(const rk_ctx* c) { return 1 + 3 * (int)(c->prm.d_g + c->prm.d_f) + 3; }
 
 // Tie-corrected ranks of a multi-ciphertext vector (Alg. 7 with Alg. 6 across blocks).
@@ -573,18 +612,18 @@ static int blocked_rank_tc_depth(const rk_ctx* c) { return 1 + 3 * (int)(c->prm.
 // of the blocks' ReplR forms.
 static std::pair<H, H> blocked_ranks_tc(rk_ctx* c, const rk_ct* const* blocks, int L, bool scaled) {
     Ev E{c};
-    const int Bsz = (int)blocks[0]->N, dg = (int)c->prm.d_g, df = (int)c->prm.d_f;
+    const int Bsz = (int)blocks[0]->N, Bq = blocks[0]->B, dg = (int)c->prm.d_g, df = (int)c->prm.d_f;
     const uint32_t Dn = scaled ? (uint32_t)(L * Bsz) : 0u;
     const uint32_t rmask = scaled ? RK_MASK_ROW0S : RK_MASK_ROW0;
     H V(ct_stack(c, blocks, L));
-    auto rc = row_col_forms(E, V);   // stacks of L
+    auto rc = row_col_forms(E, V);   // stacks of L Bq
     std::vector<H> views;
     std::vector<rk_ct*> dr, dcol, ur, uc;
     std::map<std::pair<int, int>, int> uidx;
     for (int i = 0; i < L; i++) {
-        views.emplace_back(ct_view(rc.first.p, i));
+        views.push_back(range(rc.first, i, Bq));
         dr.push_back(views.back().p);
-        views.emplace_back(ct_view(rc.second.p, i));
+        views.push_back(range(rc.second, i, Bq));
         dcol.push_back(views.back().p);
     }
     for (int i = 0; i < L; i++)
@@ -601,12 +640,12 @@ static std::pair<H, H> blocked_ranks_tc(rk_ctx* c, const rk_ct* const* blocks, i
     }
     std::vector<H> A, Bm;
     for (int i = 0; i < L; i++) {
-        H a = E.copy(H(ct_view(F.p, i)));
-        for (int j = i + 1; j < L; j++) a = E.add(a, H(ct_view(Gd.p, uidx[{i, j}])));
+        H a = E.copy(range(F, i, Bq));
+        for (int j = i + 1; j < L; j++) a = E.add(a, range(Gd, uidx[{i, j}], Bq));
         A.push_back(std::move(a));
         if (i > 0) {
-            H s = E.copy(H(ct_view(G.p, uidx[{0, i}])));
-            for (int j = 1; j < i; j++) s = E.add(s, H(ct_view(G.p, uidx[{j, i}])));
+            H s = E.copy(range(G, uidx[{0, i}], Bq));
+            for (int j = 1; j < i; j++) s = E.add(s, range(G, uidx[{j, i}], Bq));
             Bm.push_back(E.add_const(E.neg(s), (double)i));
         }
     }
@@ -621,7 +660,7 @@ static std::pair<H, H> blocked_ranks_tc(rk_ctx* c, const rk_ct* const* blocks, i
     if (L == 1) return std::make_pair(std::move(S), std::move(rc.first));
     std::vector<rk_ct*> bp;
     for (auto& b : Bm) bp.push_back(b.p);
-    H T = sum_cols(E, stack_of(c, bp), RK_MASK_COL0);   // stack of L - 1
+    H T = sum_cols(E, stack_of(c, bp), RK_MASK_COL0);   // stack of (L - 1) Bq
     {
         const int k = log2_exact((uint32_t)Bsz);
         for (int r = 1; r <= k; r++) T = E.add(T, E.rot(T, (Bsz * (Bsz - 1)) >> r));
@@ -630,11 +669,11 @@ static std::pair<H, H> blocked_ranks_tc(rk_ctx* c, const rk_ct* const* blocks, i
     std::vector<H> R;
     std::vector<rk_ct*> rp;
     for (int i = 0; i < L; i++) {
-        H si(ct_view(S.p, i));
+        H si = range(S, i, Bq);
         if (i == 0) {
             R.push_back(E.copy(si));
         } else {
-            H ti(ct_view(T.p, i - 1));
+            H ti = range(T, i - 1, Bq);
             R.push_back(E.add(si, E.level_down(ti, si->level)));
         }
         rp.push_back(R.back().p);
@@ -642,16 +681,10 @@ static std::pair<H, H> blocked_ranks_tc(rk_ctx* c, const rk_ct* const* blocks, i
     return std::make_pair(stack_of(c, rp), std::move(rc.first));
 }
 
-static void unstack_to(rk_ctx* c, const H& st, rk_ct** outs) {
-    std::vector<rk_ct*> parts(st->B, nullptr);
-    ct_unstack(c, st.p, parts.data());
-    for (int i = 0; i < st->B; i++) outs[i] = parts[i];
-}
-
 void circuit_rank_blocked_tc(rk_ctx* c, const rk_ct* const* blocks, int L, rk_ct** outs) {
     check_blocks(c, blocks, L, blocked_rank_tc_depth(c), "blocked rank");
     auto rr = blocked_ranks_tc(c, blocks, L, false);
-    unstack_to(c, rr.first, outs);
+    split_blocks(c, rr.first, L, outs);
 }
 
 // Alg. 4 on the tie-corrected blocked ranks: O_i = Ind_k(R_i), the indicator the
@@ -665,24 +698,24 @@ void circuit_order_stat_blocked(rk_ctx* c, const rk_ct* const* blocks, int L, ui
     auto rr = blocked_ranks_tc(c, blocks, L, true);
     Ev E{c};
     H O = cheb_ps(E, E.add_const(rr.first, -(double)k / D), co);
-    unstack_to(c, O, outs);
+    split_blocks(c, O, L, outs);
 }
 
 // Alg. 8 on the tie-corrected blocked ranks:
 //   S_i = TransC(SumC(sum_j Ind_0(ReplR(R_j) - offset_i) . ReplR(V_j)))
 // offset_i holds B i + a + 1 in row a: the mask RK_MASK_ROWIDX plus the constant
 // -B i / D (ranks and offsets divided by D = L B).  The L^2 indicators run as stacks of
-// at most `chunk` members so that the Paterson-Stockmeyer working set stays bounded.
+// at most `chunk` pairs so that the Paterson-Stockmeyer working set stays bounded.
 void circuit_sort_blocked(rk_ctx* c, const rk_ct* const* blocks, int L, rk_ct** outs) {
     RK_REQUIRE(L >= 1, RK_EINVAL, "no blocks");
-    const int Bsz = (int)blocks[0]->N;
+    const int Bsz = (int)blocks[0]->N, Bq = blocks[0]->B;
     const uint32_t D = (uint32_t)(L * Bsz);
     const auto& co = indicator_coeffs(c, D);
     check_blocks(c, blocks, L, blocked_rank_tc_depth(c) + cheb_depth((int)co.size()) + 3, "blocked sort");
     auto rr = blocked_ranks_tc(c, blocks, L, true);
     Ev E{c};
-    H RR = E.add_mask_d(repl_r(E, std::move(rr.first)), RK_MASK_ROWIDX, D);   // stack of L
-    const size_t ct_bytes = (size_t)2 * (RR->level + 1) * c->n * 8;
+    H RR = E.add_mask_d(repl_r(E, std::move(rr.first)), RK_MASK_ROWIDX, D);   // stack of L Bq
+    const size_t ct_bytes = (size_t)2 * (RR->level + 1) * c->n * 8 * Bq;
     const size_t live = (size_t)baby_steps((int)co.size()) + 2 * (size_t)cheb_depth((int)co.size()) + 8;
     const int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)L * L, c->ind_stack_bytes / (live * ct_bytes)));
     std::vector<H> acc(L);
@@ -694,19 +727,19 @@ void circuit_sort_blocked(rk_ctx* c, const rk_ct* const* blocks, int L, rk_ct** 
         std::vector<H> in, vr;
         std::vector<rk_ct*> ip;
         for (size_t p = p0; p < p1; p++) {
-            in.push_back(E.add_const(H(ct_view(RR.p, pairs[p].second)), -(double)Bsz * pairs[p].first / D));
+            in.push_back(E.add_const(range(RR, pairs[p].second, Bq), -(double)Bsz * pairs[p].first / D));
             ip.push_back(in.back().p);
         }
         H M = cheb_ps(E, stack_of(c, ip), co);
         in.clear();
         std::vector<rk_ct*> vp;
         for (size_t p = p0; p < p1; p++) {
-            vr.push_back(E.level_down(H(ct_view(rr.second.p, pairs[p].second)), M->level));
+            vr.push_back(E.level_down(range(rr.second, pairs[p].second, Bq), M->level));
             vp.push_back(vr.back().p);
         }
         H P = E.mul(M, stack_of(c, vp));
         for (size_t p = p0; p < p1; p++) {
-            H pm(ct_view(P.p, (int)(p - p0)));
+            H pm = range(P, (int)(p - p0), Bq);
             const int i = pairs[p].first;
             acc[i] = acc[i].p ? E.add(acc[i], pm) : E.copy(pm);
         }
@@ -714,7 +747,7 @@ void circuit_sort_blocked(rk_ctx* c, const rk_ct* const* blocks, int L, rk_ct** 
     std::vector<rk_ct*> ap;
     for (auto& a : acc) ap.push_back(a.p);
     H S = trans_c(E, sum_cols(E, stack_of(c, ap), RK_MASK_COL0));
-    unstack_to(c, S, outs);
+    split_blocks(c, S, L, outs);
 }
 
 rk_ct* circuit_compare_matrix(rk_ctx* c, const rk_ct* in) {

@@ -26,6 +26,7 @@
 #define RK_NTT_COL_BLOCKS 3
 #endif
 
+
 namespace {
 using namespace nttc;
 

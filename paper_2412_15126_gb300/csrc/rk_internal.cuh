@@ -170,8 +170,9 @@ struct rk_ctx {
     rk_server* server = nullptr;  // serving loop, when one runs (it owns the stream meanwhile)
     TuneTable tune;
     bool ks_fused = false;        // key switching with conversions fused into the NTT passes
+    bool stack_blocks = true;     // blocked rank: blocks and block pairs as stacks (else one by one)
     double ks_group_bytes = 48.0 * (1 << 20);   // lifted digits kept in L2 between the fused kernels
-    size_t ind_stack_bytes = (size_t)16 << 30;  // working set of one stacked indicator evaluation
+    size_t ind_stack_bytes = (size_t)4 << 30;   // working set of one stacked indicator evaluation
     // plaintext caches: key = (kind, N, Q, n_real, level)
     std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint32_t, int>, u64*> plain_cache;
     std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint32_t>, std::vector<double>> encodings;

@@ -96,3 +96,42 @@ def test_cfg3_blocked_two_by_64_with_ties(cfg3):
     assert np.max(np.abs(O - first)) < 0.01
     S = np.concatenate([ctx.decrypt(s) for s in ctx.sort_blocked(blocks)])
     assert np.max(np.abs(S - np.sort(v))) < 0.01
+
+
+def test_blocked_stacked_queries_identical_to_alone(ordb):
+    """Blocks given as stacks (block i of two queries) return, per query, exactly the
+    blocks of that query's circuit alone: rank (both forms), order statistic, sort."""
+    from paper_2412_15126_gb300 import rankfhe
+    P, keys, ctx = ordb
+    vs = [np.array([3, 1, 3, 0, 2, 1, 3, 2]) / 8.0, np.array([0.75, 0.125, 0.5, 0.0, 0.625, 0.25, 0.875, 0.375])]
+    qs = [_encrypt_blocks(P, keys, ctx, v, 40 + 10 * i)[1] for i, v in enumerate(vs)]
+    stacked = [ctx.stack([q[b] for q in qs]) for b in range(2)]
+    runs = [
+        (lambda bl: ctx.rank_blocked(bl)),
+        (lambda bl: ctx.rank_blocked(bl, rankfhe.TIES_CORRECT)),
+        (lambda bl: ctx.order_stat_blocked(bl, 3)),
+        (lambda bl: ctx.sort_blocked(bl)),
+    ]
+    for run in runs:
+        together = run(stacked)
+        for qi, q in enumerate(qs):
+            alone = run(q)
+            for b in range(2):
+                assert np.array_equal(ctx.unstack(together[b])[qi].export(), alone[b].export())
+
+
+def test_block_stacking_option_changes_nothing(ordb):
+    """The plain per-query form (every block and pair ciphertext on its own) returns
+    the stacked form's blocks bit for bit."""
+    from paper_2412_15126_gb300 import rankfhe
+    P, keys, ctx = ordb
+    v = np.array([0.75, 0.125, 0.5, 0.0, 0.625, 0.25, 0.875, 0.375, 0.3125, 0.5625, 0.1875, 0.9375])
+    _, g = _encrypt_blocks(P, keys, ctx, v, 60)
+    stacked = [b.export() for b in ctx.rank_blocked(g)]
+    ctx.set_option(rankfhe.OPT_BLOCK_STACKING, 0)
+    try:
+        plain = [b.export() for b in ctx.rank_blocked(g)]
+    finally:
+        ctx.set_option(rankfhe.OPT_BLOCK_STACKING, 1)
+    for a, b in zip(stacked, plain):
+        assert np.array_equal(a, b)
