@@ -277,6 +277,17 @@ rk_status rk_compare_matrix(rk_ctx* ctx, const rk_ct* in, rk_ct** out);
  * other k: fractional ranks).  Errors: RK_EDEPTH, RK_ENOKEY, RK_EINVAL. */
 rk_status rk_order_stat(rk_ctx* ctx, const rk_ct* in, uint32_t k, uint32_t flags, rk_ct** out);
 
+/* Value of the k-th smallest element (Alg. 4 with the value retrieval of Sec. 3.2):
+ * SumC(O . V) with O the tie-corrected one-hot mask of rank k, so the division by the
+ * mask's L1 norm is by one.  The value is in slot 0 of each query block (column 0 of
+ * row 0); the other slots of row 0 are zero.  Errors as rk_order_stat. */
+rk_status rk_order_value(rk_ctx* ctx, const rk_ct* in, uint32_t k, rk_ct** out);
+
+/* Median (Alg. 4's particular case): the (N+1)/2-th smallest value for odd N, the mean
+ * of the N/2-th and (N/2+1)-th for even N, from one tie-corrected rank; in slot 0 as
+ * for rk_order_value.  Errors as rk_order_stat. */
+rk_status rk_median(rk_ctx* ctx, const rk_ct* in, rk_ct** out);
+
 /* Sort (Alg. 5, column form of Sec. 3.3, with the tie-correction offset of Alg. 6):
  * the ascending values in row 0 of the output.  Errors as rk_order_stat. */
 rk_status rk_sort(rk_ctx* ctx, const rk_ct* in, uint32_t flags, rk_ct** out);

@@ -569,10 +569,11 @@ def order_statistic(B, V, N, k, dg, df, Q=1, ties="first", coeffs=None):
     other k use the fractional ranks of Alg. 3.  The ranks leave SumR divided by N
     (mask 'row0s') and Ind_k(r) = p((r - k)/N) with p the sinc^2 window."""
     coeffs = sinc2_window_coeffs(N) if coeffs is None else coeffs
-    C = comparison_matrix(B, V, N, dg, df, Q)
     if ties == "first":
-        t = B.add_const(sum_rows_masked(B, tie_fold(B, C, N, Q, "tie"), N, Q, "row0s"), -k / N)
-    elif k == 1 or k == N:
+        t = B.add_const(ranks_scaled_tc(B, V, N, dg, df, Q), -k / N)
+        return cheb_ps(B, t, coeffs)
+    C = comparison_matrix(B, V, N, dg, df, Q)
+    if k == 1 or k == N:
         C2 = B.mul(C, C)
         Cd = B.level_down(C, B.level(C2))
         if k == 1:
@@ -584,6 +585,35 @@ def order_statistic(B, V, N, k, dg, df, Q=1, ties="first", coeffs=None):
     else:
         t = B.add_const(sum_rows_masked(B, C, N, Q, "row0s"), (0.5 - k) / N)
     return cheb_ps(B, t, coeffs)
+
+
+def ranks_scaled_tc(B, V, N, dg, df, Q=1):
+    """Tie-corrected ranks divided by N (Alg. 3 + Alg. 6, SumR with the mask 'row0s')."""
+    C = comparison_matrix(B, V, N, dg, df, Q)
+    return sum_rows_masked(B, tie_fold(B, C, N, Q, "tie"), N, Q, "row0s")
+
+
+def order_value(B, V, N, k, dg, df, Q=1, coeffs=None):
+    """The k-th smallest value (Alg. 4 with the value retrieval of Sec. 3.2):
+    SumC(O . V) with O the tie-corrected one-hot mask, so that the division by the
+    mask's L1 norm is by 1.  The value sits in slot 0 of each query (column 0 of row 0)."""
+    O = order_statistic(B, V, N, k, dg, df, Q, "first", coeffs)
+    return sum_c(B, B.mul(O, B.level_down(V, B.level(O))), N, Q)
+
+
+def median(B, V, N, dg, df, Q=1, coeffs=None):
+    """Median (Alg. 4's particular case): the (N+1)/2-th statistic for odd N, the mean of
+    the N/2-th and (N/2+1)-th for even N, as SumC((O_a + O_b) . V/2) on one shared rank."""
+    coeffs = sinc2_window_coeffs(N) if coeffs is None else coeffs
+    R = ranks_scaled_tc(B, V, N, dg, df, Q)
+    if N % 2:
+        O = cheb_ps(B, B.add_const(R, -((N + 1) // 2) / N), coeffs)
+        return sum_c(B, B.mul(O, B.level_down(V, B.level(O))), N, Q)
+    Oa = cheb_ps(B, B.add_const(R, -(N // 2) / N), coeffs)
+    Ob = cheb_ps(B, B.add_const(R, -(N // 2 + 1) / N), coeffs)
+    M = B.add(Oa, Ob)
+    Vh = B.mul_scalar(V, 0.5)
+    return sum_c(B, B.mul(M, B.level_down(Vh, B.level(M))), N, Q)
 
 
 def sort(B, V, N, dg, df, Q=1, coeffs=None):

@@ -11,6 +11,8 @@ rk_ct* circuit_compare_matrix(rk_ctx* c, const rk_ct* in);
 void rescale_noalloc(rk_ctx* c, const u64* in, u64* out, int l);
 rk_ct* circuit_order_stat(rk_ctx* c, const rk_ct* in, uint32_t k, uint32_t flags);
 rk_ct* circuit_sort(rk_ctx* c, const rk_ct* in, uint32_t flags);
+rk_ct* circuit_order_value(rk_ctx* c, const rk_ct* in, uint32_t k);
+rk_ct* circuit_median(rk_ctx* c, const rk_ct* in);
 void indicator_import(rk_ctx* c, uint32_t N, const double* coeffs, size_t count);
 void circuit_rank_blocked(rk_ctx* c, const rk_ct* const* blocks, int L, rk_ct** outs);
 void circuit_rank_blocked_tc(rk_ctx* c, const rk_ct* const* blocks, int L, rk_ct** outs);
@@ -426,6 +428,29 @@ rk_status rk_sort(rk_ctx* ctx, const rk_ct* in, uint32_t flags, rk_ct** out) {
         need(out, "out");
         set_device(ctx);
         *out = circuit_sort(ctx, in, flags);
+        check_launch();
+    });
+}
+
+rk_status rk_order_value(rk_ctx* ctx, const rk_ct* in, uint32_t k, rk_ct** out) {
+    return guard([&] {
+        need(ctx, "ctx");
+        same_ctx(ctx, in);
+        need(out, "out");
+        set_device(ctx);
+        RK_REQUIRE(k >= 1 && k <= in->N, RK_EINVAL, "k must be in [1, N]");
+        *out = circuit_order_value(ctx, in, k);
+        check_launch();
+    });
+}
+
+rk_status rk_median(rk_ctx* ctx, const rk_ct* in, rk_ct** out) {
+    return guard([&] {
+        need(ctx, "ctx");
+        same_ctx(ctx, in);
+        need(out, "out");
+        set_device(ctx);
+        *out = circuit_median(ctx, in);
         check_launch();
     });
 }

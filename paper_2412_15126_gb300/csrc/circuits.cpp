@@ -431,6 +431,50 @@ rk_ct* circuit_order_stat(rk_ctx* c, const rk_ct* in, uint32_t k, uint32_t flags
     return cheb_ps(E, t, indicator_coeffs(c, in->N)).release();
 }
 
+static H stack_of(rk_ctx* c, const std::vector<rk_ct*>& xs);
+static H range(const H& st, int i, int Bq);
+
+int order_value_depth(rk_ctx* c, const rk_ct* in) { return order_stat_depth(c, in, 1, RK_TIES_FIRST) + 2; }
+
+// The k-th smallest value (Alg. 4 with the value retrieval of Sec. 3.2): SumC(O . V),
+// O the tie-corrected one-hot mask (its L1 norm is 1, so no division); the value is in
+// slot 0 of each query (column 0 of row 0; SumC's mask clears the other columns).
+rk_ct* circuit_order_value(rk_ctx* c, const rk_ct* in, uint32_t k) {
+    check_square(c, in, order_value_depth(c, in), "order value");
+    Ev E{c};
+    H O(circuit_order_stat(c, in, k, RK_TIES_FIRST));
+    H V(ct_clone_meta(in, in->level));
+    ev_copy(c, in, V.p);
+    return sum_cols(E, E.mul(O, E.level_down(V, O->level)), RK_MASK_COL0).release();
+}
+
+// Median (Alg. 4's particular case): the (N+1)/2-th statistic for odd N, else the mean
+// of the N/2-th and (N/2+1)-th, as SumC((O_a + O_b) . V/2) on one shared rank; the two
+// indicators run as one stack.
+rk_ct* circuit_median(rk_ctx* c, const rk_ct* in) {
+    check_square(c, in, order_value_depth(c, in), "median");
+    const uint32_t N = in->N;
+    const double Nd = (double)N;
+    Ev E{c};
+    H V(ct_clone_meta(in, in->level));
+    ev_copy(c, in, V.p);
+    H C = comparison_matrix(E, V, (int)c->prm.d_g, (int)c->prm.d_f);
+    H R = sum_rows(E, tie_fold(E, C, RK_MASK_TIE), RK_MASK_ROW0S);
+    const auto& co = indicator_coeffs(c, N);
+    if (N % 2) {
+        H O = cheb_ps(E, E.add_const(R, -(double)((N + 1) / 2) / Nd), co);
+        return sum_cols(E, E.mul(O, E.level_down(V, O->level)), RK_MASK_COL0).release();
+    }
+    H ta = E.add_const(R, -(double)(N / 2) / Nd);
+    H tb = E.add_const(R, -(double)(N / 2 + 1) / Nd);
+    std::vector<rk_ct*> tp = {ta.p, tb.p};
+    H O2 = cheb_ps(E, stack_of(c, tp), co);
+    const int B = in->B;
+    H M = E.add(range(O2, 0, B), range(O2, 1, B));
+    H Vh = E.mul_scalar(V, 0.5);
+    return sum_cols(E, E.mul(M, E.level_down(Vh, M->level)), RK_MASK_COL0).release();
+}
+
 int sort_depth(rk_ctx* c, const rk_ct* in) {
     const int dc = 3 * (int)(c->prm.d_g + c->prm.d_f);
     return 1 + dc + 2 + 1 + cheb_depth((int)indicator_coeffs(c, in->N).size()) + 1 + 1;

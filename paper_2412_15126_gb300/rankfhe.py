@@ -100,6 +100,8 @@ _sig("rk_rank", [_vp, _vp, _u32, ctypes.POINTER(_vp)])
 _sig("rk_compare_matrix", [_vp, _vp, ctypes.POINTER(_vp)])
 _sig("rk_order_stat", [_vp, _vp, _u32, _u32, ctypes.POINTER(_vp)])
 _sig("rk_sort", [_vp, _vp, _u32, ctypes.POINTER(_vp)])
+_sig("rk_order_value", [_vp, _vp, _u32, ctypes.POINTER(_vp)])
+_sig("rk_median", [_vp, _vp, ctypes.POINTER(_vp)])
 _sig("rk_indicator_import", [_vp, _u32, _dp, _sz])
 _sig("rk_rank_batch", [_vp, ctypes.POINTER(_vp), _sz, _u32, ctypes.POINTER(_vp)])
 _sig("rk_server_start", [_vp, _sz, _u32])
@@ -382,6 +384,12 @@ class Context:
 
     def sort(self, ct, flags=0):
         return self._out(_L.rk_sort, ct.handle, flags)
+
+    def order_value(self, ct, k):
+        return self._out(_L.rk_order_value, ct.handle, int(k))
+
+    def median(self, ct):
+        return self._out(_L.rk_median, ct.handle)
 
     def indicator_import(self, N, coeffs):
         c = np.ascontiguousarray(coeffs, dtype=np.float64)

@@ -100,3 +100,28 @@ def test_cfg3_argmin_argmax_sort_n128(cfg3, seed):
     assert np.max(np.abs(o - (v == v.max()))) < 0.01
     s = ctx.decrypt(ctx.sort(ct))
     assert np.max(np.abs(s - np.sort(v))) < 0.01
+
+
+@pytest.mark.parametrize("name", list(VECS))
+def test_order_value_and_median_bit_exact(ord_setup, name):
+    P, keys, ctx, rk = ord_setup
+    v = VECS[name]
+    ct = ckks.encrypt(P, keys, v, 6)
+    B = C.OracleCkks(P, keys)
+    ref = C.order_value(B, ct, 8, 3, 2, 1)
+    g = ctx.order_value(ctx.ct_import(ct.c, ct.level, N=8), 3)
+    assert g.level == ref.level
+    assert np.array_equal(g.export(), ref.c)
+    assert abs(ctx.decrypt(g)[0] - np.sort(v)[2]) < 0.01
+    ref = C.median(B, ct, 8, 2, 1)
+    g = ctx.median(ctx.ct_import(ct.c, ct.level, N=8))
+    assert np.array_equal(g.export(), ref.c)
+    assert abs(ctx.decrypt(g)[0] - np.median(v)) < 0.01
+
+
+@pytest.mark.parametrize("seed", [3])
+def test_cfg3_median_n128(cfg3, seed):
+    ctx = cfg3
+    v = inputs.grid_vector(128, 64, seed)
+    m = ctx.decrypt(ctx.median(ctx.encrypt(v, N=128)))
+    assert abs(m[0] - np.median(v)) < 0.01

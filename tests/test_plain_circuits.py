@@ -317,3 +317,27 @@ def test_blocked_sort_is_sorted_vector(Bsz, L):
     assert np.max(np.abs(got - np.sort(v))) < 1e-3
     for S in Ss:   # nothing outside row 0 of each block
         assert np.all(np.abs(B.values(S)[Bsz:Bsz * Bsz]) < 1e-6)
+
+
+@pytest.mark.parametrize("name", ["ties", "distinct"])
+def test_order_value_and_median(name):
+    """Value retrieval SumC(O . V) (Sec. 3.2) gives the k-th smallest value; the median
+    is the mean of the two middle statistics for even N (numpy's median)."""
+    v = {"ties": np.array([3, 1, 3, 0, 2, 1, 3, 2]) / 8.0,
+         "distinct": np.array([0.5, 0.125, 0.875, 0.25, 0.0, 0.625, 0.375, 0.75])}[name]
+    for k in (1, 4, 5, 8):
+        B = C.PlainSlots(128, 60)
+        got = B.values(C.order_value(B, B.fresh(v), 8, k, 4, 2))
+        assert abs(got[0] - np.sort(v)[k - 1]) < 1e-6
+    B = C.PlainSlots(128, 60)
+    got = B.values(C.median(B, B.fresh(v), 8, 4, 2))
+    assert abs(got[0] - np.median(v)) < 1e-6
+    assert np.all(np.abs(got[1:8]) < 1e-6)          # row 0 keeps only column 0 (SumC's mask)
+
+
+def test_order_value_middle_statistic():
+    """The value of a middle statistic (the odd-N median's form) of distinct values."""
+    v = np.array([0.3, 0.9, 0.1, 0.6, 0.2, 0.8, 0.4, 0.7])
+    B = C.PlainSlots(128, 60)
+    got = B.values(C.order_value(B, B.fresh(v), 8, 4, 4, 2))
+    assert abs(got[0] - np.sort(v)[3]) < 1e-6
