@@ -153,13 +153,14 @@ def serving_workload(stream_a, stream_b, device, count=120, rate=20.0):
     try:
         ca.keygen(501, 128)
         cs.keygen(502, 128)
-        # client encoding: values v -> v/2 in [0, 1/2), padding slots 1/2 + k/512, all distinct
-        # and above every value, so padding neither changes a real element's rank nor forms
-        # a cluster of ties (the tie offset accumulates the comparator's error at a tie once
-        # per tied partner); every gap stays >= 2^-9, the comparator's design gap
+        # client encoding: values v -> v/2 in [0, 1/2), padding slots 1/2 + min(k, 255)/512,
+        # above every value, so padding never changes a real element's rank.  A sort (at most
+        # 255 padding slots) gets distinct padding: the tie offset accumulates the comparator's
+        # error at a tie once per tied partner, and a cluster of equal padding values would
+        # blur the ranks the sort's indicator reads; every gap stays >= 2^-9
         for r in reqs:   # sorts and blocked argmins need the deeper chain
             ctx = cs if (r["op"] == "sort" or (r["op"] == "argmin" and r["Np"] > 128)) else ca
-            x = 0.5 + np.arange(r["Np"]) / 512.0
+            x = 0.5 + np.minimum(np.arange(r["Np"]) - r["N"], 255).clip(0) / 512.0
             x[:r["N"]] = r["v"] / 2.0
             r["ctx"] = ctx
             if r["Np"] <= 128:
@@ -245,8 +246,8 @@ def serving_workload(stream_a, stream_b, device, count=120, rate=20.0):
             "ops": {op: sum(1 for r in reqs if r["op"] == op) for op in ("rank", "argmin", "sort")},
             "blocked": sum(1 for r in reqs if r["Np"] > 128),
             "workload": "Poisson 20 req/s, op uniform {rank, argmin, sort}, N log-uniform 8..1024 padded to 2^k "
-                        "(blocks of 128 above 128, sorts capped at 512), 256-level grid encoded as v/2 with distinct pads "
-                        "1/2 + k/512; ranks and argmins <= 128 "
+                        "(blocks of 128 above 128, sorts capped at 512), 256-level grid encoded as v/2 with padding "
+                        "1/2 + min(k, 255)/512; ranks and argmins <= 128 "
                         "n=2^16 34+3 limbs 2^45, sorts and blocked argmins 39+3 limbs 2^40, Cmp g^4 f^2",
         }
     finally:

@@ -20,10 +20,13 @@
 
 #include "ntt_core.cuh"
 
-// Resident blocks of 256 threads per SM the column passes are compiled for (the
-// row passes keep two): three caps them at 80 registers a thread.
+// Resident blocks of 256 threads per SM the passes are compiled for: three caps a
+// thread at 80 registers, two at 128.
 #ifndef RK_NTT_COL_BLOCKS
 #define RK_NTT_COL_BLOCKS 3
+#endif
+#ifndef RK_NTT_ROW_BLOCKS
+#define RK_NTT_ROW_BLOCKS 2
 #endif
 
 
@@ -31,7 +34,7 @@ namespace {
 using namespace nttc;
 
 template <int LOG, bool INV, bool COL>
-__global__ void __launch_bounds__(256, (LOG <= 8 && COL ? RK_NTT_COL_BLOCKS : 2)) k_ntt_pass(LimbSet s, int logn, int loga, int units, const PrimeConst* __restrict__ pc,
+__global__ void __launch_bounds__(256, (LOG <= 8 ? (COL ? RK_NTT_COL_BLOCKS : RK_NTT_ROW_BLOCKS) : 2)) k_ntt_pass(LimbSet s, int logn, int loga, int units, const PrimeConst* __restrict__ pc,
                                                   const u64* __restrict__ tw) {
     using S = Shape<LOG>;
     constexpr int P = S::P, E = S::E;
