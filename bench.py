@@ -53,6 +53,41 @@ def workload_config(extra=None):
     return cfg
 
 
+SMALL_WORKLOAD = dict(log_n=13, n_limbs=14, n_special=1, digit_size=1, log_scale=40, log_q0=40, log_special=61,
+                      d_g=2, d_f=1, N=8, gap=0.05)
+
+
+def small_rank_workload(stream, device, reps=20):
+    """Rank of an 8-element vector (gap 0.05) at n = 2^13, 14 limbs + 1 special prime,
+    Cmp g^2 f^1: latency with inputs resident, CUDA events on the library stream."""
+    import numpy as np
+    import torch
+    from paper_2412_15126_gb300 import inputs, rankfhe
+    from oracle.circuits import brute_fractional_rank
+    W = SMALL_WORKLOAD
+    ctx = rankfhe.Context(W["log_n"], W["n_limbs"], W["n_special"], W["digit_size"], W["log_scale"], W["log_q0"],
+                          W["log_special"], W["d_g"], W["d_f"], device=device, stream=stream.cuda_stream)
+    try:
+        ctx.keygen(808, W["N"])
+        vecs = [inputs.gap_vector(W["N"], W["gap"], 900 + i) for i in range(reps + 3)]
+        cts = [ctx.encrypt(v, N=W["N"]) for v in vecs]
+        for ct in cts[:3]:
+            ctx.rank(ct).free()
+        ctx.sync()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+            outs = [ctx.rank(ct) for ct in cts[3:]]
+            ev1.record(stream)
+        ev1.synchronize()
+        err = max(float(np.max(np.abs(ctx.decrypt(o) - brute_fractional_rank(v)))) for o, v in zip(outs, vecs[3:]))
+        return {"workload": "rank N=8, gap 0.05, n=2^13, 14 limbs + 1 special, scale 2^40, Cmp g^2 f^1",
+                "ms": ev0.elapsed_time(ev1) / reps, "max_rank_error": err}
+    finally:
+        ctx.close()
+
+
 ORDER_WORKLOAD = dict(log_n=16, n_limbs=34, n_special=3, digit_size=3, log_scale=45, log_q0=60, log_special=61,
                       d_g=3, d_f=2, N=128, levels=64)
 
@@ -77,11 +112,13 @@ def order_sort_workload(stream, device, reps=3, seed=3):
             "argmin_first": lambda ct: ctx.order_stat(ct, 1, rankfhe.TIES_FIRST),
             "argmax_all": lambda ct: ctx.order_stat(ct, W["N"], rankfhe.TIES_ALL),
             "sort": lambda ct: ctx.sort(ct),
+            "median": lambda ct: ctx.median(ct),
         }
         exact = {
             "argmin_first": lambda v: np.eye(len(v))[int(np.argmin(v))],
             "argmax_all": lambda v: (v == v.max()).astype(float),
             "sort": lambda v: np.sort(v),
+            "median": lambda v: np.median(v),
         }
         out = {"workload": "N=128 on a 64-level grid (ties), n=2^16, 34+3 limbs, scale 2^45, Cmp g^3 f^2, "
                            "indicator degree 1023"}
@@ -97,7 +134,10 @@ def order_sort_workload(stream, device, reps=3, seed=3):
                     res.append(fn(ct))
                 ev1.record(stream)
             ev1.synchronize()
-            err = max(float(np.max(np.abs(ctx.decrypt(r) - exact[name](v)))) for r, v in zip(res, vecs[1:]))
+            if name == "median":   # the value sits in slot 0
+                err = max(abs(float(ctx.decrypt(r)[0]) - exact[name](v)) for r, v in zip(res, vecs[1:]))
+            else:
+                err = max(float(np.max(np.abs(ctx.decrypt(r) - exact[name](v)))) for r, v in zip(res, vecs[1:]))
             out[name] = {"ms": ev0.elapsed_time(ev1) / reps, "max_error": err}
             for r in res:
                 r.free()
@@ -329,16 +369,53 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-KERNEL_SOURCE = {   # kernel -> (file, first line of its source, text after its launcher)
-    "ks_inner": ("kernels.cu", "// Up to CH stacked ciphertexts per thread", "// out[c][t] = base_c[t]"),
+KERNEL_SOURCE = {   # kernel -> [(file, first line of its source or None, text after it or None)]
+    "ks_inner": [("kernels.cu", "// Up to CH stacked ciphertexts per thread", "// out[c][t] = base_c[t]")],
+    "ntt_fwd": [("ntt.cu", None, None), ("ntt_core.cuh", None, None)],
 }
 
 
 def kernel_source_sha256(kernel: str):
-    f, a, b = KERNEL_SOURCE[kernel]
-    src = open(os.path.join(ROOT, "paper_2412_15126_gb300", "csrc", f)).read()
-    i = src.index(a)
-    return hashlib.sha256(src[i:src.index(b, i)].encode()).hexdigest()
+    h = hashlib.sha256()
+    for f, a, b in KERNEL_SOURCE[kernel]:
+        src = open(os.path.join(ROOT, "paper_2412_15126_gb300", "csrc", f)).read()
+        if a is not None:
+            i = src.index(a)
+            src = src[i:src.index(b, i)]
+        h.update(src.encode())
+    return h.hexdigest()
+
+
+GB300_SMS, GB300_SCHEDULERS, GB300_MAX_SM_MHZ = 152, 4, 2070.0
+
+
+def ntt_roofline(prof, clk):
+    """Forward NTT (both passes), the dominant kernel: bound by integer issue, so the
+    ceiling is the SMs' issue rate (152 SMs x 4 schedulers x one warp instruction a
+    clock at the maximum SM clock) divided by the instructions one radix-2 butterfly
+    costs in this kernel (ncu capture in profiles/traffic.json).  achieved = butterflies
+    per launch / CUDA-event launch duration."""
+    if not prof["launches"] or prof["ms"] <= 0:
+        return None
+    per_launch = prof["ops"] / prof["launches"]
+    avg_s = prof["ms"] * 1e-3 / prof["launches"]
+    achieved = per_launch / avg_s / 1e9
+    ipb = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            ipb = json.load(f)["ntt_fwd"]["thread_instructions_per_butterfly"]
+    except Exception:
+        pass
+    peak = None
+    if ipb:
+        peak = GB300_SMS * GB300_SCHEDULERS * 32 * GB300_MAX_SM_MHZ * 1e6 / ipb / 1e9
+    return {"bound": "alu", "kernel": "ntt_fwd (column + row pass)", "achieved": achieved, "peak": peak,
+            "peak_kind": "derived: 152 SMs x 4 schedulers x 1 warp instruction/clock x 2070 MHz / instructions per "
+                         "butterfly (ncu)", "unit": "Gbutterfly/s", "frac": (achieved / peak) if peak else None,
+            "traffic": committed_traffic("ntt_fwd", prof["bytes"] / prof["launches"]),
+            "algorithmic_bytes_per_launch": prof["bytes"] / prof["launches"], "butterflies_per_launch": per_launch,
+            "avg_launch_us": avg_s * 1e6, "launches": prof["launches"],
+            "sm_mhz_under_load": (clk or {}).get("sm_mhz")}
 
 
 def committed_traffic(kernel: str, algorithmic_per_launch: float):
@@ -605,7 +682,7 @@ def run_cuda(args):
     clocks.start()
     time.sleep(0.2)
     launches0 = ctx.launch_count()
-    ctx.profile_start(args.roofline_kernel)
+    ctx.profile_start("ntt_fwd,ks_inner")   # the dominant (issue-bound) and the HBM-bound kernel
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     outs = []
@@ -618,7 +695,9 @@ def run_cuda(args):
     ev1.synchronize()
     torch.cuda.nvtx.range_pop()
     ctx.sync()
-    prof = ctx.profile_stop()
+    ctx.profile_stop()
+    prof_ntt = ctx.profile_kind("ntt_fwd")
+    prof_ks = ctx.profile_kind("ks_inner")
     launches = ctx.launch_count() - launches0
     clk = clocks.stop()
     barrier()
@@ -659,17 +738,18 @@ def run_cuda(args):
     h2d = 2 * W["n_limbs"] * n * 8
     d2h = 2 * (out_level + 1) * n * 8 if out_level is not None else 0
 
-    # per kernel kind: algorithmic bytes over event-timed duration, one rank step each
+    # per kernel kind: algorithmic bytes over event-timed duration, one profiled rank step
     kinds = None
     if not args.no_kernel_table:
         kinds = {}
-        for kind in ("ntt_fwd", "ntt_inv", "modup", "ks_inner", "moddown_conv", "ks_combine", "tensor", "rescale",
-                     "pointwise"):
-            ctx.sync()
-            ctx.profile_start(kind)
-            ctx.rank(cts[args.warmup]).free()
-            ctx.sync()
-            pr = ctx.profile_stop()
+        names = ("ntt_fwd", "ntt_inv", "modup", "ks_inner", "moddown_conv", "ks_combine", "tensor", "rescale",
+                 "pointwise")
+        ctx.sync()
+        ctx.profile_start(",".join(names))
+        ctx.rank(cts[args.warmup]).free()
+        ctx.profile_stop()
+        for kind in names:
+            pr = ctx.profile_kind(kind)
             if pr["launches"]:
                 gbs = pr["bytes"] / (pr["ms"] * 1e-3) / 1e9
                 kinds[kind] = {"launches": pr["launches"], "ms_per_step": pr["ms"], "gb": pr["bytes"] / 1e9,
@@ -702,18 +782,23 @@ def run_cuda(args):
         batched = batched_workload(ctx)
 
     order_sort = None
+    small = None
     if not args.no_order_sort and world == 1:
         order_sort = order_sort_workload(stream, local)
+        small = small_rank_workload(stream, local)
 
     serving = None
     if args.serve and world == 1:
         serving = serving_workload(stream, torch.cuda.Stream(), local, count=args.serve)
 
     peak, peak_kind = measured_peaks()
-    achieved = None
-    if prof["launches"] and prof["ms"] > 0:
-        achieved = prof["bytes"] / (prof["ms"] * 1e-3) / 1e9
-    traffic = committed_traffic(args.roofline_kernel, prof["bytes"] / max(prof["launches"], 1))
+    roof_ntt = ntt_roofline(prof_ntt, clk)
+    ks_achieved = prof_ks["bytes"] / (prof_ks["ms"] * 1e-3) / 1e9 if prof_ks["launches"] and prof_ks["ms"] > 0 else None
+    roof_ks = {"bound": "hbm", "kernel": "ks_inner", "achieved": ks_achieved, "peak": peak, "peak_kind": peak_kind,
+               "unit": "GB/s", "frac": (ks_achieved / peak) if ks_achieved else None,
+               "traffic": committed_traffic("ks_inner", prof_ks["bytes"] / max(prof_ks["launches"], 1)),
+               "algorithmic_bytes_per_launch": prof_ks["bytes"] / max(prof_ks["launches"], 1),
+               "avg_launch_us": prof_ks["ms"] * 1000.0 / max(prof_ks["launches"], 1), "launches": prof_ks["launches"]}
 
     line = None
     if rank == 0:
@@ -729,17 +814,13 @@ def run_cuda(args):
             "config": workload_config({"ranks_per_s_total": world * 1000.0 / ms_per_step,
                                        "max_rank_error": err}),
             "e2e": {"value": e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "roofline": {"bound": "hbm", "kernel": args.roofline_kernel, "achieved": achieved, "peak": peak,
-                         "peak_kind": peak_kind, "unit": "GB/s",
-                         "frac": (achieved / peak) if achieved else None,
-                         "traffic": traffic,
-                         "algorithmic_bytes_per_launch": prof["bytes"] / max(prof["launches"], 1),
-                         "avg_launch_us": prof["ms"] * 1000.0 / max(prof["launches"], 1),
-                         "launches": prof["launches"]},
+            "roofline": roof_ntt,
+            "roofline_hbm": roof_ks,
             "cpu_baseline": cpu,
             "batched": batched,
             "graph": graph,
             "order_sort": order_sort,
+            "rank8": small,
             "serving": serving,
             "autotune": tuned,
             "kernels": kinds,
@@ -785,7 +866,6 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
-    ap.add_argument("--roofline-kernel", default="ks_inner")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 104-query batched workload")
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay of the rank steps")

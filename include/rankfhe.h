@@ -387,16 +387,18 @@ rk_status rk_ntt_inverse(rk_ctx* ctx, uint64_t* d_data, uint32_t limbs, uint32_t
 
 /* ---- measurement ------------------------------------------------------------- */
 
-/* Time every launch of one kernel kind with CUDA events on the context stream:
- * "ntt_fwd", "ntt_inv", "modup", "ks_inner", "moddown_conv", "ks_combine",
- * "tensor", "rescale", "pointwise", "client"; NULL or "" stops timing.  Resets the
- * accumulators.  Errors: RK_EINVAL for an unknown name. */
-rk_status rk_profile_start(rk_ctx* ctx, const char* kind);
-/* Synchronise and report the timed launches since rk_profile_start:
- * out[0] total milliseconds, out[1] launches (an NTT counts its two passes as one),
- * out[2] algorithmic bytes (each input word read once, each output word written
- * once), out[3] modular products.  Stops timing. */
+/* Time every launch of the listed kernel kinds (comma-separated) with CUDA events on
+ * the context stream: "ntt_fwd", "ntt_inv", "modup", "ks_inner", "moddown_conv",
+ * "ks_combine", "tensor", "rescale", "pointwise", "client"; NULL or "" stops timing.
+ * Resets the accumulators.  Errors: RK_EINVAL for an unknown name. */
+rk_status rk_profile_start(rk_ctx* ctx, const char* kinds);
+/* Synchronise and report the timed launches since rk_profile_start, summed over the
+ * kinds: out[0] total milliseconds, out[1] launches (an NTT counts its two passes as
+ * one), out[2] algorithmic bytes (each input word read once, each output word written
+ * once), out[3] modular products (an NTT: its butterflies).  Stops timing. */
 rk_status rk_profile_stop(rk_ctx* ctx, double out[4]);
+/* The same four figures for one kind, after rk_profile_stop. */
+rk_status rk_profile_kind(const rk_ctx* ctx, const char* kind, double out[4]);
 /* Number of kernels this context has launched since creation. */
 uint64_t rk_launch_count(const rk_ctx* ctx);
 

@@ -654,18 +654,31 @@ rk_status rk_rescale_noalloc(rk_ctx* ctx, const uint64_t* d_in, uint64_t* d_out,
     });
 }
 
-rk_status rk_profile_start(rk_ctx* ctx, const char* kind) {
+rk_status rk_profile_start(rk_ctx* ctx, const char* kinds) {
     return guard([&] {
         need(ctx, "ctx");
         Profiler& p = ctx->prof;
-        p.target = -1;
+        p.mask = 0;
         p.used = 0;
-        p.bytes = p.ops = 0;
-        p.timed = 0;
-        if (!kind || !kind[0]) return;
-        for (int k = 0; k < KK_COUNT; k++)
-            if (std::strcmp(kind, kKernelKindNames[k]) == 0) p.target = k;
-        RK_REQUIRE(p.target >= 0, RK_EINVAL, std::string("unknown kernel kind ") + kind);
+        for (int k = 0; k < KK_COUNT; k++) {
+            p.bytes[k] = p.ops[k] = p.ms[k] = 0;
+            p.timed[k] = 0;
+        }
+        if (!kinds || !kinds[0]) return;
+        uint32_t mask = 0;
+        std::string list(kinds);
+        size_t at = 0;
+        while (at <= list.size()) {
+            const size_t end = std::min(list.find(',', at), list.size());
+            const std::string name = list.substr(at, end - at);
+            int found = -1;
+            for (int k = 0; k < KK_COUNT; k++)
+                if (name == kKernelKindNames[k]) found = k;
+            RK_REQUIRE(found >= 0, RK_EINVAL, "unknown kernel kind " + name);
+            mask |= 1u << found;
+            at = end + 1;
+        }
+        p.mask = mask;
     });
 }
 
@@ -676,18 +689,37 @@ rk_status rk_profile_stop(rk_ctx* ctx, double out[4]) {
         set_device(ctx);
         Profiler& p = ctx->prof;
         RK_CUDA(cudaStreamSynchronize(ctx->stream));
-        double ms = 0;
         for (size_t i = 0; i + 1 < p.used; i += 2) {
             float t = 0;
             RK_CUDA(cudaEventElapsedTime(&t, p.ev[i], p.ev[i + 1]));
-            ms += t;
+            p.ms[p.ev_kind[i]] += t;
         }
-        out[0] = ms;
-        out[1] = (double)p.timed;
-        out[2] = p.bytes;
-        out[3] = p.ops;
-        p.target = -1;
+        out[0] = out[1] = out[2] = out[3] = 0;
+        for (int k = 0; k < KK_COUNT; k++) {
+            out[0] += p.ms[k];
+            out[1] += (double)p.timed[k];
+            out[2] += p.bytes[k];
+            out[3] += p.ops[k];
+        }
+        p.mask = 0;
         p.used = 0;
+    });
+}
+
+rk_status rk_profile_kind(const rk_ctx* ctx, const char* kind, double out[4]) {
+    return guard([&] {
+        need(ctx, "ctx");
+        need(kind, "kind");
+        need(out, "out");
+        int found = -1;
+        for (int k = 0; k < KK_COUNT; k++)
+            if (std::strcmp(kind, kKernelKindNames[k]) == 0) found = k;
+        RK_REQUIRE(found >= 0, RK_EINVAL, std::string("unknown kernel kind ") + kind);
+        const Profiler& p = ctx->prof;
+        out[0] = p.ms[found];
+        out[1] = (double)p.timed[found];
+        out[2] = p.bytes[found];
+        out[3] = p.ops[found];
     });
 }
 

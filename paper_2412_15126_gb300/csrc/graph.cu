@@ -32,9 +32,9 @@ rk_graph* graph_rank_capture(rk_ctx* c, const rk_ct* tmpl, uint32_t flags) {
     g->input = ct_clone_meta(tmpl, tmpl->level);
     ev_copy(c, tmpl, g->input);
     RK_CUDA(cudaStreamSynchronize(c->stream));
-    const int saved = c->prof.target;
+    const uint32_t saved = c->prof.mask;
     const uint64_t launches = c->prof.launches;   // captured kernels run only on replay
-    c->prof.target = -1;
+    c->prof.mask = 0;
     RK_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     rk_ct* out = nullptr;
     try {
@@ -43,14 +43,14 @@ rk_graph* graph_rank_capture(rk_ctx* c, const rk_ct* tmpl, uint32_t flags) {
         cudaGraph_t dummy = nullptr;
         cudaStreamEndCapture(c->stream, &dummy);
         if (dummy) cudaGraphDestroy(dummy);
-        c->prof.target = saved;
+        c->prof.mask = saved;
         c->prof.launches = launches;
         ct_free(g->input);
         delete g;
         throw;
     }
     cudaError_t e = cudaStreamEndCapture(c->stream, &g->graph);
-    c->prof.target = saved;
+    c->prof.mask = saved;
     c->prof.launches = launches;
     g->out_meta = *out;
     g->out_meta.view = true;     // the graph owns this address

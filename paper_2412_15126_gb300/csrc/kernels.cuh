@@ -4,18 +4,19 @@
 #include "rk_internal.cuh"
 
 
-// Counts every launch; when `kind` is the profiled kind, brackets the launch(es) with
-// CUDA events on the launching stream and accumulates the algorithmic bytes/products.
+// Counts every launch; when `kind` is among the profiled kinds, brackets the launch(es)
+// with CUDA events on the launching stream and accumulates the algorithmic bytes/products.
 struct ProfScope {
     Profiler* p;
     bool on = false;
+    int kind;
     cudaStream_t st;
     double bytes, ops;
-    ProfScope(const KernelEnv& e, int kind, cudaStream_t s, int nlaunch, double b, double o)
-        : p(e.prof), st(s), bytes(b), ops(o) {
+    ProfScope(const KernelEnv& e, int k, cudaStream_t s, int nlaunch, double b, double o)
+        : p(e.prof), kind(k), st(s), bytes(b), ops(o) {
         if (!p) return;
         p->launches += (uint64_t)nlaunch;
-        if (p->target == kind) {
+        if (p->mask & (1u << kind)) {
             on = true;
             record();
         }
@@ -25,15 +26,17 @@ struct ProfScope {
             cudaEvent_t ev;
             cudaEventCreate(&ev);
             p->ev.push_back(ev);
+            p->ev_kind.push_back(-1);
         }
+        p->ev_kind[p->used] = kind;
         cudaEventRecord(p->ev[p->used++], st);
     }
     ~ProfScope() {
         if (on) {
             record();
-            p->bytes += bytes;
-            p->ops += ops;
-            p->timed++;
+            p->bytes[kind] += bytes;
+            p->ops[kind] += ops;
+            p->timed[kind]++;
         }
     }
 };

@@ -100,11 +100,14 @@ extern const char* const kKernelKindNames[KK_COUNT];
 // Launch counter and CUDA-event timing of one kernel kind on the context stream.
 struct Profiler {
     uint64_t launches = 0;        // every kernel this library launched
-    int target = -1;              // kind being timed, -1 = none
+    uint32_t mask = 0;            // kinds being timed (bit k for kind k), 0 = none
     std::vector<cudaEvent_t> ev;  // start/stop pairs
+    std::vector<int> ev_kind;     // kind of each pair
     size_t used = 0;
-    double bytes = 0, ops = 0;    // algorithmic bytes and modular products of the timed launches
-    uint64_t timed = 0;
+    // per kind, since the last rk_profile_start: algorithmic bytes, modular products,
+    // timed launches; milliseconds once rk_profile_stop has read the events
+    double bytes[KK_COUNT] = {}, ops[KK_COUNT] = {}, ms[KK_COUNT] = {};
+    uint64_t timed[KK_COUNT] = {};
 };
 
 // Everything a kernel launcher needs: sizes and device tables.

@@ -117,6 +117,7 @@ _sig("rk_ntt_forward", [_vp, _vp, _u32, _u32])
 _sig("rk_ntt_inverse", [_vp, _vp, _u32, _u32])
 _sig("rk_profile_start", [_vp, ctypes.c_char_p])
 _sig("rk_profile_stop", [_vp, _dp])
+_sig("rk_profile_kind", [_vp, ctypes.c_char_p, _dp])
 _sig("rk_launch_count", [_vp], ctypes.c_uint64)
 _sig("rk_last_error", [], ctypes.c_char_p)
 
@@ -461,6 +462,11 @@ class Context:
     def profile_stop(self) -> dict:
         out = (ctypes.c_double * 4)()
         _check(_L.rk_profile_stop(self.handle, out))
+        return {"ms": out[0], "launches": int(out[1]), "bytes": out[2], "ops": out[3]}
+
+    def profile_kind(self, kind) -> dict:
+        out = (ctypes.c_double * 4)()
+        _check(_L.rk_profile_kind(self.handle, kind.encode(), out))
         return {"ms": out[0], "launches": int(out[1]), "bytes": out[2], "ops": out[3]}
 
     def launch_count(self) -> int:
