@@ -162,6 +162,17 @@ rk_status rk_secret_import(rk_ctx* ctx, const int64_t* s, size_t n);
  * Errors: RK_EINVAL if words does not match, RK_ENOMEM. */
 rk_status rk_key_import(rk_ctx* ctx, uint32_t kind, uint64_t galois, const uint64_t* coeffs, size_t words);
 
+/* Every switching key of the context (relinearisation, then Galois keys by element)
+ * as one blob of little-endian 64-bit words: magic "RKKEYS01", log_n, L+1+alpha,
+ * beta_L, the key count K, then K records [kind][galois][words][words of
+ * rk_key_import's layout].  buf NULL: *len receives the size only; otherwise buf
+ * (8-byte aligned, cap >= *len bytes) receives the blob.  The secret is not included.
+ * Errors: RK_EINVAL (buffer too small or unaligned), RK_ECUDA. */
+rk_status rk_keys_export(rk_ctx* ctx, uint8_t* buf, size_t cap, size_t* len);
+/* Import every key of a blob from rk_keys_export (parameters must match).
+ * Errors: RK_EFORMAT (bad magic, parameters, length), RK_EINVAL, RK_ENOMEM. */
+rk_status rk_keys_import(rk_ctx* ctx, const uint8_t* buf, size_t len);
+
 /* Galois element of a left rotation by r slots: 5^r mod 2n. */
 uint64_t rk_galois_left(const rk_ctx* ctx, int32_t r);
 
@@ -321,6 +332,9 @@ rk_status rk_sort_blocked(rk_ctx* ctx, const rk_ct* const* blocks, uint32_t L, u
  * and vector shape are stacked and run as one circuit (one launch per kernel for
  * the group); out[i] is the rank ciphertext of in[i]. */
 rk_status rk_rank_batch(rk_ctx* ctx, const rk_ct* const* in, size_t count, uint32_t flags, rk_ct** out);
+/* The same grouping for order statistics (one k for all) and sorts. */
+rk_status rk_order_stat_batch(rk_ctx* ctx, const rk_ct* const* in, size_t count, uint32_t k, uint32_t flags, rk_ct** out);
+rk_status rk_sort_batch(rk_ctx* ctx, const rk_ct* const* in, size_t count, uint32_t flags, rk_ct** out);
 
 /* ---- serving loop ------------------------------------------------------------ */
 

@@ -70,6 +70,42 @@ void check_launch() {
 }
 }  // namespace
 
+// Queries of one level and vector shape are stacked and run as one circuit.
+template <class F>
+static void run_grouped(rk_ctx* ctx, const rk_ct* const* in, size_t count, rk_ct** out, F circuit) {
+    std::map<std::tuple<int, uint32_t, uint32_t, uint32_t, uint32_t>, std::vector<size_t>> groups;
+    for (size_t i = 0; i < count; i++) {
+        same_ctx(ctx, in[i]);
+        RK_REQUIRE(in[i]->B == 1, RK_EINVAL, "batched calls take single ciphertexts");
+        groups[std::make_tuple(in[i]->level, in[i]->N, in[i]->Q, in[i]->n_real, in[i]->layout)].push_back(i);
+    }
+    std::vector<rk_ct*> res(count, nullptr);
+    try {
+        for (auto& g : groups) {
+            std::vector<const rk_ct*> members;
+            for (size_t i : g.second) members.push_back(in[i]);
+            rk_ct* st = ct_stack(ctx, members.data(), (int)members.size());
+            rk_ct* r = nullptr;
+            try {
+                r = circuit(st);
+            } catch (...) {
+                ct_free(st);
+                throw;
+            }
+            ct_free(st);
+            std::vector<rk_ct*> parts(members.size());
+            ct_unstack(ctx, r, parts.data());
+            ct_free(r);
+            for (size_t k = 0; k < g.second.size(); k++) res[g.second[k]] = parts[k];
+        }
+        check_launch();
+    } catch (...) {
+        for (auto* p : res) ct_free(p);
+        throw;
+    }
+    for (size_t i = 0; i < count; i++) out[i] = res[i];
+}
+
 extern "C" {
 
 const char* rk_last_error(void) { return g_last_error.c_str(); }
@@ -472,38 +508,84 @@ rk_status rk_rank_batch(rk_ctx* ctx, const rk_ct* const* in, size_t count, uint3
         need(in, "in");
         need(out, "out");
         set_device(ctx);
-        // group single ciphertexts of one level and vector shape; each group is one stacked circuit
-        std::map<std::tuple<int, uint32_t, uint32_t, uint32_t, uint32_t>, std::vector<size_t>> groups;
-        for (size_t i = 0; i < count; i++) {
-            same_ctx(ctx, in[i]);
-            RK_REQUIRE(in[i]->B == 1, RK_EINVAL, "rk_rank_batch takes single ciphertexts");
-            groups[std::make_tuple(in[i]->level, in[i]->N, in[i]->Q, in[i]->n_real, in[i]->layout)].push_back(i);
+        run_grouped(ctx, in, count, out, [&](const rk_ct* st) { return circuit_rank(ctx, st, flags); });
+    });
+}
+
+rk_status rk_order_stat_batch(rk_ctx* ctx, const rk_ct* const* in, size_t count, uint32_t k, uint32_t flags, rk_ct** out) {
+    return guard([&] {
+        need(ctx, "ctx");
+        need(in, "in");
+        need(out, "out");
+        set_device(ctx);
+        run_grouped(ctx, in, count, out, [&](const rk_ct* st) { return circuit_order_stat(ctx, st, k, flags); });
+    });
+}
+
+rk_status rk_sort_batch(rk_ctx* ctx, const rk_ct* const* in, size_t count, uint32_t flags, rk_ct** out) {
+    return guard([&] {
+        need(ctx, "ctx");
+        need(in, "in");
+        need(out, "out");
+        set_device(ctx);
+        run_grouped(ctx, in, count, out, [&](const rk_ct* st) { return circuit_sort(ctx, st, flags); });
+    });
+}
+
+// ---- key set blob: little-endian u64 words ----
+//   magic, log_n, n_primes (L+1+alpha), beta_L, K, then K records
+//   [kind][galois][words][words x u64 in rk_key_import's layout]
+static const uint64_t kKeysMagic = 0x31305359454b4b52ull;   // "RKKEYS01"
+
+rk_status rk_keys_export(rk_ctx* ctx, uint8_t* buf, size_t cap, size_t* len) {
+    return guard([&] {
+        need(ctx, "ctx");
+        need(len, "len");
+        set_device(ctx);
+        const size_t words = (size_t)ctx->beta(ctx->L) * 2 * ctx->n_primes * ctx->n;
+        const size_t K = (ctx->rlk.data ? 1 : 0) + ctx->gal.size();
+        const size_t total = 8 * (5 + K * (3 + words));
+        *len = total;
+        if (!buf) return;
+        RK_REQUIRE(cap >= total, RK_EINVAL, "buffer too small for the key set");
+        uint64_t* w = reinterpret_cast<uint64_t*>(buf);
+        RK_REQUIRE(reinterpret_cast<uintptr_t>(buf) % 8 == 0, RK_EINVAL, "buffer must be 8-byte aligned");
+        w[0] = kKeysMagic;
+        w[1] = (uint64_t)ctx->log_n;
+        w[2] = (uint64_t)ctx->n_primes;
+        w[3] = (uint64_t)ctx->beta(ctx->L);
+        w[4] = K;
+        size_t at = 5;
+        auto put = [&](uint64_t kind, uint64_t g, const u64* key) {
+            w[at] = kind;
+            w[at + 1] = g;
+            w[at + 2] = words;
+            key_export(ctx, key, reinterpret_cast<u64*>(w + at + 3));
+            at += 3 + words;
+        };
+        if (ctx->rlk.data) put(RK_KEY_RELIN, 0, ctx->rlk.data);
+        for (auto& kv : ctx->gal) put(RK_KEY_GALOIS, kv.first, kv.second.data);
+    });
+}
+
+rk_status rk_keys_import(rk_ctx* ctx, const uint8_t* buf, size_t len) {
+    return guard([&] {
+        need(ctx, "ctx");
+        need(buf, "buf");
+        set_device(ctx);
+        RK_REQUIRE(len >= 40 && len % 8 == 0 && reinterpret_cast<uintptr_t>(buf) % 8 == 0, RK_EFORMAT,
+                   "key set blob: bad length or alignment");
+        const uint64_t* w = reinterpret_cast<const uint64_t*>(buf);
+        const size_t nw = len / 8;
+        RK_REQUIRE(w[0] == kKeysMagic, RK_EFORMAT, "key set blob: bad magic");
+        RK_REQUIRE(w[1] == (uint64_t)ctx->log_n && w[2] == (uint64_t)ctx->n_primes && w[3] == (uint64_t)ctx->beta(ctx->L),
+                   RK_EFORMAT, "key set blob: parameters differ from the context's");
+        size_t at = 5;
+        for (uint64_t k = 0; k < w[4]; k++) {
+            RK_REQUIRE(at + 3 <= nw && at + 3 + w[at + 2] <= nw, RK_EFORMAT, "key set blob: truncated");
+            key_import(ctx, (uint32_t)w[at], w[at + 1], w + at + 3, (size_t)w[at + 2]);
+            at += 3 + (size_t)w[at + 2];
         }
-        std::vector<rk_ct*> res(count, nullptr);
-        try {
-            for (auto& g : groups) {
-                std::vector<const rk_ct*> members;
-                for (size_t i : g.second) members.push_back(in[i]);
-                rk_ct* st = ct_stack(ctx, members.data(), (int)members.size());
-                rk_ct* r = nullptr;
-                try {
-                    r = circuit_rank(ctx, st, flags);
-                } catch (...) {
-                    ct_free(st);
-                    throw;
-                }
-                ct_free(st);
-                std::vector<rk_ct*> parts(members.size());
-                ct_unstack(ctx, r, parts.data());
-                ct_free(r);
-                for (size_t k = 0; k < g.second.size(); k++) res[g.second[k]] = parts[k];
-            }
-            check_launch();
-        } catch (...) {
-            for (auto* p : res) ct_free(p);
-            throw;
-        }
-        for (size_t i = 0; i < count; i++) out[i] = res[i];
     });
 }
 

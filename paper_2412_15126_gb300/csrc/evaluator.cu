@@ -703,6 +703,20 @@ void key_import(rk_ctx* c, uint32_t kind, uint64_t galois, const uint64_t* coeff
     }
 }
 
+// A switching key in rk_key_import's layout: [beta_L][2][L+1+alpha][n] words,
+// coefficient domain, plain residues.
+void key_export(rk_ctx* c, const u64* key, u64* host_out) {
+    const int NP = c->n_primes, BL = c->beta(c->L);
+    const size_t n = c->n, words = (size_t)BL * 2 * NP * n;
+    u64* tmp = nullptr;
+    RK_CUDA(cudaMallocAsync((void**)&tmp, words * 8, c->stream));
+    for (int p = 0; p < 2 * BL; p++) launch_from_mont(c->env, tmp + (size_t)p * NP * n, key + (size_t)p * NP * n, NP, c->stream);
+    launch_ntt_inverse(c->env, ls_all(tmp, (size_t)NP * n, BL * 2, NP), c->stream);
+    RK_CUDA(cudaMemcpyAsync(host_out, tmp, words * 8, cudaMemcpyDeviceToHost, c->stream));
+    RK_CUDA(cudaFreeAsync(tmp, c->stream));
+    RK_CUDA(cudaStreamSynchronize(c->stream));
+}
+
 // ---------------------------------------------------------------------------
 // Client operations
 // ---------------------------------------------------------------------------

@@ -213,6 +213,7 @@ rk_ct* ct_clone_meta(const rk_ct* src, int level);
 void ensure_batch(rk_ctx* c, int B);   // size the scratch for stacks of B ciphertexts
 rk_ct* ct_stack(rk_ctx* c, const rk_ct* const* in, int count);        // B = count, copies
 void ct_unstack(rk_ctx* c, const rk_ct* in, rk_ct** outs);            // B outputs of B = 1
+void key_export(rk_ctx* c, const u64* key, u64* host_out);
 rk_ct* ct_view(const rk_ct* stack, int b);                            // member b, no copy
 rk_ct* ct_view_range(const rk_ct* stack, int first, int count);      // members [first, first+count), no copy
 

@@ -104,6 +104,10 @@ _sig("rk_order_value", [_vp, _vp, _u32, ctypes.POINTER(_vp)])
 _sig("rk_median", [_vp, _vp, ctypes.POINTER(_vp)])
 _sig("rk_indicator_import", [_vp, _u32, _dp, _sz])
 _sig("rk_rank_batch", [_vp, ctypes.POINTER(_vp), _sz, _u32, ctypes.POINTER(_vp)])
+_sig("rk_order_stat_batch", [_vp, ctypes.POINTER(_vp), _sz, _u32, _u32, ctypes.POINTER(_vp)])
+_sig("rk_sort_batch", [_vp, ctypes.POINTER(_vp), _sz, _u32, ctypes.POINTER(_vp)])
+_sig("rk_keys_export", [_vp, ctypes.c_void_p, _sz, ctypes.POINTER(_sz)])
+_sig("rk_keys_import", [_vp, ctypes.c_void_p, _sz])
 _sig("rk_server_start", [_vp, _sz, _u32])
 _sig("rk_server_submit", [_vp, _u32, _u32, _u32, _vp, ctypes.POINTER(ctypes.c_uint64)])
 _sig("rk_server_wait", [_vp, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(_vp)])
@@ -449,6 +453,30 @@ class Context:
         h = _vp()
         _check(_L.rk_graph_rank(self.handle, template.handle, flags, ctypes.byref(h)))
         return RankGraph(self, h.value)
+
+    def order_stat_batch(self, cts, k, flags=0):
+        ins = (_vp * len(cts))(*[c.handle.value for c in cts])
+        outs = (_vp * len(cts))()
+        _check(_L.rk_order_stat_batch(self.handle, ins, len(cts), int(k), flags, outs))
+        return [Ciphertext(self, o) for o in outs]
+
+    def sort_batch(self, cts, flags=0):
+        ins = (_vp * len(cts))(*[c.handle.value for c in cts])
+        outs = (_vp * len(cts))()
+        _check(_L.rk_sort_batch(self.handle, ins, len(cts), flags, outs))
+        return [Ciphertext(self, o) for o in outs]
+
+    def keys_export(self) -> np.ndarray:
+        """Every switching key as one blob (uint64 words); see rk_keys_export."""
+        size = _sz()
+        _check(_L.rk_keys_export(self.handle, None, 0, ctypes.byref(size)))
+        blob = np.empty(size.value // 8, dtype=np.uint64)
+        _check(_L.rk_keys_export(self.handle, blob.ctypes.data, size.value, ctypes.byref(size)))
+        return blob
+
+    def keys_import(self, blob: np.ndarray):
+        b = np.ascontiguousarray(blob, dtype=np.uint64)
+        _check(_L.rk_keys_import(self.handle, b.ctypes.data, b.nbytes))
 
     def rank_batch(self, cts, flags=0):
         ins = (_vp * len(cts))(*[c.handle.value for c in cts])

@@ -115,3 +115,46 @@ def test_graph_rank_bit_identical_to_direct(cfg2, flags):
             assert np.array_equal(part.export(), ctx.rank(ct, flags).export())
     finally:
         gs.free()
+
+
+def test_order_stat_and_sort_batch_identical_alone():
+    from paper_2412_15126_gb300 import rankfhe
+    ctx = helpers.gpu_context("ord")
+    try:
+        ctx.keygen(66, 8)
+        cts = [ctx.encrypt(inputs.grid_vector(N, 8, 40 + i), N=N) for i, N in enumerate((8, 4, 8, 8, 4))]
+        for batch, alone in ((lambda c: ctx.order_stat_batch(c, 2, rankfhe.TIES_FIRST),
+                              lambda x: ctx.order_stat(x, 2, rankfhe.TIES_FIRST)),
+                             (lambda c: ctx.sort_batch(c), lambda x: ctx.sort(x))):
+            for ct, out in zip(cts, batch(cts)):
+                assert np.array_equal(out.export(), alone(ct).export())
+    finally:
+        ctx.close()
+
+
+def test_keys_export_returns_the_imported_keys():
+    """rk_keys_export gives back, word for word, the oracle's keys imported into the
+    context (coefficient domain, plain residues), and importing the blob again changes
+    no result."""
+    P = helpers.oracle_params("small")
+    keys = ckks.keygen(P, 17, helpers.galois_elts(P, [1, -1, 4]))
+    ctx = helpers.gpu_context("small")
+    try:
+        helpers.import_keys(ctx, keys)
+        blob = ctx.keys_export()
+        assert int(blob[0]) == 0x31305359454B4B52 and int(blob[4]) == 1 + len(keys.gal)
+        words = int(blob[7])
+        recs, at = {}, 5
+        for _ in range(int(blob[4])):
+            recs[(int(blob[at]), int(blob[at + 1]))] = blob[at + 3: at + 3 + int(blob[at + 2])]
+            at += 3 + int(blob[at + 2])
+        assert np.array_equal(recs[(1, 0)], np.asarray(keys.rlk.data, dtype=np.uint64).reshape(-1))
+        for g, k in keys.gal.items():
+            assert np.array_equal(recs[(2, g)], np.asarray(k.data, dtype=np.uint64).reshape(-1))
+        assert words == recs[(1, 0)].size
+        ct = ctx.encrypt(inputs.gap_vector(8, 0.05, 3), N=8)
+        before = ctx.rotate(ct, 1).export()
+        ctx.keys_import(blob)
+        assert np.array_equal(ctx.rotate(ct, 1).export(), before)
+    finally:
+        ctx.close()
