@@ -245,8 +245,9 @@ rk_status rk_encoding_import(rk_ctx* ctx, uint32_t kind, uint32_t N, uint32_t Q,
         need(u, "u");
         RK_REQUIRE(n == (size_t)ctx->n, RK_EINVAL, "encoding length must be n");
         RK_REQUIRE(kind >= RK_MASK_ROW0 && kind <= RK_MASK_ROWIDX, RK_EINVAL, "unknown mask kind");
-        const uint32_t nr = kind == RK_MASK_VALID ? n_real : 0;
+        const uint32_t nr = mask_nreal(kind, n_real);
         ctx->encodings[std::make_tuple(kind, N, Q, nr)] = std::vector<double>(u, u + n);
+        ctx->generation++;
         for (auto it = ctx->plain_cache.begin(); it != ctx->plain_cache.end();) {
             if (std::get<0>(it->first) == kind && std::get<1>(it->first) == N && std::get<2>(it->first) == Q &&
                 std::get<3>(it->first) == nr) {

@@ -383,6 +383,7 @@ rk_ct* circuit_rank(rk_ctx* c, const rk_ct* in, uint32_t flags) {
 void indicator_import(rk_ctx* c, uint32_t N, const double* coeffs, size_t count) {
     RK_REQUIRE(count >= 4 && (count & (count - 1)) == 0, RK_EINVAL, "coefficient count must be a power of two >= 4");
     c->indicator[N] = std::vector<double>(coeffs, coeffs + count);
+    c->generation++;
 }
 
 static void check_square(rk_ctx* c, const rk_ct* in, int need, const char* what) {

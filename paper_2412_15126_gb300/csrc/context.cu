@@ -107,6 +107,7 @@ u64* rk_ctx::scratch(size_t words) {
     if (words > scratch_words) {
         RK_CUDA(cudaStreamSynchronize(stream));
         if (d_scratch) RK_CUDA(cudaFree(d_scratch));
+        generation++;
         d_scratch = nullptr;
         RK_CUDA(cudaMalloc((void**)&d_scratch, words * 8));
         scratch_words = words;

@@ -642,7 +642,10 @@ static u64* make_switch_key(rk_ctx* c, const u64* sp, u64 stream_id) {
 static void make_relin_key(rk_ctx* c) {
     Scratch S = scratch_layout(c);
     launch_square_secret(c->env, S.misc, c->d_sk, c->n_primes, c->stream);
-    if (c->rlk.data) cudaFree(c->rlk.data);
+    if (c->rlk.data) {
+        cudaFree(c->rlk.data);
+        c->generation++;
+    }
     c->rlk.data = make_switch_key(c, S.misc, 1);
 }
 
@@ -693,6 +696,7 @@ void key_import(rk_ctx* c, uint32_t kind, uint64_t galois, const uint64_t* coeff
     launch_ntt_forward(c->env, ls_all(buf, (size_t)NP * n, BL * 2, NP), c->stream);
     launch_to_mont(c->env, ls_all(buf, (size_t)NP * n, BL * 2, NP), c->stream);
     RK_CUDA(cudaStreamSynchronize(c->stream));
+    c->generation++;
     if (kind == RK_KEY_RELIN) {
         if (c->rlk.data) cudaFree(c->rlk.data);
         c->rlk.data = buf;

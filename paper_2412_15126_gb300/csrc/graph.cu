@@ -19,6 +19,7 @@ struct rk_graph {
     bool launched = false;
     uint32_t flags = 0;
     uint64_t kernels = 0;       // kernel nodes in the graph
+    uint64_t generation = 0;    // context generation the graph's pointers belong to
 };
 
 rk_graph* graph_rank_capture(rk_ctx* c, const rk_ct* tmpl, uint32_t flags) {
@@ -29,6 +30,7 @@ rk_graph* graph_rank_capture(rk_ctx* c, const rk_ct* tmpl, uint32_t flags) {
     rk_graph* g = new rk_graph();
     g->ctx = c;
     g->flags = flags;
+    g->generation = c->generation;
     g->input = ct_clone_meta(tmpl, tmpl->level);
     ev_copy(c, tmpl, g->input);
     RK_CUDA(cudaStreamSynchronize(c->stream));
@@ -85,6 +87,8 @@ rk_ct* graph_rank_run(rk_graph* g, const rk_ct* in) {
     RK_REQUIRE(in->level == t->level && in->B == t->B && in->N == t->N && in->Q == t->Q && in->n_real == t->n_real &&
                    in->layout == t->layout,
                RK_EINVAL, "input shape differs from the captured one");
+    RK_REQUIRE(g->generation == c->generation, RK_EINVAL,
+               "the context changed since the capture (scratch grown, keys, masks or indicator replaced): capture again");
     ev_copy(c, in, g->input);
     RK_CUDA(cudaGraphLaunch(g->exec, c->stream));
     g->launched = true;

@@ -111,6 +111,12 @@ struct Profiler {
 };
 
 // Everything a kernel launcher needs: sizes and device tables.
+// Mask kinds whose n_real argument is part of the plaintext (padding length or the
+// denominator of a scaled mask); the others ignore it.
+inline uint32_t mask_nreal(uint32_t kind, uint32_t n_real) {
+    return (kind == RK_MASK_VALID || kind == RK_MASK_ROW0S || kind == RK_MASK_COL0S || kind == RK_MASK_ROWIDX) ? n_real : 0;
+}
+
 // Launch shapes chosen by rk_autotune (0 keeps the built-in rule).  NTT block widths
 // (transforms per block) indexed [inverse][column pass][small: fewer than 16 limbs].
 struct TuneTable {
@@ -171,6 +177,9 @@ struct rk_ctx {
     size_t scratch_words = 0;
     int batch_cap = 1;            // largest stack B the scratch layout is sized for
     rk_server* server = nullptr;  // serving loop, when one runs (it owns the stream meanwhile)
+    // Bumped whenever a buffer that captured CUDA graphs point into is replaced (scratch
+    // growth, switching keys, cached plaintexts, indicator coefficients).
+    uint64_t generation = 0;
     TuneTable tune;
     bool ks_fused = false;        // key switching with conversions fused into the NTT passes
     bool stack_blocks = true;     // blocked rank: blocks and block pairs as stacks (else one by one)

@@ -158,3 +158,24 @@ def test_keys_export_returns_the_imported_keys():
         assert np.array_equal(ctx.rotate(ct, 1).export(), before)
     finally:
         ctx.close()
+
+
+def test_graph_refuses_replay_after_scratch_growth(cfg2):
+    """A captured graph points into the context's scratch: once a larger stack grows
+    the scratch, replaying the old graph is refused (no access to freed memory)."""
+    from paper_2412_15126_gb300 import rankfhe
+    ctx = cfg2
+    cts = [ctx.encrypt(inputs.gap_vector(32, 2.0 ** -9, 900 + i), N=32) for i in range(12)]
+    g = ctx.graph_rank(cts[0])
+    try:
+        g.run(cts[1]).free()
+        ctx.rank(ctx.stack(cts))          # twelve members: the scratch grows
+        with pytest.raises(rankfhe.RkError):
+            g.run(cts[2])
+    finally:
+        g.free()
+    g2 = ctx.graph_rank(cts[0])           # a new capture works again
+    try:
+        assert np.array_equal(g2.run(cts[3]).export(), ctx.rank(cts[3]).export())
+    finally:
+        g2.free()
