@@ -370,7 +370,8 @@ def measured_peaks():
 
 
 KERNEL_SOURCE = {   # kernel -> [(file, first line of its source or None, text after it or None)]
-    "ks_inner": [("kernels.cu", "// Up to CH stacked ciphertexts per thread", "// out[c][t] = base_c[t]")],
+    "ks_inner": [("kernels.cu", "// Up to CH stacked ciphertexts per thread",
+                  "// ===========================================================================\n// Rescale: lift")],
     "ntt_fwd": [("ntt.cu", None, None), ("ntt_core.cuh", None, None)],
 }
 
@@ -381,7 +382,7 @@ def kernel_source_sha256(kernel: str):
         src = open(os.path.join(ROOT, "paper_2412_15126_gb300", "csrc", f)).read()
         if a is not None:
             i = src.index(a)
-            src = src[i:src.index(b, i)]
+            src = src[i:src.index(b, i)].rstrip()
         h.update(src.encode())
     return h.hexdigest()
 
@@ -403,7 +404,9 @@ def ntt_roofline(prof, clk):
     ipb = None
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            ipb = json.load(f)["ntt_fwd"]["thread_instructions_per_butterfly"]
+            rec = json.load(f)["ntt_fwd"]
+        if rec["source_sha256"] == kernel_source_sha256("ntt_fwd"):   # counts of this very kernel
+            ipb = rec["thread_instructions_per_butterfly"]
     except Exception:
         pass
     peak = None

@@ -351,34 +351,6 @@ void launch_ks_inner(const KernelEnv& env, const u64* ext, size_t ext_stride, co
     }
 }
 
-// out[c][t] = base_c[t] (automorphism applied to base0 when galois0 != 0) + (u[c][t] - w[c][t]) * P^-1;
-// base_c points at limb 0 of one polynomial, or is null.
-// z = 2b + p over B stacked ciphertexts; base_p of ciphertext b at base_p + b * bstride
-__global__ void k_ks_combine(u64* out, size_t ps, const u64* base0, u64 galois0, const u64* base1, size_t bstride,
-                             const u64* __restrict__ u, const u64* __restrict__ w, int level, int alpha, ConvTables cv,
-                             int logn, const PrimeConst* __restrict__ pc) {
-    const int n = 1 << logn;
-    const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y, c = blockIdx.z;
-    const int b = c >> 1, p = c & 1;
-    const u64 q = pc[t].q;
-    const int ul = level + 1 + alpha;
-    u64 v = sub_mod(u[(size_t)c * ul * n + (size_t)t * n + k], w[(size_t)c * (level + 1) * n + (size_t)t * n + k], q);
-    v = shoup_mul(v, cv.pinv[2 * t], cv.pinv[2 * t + 1], q);
-    const u64* base = p == 0 ? base0 : base1;
-    if (base) {
-        const int src = (p == 0 && galois0) ? galois_src(k, galois0, logn) : k;
-        v = add_mod(v, base[(size_t)b * bstride + (size_t)t * n + src], q);
-    }
-    out[(size_t)c * ps + (size_t)t * n + k] = v;
-}
-
-void launch_ks_combine(const KernelEnv& env, u64* out, size_t ps, const u64* base0, u64 galois0, const u64* base1, size_t bstride,
-                       const u64* u, const u64* w, int level, cudaStream_t st, int B) {
-    ProfScope pf(env, KK_KS_COMBINE, st, 1, 7.0 * B * (level + 1) * 8.0 * env.n, 2.0 * B * (level + 1) * env.n);
-    dim3 g(env.n / TPB, level + 1, 2 * B);
-    k_ks_combine<<<g, TPB, 0, st>>>(out, ps, base0, galois0, base1, bstride, u, w, level, env.alpha, env.conv, env.logn, env.pc);
-}
-
 // ===========================================================================
 // Rescale: lift the (coefficient-domain) last limb, centred, into the lower limbs.
 // last: 2 polys at stride ls; v: [2][level][n].  grid (n/TPB, level, 2)

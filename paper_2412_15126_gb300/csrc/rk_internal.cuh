@@ -48,6 +48,10 @@ struct LimbSet {
     // digits of a ModUp already hold their own limbs in the evaluation domain)
     int skip_ds = 0;
     int skip_beta = 1;
+    // optional: an inverse NTT's first pass reads polynomial z from src + z * src_stride
+    // (same limb layout) instead of transforming base in place
+    const u64* src = nullptr;
+    size_t src_stride = 0;
 };
 
 __host__ __device__ __forceinline__ int limb_prime(const LimbSet& s, int t) {
