@@ -370,8 +370,7 @@ def measured_peaks():
 
 
 KERNEL_SOURCE = {   # kernel -> [(file, first line of its source or None, text after it or None)]
-    "ks_inner": [("kernels.cu", "// Up to CH stacked ciphertexts per thread",
-                  "// ===========================================================================\n// Rescale: lift")],
+    "ks_inner": [("kernels.cu", "// Up to CH stacked ciphertexts per thread", "// out[c][t] = base_c[t]")],
     "ntt_fwd": [("ntt.cu", None, None), ("ntt_core.cuh", None, None)],
 }
 

@@ -19,6 +19,8 @@ LIB = os.path.join(OUT_DIR, "librankfhe.so")
 SOURCES = ["kernels.cu", "context.cu", "evaluator.cu", "encoder.cpp", "circuits.cpp", "capi.cpp", "noalloc.cu", "ntt.cu", "graph.cu", "ks_fused.cu", "server.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off", "-I", INCLUDE]
+# extra compile-time switches for tuning builds, e.g. RK_EXTRA_NVCC_FLAGS="-DRK_PDL=0"
+FLAGS += os.environ.get("RK_EXTRA_NVCC_FLAGS", "").split()
 
 
 def _nvcc() -> str:

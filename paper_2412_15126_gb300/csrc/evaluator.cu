@@ -232,14 +232,8 @@ void ev_rescale_inplace(rk_ctx* c, rk_ct* a) {
     const int polys = 2 * a->B;
     launch_ntt_inverse(c->env, ls_one(a->data + (size_t)l * n, ps, polys, l), c->stream);
     launch_rescale_lift(c->env, a->data + (size_t)l * n, ps, S.v, l, c->stream, polys);
-    // the lifted limbs' forward NTT ends in (ct - v) q_l^-1, written in place
-    NttEpilogue epi;
-    epi.mode = RK_EPI_RESCALE;
-    epi.dst = a->data;
-    epi.dst_ps = ps;
-    epi.tab = c->env.conv.rescale + (size_t)l * 3 * (c->L + 1);
-    epi.L1 = c->L + 1;
-    launch_ntt_forward(c->env, ls_q(S.v, (size_t)l * n, polys, l), c->stream, &epi);
+    launch_ntt_forward(c->env, ls_q(S.v, (size_t)l * n, polys, l), c->stream);
+    launch_rescale_combine(c->env, a->data, ps, S.v, l, c->stream, polys);
     a->level = l - 1;
     c->n_rescale++;
 }
@@ -438,19 +432,8 @@ static void ks_moddown(rk_ctx* c, int l, const u64* base0, u64 galois0, const u6
         launch_moddown_row(c->env, out, out_ps, base0, galois0, base1, bstride, S.u, S.w, l, c->stream, B);
     } else {
         launch_moddown_conv(c->env, S.u, S.w, l, c->stream, 2 * B);
-        // the conversion's forward NTT ends in out = base + (u - w) P^-1
-        NttEpilogue epi;
-        epi.mode = RK_EPI_KS;
-        epi.dst = out;
-        epi.dst_ps = out_ps;
-        epi.tab = c->env.conv.pinv;
-        epi.u = S.u;
-        epi.u_ps = (size_t)QP * n;
-        epi.base0 = base0;
-        epi.base1 = base1;
-        epi.bstride = bstride;
-        epi.galois0 = galois0;
-        launch_ntt_forward(c->env, ls_q(S.w, (size_t)(l + 1) * n, 2 * B, l + 1), c->stream, &epi);
+        launch_ntt_forward(c->env, ls_q(S.w, (size_t)(l + 1) * n, 2 * B, l + 1), c->stream);
+        launch_ks_combine(c->env, out, out_ps, base0, galois0, base1, bstride, S.u, S.w, l, c->stream, B);
     }
     c->n_ks += (uint64_t)B;
 }

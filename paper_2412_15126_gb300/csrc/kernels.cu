@@ -18,6 +18,7 @@ const char* const kKernelKindNames[KK_COUNT] = {"ntt_fwd", "ntt_inv", "modup", "
 // grid: (n / TPB, limbs, polys)
 // ===========================================================================
 __global__ void k_addsub(u64* out, const u64* a, const u64* b, int n, size_t ps, const PrimeConst* __restrict__ pc, int mode) {
+    RK_KERNEL_PROLOGUE();
     const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y, c = blockIdx.z;
     const u64 q = pc[t].q;
     const size_t off = c * ps + (size_t)t * n + k;
@@ -33,11 +34,12 @@ void launch_addsub(const KernelEnv& env, u64* out, const u64* a, const u64* b, i
                    int polys) {
     ProfScope pf(env, KK_POINTWISE, st, 1, 3.0 * polys * limbs * 8.0 * env.n, 0.0);
     dim3 g(env.n / TPB, limbs, polys);
-    k_addsub<<<g, TPB, 0, st>>>(out, a, b, env.n, ps, env.pc, mode);
+    rk_launch(k_addsub, g, TPB, 0, st, out, a, b, env.n, ps, env.pc, mode);
 }
 
 // out0 = a0 + K_t, out1 = a1
 __global__ void k_add_const(u64* out, const u64* a, ScalarArg K, int n, size_t ps, const PrimeConst* __restrict__ pc) {
+    RK_KERNEL_PROLOGUE();
     const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y, c = blockIdx.z;
     const size_t off = c * ps + (size_t)t * n + k;
     u64 x = a[off];
@@ -49,11 +51,12 @@ void launch_add_const(const KernelEnv& env, u64* out, const u64* a, const Scalar
                       int polys) {
     ProfScope pf(env, KK_POINTWISE, st, 1, 2.0 * polys * limbs * 8.0 * env.n, 0.0);
     dim3 g(env.n / TPB, limbs, polys);
-    k_add_const<<<g, TPB, 0, st>>>(out, a, K, env.n, ps, env.pc);
+    rk_launch(k_add_const, g, TPB, 0, st, out, a, K, env.n, ps, env.pc);
 }
 
 // out = a * K_t (Shoup)
 __global__ void k_mul_scalar(u64* out, const u64* a, ScalarArg K, int n, size_t ps, const PrimeConst* __restrict__ pc) {
+    RK_KERNEL_PROLOGUE();
     const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y, c = blockIdx.z;
     const size_t off = c * ps + (size_t)t * n + k;
     out[off] = shoup_mul(a[off], K.w[t], K.wsh[t], pc[t].q);
@@ -63,11 +66,12 @@ void launch_mul_scalar(const KernelEnv& env, u64* out, const u64* a, const Scala
                        int polys) {
     ProfScope pf(env, KK_POINTWISE, st, 1, 2.0 * polys * limbs * 8.0 * env.n, 1.0 * polys * limbs * env.n);
     dim3 g(env.n / TPB, limbs, polys);
-    k_mul_scalar<<<g, TPB, 0, st>>>(out, a, K, env.n, ps, env.pc);
+    rk_launch(k_mul_scalar, g, TPB, 0, st, out, a, K, env.n, ps, env.pc);
 }
 
 // out = a * pt, pt stored times R ([limbs][n])
 __global__ void k_mul_plain(u64* out, const u64* a, const u64* pt, int n, size_t ps, const PrimeConst* __restrict__ pc) {
+    RK_KERNEL_PROLOGUE();
     const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y, c = blockIdx.z;
     const size_t off = c * ps + (size_t)t * n + k;
     const PrimeConst P = pc[t];
@@ -78,11 +82,12 @@ void launch_mul_plain(const KernelEnv& env, u64* out, const u64* a, const u64* p
                       int polys) {
     ProfScope pf(env, KK_POINTWISE, st, 1, (2.0 * polys + 1.0) * limbs * 8.0 * env.n, 1.0 * polys * limbs * env.n);
     dim3 g(env.n / TPB, limbs, polys);
-    k_mul_plain<<<g, TPB, 0, st>>>(out, a, pt, env.n, ps, env.pc);
+    rk_launch(k_mul_plain, g, TPB, 0, st, out, a, pt, env.n, ps, env.pc);
 }
 
 // out (+)= sum_i x_i * K_i, exact modular arithmetic, one reduction per output
 __global__ void k_lincomb(u64* out, LincombArg a, int terms, int accumulate, int n, size_t ps, const PrimeConst* __restrict__ pc) {
+    RK_KERNEL_PROLOGUE();
     const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y, c = blockIdx.z;
     const PrimeConst P = pc[t];
     const size_t off = c * ps + (size_t)t * n + k;
@@ -97,12 +102,13 @@ void launch_lincomb(const KernelEnv& env, u64* out, const LincombArg& a, int ter
                     cudaStream_t st, int polys) {
     ProfScope pf(env, KK_POINTWISE, st, 1, (terms + 1.0) * polys * limbs * 8.0 * env.n, 1.0 * terms * polys * limbs * env.n);
     dim3 g(env.n / TPB, limbs, polys);
-    k_lincomb<<<g, TPB, 0, st>>>(out, a, terms, accumulate ? 1 : 0, env.n, ps, env.pc);
+    rk_launch(k_lincomb, g, TPB, 0, st, out, a, terms, accumulate ? 1 : 0, env.n, ps, env.pc);
 }
 
 // d = [d0 | d1 | d2] each [limbs][n]: d0 = x0 y0, d1 = x0 y1 + x1 y0, d2 = x1 y1
 // one ciphertext pair per blockIdx.z (stacked layout [B][2][L+1][n]); d is [B][3][limbs][n]
 __global__ void k_tensor(u64* d, const u64* x, const u64* y, int limbs, int n, size_t ps, const PrimeConst* __restrict__ pc) {
+    RK_KERNEL_PROLOGUE();
     const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y, b = blockIdx.z;
     const PrimeConst P = pc[t];
     const size_t pl = (size_t)limbs * n;
@@ -125,7 +131,7 @@ __global__ void k_tensor(u64* d, const u64* x, const u64* y, int limbs, int n, s
 void launch_tensor(const KernelEnv& env, u64* d, const u64* x, const u64* y, int limbs, size_t ps, cudaStream_t st, int B) {
     ProfScope pf(env, KK_TENSOR, st, 1, 7.0 * B * limbs * 8.0 * env.n, 4.0 * B * limbs * env.n);
     dim3 g(env.n / TPB, limbs, B);
-    k_tensor<<<g, TPB, 0, st>>>(d, x, y, limbs, env.n, ps, env.pc);
+    rk_launch(k_tensor, g, TPB, 0, st, d, x, y, limbs, env.n, ps, env.pc);
 }
 
 // ===========================================================================
@@ -141,6 +147,7 @@ template <int DS>
 __global__ void __launch_bounds__(TPB) k_modup(const u64* __restrict__ x, const u64* __restrict__ x_eval, u64* __restrict__ ext,
                                                size_t ext_stride, int level, int L, int alpha, ConvTables cv, int n,
                                                const PrimeConst* __restrict__ pc) {
+    RK_KERNEL_PROLOGUE();
     __shared__ u64 s_c[DS * RK_MAX_PRIMES];             // (D/q_i) R mod prime(t), [i][t]
     __shared__ u64 s_q[RK_MAX_PRIMES], s_qinv[RK_MAX_PRIMES];
     const int j = blockIdx.y;
@@ -206,7 +213,7 @@ void launch_modup(const KernelEnv& env, const u64* x, const u64* x_eval, size_t 
         switch (env.conv.dsize) {
 #define RK_MODUP_CASE(D)                                                                                                 \
     case D:                                                                                                              \
-        k_modup<D><<<g, TPB, 0, st>>>(xb, eb, ob, ext_stride, level, env.L, env.alpha, env.conv, env.n, env.pc);        \
+        rk_launch(k_modup<D>, g, TPB, 0, st, xb, eb, ob, ext_stride, level, env.L, env.alpha, env.conv, env.n, env.pc);        \
         break;
             RK_MODUP_CASE(1) RK_MODUP_CASE(2) RK_MODUP_CASE(3) RK_MODUP_CASE(4)
             RK_MODUP_CASE(5) RK_MODUP_CASE(6) RK_MODUP_CASE(7) RK_MODUP_CASE(8)
@@ -221,6 +228,7 @@ void launch_modup(const KernelEnv& env, const u64* x, const u64* x_eval, size_t 
 template <int A>
 __global__ void __launch_bounds__(TPB) k_moddown_conv(const u64* __restrict__ u, u64* __restrict__ w, int level, int L,
                                                       ConvTables cv, int n, const PrimeConst* __restrict__ pc) {
+    RK_KERNEL_PROLOGUE();
     __shared__ u64 s_c[A * RK_MAX_PRIMES];      // (P/p_k) R mod q_i, [k][i]
     __shared__ u64 s_q[RK_MAX_PRIMES], s_qinv[RK_MAX_PRIMES], s_pm[RK_MAX_PRIMES];
     const int c = blockIdx.y;
@@ -278,7 +286,7 @@ void launch_moddown_conv(const KernelEnv& env, const u64* u, u64* w, int level, 
     switch (env.alpha) {
 #define RK_MD_CASE(A)                                                                               \
     case A:                                                                                         \
-        k_moddown_conv<A><<<g, TPB, 0, st>>>(u, w, level, env.L, env.conv, env.n, env.pc);          \
+        rk_launch(k_moddown_conv<A>, g, TPB, 0, st, u, w, level, env.L, env.conv, env.n, env.pc);          \
         break;
         RK_MD_CASE(1) RK_MD_CASE(2) RK_MD_CASE(3) RK_MD_CASE(4) RK_MD_CASE(5) RK_MD_CASE(6) RK_MD_CASE(7) RK_MD_CASE(8)
 #undef RK_MD_CASE
@@ -297,6 +305,7 @@ template <int CH>
 __global__ void __launch_bounds__(TPB) k_ks_inner(const u64* __restrict__ ext, size_t ext_stride, const u64* __restrict__ key,
                                                   u64* __restrict__ u, int level, int L, int alpha, int beta, u64 galois,
                                                   int logn, int B, const PrimeConst* __restrict__ pc) {
+    RK_KERNEL_PROLOGUE();
     const int n = 1 << logn;
     const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y;
     const int b0 = blockIdx.z * CH;
@@ -344,11 +353,40 @@ void launch_ks_inner(const KernelEnv& env, const u64* ext, size_t ext_stride, co
                  2.0 * B * beta * QP * env.n);
     dim3 g(env.n / TPB, level + 1 + env.alpha, chunks);
     switch (ch) {
-        case 1: k_ks_inner<1><<<g, TPB, 0, st>>>(ext, ext_stride, key, u, level, env.L, env.alpha, beta, galois, env.logn, B, env.pc); break;
-        case 2: k_ks_inner<2><<<g, TPB, 0, st>>>(ext, ext_stride, key, u, level, env.L, env.alpha, beta, galois, env.logn, B, env.pc); break;
-        case 4: k_ks_inner<4><<<g, TPB, 0, st>>>(ext, ext_stride, key, u, level, env.L, env.alpha, beta, galois, env.logn, B, env.pc); break;
-        default: k_ks_inner<8><<<g, TPB, 0, st>>>(ext, ext_stride, key, u, level, env.L, env.alpha, beta, galois, env.logn, B, env.pc); break;
+        case 1: rk_launch(k_ks_inner<1>, g, TPB, 0, st, ext, ext_stride, key, u, level, env.L, env.alpha, beta, galois, env.logn, B, env.pc); break;
+        case 2: rk_launch(k_ks_inner<2>, g, TPB, 0, st, ext, ext_stride, key, u, level, env.L, env.alpha, beta, galois, env.logn, B, env.pc); break;
+        case 4: rk_launch(k_ks_inner<4>, g, TPB, 0, st, ext, ext_stride, key, u, level, env.L, env.alpha, beta, galois, env.logn, B, env.pc); break;
+        default: rk_launch(k_ks_inner<8>, g, TPB, 0, st, ext, ext_stride, key, u, level, env.L, env.alpha, beta, galois, env.logn, B, env.pc); break;
     }
+}
+
+// out[c][t] = base_c[t] (automorphism applied to base0 when galois0 != 0) + (u[c][t] - w[c][t]) * P^-1;
+// base_c points at limb 0 of one polynomial, or is null.
+// z = 2b + p over B stacked ciphertexts; base_p of ciphertext b at base_p + b * bstride
+__global__ void k_ks_combine(u64* out, size_t ps, const u64* base0, u64 galois0, const u64* base1, size_t bstride,
+                             const u64* __restrict__ u, const u64* __restrict__ w, int level, int alpha, ConvTables cv,
+                             int logn, const PrimeConst* __restrict__ pc) {
+    RK_KERNEL_PROLOGUE();
+    const int n = 1 << logn;
+    const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y, c = blockIdx.z;
+    const int b = c >> 1, p = c & 1;
+    const u64 q = pc[t].q;
+    const int ul = level + 1 + alpha;
+    u64 v = sub_mod(u[(size_t)c * ul * n + (size_t)t * n + k], w[(size_t)c * (level + 1) * n + (size_t)t * n + k], q);
+    v = shoup_mul(v, cv.pinv[2 * t], cv.pinv[2 * t + 1], q);
+    const u64* base = p == 0 ? base0 : base1;
+    if (base) {
+        const int src = (p == 0 && galois0) ? galois_src(k, galois0, logn) : k;
+        v = add_mod(v, base[(size_t)b * bstride + (size_t)t * n + src], q);
+    }
+    out[(size_t)c * ps + (size_t)t * n + k] = v;
+}
+
+void launch_ks_combine(const KernelEnv& env, u64* out, size_t ps, const u64* base0, u64 galois0, const u64* base1, size_t bstride,
+                       const u64* u, const u64* w, int level, cudaStream_t st, int B) {
+    ProfScope pf(env, KK_KS_COMBINE, st, 1, 7.0 * B * (level + 1) * 8.0 * env.n, 2.0 * B * (level + 1) * env.n);
+    dim3 g(env.n / TPB, level + 1, 2 * B);
+    rk_launch(k_ks_combine, g, TPB, 0, st, out, ps, base0, galois0, base1, bstride, u, w, level, env.alpha, env.conv, env.logn, env.pc);
 }
 
 // ===========================================================================
@@ -357,6 +395,7 @@ void launch_ks_inner(const KernelEnv& env, const u64* ext, size_t ext_stride, co
 // ===========================================================================
 __global__ void k_rescale_lift(const u64* last, size_t ls, u64* v, int level, int L, ConvTables cv, int n,
                                const PrimeConst* __restrict__ pc) {
+    RK_KERNEL_PROLOGUE();
     const int k = blockIdx.x * TPB + threadIdx.x, i = blockIdx.y, c = blockIdx.z;
     const u64 ql = pc[level].q;
     const u64 x = last[(size_t)c * ls + k];
@@ -369,12 +408,13 @@ __global__ void k_rescale_lift(const u64* last, size_t ls, u64* v, int level, in
 void launch_rescale_lift(const KernelEnv& env, const u64* last, size_t ls, u64* v, int level, cudaStream_t st, int polys) {
     ProfScope pf(env, KK_RESCALE, st, 1, polys * (1.0 + level) * 8.0 * env.n, 1.0 * polys * level * env.n);
     dim3 g(env.n / TPB, level, polys);
-    k_rescale_lift<<<g, TPB, 0, st>>>(last, ls, v, level, env.L, env.conv, env.n, env.pc);
+    rk_launch(k_rescale_lift, g, TPB, 0, st, last, ls, v, level, env.L, env.conv, env.n, env.pc);
 }
 
 // ct[c][i] = (ct[c][i] - v[c][i]) * q_l^-1, i < level (in place)
 __global__ void k_rescale_combine(u64* ct, size_t ps, const u64* v, int level, int L, ConvTables cv, int n,
                                   const PrimeConst* __restrict__ pc) {
+    RK_KERNEL_PROLOGUE();
     const int k = blockIdx.x * TPB + threadIdx.x, i = blockIdx.y, c = blockIdx.z;
     const u64 q = pc[i].q;
     const u64* tab = cv.rescale + (size_t)level * 3 * (L + 1);
@@ -386,7 +426,7 @@ __global__ void k_rescale_combine(u64* ct, size_t ps, const u64* v, int level, i
 void launch_rescale_combine(const KernelEnv& env, u64* ct, size_t ps, const u64* v, int level, cudaStream_t st, int polys) {
     ProfScope pf(env, KK_RESCALE, st, 1, 3.0 * polys * level * 8.0 * env.n, 1.0 * polys * level * env.n);
     dim3 g(env.n / TPB, level, polys);
-    k_rescale_combine<<<g, TPB, 0, st>>>(ct, ps, v, level, env.L, env.conv, env.n, env.pc);
+    rk_launch(k_rescale_combine, g, TPB, 0, st, ct, ps, v, level, env.L, env.conv, env.n, env.pc);
 }
 
 // ===========================================================================
@@ -394,6 +434,7 @@ void launch_rescale_combine(const KernelEnv& env, u64* ct, size_t ps, const u64*
 // ===========================================================================
 // dst[t][k] = src[k] mod prime(t) for `limbs` limbs of the LimbSet's first poly map.
 __global__ void k_reduce_signed(const int64_t* src, u64* dst, LimbSet s, int n, const PrimeConst* __restrict__ pc) {
+    RK_KERNEL_PROLOGUE();
     const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y, p = blockIdx.z;
     const PrimeConst P = pc[limb_prime(s, t)];
     const int64_t x = src[(size_t)p * n + k];
@@ -406,7 +447,7 @@ __global__ void k_reduce_signed(const int64_t* src, u64* dst, LimbSet s, int n, 
 void launch_reduce_signed(const KernelEnv& env, const int64_t* src, const LimbSet& s, cudaStream_t st) {
     ProfScope pf(env, KK_CLIENT, st, 1, 0.0, 0.0);
     dim3 g(env.n / TPB, s.n_limbs, s.n_polys);
-    k_reduce_signed<<<g, TPB, 0, st>>>(src, s.base, s, env.n, env.pc);
+    rk_launch(k_reduce_signed, g, TPB, 0, st, src, s.base, s, env.n, env.pc);
 }
 
 __device__ __forceinline__ u64 splitmix64(u64 x) {
@@ -418,6 +459,7 @@ __device__ __forceinline__ u64 splitmix64(u64 x) {
 
 // Uniform residues: word k of limb t of poly p from SplitMix64 of a per-word counter.
 __global__ void k_uniform(LimbSet s, u64 seed, u64 stream_id, int n, const PrimeConst* __restrict__ pc) {
+    RK_KERNEL_PROLOGUE();
     const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y, p = blockIdx.z;
     const u64 q = pc[limb_prime(s, t)].q;
     const u64 ctr = ((stream_id * 64 + (u64)p) * 128 + (u64)t) * (u64)n + (u64)k;
@@ -428,7 +470,7 @@ __global__ void k_uniform(LimbSet s, u64 seed, u64 stream_id, int n, const Prime
 void launch_uniform(const KernelEnv& env, const LimbSet& s, u64 seed, u64 stream_id, cudaStream_t st) {
     ProfScope pf(env, KK_CLIENT, st, 1, 0.0, 0.0);
     dim3 g(env.n / TPB, s.n_limbs, s.n_polys);
-    k_uniform<<<g, TPB, 0, st>>>(s, seed, stream_id, env.n, env.pc);
+    rk_launch(k_uniform, g, TPB, 0, st, s, seed, stream_id, env.n, env.pc);
 }
 
 // Switching-key digit in Montgomery form over all primes (eval domain):
@@ -436,6 +478,7 @@ void launch_uniform(const KernelEnv& env, const LimbSet& s, u64 seed, u64 stream
 // a, e, s' normal form; s_R = s R.  grid (n/TPB, n_primes)
 __global__ void k_key_digit(u64* kb, u64* ka, const u64* a, const u64* e, const u64* s_R, const u64* sp, const u64* gad,
                             int n, const PrimeConst* __restrict__ pc) {
+    RK_KERNEL_PROLOGUE();
     const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y;
     const PrimeConst P = pc[t];
     const size_t off = (size_t)t * n + k;
@@ -450,11 +493,12 @@ void launch_key_digit(const KernelEnv& env, u64* kb, u64* ka, const u64* a, cons
                       const u64* gad_dev, int n_primes, cudaStream_t st) {
     ProfScope pf(env, KK_CLIENT, st, 1, 0.0, 0.0);
     dim3 g(env.n / TPB, n_primes);
-    k_key_digit<<<g, TPB, 0, st>>>(kb, ka, a, e, s_R, sp, gad_dev, env.n, env.pc);
+    rk_launch(k_key_digit, g, TPB, 0, st, kb, ka, a, e, s_R, sp, gad_dev, env.n, env.pc);
 }
 
 // x <- x R (to Montgomery form), over `limbs` limbs of `polys` polys using LimbSet prime map
 __global__ void k_to_mont(LimbSet s, int n, const PrimeConst* __restrict__ pc) {
+    RK_KERNEL_PROLOGUE();
     const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y, p = blockIdx.z;
     const PrimeConst P = pc[limb_prime(s, t)];
     u64* x = s.base + (size_t)p * s.poly_stride + (size_t)t * n + k;
@@ -464,11 +508,12 @@ __global__ void k_to_mont(LimbSet s, int n, const PrimeConst* __restrict__ pc) {
 void launch_to_mont(const KernelEnv& env, const LimbSet& s, cudaStream_t st) {
     ProfScope pf(env, KK_CLIENT, st, 1, 0.0, 0.0);
     dim3 g(env.n / TPB, s.n_limbs, s.n_polys);
-    k_to_mont<<<g, TPB, 0, st>>>(s, env.n, env.pc);
+    rk_launch(k_to_mont, g, TPB, 0, st, s, env.n, env.pc);
 }
 
 // out[t][k] = x[t][src(k)] (automorphism in the eval domain) over `limbs` contiguous limbs
 __global__ void k_automorph(u64* out, const u64* x, u64 g, int logn) {
+    RK_KERNEL_PROLOGUE();
     const int n = 1 << logn;
     const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y;
     out[(size_t)t * n + k] = x[(size_t)t * n + galois_src(k, g, logn)];
@@ -477,11 +522,12 @@ __global__ void k_automorph(u64* out, const u64* x, u64 g, int logn) {
 void launch_automorph(const KernelEnv& env, u64* out, const u64* x, u64 g, int limbs, cudaStream_t st) {
     ProfScope pf(env, KK_CLIENT, st, 1, 0.0, 0.0);
     dim3 g2(env.n / TPB, limbs);
-    k_automorph<<<g2, TPB, 0, st>>>(out, x, g, env.logn);
+    rk_launch(k_automorph, g2, TPB, 0, st, out, x, g, env.logn);
 }
 
 // m[t] = c0[t] + c1[t] s[t] (s times R), t <= level; m is [limbs][n]
 __global__ void k_decrypt(u64* m, const u64* c0, const u64* c1, const u64* s_R, int n, const PrimeConst* __restrict__ pc) {
+    RK_KERNEL_PROLOGUE();
     const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y;
     const PrimeConst P = pc[t];
     const size_t off = (size_t)t * n + k;
@@ -491,13 +537,14 @@ __global__ void k_decrypt(u64* m, const u64* c0, const u64* c1, const u64* s_R, 
 void launch_decrypt(const KernelEnv& env, u64* m, const u64* c0, const u64* c1, const u64* s_R, int limbs, cudaStream_t st) {
     ProfScope pf(env, KK_CLIENT, st, 1, 0.0, 0.0);
     dim3 g(env.n / TPB, limbs);
-    k_decrypt<<<g, TPB, 0, st>>>(m, c0, c1, s_R, env.n, env.pc);
+    rk_launch(k_decrypt, g, TPB, 0, st, m, c0, c1, s_R, env.n, env.pc);
 }
 
 // Public-key encryption: c0 = v pk0 + e0 + m, c1 = v pk1 + e1 (pk times R).
 // r = [v | e0 | e1 | m] each [limbs][n] reduced and transformed.
 __global__ void k_encrypt(u64* ct, size_t ps, const u64* r, const u64* pk, size_t pk_ps, int limbs, int n,
                           const PrimeConst* __restrict__ pc) {
+    RK_KERNEL_PROLOGUE();
     const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y;
     const PrimeConst P = pc[t];
     const size_t off = (size_t)t * n + k, pl = (size_t)limbs * n;
@@ -509,11 +556,12 @@ __global__ void k_encrypt(u64* ct, size_t ps, const u64* r, const u64* pk, size_
 void launch_encrypt(const KernelEnv& env, u64* ct, size_t ps, const u64* r, const u64* pk, size_t pk_ps, int limbs, cudaStream_t st) {
     ProfScope pf(env, KK_CLIENT, st, 1, 0.0, 0.0);
     dim3 g(env.n / TPB, limbs);
-    k_encrypt<<<g, TPB, 0, st>>>(ct, ps, r, pk, pk_ps, limbs, env.n, env.pc);
+    rk_launch(k_encrypt, g, TPB, 0, st, ct, ps, r, pk, pk_ps, limbs, env.n, env.pc);
 }
 
 // pk0 = -a s + e (s times R), normal form; then both stored times R.  grid (n/TPB, limbs)
 __global__ void k_pk(u64* pk, size_t ps, const u64* a, const u64* e, const u64* s_R, int n, const PrimeConst* __restrict__ pc) {
+    RK_KERNEL_PROLOGUE();
     const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y;
     const PrimeConst P = pc[t];
     const size_t off = (size_t)t * n + k;
@@ -525,11 +573,12 @@ __global__ void k_pk(u64* pk, size_t ps, const u64* a, const u64* e, const u64* 
 void launch_pk(const KernelEnv& env, u64* pk, size_t ps, const u64* a, const u64* e, const u64* s_R, int limbs, cudaStream_t st) {
     ProfScope pf(env, KK_CLIENT, st, 1, 0.0, 0.0);
     dim3 g(env.n / TPB, limbs);
-    k_pk<<<g, TPB, 0, st>>>(pk, ps, a, e, s_R, env.n, env.pc);
+    rk_launch(k_pk, g, TPB, 0, st, pk, ps, a, e, s_R, env.n, env.pc);
 }
 
 // s' = s * s (eval domain), inputs times R: out = s_R s_R R^-1 = s^2 R -> normal form via a second redc
 __global__ void k_square_secret(u64* out, const u64* s_R, int n, const PrimeConst* __restrict__ pc) {
+    RK_KERNEL_PROLOGUE();
     const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y;
     const PrimeConst P = pc[t];
     const size_t off = (size_t)t * n + k;
@@ -541,11 +590,12 @@ __global__ void k_square_secret(u64* out, const u64* s_R, int n, const PrimeCons
 void launch_square_secret(const KernelEnv& env, u64* out, const u64* s_R, int limbs, cudaStream_t st) {
     ProfScope pf(env, KK_CLIENT, st, 1, 0.0, 0.0);
     dim3 g(env.n / TPB, limbs);
-    k_square_secret<<<g, TPB, 0, st>>>(out, s_R, env.n, env.pc);
+    rk_launch(k_square_secret, g, TPB, 0, st, out, s_R, env.n, env.pc);
 }
 
 // from Montgomery form to normal form
 __global__ void k_from_mont(u64* out, const u64* x, int n, const PrimeConst* __restrict__ pc) {
+    RK_KERNEL_PROLOGUE();
     const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y;
     const PrimeConst P = pc[t];
     const size_t off = (size_t)t * n + k;
@@ -555,5 +605,5 @@ __global__ void k_from_mont(u64* out, const u64* x, int n, const PrimeConst* __r
 void launch_from_mont(const KernelEnv& env, u64* out, const u64* x, int limbs, cudaStream_t st) {
     ProfScope pf(env, KK_CLIENT, st, 1, 0.0, 0.0);
     dim3 g(env.n / TPB, limbs);
-    k_from_mont<<<g, TPB, 0, st>>>(out, x, env.n, env.pc);
+    rk_launch(k_from_mont, g, TPB, 0, st, out, x, env.n, env.pc);
 }

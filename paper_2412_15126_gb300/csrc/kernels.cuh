@@ -3,6 +3,40 @@
 #pragma once
 #include "rk_internal.cuh"
 
+// Programmatic dependent launch: every kernel is launched so that it may begin while
+// its predecessor on the stream finishes.  Each kernel lets its own successor begin
+// launching at once and then waits for its predecessor's completion (and memory)
+// before touching any global memory, so stream order is kept for every access;
+// only the launch latency overlaps.  RK_PDL=0 builds plain launches.
+#ifndef RK_PDL
+#define RK_PDL 1
+#endif
+#if RK_PDL
+#define RK_KERNEL_PROLOGUE() asm volatile("griddepcontrol.launch_dependents;\n\tgriddepcontrol.wait;" ::: "memory")
+#else
+#define RK_KERNEL_PROLOGUE() ((void)0)
+#endif
+
+template <typename... KArgs, typename... Args>
+inline void rk_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args&&... args) {
+#if RK_PDL
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+    if (e != cudaSuccess) throw rk_error(RK_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+#else
+    kernel<<<grid, block, smem, st>>>(std::forward<Args>(args)...);
+#endif
+}
+
 
 // Counts every launch; when `kind` is among the profiled kinds, brackets the launch(es)
 // with CUDA events on the launching stream and accumulates the algorithmic bytes/products.
@@ -41,28 +75,8 @@ struct ProfScope {
     }
 };
 
-// Consumer fused into the end of a forward NTT (its row pass): instead of storing the
-// transformed value y of limb t, polynomial z,
-//   RK_EPI_RESCALE: dst_z[t] = (dst_z[t] - y) q_l^-1      (tab: the level's rescale block)
-//   RK_EPI_KS:      dst_z[t] = base_p[b][t][src] + (u_z[t] - y) P^-1,  z = 2b + p
-// (tab: P^-1 mod q_t and its Shoup companion in pairs; galois0 on base0 only).
-enum { RK_EPI_STORE = 0, RK_EPI_RESCALE = 1, RK_EPI_KS = 2 };
-struct NttEpilogue {
-    int mode = RK_EPI_STORE;
-    u64* dst = nullptr;
-    size_t dst_ps = 0;
-    const u64* tab = nullptr;
-    int L1 = 0;
-    const u64* u = nullptr;
-    size_t u_ps = 0;
-    const u64* base0 = nullptr;
-    const u64* base1 = nullptr;
-    size_t bstride = 0;
-    u64 galois0 = 0;
-};
-
 void ntt_init_attributes();
-void launch_ntt_forward(const KernelEnv& env, const LimbSet& s, cudaStream_t st, const NttEpilogue* epi = nullptr);
+void launch_ntt_forward(const KernelEnv& env, const LimbSet& s, cudaStream_t st);
 void launch_ntt_inverse(const KernelEnv& env, const LimbSet& s, cudaStream_t st);
 void launch_addsub(const KernelEnv& env, u64* out, const u64* a, const u64* b, int limbs, size_t ps, int mode, cudaStream_t st,
                    int polys = 2);
@@ -85,6 +99,8 @@ void launch_modup(const KernelEnv& env, const u64* x, const u64* x_eval, size_t 
 void launch_moddown_conv(const KernelEnv& env, const u64* u, u64* w, int level, cudaStream_t st, int polys = 2);
 void launch_ks_inner(const KernelEnv& env, const u64* ext, size_t ext_stride, const u64* key, u64* u, int level, int beta,
                      u64 galois, cudaStream_t st, int B = 1);
+void launch_ks_combine(const KernelEnv& env, u64* out, size_t ps, const u64* base0, u64 galois0, const u64* base1, size_t bstride,
+                       const u64* u, const u64* w, int level, cudaStream_t st, int B = 1);
 // fused key switching (ks_fused.cu)
 void ks_fused_init_attributes();
 void launch_modup_col(const KernelEnv& env, const u64* coef, u64* ext, size_t ext_stride, int level, int beta, int t0, int limbs,

@@ -35,6 +35,7 @@ __global__ void __launch_bounds__(256) k_modup_col(const u64* __restrict__ coef,
                                                    int level, int L, int alpha, int beta, int t0, ConvTables cv, int logn,
                                                    int loga, int units, const PrimeConst* __restrict__ pc,
                                                    const u64* __restrict__ tw) {
+    RK_KERNEL_PROLOGUE();
     using S = Shape<LOG>;
     constexpr int P = S::P, E = S::E;
     extern __shared__ u64 sm[];
@@ -100,6 +101,7 @@ __global__ void __launch_bounds__(2048 / Shape<LOG>::E, (LOG >= 7 ? 3 : 2)) k_ks
                                                 size_t eval_stride, const u64* __restrict__ key, u64* __restrict__ uo, int level,
                                                 int L, int alpha, int beta, int dsize, int t0, u64 galois, int logn, int units,
                                                 const PrimeConst* __restrict__ pc, const u64* __restrict__ tw) {
+    RK_KERNEL_PROLOGUE();
     using S = Shape<LOG>;
     constexpr int P = S::P, E = S::E, T = S::T;
     extern __shared__ u64 sm[];
@@ -181,6 +183,7 @@ template <int LOG>
 __global__ void __launch_bounds__(256) k_moddown_col(const u64* __restrict__ uin, u64* __restrict__ w, int level, int L,
                                                      int alpha, ConvTables cv, int logn, int loga, int units,
                                                      const PrimeConst* __restrict__ pc, const u64* __restrict__ tw) {
+    RK_KERNEL_PROLOGUE();
     using S = Shape<LOG>;
     constexpr int P = S::P, E = S::E;
     extern __shared__ u64 sm[];
@@ -247,6 +250,7 @@ __global__ void __launch_bounds__(256) k_moddown_row(u64* __restrict__ out, size
                                                      const u64* __restrict__ w, int level, int alpha, ConvTables cv, int logn,
                                                      int units, const PrimeConst* __restrict__ pc,
                                                      const u64* __restrict__ tw) {
+    RK_KERNEL_PROLOGUE();
     using S = Shape<LOG>;
     constexpr int P = S::P, E = S::E;
     extern __shared__ u64 sm[];
@@ -338,7 +342,7 @@ void launch_modup_col(const KernelEnv& env, const u64* coef, u64* ext, size_t ex
     const Geom g = geom_of(loga, 1 << logb);
     const dim3 grid(g.blocks, limbs, B * beta);
     const size_t smem = (size_t)(1 << loga) * g.units * 8;
-    RK_LOG_SWITCH(loga, (k_modup_col<LG><<<grid, g.threads, smem, st>>>(coef, ext, ext_stride, level, env.L, env.alpha, beta, t0,
+    RK_LOG_SWITCH(loga, (rk_launch(k_modup_col<LG>, grid, g.threads, smem, st, coef, ext, ext_stride, level, env.L, env.alpha, beta, t0,
                                                                         env.conv, logn, loga, g.units, env.pc, env.tw.psi)));
 }
 
@@ -357,7 +361,7 @@ void launch_ks_row(const KernelEnv& env, const u64* ext, size_t ext_stride, cons
     g.blocks = (1 << loga) / g.units;
     const dim3 grid(g.blocks, limbs, B);
     const size_t smem = (size_t)(1 << logb) * g.units * 26;
-    RK_LOG_SWITCH(logb, (k_ks_row<LG><<<grid, g.threads, smem, st>>>(ext, ext_stride, x_eval, eval_stride, key, u, level, env.L,
+    RK_LOG_SWITCH(logb, (rk_launch(k_ks_row<LG>, grid, g.threads, smem, st, ext, ext_stride, x_eval, eval_stride, key, u, level, env.L,
                                                                      env.alpha, beta, env.conv.dsize, t0, galois, logn, g.units,
                                                                      env.pc, env.tw.psi)));
 }
@@ -369,7 +373,7 @@ void launch_moddown_col(const KernelEnv& env, const u64* u, u64* w, int level, c
     const Geom g = geom_of(loga, 1 << logb);
     const dim3 grid(g.blocks, level + 1, polys);
     const size_t smem = (size_t)(1 << loga) * g.units * 8;
-    RK_LOG_SWITCH(loga, (k_moddown_col<LG><<<grid, g.threads, smem, st>>>(u, w, level, env.L, env.alpha, env.conv, logn, loga,
+    RK_LOG_SWITCH(loga, (rk_launch(k_moddown_col<LG>, grid, g.threads, smem, st, u, w, level, env.L, env.alpha, env.conv, logn, loga,
                                                                           g.units, env.pc, env.tw.psi)));
 }
 
@@ -380,6 +384,6 @@ void launch_moddown_row(const KernelEnv& env, u64* out, size_t ps, const u64* ba
     const Geom g = geom_of(logb, 1 << loga);
     const dim3 grid(g.blocks, level + 1, 2 * B);
     const size_t smem = (size_t)(1 << logb) * g.units * 8;
-    RK_LOG_SWITCH(logb, (k_moddown_row<LG><<<grid, g.threads, smem, st>>>(out, ps, base0, galois0, base1, bstride, u, w, level,
+    RK_LOG_SWITCH(logb, (rk_launch(k_moddown_row<LG>, grid, g.threads, smem, st, out, ps, base0, galois0, base1, bstride, u, w, level,
                                                                           env.alpha, env.conv, logn, g.units, env.pc, env.tw.psi)));
 }

@@ -35,7 +35,8 @@ using namespace nttc;
 
 template <int LOG, bool INV, bool COL>
 __global__ void __launch_bounds__(256, (LOG <= 8 ? (COL ? RK_NTT_COL_BLOCKS : RK_NTT_ROW_BLOCKS) : 2)) k_ntt_pass(LimbSet s, int logn, int loga, int units, const PrimeConst* __restrict__ pc,
-                                                  const u64* __restrict__ tw, NttEpilogue epi) {
+                                                  const u64* __restrict__ tw) {
+    RK_KERNEL_PROLOGUE();
     using S = Shape<LOG>;
     constexpr int P = S::P, E = S::E;
     extern __shared__ u64 sm[];
@@ -87,36 +88,8 @@ __global__ void __launch_bounds__(256, (LOG <= 8 ? (COL ? RK_NTT_COL_BLOCKS : RK
 #pragma unroll
             for (int m = 0; m < E; m++) sm[sidx(t * E + m)] = x[m];
             __syncthreads();
-            if (epi.mode == RK_EPI_STORE) {
 #pragma unroll
-                for (int m = 0; m < E; m++) g[t + P * m] = reduce_4q(sm[sidx(t + P * m)], q, q2);
-            } else if (epi.mode == RK_EPI_RESCALE) {
-                u64* d = epi.dst + (size_t)blockIdx.z * epi.dst_ps + (size_t)limb * n + (size_t)rho * B;
-                const u64 w = epi.tab[limb], wsh = epi.tab[epi.L1 + limb];
-#pragma unroll
-                for (int m = 0; m < E; m++) {
-                    const u64 y = reduce_4q(sm[sidx(t + P * m)], q, q2);
-                    d[t + P * m] = shoup_mul(sub_mod(d[t + P * m], y, q), w, wsh, q);
-                }
-            } else {
-                const int z = blockIdx.z, b = z >> 1, p = z & 1;
-                const u64* ur = epi.u + (size_t)z * epi.u_ps + (size_t)limb * n + (size_t)rho * B;
-                u64* d = epi.dst + (size_t)z * epi.dst_ps + (size_t)limb * n + (size_t)rho * B;
-                const u64* base = p == 0 ? epi.base0 : epi.base1;
-                const u64 w = epi.tab[2 * limb], wsh = epi.tab[2 * limb + 1];
-#pragma unroll
-                for (int m = 0; m < E; m++) {
-                    const int xo = t + P * m;
-                    const u64 y = reduce_4q(sm[sidx(xo)], q, q2);
-                    u64 v = shoup_mul(sub_mod(ur[xo], y, q), w, wsh, q);
-                    if (base) {
-                        const int k = rho * B + xo;
-                        const int src = (p == 0 && epi.galois0) ? galois_src(k, epi.galois0, logn) : k;
-                        v = add_mod(v, base[(size_t)b * epi.bstride + (size_t)limb * n + src], q);
-                    }
-                    d[xo] = v;
-                }
-            }
+            for (int m = 0; m < E; m++) g[t + P * m] = reduce_4q(sm[sidx(t + P * m)], q, q2);
         }
     } else {
         // load the contiguous set {t E + m}
@@ -151,11 +124,11 @@ __global__ void __launch_bounds__(256, (LOG <= 8 ? (COL ? RK_NTT_COL_BLOCKS : RK
 
 template <bool INV, bool COL>
 void pass_launch(int LOG, dim3 grid, int threads, size_t smem, cudaStream_t st, const LimbSet& s, int logn, int loga,
-                 int units, const PrimeConst* pc, const u64* tw, const NttEpilogue& epi = NttEpilogue{}) {
+                 int units, const PrimeConst* pc, const u64* tw) {
     switch (LOG) {
 #define RK_NTT_CASE(L)                                                                                        \
     case L:                                                                                                   \
-        k_ntt_pass<L, INV, COL><<<grid, threads, smem, st>>>(s, logn, loga, units, pc, tw, epi);              \
+        rk_launch(k_ntt_pass<L, INV, COL>, grid, threads, smem, st, s, logn, loga, units, pc, tw);                   \
         break;
         RK_NTT_CASE(5)
         RK_NTT_CASE(6)
@@ -216,7 +189,7 @@ void ntt_init_attributes() {
     set_smem_attr<true, true>();
 }
 
-void launch_ntt_forward(const KernelEnv& env, const LimbSet& s, cudaStream_t st, const NttEpilogue* epi) {
+void launch_ntt_forward(const KernelEnv& env, const LimbSet& s, cudaStream_t st) {
     if (s.n_limbs <= 0 || s.n_polys <= 0) return;
     const double limbs = (double)s.n_limbs * s.n_polys - (s.skip_ds ? (double)(s.n_polys / s.skip_beta) * s.split : 0.0);
     ProfScope ps(env, KK_NTT_FWD, st, 2, 2.0 * limbs * 8.0 * env.n, limbs * (env.n / 2) * env.logn);
@@ -225,8 +198,7 @@ void launch_ntt_forward(const KernelEnv& env, const LimbSet& s, cudaStream_t st,
     PassGeom c = geom(loga, 1 << logb, s, env.sms, env.tune ? env.tune->ntt_units[0][1][sm] : 0);
     pass_launch<false, true>(loga, c.grid, c.threads, c.smem, st, s, logn, loga, c.units, env.pc, env.tw.psi);
     PassGeom r = geom(logb, 1 << loga, s, env.sms, env.tune ? env.tune->ntt_units[0][0][sm] : 0);
-    pass_launch<false, false>(logb, r.grid, r.threads, r.smem, st, s, logn, loga, r.units, env.pc, env.tw.psi,
-                              epi ? *epi : NttEpilogue{});
+    pass_launch<false, false>(logb, r.grid, r.threads, r.smem, st, s, logn, loga, r.units, env.pc, env.tw.psi);
 }
 
 void launch_ntt_inverse(const KernelEnv& env, const LimbSet& s, cudaStream_t st) {
