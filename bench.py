@@ -88,6 +88,41 @@ def small_rank_workload(stream, device, reps=20):
         ctx.close()
 
 
+def cheb_comparator_workload(stream, device, depths=(8, 10, 12), reps=3):
+    """Rank of 128 uniform values with the Chebyshev-approximated comparison (Sec. 2.2)
+    at several comparison depths (App. B, Fig. 6): latency with inputs resident (CUDA
+    events on the library stream) and the mean / max rank error, n = 2^16, 28 limbs."""
+    import numpy as np
+    import torch
+    from paper_2412_15126_gb300 import rankfhe
+    from oracle.circuits import brute_fractional_rank
+    W = WORKLOAD
+    out = {"workload": "rank N=128, uniform values in [0, 1), n=2^16, 28+3 limbs, scale 2^45, Chebyshev comparator"}
+    rng = np.random.default_rng(606)
+    vecs = [rng.uniform(0, 1, W["N"]) for _ in range(reps + 1)]
+    for d in depths:
+        ctx = rankfhe.Context(W["log_n"], W["n_limbs"], W["n_special"], W["digit_size"], W["log_scale"], W["log_q0"],
+                              W["log_special"], 0, 0, device=device, stream=stream.cuda_stream, cmp_cheb=1 << (d - 1))
+        try:
+            ctx.keygen(700 + d, W["N"])
+            cts = [ctx.encrypt(v, N=W["N"]) for v in vecs]
+            ctx.rank(cts[0]).free()
+            ctx.sync()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                ev0.record(stream)
+                outs = [ctx.rank(ct) for ct in cts[1:]]
+                ev1.record(stream)
+            ev1.synchronize()
+            errs = np.concatenate([np.abs(ctx.decrypt(o) - brute_fractional_rank(v)) for o, v in zip(outs, vecs[1:])])
+            out[f"depth{d}"] = {"coefficients": 1 << (d - 1), "ms": ev0.elapsed_time(ev1) / reps,
+                                "mean_rank_error": float(errs.mean()), "max_rank_error": float(errs.max())}
+        finally:
+            ctx.close()
+    return out
+
+
 ORDER_WORKLOAD = dict(log_n=16, n_limbs=34, n_special=3, digit_size=3, log_scale=45, log_q0=60, log_special=61,
                       d_g=3, d_f=2, N=128, levels=64)
 
@@ -785,9 +820,11 @@ def run_cuda(args):
 
     order_sort = None
     small = None
+    cheb = None
     if not args.no_order_sort and world == 1:
         order_sort = order_sort_workload(stream, local)
         small = small_rank_workload(stream, local)
+        cheb = cheb_comparator_workload(stream, local)
 
     serving = None
     if args.serve and world == 1:
@@ -823,6 +860,7 @@ def run_cuda(args):
             "graph": graph,
             "order_sort": order_sort,
             "rank8": small,
+            "cheb_comparator": cheb,
             "serving": serving,
             "autotune": tuned,
             "kernels": kinds,

@@ -62,6 +62,11 @@ typedef struct {
     uint32_t log_special;  /* bit bound of the special primes (<= 61)                    */
     uint32_t d_g;          /* compositions of g in Cmp (Sec. 2.2)                         */
     uint32_t d_f;          /* compositions of f in Cmp (Sec. 2.2)                         */
+    uint32_t cmp_cheb;     /* 0: the composite f/g comparison; else the Chebyshev-
+                              approximated comparison (Sec. 2.2) with this many
+                              coefficients (a power of two, 4..16384): the interpolant at
+                              first-kind nodes on [-1, 1] of the step 1 / 1/2 / 0, odd part
+                              plus 1/2, by Paterson-Stockmeyer; depth log2(count) + 1      */
 } rk_params;
 
 /* Ciphertext slot layouts (Sec. 2.3 row-by-row encoding; slot q*N^2 + i*N + j is
@@ -191,6 +196,12 @@ rk_status rk_encoding_import(rk_ctx* ctx, uint32_t kind, uint32_t N, uint32_t Q,
  * p = sum_i c_i T_i).  By default the library interpolates sinc^2(N t) at the
  * count = max(8N, 128) Chebyshev nodes of the first kind with its own transform.  count
  * must be a power of two >= 4.  Errors: RK_EINVAL. */
+/* Replace the Chebyshev comparator's coefficients (cmp_cheb of them) with another
+ * implementation's, so that results can be compared bit for bit.
+ * Errors: RK_EINVAL if the context does not use the Chebyshev comparator or the count
+ * differs. */
+rk_status rk_comparator_import(rk_ctx* ctx, const double* coeffs, size_t count);
+
 rk_status rk_indicator_import(rk_ctx* ctx, uint32_t N, const double* coeffs, size_t count);
 
 /* ---- client operations ------------------------------------------------------ */

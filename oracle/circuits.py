@@ -296,8 +296,33 @@ def cmp_stages(dg: int, df: int):
     return out
 
 
+class ChebCmp:
+    """The Chebyshev-approximated comparison (Sec. 2.2): the interpolant with `count`
+    coefficients (first-kind nodes on [-1, 1]) of the step 1 (x > 0), 1/2 (x = 0),
+    0 (x < 0), evaluated by Paterson-Stockmeyer; depth log2(count) + 1.  The step less
+    1/2 is odd, so its even coefficients are zero: they are set to 0 exactly and the
+    constant to 1/2, which keeps Cmp(x, x) = 1/2 exact.  Passed in place of d_g (d_f is
+    then ignored) to every circuit below."""
+
+    def __init__(self, count: int):
+        assert count >= 4 and count & (count - 1) == 0
+        self.count = count
+        c = np.polynomial.chebyshev.chebinterpolate(
+            lambda x: np.where(x > 0, 1.0, np.where(x < 0, 0.0, 0.5)), count - 1)
+        c[2::2] = 0.0
+        c[0] = 0.5
+        self.coeffs = c
+
+    def depth(self) -> int:
+        return cheb_depth(self.count)
+
+
 def cmp(B, x, dg, df):
-    """Cmp(a, b) on x = a - b: 1 if a > b, 1/2 if equal, 0 if a < b (Eq. 1)."""
+    """Cmp(a, b) on x = a - b: 1 if a > b, 1/2 if equal, 0 if a < b (Eq. 1): the
+    composite (f^d_f(g^d_g(x)) + 1)/2, or, with a ChebCmp in place of d_g, its
+    Chebyshev approximation."""
+    if isinstance(dg, ChebCmp):
+        return cheb_ps(B, x, dg.coeffs)
     for c in cmp_stages(dg, df):
         x = poly7(B, x, c)
     return B.add_const(x, 0.5)

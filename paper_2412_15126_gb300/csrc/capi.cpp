@@ -538,6 +538,17 @@ rk_status rk_sort_batch(rk_ctx* ctx, const rk_ct* const* in, size_t count, uint3
 //   [kind][galois][words][words x u64 in rk_key_import's layout]
 static const uint64_t kKeysMagic = 0x31305359454b4b52ull;   // "RKKEYS01"
 
+rk_status rk_comparator_import(rk_ctx* ctx, const double* coeffs, size_t count) {
+    return guard([&] {
+        need(ctx, "ctx");
+        need(coeffs, "coeffs");
+        RK_REQUIRE(ctx->prm.cmp_cheb != 0 && count == ctx->prm.cmp_cheb, RK_EINVAL,
+                   "the context's comparator does not take this many Chebyshev coefficients");
+        ctx->cmp_coeffs.assign(coeffs, coeffs + count);
+        ctx->generation++;
+    });
+}
+
 rk_status rk_keys_export(rk_ctx* ctx, uint8_t* buf, size_t cap, size_t* len) {
     return guard([&] {
         need(ctx, "ctx");

@@ -180,8 +180,13 @@ H poly7(Ev& E, const H& x, const double c[4]) {
     return E.add(E.add(hz, t3), t1);
 }
 
-// Cmp = (f^df(g^dg(x)) + 1) / 2 on x = a - b; the 1/2 rides on the last stage.
+H cheb_ps(Ev& E, const H& t, const std::vector<double>& c);
+const std::vector<double>& cmp_cheb_coeffs(rk_ctx* c);
+
+// Cmp = (f^df(g^dg(x)) + 1) / 2 on x = a - b; the 1/2 rides on the last stage.  A
+// context with the Chebyshev comparator evaluates its interpolant instead (Sec. 2.2).
 H cmp(Ev& E, H x, int dg, int df) {
+    if (E.c->prm.cmp_cheb) return cheb_ps(E, x, cmp_cheb_coeffs(E.c));
     const int stages = dg + df;
     for (int s = 0; s < stages; s++) {
         const double* base = s < dg ? kG : kF;
@@ -300,6 +305,36 @@ int cheb_depth(int length) {
     return d + 1;
 }
 
+// Chebyshev coefficients (count of them) of the interpolant at the first-kind nodes on
+// [-1, 1] of the step 1 (x > 0), 1/2 (x = 0), 0 (x < 0): the step less 1/2 is odd, so the
+// even coefficients are set to 0 and the constant to 1/2 (Cmp(x, x) = 1/2 exactly).
+std::vector<double> step_coeffs(int count) {
+    std::vector<double> f(count), c(count);
+    const double pi = 3.14159265358979323846;
+    for (int kk = 0; kk < count; kk++) {
+        const double x = std::cos(pi * (kk + 0.5) / count);
+        f[kk] = x > 0 ? 1.0 : (x < 0 ? 0.0 : 0.5);
+    }
+    for (int j = 0; j < count; j++) {
+        double acc = 0.0;
+        for (int kk = 0; kk < count; kk++) acc += f[kk] * std::cos(j * pi * (kk + 0.5) / count);
+        c[j] = (j % 2) ? 2.0 * acc / count : 0.0;
+    }
+    c[0] = 0.5;
+    return c;
+}
+
+const std::vector<double>& cmp_cheb_coeffs(rk_ctx* c) {
+    if (c->cmp_coeffs.empty()) c->cmp_coeffs = step_coeffs((int)c->prm.cmp_cheb);
+    return c->cmp_coeffs;
+}
+
+// levels one comparison takes
+int cmp_depth(const rk_ctx* c) {
+    return c->prm.cmp_cheb ? cheb_depth((int)c->prm.cmp_cheb) : 3 * (int)(c->prm.d_g + c->prm.d_f);
+}
+bool cmp_ok(const rk_ctx* c) { return c->prm.cmp_cheb != 0 || c->prm.d_g + c->prm.d_f >= 1; }
+
 // V_R = ReplR(V) and V_C = ReplC(TransR(V)) (Alg. 3 lines 1-2), V_R brought down to V_C's level.
 std::pair<H, H> row_col_forms(Ev& E, const H& V) {
     const int N = (int)V->N, k = log2_exact(V->N);
@@ -355,7 +390,7 @@ const std::vector<double>& indicator_coeffs(rk_ctx* c, uint32_t N) {
 }  // namespace
 
 int rank_depth(const rk_ctx* c, const rk_ct* in, uint32_t flags) {
-    int d = 1 + 3 * (int)(c->prm.d_g + c->prm.d_f) + 1;
+    int d = 1 + cmp_depth(c) + 1;
     if (in->n_real != in->N) d += 1;
     if (flags & RK_TIES_CORRECT) d += 2;
     return d;
@@ -366,7 +401,7 @@ rk_ct* circuit_rank(rk_ctx* c, const rk_ct* in, uint32_t flags) {
     RK_REQUIRE((size_t)in->Q * in->N * in->N <= (size_t)c->n / 2, RK_EINVAL, "N^2 exceeds the slots");
     RK_REQUIRE(in->level >= rank_depth(c, in, flags), RK_EDEPTH,
                "rank needs " + std::to_string(rank_depth(c, in, flags)) + " levels, input has " + std::to_string(in->level));
-    RK_REQUIRE(c->prm.d_g + c->prm.d_f >= 1, RK_EINVAL, "comparator needs at least one stage");
+    RK_REQUIRE(cmp_ok(c), RK_EINVAL, "comparator needs at least one stage");
     RK_REQUIRE(!((flags & RK_TIES_CORRECT) && in->n_real != in->N), RK_EINVAL,
                "tie correction of a padded vector is not supported");
     Ev E{c};
@@ -390,13 +425,13 @@ static void check_square(rk_ctx* c, const rk_ct* in, int need, const char* what)
     RK_REQUIRE(in->layout == RK_LAYOUT_ROW, RK_EINVAL, std::string(what) + " expects a row vector");
     RK_REQUIRE((size_t)in->Q * in->N * in->N <= (size_t)c->n / 2, RK_EINVAL, "N^2 exceeds the slots");
     RK_REQUIRE(in->n_real == in->N, RK_EINVAL, std::string(what) + " of a padded vector is not supported");
-    RK_REQUIRE(c->prm.d_g + c->prm.d_f >= 1, RK_EINVAL, "comparator needs at least one stage");
+    RK_REQUIRE(cmp_ok(c), RK_EINVAL, "comparator needs at least one stage");
     RK_REQUIRE(in->level >= need, RK_EDEPTH,
                std::string(what) + " needs " + std::to_string(need) + " levels, input has " + std::to_string(in->level));
 }
 
 int order_stat_depth(rk_ctx* c, const rk_ct* in, uint32_t k, uint32_t flags) {
-    const int dc = 3 * (int)(c->prm.d_g + c->prm.d_f);
+    const int dc = cmp_depth(c);
     const int ind = cheb_depth((int)indicator_coeffs(c, in->N).size());
     int extra = 0;
     if (!(flags & RK_TIES_ALL)) extra = 2;                              // tie fold
@@ -477,7 +512,7 @@ rk_ct* circuit_median(rk_ctx* c, const rk_ct* in) {
 }
 
 int sort_depth(rk_ctx* c, const rk_ct* in) {
-    const int dc = 3 * (int)(c->prm.d_g + c->prm.d_f);
+    const int dc = cmp_depth(c);
     return 1 + dc + 2 + 1 + cheb_depth((int)indicator_coeffs(c, in->N).size()) + 1 + 1;
 }
 
@@ -554,7 +589,7 @@ static void check_blocks(rk_ctx* c, const rk_ct* const* blocks, int L, int need,
 // (j >= i) as one stack through Cmp; then
 // R_i = TransC(SumC(sum_{j<i} (1 - C_{j,i}))) + SumR(sum_{j>=i} C_{i,j}) + 1/2 (Eq. 3).
 void circuit_rank_blocked(rk_ctx* c, const rk_ct* const* blocks, int L, rk_ct** outs) {
-    const int need = 3 + 3 * (int)(c->prm.d_g + c->prm.d_f);
+    const int need = 3 + cmp_depth(c);
     check_blocks(c, blocks, L, need, "blocked rank");
     const int Bq = blocks[0]->B;
     Ev E{c};
@@ -644,7 +679,7 @@ static H repl_r(Ev& E, H x) {
     return x;
 }
 
-static int blocked_rank_tc_depth(const rk_ctx* c) { return 1 + 3 * (int)(c->prm.d_g + c->prm.d_f) + 3; }
+static int blocked_rank_tc_depth(const rk_ctx* c) { return 1 + cmp_depth(c) + 3; }
 
 // Tie-corrected ranks of a multi-ciphertext vector (Alg. 7 with Alg. 6 across blocks).
 // The rank of element b of block i counts the smaller values and the equal values at
@@ -798,9 +833,9 @@ void circuit_sort_blocked(rk_ctx* c, const rk_ct* const* blocks, int L, rk_ct** 
 rk_ct* circuit_compare_matrix(rk_ctx* c, const rk_ct* in) {
     RK_REQUIRE(in->layout == RK_LAYOUT_ROW, RK_EINVAL, "compare_matrix expects a row vector");
     RK_REQUIRE((size_t)in->Q * in->N * in->N <= (size_t)c->n / 2, RK_EINVAL, "N^2 exceeds the slots");
-    const int need = 1 + 3 * (int)(c->prm.d_g + c->prm.d_f);
+    const int need = 1 + cmp_depth(c);
     RK_REQUIRE(in->level >= need, RK_EDEPTH, "comparison needs " + std::to_string(need) + " levels");
-    RK_REQUIRE(c->prm.d_g + c->prm.d_f >= 1, RK_EINVAL, "comparator needs at least one stage");
+    RK_REQUIRE(cmp_ok(c), RK_EINVAL, "comparator needs at least one stage");
     Ev E{c};
     H V(ct_clone_meta(in, in->level));
     ev_copy(c, in, V.p);

@@ -121,6 +121,8 @@ static void validate(const rk_params* p) {
     RK_REQUIRE(p->n_limbs >= 1 && p->n_special >= 1 && p->n_special <= RK_MAX_SPECIAL, RK_EINVAL, "bad limb counts");
     RK_REQUIRE(p->n_limbs + p->n_special <= RK_MAX_PRIMES, RK_EINVAL, "too many primes");
     RK_REQUIRE(p->digit_size >= 1 && p->digit_size <= RK_MAX_DIGIT, RK_EINVAL, "digit_size must be in [1, 8]");
+    RK_REQUIRE(p->cmp_cheb == 0 || (p->cmp_cheb >= 4 && p->cmp_cheb <= 16384 && (p->cmp_cheb & (p->cmp_cheb - 1)) == 0),
+               RK_EINVAL, "cmp_cheb must be 0 or a power of two in [4, 16384]");
     RK_REQUIRE((p->n_limbs + p->digit_size - 1) / p->digit_size <= 16, RK_EINVAL, "at most 16 key-switching digits");
     RK_REQUIRE(p->log_scale >= 20 && p->log_scale <= 58, RK_EINVAL, "log_scale must be in [20, 58]");
     RK_REQUIRE(p->log_q0 >= 20 && p->log_q0 <= 61, RK_EINVAL, "log_q0 must be in [20, 61]");

@@ -189,6 +189,7 @@ struct rk_ctx {
     bool stack_blocks = true;     // blocked rank: blocks and block pairs as stacks (else one by one)
     double ks_group_bytes = 48.0 * (1 << 20);   // lifted digits kept in L2 between the fused kernels
     size_t ind_stack_bytes = (size_t)4 << 30;   // working set of one stacked indicator evaluation
+    std::vector<double> cmp_coeffs;             // Chebyshev comparator coefficients (computed or imported)
     // plaintext caches: key = (kind, N, Q, n_real, level)
     std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint32_t, int>, u64*> plain_cache;
     std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint32_t>, std::vector<double>> encodings;

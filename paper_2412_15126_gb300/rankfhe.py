@@ -41,7 +41,8 @@ class RkError(RuntimeError):
 
 class Params(ctypes.Structure):
     _fields_ = [(name, ctypes.c_uint32) for name in
-                ("log_n", "n_limbs", "n_special", "digit_size", "log_scale", "log_q0", "log_special", "d_g", "d_f")]
+                ("log_n", "n_limbs", "n_special", "digit_size", "log_scale", "log_q0", "log_special", "d_g", "d_f",
+                 "cmp_cheb")]
 
 
 _vp = ctypes.c_void_p
@@ -103,6 +104,7 @@ _sig("rk_sort", [_vp, _vp, _u32, ctypes.POINTER(_vp)])
 _sig("rk_order_value", [_vp, _vp, _u32, ctypes.POINTER(_vp)])
 _sig("rk_median", [_vp, _vp, ctypes.POINTER(_vp)])
 _sig("rk_indicator_import", [_vp, _u32, _dp, _sz])
+_sig("rk_comparator_import", [_vp, _dp, _sz])
 _sig("rk_rank_batch", [_vp, ctypes.POINTER(_vp), _sz, _u32, ctypes.POINTER(_vp)])
 _sig("rk_order_stat_batch", [_vp, ctypes.POINTER(_vp), _sz, _u32, _u32, ctypes.POINTER(_vp)])
 _sig("rk_sort_batch", [_vp, ctypes.POINTER(_vp), _sz, _u32, ctypes.POINTER(_vp)])
@@ -195,8 +197,8 @@ class RankGraph:
 
 class Context:
     def __init__(self, log_n, n_limbs, n_special, digit_size, log_scale, log_q0=60, log_special=61,
-                 d_g=4, d_f=2, device=0, stream=None):
-        self.params = Params(log_n, n_limbs, n_special, digit_size, log_scale, log_q0, log_special, d_g, d_f)
+                 d_g=4, d_f=2, device=0, stream=None, cmp_cheb=0):
+        self.params = Params(log_n, n_limbs, n_special, digit_size, log_scale, log_q0, log_special, d_g, d_f, cmp_cheb)
         h = _vp()
         _check(_L.rk_ctx_create(ctypes.byref(self.params), device, _vp(stream) if stream else None, ctypes.byref(h)))
         self.handle = h
@@ -395,6 +397,10 @@ class Context:
 
     def median(self, ct):
         return self._out(_L.rk_median, ct.handle)
+
+    def comparator_import(self, coeffs):
+        c = np.ascontiguousarray(coeffs, dtype=np.float64)
+        _check(_L.rk_comparator_import(self.handle, c.ctypes.data_as(_dp), c.size))
 
     def indicator_import(self, N, coeffs):
         c = np.ascontiguousarray(coeffs, dtype=np.float64)

@@ -341,3 +341,37 @@ def test_order_value_middle_statistic():
     B = C.PlainSlots(128, 60)
     got = B.values(C.order_value(B, B.fresh(v), 8, 4, 4, 2))
     assert abs(got[0] - np.sort(v)[3]) < 1e-6
+
+
+def test_chebyshev_comparator_closed_form_and_ties():
+    """The Chebyshev comparator evaluated by Paterson-Stockmeyer equals numpy's chebval
+    of its coefficients, is 1/2 exactly at x = 0, and tends to the step away from 0."""
+    for count in (16, 64, 256):
+        cc = C.ChebCmp(count)
+        x = np.linspace(-1, 1, 401)
+        B = C.PlainSlots(401, 40)
+        got = B.values(C.cmp(B, C.PV(x.copy(), 40), cc, 0))
+        assert np.max(np.abs(got - np.polynomial.chebyshev.chebval(x, cc.coeffs))) < 1e-9
+        assert got[200] == 0.5
+        far = np.abs(x) > 8.0 / count
+        assert np.max(np.abs(got[far] - (x[far] > 0))) < 0.1
+
+
+def test_chebyshev_comparator_reproduces_fig6(golden):
+    """Rank error against comparison depth with the Chebyshev comparator (App. B,
+    Fig. 6): on seeded uniform 128-element vectors the mean error of the ranks lies
+    within 25 % of the paper's printed average at every depth 6..13."""
+    g = golden["fig6_rank_error"]
+    rng = np.random.default_rng(66)
+    vs = [rng.uniform(0, 1, 128) for _ in range(8)]
+    for depth, paper in zip(g["depth"], g["avg_error"]):
+        if depth > 13:
+            continue
+        cc = C.ChebCmp(1 << (depth - 1))
+        errs = []
+        for v in vs:
+            B = C.PlainSlots(2 * 128 * 128, 40)
+            R = B.values(C.rank(B, B.fresh(v), 128, cc, 0))[:128]
+            errs.append(np.abs(R - C.brute_fractional_rank(v)))
+        mean = float(np.mean(errs))
+        assert abs(mean - paper) < 0.25 * paper, (depth, mean, paper)
