@@ -272,16 +272,19 @@ def trans_c(B, x, N, Q=1, trace=None):
 # --------------------------------------------------------------------------
 def poly7(B, x, c):
     """Odd degree-7 polynomial c1 x + c3 x^3 + c5 x^5 + c7 x^7 in multiplicative depth 3
-    with four ciphertext products:  p = (c5 x + c7 x^3) x^4 + (c3/c7)(c7 x^3) + c1 x."""
+    with four ciphertext products:  p = (c5 x + c7 x^3) x^4 + [(c3/c7)(c7 x^3) + c1 x],
+    the bracket one exact linear combination (one rescale) of c7 x^3 and x brought down
+    two levels; nine rescales in all."""
     c1, c3, c5, c7 = c
-    y = B.mul(x, x)                                        # x^2
-    z = B.mul(y, y)                                        # x^4
-    b7 = B.mul(B.mul_scalar(x, c7), y)                     # c7 x^3
-    a5 = B.mul_scalar(B.mul_scalar(x, c5), 1.0)            # c5 x
-    hz = B.mul(B.add(a5, b7), z)                           # c5 x^5 + c7 x^7
-    t3 = B.mul_scalar(b7, c3 / c7)                         # c3 x^3
-    t1 = B.mul_scalar(B.mul_scalar(B.mul_scalar(x, c1), 1.0), 1.0)   # c1 x
-    return B.add(B.add(hz, t3), t1)
+    y = B.mul(x, x)                                        # x^2          (l-1)
+    z = B.mul(y, y)                                        # x^4          (l-2)
+    x1 = B.mul_scalar(x, 1.0)                              # x            (l-1)
+    b7 = B.mul(B.mul_scalar(x, c7), y)                     # c7 x^3       (l-2)
+    a5 = B.mul_scalar(x1, c5)                              # c5 x         (l-2)
+    hz = B.mul(B.add(a5, b7), z)                           # c5 x^5 + c7 x^7 (l-3)
+    x2 = B.mul_scalar(x1, 1.0)                             # x            (l-2)
+    rest = B.lincomb([b7, x2], [c3 / c7, c1])              # c3 x^3 + c1 x (l-3)
+    return B.add(hz, rest)
 
 
 def cmp_stages(dg: int, df: int):

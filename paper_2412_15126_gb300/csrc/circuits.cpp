@@ -167,17 +167,23 @@ const double kF[4] = {35.0 / 16, -35.0 / 16, 21.0 / 16, -5.0 / 16};
 const double kG[4] = {4589.0 / 1024, -16577.0 / 1024, 25614.0 / 1024, -12860.0 / 1024};
 
 // c1 x + c3 x^3 + c5 x^5 + c7 x^7 in depth 3 with four ciphertext products:
-// p = (c5 x + c7 x^3) x^4 + (c3/c7)(c7 x^3) + c1 x.
+// p = (c5 x + c7 x^3) x^4 + [(c3/c7)(c7 x^3) + c1 x], the bracket one exact linear
+// combination (one rescale) of c7 x^3 and x brought down two levels; nine rescales.
 H poly7(Ev& E, const H& x, const double c[4]) {
     const double c1 = c[0], c3 = c[1], c5 = c[2], c7 = c[3];
-    H y = E.mul(x, x);
-    H z = E.mul(y, y);
-    H b7 = E.mul(E.mul_scalar(x, c7), y);
-    H a5 = E.mul_scalar(E.mul_scalar(x, c5), 1.0);
-    H hz = E.mul(E.add(a5, b7), z);
-    H t3 = E.mul_scalar(b7, c3 / c7);
-    H t1 = E.mul_scalar(E.mul_scalar(E.mul_scalar(x, c1), 1.0), 1.0);
-    return E.add(E.add(hz, t3), t1);
+    H y = E.mul(x, x);                        // x^2      (l-1)
+    H z = E.mul(y, y);                        // x^4      (l-2)
+    H x1 = E.mul_scalar(x, 1.0);              // x        (l-1)
+    H b7 = E.mul(E.mul_scalar(x, c7), y);     // c7 x^3   (l-2)
+    H a5 = E.mul_scalar(x1, c5);              // c5 x     (l-2)
+    H hz = E.mul(E.add(a5, b7), z);           // c5 x^5 + c7 x^7 (l-3)
+    H x2 = E.mul_scalar(x1, 1.0);             // x        (l-2)
+    std::vector<H> terms;
+    terms.push_back(std::move(b7));
+    terms.push_back(std::move(x2));
+    const double cs[2] = {c3 / c7, c1};
+    H rest = E.lincomb(terms, cs);            // c3 x^3 + c1 x (l-3)
+    return E.add(hz, rest);
 }
 
 H cheb_ps(Ev& E, const H& t, const std::vector<double>& c);
