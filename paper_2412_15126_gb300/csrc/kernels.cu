@@ -300,51 +300,33 @@ void launch_moddown_conv(const KernelEnv& env, const u64* u, u64* w, int level, 
 // ===========================================================================
 // Up to CH stacked ciphertexts per thread: each key word is read once per chunk.
 // CH is the smallest of 1, 2, 4, 8 that covers the stack (chunks of 8 beyond), so a
-// single ciphertext keeps two accumulators and the digit loop stays unrolled.  With
-// EL = 2 a thread takes two adjacent coefficients, so the key stream moves in 16-byte
-// loads and stores.
-template <int CH, int EL>
+// single ciphertext keeps two accumulators and the digit loop stays unrolled.
+template <int CH>
 __global__ void __launch_bounds__(TPB) k_ks_inner(const u64* __restrict__ ext, size_t ext_stride, const u64* __restrict__ key,
                                                   u64* __restrict__ u, int level, int L, int alpha, int beta, u64 galois,
                                                   int logn, int B, const PrimeConst* __restrict__ pc) {
     RK_KERNEL_PROLOGUE();
     const int n = 1 << logn;
-    const int k = (blockIdx.x * TPB + threadIdx.x) * EL, t = blockIdx.y;
+    const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y;
     const int b0 = blockIdx.z * CH;
     const int nb = min(CH, B - b0);
     const int pid = t <= level ? t : L + 1 + (t - level - 1);
     const PrimeConst P = pc[pid];
-    int src[EL];
-#pragma unroll
-    for (int e = 0; e < EL; e++) src[e] = galois ? galois_src(k + e, galois, logn) : k + e;
+    const int src = galois ? galois_src(k, galois, logn) : k;
     const size_t KL = (size_t)(L + 1 + alpha) * n;
     const size_t estride = (size_t)beta * ext_stride;   // between stacked ciphertexts
-    Acc128 a0[CH][EL], a1[CH][EL];
+    Acc128 a0[CH], a1[CH];
     const u64* kj = key + (size_t)pid * n + k;
-    const u64* ej = ext + (size_t)b0 * estride + (size_t)t * n;
+    const u64* ej = ext + (size_t)b0 * estride + (size_t)t * n + src;
 #pragma unroll 4
     for (int j = 0; j < beta; j++) {
-        u64 kb[EL], ka[EL];
-        if (EL == 2) {
-            const ulonglong2 pb = __ldg(reinterpret_cast<const ulonglong2*>(kj));
-            const ulonglong2 pa = __ldg(reinterpret_cast<const ulonglong2*>(kj + KL));
-            kb[0] = pb.x;
-            kb[EL - 1] = pb.y;
-            ka[0] = pa.x;
-            ka[EL - 1] = pa.y;
-        } else {
-            kb[0] = __ldg(kj);
-            ka[0] = __ldg(kj + KL);
-        }
+        const u64 kb = __ldg(kj), ka = __ldg(kj + KL);
 #pragma unroll
         for (int b = 0; b < CH; b++) {
             if (CH == 1 || b < nb) {
-#pragma unroll
-                for (int e = 0; e < EL; e++) {
-                    const u64 x = ej[(size_t)b * estride + src[e]];
-                    a0[b][e].mac(x, kb[e]);
-                    a1[b][e].mac(x, ka[e]);
-                }
+                const u64 e = ej[(size_t)b * estride];
+                a0[b].mac(e, kb);
+                a1[b].mac(e, ka);
             }
         }
         kj += 2 * KL;
@@ -354,15 +336,9 @@ __global__ void __launch_bounds__(TPB) k_ks_inner(const u64* __restrict__ ext, s
 #pragma unroll
     for (int b = 0; b < CH; b++) {
         if (CH == 1 || b < nb) {
-            u64* ub = u + (size_t)(b0 + b) * 2 * ul * n + (size_t)t * n + k;
-            if (EL == 2) {
-                *reinterpret_cast<ulonglong2*>(ub) = make_ulonglong2(a0[b][0].redc(P.q, P.qinv), a0[b][EL - 1].redc(P.q, P.qinv));
-                *reinterpret_cast<ulonglong2*>(ub + (size_t)ul * n) =
-                    make_ulonglong2(a1[b][0].redc(P.q, P.qinv), a1[b][EL - 1].redc(P.q, P.qinv));
-            } else {
-                ub[0] = a0[b][0].redc(P.q, P.qinv);
-                ub[(size_t)ul * n] = a1[b][0].redc(P.q, P.qinv);
-            }
+            u64* ub = u + (size_t)(b0 + b) * 2 * ul * n;
+            ub[(size_t)t * n + k] = a0[b].redc(P.q, P.qinv);
+            ub[(size_t)ul * n + (size_t)t * n + k] = a1[b].redc(P.q, P.qinv);
         }
     }
 }
@@ -375,13 +351,12 @@ void launch_ks_inner(const KernelEnv& env, const u64* ext, size_t ext_stride, co
     const int chunks = (B + ch - 1) / ch;
     ProfScope pf(env, KK_KS_INNER, st, 1, ((double)B * beta + 2.0 * beta * chunks + 2.0 * B) * QP * 8.0 * env.n,
                  2.0 * B * beta * QP * env.n);
-    const dim3 g(env.n / TPB, level + 1 + env.alpha, chunks);
-    const dim3 g2(env.n / (2 * TPB), level + 1 + env.alpha, chunks);
+    dim3 g(env.n / TPB, level + 1 + env.alpha, chunks);
     switch (ch) {
-        case 1: rk_launch(k_ks_inner<1, 2>, g2, TPB, 0, st, ext, ext_stride, key, u, level, env.L, env.alpha, beta, galois, env.logn, B, env.pc); break;
-        case 2: rk_launch(k_ks_inner<2, 1>, g, TPB, 0, st, ext, ext_stride, key, u, level, env.L, env.alpha, beta, galois, env.logn, B, env.pc); break;
-        case 4: rk_launch(k_ks_inner<4, 1>, g, TPB, 0, st, ext, ext_stride, key, u, level, env.L, env.alpha, beta, galois, env.logn, B, env.pc); break;
-        default: rk_launch(k_ks_inner<8, 1>, g, TPB, 0, st, ext, ext_stride, key, u, level, env.L, env.alpha, beta, galois, env.logn, B, env.pc); break;
+        case 1: rk_launch(k_ks_inner<1>, g, TPB, 0, st, ext, ext_stride, key, u, level, env.L, env.alpha, beta, galois, env.logn, B, env.pc); break;
+        case 2: rk_launch(k_ks_inner<2>, g, TPB, 0, st, ext, ext_stride, key, u, level, env.L, env.alpha, beta, galois, env.logn, B, env.pc); break;
+        case 4: rk_launch(k_ks_inner<4>, g, TPB, 0, st, ext, ext_stride, key, u, level, env.L, env.alpha, beta, galois, env.logn, B, env.pc); break;
+        default: rk_launch(k_ks_inner<8>, g, TPB, 0, st, ext, ext_stride, key, u, level, env.L, env.alpha, beta, galois, env.logn, B, env.pc); break;
     }
 }
 
