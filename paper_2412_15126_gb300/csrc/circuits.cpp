@@ -79,6 +79,11 @@ struct Ev {
         ev_rotate_many(c, x.p, &r, 1, outs);
         return o;
     }
+    H rot_add(const H& x, int r) {   // x + rot(x, r)
+        H o = fresh(x, x->level);
+        ev_rotate_add(c, x.p, r, o.p);
+        return o;
+    }
     std::pair<H, H> rot2(const H& x, int r1, int r2) {
         H a = fresh(x, x->level), b = fresh(x, x->level);
         int r[2] = {r1, r2};
@@ -207,7 +212,7 @@ H cmp(Ev& E, H x, int dg, int df) {
 // SumR (Alg. 8) with the row mask `kind` (RK_MASK_ROW0, or RK_MASK_ROW0S to divide by N)
 H sum_rows(Ev& E, H x, uint32_t kind) {
     const int N = (int)x->N, k = log2_exact(x->N);
-    for (int i = 0; i < k; i++) x = E.add(x, E.rot(x, N << i));
+    for (int i = 0; i < k; i++) x = E.rot_add(x, N << i);
     return E.mul_mask(x, kind);
 }
 H sum_r(Ev& E, H x) { return sum_rows(E, std::move(x), RK_MASK_ROW0); }
@@ -215,20 +220,20 @@ H sum_r(Ev& E, H x) { return sum_rows(E, std::move(x), RK_MASK_ROW0); }
 // SumC (Alg. 9) with the column mask `kind`
 H sum_cols(Ev& E, H x, uint32_t kind) {
     const int k = log2_exact(x->N);
-    for (int i = 0; i < k; i++) x = E.add(x, E.rot(x, 1 << i));
+    for (int i = 0; i < k; i++) x = E.rot_add(x, 1 << i);
     return E.mul_mask(x, kind);
 }
 
 // TransC (Alg. 2): X <- X + (X << N(N-1)/2^i), i = 1 .. log N, then MaskR(X, 0)
 H trans_c(Ev& E, H x) {
     const int N = (int)x->N, k = log2_exact(x->N);
-    for (int i = 1; i <= k; i++) x = E.add(x, E.rot(x, (N * (N - 1)) >> i));
+    for (int i = 1; i <= k; i++) x = E.rot_add(x, (N * (N - 1)) >> i);
     return E.mul_mask(x, RK_MASK_ROW0);
 }
 // ReplC (Alg. 11)
 H repl_c(Ev& E, H x) {
     const int k = log2_exact(x->N);
-    for (int i = 0; i < k; i++) x = E.add(x, E.rot(x, -(1 << i)));
+    for (int i = 0; i < k; i++) x = E.rot_add(x, -(1 << i));
     return x;
 }
 
@@ -351,9 +356,9 @@ std::pair<H, H> row_col_forms(Ev& E, const H& V) {
     } else {
         auto rt = E.rot2(V, -N, -((N * (N - 1)) >> 1));   // hoisted: one ModUp for both
         VR = E.add(V, rt.first);
-        for (int i = 1; i < k; i++) VR = E.add(VR, E.rot(VR, -(N << i)));
+        for (int i = 1; i < k; i++) VR = E.rot_add(VR, -(N << i));
         VT = E.add(V, rt.second);
-        for (int i = 2; i <= k; i++) VT = E.add(VT, E.rot(VT, -((N * (N - 1)) >> i)));
+        for (int i = 2; i <= k; i++) VT = E.rot_add(VT, -((N * (N - 1)) >> i));
     }
     H VC = E.mul_mask(VT, RK_MASK_COL0);                 // TransR's MaskC
     VC = repl_c(E, std::move(VC));
@@ -681,7 +686,7 @@ static H cmp_strict(Ev& E, const H& C) {
 // ReplR (Alg. 10): X <- X + (X >> N 2^i)
 static H repl_r(Ev& E, H x) {
     const int N = (int)x->N, k = log2_exact(x->N);
-    for (int i = 0; i < k; i++) x = E.add(x, E.rot(x, -(N << i)));
+    for (int i = 0; i < k; i++) x = E.rot_add(x, -(N << i));
     return x;
 }
 
@@ -740,7 +745,7 @@ static std::pair<H, H> blocked_ranks_tc(rk_ctx* c, const rk_ct* const* blocks, i
     H S = stack_of(c, ap);
     {
         const int k = log2_exact((uint32_t)Bsz);
-        for (int r = 0; r < k; r++) S = E.add(S, E.rot(S, Bsz << r));
+        for (int r = 0; r < k; r++) S = E.rot_add(S, Bsz << r);
         S = E.mul_mask_d(S, rmask, Dn);
     }
     if (L == 1) return std::make_pair(std::move(S), std::move(rc.first));
@@ -749,7 +754,7 @@ static std::pair<H, H> blocked_ranks_tc(rk_ctx* c, const rk_ct* const* blocks, i
     H T = sum_cols(E, stack_of(c, bp), RK_MASK_COL0);   // stack of (L - 1) Bq
     {
         const int k = log2_exact((uint32_t)Bsz);
-        for (int r = 1; r <= k; r++) T = E.add(T, E.rot(T, (Bsz * (Bsz - 1)) >> r));
+        for (int r = 1; r <= k; r++) T = E.rot_add(T, (Bsz * (Bsz - 1)) >> r);
         T = E.mul_mask_d(T, rmask, Dn);
     }
     std::vector<H> R;

@@ -223,19 +223,32 @@ void ev_add_const(rk_ctx* c, const rk_ct* a, double v, rk_ct* out) {
     copy_meta(out, a);
 }
 
-void ev_rescale_inplace(rk_ctx* c, rk_ct* a) {
+// Rescale of `a` (level l) into `out` (level l - 1): out_i = (K_i a_i - v_i) q_l^-1,
+// i < l, where v is the centred lift of the last limb of `out` (which must hold
+// K_l a_l) taken back to the evaluation domain.  K null means K = 1 (out may be a);
+// otherwise it is the scalar product fused with its rescale.
+static void rescale_into(rk_ctx* c, const rk_ct* a, const ScalarArg* K, rk_ct* out) {
     const int l = a->level;
-    RK_REQUIRE(l >= 1, RK_EDEPTH, "rescale: no level left");
     ensure_batch(c, a->B);
     Scratch S = scratch_layout(c);
     const size_t ps = c->poly_stride(), n = c->n;
     const int polys = 2 * a->B;
-    launch_ntt_inverse(c->env, ls_one(a->data + (size_t)l * n, ps, polys, l), c->stream);
-    launch_rescale_lift(c->env, a->data + (size_t)l * n, ps, S.v, l, c->stream, polys);
-    launch_ntt_forward(c->env, ls_q(S.v, (size_t)l * n, polys, l), c->stream);
-    launch_rescale_combine(c->env, a->data, ps, S.v, l, c->stream, polys);
-    a->level = l - 1;
+    u64* last = out->data + (size_t)l * n;
+    launch_ntt_inverse(c->env, ls_one(last, ps, polys, l), c->stream);
+    LimbSet v = ls_q(S.v, (size_t)l * n, polys, l);   // the lift happens in the first forward pass
+    v.lift = last;
+    v.lift_stride = ps;
+    v.lift_mod = c->env.conv.rescale + (size_t)l * 3 * (c->L + 1) + 2 * (c->L + 1);
+    v.lift_q = c->primes[l];
+    launch_ntt_forward(c->env, v, c->stream);
+    launch_rescale_combine(c->env, out->data, a->data, ps, S.v, l, K, c->stream, polys);
+    out->level = l - 1;
     c->n_rescale++;
+}
+
+void ev_rescale_inplace(rk_ctx* c, rk_ct* a) {
+    RK_REQUIRE(a->level >= 1, RK_EDEPTH, "rescale: no level left");
+    rescale_into(c, a, nullptr, a);
 }
 
 static double factor_scale(const rk_ctx* c, int l) {
@@ -245,11 +258,14 @@ static double factor_scale(const rk_ctx* c, int l) {
 void ev_mul_scalar(rk_ctx* c, const rk_ct* a, double v, rk_ct* out) {
     const int l = a->level;
     RK_REQUIRE(l >= 1, RK_EDEPTH, "mul_scalar: no level left");
+    RK_REQUIRE(out->B == a->B, RK_EINVAL, "mul_scalar: stack size mismatch");
     const int64_t K = round_half_away(v * factor_scale(c, l));
-    launch_mul_scalar(c->env, out->data, a->data, scalar_residues(c, K, l + 1), l + 1, c->poly_stride(), c->stream, 2 * a->B);
-    out->level = l;
+    const ScalarArg Kr = scalar_residues(c, K, l + 1);
+    // the product's last limb only; the other limbs are scaled inside the rescale
+    launch_mul_scalar(c->env, out->data, a->data, Kr, 1, c->poly_stride(), c->stream, 2 * a->B, l);
     copy_meta(out, a);
-    ev_rescale_inplace(c, out);
+    out->level = l;
+    rescale_into(c, a, &Kr, out);
 }
 
 void ev_level_down(rk_ctx* c, const rk_ct* a, int target, rk_ct* out) {
@@ -420,20 +436,22 @@ static void ks_inner(rk_ctx* c, const u64* key, int l, u64 galois, const u64* d_
 }
 
 // ModDown of S.u and out_b = base_b + result_b (automorphism galois0 on base0), for B
-// stacked inputs (base_p of member b at base_p + b * bstride).
+// stacked inputs (base_p of member b at base_p + b * bstride); plus `addend` (the
+// output's layout) when it is not null, on the staged path only.
 static void ks_moddown(rk_ctx* c, int l, const u64* base0, u64 galois0, const u64* base1, size_t bstride, u64* out, size_t out_ps,
-                       int B) {
+                       int B, const u64* addend = nullptr) {
     Scratch S = scratch_layout(c);
     const size_t n = c->n;
     const int QP = l + 1 + c->alpha;
     launch_ntt_inverse(c->env, LimbSet{S.u + (size_t)(l + 1) * n, (size_t)QP * n, 2 * B, c->alpha, 0, 0, c->L + 1}, c->stream);
     if (c->ks_fused) {
+        RK_REQUIRE(!addend, RK_EINVAL, "fused key switching takes no addend");
         launch_moddown_col(c->env, S.u, S.w, l, c->stream, 2 * B);
         launch_moddown_row(c->env, out, out_ps, base0, galois0, base1, bstride, S.u, S.w, l, c->stream, B);
     } else {
         launch_moddown_conv(c->env, S.u, S.w, l, c->stream, 2 * B);
         launch_ntt_forward(c->env, ls_q(S.w, (size_t)(l + 1) * n, 2 * B, l + 1), c->stream);
-        launch_ks_combine(c->env, out, out_ps, base0, galois0, base1, bstride, S.u, S.w, l, c->stream, B);
+        launch_ks_combine(c->env, out, out_ps, base0, galois0, base1, bstride, S.u, S.w, l, c->stream, B, addend);
     }
     c->n_ks += (uint64_t)B;
 }
@@ -483,6 +501,30 @@ void ev_rotate_many(rk_ctx* c, const rk_ct* a, const int* r, int k, rk_ct** outs
         copy_meta(outs[i], a);
         c->n_rot += (uint64_t)a->B;
     }
+}
+
+// out = a + (a <<< r): the sum rides on the key switch's final combine (staged path).
+void ev_rotate_add(rk_ctx* c, const rk_ct* a, int r, rk_ct* out) {
+    RK_REQUIRE(out != a, RK_EINVAL, "rotate_add: output aliases input");
+    RK_REQUIRE(out->B == a->B, RK_EINVAL, "rotate_add: stack size mismatch");
+    const u64 g = galois_left(c, r);
+    if (g == 1 || c->ks_fused) {
+        rk_ct* outs[1] = {out};
+        ev_rotate_many(c, a, &r, 1, outs);
+        ev_add(c, a, out, out);
+        return;
+    }
+    RK_REQUIRE(c->gal.count(g), RK_ENOKEY, "rotation key missing for r = " + std::to_string(r));
+    const int l = a->level;
+    const size_t ps = c->poly_stride();
+    const u64* d = a->data + ps;
+    ks_lift(c, d, 2 * ps, l, a->B);
+    ks_lift_ext(c, d, 2 * ps, l, a->B);
+    ks_inner(c, c->gal[g].data, l, g, d, 2 * ps, a->B, true);
+    ks_moddown(c, l, a->data, g, nullptr, 2 * ps, out->data, ps, a->B, a->data);
+    out->level = l;
+    copy_meta(out, a);
+    c->n_rot += (uint64_t)a->B;
 }
 
 void ev_mul(rk_ctx* c, const rk_ct* a, const rk_ct* b, rk_ct* out) {

@@ -55,18 +55,19 @@ void launch_add_const(const KernelEnv& env, u64* out, const u64* a, const Scalar
 }
 
 // out = a * K_t (Shoup)
-__global__ void k_mul_scalar(u64* out, const u64* a, ScalarArg K, int n, size_t ps, const PrimeConst* __restrict__ pc) {
+// limbs t0 .. t0 + gridDim.y - 1
+__global__ void k_mul_scalar(u64* out, const u64* a, ScalarArg K, int n, size_t ps, int t0, const PrimeConst* __restrict__ pc) {
     RK_KERNEL_PROLOGUE();
-    const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y, c = blockIdx.z;
+    const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y + t0, c = blockIdx.z;
     const size_t off = c * ps + (size_t)t * n + k;
     out[off] = shoup_mul(a[off], K.w[t], K.wsh[t], pc[t].q);
 }
 
 void launch_mul_scalar(const KernelEnv& env, u64* out, const u64* a, const ScalarArg& K, int limbs, size_t ps, cudaStream_t st,
-                       int polys) {
+                       int polys, int t0) {
     ProfScope pf(env, KK_POINTWISE, st, 1, 2.0 * polys * limbs * 8.0 * env.n, 1.0 * polys * limbs * env.n);
     dim3 g(env.n / TPB, limbs, polys);
-    rk_launch(k_mul_scalar, g, TPB, 0, st, out, a, K, env.n, ps, env.pc);
+    rk_launch(k_mul_scalar, g, TPB, 0, st, out, a, K, env.n, ps, t0, env.pc);
 }
 
 // out = a * pt, pt stored times R ([limbs][n])
@@ -360,12 +361,14 @@ void launch_ks_inner(const KernelEnv& env, const u64* ext, size_t ext_stride, co
     }
 }
 
-// out[c][t] = base_c[t] (automorphism applied to base0 when galois0 != 0) + (u[c][t] - w[c][t]) * P^-1;
+// out[c][t] = base_c[t] (automorphism applied to base0 when galois0 != 0) + (u[c][t] - w[c][t]) * P^-1
+// (+ addend[c][t] when addend is not null: a rotation fused with the sum x + rot(x));
 // base_c points at limb 0 of one polynomial, or is null.
-// z = 2b + p over B stacked ciphertexts; base_p of ciphertext b at base_p + b * bstride
+// z = 2b + p over B stacked ciphertexts; base_p of ciphertext b at base_p + b * bstride;
+// the addend has the output's layout (polynomial c at addend + c * ps)
 __global__ void k_ks_combine(u64* out, size_t ps, const u64* base0, u64 galois0, const u64* base1, size_t bstride,
-                             const u64* __restrict__ u, const u64* __restrict__ w, int level, int alpha, ConvTables cv,
-                             int logn, const PrimeConst* __restrict__ pc) {
+                             const u64* __restrict__ u, const u64* __restrict__ w, const u64* addend, int level, int alpha,
+                             ConvTables cv, int logn, const PrimeConst* __restrict__ pc) {
     RK_KERNEL_PROLOGUE();
     const int n = 1 << logn;
     const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y, c = blockIdx.z;
@@ -379,14 +382,17 @@ __global__ void k_ks_combine(u64* out, size_t ps, const u64* base0, u64 galois0,
         const int src = (p == 0 && galois0) ? galois_src(k, galois0, logn) : k;
         v = add_mod(v, base[(size_t)b * bstride + (size_t)t * n + src], q);
     }
-    out[(size_t)c * ps + (size_t)t * n + k] = v;
+    const size_t off = (size_t)c * ps + (size_t)t * n + k;
+    if (addend) v = add_mod(v, addend[off], q);
+    out[off] = v;
 }
 
 void launch_ks_combine(const KernelEnv& env, u64* out, size_t ps, const u64* base0, u64 galois0, const u64* base1, size_t bstride,
-                       const u64* u, const u64* w, int level, cudaStream_t st, int B) {
-    ProfScope pf(env, KK_KS_COMBINE, st, 1, 7.0 * B * (level + 1) * 8.0 * env.n, 2.0 * B * (level + 1) * env.n);
+                       const u64* u, const u64* w, int level, cudaStream_t st, int B, const u64* addend) {
+    ProfScope pf(env, KK_KS_COMBINE, st, 1, (addend ? 9.0 : 7.0) * B * (level + 1) * 8.0 * env.n, 2.0 * B * (level + 1) * env.n);
     dim3 g(env.n / TPB, level + 1, 2 * B);
-    rk_launch(k_ks_combine, g, TPB, 0, st, out, ps, base0, galois0, base1, bstride, u, w, level, env.alpha, env.conv, env.logn, env.pc);
+    rk_launch(k_ks_combine, g, TPB, 0, st, out, ps, base0, galois0, base1, bstride, u, w, addend, level, env.alpha, env.conv,
+              env.logn, env.pc);
 }
 
 // ===========================================================================
@@ -411,22 +417,34 @@ void launch_rescale_lift(const KernelEnv& env, const u64* last, size_t ls, u64* 
     rk_launch(k_rescale_lift, g, TPB, 0, st, last, ls, v, level, env.L, env.conv, env.n, env.pc);
 }
 
-// ct[c][i] = (ct[c][i] - v[c][i]) * q_l^-1, i < level (in place)
-__global__ void k_rescale_combine(u64* ct, size_t ps, const u64* v, int level, int L, ConvTables cv, int n,
-                                  const PrimeConst* __restrict__ pc) {
+// out[c][i] = (K_i in[c][i] - v[c][i]) * q_l^-1, i < level (K_i = 1 without SCALE;
+// out may be in)
+template <bool SCALE>
+__global__ void k_rescale_combine(u64* out, const u64* in, size_t ps, const u64* v, int level, int L, ConvTables cv, ScalarArg K,
+                                  int n, const PrimeConst* __restrict__ pc) {
     RK_KERNEL_PROLOGUE();
     const int k = blockIdx.x * TPB + threadIdx.x, i = blockIdx.y, c = blockIdx.z;
     const u64 q = pc[i].q;
     const u64* tab = cv.rescale + (size_t)level * 3 * (L + 1);
     const size_t off = (size_t)c * ps + (size_t)i * n + k;
-    u64 d = sub_mod(ct[off], v[(size_t)c * level * n + (size_t)i * n + k], q);
-    ct[off] = shoup_mul(d, tab[i], tab[(L + 1) + i], q);
+    u64 x = in[off];
+    if (SCALE) x = shoup_mul(x, K.w[i], K.wsh[i], q);
+    const u64 d = sub_mod(x, v[(size_t)c * level * n + (size_t)i * n + k], q);
+    out[off] = shoup_mul(d, tab[i], tab[(L + 1) + i], q);
+}
+
+void launch_rescale_combine(const KernelEnv& env, u64* out, const u64* in, size_t ps, const u64* v, int level, const ScalarArg* K,
+                            cudaStream_t st, int polys) {
+    ProfScope pf(env, KK_RESCALE, st, 1, 3.0 * polys * level * 8.0 * env.n, 1.0 * polys * level * env.n);
+    dim3 g(env.n / TPB, level, polys);
+    if (K)
+        rk_launch(k_rescale_combine<true>, g, TPB, 0, st, out, in, ps, v, level, env.L, env.conv, *K, env.n, env.pc);
+    else
+        rk_launch(k_rescale_combine<false>, g, TPB, 0, st, out, in, ps, v, level, env.L, env.conv, ScalarArg{}, env.n, env.pc);
 }
 
 void launch_rescale_combine(const KernelEnv& env, u64* ct, size_t ps, const u64* v, int level, cudaStream_t st, int polys) {
-    ProfScope pf(env, KK_RESCALE, st, 1, 3.0 * polys * level * 8.0 * env.n, 1.0 * polys * level * env.n);
-    dim3 g(env.n / TPB, level, polys);
-    rk_launch(k_rescale_combine, g, TPB, 0, st, ct, ps, v, level, env.L, env.conv, env.n, env.pc);
+    launch_rescale_combine(env, ct, ct, ps, v, level, nullptr, st, polys);
 }
 
 // ===========================================================================

@@ -83,7 +83,7 @@ void launch_addsub(const KernelEnv& env, u64* out, const u64* a, const u64* b, i
 void launch_add_const(const KernelEnv& env, u64* out, const u64* a, const ScalarArg& K, int limbs, size_t ps, cudaStream_t st,
                       int polys = 2);
 void launch_mul_scalar(const KernelEnv& env, u64* out, const u64* a, const ScalarArg& K, int limbs, size_t ps, cudaStream_t st,
-                       int polys = 2);
+                       int polys = 2, int t0 = 0);
 void launch_mul_plain(const KernelEnv& env, u64* out, const u64* a, const u64* pt, int limbs, size_t ps, cudaStream_t st,
                       int polys = 2);
 // out[c][t] (+)= sum_i x_i[c][t] * K_i[t] for up to 16 terms; KR holds K_i times R
@@ -100,7 +100,7 @@ void launch_moddown_conv(const KernelEnv& env, const u64* u, u64* w, int level, 
 void launch_ks_inner(const KernelEnv& env, const u64* ext, size_t ext_stride, const u64* key, u64* u, int level, int beta,
                      u64 galois, cudaStream_t st, int B = 1);
 void launch_ks_combine(const KernelEnv& env, u64* out, size_t ps, const u64* base0, u64 galois0, const u64* base1, size_t bstride,
-                       const u64* u, const u64* w, int level, cudaStream_t st, int B = 1);
+                       const u64* u, const u64* w, int level, cudaStream_t st, int B = 1, const u64* addend = nullptr);
 // fused key switching (ks_fused.cu)
 void ks_fused_init_attributes();
 void launch_modup_col(const KernelEnv& env, const u64* coef, u64* ext, size_t ext_stride, int level, int beta, int t0, int limbs,
@@ -112,6 +112,9 @@ void launch_moddown_row(const KernelEnv& env, u64* out, size_t ps, const u64* ba
                         const u64* u, const u64* w, int level, cudaStream_t st, int B = 1);
 void launch_rescale_lift(const KernelEnv& env, const u64* last, size_t ls, u64* v, int level, cudaStream_t st, int polys = 2);
 void launch_rescale_combine(const KernelEnv& env, u64* ct, size_t ps, const u64* v, int level, cudaStream_t st, int polys = 2);
+// out = (K in - v) q_l^-1 on limbs < level; K null for K = 1
+void launch_rescale_combine(const KernelEnv& env, u64* out, const u64* in, size_t ps, const u64* v, int level, const ScalarArg* K,
+                            cudaStream_t st, int polys);
 void launch_reduce_signed(const KernelEnv& env, const int64_t* src, const LimbSet& s, cudaStream_t st);
 void launch_uniform(const KernelEnv& env, const LimbSet& s, u64 seed, u64 stream_id, cudaStream_t st);
 void launch_key_digit(const KernelEnv& env, u64* kb, u64* ka, const u64* a, const u64* e, const u64* s_R, const u64* sp,

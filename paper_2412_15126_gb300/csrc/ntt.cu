@@ -33,7 +33,8 @@
 namespace {
 using namespace nttc;
 
-template <int LOG, bool INV, bool COL>
+// LIFT (forward column pass only): the input is the centred lift of one limb (rescale).
+template <int LOG, bool INV, bool COL, bool LIFT = false>
 __global__ void __launch_bounds__(256, (LOG <= 8 ? (COL ? RK_NTT_COL_BLOCKS : RK_NTT_ROW_BLOCKS) : 2)) k_ntt_pass(LimbSet s, int logn, int loga, int units, const PrimeConst* __restrict__ pc,
                                                   const u64* __restrict__ tw) {
     RK_KERNEL_PROLOGUE();
@@ -70,8 +71,20 @@ __global__ void __launch_bounds__(256, (LOG <= 8 ? (COL ? RK_NTT_COL_BLOCKS : RK
 
     if (!INV) {
         // load the strided set {t + P m}: coalesced over u (columns) or t (rows)
+        if (LIFT) {
+            // centred representative of the source residue x (mod lift_q), modulo q
+            const u64* lg = s.lift + (size_t)blockIdx.z * s.lift_stride + (size_t)blockIdx.x * units + u;
+            const u64 half = s.lift_q >> 1, qlm = s.lift_mod[limb];
 #pragma unroll
-        for (int m = 0; m < E; m++) x[m] = g[(size_t)(t + P * m) * gs];
+            for (int m = 0; m < E; m++) {
+                const u64 v = lg[(size_t)(t + P * m) * gs];
+                const u64 r = shoup_mul(v, 1, PC.one_shoup, q);
+                x[m] = v > half ? sub_mod(r, qlm, q) : r;
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < E; m++) x[m] = g[(size_t)(t + P * m) * gs];
+        }
         fwd_strided<LOG>(x, t, tw_, q, q2);
 #pragma unroll
         for (int m = 0; m < E; m++) sm[sidx(t + P * m)] = x[m];
@@ -122,13 +135,13 @@ __global__ void __launch_bounds__(256, (LOG <= 8 ? (COL ? RK_NTT_COL_BLOCKS : RK
     }
 }
 
-template <bool INV, bool COL>
+template <bool INV, bool COL, bool LIFT = false>
 void pass_launch(int LOG, dim3 grid, int threads, size_t smem, cudaStream_t st, const LimbSet& s, int logn, int loga,
                  int units, const PrimeConst* pc, const u64* tw) {
     switch (LOG) {
 #define RK_NTT_CASE(L)                                                                                        \
     case L:                                                                                                   \
-        rk_launch(k_ntt_pass<L, INV, COL>, grid, threads, smem, st, s, logn, loga, units, pc, tw);                   \
+        rk_launch(k_ntt_pass<L, INV, COL, LIFT>, grid, threads, smem, st, s, logn, loga, units, pc, tw);             \
         break;
         RK_NTT_CASE(5)
         RK_NTT_CASE(6)
@@ -141,14 +154,14 @@ void pass_launch(int LOG, dim3 grid, int threads, size_t smem, cudaStream_t st, 
     }
 }
 
-template <bool INV, bool COL>
+template <bool INV, bool COL, bool LIFT = false>
 void set_smem_attr() {
     const int bytes = 96 * 1024;
-    cudaFuncSetAttribute(k_ntt_pass<5, INV, COL>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    cudaFuncSetAttribute(k_ntt_pass<6, INV, COL>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    cudaFuncSetAttribute(k_ntt_pass<7, INV, COL>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    cudaFuncSetAttribute(k_ntt_pass<8, INV, COL>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    cudaFuncSetAttribute(k_ntt_pass<9, INV, COL>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_ntt_pass<5, INV, COL, LIFT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_ntt_pass<6, INV, COL, LIFT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_ntt_pass<7, INV, COL, LIFT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_ntt_pass<8, INV, COL, LIFT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_ntt_pass<9, INV, COL, LIFT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 // geometry of one pass: transforms of 2^LOG points, `count` of them per limb
@@ -185,6 +198,7 @@ PassGeom geom(int LOG, int count, const LimbSet& s, int sms, int forced = 0) {
 void ntt_init_attributes() {
     set_smem_attr<false, false>();
     set_smem_attr<false, true>();
+    set_smem_attr<false, true, true>();
     set_smem_attr<true, false>();
     set_smem_attr<true, true>();
 }
@@ -196,7 +210,10 @@ void launch_ntt_forward(const KernelEnv& env, const LimbSet& s, cudaStream_t st)
     const int logn = env.logn, loga = logn / 2, logb = logn - loga;
     const int sm = small_set(s);
     PassGeom c = geom(loga, 1 << logb, s, env.sms, env.tune ? env.tune->ntt_units[0][1][sm] : 0);
-    pass_launch<false, true>(loga, c.grid, c.threads, c.smem, st, s, logn, loga, c.units, env.pc, env.tw.psi);
+    if (s.lift)
+        pass_launch<false, true, true>(loga, c.grid, c.threads, c.smem, st, s, logn, loga, c.units, env.pc, env.tw.psi);
+    else
+        pass_launch<false, true>(loga, c.grid, c.threads, c.smem, st, s, logn, loga, c.units, env.pc, env.tw.psi);
     PassGeom r = geom(logb, 1 << loga, s, env.sms, env.tune ? env.tune->ntt_units[0][0][sm] : 0);
     pass_launch<false, false>(logb, r.grid, r.threads, r.smem, st, s, logn, loga, r.units, env.pc, env.tw.psi);
 }

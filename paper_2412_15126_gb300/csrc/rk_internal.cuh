@@ -52,6 +52,14 @@ struct LimbSet {
     // (same limb layout) instead of transforming base in place
     const u64* src = nullptr;
     size_t src_stride = 0;
+    // optional (rescale): a forward NTT's first pass reads, for polynomial z, the one
+    // coefficient-domain limb lift + z * lift_stride, residues modulo lift_q, and takes
+    // its centred representative modulo each limb's prime; lift_mod[t] = lift_q mod
+    // prime(t)
+    const u64* lift = nullptr;
+    size_t lift_stride = 0;
+    const u64* lift_mod = nullptr;
+    u64 lift_q = 0;
 };
 
 __host__ __device__ __forceinline__ int limb_prime(const LimbSet& s, int t) {
@@ -240,6 +248,7 @@ void ev_mul_scalar(rk_ctx* c, const rk_ct* a, double v, rk_ct* out);        // o
 void ev_mul(rk_ctx* c, const rk_ct* a, const rk_ct* b, rk_ct* out);         // out at level-1
 void ev_mul_plain(rk_ctx* c, const rk_ct* a, uint32_t kind, uint32_t N, uint32_t Q, uint32_t n_real, rk_ct* out);
 void ev_rotate_many(rk_ctx* c, const rk_ct* a, const int* r, int k, rk_ct** outs);  // left rotations
+void ev_rotate_add(rk_ctx* c, const rk_ct* a, int r, rk_ct* out);               // a + (a <<< r)
 void ev_add_plain(rk_ctx* c, const rk_ct* a, uint32_t kind, uint32_t N, uint32_t Q, uint32_t n_real, rk_ct* out);
 void ev_lincomb(rk_ctx* c, const std::vector<const rk_ct*>& xs, const std::vector<double>& cs, rk_ct* out);  // out at level-1
 void ev_level_down(rk_ctx* c, const rk_ct* a, int target, rk_ct* out);
