@@ -135,9 +135,163 @@ __global__ void __launch_bounds__(256, (LOG <= 8 ? (COL ? RK_NTT_COL_BLOCKS : RK
     }
 }
 
+
+// Row pass for 256-point rows (n = 2^16 splits as 2^8 x 2^8): one warp a row, eight
+// residues a thread, three register phases joined by two warp-local shared-memory
+// exchanges (no block barrier):
+//   set A = {t + 32 m}                 spans 128, 64, 32   (twiddles shared by the row)
+//   set B = {32 (t / 4) + 4 m + t % 4} spans 16, 8, 4
+//   set C = {8 t + m}                  spans 2, 1          (16-byte global accesses)
+// Forward runs A, B, C and leaves from C reduced to [0, q); inverse runs C, B, A and
+// leaves from A in [0, 2q).  Half the registers of the two-set form, so twice the
+// resident warps.  Element x of a row sits in word x ^ ((x >> 3) & 15) of the row's
+// shared buffer: every set's half-warp accesses hit 16 distinct 8-byte bank pairs.
+__device__ __forceinline__ int row8_slot(int x) { return x ^ ((x >> 3) & 15); }
+__device__ __forceinline__ int row8_b(int t, int m) { return ((t >> 2) << 5) | (m << 2) | (t & 3); }
+
+template <bool INV>
+__global__ void __launch_bounds__(256, 4) k_ntt_row8(LimbSet s, int logn, int loga, const PrimeConst* __restrict__ pc,
+                                                   const u64* __restrict__ tw) {
+    RK_KERNEL_PROLOGUE();
+    extern __shared__ u64 sm[];
+    const int n = 1 << logn, B = 1 << (logn - loga);
+    const int limb = blockIdx.y;
+    if (s.skip_ds && limb < s.split && limb / s.skip_ds == (int)(blockIdx.z % s.skip_beta)) return;   // block-uniform
+    const int pid = limb_prime(s, limb);
+    const u64 q = pc[pid].q, q2 = 2 * q;
+    const int wi = threadIdx.x >> 5, t = threadIdx.x & 31;
+    const int rho = blockIdx.x * (blockDim.x >> 5) + wi;
+    u64* g = s.base + (size_t)blockIdx.z * s.poly_stride + (size_t)limb * n + (size_t)rho * B;
+    u64* row = sm + wi * 256;
+    const Twid tw_{tw + (size_t)pid * 2 * n, logn - 1, rho};
+    auto stage = [&](int v) { return twid_stage<8>(tw_, v); };
+    u64 x[8];
+    if (!INV) {
+#pragma unroll
+        for (int m = 0; m < 8; m++) x[m] = g[t + 32 * m];
+#pragma unroll
+        for (int v = 7; v >= 5; v--) {
+            const int h = 1 << (v - 5);
+            const ulonglong2* T = stage(v);
+#pragma unroll
+            for (int m = 0; m < 8; m++) {
+                if (m & h) continue;
+                u64 w, wsh;   // (t + 32 m) >> (v + 1) = m >> (v - 4)
+                twid_fetch(T + (m >> (v - 4)), w, wsh);
+                ct_bfly(x[m], x[m + h], w, wsh, q, q2);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < 8; m++) row[row8_slot(t + 32 * m)] = x[m];
+        __syncwarp();
+#pragma unroll
+        for (int m = 0; m < 8; m++) x[m] = row[row8_slot(row8_b(t, m))];
+#pragma unroll
+        for (int v = 4; v >= 2; v--) {
+            const int h = 1 << (v - 2);
+            const ulonglong2* T = stage(v) + ((t >> 2) << (4 - v));
+#pragma unroll
+            for (int m = 0; m < 8; m++) {
+                if (m & h) continue;
+                u64 w, wsh;   // row8_b(t, m) >> (v + 1) = ((t / 4) << (4 - v)) + (4 m >> (v + 1))
+                twid_fetch(T + ((m << 2) >> (v + 1)), w, wsh);
+                ct_bfly(x[m], x[m + h], w, wsh, q, q2);
+            }
+        }
+        // the slots written back were read above by this thread alone
+#pragma unroll
+        for (int m = 0; m < 8; m++) row[row8_slot(row8_b(t, m))] = x[m];
+        __syncwarp();
+#pragma unroll
+        for (int m = 0; m < 8; m++) x[m] = row[row8_slot(8 * t + m)];
+#pragma unroll
+        for (int v = 1; v >= 0; v--) {
+            const int h = 1 << v;
+            const ulonglong2* T = stage(v) + ((8 * t) >> (v + 1));
+#pragma unroll
+            for (int m = 0; m < 8; m++) {
+                if (m & h) continue;
+                u64 w, wsh;
+                twid_fetch(T + (m >> (v + 1)), w, wsh);
+                ct_bfly(x[m], x[m + h], w, wsh, q, q2);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < 8; m += 2) {
+            ulonglong2 pr;
+            pr.x = reduce_4q(x[m], q, q2);
+            pr.y = reduce_4q(x[m + 1], q, q2);
+            reinterpret_cast<ulonglong2*>(g + 8 * t)[m >> 1] = pr;
+        }
+    } else {
+        const u64* gin = s.src ? s.src + (size_t)blockIdx.z * s.src_stride + (size_t)limb * n + (size_t)rho * B : g;
+#pragma unroll
+        for (int m = 0; m < 8; m += 2) {
+            const ulonglong2 pr = reinterpret_cast<const ulonglong2*>(gin + 8 * t)[m >> 1];
+            x[m] = pr.x;
+            x[m + 1] = pr.y;
+        }
+#pragma unroll
+        for (int v = 0; v <= 1; v++) {
+            const int h = 1 << v;
+            const ulonglong2* T = stage(v) + ((8 * t) >> (v + 1));
+#pragma unroll
+            for (int m = 0; m < 8; m++) {
+                if (m & h) continue;
+                u64 w, wsh;
+                twid_fetch(T + (m >> (v + 1)), w, wsh);
+                gs_bfly(x[m], x[m + h], w, wsh, q, q2);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < 8; m++) row[row8_slot(8 * t + m)] = x[m];
+        __syncwarp();
+#pragma unroll
+        for (int m = 0; m < 8; m++) x[m] = row[row8_slot(row8_b(t, m))];
+#pragma unroll
+        for (int v = 2; v <= 4; v++) {
+            const int h = 1 << (v - 2);
+            const ulonglong2* T = stage(v) + ((t >> 2) << (4 - v));
+#pragma unroll
+            for (int m = 0; m < 8; m++) {
+                if (m & h) continue;
+                u64 w, wsh;
+                twid_fetch(T + ((m << 2) >> (v + 1)), w, wsh);
+                gs_bfly(x[m], x[m + h], w, wsh, q, q2);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < 8; m++) row[row8_slot(row8_b(t, m))] = x[m];
+        __syncwarp();
+#pragma unroll
+        for (int m = 0; m < 8; m++) x[m] = row[row8_slot(t + 32 * m)];
+#pragma unroll
+        for (int v = 5; v <= 7; v++) {
+            const int h = 1 << (v - 5);
+            const ulonglong2* T = stage(v);
+#pragma unroll
+            for (int m = 0; m < 8; m++) {
+                if (m & h) continue;
+                u64 w, wsh;
+                twid_fetch(T + (m >> (v - 4)), w, wsh);
+                gs_bfly(x[m], x[m + h], w, wsh, q, q2);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < 8; m++) g[t + 32 * m] = x[m];
+    }
+}
+
+// threads owning one transform of a pass
+constexpr int pass_threads(int LOG, bool COL) { return (!COL && LOG == 8) ? 32 : 1 << (LOG / 2); }
+
 template <bool INV, bool COL, bool LIFT = false>
 void pass_launch(int LOG, dim3 grid, int threads, size_t smem, cudaStream_t st, const LimbSet& s, int logn, int loga,
                  int units, const PrimeConst* pc, const u64* tw) {
+    if (!COL && LOG == 8) {
+        rk_launch(k_ntt_row8<INV>, grid, threads, smem, st, s, logn, loga, pc, tw);
+        return;
+    }
     switch (LOG) {
 #define RK_NTT_CASE(L)                                                                                        \
     case L:                                                                                                   \
@@ -174,8 +328,8 @@ struct PassGeom {
 bool small_set(const LimbSet& s) { return (long)s.n_limbs * s.n_polys < 16; }
 
 // forced > 0: that many transforms a block (autotuned), clamped to the valid range
-PassGeom geom(int LOG, int count, const LimbSet& s, int sms, int forced = 0) {
-    const int P = 1 << (LOG / 2);
+PassGeom geom(int LOG, bool COL, int count, const LimbSet& s, int sms, int forced = 0) {
+    const int P = pass_threads(LOG, COL);
     int units = std::min(256 / P, count);
     const long limbs = (long)s.n_limbs * s.n_polys;
     if (forced > 0) {
@@ -209,12 +363,12 @@ void launch_ntt_forward(const KernelEnv& env, const LimbSet& s, cudaStream_t st)
     ProfScope ps(env, KK_NTT_FWD, st, 2, 2.0 * limbs * 8.0 * env.n, limbs * (env.n / 2) * env.logn);
     const int logn = env.logn, loga = logn / 2, logb = logn - loga;
     const int sm = small_set(s);
-    PassGeom c = geom(loga, 1 << logb, s, env.sms, env.tune ? env.tune->ntt_units[0][1][sm] : 0);
+    PassGeom c = geom(loga, true, 1 << logb, s, env.sms, env.tune ? env.tune->ntt_units[0][1][sm] : 0);
     if (s.lift)
         pass_launch<false, true, true>(loga, c.grid, c.threads, c.smem, st, s, logn, loga, c.units, env.pc, env.tw.psi);
     else
         pass_launch<false, true>(loga, c.grid, c.threads, c.smem, st, s, logn, loga, c.units, env.pc, env.tw.psi);
-    PassGeom r = geom(logb, 1 << loga, s, env.sms, env.tune ? env.tune->ntt_units[0][0][sm] : 0);
+    PassGeom r = geom(logb, false, 1 << loga, s, env.sms, env.tune ? env.tune->ntt_units[0][0][sm] : 0);
     pass_launch<false, false>(logb, r.grid, r.threads, r.smem, st, s, logn, loga, r.units, env.pc, env.tw.psi);
 }
 
@@ -224,9 +378,9 @@ void launch_ntt_inverse(const KernelEnv& env, const LimbSet& s, cudaStream_t st)
                  (double)s.n_limbs * s.n_polys * (env.n / 2) * env.logn);
     const int logn = env.logn, loga = logn / 2, logb = logn - loga;
     const int sm = small_set(s);
-    PassGeom r = geom(logb, 1 << loga, s, env.sms, env.tune ? env.tune->ntt_units[1][0][sm] : 0);
+    PassGeom r = geom(logb, false, 1 << loga, s, env.sms, env.tune ? env.tune->ntt_units[1][0][sm] : 0);
     pass_launch<true, false>(logb, r.grid, r.threads, r.smem, st, s, logn, loga, r.units, env.pc, env.tw.ipsi);
-    PassGeom c = geom(loga, 1 << logb, s, env.sms, env.tune ? env.tune->ntt_units[1][1][sm] : 0);
+    PassGeom c = geom(loga, true, 1 << logb, s, env.sms, env.tune ? env.tune->ntt_units[1][1][sm] : 0);
     pass_launch<true, true>(loga, c.grid, c.threads, c.smem, st, s, logn, loga, c.units, env.pc, env.tw.ipsi);
 }
 
@@ -241,7 +395,7 @@ template <bool INV, bool COL>
 float time_pass(const KernelEnv& env, const LimbSet& s, int LOG, int count, int units, cudaStream_t st, cudaEvent_t e0,
                 cudaEvent_t e1, int reps) {
     const int logn = env.logn, loga = logn / 2;
-    PassGeom g = geom(LOG, count, s, env.sms, units);
+    PassGeom g = geom(LOG, COL, count, s, env.sms, units);
     const u64* tw = INV ? env.tw.ipsi : env.tw.psi;
     pass_launch<INV, COL>(LOG, g.grid, g.threads, g.smem, st, s, logn, loga, g.units, env.pc, tw);   // warm
     RK_CUDA(cudaEventRecord(e0, st));
@@ -275,7 +429,7 @@ void ntt_autotune(rk_ctx* c, std::vector<double>& report) {
             for (int inv = 0; inv < 2; inv++)
                 for (int col = 0; col < 2; col++) {
                     const int LOG = col ? loga : logb, count = 1 << (col ? logb : loga);
-                    const int P = 1 << (LOG / 2);
+                    const int P = pass_threads(LOG, col);
                     float best = 1e30f;
                     int best_u = 0;
                     for (int u = std::min(256 / P, count); u >= 1 && P * u >= 32; u >>= 1) {

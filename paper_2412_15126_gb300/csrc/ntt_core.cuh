@@ -50,14 +50,17 @@ struct Twid {
     int Sbase, rho;
 };
 
-// Twiddle of the butterflies at span 2^v whose lower element has in-transform index
-// x, given g = x >> (v + 1): one 16-byte load of the pair.
+// First (w, Shoup) pair of stage v of the transform (g = 0); a stage's loads then
+// differ from it by offsets the unrolled loops know at compile time.
 template <int LOG>
-__device__ __forceinline__ void twid_at(const Twid& tw, int v, int g, u64& w, u64& wsh) {
-    const int idx = (1 << (tw.Sbase - v)) + (tw.rho << (LOG - 1 - v)) + g;
-    const ulonglong2 p = __ldg(reinterpret_cast<const ulonglong2*>(tw.W) + idx);
-    w = p.x;
-    wsh = p.y;
+__device__ __forceinline__ const ulonglong2* twid_stage(const Twid& tw, int v) {
+    return reinterpret_cast<const ulonglong2*>(tw.W) + (1 << (tw.Sbase - v)) + (tw.rho << (LOG - 1 - v));
+}
+
+__device__ __forceinline__ void twid_fetch(const ulonglong2* p, u64& w, u64& wsh) {
+    const ulonglong2 pr = __ldg(p);
+    w = pr.x;
+    wsh = pr.y;
 }
 
 // forward stages with span 2^v >= P (v = LOG-1 .. LOGP) on the strided set
@@ -67,11 +70,12 @@ __device__ __forceinline__ void fwd_strided(u64 (&x)[Shape<LOG>::E], int t, cons
 #pragma unroll
     for (int v = LOG - 1; v >= S::LOGP; v--) {
         const int h = 1 << (v - S::LOGP);
+        const ulonglong2* T = twid_stage<LOG>(tw, v);
 #pragma unroll
         for (int m = 0; m < S::E; m++) {
             if (m & h) continue;
             u64 w, wsh;   // (t + P m) >> (v + 1) = m >> (v + 1 - LOGP): shared by the whole transform
-            twid_at<LOG>(tw, v, m >> (v + 1 - S::LOGP), w, wsh);
+            twid_fetch(T + (m >> (v + 1 - S::LOGP)), w, wsh);
             ct_bfly(x[m], x[m + h], w, wsh, q, q2);
         }
     }
@@ -84,11 +88,12 @@ __device__ __forceinline__ void fwd_contig(u64 (&x)[Shape<LOG>::E], int t, const
 #pragma unroll
     for (int v = S::LOGP - 1; v >= 0; v--) {
         const int h = 1 << v;
+        const ulonglong2* T = twid_stage<LOG>(tw, v) + (t << (S::LOGE - v - 1));
 #pragma unroll
         for (int m = 0; m < S::E; m++) {
             if (m & h) continue;
             u64 w, wsh;   // (t E + m) >> (v + 1) = t E / 2^(v+1) + (m >> (v + 1))
-            twid_at<LOG>(tw, v, (t << (S::LOGE - v - 1)) + (m >> (v + 1)), w, wsh);
+            twid_fetch(T + (m >> (v + 1)), w, wsh);
             ct_bfly(x[m], x[m + h], w, wsh, q, q2);
         }
     }
@@ -101,11 +106,12 @@ __device__ __forceinline__ void inv_contig(u64 (&x)[Shape<LOG>::E], int t, const
 #pragma unroll
     for (int v = 0; v < S::LOGP; v++) {
         const int h = 1 << v;
+        const ulonglong2* T = twid_stage<LOG>(tw, v) + (t << (S::LOGE - v - 1));
 #pragma unroll
         for (int m = 0; m < S::E; m++) {
             if (m & h) continue;
             u64 w, wsh;
-            twid_at<LOG>(tw, v, (t << (S::LOGE - v - 1)) + (m >> (v + 1)), w, wsh);
+            twid_fetch(T + (m >> (v + 1)), w, wsh);
             gs_bfly(x[m], x[m + h], w, wsh, q, q2);
         }
     }
@@ -118,11 +124,12 @@ __device__ __forceinline__ void inv_strided(u64 (&x)[Shape<LOG>::E], int t, cons
 #pragma unroll
     for (int v = S::LOGP; v < LOG; v++) {
         const int h = 1 << (v - S::LOGP);
+        const ulonglong2* T = twid_stage<LOG>(tw, v);
 #pragma unroll
         for (int m = 0; m < S::E; m++) {
             if (m & h) continue;
             u64 w, wsh;
-            twid_at<LOG>(tw, v, m >> (v + 1 - S::LOGP), w, wsh);
+            twid_fetch(T + (m >> (v + 1 - S::LOGP)), w, wsh);
             gs_bfly(x[m], x[m + h], w, wsh, q, q2);
         }
     }
