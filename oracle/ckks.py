@@ -433,7 +433,24 @@ def mod_down(P: Params, u: np.ndarray, level: int) -> np.ndarray:
     return mul_scalar_mod(sub_mod(u[: level + 1], w, q), pinv, q)
 
 
-def key_switch(P: Params, d: np.ndarray, key: SwitchKey, level: int, g: int | None = None):
+def mod_down_rescale(P: Params, u: np.ndarray, level: int) -> np.ndarray:
+    """(u - [u]_S) / S over Q_(l-1), S = P q_l, [u]_S by the centred fast conversion
+    from the basis {q_l, p_0 .. p_(alpha-1)}: a key switch's ModDown and the rescale
+    that follows it, in one rounding (u over Q_l P, limbs 0..l then the P limbs)."""
+    q = P.q[:level]
+    src_primes = [P.q[level]] + list(P.p)
+    src = np.concatenate([u[level:level + 1], u[level + 1:]])
+    w = fast_base_conv_centered(src, src_primes, q)
+    S = int(P.q[level])
+    for pk in P.p:
+        S *= int(pk)
+    sinv = [pow(S % int(qi), -1, int(qi)) for qi in q]
+    return mul_scalar_mod(sub_mod(u[:level], w, q), sinv, q)
+
+
+def key_switch_raw(P: Params, d: np.ndarray, key: SwitchKey, level: int, g: int | None = None):
+    """Inner products u_0, u_1 over Q_l P of the lifted digits of d (automorphism g
+    on the digits) with the switching key, before ModDown."""
     primes = P.qp(level)
     sel = list(range(level + 1)) + list(range(P.L + 1, P.L + 1 + P.alpha))
     beta = P.beta(level)
@@ -442,8 +459,11 @@ def key_switch(P: Params, d: np.ndarray, key: SwitchKey, level: int, g: int | No
         digits = np.stack([automorphism(dg, g, primes) for dg in digits])
     kb = np.ascontiguousarray(key.data[:beta, 0][:, sel])
     ka = np.ascontiguousarray(key.data[:beta, 1][:, sel])
-    u0 = ring_mac(digits, kb, primes)
-    u1 = ring_mac(digits, ka, primes)
+    return ring_mac(digits, kb, primes), ring_mac(digits, ka, primes)
+
+
+def key_switch(P: Params, d: np.ndarray, key: SwitchKey, level: int, g: int | None = None):
+    u0, u1 = key_switch_raw(P, d, key, level, g)
     return mod_down(P, u0, level), mod_down(P, u1, level)
 
 
@@ -498,8 +518,18 @@ def mul(P: Params, keys: Keys, x: Ct, y: Ct) -> Ct:
     d0 = ring_mul(x.c[0], y.c[0], q)
     d1 = ring_mac(np.stack([x.c[0], x.c[1]]), np.stack([y.c[1], y.c[0]]), q)
     d2 = ring_mul(x.c[1], y.c[1], q)
-    k0, k1 = key_switch(P, d2, keys.rlk, lvl)
-    return rescale(P, Ct(np.stack([add_mod(d0, k0, q), add_mod(d1, k1, q)]), lvl))
+    # relinearisation and rescale in one rounding: (P d_i + u_i) / (P q_l)
+    u0, u1 = key_switch_raw(P, d2, keys.rlk, lvl)
+    Pprod = 1
+    for pk in P.p:
+        Pprod *= int(pk)
+    pm = [Pprod % int(qi) for qi in q]
+    out = []
+    for d, u in ((d0, u0), (d1, u1)):
+        U = u.copy()
+        U[: lvl + 1] = add_mod(u[: lvl + 1], mul_scalar_mod(d, pm, q), q)
+        out.append(mod_down_rescale(P, U, lvl))
+    return Ct(np.stack(out), lvl - 1)
 
 
 def scalar_scale(P: Params, level: int) -> float:

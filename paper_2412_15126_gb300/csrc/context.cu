@@ -305,6 +305,39 @@ void ctx_build(rk_ctx* c, const rk_params* p, int device, void* stream) {
             blk[2 * (L + 1) + i] = q[l] % q[i];
         }
     }
+    // fused ModDown + rescale blocks
+    const size_t A1 = (size_t)A + 1, rs_stride = 2 * A1 + A1 * (L + 1) + 3 * (size_t)(L + 1);
+    const size_t mr_off = conv.size();
+    conv.resize(mr_off + (size_t)(L + 1) * rs_stride, 0);
+    for (int l = 1; l <= L; l++) {
+        u64* blk = conv.data() + mr_off + (size_t)l * rs_stride;
+        std::vector<u64> src(1, q[l]);
+        for (int k = 0; k < A; k++) src.push_back(sp[k]);
+        for (size_t k = 0; k < A1; k++) {
+            const u64 sk = src[k];
+            u64 rest = 1 % sk;   // S / s_k mod s_k
+            for (size_t k2 = 0; k2 < A1; k2++)
+                if (k2 != k) rest = h_mulmod(rest, src[k2] % sk, sk);
+            const u64 inv = h_invmod(rest, sk);
+            blk[k] = inv;
+            blk[A1 + k] = shoup_of(inv, sk);
+            for (int i = 0; i < l; i++) {
+                u64 v = 1 % q[i];
+                for (size_t k2 = 0; k2 < A1; k2++)
+                    if (k2 != k) v = h_mulmod(v, src[k2] % q[i], q[i]);
+                blk[2 * A1 + k * (L + 1) + i] = h_mulmod(v, c->h_pc[i].r_mod, q[i]);
+            }
+        }
+        u64* smod = blk + 2 * A1 + A1 * (L + 1);
+        for (int i = 0; i < l; i++) {
+            u64 v = 1 % q[i];
+            for (size_t k = 0; k < A1; k++) v = h_mulmod(v, src[k] % q[i], q[i]);
+            smod[i] = v;
+            const u64 inv = h_invmod(v, q[i]);
+            smod[(L + 1) + i] = inv;
+            smod[2 * (L + 1) + i] = shoup_of(inv, q[i]);
+        }
+    }
     RK_CUDA(cudaMalloc((void**)&c->d_conv, conv.size() * 8));
     RK_CUDA(cudaMemcpy(c->d_conv, conv.data(), conv.size() * 8, cudaMemcpyHostToDevice));
 
@@ -323,6 +356,8 @@ void ctx_build(rk_ctx* c, const rk_params* p, int device, void* stream) {
     e.conv.moddown = c->d_conv + md_off;
     e.conv.pinv = c->d_conv + pi_off;
     e.conv.rescale = c->d_conv + rs_off;
+    e.conv.mdrs = c->d_conv + mr_off;
+    e.conv.mdrs_stride = rs_stride;
     e.prof = &c->prof;
     e.tune = &c->tune;
     int sms = 0;

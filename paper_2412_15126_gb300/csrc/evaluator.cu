@@ -540,11 +540,22 @@ void ev_mul(rk_ctx* c, const rk_ct* a, const rk_ct* b, rk_ct* out) {
     ks_lift(c, S.d + 2 * pl, 3 * pl, l, B);
     if (!c->ks_fused) ks_lift_ext(c, S.d + 2 * pl, 3 * pl, l, B);
     ks_inner(c, c->rlk.data, l, 0, S.d + 2 * pl, 3 * pl, B, !c->ks_fused);
-    ks_moddown(c, l, S.d, 0, S.d + pl, 3 * pl, out->data, c->poly_stride(), B);
-    out->level = l;
+    // ModDown and rescale in one rounding: (P d_p + u_p) / (q_l P) over q_0 .. q_(l-1)
+    const size_t n = c->n;
+    const int QP = l + 1 + c->alpha;
+    const u64 ql = c->primes[l];
+    u64 pm = 1 % ql;
+    for (int k = 0; k < c->alpha; k++) pm = h_mulmod(pm, c->primes[c->L + 1 + k] % ql, ql);
+    launch_ks_add_pd(c->env, S.u, S.d, l, pm, shoup_companion(pm, ql), c->stream, B);
+    launch_ntt_inverse(c->env, LimbSet{S.u + (size_t)l * n, (size_t)QP * n, 2 * B, c->alpha + 1, 1, l, c->L + 1}, c->stream);
+    launch_moddown_rs_conv(c->env, S.u, S.w, l, c->stream, 2 * B);
+    launch_ntt_forward(c->env, ls_q(S.w, (size_t)l * n, 2 * B, l), c->stream);
+    launch_ks_combine_rs(c->env, out->data, c->poly_stride(), S.u, S.w, S.d, l, c->stream, B);
+    out->level = l - 1;
     copy_meta(out, a);
+    c->n_ks += (uint64_t)B;
     c->n_mul += (uint64_t)B;
-    ev_rescale_inplace(c, out);
+    c->n_rescale++;
 }
 
 // Times one top-level rotation with the staged key switching and with the fused

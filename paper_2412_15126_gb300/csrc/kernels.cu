@@ -226,20 +226,25 @@ void launch_modup(const KernelEnv& env, const u64* x, const u64* x_eval, size_t 
 
 // ModDown conversion of the P part of u ([2][l+1+alpha][n], P limbs already in the
 // coefficient domain) to w = [2][l+1][n]; CONV_EL coefficients a thread.
-template <int A>
+// RS (a product's ModDown fused with its rescale): the sources are limbs l .. l+alpha
+// (q_l then the P limbs, coefficient domain), S = q_l P, and w = [2][l][n].
+template <int A, bool RS>
 __global__ void __launch_bounds__(TPB) k_moddown_conv(const u64* __restrict__ u, u64* __restrict__ w, int level, int L,
                                                       ConvTables cv, int n, const PrimeConst* __restrict__ pc) {
     RK_KERNEL_PROLOGUE();
-    __shared__ u64 s_c[A * RK_MAX_PRIMES];      // (P/p_k) R mod q_i, [k][i]
+    constexpr int NS = A + (RS ? 1 : 0);
+    __shared__ u64 s_c[NS * RK_MAX_PRIMES];     // (S/s_k) R mod q_i, [k][i]
     __shared__ u64 s_q[RK_MAX_PRIMES], s_qinv[RK_MAX_PRIMES], s_pm[RK_MAX_PRIMES];
     const int c = blockIdx.y;
-    const u64* cm = cv.moddown + 2 * A;
-    const u64* pmod = cm + (size_t)A * (L + 1);
-    for (int idx = threadIdx.x; idx < A * (level + 1); idx += TPB) {
-        const int kk = idx / (level + 1), i = idx - kk * (level + 1);
+    const int nt = RS ? level : level + 1;   // target limbs
+    const u64* blk = RS ? cv.mdrs + (size_t)level * cv.mdrs_stride : cv.moddown;
+    const u64* cm = blk + 2 * NS;
+    const u64* pmod = cm + (size_t)NS * (L + 1);
+    for (int idx = threadIdx.x; idx < NS * nt; idx += TPB) {
+        const int kk = idx / nt, i = idx - kk * nt;
         s_c[kk * RK_MAX_PRIMES + i] = cm[(size_t)kk * (L + 1) + i];
     }
-    for (int i = threadIdx.x; i <= level; i += TPB) {
+    for (int i = threadIdx.x; i < nt; i += TPB) {
         s_q[i] = pc[i].q;
         s_qinv[i] = pc[i].qinv;
         s_pm[i] = pmod[i];
@@ -247,27 +252,28 @@ __global__ void __launch_bounds__(TPB) k_moddown_conv(const u64* __restrict__ u,
     __syncthreads();
     const int ul = level + 1 + A;
     const int k0 = blockIdx.x * (TPB * CONV_EL) + threadIdx.x;
-    const u64* up = u + (size_t)c * ul * n + (size_t)(level + 1) * n + k0;
-    // centred terms: y_k in (-p_k/2, p_k/2]; a negative term contributes y_k (P/p_k) - P
-    u64 y[CONV_EL][A];
+    const u64* up = u + (size_t)c * ul * n + (size_t)(RS ? level : level + 1) * n + k0;
+    // centred terms: y_k in (-s_k/2, s_k/2]; a negative term contributes y_k (S/s_k) - S
+    u64 y[CONV_EL][NS];
     int nneg[CONV_EL];
 #pragma unroll
     for (int e = 0; e < CONV_EL; e++) nneg[e] = 0;
 #pragma unroll
-    for (int kk = 0; kk < A; kk++) {
-        const u64 pk = pc[L + 1 + kk].q, iv = cv.moddown[kk], ivsh = cv.moddown[A + kk];
+    for (int kk = 0; kk < NS; kk++) {
+        const u64 sk = RS ? (kk == 0 ? pc[level].q : pc[L + kk].q) : pc[L + 1 + kk].q;
+        const u64 iv = blk[kk], ivsh = blk[NS + kk];
 #pragma unroll
         for (int e = 0; e < CONV_EL; e++) {
-            y[e][kk] = shoup_mul(up[(size_t)kk * n + e * TPB], iv, ivsh, pk);
-            nneg[e] += y[e][kk] > (pk >> 1) ? 1 : 0;
+            y[e][kk] = shoup_mul(up[(size_t)kk * n + e * TPB], iv, ivsh, sk);
+            nneg[e] += y[e][kk] > (sk >> 1) ? 1 : 0;
         }
     }
-    u64* out = w + (size_t)c * (level + 1) * n + k0;
-    for (int i = 0; i <= level; i++) {
+    u64* out = w + (size_t)c * nt * n + k0;
+    for (int i = 0; i < nt; i++) {
         const u64 q = s_q[i], qinv = s_qinv[i], pm = s_pm[i];
         Acc128 acc[CONV_EL];
 #pragma unroll
-        for (int kk = 0; kk < A; kk++) {
+        for (int kk = 0; kk < NS; kk++) {
             const u64 cst = s_c[kk * RK_MAX_PRIMES + i];
 #pragma unroll
             for (int e = 0; e < CONV_EL; e++) acc[e].mac(y[e][kk], cst);
@@ -281,18 +287,75 @@ __global__ void __launch_bounds__(TPB) k_moddown_conv(const u64* __restrict__ u,
     }
 }
 
-void launch_moddown_conv(const KernelEnv& env, const u64* u, u64* w, int level, cudaStream_t st, int polys) {
-    ProfScope pf(env, KK_MODDOWN, st, 1, polys * (1.0 * env.alpha + (level + 1)) * 8.0 * env.n, 1.0 * polys * (level + 1) * env.alpha * env.n);
+template <bool RS>
+static void moddown_conv_launch(const KernelEnv& env, const u64* u, u64* w, int level, cudaStream_t st, int polys) {
+    const int nt = RS ? level : level + 1, ns = env.alpha + (RS ? 1 : 0);
+    ProfScope pf(env, KK_MODDOWN, st, 1, polys * (1.0 * ns + nt) * 8.0 * env.n, 1.0 * polys * nt * ns * env.n);
     dim3 g(env.n / (TPB * CONV_EL), polys);
     switch (env.alpha) {
 #define RK_MD_CASE(A)                                                                               \
     case A:                                                                                         \
-        rk_launch(k_moddown_conv<A>, g, TPB, 0, st, u, w, level, env.L, env.conv, env.n, env.pc);          \
+        rk_launch(k_moddown_conv<A, RS>, g, TPB, 0, st, u, w, level, env.L, env.conv, env.n, env.pc);      \
         break;
         RK_MD_CASE(1) RK_MD_CASE(2) RK_MD_CASE(3) RK_MD_CASE(4) RK_MD_CASE(5) RK_MD_CASE(6) RK_MD_CASE(7) RK_MD_CASE(8)
 #undef RK_MD_CASE
         default: throw rk_error(RK_EINVAL, "special prime count out of range");
     }
+}
+
+void launch_moddown_conv(const KernelEnv& env, const u64* u, u64* w, int level, cudaStream_t st, int polys) {
+    moddown_conv_launch<false>(env, u, w, level, st, polys);
+}
+
+void launch_moddown_rs_conv(const KernelEnv& env, const u64* u, u64* w, int level, cudaStream_t st, int polys) {
+    moddown_conv_launch<true>(env, u, w, level, st, polys);
+}
+
+// Limb l of a product's inner products gains P d (d the tensor's d_0 / d_1, evaluation
+// domain): u_c[l] += (P mod q_l) d_p[l], c = 2b + p.  grid (n/TPB, 1, 2B)
+__global__ void k_ks_add_pd(u64* u, const u64* d, int level, int alpha, u64 pm, u64 pm_sh, int n,
+                            const PrimeConst* __restrict__ pc) {
+    RK_KERNEL_PROLOGUE();
+    const int k = blockIdx.x * TPB + threadIdx.x, c = blockIdx.z;
+    const int b = c >> 1, p = c & 1;
+    const size_t pl = (size_t)(level + 1) * n;
+    const u64 q = pc[level].q;
+    u64* up = u + (size_t)c * (level + 1 + alpha) * n + (size_t)level * n + k;
+    const u64 dv = d[(size_t)b * 3 * pl + (size_t)p * pl + (size_t)level * n + k];
+    *up = add_mod(*up, shoup_mul(dv, pm, pm_sh, q), q);
+}
+
+void launch_ks_add_pd(const KernelEnv& env, u64* u, const u64* d, int level, u64 pm, u64 pm_sh, cudaStream_t st, int B) {
+    ProfScope pf(env, KK_KS_COMBINE, st, 1, 3.0 * 2 * B * 8.0 * env.n, 2.0 * B * env.n);
+    dim3 g(env.n / TPB, 1, 2 * B);
+    rk_launch(k_ks_add_pd, g, TPB, 0, st, u, d, level, env.alpha, pm, pm_sh, env.n, env.pc);
+}
+
+// Product output at level l-1: out_c[i] = (u_c[i] - w_c[i]) S^-1 + d_p[i] q_l^-1 (mod q_i),
+// i < l, S = q_l P: the relinearised product (d_0 + KS_0, d_1 + KS_1) divided by q_l
+// with one rounding.  grid (n/TPB, l, 2B)
+__global__ void k_ks_combine_rs(u64* out, size_t ps, const u64* __restrict__ u, const u64* __restrict__ w,
+                                const u64* __restrict__ d, int level, int L, int alpha, ConvTables cv, int n,
+                                const PrimeConst* __restrict__ pc) {
+    RK_KERNEL_PROLOGUE();
+    const int k = blockIdx.x * TPB + threadIdx.x, i = blockIdx.y, c = blockIdx.z;
+    const int b = c >> 1, p = c & 1;
+    const u64 q = pc[i].q;
+    const size_t pl = (size_t)(level + 1) * n;
+    const u64* sinv = cv.mdrs + (size_t)level * cv.mdrs_stride + 2 * (alpha + 1) + (size_t)(alpha + 1) * (L + 1) + (L + 1);
+    const u64* rs = cv.rescale + (size_t)level * 3 * (L + 1);
+    const u64 uv = u[(size_t)c * (level + 1 + alpha) * n + (size_t)i * n + k];
+    const u64 wv = w[(size_t)c * level * n + (size_t)i * n + k];
+    const u64 dv = d[(size_t)b * 3 * pl + (size_t)p * pl + (size_t)i * n + k];
+    const u64 a = shoup_mul(sub_mod(uv, wv, q), sinv[i], sinv[(L + 1) + i], q);
+    out[(size_t)c * ps + (size_t)i * n + k] = add_mod(a, shoup_mul(dv, rs[i], rs[(L + 1) + i], q), q);
+}
+
+void launch_ks_combine_rs(const KernelEnv& env, u64* out, size_t ps, const u64* u, const u64* w, const u64* d, int level,
+                          cudaStream_t st, int B) {
+    ProfScope pf(env, KK_KS_COMBINE, st, 1, 8.0 * B * level * 8.0 * env.n, 2.0 * B * level * env.n);
+    dim3 g(env.n / TPB, level, 2 * B);
+    rk_launch(k_ks_combine_rs, g, TPB, 0, st, out, ps, u, w, d, level, env.L, env.alpha, env.conv, env.n, env.pc);
 }
 
 // ===========================================================================

@@ -97,6 +97,11 @@ void launch_tensor(const KernelEnv& env, u64* d, const u64* x, const u64* y, int
 void launch_modup(const KernelEnv& env, const u64* x, const u64* x_eval, size_t eval_stride, u64* ext, size_t ext_stride,
                   int level, int beta, cudaStream_t st, int B = 1);
 void launch_moddown_conv(const KernelEnv& env, const u64* u, u64* w, int level, cudaStream_t st, int polys = 2);
+// a product's ModDown fused with its rescale (sources q_l and P, targets q_0 .. q_(l-1))
+void launch_moddown_rs_conv(const KernelEnv& env, const u64* u, u64* w, int level, cudaStream_t st, int polys);
+void launch_ks_add_pd(const KernelEnv& env, u64* u, const u64* d, int level, u64 pm, u64 pm_sh, cudaStream_t st, int B);
+void launch_ks_combine_rs(const KernelEnv& env, u64* out, size_t ps, const u64* u, const u64* w, const u64* d, int level,
+                          cudaStream_t st, int B);
 void launch_ks_inner(const KernelEnv& env, const u64* ext, size_t ext_stride, const u64* key, u64* u, int level, int beta,
                      u64 galois, cudaStream_t st, int B = 1);
 void launch_ks_combine(const KernelEnv& env, u64* out, size_t ps, const u64* base0, u64 galois0, const u64* base1, size_t bstride,

@@ -86,6 +86,13 @@ struct ConvTables {
     // Rescale for level l: block at rescale + l * 3 * (L+1):
     //   [0, L+1) q_l^-1 mod q_i; [L+1, 2(L+1)) Shoup; [2(L+1), 3(L+1)) q_l mod q_i
     const u64* rescale;
+    // ModDown fused with the rescale of a product at level l (S = q_l P, sources
+    // s_0 = q_l, s_(k+1) = p_k): block at mdrs + l * mdrs_stride:
+    //   [0, A+1) (S/s_k)^-1 mod s_k, [A+1, 2(A+1)) Shoup,
+    //   [2(A+1), 2(A+1) + (A+1)(L+1)) (S/s_k) mod q_i times R, row-major [k][i],
+    //   then (L+1) words S mod q_i, then (L+1) words S^-1 mod q_i and (L+1) Shoup
+    const u64* mdrs;
+    size_t mdrs_stride;
 };
 
 struct DevTables {

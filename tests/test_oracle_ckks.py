@@ -160,3 +160,44 @@ def test_key_switch_relation(setup):
         rhs = ckks.ring_mul(d, ckks.ring_mul(s, s, q), q)
         err = ckks.crt_centered(ckks.sub_mod(lhs, rhs, q), q)
         assert max(abs(int(e)) for e in err) < 2 ** 24
+
+
+def test_mod_down_rescale_divides_by_P_ql(setup):
+    """Fused ModDown + rescale: out = (u - X) / (P q_l) with X = u mod P q_l up to the
+    centred fast conversion, |X| <= (alpha + 1) P q_l / 2 (every centred term is at
+    most half its prime)."""
+    P, _, _, _, _, _, _ = setup
+    for lvl in (3, P.L):
+        primes = P.qp(lvl)
+        rng = np.random.default_rng(40 + lvl)
+        u = np.stack([rng.integers(0, q, P.n, dtype=np.uint64) for q in primes])
+        out = ckks.mod_down_rescale(P, u, lvl)
+        assert out.shape == (lvl, P.n)
+        S = math.prod(P.p) * int(P.q[lvl])
+        Q = math.prod(P.q[:lvl])
+        U = ckks.crt_centered(u, primes)
+        Y = ckks.crt_centered(out, P.q[:lvl])
+        for k in range(0, P.n, 23):
+            d = (int(Y[k]) * S - int(U[k])) % (Q * S)
+            if d > (Q * S) // 2:
+                d -= Q * S
+            assert abs(d) <= (P.alpha + 1) * S // 2
+
+
+def test_fused_product_matches_two_step(setup):
+    """The product's fused rounding and ModDown-then-rescale differ by a few units
+    of the last place: decryptions agree far below the noise."""
+    P, keys, z1, z2, c1, c2, _ = setup
+    lvl = c1.level
+    q = P.q[: lvl + 1]
+    d0 = ckks.ring_mul(c1.c[0], c2.c[0], q)
+    d1 = ckks.ring_mac(np.stack([c1.c[0], c1.c[1]]), np.stack([c2.c[1], c2.c[0]]), q)
+    d2 = ckks.ring_mul(c1.c[1], c2.c[1], q)
+    k0, k1 = ckks.key_switch(P, d2, keys.rlk, lvl)
+    two = ckks.rescale(P, ckks.Ct(np.stack([ckks.add_mod(d0, k0, q), ckks.add_mod(d1, k1, q)]), lvl))
+    fused = ckks.mul(P, keys, c1, c2)
+    for c in range(2):
+        a = ckks.crt_centered(two.c[c], P.q[:lvl])
+        b = ckks.crt_centered(fused.c[c], P.q[:lvl])
+        assert max(abs(int(x) - int(y)) for x, y in zip(a[::37], b[::37])) <= P.alpha + 2
+    assert np.max(np.abs(ckks.decrypt(P, keys, fused) - z1 * z2)) < 2.0 ** -20
