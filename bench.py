@@ -435,20 +435,26 @@ def ntt_roofline(prof, clk):
     per_launch = prof["ops"] / prof["launches"]
     avg_s = prof["ms"] * 1e-3 / prof["launches"]
     achieved = per_launch / avg_s / 1e9
-    ipb = None
+    ipb = hpb = None
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             rec = json.load(f)["ntt_fwd"]
         if rec["source_sha256"] == kernel_source_sha256("ntt_fwd"):   # counts of this very kernel
             ipb = rec["thread_instructions_per_butterfly"]
+            hpb = rec.get("fmaheavy_cycles_per_butterfly")
     except Exception:
         pass
-    peak = None
+    peak = mul_peak = None
     if ipb:
         peak = GB300_SMS * GB300_SCHEDULERS * 32 * GB300_MAX_SM_MHZ * 1e6 / ipb / 1e9
+    if hpb:
+        # the integer multiplier (FMA-heavy) pipe: one busy cycle of each of the 608
+        # sub-partitions per clock, hpb busy cycles a butterfly
+        mul_peak = GB300_SMS * GB300_SCHEDULERS * GB300_MAX_SM_MHZ * 1e6 / hpb / 1e9
     return {"bound": "alu", "kernel": "ntt_fwd (column + row pass)", "achieved": achieved, "peak": peak,
             "peak_kind": "derived: 152 SMs x 4 schedulers x 1 warp instruction/clock x 2070 MHz / instructions per "
                          "butterfly (ncu)", "unit": "Gbutterfly/s", "frac": (achieved / peak) if peak else None,
+            "multiplier_pipe_peak": mul_peak, "multiplier_pipe_frac": (achieved / mul_peak) if mul_peak else None,
             "traffic": committed_traffic("ntt_fwd", prof["bytes"] / prof["launches"]),
             "algorithmic_bytes_per_launch": prof["bytes"] / prof["launches"], "butterflies_per_launch": per_launch,
             "avg_launch_us": avg_s * 1e6, "launches": prof["launches"],
