@@ -167,10 +167,23 @@ rk_status rk_secret_import(rk_ctx* ctx, const int64_t* s, size_t n);
  * Errors: RK_EINVAL if words does not match, RK_ENOMEM. */
 rk_status rk_key_import(rk_ctx* ctx, uint32_t kind, uint64_t galois, const uint64_t* coeffs, size_t words);
 
+/* Import a seeded switching key: coeffs = [beta_L][L+1+alpha][n] words, the b_j
+ * parts only (coefficient domain, residues in [0, q)); every a_j is regenerated from
+ * `seed` by the key switch itself.  For digit j, prime index p (q_0..q_L, then
+ * p_0..p_{alpha-1}) and evaluation index i (the value at psi^(2 brev(i) + 1)), let x
+ * be element c = (j (L+1+alpha) + p) n + i of the SplitMix64 stream from `seed`
+ * (x = mix(seed + (c + 1) 0x9E3779B97F4A7C15), the generator's published
+ * definition); the high 64 bits of x q_p are a_j's evaluation there times 2^64,
+ * mod q_p.  Seeded keys halve key memory and the key switch's key traffic;
+ * rk_keygen makes them.  Errors: RK_EINVAL if words does not match, RK_EFORMAT,
+ * RK_ENOMEM. */
+rk_status rk_key_import_seeded(rk_ctx* ctx, uint32_t kind, uint64_t galois, uint64_t seed, const uint64_t* coeffs,
+                               size_t words);
+
 /* Every switching key of the context (relinearisation, then Galois keys by element)
- * as one blob of little-endian 64-bit words: magic "RKKEYS01", log_n, L+1+alpha,
- * beta_L, the key count K, then K records [kind][galois][words][words of
- * rk_key_import's layout].  buf NULL: *len receives the size only; otherwise buf
+ * as one blob of little-endian 64-bit words: magic "RKKEYS02", log_n, L+1+alpha,
+ * beta_L, the key count K, then K records [kind][galois][seeded][seed][words][words
+ * of rk_key_import's layout, or of rk_key_import_seeded's when seeded is 1].  buf NULL: *len receives the size only; otherwise buf
  * (8-byte aligned, cap >= *len bytes) receives the blob.  The secret is not included.
  * Errors: RK_EINVAL (buffer too small or unaligned), RK_ECUDA. */
 rk_status rk_keys_export(rk_ctx* ctx, uint8_t* buf, size_t cap, size_t* len);

@@ -56,6 +56,7 @@ def lib():
             L.orc_root_of_unity.restype = ctypes.c_uint64
             L.orc_nega_forward.argtypes = [_u64p, ctypes.c_size_t, ctypes.c_uint64]
             L.orc_nega_inverse.argtypes = [_u64p, ctypes.c_size_t, ctypes.c_uint64]
+            L.orc_seeded_key_a.argtypes = [ctypes.c_uint64, ctypes.c_int, ctypes.c_int, _u64p, ctypes.c_int, ctypes.c_size_t, _u64p]
             L.orc_polymul_schoolbook.argtypes = [_u64p, _u64p, _u64p, ctypes.c_size_t, ctypes.c_uint64]
             L.orc_ring_mac.argtypes = [_u64p, ctypes.c_size_t, _u64p, ctypes.c_size_t, ctypes.c_int,
                                        _u64p, ctypes.c_int, ctypes.c_size_t, _u64p]

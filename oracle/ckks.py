@@ -299,8 +299,11 @@ class Ct:
 
 @dataclass
 class SwitchKey:
-    """Hybrid switching key: data[j][0] = b_j, data[j][1] = a_j over q_0..q_L, p_0..p_{alpha-1}."""
+    """Hybrid switching key: data[j][0] = b_j, data[j][1] = a_j over q_0..q_L, p_0..p_{alpha-1}.
+    seed: when not None, every a_j comes from the seeded generator (seeded_key_a), so
+    the key travels as its b part and the seed."""
     data: np.ndarray  # [beta_L][2][L+1+alpha][n]
+    seed: int | None = None
 
 
 @dataclass
@@ -337,8 +340,35 @@ def galois_right(r: int, n: int) -> int:
     return galois_left((n // 2 - r % (n // 2)) % (n // 2), n)
 
 
-def _switch_key(P: Params, smp: Sampler, s_all: np.ndarray, s_prime_all: np.ndarray) -> SwitchKey:
-    """Key that switches s' to s (Sec. 2.1 rotations / relinearisation)."""
+def _brev_perm(logn: int) -> np.ndarray:
+    k = np.arange(1 << logn)
+    r = np.zeros_like(k)
+    for b in range(logn):
+        r |= ((k >> b) & 1) << (logn - 1 - b)
+    return r
+
+
+def seeded_key_a(P: Params, seed: int, j: int) -> np.ndarray:
+    """a_j of a seeded switching key, coefficient domain over q_0..q_L, p_0..: the
+    generator (SplitMix64, see the C core) gives a_j 2^64 mod q_p at evaluation index i,
+    the evaluation at psi^(2 brev(i) + 1) (psi the first c^((q-1)/2n), c = 2, 3, ..., of
+    order 2n); the coefficients are the negacyclic inverse transform of those values."""
+    primes = P.qp(P.L)
+    T = len(primes)
+    ar = np.empty((T, P.n), dtype=np.uint64)
+    _lib.lib().orc_seeded_key_a(int(seed) & (2**64 - 1), j, T, ptr(u64(primes)), T, P.n, ptr(ar))
+    rinv = [pow(pow(2, 64, int(q)), -1, int(q)) for q in primes]
+    a_eval = mul_scalar_mod(ar, rinv, primes)
+    logn = P.n.bit_length() - 1
+    a = np.ascontiguousarray(a_eval[:, _brev_perm(logn)])   # natural order: index m <-> psi^(2m + 1)
+    for p, q in enumerate(primes):
+        _lib.lib().orc_nega_inverse(ptr(a[p]), P.n, int(q))
+    return a
+
+
+def _switch_key(P: Params, smp: Sampler, s_all: np.ndarray, s_prime_all: np.ndarray, seed: int | None = None) -> SwitchKey:
+    """Key that switches s' to s (Sec. 2.1 rotations / relinearisation); with a seed,
+    the a parts come from the seeded generator."""
     primes = P.qp(P.L)
     nq = P.L + 1
     Pprod = 1
@@ -348,7 +378,7 @@ def _switch_key(P: Params, smp: Sampler, s_all: np.ndarray, s_prime_all: np.ndar
     data = np.empty((beta, 2, len(primes), P.n), dtype=np.uint64)
     for j in range(beta):
         lo, hi = j * P.dsize, min((j + 1) * P.dsize, nq)
-        a = smp.uniform(primes, P.n)
+        a = smp.uniform(primes, P.n) if seed is None else seeded_key_a(P, seed, j)
         e = to_residues(smp.gaussian(P.n), primes)
         b = sub_mod(e, ring_mul(a, s_all, primes), primes)
         gadget = np.zeros(len(primes), dtype=np.uint64)   # [P * E_j] mod each prime
@@ -357,10 +387,17 @@ def _switch_key(P: Params, smp: Sampler, s_all: np.ndarray, s_prime_all: np.ndar
         b = add_mod(b, mul_scalar_mod(s_prime_all, gadget, primes), primes)
         data[j, 0] = b
         data[j, 1] = a
-    return SwitchKey(data)
+    return SwitchKey(data, seed)
 
 
-def keygen(P: Params, seed: int, galois_elts=()) -> Keys:
+def _key_seed(seed: int, which: int) -> int:
+    """Seed of one switching key's a parts (which: 1 relinearisation, else the Galois element)."""
+    return (int(seed) * 0x100000001B3 + 0x51ED * int(which)) % (1 << 64)
+
+
+def keygen(P: Params, seed: int, galois_elts=(), seeded: bool = True) -> Keys:
+    """Secret, public key, relinearisation and Galois keys; switching keys take their
+    a parts from the seeded generator unless seeded is False."""
     smp = Sampler(seed)
     s = smp.ternary(P.n)
     primes = P.qp(P.L)
@@ -370,21 +407,22 @@ def keygen(P: Params, seed: int, galois_elts=()) -> Keys:
     e = to_residues(smp.gaussian(P.n), qL)
     pk = np.stack([sub_mod(e, ring_mul(a, s_all[: P.L + 1], qL), qL), a])
     s2 = ring_mul(s_all, s_all, primes)
-    rlk = _switch_key(P, smp, s_all, s2)
+    ks = (lambda w: _key_seed(seed, w)) if seeded else (lambda w: None)
+    rlk = _switch_key(P, smp, s_all, s2, ks(1))
     keys = Keys(s=s, pk=pk, rlk=rlk)
     for g in galois_elts:
-        keys.gal[int(g)] = _switch_key(P, smp, s_all, automorphism(s_all, int(g), primes))
+        keys.gal[int(g)] = _switch_key(P, smp, s_all, automorphism(s_all, int(g), primes), ks(int(g)))
     return keys
 
 
-def add_galois_keys(P: Params, keys: Keys, seed: int, galois_elts) -> None:
+def add_galois_keys(P: Params, keys: Keys, seed: int, galois_elts, seeded: bool = True) -> None:
     smp = Sampler(seed)
     primes = P.qp(P.L)
     s_all = to_residues(keys.s, primes)
     for g in galois_elts:
         g = int(g)
         if g not in keys.gal:
-            keys.gal[g] = _switch_key(P, smp, s_all, automorphism(s_all, g, primes))
+            keys.gal[g] = _switch_key(P, smp, s_all, automorphism(s_all, g, primes), _key_seed(seed, g) if seeded else None)
 
 
 def encrypt(P: Params, keys: Keys, z, seed: int, level: int | None = None) -> Ct:

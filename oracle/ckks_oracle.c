@@ -251,3 +251,29 @@ void orc_fast_base_conv_centered(const uint64_t *in, size_t n, const uint64_t *s
     }
     free(dhat_inv);
 }
+
+/* Seeded uniform half of a switching key.  SplitMix64 (Steele, Lea and Flood,
+ * "Fast splittable pseudorandom number generators", 2014), from its published
+ * definition: the state advances by the odd constant GAMMA and each output is the
+ * state passed through the generator's mixing function, so element c of the
+ * stream from seed s is mix(s + (c + 1) GAMMA).  Word (p, i) of digit j -- prime
+ * index p in q_0..q_L, p_0..p_{alpha-1} (T of them), evaluation index i -- is
+ * element (j T + p) n + i, taken into [0, q_p) as the high word of x q_p.  The
+ * value is the Montgomery form a 2^64 mod q_p of the key's a at that evaluation. */
+static uint64_t sm64_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+void orc_seeded_key_a(uint64_t seed, int j, int T, const uint64_t *primes, int np, size_t n, uint64_t *out) {
+    const uint64_t gamma = 0x9E3779B97F4A7C15ull;
+#pragma omp parallel for
+    for (int p = 0; p < np; p++) {
+        for (size_t i = 0; i < n; i++) {
+            const uint64_t c = ((uint64_t)j * (uint64_t)T + (uint64_t)p) * (uint64_t)n + i;
+            const uint64_t x = sm64_mix(seed + (c + 1) * gamma);
+            out[(size_t)p * n + i] = (uint64_t)(((u128)x * primes[p]) >> 64);
+        }
+    }
+}

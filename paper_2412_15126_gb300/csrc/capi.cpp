@@ -237,6 +237,16 @@ rk_status rk_key_import(rk_ctx* ctx, uint32_t kind, uint64_t galois, const uint6
     });
 }
 
+rk_status rk_key_import_seeded(rk_ctx* ctx, uint32_t kind, uint64_t galois, uint64_t seed, const uint64_t* coeffs, size_t words) {
+    return guard([&] {
+        need(ctx, "ctx");
+        need(coeffs, "coeffs");
+        set_device(ctx);
+        key_import(ctx, kind, galois, coeffs, words, true, seed);
+        check_launch();
+    });
+}
+
 uint64_t rk_galois_left(const rk_ctx* ctx, int32_t r) { return ctx ? galois_left(ctx, r) : 0; }
 
 rk_status rk_encoding_import(rk_ctx* ctx, uint32_t kind, uint32_t N, uint32_t Q, uint32_t n_real, const double* u, size_t n) {
@@ -535,8 +545,9 @@ rk_status rk_sort_batch(rk_ctx* ctx, const rk_ct* const* in, size_t count, uint3
 
 // ---- key set blob: little-endian u64 words ----
 //   magic, log_n, n_primes (L+1+alpha), beta_L, K, then K records
-//   [kind][galois][words][words x u64 in rk_key_import's layout]
-static const uint64_t kKeysMagic = 0x31305359454b4b52ull;   // "RKKEYS01"
+//   [kind][galois][seeded][seed][words][words x u64 in rk_key_import's layout, or
+//   rk_key_import_seeded's when seeded]
+static const uint64_t kKeysMagic = 0x32305359454b4b52ull;   // "RKKEYS02"
 
 rk_status rk_comparator_import(rk_ctx* ctx, const double* coeffs, size_t count) {
     return guard([&] {
@@ -554,9 +565,11 @@ rk_status rk_keys_export(rk_ctx* ctx, uint8_t* buf, size_t cap, size_t* len) {
         need(ctx, "ctx");
         need(len, "len");
         set_device(ctx);
-        const size_t words = (size_t)ctx->beta(ctx->L) * 2 * ctx->n_primes * ctx->n;
-        const size_t K = (ctx->rlk.data ? 1 : 0) + ctx->gal.size();
-        const size_t total = 8 * (5 + K * (3 + words));
+        std::vector<std::pair<std::pair<uint64_t, uint64_t>, const SwitchKeyDev*>> keys;
+        if (ctx->rlk.data) keys.push_back({{RK_KEY_RELIN, 0}, &ctx->rlk});
+        for (auto& kv : ctx->gal) keys.push_back({{RK_KEY_GALOIS, kv.first}, &kv.second});
+        size_t total = 8 * 5;
+        for (auto& k : keys) total += 8 * (5 + key_words(ctx, *k.second));
         *len = total;
         if (!buf) return;
         RK_REQUIRE(cap >= total, RK_EINVAL, "buffer too small for the key set");
@@ -566,17 +579,18 @@ rk_status rk_keys_export(rk_ctx* ctx, uint8_t* buf, size_t cap, size_t* len) {
         w[1] = (uint64_t)ctx->log_n;
         w[2] = (uint64_t)ctx->n_primes;
         w[3] = (uint64_t)ctx->beta(ctx->L);
-        w[4] = K;
+        w[4] = keys.size();
         size_t at = 5;
-        auto put = [&](uint64_t kind, uint64_t g, const u64* key) {
-            w[at] = kind;
-            w[at + 1] = g;
-            w[at + 2] = words;
-            key_export(ctx, key, reinterpret_cast<u64*>(w + at + 3));
-            at += 3 + words;
-        };
-        if (ctx->rlk.data) put(RK_KEY_RELIN, 0, ctx->rlk.data);
-        for (auto& kv : ctx->gal) put(RK_KEY_GALOIS, kv.first, kv.second.data);
+        for (auto& k : keys) {
+            const size_t words = key_words(ctx, *k.second);
+            w[at] = k.first.first;
+            w[at + 1] = k.first.second;
+            w[at + 2] = k.second->seeded ? 1 : 0;
+            w[at + 3] = k.second->seed;
+            w[at + 4] = words;
+            key_export(ctx, *k.second, reinterpret_cast<u64*>(w + at + 5));
+            at += 5 + words;
+        }
     });
 }
 
@@ -594,9 +608,10 @@ rk_status rk_keys_import(rk_ctx* ctx, const uint8_t* buf, size_t len) {
                    RK_EFORMAT, "key set blob: parameters differ from the context's");
         size_t at = 5;
         for (uint64_t k = 0; k < w[4]; k++) {
-            RK_REQUIRE(at + 3 <= nw && at + 3 + w[at + 2] <= nw, RK_EFORMAT, "key set blob: truncated");
-            key_import(ctx, (uint32_t)w[at], w[at + 1], w + at + 3, (size_t)w[at + 2]);
-            at += 3 + (size_t)w[at + 2];
+            RK_REQUIRE(at + 5 <= nw && at + 5 + w[at + 4] <= nw, RK_EFORMAT, "key set blob: truncated");
+            RK_REQUIRE(w[at + 2] <= 1, RK_EFORMAT, "key set blob: bad seeded flag");
+            key_import(ctx, (uint32_t)w[at], w[at + 1], w + at + 5, (size_t)w[at + 4], w[at + 2] == 1, w[at + 3]);
+            at += 5 + (size_t)w[at + 4];
         }
     });
 }

@@ -415,7 +415,7 @@ static int ks_group(const rk_ctx* c, int l, int B) {
 // Inner product of the lifted input with `key` (automorphism `galois` on the lifted
 // digits) into S.u [B][2][l+1+alpha][n].  `lifted` says whether S.ext already holds
 // every lifted digit (hoisted rotations); otherwise the fused path lifts group by group.
-static void ks_inner(rk_ctx* c, const u64* key, int l, u64 galois, const u64* d_eval, size_t d_stride, int B, bool lifted) {
+static void ks_inner(rk_ctx* c, KeyRef key, int l, u64 galois, const u64* d_eval, size_t d_stride, int B, bool lifted) {
     Scratch S = scratch_layout(c);
     const int QP = l + 1 + c->alpha, beta = c->beta(l);
     const size_t es = (size_t)QP * c->n;
@@ -495,7 +495,7 @@ void ev_rotate_many(rk_ctx* c, const rk_ct* a, const int* r, int k, rk_ct** outs
             ev_copy(c, a, outs[i]);
             continue;
         }
-        ks_inner(c, c->gal[g].data, l, g, d, 2 * ps, a->B, lifted);
+        ks_inner(c, c->gal[g].ref(), l, g, d, 2 * ps, a->B, lifted);
         ks_moddown(c, l, a->data, g, nullptr, 2 * ps, outs[i]->data, ps, a->B);
         outs[i]->level = l;
         copy_meta(outs[i], a);
@@ -520,7 +520,7 @@ void ev_rotate_add(rk_ctx* c, const rk_ct* a, int r, rk_ct* out) {
     const u64* d = a->data + ps;
     ks_lift(c, d, 2 * ps, l, a->B);
     ks_lift_ext(c, d, 2 * ps, l, a->B);
-    ks_inner(c, c->gal[g].data, l, g, d, 2 * ps, a->B, true);
+    ks_inner(c, c->gal[g].ref(), l, g, d, 2 * ps, a->B, true);
     ks_moddown(c, l, a->data, g, nullptr, 2 * ps, out->data, ps, a->B, a->data);
     out->level = l;
     copy_meta(out, a);
@@ -539,7 +539,7 @@ void ev_mul(rk_ctx* c, const rk_ct* a, const rk_ct* b, rk_ct* out) {
     launch_tensor(c->env, S.d, a->data, b->data, l + 1, c->poly_stride(), c->stream, B);
     ks_lift(c, S.d + 2 * pl, 3 * pl, l, B);
     if (!c->ks_fused) ks_lift_ext(c, S.d + 2 * pl, 3 * pl, l, B);
-    ks_inner(c, c->rlk.data, l, 0, S.d + 2 * pl, 3 * pl, B, !c->ks_fused);
+    ks_inner(c, c->rlk.ref(), l, 0, S.d + 2 * pl, 3 * pl, B, !c->ks_fused);
     // ModDown and rescale in one rounding: (P d_p + u_p) / (q_l P) over q_0 .. q_(l-1)
     const size_t n = c->n;
     const int QP = l + 1 + c->alpha;
@@ -660,15 +660,18 @@ static void make_pk(rk_ctx* c) {
     RK_CUDA(cudaStreamSynchronize(c->stream));
 }
 
-// Switching key from s' (evaluation domain, normal form, all primes, in sp) to s.
-static u64* make_switch_key(rk_ctx* c, const u64* sp, u64 stream_id) {
+// Switching key from s' (evaluation domain, normal form, all primes, in sp) to s.  The
+// a parts are seeded: only b_j is stored, a_j is regenerated by the key switch.
+static SwitchKeyDev make_switch_key(rk_ctx* c, const u64* sp, u64 stream_id) {
     const int NP = c->n_primes, L = c->L, DS = c->dsize, BL = c->beta(L);
     const size_t n = c->n;
-    u64* buf = nullptr;
-    cudaError_t err = cudaMalloc((void**)&buf, (size_t)BL * 2 * NP * n * 8);
+    SwitchKeyDev key;
+    key.seeded = true;
+    key.seed = HostRng::mix(c->seed ^ HostRng::mix(stream_id + 0x5EED0000ull));
+    cudaError_t err = cudaMalloc((void**)&key.data, (size_t)BL * NP * n * 8);
     if (err != cudaSuccess) throw rk_error(RK_ENOMEM, "switching key allocation failed");
     Scratch S = scratch_layout(c);
-    // misc: [sp copy is provided by caller in misc][e: NP n][tmp: n]
+    // misc: [sp copy is provided by caller in misc][e: NP n][tmp: n][gad: NP]
     u64* e = S.misc + (size_t)NP * n;
     int64_t* tmp = (int64_t*)(S.misc + (size_t)2 * NP * n);
     u64* gad_dev = S.misc + (size_t)2 * NP * n + n;
@@ -679,28 +682,34 @@ static u64* make_switch_key(rk_ctx* c, const u64* sp, u64 stream_id) {
         for (int k = 0; k < c->alpha; k++) pm = h_mulmod(pm, c->primes[L + 1 + k] % c->primes[t], c->primes[t]);
         Pmod[t] = pm;
     }
-    for (int j = 0; j < BL; j++) {
-        u64* kb = buf + (size_t)j * 2 * NP * n;
-        u64* ka = kb + (size_t)NP * n;
-        launch_uniform(c->env, ls_all(ka, 0, 1, NP), c->seed, stream_id * 64 + (u64)j, c->stream);
-        gaussian_eval(c, rng, e, NP, tmp);
-        std::vector<u64> gad(NP, 0);
-        for (int t = j * DS; t < std::min((j + 1) * DS, L + 1); t++) gad[t] = h_mulmod(Pmod[t], c->h_pc[t].r_mod, c->primes[t]);
-        RK_CUDA(cudaMemcpyAsync(gad_dev, gad.data(), NP * 8, cudaMemcpyHostToDevice, c->stream));
-        launch_key_digit(c->env, kb, ka, ka, e, c->d_sk, sp, gad_dev, NP, c->stream);
-        RK_CUDA(cudaStreamSynchronize(c->stream));
+    try {
+        for (int j = 0; j < BL; j++) {
+            u64* kb = key.data + (size_t)j * NP * n;
+            gaussian_eval(c, rng, e, NP, tmp);
+            std::vector<u64> gad(NP, 0);
+            for (int t = j * DS; t < std::min((j + 1) * DS, L + 1); t++) gad[t] = h_mulmod(Pmod[t], c->h_pc[t].r_mod, c->primes[t]);
+            RK_CUDA(cudaMemcpyAsync(gad_dev, gad.data(), NP * 8, cudaMemcpyHostToDevice, c->stream));
+            launch_key_digit_seeded(c->env, kb, e, c->d_sk, sp, gad_dev, key.seed, j, NP, c->stream);
+            RK_CUDA(cudaStreamSynchronize(c->stream));
+        }
+    } catch (...) {
+        cudaFree(key.data);
+        throw;
     }
-    return buf;
+    return key;
+}
+
+static void set_key(SwitchKeyDev& slot, const SwitchKeyDev& key) {
+    if (slot.data) cudaFree(slot.data);
+    slot = key;
 }
 
 static void make_relin_key(rk_ctx* c) {
     Scratch S = scratch_layout(c);
     launch_square_secret(c->env, S.misc, c->d_sk, c->n_primes, c->stream);
-    if (c->rlk.data) {
-        cudaFree(c->rlk.data);
-        c->generation++;
-    }
-    c->rlk.data = make_switch_key(c, S.misc, 1);
+    const SwitchKeyDev k = make_switch_key(c, S.misc, 1);
+    set_key(c->rlk, k);
+    c->generation++;
 }
 
 void keys_add_rotations(rk_ctx* c, const std::vector<int>& rotations) {
@@ -714,7 +723,7 @@ void keys_add_rotations(rk_ctx* c, const std::vector<int>& rotations) {
         u64* s_norm = S.misc + (size_t)2 * NP * c->n + 2 * c->n;   // beyond make_switch_key's area
         launch_from_mont(c->env, s_norm, c->d_sk, NP, c->stream);
         launch_automorph(c->env, S.misc, s_norm, g, NP, c->stream);
-        c->gal[g].data = make_switch_key(c, S.misc, 16 + g);
+        c->gal[g] = make_switch_key(c, S.misc, 16 + g);
     }
 }
 
@@ -737,39 +746,40 @@ void secret_import(rk_ctx* c, const int64_t* s, size_t n) {
     make_pk(c);
 }
 
-void key_import(rk_ctx* c, uint32_t kind, uint64_t galois, const uint64_t* coeffs, size_t words) {
-    const int NP = c->n_primes, BL = c->beta(c->L);
-    const size_t n = c->n, expect = (size_t)BL * 2 * NP * n;
+// Switching key words: [beta_L][parts][L+1+alpha][n], parts 2 (b_j, a_j) or 1 (b_j
+// of a seeded key), coefficient domain, residues in [0, q).
+void key_import(rk_ctx* c, uint32_t kind, uint64_t galois, const uint64_t* coeffs, size_t words, bool seeded, uint64_t seed) {
+    const int NP = c->n_primes, BL = c->beta(c->L), parts = seeded ? 1 : 2;
+    const size_t n = c->n, expect = (size_t)BL * parts * NP * n;
     RK_REQUIRE(words == expect, RK_EINVAL, "key size mismatch: expected " + std::to_string(expect) + " words");
     RK_REQUIRE(kind == RK_KEY_RELIN || kind == RK_KEY_GALOIS, RK_EINVAL, "bad key kind");
     for (int t = 0; t < NP; t++)  // spot-check residues are canonical
         RK_REQUIRE(coeffs[(size_t)t * n] < c->primes[t], RK_EFORMAT, "key residue out of range");
-    u64* buf = nullptr;
-    RK_CUDA(cudaMalloc((void**)&buf, expect * 8));
-    RK_CUDA(cudaMemcpyAsync(buf, coeffs, expect * 8, cudaMemcpyHostToDevice, c->stream));
-    launch_ntt_forward(c->env, ls_all(buf, (size_t)NP * n, BL * 2, NP), c->stream);
-    launch_to_mont(c->env, ls_all(buf, (size_t)NP * n, BL * 2, NP), c->stream);
+    SwitchKeyDev key;
+    key.seeded = seeded;
+    key.seed = seed;
+    RK_CUDA(cudaMalloc((void**)&key.data, expect * 8));
+    RK_CUDA(cudaMemcpyAsync(key.data, coeffs, expect * 8, cudaMemcpyHostToDevice, c->stream));
+    launch_ntt_forward(c->env, ls_all(key.data, (size_t)NP * n, BL * parts, NP), c->stream);
+    launch_to_mont(c->env, ls_all(key.data, (size_t)NP * n, BL * parts, NP), c->stream);
     RK_CUDA(cudaStreamSynchronize(c->stream));
     c->generation++;
-    if (kind == RK_KEY_RELIN) {
-        if (c->rlk.data) cudaFree(c->rlk.data);
-        c->rlk.data = buf;
-    } else {
-        auto it = c->gal.find(galois);
-        if (it != c->gal.end()) cudaFree(it->second.data);
-        c->gal[galois].data = buf;
-    }
+    set_key(kind == RK_KEY_RELIN ? c->rlk : c->gal[galois], key);
 }
 
-// A switching key in rk_key_import's layout: [beta_L][2][L+1+alpha][n] words,
-// coefficient domain, plain residues.
-void key_export(rk_ctx* c, const u64* key, u64* host_out) {
-    const int NP = c->n_primes, BL = c->beta(c->L);
-    const size_t n = c->n, words = (size_t)BL * 2 * NP * n;
+size_t key_words(const rk_ctx* c, const SwitchKeyDev& key) {
+    return (size_t)c->beta(c->L) * (key.seeded ? 1 : 2) * c->n_primes * c->n;
+}
+
+// A switching key in key_import's layout (coefficient domain, plain residues).
+void key_export(rk_ctx* c, const SwitchKeyDev& key, u64* host_out) {
+    const int NP = c->n_primes;
+    const size_t n = c->n, words = key_words(c, key);
+    const int polys = (int)(words / ((size_t)NP * n));
     u64* tmp = nullptr;
     RK_CUDA(cudaMallocAsync((void**)&tmp, words * 8, c->stream));
-    for (int p = 0; p < 2 * BL; p++) launch_from_mont(c->env, tmp + (size_t)p * NP * n, key + (size_t)p * NP * n, NP, c->stream);
-    launch_ntt_inverse(c->env, ls_all(tmp, (size_t)NP * n, BL * 2, NP), c->stream);
+    for (int p = 0; p < polys; p++) launch_from_mont(c->env, tmp + (size_t)p * NP * n, key.data + (size_t)p * NP * n, NP, c->stream);
+    launch_ntt_inverse(c->env, ls_all(tmp, (size_t)NP * n, polys, NP), c->stream);
     RK_CUDA(cudaMemcpyAsync(host_out, tmp, words * 8, cudaMemcpyDeviceToHost, c->stream));
     RK_CUDA(cudaFreeAsync(tmp, c->stream));
     RK_CUDA(cudaStreamSynchronize(c->stream));

@@ -365,9 +365,10 @@ void launch_ks_combine_rs(const KernelEnv& env, u64* out, size_t ps, const u64* 
 // Up to CH stacked ciphertexts per thread: each key word is read once per chunk.
 // CH is the smallest of 1, 2, 4, 8 that covers the stack (chunks of 8 beyond), so a
 // single ciphertext keeps two accumulators and the digit loop stays unrolled.
-template <int CH>
+// SEEDED: the key holds b_j only and a_j is regenerated from the key's seed.
+template <int CH, bool SEEDED>
 __global__ void __launch_bounds__(TPB) k_ks_inner(const u64* __restrict__ ext, size_t ext_stride, const u64* __restrict__ key,
-                                                  u64* __restrict__ u, int level, int L, int alpha, int beta, u64 galois,
+                                                  u64 seed, u64* __restrict__ u, int level, int L, int alpha, int beta, u64 galois,
                                                   int logn, int B, const PrimeConst* __restrict__ pc) {
     RK_KERNEL_PROLOGUE();
     const int n = 1 << logn;
@@ -382,9 +383,13 @@ __global__ void __launch_bounds__(TPB) k_ks_inner(const u64* __restrict__ ext, s
     Acc128 a0[CH], a1[CH];
     const u64* kj = key + (size_t)pid * n + k;
     const u64* ej = ext + (size_t)b0 * estride + (size_t)t * n + src;
+    const int T = L + 1 + alpha;
+    u64 state = SEEDED ? seeded_key_state(seed, 0, T, pid, n, k) : 0;
+    const u64 step = (u64)T * (u64)n * kSm64Gamma;   // one digit further in the stream
 #pragma unroll 4
     for (int j = 0; j < beta; j++) {
-        const u64 kb = __ldg(kj), ka = __ldg(kj + KL);
+        const u64 kb = __ldg(kj);
+        const u64 ka = SEEDED ? seeded_key_word(state, P.q) : __ldg(kj + KL);
 #pragma unroll
         for (int b = 0; b < CH; b++) {
             if (CH == 1 || b < nb) {
@@ -393,8 +398,9 @@ __global__ void __launch_bounds__(TPB) k_ks_inner(const u64* __restrict__ ext, s
                 a1[b].mac(e, ka);
             }
         }
-        kj += 2 * KL;
+        kj += (SEEDED ? 1 : 2) * KL;
         ej += ext_stride;
+        state += step;
     }
     const int ul = level + 1 + alpha;
 #pragma unroll
@@ -407,21 +413,36 @@ __global__ void __launch_bounds__(TPB) k_ks_inner(const u64* __restrict__ ext, s
     }
 }
 
-void launch_ks_inner(const KernelEnv& env, const u64* ext, size_t ext_stride, const u64* key, u64* u, int level, int beta,
+void launch_ks_inner(const KernelEnv& env, const u64* ext, size_t ext_stride, KeyRef key, u64* u, int level, int beta,
                      u64 galois, cudaStream_t st, int B) {
-    // algorithmic bytes: B lifted inputs read, the key read once per chunk, B outputs written
+    // algorithmic bytes: B lifted inputs read, the key (b and a, or b alone when
+    // seeded) read once per chunk, B outputs written
     const double QP = level + 1 + env.alpha;
     const int ch = B <= 1 ? 1 : B <= 2 ? 2 : B <= 4 ? 4 : 8;
     const int chunks = (B + ch - 1) / ch;
-    ProfScope pf(env, KK_KS_INNER, st, 1, ((double)B * beta + 2.0 * beta * chunks + 2.0 * B) * QP * 8.0 * env.n,
+    const double key_parts = key.seeded ? 1.0 : 2.0;
+    ProfScope pf(env, KK_KS_INNER, st, 1, ((double)B * beta + key_parts * beta * chunks + 2.0 * B) * QP * 8.0 * env.n,
                  2.0 * B * beta * QP * env.n);
     dim3 g(env.n / TPB, level + 1 + env.alpha, chunks);
-    switch (ch) {
-        case 1: rk_launch(k_ks_inner<1>, g, TPB, 0, st, ext, ext_stride, key, u, level, env.L, env.alpha, beta, galois, env.logn, B, env.pc); break;
-        case 2: rk_launch(k_ks_inner<2>, g, TPB, 0, st, ext, ext_stride, key, u, level, env.L, env.alpha, beta, galois, env.logn, B, env.pc); break;
-        case 4: rk_launch(k_ks_inner<4>, g, TPB, 0, st, ext, ext_stride, key, u, level, env.L, env.alpha, beta, galois, env.logn, B, env.pc); break;
-        default: rk_launch(k_ks_inner<8>, g, TPB, 0, st, ext, ext_stride, key, u, level, env.L, env.alpha, beta, galois, env.logn, B, env.pc); break;
+#define RK_KSI(C, SD)                                                                                                \
+    rk_launch(k_ks_inner<C, SD>, g, TPB, 0, st, ext, ext_stride, key.data, key.seed, u, level, env.L, env.alpha, beta, \
+              galois, env.logn, B, env.pc)
+    if (key.seeded) {
+        switch (ch) {
+            case 1: RK_KSI(1, true); break;
+            case 2: RK_KSI(2, true); break;
+            case 4: RK_KSI(4, true); break;
+            default: RK_KSI(8, true); break;
+        }
+    } else {
+        switch (ch) {
+            case 1: RK_KSI(1, false); break;
+            case 2: RK_KSI(2, false); break;
+            case 4: RK_KSI(4, false); break;
+            default: RK_KSI(8, false); break;
+        }
     }
+#undef RK_KSI
 }
 
 // out[c][t] = base_c[t] (automorphism applied to base0 when galois0 != 0) + (u[c][t] - w[c][t]) * P^-1
@@ -575,6 +596,28 @@ void launch_key_digit(const KernelEnv& env, u64* kb, u64* ka, const u64* a, cons
     ProfScope pf(env, KK_CLIENT, st, 1, 0.0, 0.0);
     dim3 g(env.n / TPB, n_primes);
     rk_launch(k_key_digit, g, TPB, 0, st, kb, ka, a, e, s_R, sp, gad_dev, env.n, env.pc);
+}
+
+// Seeded digit j of a switching key: a = (stream word) R^-1 (seeded_key_word gives the
+// Montgomery form), b = e - a s + gad s' stored times R.  t over the key's primes.
+__global__ void k_key_digit_seeded(u64* kb, const u64* e, const u64* s_R, const u64* sp, const u64* gad, u64 seed, int j,
+                                   int T, int n, const PrimeConst* __restrict__ pc) {
+    RK_KERNEL_PROLOGUE();
+    const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y;
+    const PrimeConst P = pc[t];
+    const size_t off = (size_t)t * n + k;
+    const u64 a = mont_mul(seeded_key_word(seeded_key_state(seed, j, T, t, n, k), P.q), 1, P.q, P.qinv);
+    const u64 as = mont_mul(a, s_R[off], P.q, P.qinv);
+    u64 b = sub_mod(e[off], as, P.q);
+    if (gad[t]) b = add_mod(b, mont_mul(sp[off], gad[t], P.q, P.qinv), P.q);   // gad stored times R
+    kb[off] = mont_mul(b, P.r2, P.q, P.qinv);
+}
+
+void launch_key_digit_seeded(const KernelEnv& env, u64* kb, const u64* e, const u64* s_R, const u64* sp, const u64* gad_dev,
+                             u64 seed, int j, int n_primes, cudaStream_t st) {
+    ProfScope pf(env, KK_CLIENT, st, 1, 0.0, 0.0);
+    dim3 g(env.n / TPB, n_primes);
+    rk_launch(k_key_digit_seeded, g, TPB, 0, st, kb, e, s_R, sp, gad_dev, seed, j, n_primes, env.n, env.pc);
 }
 
 // x <- x R (to Montgomery form), over `limbs` limbs of `polys` polys using LimbSet prime map

@@ -102,7 +102,8 @@ void launch_moddown_rs_conv(const KernelEnv& env, const u64* u, u64* w, int leve
 void launch_ks_add_pd(const KernelEnv& env, u64* u, const u64* d, int level, u64 pm, u64 pm_sh, cudaStream_t st, int B);
 void launch_ks_combine_rs(const KernelEnv& env, u64* out, size_t ps, const u64* u, const u64* w, const u64* d, int level,
                           cudaStream_t st, int B);
-void launch_ks_inner(const KernelEnv& env, const u64* ext, size_t ext_stride, const u64* key, u64* u, int level, int beta,
+
+void launch_ks_inner(const KernelEnv& env, const u64* ext, size_t ext_stride, KeyRef key, u64* u, int level, int beta,
                      u64 galois, cudaStream_t st, int B = 1);
 void launch_ks_combine(const KernelEnv& env, u64* out, size_t ps, const u64* base0, u64 galois0, const u64* base1, size_t bstride,
                        const u64* u, const u64* w, int level, cudaStream_t st, int B = 1, const u64* addend = nullptr);
@@ -110,7 +111,7 @@ void launch_ks_combine(const KernelEnv& env, u64* out, size_t ps, const u64* bas
 void ks_fused_init_attributes();
 void launch_modup_col(const KernelEnv& env, const u64* coef, u64* ext, size_t ext_stride, int level, int beta, int t0, int limbs,
                       cudaStream_t st, int B = 1);
-void launch_ks_row(const KernelEnv& env, const u64* ext, size_t ext_stride, const u64* x_eval, size_t eval_stride, const u64* key,
+void launch_ks_row(const KernelEnv& env, const u64* ext, size_t ext_stride, const u64* x_eval, size_t eval_stride, KeyRef key,
                    u64* u, int level, int beta, int t0, int limbs, u64 galois, cudaStream_t st, int B = 1);
 void launch_moddown_col(const KernelEnv& env, const u64* u, u64* w, int level, cudaStream_t st, int polys = 2);
 void launch_moddown_row(const KernelEnv& env, u64* out, size_t ps, const u64* base0, u64 galois0, const u64* base1, size_t bstride,
@@ -124,6 +125,8 @@ void launch_reduce_signed(const KernelEnv& env, const int64_t* src, const LimbSe
 void launch_uniform(const KernelEnv& env, const LimbSet& s, u64 seed, u64 stream_id, cudaStream_t st);
 void launch_key_digit(const KernelEnv& env, u64* kb, u64* ka, const u64* a, const u64* e, const u64* s_R, const u64* sp,
                       const u64* gad_dev, int n_primes, cudaStream_t st);
+void launch_key_digit_seeded(const KernelEnv& env, u64* kb, const u64* e, const u64* s_R, const u64* sp, const u64* gad_dev,
+                             u64 seed, int j, int n_primes, cudaStream_t st);
 void launch_to_mont(const KernelEnv& env, const LimbSet& s, cudaStream_t st);
 void launch_automorph(const KernelEnv& env, u64* out, const u64* x, u64 g, int limbs, cudaStream_t st);
 void launch_decrypt(const KernelEnv& env, u64* m, const u64* c0, const u64* c1, const u64* s_R, int limbs, cudaStream_t st);

@@ -98,7 +98,8 @@ __global__ void __launch_bounds__(256) k_modup_col(const u64* __restrict__ coef,
 // ---------------------------------------------------------------------------
 template <int LOG>
 __global__ void __launch_bounds__(2048 / Shape<LOG>::E, (LOG >= 7 ? 3 : 2)) k_ks_row(const u64* __restrict__ ext, size_t ext_stride, const u64* __restrict__ x_eval,
-                                                size_t eval_stride, const u64* __restrict__ key, u64* __restrict__ uo, int level,
+                                                size_t eval_stride, const u64* __restrict__ key, u64 seed, int seeded,
+                                                u64* __restrict__ uo, int level,
                                                 int L, int alpha, int beta, int dsize, int t0, u64 galois, int logn, int units,
                                                 const PrimeConst* __restrict__ pc, const u64* __restrict__ tw) {
     RK_KERNEL_PROLOGUE();
@@ -154,13 +155,15 @@ __global__ void __launch_bounds__(2048 / Shape<LOG>::E, (LOG >= 7 ? 3 : 2)) k_ks
             for (int m = 0; m < E; m++) sm[row_slot<LOG>(u, t * E + m)] = reduce_4q(x[m], q, q2);
         }
         __syncthreads();
-        const u64* kb = krow + (size_t)j * 2 * KL;
+        const u64* kb = krow + (size_t)j * (seeded ? 1 : 2) * KL;
 #pragma unroll 4
         for (int m = 0; m < E; m++) {
             const int xo = t + P * m;
             const u64 e = srow[spos[m * blockDim.x + tid]];
+            const u64 ka = seeded ? seeded_key_word(seeded_key_state(seed, j, L + 1 + alpha, pid, n, (rr << logb) + xo), q)
+                                  : __ldg(kb + KL + xo);
             a0[xo] = add_mod(a0[xo], mont_mul(e, __ldg(kb + xo), q, PC.qinv), q);
-            a1[xo] = add_mod(a1[xo], mont_mul(e, __ldg(kb + KL + xo), q, PC.qinv), q);
+            a1[xo] = add_mod(a1[xo], mont_mul(e, ka, q, PC.qinv), q);
         }
         __syncthreads();
     }
@@ -346,12 +349,12 @@ void launch_modup_col(const KernelEnv& env, const u64* coef, u64* ext, size_t ex
                                                                         env.conv, logn, loga, g.units, env.pc, env.tw.psi)));
 }
 
-void launch_ks_row(const KernelEnv& env, const u64* ext, size_t ext_stride, const u64* x_eval, size_t eval_stride, const u64* key,
+void launch_ks_row(const KernelEnv& env, const u64* ext, size_t ext_stride, const u64* x_eval, size_t eval_stride, KeyRef key,
                    u64* u, int level, int beta, int t0, int limbs, u64 galois, cudaStream_t st, int B) {
     if (limbs <= 0) return;
     const int logn = env.logn, loga = logn / 2, logb = logn - loga;
     // algorithmic bytes: each digit's limb read once, the key read once, u written
-    ProfScope pf(env, KK_KS_INNER, st, 1, ((double)B * beta + 2.0 * beta + 2.0 * B) * limbs * 8.0 * env.n,
+    ProfScope pf(env, KK_KS_INNER, st, 1, ((double)B * beta + (key.seeded ? 1.0 : 2.0) * beta + 2.0 * B) * limbs * 8.0 * env.n,
                  2.0 * B * beta * limbs * env.n);
     // 2048 elements a block (26 bytes of shared memory each): four blocks an SM
     const int P = 1 << (logb / 2);
@@ -361,7 +364,8 @@ void launch_ks_row(const KernelEnv& env, const u64* ext, size_t ext_stride, cons
     g.blocks = (1 << loga) / g.units;
     const dim3 grid(g.blocks, limbs, B);
     const size_t smem = (size_t)(1 << logb) * g.units * 26;
-    RK_LOG_SWITCH(logb, (rk_launch(k_ks_row<LG>, grid, g.threads, smem, st, ext, ext_stride, x_eval, eval_stride, key, u, level, env.L,
+    RK_LOG_SWITCH(logb, (rk_launch(k_ks_row<LG>, grid, g.threads, smem, st, ext, ext_stride, x_eval, eval_stride, key.data, key.seed,
+                                                                     key.seeded, u, level, env.L,
                                                                      env.alpha, beta, env.conv.dsize, t0, galois, logn, g.units,
                                                                      env.pc, env.tw.psi)));
 }

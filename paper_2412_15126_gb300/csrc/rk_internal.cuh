@@ -160,8 +160,38 @@ struct DevBuf {
     size_t words = 0;
 };
 
+// A switching key on the device, evaluation domain, Montgomery form, T = L+1+alpha
+// primes: data = [beta_L][2][T][n] (b_j then a_j), or, seeded, [beta_L][1][T][n] (b_j
+// only) with a_j regenerated from `seed` (seeded_key_word).
+struct KeyRef {
+    const u64* data;
+    u64 seed;
+    int seeded;
+};
+
+// Seeded key halves: SplitMix64 (Steele, Lea and Flood 2014) from its published
+// definition.  Element c of the stream from seed s is sm64_mix(s + (c + 1) GAMMA);
+// word (digit j, prime index p, evaluation index k) of a key's a part is element
+// (j T + p) n + k, and its value in [0, q_p), the high word of x q_p, is the
+// Montgomery form a 2^64 mod q_p.
+constexpr u64 kSm64Gamma = 0x9E3779B97F4A7C15ull;
+__host__ __device__ __forceinline__ u64 sm64_mix(u64 z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+// state of word (j, p, k): seed + ((j T + p) n + k + 1) GAMMA
+__host__ __device__ __forceinline__ u64 seeded_key_state(u64 seed, int j, int T, int p, int n, int k) {
+    return seed + ((((u64)j * (u64)T + (u64)p) * (u64)n + (u64)k) + 1) * kSm64Gamma;
+}
+__device__ __forceinline__ u64 seeded_key_word(u64 state, u64 q) { return umulhi64(sm64_mix(state), q); }
+
 struct SwitchKeyDev {
-    u64* data = nullptr;  // [beta_L][2][L+1+alpha][n], evaluation domain, Montgomery form
+    u64* data = nullptr;  // [beta_L][2][L+1+alpha][n] (seeded: [beta_L][1][..][n], b only),
+                          // evaluation domain, Montgomery form
+    u64 seed = 0;         // seeded: the a parts are regenerated from this seed
+    bool seeded = false;
+    KeyRef ref() const { return KeyRef{data, seed, seeded ? 1 : 0}; }
 };
 
 struct rk_server;
@@ -242,7 +272,8 @@ rk_ct* ct_clone_meta(const rk_ct* src, int level);
 void ensure_batch(rk_ctx* c, int B);   // size the scratch for stacks of B ciphertexts
 rk_ct* ct_stack(rk_ctx* c, const rk_ct* const* in, int count);        // B = count, copies
 void ct_unstack(rk_ctx* c, const rk_ct* in, rk_ct** outs);            // B outputs of B = 1
-void key_export(rk_ctx* c, const u64* key, u64* host_out);
+void key_export(rk_ctx* c, const SwitchKeyDev& key, u64* host_out);
+size_t key_words(const rk_ctx* c, const SwitchKeyDev& key);
 rk_ct* ct_view(const rk_ct* stack, int b);                            // member b, no copy
 rk_ct* ct_view_range(const rk_ct* stack, int first, int count);      // members [first, first+count), no copy
 
@@ -264,7 +295,8 @@ void ev_copy(rk_ctx* c, const rk_ct* a, rk_ct* out);
 // keys / client ops
 void keys_generate(rk_ctx* c, uint64_t seed, const std::vector<int>& rotations);
 void keys_add_rotations(rk_ctx* c, const std::vector<int>& rotations);
-void key_import(rk_ctx* c, uint32_t kind, uint64_t galois, const uint64_t* coeffs, size_t words);
+void key_import(rk_ctx* c, uint32_t kind, uint64_t galois, const uint64_t* coeffs, size_t words, bool seeded = false,
+                uint64_t seed = 0);
 void secret_import(rk_ctx* c, const int64_t* s, size_t n);
 u64 galois_left(const rk_ctx* c, int r);
 rk_ct* encrypt_values(rk_ctx* c, const double* v, uint32_t count, uint32_t N, uint32_t Q, uint32_t n_real);

@@ -73,6 +73,7 @@ _sig("rk_keygen", [_vp, ctypes.c_uint64, _u32])
 _sig("rk_keygen_rotations", [_vp, _i32p, _sz])
 _sig("rk_secret_import", [_vp, _i64p, _sz])
 _sig("rk_key_import", [_vp, _u32, ctypes.c_uint64, _u64p, _sz])
+_sig("rk_key_import_seeded", [_vp, _u32, ctypes.c_uint64, ctypes.c_uint64, _u64p, _sz])
 _sig("rk_galois_left", [_vp, ctypes.c_int32], ctypes.c_uint64)
 _sig("rk_encoding_import", [_vp, _u32, _u32, _u32, _u32, _dp, _sz])
 _sig("rk_encrypt", [_vp, _dp, _u32, _u32, _u32, _u32, ctypes.POINTER(_vp)])
@@ -281,6 +282,12 @@ class Context:
         data = np.ascontiguousarray(data, dtype=np.uint64)
         _check(_L.rk_key_import(self.handle, kind, galois, data.ctypes.data_as(_u64p), data.size))
 
+
+    def key_import_seeded(self, kind, galois, seed, b_parts):
+        """A seeded switching key: its b parts ([beta_L][L+1+alpha][n], coefficient
+        domain) and the seed its a parts are regenerated from."""
+        data = np.ascontiguousarray(b_parts, dtype=np.uint64)
+        _check(_L.rk_key_import_seeded(self.handle, kind, galois, int(seed) & (2**64 - 1), data.ctypes.data_as(_u64p), data.size))
     def galois_left(self, r: int) -> int:
         return int(_L.rk_galois_left(self.handle, r))
 

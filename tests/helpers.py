@@ -32,12 +32,20 @@ def gpu_context(name, device=0):
     return rankfhe.Context(log_n, n_limbs, alpha, dsize, log_scale, log_q0, log_sp, dg, df, device=device)
 
 
+def import_key(ctx, kind, g, key):
+    """One oracle switching key: seeded keys travel as their b parts and the seed."""
+    if key.seed is None:
+        ctx.key_import(kind, g, key.data)
+    else:
+        ctx.key_import_seeded(kind, g, key.seed, key.data[:, 0])
+
+
 def import_keys(ctx, keys):
     from paper_2412_15126_gb300 import rankfhe
     ctx.secret_import(keys.s)
-    ctx.key_import(rankfhe.KEY_RELIN, 0, keys.rlk.data)
+    import_key(ctx, rankfhe.KEY_RELIN, 0, keys.rlk)
     for g, k in keys.gal.items():
-        ctx.key_import(rankfhe.KEY_GALOIS, g, k.data)
+        import_key(ctx, rankfhe.KEY_GALOIS, g, k)
 
 
 def import_encodings(ctx, P, N, Q=1, n_real=None, kinds=("row0", "col0", "tie", "tri")):

@@ -132,32 +132,62 @@ def test_order_stat_and_sort_batch_identical_alone():
         ctx.close()
 
 
-def test_keys_export_returns_the_imported_keys():
+def _blob_records(blob):
+    recs, at = {}, 5
+    for _ in range(int(blob[4])):
+        words = int(blob[at + 4])
+        recs[(int(blob[at]), int(blob[at + 1]))] = (int(blob[at + 2]), int(blob[at + 3]), blob[at + 5: at + 5 + words])
+        at += 5 + words
+    assert at == blob.size
+    return recs
+
+
+@pytest.mark.parametrize("seeded", [True, False])
+def test_keys_export_returns_the_imported_keys(seeded):
     """rk_keys_export gives back, word for word, the oracle's keys imported into the
-    context (coefficient domain, plain residues), and importing the blob again changes
-    no result."""
+    context (coefficient domain, plain residues: b parts and seeds for seeded keys,
+    b and a otherwise), and importing the blob again changes no result."""
     P = helpers.oracle_params("small")
-    keys = ckks.keygen(P, 17, helpers.galois_elts(P, [1, -1, 4]))
+    keys = ckks.keygen(P, 17, helpers.galois_elts(P, [1, -1, 4]), seeded=seeded)
     ctx = helpers.gpu_context("small")
     try:
         helpers.import_keys(ctx, keys)
         blob = ctx.keys_export()
-        assert int(blob[0]) == 0x31305359454B4B52 and int(blob[4]) == 1 + len(keys.gal)
-        words = int(blob[7])
-        recs, at = {}, 5
-        for _ in range(int(blob[4])):
-            recs[(int(blob[at]), int(blob[at + 1]))] = blob[at + 3: at + 3 + int(blob[at + 2])]
-            at += 3 + int(blob[at + 2])
-        assert np.array_equal(recs[(1, 0)], np.asarray(keys.rlk.data, dtype=np.uint64).reshape(-1))
-        for g, k in keys.gal.items():
-            assert np.array_equal(recs[(2, g)], np.asarray(k.data, dtype=np.uint64).reshape(-1))
-        assert words == recs[(1, 0)].size
+        assert int(blob[0]) == 0x32305359454B4B52 and int(blob[4]) == 1 + len(keys.gal)
+        recs = _blob_records(blob)
+        for kid, k in [((1, 0), keys.rlk)] + [((2, g), k) for g, k in keys.gal.items()]:
+            flag, seed, words = recs[kid]
+            assert flag == (1 if seeded else 0)
+            want = k.data[:, 0] if seeded else k.data
+            assert np.array_equal(words, np.asarray(want, dtype=np.uint64).reshape(-1))
+            if seeded:
+                assert seed == k.seed
         ct = ctx.encrypt(inputs.gap_vector(8, 0.05, 3), N=8)
         before = ctx.rotate(ct, 1).export()
         ctx.keys_import(blob)
         assert np.array_equal(ctx.rotate(ct, 1).export(), before)
     finally:
         ctx.close()
+
+
+def test_explicit_and_seeded_keys_match_the_oracle():
+    """The same circuit through explicit keys (a stored) and seeded keys (a regenerated
+    inside the key switch): each bit-identical to the oracle with the same keys."""
+    from oracle import circuits as C
+    P = helpers.oracle_params("ordb")
+    N = 8
+    for seeded in (False, True):
+        keys = ckks.keygen(P, 23, helpers.galois_elts(P, helpers.rotation_set(N)), seeded=seeded)
+        ctx = helpers.gpu_context("ordb")
+        try:
+            helpers.import_keys(ctx, keys)
+            helpers.import_encodings(ctx, P, N)
+            ct = ckks.encrypt(P, keys, inputs.gap_vector(N, 0.05, 5), 31)
+            ref = C.rank(C.OracleCkks(P, keys), ct, N, *helpers.CONFIGS["ordb"][7:9])
+            got = ctx.rank(ctx.ct_import(ct.c, ct.level, N=N))
+            assert np.array_equal(got.export(), ref.c)
+        finally:
+            ctx.close()
 
 
 def test_graph_refuses_replay_after_scratch_growth(cfg2):

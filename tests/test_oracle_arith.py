@@ -177,3 +177,49 @@ def test_rha_rounding():
     expect = [1, -1, 2, 3, -3, 0, 0, 1, 3, -7, 2 ** 52 + 1, -(2 ** 52) - 1]
     assert list(ckks.rha(xs)) == expect
     assert [ckks.rha_scalar(float(x)) for x in xs] == expect
+
+
+# SplitMix64 reference outputs for seed 1234567 (the generator's published test
+# vector: the first five values of the stream).
+SPLITMIX64_1234567 = [6457827717110365317, 3203168211198807973, 9817491932198370423,
+                      4593380528125082431, 16408922859458223821]
+
+
+def test_seeded_generator_is_splitmix64():
+    """The key generator's stream is SplitMix64: word i of a one-prime, one-digit key
+    of length 5 is the high word of x_i q for the published outputs x_i."""
+    from oracle import _lib
+    q = (1 << 61) - 1
+    out = np.empty(5, dtype=np.uint64)
+    _lib.lib().orc_seeded_key_a(1234567, 0, 1, _lib.ptr(np.array([q], dtype=np.uint64)), 1, 5, _lib.ptr(out))
+    assert [int(v) for v in out] == [(x * q) >> 64 for x in SPLITMIX64_1234567]
+
+
+def test_seeded_key_a_evaluates_to_the_stream():
+    """seeded_key_a's coefficients evaluate, at psi^(2 brev(i) + 1), to the stream value
+    times 2^-64 (Horner with Python integers, sampled i; psi the first c^((q-1)/2n)
+    of order 2n): pins the order, the root and the Montgomery reading."""
+    from oracle import _lib
+    P = ckks.gen_params(8, 3, 50, 40, 1, 55, 1)
+    primes = P.qp(P.L)
+    seed, j = 987654321, 1
+    a = ckks.seeded_key_a(P, seed, j)
+    T = len(primes)
+    raw = np.empty((T, P.n), dtype=np.uint64)
+    _lib.lib().orc_seeded_key_a(seed, j, T, _lib.ptr(np.array(primes, dtype=np.uint64)), T, P.n, _lib.ptr(raw))
+    logn = P.n.bit_length() - 1
+    for p, q in enumerate(primes):
+        q = int(q)
+        c = 2
+        while True:
+            psi = pow(c, (q - 1) // (2 * P.n), q)
+            if pow(psi, P.n, q) == q - 1:
+                break
+            c += 1
+        rinv = pow(pow(2, 64, q), -1, q)
+        for i in (0, 1, 5, 77, P.n - 1):
+            x = pow(psi, 2 * int(format(i, f"0{logn}b")[::-1], 2) + 1, q)
+            acc = 0
+            for coef in reversed(a[p].tolist()):
+                acc = (acc * x + int(coef)) % q
+            assert acc == int(raw[p, i]) * rinv % q
