@@ -321,7 +321,7 @@ class Context:
     def ct_import(self, coeffs, level, N=1, Q=1, n_real=None) -> Ciphertext:
         c = np.ascontiguousarray(coeffs, dtype=np.uint64)
         h = _vp()
-        _check(_L.rk_ct_import(self.handle, c.ctypes.data_as(_u64p), level, N, Q, n_real or N, ctypes.byref(h)))
+        _check(_L.rk_ct_import(self.handle, c.ctypes.data_as(_u64p), level, N, Q, N if n_real is None else n_real, ctypes.byref(h)))
         return Ciphertext(self, h.value)
 
     # ---- operations ----

@@ -75,6 +75,34 @@ def test_rank_padded_n5(cfg1):
     assert np.max(np.abs(ctx.decrypt(g) - C.brute_fractional_rank(v))) < 0.25
 
 
+@pytest.mark.parametrize("N, n_real", [(1, 1), (2, 2), (2, 1)])
+def test_rank_degenerate_lengths(cfg1, N, n_real):
+    """The degenerate lengths: one element (no rotation at all: rank 1), two, and one
+    real value padded to two; bit-exact with the oracle."""
+    P, keys, ctx = cfg1
+    helpers.import_encodings(ctx, P, N)
+    if n_real != N:
+        helpers.import_encodings(ctx, P, N, n_real=n_real, kinds=())
+    v = inputs.gap_vector(n_real, 0.05, 40 + N + n_real)
+    ct = ckks.encrypt(P, keys, np.r_[v, np.zeros(N - n_real)], 17)
+    R = C.rank(C.OracleCkks(P, keys), ct, N, 2, 1, n_real=n_real)
+    g = ctx.rank(ctx.ct_import(ct.c, ct.level, N=N, n_real=n_real))
+    assert np.array_equal(g.export(), R.c)
+    assert np.max(np.abs(ctx.decrypt(g)[:n_real] - C.brute_fractional_rank(v))) < 0.25
+
+
+def test_rank_rejects_empty_and_bad_lengths(cfg1):
+    """No real value, a length that is not a power of two, or N^2 beyond the slots:
+    RK_EINVAL before any kernel runs."""
+    from paper_2412_15126_gb300 import rankfhe
+    P, keys, ctx = cfg1
+    ct = ckks.encrypt(P, keys, np.zeros(8), 3)
+    for kw in (dict(N=8, n_real=0), dict(N=6), dict(N=1 << 12)):
+        with pytest.raises(rankfhe.RkError) as e:
+            ctx.rank(ctx.ct_import(ct.c, ct.level, **kw))
+        assert e.value.status == rankfhe.RK_EINVAL
+
+
 def test_depth_error(cfg1):
     from paper_2412_15126_gb300 import rankfhe
     P, keys, ctx = cfg1
