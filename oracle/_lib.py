@@ -30,7 +30,7 @@ def build(force: bool = False) -> str:
     os.makedirs(_OUT_DIR, exist_ok=True)
     if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
         tmp = _OUT + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared",
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
                                "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _OUT)
     return _OUT
@@ -56,6 +56,7 @@ def lib():
             L.orc_root_of_unity.restype = ctypes.c_uint64
             L.orc_nega_forward.argtypes = [_u64p, ctypes.c_size_t, ctypes.c_uint64]
             L.orc_nega_inverse.argtypes = [_u64p, ctypes.c_size_t, ctypes.c_uint64]
+            L.orc_base_conv_rounded.argtypes = [_u64p, ctypes.c_size_t, _u64p, ctypes.c_int, _u64p, ctypes.c_int, _u64p]
             L.orc_seeded_key_a.argtypes = [ctypes.c_uint64, ctypes.c_int, ctypes.c_int, _u64p, ctypes.c_int, ctypes.c_size_t, _u64p]
             L.orc_polymul_schoolbook.argtypes = [_u64p, _u64p, _u64p, ctypes.c_size_t, ctypes.c_uint64]
             L.orc_ring_mac.argtypes = [_u64p, ctypes.c_size_t, _u64p, ctypes.c_size_t, ctypes.c_int,

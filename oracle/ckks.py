@@ -471,14 +471,26 @@ def mod_down(P: Params, u: np.ndarray, level: int) -> np.ndarray:
     return mul_scalar_mod(sub_mod(u[: level + 1], w, q), pinv, q)
 
 
+def base_conv_rounded(x, src, dst):
+    """Basis conversion to the centred representative of x mod prod(src): the
+    multiple of the product is decided by rounding sum_i y_i / s_i in IEEE double
+    (see the C core); exact unless that sum lies within double rounding of a
+    half-integer."""
+    x = u64(x)
+    out = np.empty((len(dst), x.shape[1]), dtype=np.uint64)
+    _lib.lib().orc_base_conv_rounded(ptr(x), x.shape[1], ptr(u64(src)), len(src), ptr(u64(dst)), len(dst), ptr(out))
+    return out
+
+
 def mod_down_rescale(P: Params, u: np.ndarray, level: int) -> np.ndarray:
-    """(u - [u]_S) / S over Q_(l-1), S = P q_l, [u]_S by the centred fast conversion
-    from the basis {q_l, p_0 .. p_(alpha-1)}: a key switch's ModDown and the rescale
-    that follows it, in one rounding (u over Q_l P, limbs 0..l then the P limbs)."""
+    """round(u / S) over Q_(l-1), S = P q_l: (u - [u]_S) / S with [u]_S the centred
+    representative of u mod S from the basis {q_l, p_0 .. p_(alpha-1)} (rounded
+    conversion): a key switch's ModDown and the rescale that follows it, in one
+    rounding (u over Q_l P, limbs 0..l then the P limbs)."""
     q = P.q[:level]
     src_primes = [P.q[level]] + list(P.p)
     src = np.concatenate([u[level:level + 1], u[level + 1:]])
-    w = fast_base_conv_centered(src, src_primes, q)
+    w = base_conv_rounded(src, src_primes, q)
     S = int(P.q[level])
     for pk in P.p:
         S *= int(pk)

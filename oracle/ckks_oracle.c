@@ -19,6 +19,7 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <math.h>
 
 typedef unsigned __int128 u128;
 
@@ -276,4 +277,54 @@ void orc_seeded_key_a(uint64_t seed, int j, int T, const uint64_t *primes, int n
             out[(size_t)p * n + i] = (uint64_t)(((u128)x * primes[p]) >> 64);
         }
     }
+}
+
+/* Basis conversion with the multiple of D decided by one rounding: for source
+ * residues x_i (basis s_i, D = prod s_i), y_i = x_i (D/s_i)^-1 mod s_i in [0, s_i),
+ * f = sum_i y_i * (1/s_i) in IEEE double (each product and sum rounded to nearest,
+ * in source order, 1/s_i the correctly rounded reciprocal), v = floor(f + 1/2), and
+ *   out_m = ( sum_i y_i (D/s_i) - v D ) mod t_m,
+ * the centred representative of x mod D (the exact one unless f lies within double
+ * rounding of a half-integer). */
+void orc_base_conv_rounded(const uint64_t *in, size_t n, const uint64_t *src, int n_src,
+                           const uint64_t *dst, int n_dst, uint64_t *out) {
+    uint64_t *dhat_inv = (uint64_t *)malloc(sizeof(uint64_t) * n_src);
+    double *rcp = (double *)malloc(sizeof(double) * n_src);
+    for (int i = 0; i < n_src; i++) {
+        uint64_t h = 1;
+        for (int j = 0; j < n_src; j++) if (j != i) h = mulmod(h, src[j] % src[i], src[i]);
+        dhat_inv[i] = invmod(h, src[i]);
+        rcp[i] = 1.0 / (double)src[i];
+    }
+    int64_t *v = (int64_t *)malloc(sizeof(int64_t) * n);
+#pragma omp parallel for
+    for (size_t k = 0; k < n; k++) {
+        double f = 0.0;
+        for (int i = 0; i < n_src; i++) {
+            const uint64_t y = mulmod(in[(size_t)i * n + k], dhat_inv[i], src[i]);
+            const double p = (double)y * rcp[i];
+            f = f + p;
+        }
+        v[k] = (int64_t)floor(f + 0.5);
+    }
+#pragma omp parallel for
+    for (int m = 0; m < n_dst; m++) {
+        uint64_t tm = dst[m];
+        uint64_t Dm = 1 % tm;
+        for (int j = 0; j < n_src; j++) Dm = mulmod(Dm, src[j] % tm, tm);
+        for (size_t k = 0; k < n; k++) {
+            uint64_t acc = 0;
+            for (int i = 0; i < n_src; i++) {
+                uint64_t dh = 1 % tm;   /* D / s_i mod t_m */
+                for (int j = 0; j < n_src; j++) if (j != i) dh = mulmod(dh, src[j] % tm, tm);
+                const uint64_t y = mulmod(in[(size_t)i * n + k], dhat_inv[i], src[i]);
+                acc = addmod(acc, mulmod(y % tm, dh, tm), tm);
+            }
+            acc = submod(acc, mulmod((uint64_t)v[k] % tm, Dm, tm), tm);
+            out[(size_t)m * n + k] = acc;
+        }
+    }
+    free(v);
+    free(rcp);
+    free(dhat_inv);
 }

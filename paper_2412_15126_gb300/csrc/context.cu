@@ -306,7 +306,7 @@ void ctx_build(rk_ctx* c, const rk_params* p, int device, void* stream) {
         }
     }
     // fused ModDown + rescale blocks
-    const size_t A1 = (size_t)A + 1, rs_stride = 2 * A1 + A1 * (L + 1) + 3 * (size_t)(L + 1);
+    const size_t A1 = (size_t)A + 1, rs_stride = 2 * A1 + A1 * (L + 1) + 3 * (size_t)(L + 1) + A1;
     const size_t mr_off = conv.size();
     conv.resize(mr_off + (size_t)(L + 1) * rs_stride, 0);
     for (int l = 1; l <= L; l++) {
@@ -337,6 +337,8 @@ void ctx_build(rk_ctx* c, const rk_params* p, int device, void* stream) {
             smod[(L + 1) + i] = inv;
             smod[2 * (L + 1) + i] = shoup_of(inv, q[i]);
         }
+        double* rcp = reinterpret_cast<double*>(smod + 3 * (L + 1));   // 1 / s_k, correctly rounded
+        for (size_t k = 0; k < A1; k++) rcp[k] = 1.0 / (double)src[k];
     }
     RK_CUDA(cudaMalloc((void**)&c->d_conv, conv.size() * 8));
     RK_CUDA(cudaMemcpy(c->d_conv, conv.data(), conv.size() * 8, cudaMemcpyHostToDevice));

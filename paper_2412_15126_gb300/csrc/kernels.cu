@@ -225,9 +225,13 @@ void launch_modup(const KernelEnv& env, const u64* x, const u64* x_eval, size_t 
 }
 
 // ModDown conversion of the P part of u ([2][l+1+alpha][n], P limbs already in the
-// coefficient domain) to w = [2][l+1][n]; CONV_EL coefficients a thread.
+// coefficient domain) to w = [2][l+1][n]; CONV_EL coefficients a thread.  Each term
+// y_k is centred on its own (the multiple of S is the count of terms above s_k / 2).
 // RS (a product's ModDown fused with its rescale): the sources are limbs l .. l+alpha
-// (q_l then the P limbs, coefficient domain), S = q_l P, and w = [2][l][n].
+// (q_l then the P limbs, coefficient domain), S = q_l P, w = [2][l][n], and the
+// multiple of S is decided by one rounding, v = floor(sum_k y_k (1/s_k) + 1/2) in
+// IEEE double (products and sums rounded to nearest in source order), so that w is the
+// centred residue of u mod S and the product is round(u / S).
 template <int A, bool RS>
 __global__ void __launch_bounds__(TPB) k_moddown_conv(const u64* __restrict__ u, u64* __restrict__ w, int level, int L,
                                                       ConvTables cv, int n, const PrimeConst* __restrict__ pc) {
@@ -256,8 +260,13 @@ __global__ void __launch_bounds__(TPB) k_moddown_conv(const u64* __restrict__ u,
     // centred terms: y_k in (-s_k/2, s_k/2]; a negative term contributes y_k (S/s_k) - S
     u64 y[CONV_EL][NS];
     int nneg[CONV_EL];
+    double f[CONV_EL];
+    const double* rcp = reinterpret_cast<const double*>(pmod + 3 * (L + 1));
 #pragma unroll
-    for (int e = 0; e < CONV_EL; e++) nneg[e] = 0;
+    for (int e = 0; e < CONV_EL; e++) {
+        nneg[e] = 0;
+        f[e] = 0.0;
+    }
 #pragma unroll
     for (int kk = 0; kk < NS; kk++) {
         const u64 sk = RS ? (kk == 0 ? pc[level].q : pc[L + kk].q) : pc[L + 1 + kk].q;
@@ -265,8 +274,15 @@ __global__ void __launch_bounds__(TPB) k_moddown_conv(const u64* __restrict__ u,
 #pragma unroll
         for (int e = 0; e < CONV_EL; e++) {
             y[e][kk] = shoup_mul(up[(size_t)kk * n + e * TPB], iv, ivsh, sk);
-            nneg[e] += y[e][kk] > (sk >> 1) ? 1 : 0;
+            if (RS)
+                f[e] = __dadd_rn(f[e], __dmul_rn(__ull2double_rn(y[e][kk]), rcp[kk]));
+            else
+                nneg[e] += y[e][kk] > (sk >> 1) ? 1 : 0;
         }
+    }
+    if (RS) {
+#pragma unroll
+        for (int e = 0; e < CONV_EL; e++) nneg[e] = (int)floor(__dadd_rn(f[e], 0.5));
     }
     u64* out = w + (size_t)c * nt * n + k0;
     for (int i = 0; i < nt; i++) {

@@ -90,7 +90,8 @@ struct ConvTables {
     // s_0 = q_l, s_(k+1) = p_k): block at mdrs + l * mdrs_stride:
     //   [0, A+1) (S/s_k)^-1 mod s_k, [A+1, 2(A+1)) Shoup,
     //   [2(A+1), 2(A+1) + (A+1)(L+1)) (S/s_k) mod q_i times R, row-major [k][i],
-    //   then (L+1) words S mod q_i, then (L+1) words S^-1 mod q_i and (L+1) Shoup
+    //   then (L+1) words S mod q_i, then (L+1) words S^-1 mod q_i and (L+1) Shoup,
+    //   then A+1 doubles 1/s_k (the rounded conversion's reciprocals)
     const u64* mdrs;
     size_t mdrs_stride;
 };
