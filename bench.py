@@ -820,6 +820,34 @@ def run_cuda(args):
             o.free()
         g.free()
 
+    # the same rank with the input first brought down to the lowest level the circuit
+    # needs (RK_OPT_TRIM_LEVELS): the same work on fewer limbs, result at level 0
+    trimmed = None
+    if not args.no_graph:
+        ctx.set_option(rankfhe.OPT_TRIM_LEVELS, 1)
+        try:
+            for i in range(args.warmup):
+                ctx.rank(cts[i]).free()
+            ctx.sync()
+            tev0 = torch.cuda.Event(enable_timing=True)
+            tev1 = torch.cuda.Event(enable_timing=True)
+            touts = []
+            with torch.cuda.stream(stream):
+                tev0.record(stream)
+                for i in range(args.steps):
+                    touts.append(ctx.rank(cts[args.warmup + i]))
+                tev1.record(stream)
+            tev1.synchronize()
+            terr = max(float(np.max(np.abs(ctx.decrypt(touts[i]) - brute_fractional_rank(vecs[args.warmup + i]))))
+                       for i in (0, args.steps - 1))
+            trimmed = {"ms_per_step": tev0.elapsed_time(tev1) / args.steps, "out_level": touts[0].level,
+                       "max_rank_error": terr,
+                       "note": "opt-in: input brought down to the level the circuit needs before the rank"}
+            for o in touts:
+                o.free()
+        finally:
+            ctx.set_option(rankfhe.OPT_TRIM_LEVELS, 0)
+
     batched = None
     if not args.no_batched:
         batched = batched_workload(ctx)
@@ -863,7 +891,7 @@ def run_cuda(args):
             "roofline_hbm": roof_ks,
             "cpu_baseline": cpu,
             "batched": batched,
-            "graph": graph,
+            "graph": graph, "trimmed_levels": trimmed,
             "order_sort": order_sort,
             "rank8": small,
             "cheb_comparator": cheb,

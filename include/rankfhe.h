@@ -117,7 +117,8 @@ rk_status rk_sync(rk_ctx* ctx);
 /* Counters since creation: [key switches, rotations, ciphertext products, rescales]. */
 rk_status rk_ctx_counters(const rk_ctx* ctx, uint64_t out[4]);
 
-/* Execution options (the paper has no counterpart; results do not depend on them).
+/* Execution options (the paper has no counterpart; results do not depend on them,
+ * except RK_OPT_TRIM_LEVELS, which changes the output level).
  * RK_OPT_KS_FUSED: 0 (default) runs hybrid key switching as staged kernels, which
  *   materialise every lifted digit in device memory; 1 fuses the ModUp and ModDown
  *   conversions into the NTT column passes and the key inner product and the final
@@ -129,10 +130,16 @@ rk_status rk_ctx_counters(const rk_ctx* ctx, uint64_t out[4]);
  * RK_OPT_BLOCK_STACKING: 1 (default) runs the blocks and block pairs of
  *   rk_rank_blocked (flags 0) as stacks; 0 runs every block and pair ciphertext with
  *   its own launches (the plain per-query form, for comparison).  Same results.
+ * RK_OPT_TRIM_LEVELS: 0 (default) evaluates rk_rank / rk_rank_batch at the input's
+ *   level; 1 first brings the input down (scalar products by 1 and rescales, as
+ *   rk_level_down) to the lowest level the rank circuit needs, so that every key
+ *   switch runs on fewer limbs and the result leaves at level 0.  The ranks are the
+ *   same up to rounding; the ciphertexts differ.
  * Errors: RK_EINVAL for an unknown option or a negative value. */
 #define RK_OPT_KS_FUSED 1
 #define RK_OPT_KS_GROUP_BYTES 2
 #define RK_OPT_BLOCK_STACKING 3
+#define RK_OPT_TRIM_LEVELS 4
 rk_status rk_ctx_set_option(rk_ctx* ctx, uint32_t option, int64_t value);
 
 /* Autotune the launch shapes on this device (the paper has no counterpart): times

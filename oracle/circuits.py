@@ -360,10 +360,33 @@ def row_col_forms(B, V, N, Q=1):
     return B.level_down(VR, B.level(VC)), VC
 
 
-def rank(B, V, N, dg, df, Q=1, n_real=None):
+def rank_out_level(P, N) -> int:
+    """Lowest level r whose modulus q_0 ... q_r holds ranks up to N at the canonical
+    scale with two bits to spare: sum_i<=r log2 q_i >= log2 Delta_r + log2 N + 2."""
+    bits = 0.0
+    for r in range(P.L + 1):
+        bits += math.log2(int(P.q[r]))
+        if bits >= math.log2(P.scales[r]) + math.log2(N) + 2:
+            return r
+    return P.L
+
+
+def cmp_levels(dg, df) -> int:
+    """Levels one comparison consumes: 3 per composite stage (depth-3 degree-7
+    polynomial), or the Chebyshev evaluation's depth."""
+    return dg.depth() if isinstance(dg, ChebCmp) else 3 * (dg + df)
+
+
+def rank(B, V, N, dg, df, Q=1, n_real=None, trim=False):
     """Alg. 3: R = SumR(C) + 1/2 (fractional ranks in row 0).  With n_real < N the
     vector was zero-padded to N = 2^k and the comparison matrix is masked to the
-    n_real x n_real block before summing (Sec. 3.1)."""
+    n_real x n_real block before summing (Sec. 3.1).  trim: V is first brought down
+    (level_down) to the lowest level the circuit needs, TransR's mask, the
+    comparison, the padding mask and SumR's mask, so that the result leaves at
+    level 0."""
+    if trim:
+        need = 1 + cmp_levels(dg, df) + 1 + (1 if n_real is not None and n_real != N else 0)
+        V = B.level_down(V, need + rank_out_level(B.P, N))
     C = comparison_matrix(B, V, N, dg, df, Q)
     if n_real is not None and n_real != N:
         C = B.mul_plain(C, ("valid", N, Q, n_real))

@@ -176,6 +176,7 @@ rk_status rk_ctx_set_option(rk_ctx* ctx, uint32_t option, int64_t value) {
             case RK_OPT_KS_FUSED: ctx->ks_fused = value != 0; break;
             case RK_OPT_KS_GROUP_BYTES: ctx->ks_group_bytes = (double)value; break;
             case RK_OPT_BLOCK_STACKING: ctx->stack_blocks = value != 0; break;
+            case RK_OPT_TRIM_LEVELS: ctx->trim_levels = value != 0; break;
             default: throw rk_error(RK_EINVAL, "unknown option " + std::to_string(option));
         }
     });

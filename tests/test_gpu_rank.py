@@ -103,6 +103,25 @@ def test_rank_rejects_empty_and_bad_lengths(cfg1):
         assert e.value.status == rankfhe.RK_EINVAL
 
 
+def test_rank_trimmed_levels_bit_exact(cfg1):
+    """RK_OPT_TRIM_LEVELS: the input is brought down to the lowest level the rank
+    needs (keeping one more level when q_0 cannot hold ranks at the scale); the
+    result equals the oracle's trimmed schedule bit for bit."""
+    from paper_2412_15126_gb300 import rankfhe
+    P, keys, ctx = cfg1
+    v = inputs.gap_vector(8, 0.05, 12)
+    ct = ckks.encrypt(P, keys, v, 12)
+    R = C.rank(C.OracleCkks(P, keys), ct, 8, 2, 1, trim=True)
+    ctx.set_option(rankfhe.OPT_TRIM_LEVELS, 1)
+    try:
+        g = ctx.rank(ctx.ct_import(ct.c, ct.level, N=8))
+    finally:
+        ctx.set_option(rankfhe.OPT_TRIM_LEVELS, 0)
+    assert g.level == R.level == C.rank_out_level(P, 8)
+    assert np.array_equal(g.export(), R.c)
+    assert np.max(np.abs(ctx.decrypt(g) - C.brute_fractional_rank(v))) < 0.25
+
+
 def test_depth_error(cfg1):
     from paper_2412_15126_gb300 import rankfhe
     P, keys, ctx = cfg1
@@ -164,6 +183,21 @@ def test_cfg2_comparison_matrix_slots(cfg2_gpu_keys):
     Bp = C.PlainSlots(P.slots, P.L)
     ideal = Bp.values(C.comparison_matrix(Bp, Bp.fresh(v), N, 4, 2))
     assert np.max(np.abs(ctx.decrypt_slots(Cm) - ideal)) < 2.0 ** -10
+
+
+def test_cfg2_trimmed_rank_n128(cfg2_gpu_keys):
+    """The 128-element rank with RK_OPT_TRIM_LEVELS: it leaves at level 0 and still
+    decrypts to the brute-force ranks within 0.25."""
+    from paper_2412_15126_gb300 import rankfhe
+    ctx = cfg2_gpu_keys
+    v = inputs.gap_vector(128, 2.0 ** -9, 77)
+    ctx.set_option(rankfhe.OPT_TRIM_LEVELS, 1)
+    try:
+        g = ctx.rank(ctx.encrypt(v, N=128))
+    finally:
+        ctx.set_option(rankfhe.OPT_TRIM_LEVELS, 0)
+    assert g.level == 0
+    assert np.max(np.abs(ctx.decrypt(g) - C.brute_fractional_rank(v))) < 0.25
 
 
 def test_cfg2_rank_n16_and_n64(cfg2_gpu_keys):

@@ -42,6 +42,23 @@ def test_encrypted_rank_n8(small, seed):
     assert np.max(np.abs(B.values(R) - ideal)) < 2.0 ** -12
 
 
+def test_rank_out_level_and_trimmed_rank(small):
+    """With q_0 of 40 bits at scale 2^40, level 0 cannot hold ranks up to 8, so the
+    result keeps level 1 (a 60-bit q_0 at 2^45 holds ranks up to 2^13 at level 0); the
+    trimmed schedule decrypts to the brute-force ranks from level 1, and without
+    trimming the same levels are simply not spent."""
+    P, keys = small
+    assert C.rank_out_level(P, 8) == 1
+    P60 = ckks.gen_params(10, 6, 60, 45, 1, 61, 1)
+    assert C.rank_out_level(P60, 128) == 0 and C.rank_out_level(P60, 1 << 14) == 1
+    v = inputs.gap_vector(8, 0.05, 21)
+    ct = ckks.encrypt(P, keys, v, 21)
+    B = C.OracleCkks(P, keys)
+    R = C.rank(B, ct, 8, 2, 1, trim=True)
+    assert R.level == 1
+    assert np.max(np.abs(B.values(R)[:8] - C.brute_fractional_rank(v))) < 0.25
+
+
 def test_encrypted_tie_corrected_rank(small):
     P, keys = small
     v = np.array([3, 1, 3, 0, 2, 1, 3, 2]) / 4.0
