@@ -133,8 +133,10 @@ rk_status rk_ctx_counters(const rk_ctx* ctx, uint64_t out[4]);
  * RK_OPT_TRIM_LEVELS: 0 (default) evaluates rk_rank / rk_rank_batch at the input's
  *   level; 1 first brings the input down (scalar products by 1 and rescales, as
  *   rk_level_down) to the lowest level the rank circuit needs, so that every key
- *   switch runs on fewer limbs and the result leaves at level 0.  The ranks are the
- *   same up to rounding; the ciphertexts differ.
+ *   switch runs on fewer limbs; the result leaves at the lowest level whose modulus
+ *   holds ranks up to N at its scale with two bits to spare (level 0 when q_0 has
+ *   room, e.g. a 60-bit q_0 at scale 2^45).  The ranks are the same up to rounding;
+ *   the ciphertexts differ.
  * Errors: RK_EINVAL for an unknown option or a negative value. */
 #define RK_OPT_KS_FUSED 1
 #define RK_OPT_KS_GROUP_BYTES 2

@@ -401,7 +401,8 @@ const std::vector<double>& indicator_coeffs(rk_ctx* c, uint32_t N) {
 }  // namespace
 
 // Lowest level r whose modulus q_0 .. q_r holds ranks up to N at the canonical scale
-// with two bits to spare.
+// with two bits to spare: where a trimmed rank leaves (q_0 of 40 bits at scale 2^40
+// cannot hold the 1/2 the rank adds to every slot).
 static int rank_out_level(const rk_ctx* c, uint32_t N) {
     double bits = 0.0;
     for (int r = 0; r <= c->L; r++) {
@@ -411,12 +412,12 @@ static int rank_out_level(const rk_ctx* c, uint32_t N) {
     return c->L;
 }
 
-// levels the rank circuit consumes, plus the level its result must keep
+// levels the rank circuit consumes
 int rank_depth(const rk_ctx* c, const rk_ct* in, uint32_t flags) {
     int d = 1 + cmp_depth(c) + 1;
     if (in->n_real != in->N) d += 1;
     if (flags & RK_TIES_CORRECT) d += 2;
-    return d + rank_out_level(c, in->N);
+    return d;
 }
 
 rk_ct* circuit_rank(rk_ctx* c, const rk_ct* in, uint32_t flags) {
@@ -430,8 +431,8 @@ rk_ct* circuit_rank(rk_ctx* c, const rk_ct* in, uint32_t flags) {
     Ev E{c};
     H V(ct_clone_meta(in, in->level));
     ev_copy(c, in, V.p);
-    const int need = rank_depth(c, in, flags);
-    if (c->trim_levels && V->level > need) V = E.level_down(V, need);   // the result leaves at level 0
+    const int keep = rank_depth(c, in, flags) + rank_out_level(c, in->N);
+    if (c->trim_levels && V->level > keep) V = E.level_down(V, keep);   // the result leaves at rank_out_level
     H C = comparison_matrix(E, V, (int)c->prm.d_g, (int)c->prm.d_f);
     if (in->n_real != in->N) C = E.mul_mask(C, RK_MASK_VALID);
     if (flags & RK_TIES_CORRECT)   // R + F = SumR(C + E (delta - 1/2)) (Alg. 6 folded)
