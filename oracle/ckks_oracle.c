@@ -7,7 +7,9 @@
  * TEST INFRASTRUCTURE ONLY.  This file is part of the oracle that the tests,
  * the smoke check and the CPU-baseline leg of the benchmark compare the CUDA
  * path against.  The product path never loads it.  It shares no code, tables
- * or constants with the CUDA library.
+ * or constants with the CUDA library; the one common definition is the
+ * published SplitMix64 generator of seeded switching keys, which each side
+ * implements on its own from the published description.
  *
  * Everything here is deliberately plain: every modular product is a 128-bit
  * product followed by the C remainder operator, the number-theoretic
