@@ -446,6 +446,12 @@ rk_status rk_profile_start(rk_ctx* ctx, const char* kinds);
 rk_status rk_profile_stop(rk_ctx* ctx, double out[4]);
 /* The same four figures for one kind, after rk_profile_stop. */
 rk_status rk_profile_kind(const rk_ctx* ctx, const char* kind, double out[4]);
+/* Suspend (paused = 1) or resume (0) the timing started by rk_profile_start without
+ * synchronising or resetting the accumulators: launches in between are not timed.
+ * The events bracketing each timed launch cost a few microseconds of device time
+ * (they separate it from its neighbours), so a long run can time a sample of its
+ * steps.  Errors: RK_EINVAL on a null context. */
+rk_status rk_profile_pause(rk_ctx* ctx, int paused);
 /* Number of kernels this context has launched since creation. */
 uint64_t rk_launch_count(const rk_ctx* ctx);
 

@@ -770,6 +770,7 @@ rk_status rk_profile_start(rk_ctx* ctx, const char* kinds) {
         Profiler& p = ctx->prof;
         p.mask = 0;
         p.used = 0;
+        p.paused = false;
         for (int k = 0; k < KK_COUNT; k++) {
             p.bytes[k] = p.ops[k] = p.ms[k] = 0;
             p.timed[k] = 0;
@@ -813,6 +814,13 @@ rk_status rk_profile_stop(rk_ctx* ctx, double out[4]) {
         }
         p.mask = 0;
         p.used = 0;
+    });
+}
+
+rk_status rk_profile_pause(rk_ctx* ctx, int paused) {
+    return guard([&] {
+        need(ctx, "ctx");
+        ctx->prof.paused = paused != 0;
     });
 }
 

@@ -50,7 +50,7 @@ struct ProfScope {
         : p(e.prof), kind(k), st(s), bytes(b), ops(o) {
         if (!p) return;
         p->launches += (uint64_t)nlaunch;
-        if (p->mask & (1u << kind)) {
+        if ((p->mask & (1u << kind)) && !p->paused) {
             on = true;
             record();
         }

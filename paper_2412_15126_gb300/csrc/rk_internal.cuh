@@ -121,6 +121,7 @@ extern const char* const kKernelKindNames[KK_COUNT];
 struct Profiler {
     uint64_t launches = 0;        // every kernel this library launched
     uint32_t mask = 0;            // kinds being timed (bit k for kind k), 0 = none
+    bool paused = false;          // timing suspended (rk_profile_pause)
     std::vector<cudaEvent_t> ev;  // start/stop pairs
     std::vector<int> ev_kind;     // kind of each pair
     size_t used = 0;

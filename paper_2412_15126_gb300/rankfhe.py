@@ -126,6 +126,7 @@ _sig("rk_ntt_inverse", [_vp, _vp, _u32, _u32])
 _sig("rk_profile_start", [_vp, ctypes.c_char_p])
 _sig("rk_profile_stop", [_vp, _dp])
 _sig("rk_profile_kind", [_vp, ctypes.c_char_p, _dp])
+_sig("rk_profile_pause", [_vp, ctypes.c_int])
 _sig("rk_launch_count", [_vp], ctypes.c_uint64)
 _sig("rk_last_error", [], ctypes.c_char_p)
 
@@ -500,6 +501,10 @@ class Context:
 
     def profile_start(self, kind):
         _check(_L.rk_profile_start(self.handle, kind.encode() if kind else None))
+
+    def profile_pause(self, paused: bool):
+        """Suspend or resume the timing started by profile_start (no synchronisation)."""
+        _check(_L.rk_profile_pause(self.handle, 1 if paused else 0))
 
     def profile_stop(self) -> dict:
         out = (ctypes.c_double * 4)()

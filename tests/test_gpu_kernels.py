@@ -106,3 +106,23 @@ def test_encrypt_on_gpu_decrypts(setup):
     # the oracle decrypts the GPU's encryption under the same secret
     o = ckks.Ct(g.export(), g.level)
     assert np.max(np.abs(ckks.decrypt(P, keys, o)[:8] - v)) < 2.0 ** -20
+
+
+def test_profile_pause_times_only_resumed_launches(setup):
+    """rk_profile_pause: launches while paused are neither timed nor counted, the
+    accumulators keep what was timed before, and results do not change."""
+    P, keys, ctx, c1, c2, g1, g2, rots = setup
+    ctx.profile_start("ks_inner")
+    a = ctx.rotate(g1, rots[0])
+    ctx.profile_pause(True)
+    b = ctx.rotate(g1, rots[0])
+    ctx.profile_pause(False)
+    ctx.profile_stop()
+    one = ctx.profile_kind("ks_inner")
+    ctx.profile_start("ks_inner")
+    ctx.rotate(g1, rots[0])
+    ctx.profile_stop()
+    alone = ctx.profile_kind("ks_inner")
+    assert one["launches"] == alone["launches"] >= 1 and one["ms"] > 0
+    assert one["bytes"] == alone["bytes"]
+    assert np.array_equal(a.export(), b.export())
