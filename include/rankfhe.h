@@ -41,7 +41,7 @@ typedef enum {
     RK_EINVAL = 1,    /* bad argument (size, range, layout, level mismatch)            */
     RK_ENOMEM = 2,    /* device or host allocation failed                               */
     RK_EDEPTH = 3,    /* the circuit needs more levels than the ciphertext has left     */
-    RK_ETIMEOUT = 4,  /* a bounded device-side wait gave up                             */
+    RK_ETIMEOUT = 4,  /* reserved: no kernel here waits on a flag or peer (finite grids) */
     RK_ECUDA = 5,     /* a CUDA runtime call failed (message has the CUDA error text)   */
     RK_EFORMAT = 6,   /* malformed or truncated serialised data                         */
     RK_ENOKEY = 7     /* a switching key (relinearisation or rotation) is missing      */
