@@ -84,6 +84,11 @@ struct Ev {
         ev_rotate_add(c, x.p, r, o.p);
         return o;
     }
+    H rot_add_multi(const H& x, const std::vector<int>& r) {   // member b: x_b + rot(x_b, r[b])
+        H o = fresh(x, x->level);
+        ev_rotate_multi(c, x.p, r.data(), true, o.p);
+        return o;
+    }
     std::pair<H, H> rot2(const H& x, int r1, int r2) {
         H a = fresh(x, x->level), b = fresh(x, x->level);
         int r[2] = {r1, r2};
@@ -356,9 +361,18 @@ std::pair<H, H> row_col_forms(Ev& E, const H& V) {
     } else {
         auto rt = E.rot2(V, -N, -((N * (N - 1)) >> 1));   // hoisted: one ModUp for both
         VR = E.add(V, rt.first);
-        for (int i = 1; i < k; i++) VR = E.rot_add(VR, -(N << i));
         VT = E.add(V, rt.second);
-        for (int i = 2; i <= k; i++) VT = E.rot_add(VT, -((N * (N - 1)) >> i));
+        if (V->B == 1 && k > 1) {
+            // the two chains in step, as one two-member stack with a key per member
+            const rk_ct* pair[2] = {VR.p, VT.p};
+            H S(ct_stack(E.c, pair, 2));
+            for (int i = 1; i < k; i++) S = E.rot_add_multi(S, {-(N << i), -((N * (N - 1)) >> (i + 1))});
+            VR = E.copy(H(ct_view(S.p, 0)));
+            VT = E.copy(H(ct_view(S.p, 1)));
+        } else {
+            for (int i = 1; i < k; i++) VR = E.rot_add(VR, -(N << i));
+            for (int i = 2; i <= k; i++) VT = E.rot_add(VT, -((N * (N - 1)) >> i));
+        }
     }
     H VC = E.mul_mask(VT, RK_MASK_COL0);                 // TransR's MaskC
     VC = repl_c(E, std::move(VC));

@@ -527,6 +527,67 @@ void ev_rotate_add(rk_ctx* c, const rk_ct* a, int r, rk_ct* out) {
     c->n_rot += (uint64_t)a->B;
 }
 
+// Member b of the stack `a` rotated left by r[b] (a different Galois element and key
+// per member), plus member b of `a` when `add`: one ModUp, ModDown and NTT launch for
+// the whole stack; the key inner product and the final combine run per member.
+void ev_rotate_multi(rk_ctx* c, const rk_ct* a, const int* r, bool add, rk_ct* out) {
+    RK_REQUIRE(out != a, RK_EINVAL, "rotate_multi: output aliases input");
+    RK_REQUIRE(out->B == a->B, RK_EINVAL, "rotate_multi: stack size mismatch");
+    const int B = a->B, l = a->level;
+    std::vector<u64> gs(B);
+    for (int b = 0; b < B; b++) {
+        gs[b] = galois_left(c, r[b]);
+        RK_REQUIRE(gs[b] == 1 || c->gal.count(gs[b]), RK_ENOKEY, "rotation key missing for r = " + std::to_string(r[b]));
+    }
+    bool all_keyed = !c->ks_fused;
+    for (int b = 0; b < B; b++) all_keyed = all_keyed && gs[b] != 1;
+    if (!all_keyed) {   // member by member (fused key switching, or a rotation by 0)
+        for (int b = 0; b < B; b++) {
+            rk_ct* ab = ct_view(a, b);
+            rk_ct* ob = ct_view(out, b);
+            try {
+                if (add) {
+                    ev_rotate_add(c, ab, r[b], ob);
+                } else {
+                    rk_ct* outs[1] = {ob};
+                    ev_rotate_many(c, ab, &r[b], 1, outs);
+                }
+            } catch (...) {
+                ct_free(ab);
+                ct_free(ob);
+                throw;
+            }
+            ct_free(ab);
+            ct_free(ob);
+        }
+        out->level = l;
+        copy_meta(out, a);
+        return;
+    }
+    const size_t ps = c->poly_stride(), n = c->n;
+    const int QP = l + 1 + c->alpha, beta = c->beta(l);
+    const u64* d = a->data + ps;
+    ks_lift(c, d, 2 * ps, l, B);
+    ks_lift_ext(c, d, 2 * ps, l, B);
+    Scratch S = scratch_layout(c);
+    const size_t es = (size_t)QP * n;
+    for (int b = 0; b < B; b++)
+        launch_ks_inner(c->env, S.ext + (size_t)b * beta * es, es, c->gal[gs[b]].ref(), S.u + (size_t)b * 2 * es, l, beta, gs[b],
+                        c->stream, 1);
+    launch_ntt_inverse(c->env, LimbSet{S.u + (size_t)(l + 1) * n, es, 2 * B, c->alpha, 0, 0, c->L + 1}, c->stream);
+    launch_moddown_conv(c->env, S.u, S.w, l, c->stream, 2 * B);
+    launch_ntt_forward(c->env, ls_q(S.w, (size_t)(l + 1) * n, 2 * B, l + 1), c->stream);
+    for (int b = 0; b < B; b++) {
+        const u64* ab = a->data + (size_t)b * 2 * ps;
+        launch_ks_combine(c->env, out->data + (size_t)b * 2 * ps, ps, ab, gs[b], nullptr, 2 * ps, S.u + (size_t)b * 2 * es,
+                          S.w + (size_t)b * 2 * (l + 1) * n, l, c->stream, 1, add ? ab : nullptr);
+    }
+    c->n_ks += (uint64_t)B;
+    c->n_rot += (uint64_t)B;
+    out->level = l;
+    copy_meta(out, a);
+}
+
 void ev_mul(rk_ctx* c, const rk_ct* a, const rk_ct* b, rk_ct* out) {
     RK_REQUIRE(a->level == b->level, RK_EINVAL, "mul: level mismatch");
     RK_REQUIRE(a->B == b->B && out->B == a->B, RK_EINVAL, "mul: stack size mismatch");

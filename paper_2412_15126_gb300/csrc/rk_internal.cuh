@@ -290,6 +290,7 @@ void ev_mul(rk_ctx* c, const rk_ct* a, const rk_ct* b, rk_ct* out);         // o
 void ev_mul_plain(rk_ctx* c, const rk_ct* a, uint32_t kind, uint32_t N, uint32_t Q, uint32_t n_real, rk_ct* out);
 void ev_rotate_many(rk_ctx* c, const rk_ct* a, const int* r, int k, rk_ct** outs);  // left rotations
 void ev_rotate_add(rk_ctx* c, const rk_ct* a, int r, rk_ct* out);               // a + (a <<< r)
+void ev_rotate_multi(rk_ctx* c, const rk_ct* a, const int* r, bool add, rk_ct* out);  // member b by r[b]
 void ev_add_plain(rk_ctx* c, const rk_ct* a, uint32_t kind, uint32_t N, uint32_t Q, uint32_t n_real, rk_ct* out);
 void ev_lincomb(rk_ctx* c, const std::vector<const rk_ct*>& xs, const std::vector<double>& cs, rk_ct* out);  // out at level-1
 void ev_level_down(rk_ctx* c, const rk_ct* a, int target, rk_ct* out);
