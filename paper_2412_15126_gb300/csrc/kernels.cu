@@ -383,7 +383,7 @@ void launch_ks_combine_rs(const KernelEnv& env, u64* out, size_t ps, const u64* 
 // single ciphertext keeps two accumulators and the digit loop stays unrolled.
 // SEEDED: the key holds b_j only and a_j is regenerated from the key's seed.
 template <int CH, bool SEEDED>
-__global__ void __launch_bounds__(TPB) k_ks_inner(const u64* __restrict__ ext, size_t ext_stride, const u64* __restrict__ key,
+__global__ void __launch_bounds__(TPB, (CH == 1 ? 6 : (CH == 2 ? 4 : (CH == 4 ? 3 : 2)))) k_ks_inner(const u64* __restrict__ ext, size_t ext_stride, const u64* __restrict__ key,
                                                   u64 seed, u64* __restrict__ u, int level, int L, int alpha, int beta, u64 galois,
                                                   int logn, int B, const PrimeConst* __restrict__ pc) {
     RK_KERNEL_PROLOGUE();
