@@ -378,12 +378,14 @@ void launch_ks_combine_rs(const KernelEnv& env, u64* out, size_t ps, const u64* 
 // Key-switching inner product (evaluation domain), automorphism fused:
 //   u_c[t][k] = sum_j ext[j][t][src(k)] * key[j][c][prime(t)][k]   (key times R)
 // ===========================================================================
-// Up to CH stacked ciphertexts per thread: each key word is read once per chunk.
-// CH is the smallest of 1, 2, 4, 8 that covers the stack (chunks of 8 beyond), so a
-// single ciphertext keeps two accumulators and the digit loop stays unrolled.
+// Up to CH stacked ciphertexts per thread: each key word is read (or regenerated)
+// once per chunk.  CH is the smallest of 1, 2, 4 that covers the stack (chunks of 4
+// beyond: eight members a thread held too many registers for the occupancy that
+// hides the key stream), so a single ciphertext keeps two accumulators and the digit
+// loop stays unrolled.
 // SEEDED: the key holds b_j only and a_j is regenerated from the key's seed.
 template <int CH, bool SEEDED>
-__global__ void __launch_bounds__(TPB, (CH == 1 ? 6 : (CH == 2 ? 4 : (CH == 4 ? 3 : 2)))) k_ks_inner(const u64* __restrict__ ext, size_t ext_stride, const u64* __restrict__ key,
+__global__ void __launch_bounds__(TPB, (CH == 1 ? 6 : (CH == 2 ? 4 : 3))) k_ks_inner(const u64* __restrict__ ext, size_t ext_stride, const u64* __restrict__ key,
                                                   u64 seed, u64* __restrict__ u, int level, int L, int alpha, int beta, u64 galois,
                                                   int logn, int B, const PrimeConst* __restrict__ pc) {
     RK_KERNEL_PROLOGUE();
@@ -434,7 +436,7 @@ void launch_ks_inner(const KernelEnv& env, const u64* ext, size_t ext_stride, Ke
     // algorithmic bytes: B lifted inputs read, the key (b and a, or b alone when
     // seeded) read once per chunk, B outputs written
     const double QP = level + 1 + env.alpha;
-    const int ch = B <= 1 ? 1 : B <= 2 ? 2 : B <= 4 ? 4 : 8;
+    const int ch = B <= 1 ? 1 : B <= 2 ? 2 : 4;
     const int chunks = (B + ch - 1) / ch;
     const double key_parts = key.seeded ? 1.0 : 2.0;
     ProfScope pf(env, KK_KS_INNER, st, 1, ((double)B * beta + key_parts * beta * chunks + 2.0 * B) * QP * 8.0 * env.n,
@@ -447,15 +449,13 @@ void launch_ks_inner(const KernelEnv& env, const u64* ext, size_t ext_stride, Ke
         switch (ch) {
             case 1: RK_KSI(1, true); break;
             case 2: RK_KSI(2, true); break;
-            case 4: RK_KSI(4, true); break;
-            default: RK_KSI(8, true); break;
+            default: RK_KSI(4, true); break;
         }
     } else {
         switch (ch) {
             case 1: RK_KSI(1, false); break;
             case 2: RK_KSI(2, false); break;
-            case 4: RK_KSI(4, false); break;
-            default: RK_KSI(8, false); break;
+            default: RK_KSI(4, false); break;
         }
     }
 #undef RK_KSI
