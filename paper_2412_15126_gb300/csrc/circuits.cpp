@@ -264,32 +264,99 @@ int baby_steps(int length) {
     return std::min(k, length);
 }
 
+// Products a_i * b_i (a_i and b_i of one level, all pairs of one level) as stacked
+// products of up to 16 members: one launch per kernel and one key stream for a group.
+// Each result is a view into its group's product, which `hold` keeps alive.
+static std::vector<H> mul_group(Ev& E, const std::vector<const rk_ct*>& a, const std::vector<const rk_ct*>& b,
+                                std::vector<H>& hold) {
+    const int n = (int)a.size(), B = a[0]->B;
+    const int per = std::max(1, 16 / B);
+    std::vector<H> out;
+    for (int g0 = 0; g0 < n; g0 += per) {
+        const int g = std::min(per, n - g0);
+        if (g == 1) {
+            H o(ct_clone_meta(a[g0], a[g0]->level));
+            ev_mul(E.c, a[g0], b[g0], o.p);
+            out.push_back(std::move(o));
+            continue;
+        }
+        H A(ct_stack(E.c, a.data() + g0, g)), Bs(ct_stack(E.c, b.data() + g0, g));
+        H P = E.mul(A, Bs);
+        for (int i = 0; i < g; i++) out.push_back(H(ct_view_range(P.p, i * B, B)));
+        hold.push_back(std::move(P));
+    }
+    return out;
+}
+
 // p(t) = sum_i c_i T_i(t), Paterson-Stockmeyer in the Chebyshev basis: baby steps T_1..T_k,
 // giant steps T_2m = 2 T_m^2 - 1; p = q T_m + r with m half the coefficient count,
 // q = c_m + sum_{j>=1} 2 c_{m+j} T_j, r = c_0 + sum_{i=1}^{m-1} (c_i - c_{2m-i}) T_i; a part of
 // k coefficients is sum_{i>=1} c_i T_i (one exact combination, one rescale) plus c_0.
+// The baby steps of one doubling (T_{2^(w-1)+1} .. T_{2^w}) and the products of one depth
+// of the split tree are independent: each group runs as stacked products.
 struct ChebPS {
     Ev& E;
     int k;
     std::map<int, H> T, G;
-    std::vector<H> TL;   // T_1..T_{k-1} at the leaf level
+    std::vector<H> TL;     // T_1..T_{k-1} at the leaf level
+    std::vector<H> hold;   // stacked products the views point into
     H leaf(const std::vector<double>& cc) {
         H o = E.lincomb(TL, cc.data() + 1);
         return E.add_const(o, cc[0]);
     }
-    H rec(const std::vector<double>& cc) {
-        if ((int)cc.size() == k) return leaf(cc);
+    struct Node {
+        std::vector<double> cc;
+        int q = -1, r = -1, depth = 0;
+    };
+    std::vector<Node> nodes;
+    int build(const std::vector<double>& cc, int depth) {
+        const int id = (int)nodes.size();
+        nodes.push_back(Node{cc, -1, -1, depth});
+        if ((int)cc.size() == k) return id;
         const int m = (int)cc.size() / 2;
         std::vector<double> q(m), r(m);
         q[0] = cc[m];
         for (int j = 1; j < m; j++) q[j] = 2.0 * cc[m + j];
         r[0] = cc[0];
         for (int i = 1; i < m; i++) r[i] = cc[i] - cc[2 * m - i];
-        H Qc = rec(q);
-        H Rc = rec(r);
-        const int lo = std::min(Qc->level, G[m]->level);
-        H Pm = E.mul(E.level_down(Qc, lo), E.level_down(G[m], lo));
-        return E.add(Pm, E.level_down(Rc, Pm->level));
+        const int qi = build(q, depth + 1);
+        const int ri = build(r, depth + 1);
+        nodes[id].q = qi;
+        nodes[id].r = ri;
+        return id;
+    }
+    // value of every node, deepest first: a node is Q T_m + R over its children
+    H eval(const std::vector<double>& c) {
+        nodes.clear();
+        build(c, 0);
+        int deepest = 0;
+        for (auto& nd : nodes) deepest = std::max(deepest, nd.depth);
+        std::vector<H> val(nodes.size());
+        for (size_t i = 0; i < nodes.size(); i++)
+            if (nodes[i].q < 0) val[i] = leaf(nodes[i].cc);
+        for (int d = deepest - 1; d >= 0; d--) {
+            std::vector<int> ids;
+            for (size_t i = 0; i < nodes.size(); i++)
+                if (nodes[i].depth == d && nodes[i].q >= 0) ids.push_back((int)i);
+            if (ids.empty()) continue;
+            const int m = (int)nodes[ids[0]].cc.size() / 2;
+            std::vector<H> qs, gs;   // T_m brought down once per distinct level
+            std::vector<const rk_ct*> a, b;
+            for (int id : ids) {
+                const H& Qc = val[nodes[id].q];
+                const int lo = std::min(Qc->level, G[m]->level);
+                qs.push_back(E.level_down(Qc, lo));
+                if (gs.empty() || gs.back()->level != lo) gs.push_back(E.level_down(G[m], lo));
+                a.push_back(qs.back().p);
+                b.push_back(gs.back().p);
+            }
+            std::vector<H> prods = mul_group(E, a, b, hold);
+            for (size_t i = 0; i < ids.size(); i++) {
+                const H& Rc = val[nodes[ids[i]].r];
+                val[ids[i]] = E.add(prods[i], E.level_down(Rc, prods[i]->level));
+            }
+        }
+        return std::move(val[0]);
     }
 };
 
@@ -299,12 +366,27 @@ H cheb_ps(Ev& E, const H& t, const std::vector<double>& c) {
     ChebPS ps{E, baby_steps(length)};
     const int k = ps.k;
     ps.T[1] = E.copy(t);
-    for (int i = 2; i <= k; i++) {
-        if (i % 2 == 0) {
-            ps.T[i] = E.add_const(prod2(E, ps.T[i / 2], ps.T[i / 2]), -1.0);
-        } else {
-            H y = prod2(E, ps.T[i / 2], ps.T[i / 2 + 1]);
-            ps.T[i] = E.sub(y, E.level_down(ps.T[1], y->level));
+    // baby steps by doubling: T_i for i in (w/2, w] from T_{i/2} and T_{i/2 + 1}, 2 a b
+    // with both operands at the lower level (prod2)
+    for (int w = 2; w <= k; w *= 2) {
+        std::vector<H> ops;
+        std::vector<const rk_ct*> a, b;
+        std::vector<int> idx;
+        for (int i = w / 2 + 1; i <= w; i++) {
+            const H& x = ps.T[i / 2];
+            const H& y = ps.T[i % 2 == 0 ? i / 2 : i / 2 + 1];
+            const int lo = std::min(x->level, y->level);
+            ops.push_back(E.level_down(x, lo));
+            a.push_back(ops.back().p);
+            ops.push_back(E.level_down(y, lo));
+            b.push_back(ops.back().p);
+            idx.push_back(i);
+        }
+        std::vector<H> prods = mul_group(E, a, b, ps.hold);
+        for (size_t j = 0; j < idx.size(); j++) {
+            const int i = idx[j];
+            H y2 = E.add(prods[j], prods[j]);
+            ps.T[i] = i % 2 == 0 ? E.add_const(y2, -1.0) : E.sub(y2, E.level_down(ps.T[1], y2->level));
         }
     }
     ps.G[k] = E.copy(ps.T[k]);
@@ -312,7 +394,7 @@ H cheb_ps(Ev& E, const H& t, const std::vector<double>& c) {
     int leaf_level = 1 << 30;
     for (int i = 1; i < k; i++) leaf_level = std::min(leaf_level, ps.T[i]->level);
     for (int i = 1; i < k; i++) ps.TL.push_back(E.level_down(ps.T[i], leaf_level));
-    return ps.rec(c);
+    return ps.eval(c);
 }
 
 int cheb_depth(int length) {
