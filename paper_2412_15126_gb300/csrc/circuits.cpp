@@ -300,10 +300,6 @@ struct ChebPS {
     std::map<int, H> T, G;
     std::vector<H> TL;     // T_1..T_{k-1} at the leaf level
     std::vector<H> hold;   // stacked products the views point into
-    H leaf(const std::vector<double>& cc) {
-        H o = E.lincomb(TL, cc.data() + 1);
-        return E.add_const(o, cc[0]);
-    }
     struct Node {
         std::vector<double> cc;
         int q = -1, r = -1, depth = 0;
@@ -332,8 +328,32 @@ struct ChebPS {
         int deepest = 0;
         for (auto& nd : nodes) deepest = std::max(deepest, nd.depth);
         std::vector<H> val(nodes.size());
+        // leaves: every combination of T_1..T_{k-1} lands in one member of a stack,
+        // which takes one rescale for all of them; then each adds its c_0
+        std::vector<int> leaves;
         for (size_t i = 0; i < nodes.size(); i++)
-            if (nodes[i].q < 0) val[i] = leaf(nodes[i].cc);
+            if (nodes[i].q < 0) leaves.push_back((int)i);
+        const int B = TL[0]->B, lvl = TL[0]->level;
+        RK_REQUIRE(lvl >= 1, RK_EDEPTH, "Chebyshev leaves: no level left");
+        H Lst(ct_alloc_like(TL[0].p, lvl, (int)leaves.size() * B));
+        std::vector<const rk_ct*> terms;
+        for (auto& t : TL) terms.push_back(t.p);
+        for (size_t j = 0; j < leaves.size(); j++) {
+            H v(ct_view_range(Lst.p, (int)j * B, B));
+            const std::vector<double>& cc = nodes[leaves[j]].cc;
+            ev_lincomb(E.c, terms, std::vector<double>(cc.begin() + 1, cc.end()), v.p, false);
+        }
+        // one rescale per group of up to 16 members (the scratch is sized by the stack)
+        const int per = std::max(1, 16 / B), nl = (int)leaves.size();
+        for (int j0 = 0; j0 < nl; j0 += per) {
+            H v(ct_view_range(Lst.p, j0 * B, std::min(per, nl - j0) * B));
+            v->level = lvl;
+            ev_rescale_inplace(E.c, v.p);
+        }
+        Lst->level = lvl - 1;
+        for (size_t j = 0; j < leaves.size(); j++)
+            val[leaves[j]] = E.add_const(H(ct_view_range(Lst.p, (int)j * B, B)), nodes[leaves[j]].cc[0]);
+        hold.push_back(std::move(Lst));
         for (int d = deepest - 1; d >= 0; d--) {
             std::vector<int> ids;
             for (size_t i = 0; i < nodes.size(); i++)

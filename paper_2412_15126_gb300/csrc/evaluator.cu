@@ -347,7 +347,13 @@ void ev_add_plain(rk_ctx* c, const rk_ct* a, uint32_t kind, uint32_t N, uint32_t
     copy_meta(out, a);
 }
 
-void ev_lincomb(rk_ctx* c, const std::vector<const rk_ct*>& xs, const std::vector<double>& cs, rk_ct* out) {
+rk_ct* ct_alloc_like(const rk_ct* like, int level, int B) {
+    rk_ct* o = ct_alloc(like->ctx, level, B);
+    copy_meta(o, like);
+    return o;
+}
+
+void ev_lincomb(rk_ctx* c, const std::vector<const rk_ct*>& xs, const std::vector<double>& cs, rk_ct* out, bool rescale) {
     RK_REQUIRE(!xs.empty() && xs.size() == cs.size(), RK_EINVAL, "lincomb: bad term lists");
     const int l = xs[0]->level;
     RK_REQUIRE(l >= 1, RK_EDEPTH, "lincomb: no level left");
@@ -373,7 +379,7 @@ void ev_lincomb(rk_ctx* c, const std::vector<const rk_ct*>& xs, const std::vecto
     }
     out->level = l;
     copy_meta(out, xs[0]);
-    ev_rescale_inplace(c, out);
+    if (rescale) ev_rescale_inplace(c, out);
 }
 
 // ---------------------------------------------------------------------------

@@ -277,6 +277,7 @@ rk_ct* ct_stack(rk_ctx* c, const rk_ct* const* in, int count);        // B = cou
 void ct_unstack(rk_ctx* c, const rk_ct* in, rk_ct** outs);            // B outputs of B = 1
 void key_export(rk_ctx* c, const SwitchKeyDev& key, u64* host_out);
 size_t key_words(const rk_ctx* c, const SwitchKeyDev& key);
+rk_ct* ct_alloc_like(const rk_ct* like, int level, int B);   // vector metadata of `like`, B members
 rk_ct* ct_view(const rk_ct* stack, int b);                            // member b, no copy
 rk_ct* ct_view_range(const rk_ct* stack, int first, int count);      // members [first, first+count), no copy
 
@@ -292,7 +293,8 @@ void ev_rotate_many(rk_ctx* c, const rk_ct* a, const int* r, int k, rk_ct** outs
 void ev_rotate_add(rk_ctx* c, const rk_ct* a, int r, rk_ct* out);               // a + (a <<< r)
 void ev_rotate_multi(rk_ctx* c, const rk_ct* a, const int* r, bool add, rk_ct* out);  // member b by r[b]
 void ev_add_plain(rk_ctx* c, const rk_ct* a, uint32_t kind, uint32_t N, uint32_t Q, uint32_t n_real, rk_ct* out);
-void ev_lincomb(rk_ctx* c, const std::vector<const rk_ct*>& xs, const std::vector<double>& cs, rk_ct* out);  // out at level-1
+void ev_lincomb(rk_ctx* c, const std::vector<const rk_ct*>& xs, const std::vector<double>& cs, rk_ct* out,
+                bool rescale = true);   // sum c_i x_i, then a rescale unless told not to  // out at level-1
 void ev_level_down(rk_ctx* c, const rk_ct* a, int target, rk_ct* out);
 void ev_copy(rk_ctx* c, const rk_ct* a, rk_ct* out);
 
