@@ -397,6 +397,8 @@ rk_status rk_server_submit(rk_ctx* ctx, uint32_t op, uint32_t arg, uint32_t flag
  * up to timeout_s seconds (0: poll, negative: no limit).  A failed request returns its
  * error status.  Each ticket is collected once; RK_EINVAL for unknown tickets. */
 rk_status rk_server_wait(rk_ctx* ctx, uint64_t ticket, double timeout_s, rk_ct** out);
+/* rk_server_wait without waiting: *out = the result, or NULL while it is pending. */
+rk_status rk_server_poll(rk_ctx* ctx, uint64_t ticket, rk_ct** out);
 /* out[8]: requests finished, p50 and p99 and max latency (s, submit to result on the
  * device), batches run, mean batch size, peak device memory in use on the whole device
  * above the level at rk_server_start (bytes; includes other users of the device),

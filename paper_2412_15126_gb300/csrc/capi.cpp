@@ -686,6 +686,8 @@ rk_status rk_server_wait(rk_ctx* ctx, uint64_t ticket, double timeout_s, rk_ct**
     });
 }
 
+rk_status rk_server_poll(rk_ctx* ctx, uint64_t ticket, rk_ct** out) { return rk_server_wait(ctx, ticket, 0.0, out); }
+
 rk_status rk_server_stats(rk_ctx* ctx, double out[8]) {
     return guard([&] {
         need(ctx, "ctx");

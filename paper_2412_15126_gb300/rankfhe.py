@@ -115,6 +115,7 @@ _sig("rk_keys_import", [_vp, ctypes.c_void_p, _sz])
 _sig("rk_server_start", [_vp, _sz, _u32])
 _sig("rk_server_submit", [_vp, _u32, _u32, _u32, _vp, ctypes.POINTER(ctypes.c_uint64)])
 _sig("rk_server_wait", [_vp, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(_vp)])
+_sig("rk_server_poll", [_vp, ctypes.c_uint64, ctypes.POINTER(_vp)])
 _sig("rk_server_stats", [_vp, _dp])
 _sig("rk_server_stop", [_vp])
 _sig("rk_server_latencies", [_vp, _dp, _sz, ctypes.POINTER(_sz)])
@@ -446,6 +447,10 @@ class Context:
         self._server_inputs.pop(ticket, None)
         return Ciphertext(self, h.value)
 
+
+    def server_poll(self, ticket: int):
+        """The finished request's result, or None while it is pending (no waiting)."""
+        return self.server_wait(ticket, 0.0)
     def server_stats(self) -> dict:
         out = (ctypes.c_double * 8)()
         _check(_L.rk_server_stats(self.handle, out))
