@@ -321,39 +321,55 @@ struct ChebPS {
         nodes[id].r = ri;
         return id;
     }
-    // value of every node, deepest first: a node is Q T_m + R over its children
+    // depth first, one leaf at a time (little memory: for wide stacks)
+    H rec(const std::vector<double>& cc) {
+        if ((int)cc.size() == k) {
+            H o = E.lincomb(TL, cc.data() + 1);
+            return E.add_const(o, cc[0]);
+        }
+        const int m = (int)cc.size() / 2;
+        std::vector<double> q(m), r(m);
+        q[0] = cc[m];
+        for (int j = 1; j < m; j++) q[j] = 2.0 * cc[m + j];
+        r[0] = cc[0];
+        for (int i = 1; i < m; i++) r[i] = cc[i] - cc[2 * m - i];
+        H Qc = rec(q);
+        H Rc = rec(r);
+        const int lo = std::min(Qc->level, G[m]->level);
+        H Pm = E.mul(E.level_down(Qc, lo), E.level_down(G[m], lo));
+        return E.add(Pm, E.level_down(Rc, Pm->level));
+    }
+    // value of every node, deepest first: a node is Q T_m + R over its children; all
+    // leaves are held at once, so this form is for stacks of at most two members
     H eval(const std::vector<double>& c) {
         nodes.clear();
         build(c, 0);
         int deepest = 0;
         for (auto& nd : nodes) deepest = std::max(deepest, nd.depth);
         std::vector<H> val(nodes.size());
-        // leaves: every combination of T_1..T_{k-1} lands in one member of a stack,
-        // which takes one rescale for all of them; then each adds its c_0
+        // leaves: the combinations of T_1..T_{k-1} of a group land in the members of one
+        // stack (up to 16 members), which takes one rescale; then each adds its c_0
         std::vector<int> leaves;
         for (size_t i = 0; i < nodes.size(); i++)
             if (nodes[i].q < 0) leaves.push_back((int)i);
         const int B = TL[0]->B, lvl = TL[0]->level;
         RK_REQUIRE(lvl >= 1, RK_EDEPTH, "Chebyshev leaves: no level left");
-        H Lst(ct_alloc_like(TL[0].p, lvl, (int)leaves.size() * B));
         std::vector<const rk_ct*> terms;
         for (auto& t : TL) terms.push_back(t.p);
-        for (size_t j = 0; j < leaves.size(); j++) {
-            H v(ct_view_range(Lst.p, (int)j * B, B));
-            const std::vector<double>& cc = nodes[leaves[j]].cc;
-            ev_lincomb(E.c, terms, std::vector<double>(cc.begin() + 1, cc.end()), v.p, false);
-        }
-        // one rescale per group of up to 16 members (the scratch is sized by the stack)
         const int per = std::max(1, 16 / B), nl = (int)leaves.size();
         for (int j0 = 0; j0 < nl; j0 += per) {
-            H v(ct_view_range(Lst.p, j0 * B, std::min(per, nl - j0) * B));
-            v->level = lvl;
-            ev_rescale_inplace(E.c, v.p);
+            const int g = std::min(per, nl - j0);
+            H Lst(ct_alloc_like(TL[0].p, lvl, g * B));
+            for (int j = 0; j < g; j++) {
+                H v(ct_view_range(Lst.p, j * B, B));
+                const std::vector<double>& cc = nodes[leaves[j0 + j]].cc;
+                ev_lincomb(E.c, terms, std::vector<double>(cc.begin() + 1, cc.end()), v.p, false);
+            }
+            Lst->level = lvl;
+            ev_rescale_inplace(E.c, Lst.p);
+            for (int j = 0; j < g; j++)
+                val[leaves[j0 + j]] = E.add_const(H(ct_view_range(Lst.p, j * B, B)), nodes[leaves[j0 + j]].cc[0]);
         }
-        Lst->level = lvl - 1;
-        for (size_t j = 0; j < leaves.size(); j++)
-            val[leaves[j]] = E.add_const(H(ct_view_range(Lst.p, (int)j * B, B)), nodes[leaves[j]].cc[0]);
-        hold.push_back(std::move(Lst));
         for (int d = deepest - 1; d >= 0; d--) {
             std::vector<int> ids;
             for (size_t i = 0; i < nodes.size(); i++)
@@ -388,25 +404,27 @@ H cheb_ps(Ev& E, const H& t, const std::vector<double>& c) {
     ps.T[1] = E.copy(t);
     // baby steps by doubling: T_i for i in (w/2, w] from T_{i/2} and T_{i/2 + 1}, 2 a b
     // with both operands at the lower level (prod2)
+    const int per = std::max(1, 16 / t->B);   // products a stacked group holds
     for (int w = 2; w <= k; w *= 2) {
-        std::vector<H> ops;
-        std::vector<const rk_ct*> a, b;
-        std::vector<int> idx;
-        for (int i = w / 2 + 1; i <= w; i++) {
-            const H& x = ps.T[i / 2];
-            const H& y = ps.T[i % 2 == 0 ? i / 2 : i / 2 + 1];
-            const int lo = std::min(x->level, y->level);
-            ops.push_back(E.level_down(x, lo));
-            a.push_back(ops.back().p);
-            ops.push_back(E.level_down(y, lo));
-            b.push_back(ops.back().p);
-            idx.push_back(i);
-        }
-        std::vector<H> prods = mul_group(E, a, b, ps.hold);
-        for (size_t j = 0; j < idx.size(); j++) {
-            const int i = idx[j];
-            H y2 = E.add(prods[j], prods[j]);
-            ps.T[i] = i % 2 == 0 ? E.add_const(y2, -1.0) : E.sub(y2, E.level_down(ps.T[1], y2->level));
+        for (int i0 = w / 2 + 1; i0 <= w; i0 += per) {
+            std::vector<H> ops, hold;
+            std::vector<const rk_ct*> a, b;
+            const int i1 = std::min(w, i0 + per - 1);
+            for (int i = i0; i <= i1; i++) {
+                const H& x = ps.T[i / 2];
+                const H& y = ps.T[i % 2 == 0 ? i / 2 : i / 2 + 1];
+                const int lo = std::min(x->level, y->level);
+                ops.push_back(E.level_down(x, lo));
+                a.push_back(ops.back().p);
+                ops.push_back(E.level_down(y, lo));
+                b.push_back(ops.back().p);
+            }
+            std::vector<H> prods = mul_group(E, a, b, hold);
+            for (int i = i0; i <= i1; i++) {
+                const H& p = prods[i - i0];
+                H y2 = E.add(p, p);
+                ps.T[i] = i % 2 == 0 ? E.add_const(y2, -1.0) : E.sub(y2, E.level_down(ps.T[1], y2->level));
+            }
         }
     }
     ps.G[k] = E.copy(ps.T[k]);
@@ -414,7 +432,7 @@ H cheb_ps(Ev& E, const H& t, const std::vector<double>& c) {
     int leaf_level = 1 << 30;
     for (int i = 1; i < k; i++) leaf_level = std::min(leaf_level, ps.T[i]->level);
     for (int i = 1; i < k; i++) ps.TL.push_back(E.level_down(ps.T[i], leaf_level));
-    return ps.eval(c);
+    return t->B <= 2 ? ps.eval(c) : ps.rec(c);
 }
 
 int cheb_depth(int length) {
