@@ -73,3 +73,20 @@ def test_autotune_keeps_results():
         assert np.array_equal(before, after)
     finally:
         ctx.close()
+
+
+def test_fused_rank_equals_staged():
+    """A whole rank (hoisted pair of rotations, the ReplR/TransR chains as one stack
+    with a key per member, products with the single-rounding ModDown) through fused
+    key switching equals the staged path bit for bit."""
+    ctx = helpers.gpu_context("cfg1")
+    try:
+        ctx.keygen(31, 8)
+        ct = ctx.encrypt(inputs.gap_vector(8, 0.05, 6), N=8)
+        staged = ctx.rank(ct).export()
+        ctx.set_option(rankfhe.OPT_KS_FUSED, 1)
+        fused = ctx.rank(ct).export()
+        ctx.set_option(rankfhe.OPT_KS_FUSED, 0)
+        assert np.array_equal(staged, fused)
+    finally:
+        ctx.close()
