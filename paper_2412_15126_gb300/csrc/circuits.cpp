@@ -182,9 +182,22 @@ const double kG[4] = {4589.0 / 1024, -16577.0 / 1024, 25614.0 / 1024, -12860.0 /
 H poly7(Ev& E, const H& x, const double c[4]) {
     const double c1 = c[0], c3 = c[1], c5 = c[2], c7 = c[3];
     H y = E.mul(x, x);                        // x^2      (l-1)
-    H z = E.mul(y, y);                        // x^4      (l-2)
     H x1 = E.mul_scalar(x, 1.0);              // x        (l-1)
-    H b7 = E.mul(E.mul_scalar(x, c7), y);     // c7 x^3   (l-2)
+    H c7x = E.mul_scalar(x, c7);              // c7 x     (l-1)
+    H P, z, b7;                               // x^4, c7 x^3 (l-2)
+    if (x->B == 1) {
+        // the two products of level l-1 as one two-member stack (no operand copies);
+        // z and b7 are views into P, which outlives them
+        const rk_ct* lhs[2] = {y.p, c7x.p};
+        const rk_ct* rhs[2] = {y.p, y.p};
+        P = H(ct_alloc_like(y.p, y->level, 2));
+        ev_mul_pairs(E.c, lhs, rhs, 2, P.p);
+        z = H(ct_view(P.p, 0));
+        b7 = H(ct_view(P.p, 1));
+    } else {
+        z = E.mul(y, y);
+        b7 = E.mul(c7x, y);
+    }
     H a5 = E.mul_scalar(x1, c5);              // c5 x     (l-2)
     H hz = E.mul(E.add(a5, b7), z);           // c5 x^5 + c7 x^7 (l-3)
     H x2 = E.mul_scalar(x1, 1.0);             // x        (l-2)

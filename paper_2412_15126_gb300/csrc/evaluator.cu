@@ -594,21 +594,15 @@ void ev_rotate_multi(rk_ctx* c, const rk_ct* a, const int* r, bool add, rk_ct* o
     copy_meta(out, a);
 }
 
-void ev_mul(rk_ctx* c, const rk_ct* a, const rk_ct* b, rk_ct* out) {
-    RK_REQUIRE(a->level == b->level, RK_EINVAL, "mul: level mismatch");
-    RK_REQUIRE(a->B == b->B && out->B == a->B, RK_EINVAL, "mul: stack size mismatch");
-    const int l = a->level, B = a->B;
-    RK_REQUIRE(l >= 1, RK_EDEPTH, "mul: no level left");
-    RK_REQUIRE(c->rlk.data, RK_ENOKEY, "relinearisation key missing");
-    ensure_batch(c, B);
+// The relinearisation and rescale of B tensor products already in S.d ([B][3][l+1][n]),
+// into out ([B] members at level l - 1).
+static void mul_finish(rk_ctx* c, int l, int B, const rk_ct* meta, rk_ct* out) {
     Scratch S = scratch_layout(c);
-    const size_t pl = (size_t)(l + 1) * c->n;
-    launch_tensor(c->env, S.d, a->data, b->data, l + 1, c->poly_stride(), c->stream, B);
+    const size_t n = c->n, pl = (size_t)(l + 1) * n;
     ks_lift(c, S.d + 2 * pl, 3 * pl, l, B);
     if (!c->ks_fused) ks_lift_ext(c, S.d + 2 * pl, 3 * pl, l, B);
     ks_inner(c, c->rlk.ref(), l, 0, S.d + 2 * pl, 3 * pl, B, !c->ks_fused);
     // ModDown and rescale in one rounding: (P d_p + u_p) / (q_l P) over q_0 .. q_(l-1)
-    const size_t n = c->n;
     const int QP = l + 1 + c->alpha;
     const u64 ql = c->primes[l];
     u64 pm = 1 % ql;
@@ -619,10 +613,41 @@ void ev_mul(rk_ctx* c, const rk_ct* a, const rk_ct* b, rk_ct* out) {
     launch_ntt_forward(c->env, ls_q(S.w, (size_t)l * n, 2 * B, l), c->stream);
     launch_ks_combine_rs(c->env, out->data, c->poly_stride(), S.u, S.w, S.d, l, c->stream, B);
     out->level = l - 1;
-    copy_meta(out, a);
+    copy_meta(out, meta);
     c->n_ks += (uint64_t)B;
     c->n_mul += (uint64_t)B;
     c->n_rescale++;
+}
+
+void ev_mul(rk_ctx* c, const rk_ct* a, const rk_ct* b, rk_ct* out) {
+    RK_REQUIRE(a->level == b->level, RK_EINVAL, "mul: level mismatch");
+    RK_REQUIRE(a->B == b->B && out->B == a->B, RK_EINVAL, "mul: stack size mismatch");
+    const int l = a->level, B = a->B;
+    RK_REQUIRE(l >= 1, RK_EDEPTH, "mul: no level left");
+    RK_REQUIRE(c->rlk.data, RK_ENOKEY, "relinearisation key missing");
+    ensure_batch(c, B);
+    Scratch S = scratch_layout(c);
+    launch_tensor(c->env, S.d, a->data, b->data, l + 1, c->poly_stride(), c->stream, B);
+    mul_finish(c, l, B, a, out);
+}
+
+// Products a[i] * b[i] of separate single ciphertexts of one level as one stack: a
+// tensor launch per pair writes member i of the scratch, then one relinearisation and
+// rescale for all; out is a stack of n members.
+void ev_mul_pairs(rk_ctx* c, const rk_ct* const* a, const rk_ct* const* b, int n, rk_ct* out) {
+    RK_REQUIRE(n >= 1 && out->B == n, RK_EINVAL, "mul_pairs: output must hold one member a pair");
+    const int l = a[0]->level;
+    RK_REQUIRE(l >= 1, RK_EDEPTH, "mul_pairs: no level left");
+    RK_REQUIRE(c->rlk.data, RK_ENOKEY, "relinearisation key missing");
+    for (int i = 0; i < n; i++)
+        RK_REQUIRE(a[i]->level == l && b[i]->level == l && a[i]->B == 1 && b[i]->B == 1, RK_EINVAL,
+                   "mul_pairs: single ciphertexts of one level");
+    ensure_batch(c, n);
+    Scratch S = scratch_layout(c);
+    const size_t pl = (size_t)(l + 1) * c->n;
+    for (int i = 0; i < n; i++)
+        launch_tensor(c->env, S.d + (size_t)i * 3 * pl, a[i]->data, b[i]->data, l + 1, c->poly_stride(), c->stream, 1);
+    mul_finish(c, l, n, a[0], out);
 }
 
 // Times one top-level rotation with the staged key switching and with the fused

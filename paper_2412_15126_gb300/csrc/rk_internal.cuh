@@ -288,6 +288,7 @@ void ev_add_const(rk_ctx* c, const rk_ct* a, double v, rk_ct* out);
 void ev_rescale_inplace(rk_ctx* c, rk_ct* a);
 void ev_mul_scalar(rk_ctx* c, const rk_ct* a, double v, rk_ct* out);        // out at level-1
 void ev_mul(rk_ctx* c, const rk_ct* a, const rk_ct* b, rk_ct* out);         // out at level-1
+void ev_mul_pairs(rk_ctx* c, const rk_ct* const* a, const rk_ct* const* b, int n, rk_ct* out);   // stack of a[i] b[i]
 void ev_mul_plain(rk_ctx* c, const rk_ct* a, uint32_t kind, uint32_t N, uint32_t Q, uint32_t n_real, rk_ct* out);
 void ev_rotate_many(rk_ctx* c, const rk_ct* a, const int* r, int k, rk_ct** outs);  // left rotations
 void ev_rotate_add(rk_ctx* c, const rk_ct* a, int r, rk_ct* out);               // a + (a <<< r)
