@@ -185,15 +185,16 @@ H poly7(Ev& E, const H& x, const double c[4]) {
     H x1 = E.mul_scalar(x, 1.0);              // x        (l-1)
     H c7x = E.mul_scalar(x, c7);              // c7 x     (l-1)
     H P, z, b7;                               // x^4, c7 x^3 (l-2)
-    if (x->B == 1) {
-        // the two products of level l-1 as one two-member stack (no operand copies);
-        // z and b7 are views into P, which outlives them
+    if (x->B <= 8) {
+        // the two products of level l-1 as one stack of twice the members (no operand
+        // copies); z and b7 are views into P, which outlives them
+        const int B = x->B;
         const rk_ct* lhs[2] = {y.p, c7x.p};
         const rk_ct* rhs[2] = {y.p, y.p};
-        P = H(ct_alloc_like(y.p, y->level, 2));
+        P = H(ct_alloc_like(y.p, y->level, 2 * B));
         ev_mul_pairs(E.c, lhs, rhs, 2, P.p);
-        z = H(ct_view(P.p, 0));
-        b7 = H(ct_view(P.p, 1));
+        z = H(ct_view_range(P.p, 0, B));
+        b7 = H(ct_view_range(P.p, B, B));
     } else {
         z = E.mul(y, y);
         b7 = E.mul(c7x, y);

@@ -631,23 +631,24 @@ void ev_mul(rk_ctx* c, const rk_ct* a, const rk_ct* b, rk_ct* out) {
     mul_finish(c, l, B, a, out);
 }
 
-// Products a[i] * b[i] of separate single ciphertexts of one level as one stack: a
-// tensor launch per pair writes member i of the scratch, then one relinearisation and
-// rescale for all; out is a stack of n members.
+// Products a[i] * b[i] of separate ciphertexts (or stacks of one size B) of one level
+// as one stack: a tensor launch per pair writes members [i B, (i+1) B) of the scratch,
+// then one relinearisation and rescale for all; out is a stack of n B members.
 void ev_mul_pairs(rk_ctx* c, const rk_ct* const* a, const rk_ct* const* b, int n, rk_ct* out) {
-    RK_REQUIRE(n >= 1 && out->B == n, RK_EINVAL, "mul_pairs: output must hold one member a pair");
-    const int l = a[0]->level;
+    RK_REQUIRE(n >= 1, RK_EINVAL, "mul_pairs: no pairs");
+    const int l = a[0]->level, B = a[0]->B;
+    RK_REQUIRE(out->B == n * B, RK_EINVAL, "mul_pairs: output must hold every pair's members");
     RK_REQUIRE(l >= 1, RK_EDEPTH, "mul_pairs: no level left");
     RK_REQUIRE(c->rlk.data, RK_ENOKEY, "relinearisation key missing");
     for (int i = 0; i < n; i++)
-        RK_REQUIRE(a[i]->level == l && b[i]->level == l && a[i]->B == 1 && b[i]->B == 1, RK_EINVAL,
-                   "mul_pairs: single ciphertexts of one level");
-    ensure_batch(c, n);
+        RK_REQUIRE(a[i]->level == l && b[i]->level == l && a[i]->B == B && b[i]->B == B, RK_EINVAL,
+                   "mul_pairs: operands of one level and stack size");
+    ensure_batch(c, n * B);
     Scratch S = scratch_layout(c);
     const size_t pl = (size_t)(l + 1) * c->n;
     for (int i = 0; i < n; i++)
-        launch_tensor(c->env, S.d + (size_t)i * 3 * pl, a[i]->data, b[i]->data, l + 1, c->poly_stride(), c->stream, 1);
-    mul_finish(c, l, n, a[0], out);
+        launch_tensor(c->env, S.d + (size_t)i * B * 3 * pl, a[i]->data, b[i]->data, l + 1, c->poly_stride(), c->stream, B);
+    mul_finish(c, l, n * B, a[0], out);
 }
 
 // Times one top-level rotation with the staged key switching and with the fused
