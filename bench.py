@@ -47,7 +47,7 @@ def workload_config(extra=None):
     cfg = {"workload": "rank N=128, n=2^16, 28+3 limbs, scale 2^45, dnum digits of 3, Cmp g^4 f^2",
            "vector_len": WORKLOAD["N"], "ring_degree": 1 << WORKLOAD["log_n"], "limbs": WORKLOAD["n_limbs"],
            "special_primes": WORKLOAD["n_special"], "gap": "2^-9",
-           "l2": "working set larger than L2 (rotation keys ~8.7 GB read every step)"}
+           "l2": "working set larger than L2 (seeded rotation and relinearisation keys, ~4.4 GB of b parts, read every step)"}
     if extra:
         cfg.update(extra)
     return cfg
