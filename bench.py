@@ -5,14 +5,17 @@ Workload: rank of a 128-element vector, values uniform in [0, 1) with pairwise
 gap >= 2^-9 (seeded), RNS-CKKS with n = 2^16, 28 limbs (scale 2^45) plus 3
 special primes, digits of 3 limbs, comparator g^4 then f^2 (Sec. 2.2).  One step
 = one complete rank circuit on one encrypted vector (ReplR, TransR, ReplC, Cmp,
-SumR), inputs already resident in HBM; the rotation keys (8.7 GB) exceed L2, so
-every step streams from HBM.
+SumR), inputs already resident in HBM; the seeded switching keys (4.4 GB of b
+parts) exceed L2, so every step streams them from HBM.
 
 Reported (one JSON line from rank 0):
   value          seconds per rank (CUDA events on the library stream), max over ranks
   e2e            the same through the C-ABI from pinned host ciphertexts, with the
                  host->device import and the device->host export of the result timed
-  roofline       the profiled kernel's algorithmic bytes / its event-timed duration
+  roofline       the forward NTT's butterflies / its event-timed duration (every
+                 fourth timed step's launches), against the issue and the integer-
+                 multiplier ceilings; roofline_hbm the same for the key inner product
+                 in bytes against the measured HBM copy rate
   cpu_baseline   the oracle (plain CPU RNS-CKKS) on a bounded sample, scaled to a rank
   clocks         nvidia-smi SM clocks sampled during the timed region
   gpu_launches   kernels this library launched inside the timed region
