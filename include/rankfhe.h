@@ -159,7 +159,9 @@ rk_status rk_autotune(rk_ctx* ctx, double* report, size_t cap, size_t* count);
 /* Generate secret, public, relinearisation key and the rotation (Galois) keys
  * the circuits need for every power-of-two length N <= max_len (Sec. 3.1: the
  * rotations of ReplR, ReplC, TransR, SumR, SumC, TransC), on the device, from
- * `seed` (SplitMix64 counter stream).  Errors: RK_EINVAL, RK_ENOMEM, RK_ECUDA. */
+ * `seed` (SplitMix64 counter stream).  The switching keys are seeded (see
+ * rk_key_import_seeded): only their b parts are stored.
+ * Errors: RK_EINVAL, RK_ENOMEM, RK_ECUDA. */
 rk_status rk_keygen(rk_ctx* ctx, uint64_t seed, uint32_t max_len);
 
 /* Add rotation keys for left rotations by r[i] slots (negative = right). */
@@ -192,7 +194,8 @@ rk_status rk_key_import_seeded(rk_ctx* ctx, uint32_t kind, uint64_t galois, uint
 /* Every switching key of the context (relinearisation, then Galois keys by element)
  * as one blob of little-endian 64-bit words: magic "RKKEYS02", log_n, L+1+alpha,
  * beta_L, the key count K, then K records [kind][galois][seeded][seed][words][words
- * of rk_key_import's layout, or of rk_key_import_seeded's when seeded is 1].  buf NULL: *len receives the size only; otherwise buf
+ * of rk_key_import's layout, or of rk_key_import_seeded's when seeded is 1].
+ * buf NULL: *len receives the size only; otherwise buf
  * (8-byte aligned, cap >= *len bytes) receives the blob.  The secret is not included.
  * Errors: RK_EINVAL (buffer too small or unaligned), RK_ECUDA. */
 rk_status rk_keys_export(rk_ctx* ctx, uint8_t* buf, size_t cap, size_t* len);
@@ -305,8 +308,10 @@ rk_status rk_rescale_noalloc(rk_ctx* ctx, const uint64_t* d_in, uint64_t* d_out,
 
 /* Rank (Alg. 3): fractional ranks of the vector in row 0 of `in` (fresh, top
  * level), in row 0 of the output.  flags: RK_TIES_CORRECT adds the tie-correction
- * offset of Alg. 6.  Errors: RK_EDEPTH if the parameters lack the levels,
- * RK_ENOKEY, RK_EINVAL. */
+ * offset of Alg. 6.  The circuit takes 2 + the comparison's levels (+1 for a padded
+ * vector, +2 with RK_TIES_CORRECT); with RK_OPT_TRIM_LEVELS the input is first
+ * brought down to that many levels plus the level the result must keep.
+ * Errors: RK_EDEPTH if the parameters lack the levels, RK_ENOKEY, RK_EINVAL. */
 rk_status rk_rank(rk_ctx* ctx, const rk_ct* in, uint32_t flags, rk_ct** out);
 
 /* Comparison matrix (Alg. 3 lines 1-3): C = Cmp(ReplR(V), ReplC(TransR(V))), slot
