@@ -16,12 +16,13 @@ Reported (one JSON line from rank 0):
                  fourth timed step's launches), against the issue and the integer-
                  multiplier ceilings; roofline_hbm the same for the key inner product
                  in bytes against the measured HBM copy rate
-  cpu_baseline   the oracle (plain CPU RNS-CKKS) on a bounded sample, scaled to a rank
+  cpu_baseline   one complete rank on the oracle (plain CPU RNS-CKKS) on the host cores
   clocks         nvidia-smi SM clocks sampled during the timed region
   gpu_launches   kernels this library launched inside the timed region
 
 `--impl reference` times the oracle itself (the CPU reference of this project) on
-the same workload: each step is the bounded sample described in `cpu_baseline`.
+the same workload: each step is one complete oracle rank, as many as fit a bounded
+host budget (the line reports the steps actually run).
 """
 from __future__ import annotations
 
@@ -430,12 +431,15 @@ GB300_SMS, GB300_SCHEDULERS, GB300_MAX_SM_MHZ = 152, 4, 2070.0
 PROF_EVERY = 4   # timed steps whose kernel launches the roofline events bracket: every 4th
 
 
-def ntt_roofline(prof, clk):
-    """Forward NTT (both passes), the dominant kernel: bound by integer issue, so the
-    ceiling is the SMs' issue rate (152 SMs x 4 schedulers x one warp instruction a
-    clock at the maximum SM clock) divided by the instructions one radix-2 butterfly
-    costs in this kernel (ncu capture in profiles/traffic.json).  achieved = butterflies
-    per launch / CUDA-event launch duration."""
+def ntt_roofline(prof, clk, alu=None):
+    """Forward NTT (both passes), the dominant kernel: bound by integer arithmetic, so
+    the ceiling is the device's measured butterfly rate (rk_measure_alu: the same
+    Cooley-Tukey butterfly with its operands in registers, no memory traffic, over
+    every SM).  achieved = butterflies per launch / CUDA-event launch duration.  Also
+    reported: the SMs' issue rate (152 SMs x 4 schedulers x one warp instruction a
+    clock at the maximum SM clock) divided by the instructions one butterfly costs in
+    this kernel (ncu capture in profiles/traffic.json), and the integer-multiplier
+    pipe's rate over its busy cycles a butterfly."""
     if not prof["launches"] or prof["ms"] <= 0:
         return None
     per_launch = prof["ops"] / prof["launches"]
@@ -457,14 +461,74 @@ def ntt_roofline(prof, clk):
         # the integer multiplier (FMA-heavy) pipe: one busy cycle of each of the 608
         # sub-partitions per clock, hpb busy cycles a butterfly
         mul_peak = GB300_SMS * GB300_SCHEDULERS * GB300_MAX_SM_MHZ * 1e6 / hpb / 1e9
-    return {"bound": "alu", "kernel": "ntt_fwd (column + row pass)", "achieved": achieved, "peak": peak,
-            "peak_kind": "derived: 152 SMs x 4 schedulers x 1 warp instruction/clock x 2070 MHz / instructions per "
-                         "butterfly (ncu)", "unit": "Gbutterfly/s", "frac": (achieved / peak) if peak else None,
+    bpeak = alu["butterfly_per_s"] / 1e9 if alu and alu.get("butterfly_per_s") else None
+    return {"bound": "alu", "kernel": "ntt_fwd (column + row pass)", "achieved": achieved, "peak": bpeak,
+            "peak_kind": "measured: register-resident Cooley-Tukey butterflies a second over every SM "
+                         "(rk_measure_alu microbenchmark)", "unit": "Gbutterfly/s",
+            "frac": (achieved / bpeak) if bpeak else None,
+            "issue_peak": peak, "issue_frac": (achieved / peak) if peak else None,
+            "issue_peak_kind": "derived: 152 SMs x 4 schedulers x 1 warp instruction/clock x 2070 MHz / "
+                               "instructions per butterfly of this kernel (ncu)",
             "multiplier_pipe_peak": mul_peak, "multiplier_pipe_frac": (achieved / mul_peak) if mul_peak else None,
             "traffic": committed_traffic("ntt_fwd", prof["bytes"] / prof["launches"]),
             "algorithmic_bytes_per_launch": prof["bytes"] / prof["launches"], "butterflies_per_launch": per_launch,
             "avg_launch_us": avg_s * 1e6, "launches": prof["launches"],
             "sm_mhz_under_load": (clk or {}).get("sm_mhz")}
+
+
+def ks_algorithmic(limbs: int, log_n: int = 16, alpha: int = 3, dsize: int = 3, seeded: bool = True):
+    """Algorithmic cost of one hybrid key switch at `limbs` = l+1 live limbs: bytes =
+    8n [2(l+1) input + parts beta (l+1+alpha) key + 2(l+1) output], parts = 1 for seeded
+    keys (the a parts regenerated, so the key stream is the b parts), 2 for explicit
+    keys; modular products = (n/2) log2 n [beta (l+1+alpha) + 2(l+1) + 2 alpha]
+    butterflies of the transforms plus n [3 beta (l+1) + 6(l+1) + 2 beta (l+1+alpha)] of
+    the conversions and the inner product."""
+    n = 1 << log_n
+    beta = -(-limbs // dsize)
+    qp = limbs + alpha
+    bytes_ = 8 * n * (2 * limbs + (1 if seeded else 2) * beta * qp + 2 * limbs)
+    modmuls = (n // 2) * log_n * (beta * qp + 2 * limbs + 2 * alpha) + n * (3 * beta * limbs + 6 * limbs + 2 * beta * qp)
+    return bytes_, modmuls
+
+
+def keyswitch_roofline(ctx, stream, alu, hbm_peak, reps=10):
+    """One complete key switch (a rotation: ModUp with its transforms, the key inner
+    product, ModDown with its transforms and the combine) at 28, 18 and 9 limbs,
+    timed with CUDA events on the library stream around `reps` back-to-back
+    rotations of a resident ciphertext: algorithmic bytes and modular products per
+    switch over its average duration, against the measured HBM copy rate and the
+    measured modular-product rate."""
+    import torch
+    from paper_2412_15126_gb300 import inputs
+    W = WORKLOAD
+    ct = ctx.encrypt(inputs.gap_vector(W["N"], W["gap"], 77), N=W["N"])
+    out = {}
+    for limbs in (28, 18, 9):
+        x = ct
+        while x.level + 1 > limbs:
+            x = ctx.mul_scalar(x, 1.0)
+        for _ in range(2):
+            ctx.rotate(x, -W["N"]).free()
+        ctx.sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        res = []
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(reps):
+                res.append(ctx.rotate(x, -W["N"]))
+            e1.record(stream)
+        e1.synchronize()
+        us = e0.elapsed_time(e1) * 1000.0 / reps
+        for r in res:
+            r.free()
+        b, m = ks_algorithmic(limbs)
+        gbs = b / (us * 1e-6) / 1e9
+        gmm = m / (us * 1e-6) / 1e9
+        out[str(limbs)] = {"us": us, "algorithmic_mb": b / 1e6, "gb_per_s": gbs, "frac_hbm": gbs / hbm_peak,
+                           "gmodmul_per_s": gmm,
+                           "frac_modmul_peak": (gmm * 1e9 / alu["modmul_per_s"]) if alu else None}
+    return out
 
 
 def committed_traffic(kernel: str, algorithmic_per_launch: float):
@@ -485,21 +549,89 @@ def committed_traffic(kernel: str, algorithmic_per_launch: float):
 # ---------------------------------------------------------------------------
 # CPU baseline: the oracle on a bounded sample
 # ---------------------------------------------------------------------------
-def oracle_rank_estimate(steps: int = 1, warmup: int = 0):
+def rank_rotations(N):
+    """The rotation amounts of a rank circuit (ReplR, TransR, ReplC, SumR; Sec. 3.1)."""
+    k = N.bit_length() - 1
+    rs = set()
+    for i in range(k):
+        rs.update({-(N << i), -(1 << i), N << i})
+    for i in range(1, k + 1):
+        rs.add(-((N * (N - 1)) >> i))
+    return sorted(rs)
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def oracle_rank_setup(seed: int = 3):
+    """The oracle's parameters, keys (the rank's 28 rotations and relinearisation) and
+    one encrypted input of the 128-element workload (none of it timed)."""
+    from oracle import ckks
+    from paper_2412_15126_gb300 import inputs
+    W = WORKLOAD
+    P = ckks.gen_params(W["log_n"], W["n_limbs"], W["log_q0"], W["log_scale"], W["n_special"],
+                        W["log_special"], W["digit_size"])
+    keys = ckks.keygen(P, seed, sorted({ckks.galois_left(r % P.slots, P.n) for r in rank_rotations(W["N"])}))
+    v = inputs.gap_vector(W["N"], W["gap"], seed)
+    return P, keys, v, ckks.encrypt(P, keys, v, seed)
+
+
+def oracle_rank_timed(setup, max_ranks: int, budget_s: float):
+    """Complete oracle ranks (Alg. 3 on the plain CPU RNS-CKKS, every rotation, product
+    and rescale of the circuit) of the 128-element workload, one after another until
+    `max_ranks` are done or `budget_s` seconds have passed (at least one).  Returns the
+    per-rank seconds and the largest rank error of the decrypted results."""
+    import numpy as np
+    from oracle import ckks, circuits as C
+    P, keys, v, ct = setup
+    W = WORKLOAD
+    times, err = [], 0.0
+    t_all = time.perf_counter()
+    while len(times) < max_ranks:
+        t0 = time.perf_counter()
+        R = C.rank(C.OracleCkks(P, keys), ct, W["N"], W["d_g"], W["d_f"])
+        times.append(time.perf_counter() - t0)
+        got = ckks.decrypt(P, keys, R)[: W["N"]]
+        err = max(err, float(np.max(np.abs(got - C.brute_fractional_rank(v)))))
+        if time.perf_counter() - t_all >= budget_s:
+            break
+    return times, err
+
+
+def oracle_rank_estimate(steps: int = 1, warmup: int = 0, setup=None):
     """Time the oracle's rotation, product and scalar product at the top level (28
     limbs), `steps` times each, and scale to one full rank circuit: each key switch
     (rotation or product) at level l weighted by beta_l (l+1+alpha) relative to the
     top level, each scalar/mask product by (l+1).  Returns seconds per rank and the
-    per-step samples."""
+    per-step samples.  A model, kept beside the complete ranks as a cross-check."""
     import numpy as np
     from oracle import ckks, circuits as C
 
     W = WORKLOAD
-    P = ckks.gen_params(W["log_n"], W["n_limbs"], W["log_q0"], W["log_scale"], W["n_special"],
-                        W["log_special"], W["digit_size"])
-    keys = ckks.keygen(P, 3, [ckks.galois_left(P.slots - W["N"], P.n)])
-    from paper_2412_15126_gb300 import inputs
-    ct = ckks.encrypt(P, keys, inputs.gap_vector(W["N"], W["gap"], 1), 1)
+    if setup is None:
+        P = ckks.gen_params(W["log_n"], W["n_limbs"], W["log_q0"], W["log_scale"], W["n_special"],
+                            W["log_special"], W["digit_size"])
+        keys = ckks.keygen(P, 3, [ckks.galois_left(P.slots - W["N"], P.n)])
+        from paper_2412_15126_gb300 import inputs
+        ct = ckks.encrypt(P, keys, inputs.gap_vector(W["N"], W["gap"], 1), 1)
+    else:
+        P, keys, _, ct = setup
 
     # op trace of the rank circuit (levels from the noiseless model of the same schedule)
     class Trace(C.PlainSlots):
@@ -672,21 +804,38 @@ def replica_seed(rank: int, i: int) -> int:
     return 1 + rank * 1000 + i
 
 
+REF_BUDGET_S = 120.0   # host seconds the reference arm spends on complete oracle ranks
+
+
 def run_reference(args):
+    """The oracle as it stands on the host cores: complete 128-element ranks, as many
+    as --steps asks for or as fit REF_BUDGET_S (at least one); `steps` reports the
+    ranks actually timed.  The oracle has nothing to warm up (no caches, no JIT), so
+    no untimed ranks run; key generation is outside the timed ranks."""
     rank, world, _ = dist_info()
     if rank != 0:
         return 0
     from oracle import _lib
     _lib.build()
-    samples, desc = oracle_rank_estimate(steps=args.steps, warmup=args.warmup)
-    est = [s["est_s"] for s in samples]
-    value = statistics.mean(est)
+    t0 = time.perf_counter()
+    setup = oracle_rank_setup()
+    keygen_s = time.perf_counter() - t0
+    times, err = oracle_rank_timed(setup, args.steps, REF_BUDGET_S)
+    value = statistics.mean(times)
+    model, desc = oracle_rank_estimate(steps=1, setup=setup)
+    sample = (f"{len(times)} complete rank circuit(s) of the 128-element workload on the oracle (28 rotations, "
+              f"24 products, every rescale), one encrypted input, keys generated beforehand ({keygen_s:.0f} s, not "
+              f"timed); up to --steps ranks within {REF_BUDGET_S:.0f} s")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1000.0, "higher_is_better": False,
+        "steps": len(times), "warmup": 0, "ms_per_step": value * 1000.0, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": value / PAPER_RANK128_S, "dtype": "u64", "data": "synthetic",
-        "config": workload_config({"impl_detail": "plain CPU RNS-CKKS oracle (C core, OpenMP over residues)"}),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": desc},
+        "config": workload_config({"impl_detail": "plain CPU RNS-CKKS oracle (C core, OpenMP over residues)",
+                                   "steps_requested": args.steps, "warmup_requested": args.warmup,
+                                   "max_rank_error": err}),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": sample,
+                         "host_cpu": cpu_model(), "rank_seconds": times,
+                         "model_estimate_s": model[0]["est_s"], "model": desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -710,6 +859,7 @@ def run_cuda(args):
                           W["log_special"], W["d_g"], W["d_f"], device=local, stream=stream.cuda_stream)
     ctx.keygen(1000 + rank, W["N"])
     tuned = ctx.autotune() if not args.no_autotune else None
+    alu = ctx.measure_alu()
     n_in = args.warmup + args.steps
     vecs = [inputs.gap_vector(W["N"], W["gap"], replica_seed(rank, i)) for i in range(n_in)]
     cts = [ctx.encrypt(v, N=W["N"]) for v in vecs]
@@ -880,7 +1030,10 @@ def run_cuda(args):
         serving = serving_workload(stream, torch.cuda.Stream(), local, count=args.serve)
 
     peak, peak_kind = measured_peaks()
-    roof_ntt = ntt_roofline(prof_ntt, clk)
+    keyswitch = None
+    if not args.no_kernel_table:
+        keyswitch = keyswitch_roofline(ctx, stream, alu, peak)
+    roof_ntt = ntt_roofline(prof_ntt, clk, alu)
     sampled = "launches of every %dth timed step (%d of %d steps)" % (PROF_EVERY, n_prof, args.steps)
     if roof_ntt:
         roof_ntt["events_on"] = sampled
@@ -897,8 +1050,12 @@ def run_cuda(args):
         value = ms_per_step / 1000.0
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            samples, desc = oracle_rank_estimate(steps=1)
-            cpu = {"value": samples[0]["est_s"], "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": desc}
+            setup = oracle_rank_setup()
+            times, cerr = oracle_rank_timed(setup, 1, 0.0)
+            cpu = {"value": times[0], "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                   "sample": "one complete rank circuit of the 128-element workload on the oracle (28 rotations, 24 "
+                             "products, every rescale), keys generated beforehand (not timed)",
+                   "host_cpu": cpu_model(), "max_rank_error": cerr}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
@@ -908,6 +1065,8 @@ def run_cuda(args):
             "e2e": {"value": e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "roofline": roof_ntt,
             "roofline_hbm": roof_ks,
+            "keyswitch": keyswitch,
+            "alu_peaks": alu,
             "cpu_baseline": cpu,
             "batched": batched,
             "graph": graph, "trimmed_levels": trimmed,

@@ -216,6 +216,23 @@ uint64_t rk_galois_left(const rk_ctx* ctx, int32_t r);
 rk_status rk_encoding_import(rk_ctx* ctx, uint32_t kind, uint32_t N, uint32_t Q, uint32_t n_real,
                              const double* u, size_t n);
 
+/* The unscaled encoding the library uses for mask `kind` at (N, Q, n_real): n doubles,
+ * the real polynomial whose slot values are the mask (Sec. 2.1 canonical embedding:
+ * slot j <-> zeta^(5^j)), from the library's own FFT unless rk_encoding_import replaced
+ * it.  u receives n values.  Errors: RK_EINVAL on a bad kind, shape or length. */
+rk_status rk_encoding_export(rk_ctx* ctx, uint32_t kind, uint32_t N, uint32_t Q, uint32_t n_real, double* u, size_t n);
+
+/* The Chebyshev coefficients of the indicator window the order-statistic and sorting
+ * circuits use for padded length N (Alg. 4, 5; see rk_indicator_import), computed by
+ * the library unless imported.  *count receives their number; out (may be NULL)
+ * receives min(cap, count) values.  Errors: RK_EINVAL. */
+rk_status rk_indicator_export(rk_ctx* ctx, uint32_t N, double* out, size_t cap, size_t* count);
+
+/* The Chebyshev comparator's coefficients (Sec. 2.2; the context's cmp_cheb of them),
+ * computed by the library unless imported; out and count as rk_indicator_export.
+ * Errors: RK_EINVAL if the context uses the composite comparator. */
+rk_status rk_comparator_export(rk_ctx* ctx, double* out, size_t cap, size_t* count);
+
 /* Override the Chebyshev coefficients c_0..c_{count-1} of the indicator window
  * used for vectors of padded length N (Alg. 4, 5: Ind_k(r) = p((r - k)/N) with
  * p = sum_i c_i T_i).  By default the library interpolates sinc^2(N t) at the
@@ -297,10 +314,14 @@ rk_status rk_rescale(rk_ctx* ctx, const rk_ct* a, rk_ct** out);
  * The temporary lives in one fixed 4 MiB array in device memory declared by the
  * library (held by every GPU that loads the library until the process exits), so
  * 2*(level+1)*n must not exceed 2^19 words: larger sizes fail with RK_EINVAL.
- * The first call on a device resolves that array's address; make that first call
- * before any CUDA stream capture.  All calls share the array (nothing in it needs
- * to start at zero): calls whose work overlaps on the GPU, e.g. from two contexts
- * on different streams of one device, race.  Work is queued on the context stream.
+ * The first call on each context resolves that array's address (with the context's
+ * device current) and keeps it in the context; make that first call before any CUDA
+ * stream capture.  A context created after the device was reset resolves it anew; a
+ * context that outlives a reset of its device is unusable, as for every call.  All
+ * calls share the array (nothing in it needs to start at zero): calls whose work
+ * overlaps on the GPU, e.g. from two contexts on different streams of one device,
+ * race.  Work is queued on the context stream.  rk_device_alloc_count() does not
+ * change across a call.
  * Errors: RK_EINVAL (NULL, level out of range, too large, overlap), RK_ECUDA. */
 rk_status rk_rescale_noalloc(rk_ctx* ctx, const uint64_t* d_in, uint64_t* d_out, uint32_t level);
 
@@ -459,6 +480,18 @@ rk_status rk_profile_kind(const rk_ctx* ctx, const char* kind, double out[4]);
  * (they separate it from its neighbours), so a long run can time a sample of its
  * steps.  Errors: RK_EINVAL on a null context. */
 rk_status rk_profile_pause(rk_ctx* ctx, int paused);
+/* Integer throughput of the device (the paper has no counterpart): the ceilings of
+ * the integer-bound kernels, measured by project-written microbenchmarks with every
+ * operand in registers (independent dependency chains per thread, grids over every
+ * SM; the best of three timed launches each).  out[0]: 32-bit integer multiply-adds
+ * a second; out[1]: 64-bit Shoup modular products a second (x w mod q with a
+ * precomputed companion, the NTT's product); out[2]: forward NTT butterflies
+ * (Cooley-Tukey, values in [0, 4q)) a second.  Synchronises; takes about a second.
+ * Errors: RK_ECUDA. */
+rk_status rk_measure_alu(rk_ctx* ctx, double out[3]);
+/* Device allocations (cudaMalloc and cudaMallocAsync calls) the library has made in
+ * this process, over every context. */
+uint64_t rk_device_alloc_count(void);
 /* Number of kernels this context has launched since creation. */
 uint64_t rk_launch_count(const rk_ctx* ctx);
 

@@ -34,6 +34,8 @@ library):
 from __future__ import annotations
 
 import math
+import os
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -361,8 +363,10 @@ def seeded_key_a(P: Params, seed: int, j: int) -> np.ndarray:
     a_eval = mul_scalar_mod(ar, rinv, primes)
     logn = P.n.bit_length() - 1
     a = np.ascontiguousarray(a_eval[:, _brev_perm(logn)])   # natural order: index m <-> psi^(2m + 1)
-    for p, q in enumerate(primes):
-        _lib.lib().orc_nega_inverse(ptr(a[p]), P.n, int(q))
+    # one inverse transform per prime, independent of each other: run them on threads
+    # (the C core releases the interpreter lock)
+    with ThreadPoolExecutor(max_workers=min(len(primes), os.cpu_count() or 1)) as ex:
+        list(ex.map(lambda pq: _lib.lib().orc_nega_inverse(ptr(a[pq[0]]), P.n, int(pq[1])), enumerate(primes)))
     return a
 
 

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "librankfhe.so")
-SOURCES = ["kernels.cu", "context.cu", "evaluator.cu", "encoder.cpp", "circuits.cpp", "capi.cpp", "noalloc.cu", "ntt.cu", "graph.cu", "ks_fused.cu", "server.cpp"]
+SOURCES = ["kernels.cu", "context.cu", "evaluator.cu", "encoder.cpp", "circuits.cpp", "capi.cpp", "noalloc.cu", "ntt.cu", "graph.cu", "ks_fused.cu", "server.cpp", "alu_bench.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off", "-I", INCLUDE]
 # extra compile-time switches for tuning builds, e.g. RK_EXTRA_NVCC_FLAGS="-DRK_PDL=0"

@@ -31,6 +31,7 @@ rk_ct* graph_rank_run(rk_graph* g, const rk_ct* in);
 void graph_free(rk_graph* g);
 rk_ctx* graph_context(const rk_graph* g);
 void circuit_rotations(uint32_t N, std::vector<int>& out);
+void measure_alu(rk_ctx* c, double out[3]);
 
 namespace {
 thread_local std::string g_last_error;
@@ -268,6 +269,52 @@ rk_status rk_encoding_import(rk_ctx* ctx, uint32_t kind, uint32_t N, uint32_t Q,
                 ++it;
             }
         }
+    });
+}
+
+uint64_t rk_device_alloc_count(void) { return rk_alloc_counted(); }
+
+rk_status rk_measure_alu(rk_ctx* ctx, double out[3]) {
+    return guard([&] {
+        need(ctx, "ctx");
+        need(out, "out");
+        set_device(ctx);
+        measure_alu(ctx, out);
+    });
+}
+
+rk_status rk_encoding_export(rk_ctx* ctx, uint32_t kind, uint32_t N, uint32_t Q, uint32_t n_real, double* u, size_t n) {
+    return guard([&] {
+        need(ctx, "ctx");
+        need(u, "u");
+        RK_REQUIRE(n == (size_t)ctx->n, RK_EINVAL, "encoding length must be n");
+        RK_REQUIRE(kind >= RK_MASK_ROW0 && kind <= RK_MASK_ROWIDX, RK_EINVAL, "unknown mask kind");
+        RK_REQUIRE(N >= 1 && (N & (N - 1)) == 0 && Q >= 1 && (size_t)Q * N * N <= (size_t)ctx->n / 2, RK_EINVAL,
+                   "N must be a power of two with Q N^2 <= n/2");
+        const std::vector<double>& e = encoding_of(ctx, kind, N, Q, mask_nreal(kind, n_real));
+        std::copy(e.begin(), e.end(), u);
+    });
+}
+
+static void copy_coeffs(const std::vector<double>& c, double* out, size_t cap, size_t* count) {
+    *count = c.size();
+    if (out) std::copy(c.begin(), c.begin() + std::min(cap, c.size()), out);
+}
+
+rk_status rk_indicator_export(rk_ctx* ctx, uint32_t N, double* out, size_t cap, size_t* count) {
+    return guard([&] {
+        need(ctx, "ctx");
+        need(count, "count");
+        RK_REQUIRE(N >= 1 && (N & (N - 1)) == 0, RK_EINVAL, "N must be a power of two");
+        copy_coeffs(indicator_coeffs_of(ctx, N), out, cap, count);
+    });
+}
+
+rk_status rk_comparator_export(rk_ctx* ctx, double* out, size_t cap, size_t* count) {
+    return guard([&] {
+        need(ctx, "ctx");
+        need(count, "count");
+        copy_coeffs(comparator_coeffs_of(ctx), out, cap, count);
     });
 }
 

@@ -589,6 +589,12 @@ rk_ct* circuit_rank(rk_ctx* c, const rk_ct* in, uint32_t flags) {
     return R.release();
 }
 
+const std::vector<double>& indicator_coeffs_of(rk_ctx* c, uint32_t N) { return indicator_coeffs(c, N); }
+const std::vector<double>& comparator_coeffs_of(rk_ctx* c) {
+    RK_REQUIRE(c->prm.cmp_cheb != 0, RK_EINVAL, "the context uses the composite comparator (no Chebyshev coefficients)");
+    return cmp_cheb_coeffs(c);
+}
+
 void indicator_import(rk_ctx* c, uint32_t N, const double* coeffs, size_t count) {
     RK_REQUIRE(count >= 4 && (count & (count - 1)) == 0, RK_EINVAL, "coefficient count must be a power of two >= 4");
     c->indicator[N] = std::vector<double>(coeffs, coeffs + count);

@@ -1,5 +1,6 @@
 // Context creation: prime chain, canonical scales, NTT twiddles and the constant
 // tables of the RNS basis conversions (Sec. 2.1 scheme substrate).
+#include <atomic>
 #include <cmath>
 #include <cstring>
 
@@ -103,13 +104,24 @@ static int bitrev(int x, int bits) {
     return r;
 }
 
+static std::atomic<uint64_t> g_device_allocs{0};
+uint64_t rk_alloc_counted() { return g_device_allocs.load(); }
+cudaError_t rk_malloc(void** p, size_t bytes) {
+    g_device_allocs++;
+    return cudaMalloc(p, bytes);
+}
+cudaError_t rk_malloc_async(void** p, size_t bytes, cudaStream_t st) {
+    g_device_allocs++;
+    return cudaMallocAsync(p, bytes, st);
+}
+
 u64* rk_ctx::scratch(size_t words) {
     if (words > scratch_words) {
         RK_CUDA(cudaStreamSynchronize(stream));
         if (d_scratch) RK_CUDA(cudaFree(d_scratch));
         generation++;
         d_scratch = nullptr;
-        RK_CUDA(cudaMalloc((void**)&d_scratch, words * 8));
+        RK_CUDA(rk_malloc((void**)&d_scratch, words * 8));
         scratch_words = words;
     }
     return d_scratch;
@@ -200,7 +212,7 @@ void ctx_build(rk_ctx* c, const rk_params* p, int device, void* stream) {
         P.ninv_shoup = shoup_of(P.ninv, qi);
         P.one_shoup = shoup_of(1, qi);
     }
-    RK_CUDA(cudaMalloc((void**)&c->d_pc, NP * sizeof(PrimeConst)));
+    RK_CUDA(rk_malloc((void**)&c->d_pc, NP * sizeof(PrimeConst)));
     RK_CUDA(cudaMemcpy(c->d_pc, c->h_pc.data(), NP * sizeof(PrimeConst), cudaMemcpyHostToDevice));
 
     // ---- twiddles: (psi^brev(i), Shoup companion) and (psi^-brev(i), companion) pairs ----
@@ -224,7 +236,7 @@ void ctx_build(rk_ctx* c, const rk_params* p, int device, void* stream) {
             I[2 * k + 1] = shoup_of(ipw[r], qi);
         }
     }
-    RK_CUDA(cudaMalloc((void**)&c->d_tw, tw.size() * 8));
+    RK_CUDA(rk_malloc((void**)&c->d_tw, tw.size() * 8));
     RK_CUDA(cudaMemcpy(c->d_tw, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice));
 
     // ---- basis conversion constants ----
@@ -340,7 +352,7 @@ void ctx_build(rk_ctx* c, const rk_params* p, int device, void* stream) {
         double* rcp = reinterpret_cast<double*>(smod + 3 * (L + 1));   // 1 / s_k, correctly rounded
         for (size_t k = 0; k < A1; k++) rcp[k] = 1.0 / (double)src[k];
     }
-    RK_CUDA(cudaMalloc((void**)&c->d_conv, conv.size() * 8));
+    RK_CUDA(rk_malloc((void**)&c->d_conv, conv.size() * 8));
     RK_CUDA(cudaMemcpy(c->d_conv, conv.data(), conv.size() * 8, cudaMemcpyHostToDevice));
 
     KernelEnv& e = c->env;

@@ -117,7 +117,7 @@ rk_ct* ct_alloc(rk_ctx* c, int level, int B) {
     ct->ctx = c;
     ct->level = level;
     ct->B = B;
-    cudaError_t e = cudaMallocAsync((void**)&ct->data, (size_t)B * c->ct_words() * 8, c->stream);
+    cudaError_t e = rk_malloc_async((void**)&ct->data, (size_t)B * c->ct_words() * 8, c->stream);
     if (e != cudaSuccess) {
         delete ct;
         throw rk_error(RK_ENOMEM, std::string("ciphertext allocation: ") + cudaGetErrorString(e));
@@ -278,7 +278,7 @@ void ev_level_down(rk_ctx* c, const rk_ct* a, int target, rk_ct* out) {
     while (out->level > target) ev_mul_scalar(c, out, 1.0, out);
 }
 
-static const std::vector<double>& encoding_of(rk_ctx* c, uint32_t kind, uint32_t N, uint32_t Q, uint32_t n_real) {
+const std::vector<double>& encoding_of(rk_ctx* c, uint32_t kind, uint32_t N, uint32_t Q, uint32_t n_real) {
     auto ekey = std::make_tuple(kind, N, Q, n_real);
     if (!c->encodings.count(ekey)) {
         std::vector<double> slots;
@@ -296,7 +296,7 @@ static u64* plain_make(rk_ctx* c, const std::vector<double>& u, double s, int l,
     for (int k = 0; k < c->n; k++) m[k] = round_half_away(s * u[k]);
     Scratch S = scratch_layout(c);
     u64* buf = nullptr;
-    RK_CUDA(cudaMalloc((void**)&buf, (size_t)(l + 1) * c->n * 8));
+    RK_CUDA(rk_malloc((void**)&buf, (size_t)(l + 1) * c->n * 8));
     int64_t* tmp = (int64_t*)S.misc;
     upload_i64_sync(c, tmp, m.data(), c->n);
     launch_reduce_signed(c->env, tmp, ls_q(buf, 0, 1, l + 1), c->stream);
@@ -722,7 +722,7 @@ void ks_autotune(rk_ctx* c, std::vector<double>& report) {
 static void secret_set(rk_ctx* c, const std::vector<int64_t>& s) {
     const int NP = c->n_primes;
     c->h_sk = s;
-    if (!c->d_sk) RK_CUDA(cudaMalloc((void**)&c->d_sk, (size_t)NP * c->n * 8));
+    if (!c->d_sk) RK_CUDA(rk_malloc((void**)&c->d_sk, (size_t)NP * c->n * 8));
     Scratch S = scratch_layout(c);
     upload_i64_sync(c, (int64_t*)S.misc, s.data(), c->n);
     launch_reduce_signed(c->env, (int64_t*)S.misc, ls_all(c->d_sk, 0, 1, NP), c->stream);
@@ -742,7 +742,7 @@ static void gaussian_eval(rk_ctx* c, HostRng& rng, u64* dst, int limbs, int64_t*
 static void make_pk(rk_ctx* c) {
     const int L1 = c->L + 1;
     Scratch S = scratch_layout(c);
-    if (!c->d_pk) RK_CUDA(cudaMalloc((void**)&c->d_pk, (size_t)2 * L1 * c->n * 8));
+    if (!c->d_pk) RK_CUDA(rk_malloc((void**)&c->d_pk, (size_t)2 * L1 * c->n * 8));
     HostRng rng(c->seed ^ 0x5045524B45590001ull);
     u64* a = S.misc;
     u64* e = S.misc + (size_t)L1 * c->n;
@@ -761,7 +761,7 @@ static SwitchKeyDev make_switch_key(rk_ctx* c, const u64* sp, u64 stream_id) {
     SwitchKeyDev key;
     key.seeded = true;
     key.seed = HostRng::mix(c->seed ^ HostRng::mix(stream_id + 0x5EED0000ull));
-    cudaError_t err = cudaMalloc((void**)&key.data, (size_t)BL * NP * n * 8);
+    cudaError_t err = rk_malloc((void**)&key.data, (size_t)BL * NP * n * 8);
     if (err != cudaSuccess) throw rk_error(RK_ENOMEM, "switching key allocation failed");
     Scratch S = scratch_layout(c);
     // misc: [sp copy is provided by caller in misc][e: NP n][tmp: n][gad: NP]
@@ -851,7 +851,7 @@ void key_import(rk_ctx* c, uint32_t kind, uint64_t galois, const uint64_t* coeff
     SwitchKeyDev key;
     key.seeded = seeded;
     key.seed = seed;
-    RK_CUDA(cudaMalloc((void**)&key.data, expect * 8));
+    RK_CUDA(rk_malloc((void**)&key.data, expect * 8));
     RK_CUDA(cudaMemcpyAsync(key.data, coeffs, expect * 8, cudaMemcpyHostToDevice, c->stream));
     launch_ntt_forward(c->env, ls_all(key.data, (size_t)NP * n, BL * parts, NP), c->stream);
     launch_to_mont(c->env, ls_all(key.data, (size_t)NP * n, BL * parts, NP), c->stream);
@@ -870,7 +870,7 @@ void key_export(rk_ctx* c, const SwitchKeyDev& key, u64* host_out) {
     const size_t n = c->n, words = key_words(c, key);
     const int polys = (int)(words / ((size_t)NP * n));
     u64* tmp = nullptr;
-    RK_CUDA(cudaMallocAsync((void**)&tmp, words * 8, c->stream));
+    RK_CUDA(rk_malloc_async((void**)&tmp, words * 8, c->stream));
     for (int p = 0; p < polys; p++) launch_from_mont(c->env, tmp + (size_t)p * NP * n, key.data + (size_t)p * NP * n, NP, c->stream);
     launch_ntt_inverse(c->env, ls_all(tmp, (size_t)NP * n, polys, NP), c->stream);
     RK_CUDA(cudaMemcpyAsync(host_out, tmp, words * 8, cudaMemcpyDeviceToHost, c->stream));

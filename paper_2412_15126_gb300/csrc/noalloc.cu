@@ -7,8 +7,6 @@
 // keeps its temporary (the centred lift of the dropped residue) in a fixed array
 // in device memory that the library declares at file scope, so it performs no
 // cudaMalloc, cudaFree or allocating library call.
-#include <mutex>
-
 #include "kernels.cuh"
 
 // Scratch of the allocation-free rescale: 2 * (level + 1) * n words at most.
@@ -16,21 +14,18 @@
 static __device__ __align__(256) u64 g_noalloc_scratch[RK_NOALLOC_SCRATCH_WORDS];
 
 namespace {
-std::mutex g_mu;
-u64* g_scratch_addr[128] = {nullptr};   // host copy of the array's device address, per device
-
-// Resolve the array's device address once per device (the device must be current).
-u64* scratch_address(int device) {
-    RK_REQUIRE(device >= 0 && device < 128, RK_EINVAL, "device ordinal out of range");
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[device]) {
+// The array's device address, resolved by the first call on each context (with the
+// context's device current) and kept in the context: a context created after the
+// device was reset resolves it again, since the array may then sit elsewhere.
+u64* scratch_address(rk_ctx* c) {
+    if (!c->noalloc_scratch) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess)
             throw rk_error(RK_ECUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
-        g_scratch_addr[device] = (u64*)p;
+        c->noalloc_scratch = (u64*)p;
     }
-    return g_scratch_addr[device];
+    return c->noalloc_scratch;
 }
 }  // namespace
 
@@ -46,7 +41,7 @@ void rescale_noalloc(rk_ctx* c, const u64* in, u64* out, int l) {
     const u64* out_end = out + (size_t)2 * l * n;
     RK_REQUIRE(out_end <= in || in_end <= out, RK_EINVAL, "input and output buffers overlap");
     RK_CUDA(cudaSetDevice(c->device));
-    u64* S = scratch_address(c->device);
+    u64* S = scratch_address(c);
     KernelEnv env = c->env;
     env.prof = nullptr;   // never create profiling events on this path
     cudaStream_t st = c->stream;

@@ -415,7 +415,7 @@ void ntt_autotune(rk_ctx* c, std::vector<double>& report) {
     const int L1 = c->L + 1;
     const int polys_large = std::max(1, 224 / L1);
     u64* buf = nullptr;
-    RK_CUDA(cudaMallocAsync((void**)&buf, (size_t)polys_large * L1 * n * 8, c->stream));
+    RK_CUDA(rk_malloc_async((void**)&buf, (size_t)polys_large * L1 * n * 8, c->stream));
     RK_CUDA(cudaMemsetAsync(buf, 0, (size_t)polys_large * L1 * n * 8, c->stream));
     cudaEvent_t e0, e1;
     RK_CUDA(cudaEventCreate(&e0));

@@ -31,6 +31,12 @@ struct rk_error : std::runtime_error {
         if (!(cond)) throw rk_error((code), (msg));  \
     } while (0)
 
+// Every device allocation of the library goes through these two, which count the
+// calls (rk_device_alloc_count reports the total).
+uint64_t rk_alloc_counted();
+cudaError_t rk_malloc(void** p, size_t bytes);
+cudaError_t rk_malloc_async(void** p, size_t bytes, cudaStream_t st);
+
 // ---------------------------------------------------------------------------
 // Device-side description of a set of residue polynomials.
 // Limb t of poly p lives at base + p * poly_stride + t * n.
@@ -237,6 +243,7 @@ struct rk_ctx {
     bool trim_levels = false;     // rank: bring the input down to the level the circuit needs first
     double ks_group_bytes = 48.0 * (1 << 20);   // lifted digits kept in L2 between the fused kernels
     size_t ind_stack_bytes = (size_t)4 << 30;   // working set of one stacked indicator evaluation
+    u64* noalloc_scratch = nullptr;             // device address of the allocation-free rescale's array
     std::vector<double> cmp_coeffs;             // Chebyshev comparator coefficients (computed or imported)
     // plaintext caches: key = (kind, N, Q, n_real, level)
     std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint32_t, int>, u64*> plain_cache;
@@ -317,6 +324,11 @@ void decode_coeffs(int log_n, const std::vector<double>& m, std::vector<double>&
 
 // masks (circuits.cpp)
 void mask_slot_values(uint32_t kind, uint32_t N, uint32_t Q, uint32_t n_real, size_t slots, std::vector<double>& v);
+// the unscaled encoding of a mask the evaluator uses (its own FFT unless imported; evaluator.cu)
+const std::vector<double>& encoding_of(rk_ctx* c, uint32_t kind, uint32_t N, uint32_t Q, uint32_t n_real);
+// the indicator's and the Chebyshev comparator's coefficients the circuits use (circuits.cpp)
+const std::vector<double>& indicator_coeffs_of(rk_ctx* c, uint32_t N);
+const std::vector<double>& comparator_coeffs_of(rk_ctx* c);
 
 // host number theory (context.cu)
 u64 h_mulmod(u64 a, u64 b, u64 q);

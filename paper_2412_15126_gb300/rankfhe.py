@@ -77,6 +77,11 @@ _sig("rk_key_import", [_vp, _u32, ctypes.c_uint64, _u64p, _sz])
 _sig("rk_key_import_seeded", [_vp, _u32, ctypes.c_uint64, ctypes.c_uint64, _u64p, _sz])
 _sig("rk_galois_left", [_vp, ctypes.c_int32], ctypes.c_uint64)
 _sig("rk_encoding_import", [_vp, _u32, _u32, _u32, _u32, _dp, _sz])
+_sig("rk_encoding_export", [_vp, _u32, _u32, _u32, _u32, _dp, _sz])
+_sig("rk_indicator_export", [_vp, _u32, _dp, _sz, ctypes.POINTER(_sz)])
+_sig("rk_comparator_export", [_vp, _dp, _sz, ctypes.POINTER(_sz)])
+_sig("rk_measure_alu", [_vp, _dp])
+_sig("rk_device_alloc_count", [], ctypes.c_uint64)
 _sig("rk_encrypt", [_vp, _dp, _u32, _u32, _u32, _u32, ctypes.POINTER(_vp)])
 _sig("rk_decrypt_slots", [_vp, _vp, _dp, _sz])
 _sig("rk_decrypt", [_vp, _vp, _dp, _sz, ctypes.POINTER(_u32)])
@@ -135,6 +140,11 @@ _sig("rk_last_error", [], ctypes.c_char_p)
 def _check(status):
     if status != RK_OK:
         raise RkError(status, _L.rk_last_error().decode(errors="replace"))
+
+
+def device_alloc_count() -> int:
+    """Device allocations the library has made in this process (every context)."""
+    return int(_L.rk_device_alloc_count())
 
 
 def raw(name):
@@ -297,6 +307,31 @@ class Context:
     def encoding_import(self, kind, N, Q, n_real, u):
         u = np.ascontiguousarray(u, dtype=np.float64)
         _check(_L.rk_encoding_import(self.handle, kind, N, Q, n_real, u.ctypes.data_as(_dp), u.size))
+
+    def encoding_export(self, kind, N, Q=1, n_real=0):
+        u = np.empty(self.n, dtype=np.float64)
+        _check(_L.rk_encoding_export(self.handle, kind, N, Q, n_real, u.ctypes.data_as(_dp), u.size))
+        return u
+
+    def _coeffs_export(self, fn, *args):
+        cnt = _sz(0)
+        _check(fn(self.handle, *args, None, 0, ctypes.byref(cnt)))
+        out = np.empty(cnt.value, dtype=np.float64)
+        _check(fn(self.handle, *args, out.ctypes.data_as(_dp), out.size, ctypes.byref(cnt)))
+        return out
+
+    def measure_alu(self) -> dict:
+        """Integer throughput of the device: 32-bit multiply-adds, Shoup modular products
+        and forward NTT butterflies a second (register-resident microbenchmarks)."""
+        out = (ctypes.c_double * 3)()
+        _check(_L.rk_measure_alu(self.handle, out))
+        return {"imad_per_s": out[0], "modmul_per_s": out[1], "butterfly_per_s": out[2]}
+
+    def indicator_export(self, N):
+        return self._coeffs_export(_L.rk_indicator_export, N)
+
+    def comparator_export(self):
+        return self._coeffs_export(_L.rk_comparator_export)
 
     # ---- client ----
     def encrypt(self, values, N=None, Q=1, n_real=None) -> Ciphertext:

@@ -14,6 +14,9 @@ CONFIGS = {
     "cfg3": (16, 34, 60, 45, 3, 61, 3, 3, 2),       # N = 128 ties, 34 limbs
     "ord": (11, 24, 60, 40, 2, 61, 2, 2, 1),        # deep small ring for order statistics / sort parity
     "ordb": (11, 24, 60, 40, 2, 61, 2, 1, 1),       # the same ring, shallower comparator: blocked sort parity
+    # the smallest ring holding a 128 x 128 matrix, with the 34-limb chain of the tie
+    # workload (not 128-bit secure at n = 2^15: a parity set only)
+    "big15": (15, 34, 60, 45, 3, 61, 3, 3, 2),
 }
 
 MASK_IDS = {"row0": 1, "col0": 2, "tie": 3, "tri": 4, "valid": 5, "row0s": 6, "col0s": 7, "tiec": 8, "sortidx": 9,
@@ -26,10 +29,11 @@ def oracle_params(name):
     return ckks.gen_params(log_n, n_limbs, log_q0, log_scale, alpha, log_sp, dsize)
 
 
-def gpu_context(name, device=0):
+def gpu_context(name, device=0, cmp_cheb=0):
     from paper_2412_15126_gb300 import rankfhe
     log_n, n_limbs, log_q0, log_scale, alpha, log_sp, dsize, dg, df = CONFIGS[name]
-    return rankfhe.Context(log_n, n_limbs, alpha, dsize, log_scale, log_q0, log_sp, dg, df, device=device)
+    return rankfhe.Context(log_n, n_limbs, alpha, dsize, log_scale, log_q0, log_sp, dg, df, device=device,
+                           cmp_cheb=cmp_cheb)
 
 
 def import_key(ctx, kind, g, key):

@@ -14,16 +14,19 @@ def test_ntt_roofline_arithmetic():
     with open(bench.os.path.join(bench.ROOT, "profiles", "traffic.json")) as f:
         rec = json.load(f)["ntt_fwd"]
     prof = {"launches": 10, "ms": 0.8, "ops": 10 * 4.0e7, "bytes": 10 * 8.0e7}
-    r = bench.ntt_roofline(prof, {"sm_mhz": 2070.0})
+    r = bench.ntt_roofline(prof, {"sm_mhz": 2070.0}, {"butterfly_per_s": 2.0e12})
     assert r["bound"] == "alu" and r["unit"] == "Gbutterfly/s"
     assert r["achieved"] == pytest.approx(4.0e7 / 80e-6 / 1e9)
+    assert r["peak"] == pytest.approx(2000.0)                  # the measured butterfly rate
+    assert r["frac"] == pytest.approx(r["achieved"] / 2000.0)
+    assert bench.ntt_roofline(prof, None)["frac"] is None      # no measurement, no fraction
     if rec["source_sha256"] == bench.kernel_source_sha256("ntt_fwd"):
         issue = 152 * 4 * 32 * 2070e6 / rec["thread_instructions_per_butterfly"] / 1e9
-        assert r["peak"] == pytest.approx(issue)
-        assert r["frac"] == pytest.approx(r["achieved"] / issue)
+        assert r["issue_peak"] == pytest.approx(issue)
+        assert r["issue_frac"] == pytest.approx(r["achieved"] / issue)
         mul = 152 * 4 * 2070e6 / rec["fmaheavy_cycles_per_butterfly"] / 1e9
         assert r["multiplier_pipe_peak"] == pytest.approx(mul)
-        assert r["multiplier_pipe_peak"] < r["peak"]   # the multiplier binds first
+        assert r["multiplier_pipe_peak"] < r["issue_peak"]   # the multiplier binds first
     assert bench.ntt_roofline({"launches": 0, "ms": 0.0, "ops": 0, "bytes": 0}, None) is None
 
 
@@ -52,3 +55,17 @@ def test_kernel_source_hash_covers_the_kernel_text():
 def test_measured_peaks_are_positive():
     peak, kind = bench.measured_peaks()
     assert peak > 0 and isinstance(kind, str)
+
+
+def test_key_switch_algorithmic_cost():
+    """Explicit keys at 28 limbs (n = 2^16, alpha = 3, digits of 3): 8n [2 28 + 2 10 31 +
+    2 28] bytes = 366 MiB; seeded keys stream one key part less; 18 and 9 limbs as the
+    formula gives (162 and 54 MiB explicit)."""
+    b, m = bench.ks_algorithmic(28, seeded=False)
+    assert b == 8 * 65536 * (56 + 620 + 56)
+    assert round(b / 2 ** 20) == 366
+    bs, ms = bench.ks_algorithmic(28)
+    assert b - bs == 8 * 65536 * 10 * 31 and ms == m
+    assert round(bench.ks_algorithmic(18, seeded=False)[0] / 2 ** 20) == 162
+    assert round(bench.ks_algorithmic(9, seeded=False)[0] / 2 ** 20) == 54
+    assert m == 32768 * 16 * (310 + 56 + 6) + 65536 * (3 * 10 * 28 + 6 * 28 + 2 * 310)

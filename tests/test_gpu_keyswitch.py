@@ -1,13 +1,35 @@
 """GPU: the fused key-switching path (conversions inside the NTT passes, inner
 product inside the row pass) against the staged one (lifted digits materialised),
 bit for bit, for rotations (single and hoisted), products, stacked ciphertexts and
-every L2 grouping of the lifted limbs.  Parity of either path with the oracle is
-covered by the rotation / product tests, which run the default (fused) path."""
+every L2 grouping of the lifted limbs.  The default path is the staged one; the
+rotation / product parity tests elsewhere run it against the oracle, and
+test_fused_path_matches_the_oracle runs the fused path against the oracle directly."""
 import numpy as np
 import pytest
 
+from oracle import ckks
 from paper_2412_15126_gb300 import inputs, rankfhe
 from tests import helpers
+
+
+def test_fused_path_matches_the_oracle():
+    """With RK_OPT_KS_FUSED, a single rotation, a hoisted pair of rotations and a
+    product equal the oracle's ciphertexts bit for bit (n = 2^13, 14 limbs)."""
+    P = helpers.oracle_params("cfg1")
+    rots = [-8, 3]
+    keys = ckks.keygen(P, 19, helpers.galois_elts(P, rots))
+    ctx = helpers.gpu_context("cfg1")
+    try:
+        helpers.import_keys(ctx, keys)
+        ctx.set_option(rankfhe.OPT_KS_FUSED, 1)
+        ct = ckks.encrypt(P, keys, inputs.gap_vector(8, 0.05, 19), 19)
+        g = ctx.ct_import(ct.c, ct.level, N=8)
+        assert np.array_equal(ctx.rotate(g, rots[0]).export(), ckks.rotate(P, keys, ct, rots[0]).c)
+        for got, r in zip(ctx.rotate_many(g, rots), rots):
+            assert np.array_equal(got.export(), ckks.rotate(P, keys, ct, r).c)
+        assert np.array_equal(ctx.mul(g, g).export(), ckks.mul(P, keys, ct, ct).c)
+    finally:
+        ctx.close()
 
 pytestmark = pytest.mark.gpu
 

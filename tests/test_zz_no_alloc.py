@@ -35,6 +35,11 @@ def _to_canonical(ctx, dev, limbs):
 
 
 def test_rescale_noalloc_matches_rescale_twice():
+    """Two calls in a row, each bit for bit rk_rescale's result; across each call the
+    library makes no device allocation (its own counter of cudaMalloc and
+    cudaMallocAsync calls), and across the second call the device's free memory does
+    not move (the first call may still load the library's code and its array)."""
+    from paper_2412_15126_gb300 import rankfhe
     ctx = helpers.gpu_context("cfg1")
     try:
         ctx.keygen(99, 8)
@@ -47,7 +52,14 @@ def test_rescale_noalloc_matches_rescale_twice():
             expect = ctx.rescale(ct).export()
             d_in = _to_eval_device(ctx, ct.export())
             d_out = torch.empty(2 * level * ctx.n, dtype=torch.int64, device="cuda")
+            ctx.sync()
+            torch.cuda.synchronize()
+            allocs, free0 = rankfhe.device_alloc_count(), torch.cuda.mem_get_info()[0]
             ctx.rescale_noalloc(d_in.data_ptr(), d_out.data_ptr(), level)
+            ctx.sync()
+            assert rankfhe.device_alloc_count() == allocs, f"call {call} allocated device memory"
+            if call == 1:
+                assert torch.cuda.mem_get_info()[0] == free0, "the second call changed the free device memory"
             got = _to_canonical(ctx, d_out, level)
             assert np.array_equal(got, expect), f"call {call}"
     finally:
