@@ -190,6 +190,7 @@ def order_sort_workload(stream, device, reps=3, seed=3):
 # ---------------------------------------------------------------------------
 SERVE_RANK = dict(log_n=16, n_limbs=34, n_special=3, digit_size=3, log_scale=45, log_q0=60, log_special=61, d_g=4, d_f=2)
 SERVE_SORT = dict(log_n=16, n_limbs=39, n_special=3, digit_size=3, log_scale=40, log_q0=60, log_special=61, d_g=4, d_f=2)
+SERVE_LANES = 2   # execution lanes of each serving loop
 
 
 def serving_requests(count, rate, seed=5, sort_cap=512):
@@ -213,7 +214,8 @@ def serving_requests(count, rate, seed=5, sort_cap=512):
 
 
 def serving_workload(stream_a, stream_b, device, count=120, rate=20.0):
-    """Two contexts, each with its serving loop (worker thread, continuous batching):
+    """Two contexts, each with its serving loop (SERVE_LANES execution lanes, continuous
+    batching, slot packing of short requests):
     34 limbs at 2^45 for ranks and argmins up to 128 elements, 39 limbs at 2^40 for
     sorts and blocked argmins.  Inputs are
     encrypted before the clock starts; a client thread submits each request at its
@@ -247,6 +249,10 @@ def serving_workload(stream_a, stream_b, device, count=120, rate=20.0):
             else:
                 r["ct"] = ctx.stack([ctx.encrypt(x[b * 128:(b + 1) * 128], N=128) for b in range(r["Np"] // 128)])
         for ctx in (ca, cs):
+            # slot packing of short requests: rotations by +-N^2 2^k; the circuits' keys
+            # cover all of them except +-n/4 (one Galois element)
+            ctx.keygen_rotations([ctx.n // 4])
+            ctx.set_option(rankfhe.OPT_SERVER_LANES, SERVE_LANES)
             ctx.sync()
             ctx.server_start(24 << 30, 16)
         tickets = [None] * len(reqs)
@@ -275,6 +281,8 @@ def serving_workload(stream_a, stream_b, device, count=120, rate=20.0):
         outs = [r["ctx"].server_wait(tk) for r, tk in zip(reqs, tickets)]
         wall = time.perf_counter() - t_start
         stats = {"rank_argmin": ca.server_stats(), "sort_deep": cs.server_stats()}
+        for k, ctx in (("rank_argmin", ca), ("sort_deep", cs)):
+            stats[k].update(ctx.server_stats_lanes())
         lat = sorted(ca.server_latencies() + cs.server_latencies())
         ca.server_stop()
         cs.server_stop()
@@ -301,9 +309,10 @@ def serving_workload(stream_a, stream_b, device, count=120, rate=20.0):
             err[r["op"]] = max(err[r["op"]], e)
             if e > 0.25:
                 bad.append({"op": r["op"], "N": r["N"], "Np": r["Np"], "error": e})
-        # identical alone and in the mix: three requests re-run directly
-        same = True
-        for r, o in list(zip(reqs, outs))[:3]:
+        # alone and in the mix: requests re-run directly; a stacked (unpacked) result
+        # must be bit-identical, a slot-packed one within 1e-3 of the alone decryption
+        same, mix_err = True, 0.0
+        for r, o in list(zip(reqs, outs))[:6]:
             ctx, blocked = r["ctx"], r["Np"] > 128
             parts = ctx.unstack(r["ct"]) if blocked else None
             if r["op"] == "rank":
@@ -313,7 +322,11 @@ def serving_workload(stream_a, stream_b, device, count=120, rate=20.0):
             else:
                 ref = ctx.sort_blocked(parts) if blocked else [ctx.sort(r["ct"])]
             got = ctx.unstack(o) if blocked else [o]
-            same = same and all(np.array_equal(a.export(), b.export()) for a, b in zip(got, ref))
+            for a, b in zip(got, ref):
+                e = float(np.max(np.abs(ctx.decrypt(a)[:r["N"]] - ctx.decrypt(b)[:r["N"]])))
+                mix_err = max(mix_err, e)
+                if blocked:
+                    same = same and np.array_equal(a.export(), b.export())
         sizes = [r["N"] for r in reqs]
         return {
             "requests": len(reqs), "rate_per_s": rate, "wall_s": wall, "requests_per_s": len(reqs) / wall,
@@ -321,7 +334,9 @@ def serving_workload(stream_a, stream_b, device, count=120, rate=20.0):
             "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)), "max_s": float(lat[-1]),
             "peak_device_bytes_above_start": max(stats["rank_argmin"]["peak_bytes"], stats["sort_deep"]["peak_bytes"]),
             "rank_argmin_server": stats["rank_argmin"], "deep_server": stats["sort_deep"],
-            "max_abs_error": err, "requests_over_0.25": bad, "identical_alone_vs_mix": same,
+            "max_abs_error": err, "requests_over_0.25": bad, "blocked_identical_alone_vs_mix": same,
+            "max_decrypted_diff_alone_vs_mix": mix_err, "alone_vs_mix_tolerance": 1e-3,
+            "alone_vs_mix_ok": same and mix_err < 1e-3,
             "ops": {op: sum(1 for r in reqs if r["op"] == op) for op in ("rank", "argmin", "sort")},
             "blocked": sum(1 for r in reqs if r["Np"] > 128),
             "workload": "Poisson 20 req/s, op uniform {rank, argmin, sort}, N log-uniform 8..1024 padded to 2^k "
@@ -1123,7 +1138,7 @@ def main():
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay of the rank steps")
     ap.add_argument("--no-kernel-table", action="store_true", help="skip the per-kernel-kind roofline table")
     ap.add_argument("--no-order-sort", action="store_true", help="skip the 34-limb argmin/argmax/sort latencies")
-    ap.add_argument("--serve", type=int, default=0, help="requests of the serving sample (0: skip)")
+    ap.add_argument("--serve", type=int, default=40, help="requests of the serving sample (0: skip)")
     ap.add_argument("--profile-case", action="store_true", help="run the small ncu capture case and exit")
     ap.add_argument("--no-autotune", action="store_true", help="keep the built-in launch shapes")
     args = ap.parse_args()

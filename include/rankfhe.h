@@ -130,6 +130,8 @@ rk_status rk_ctx_counters(const rk_ctx* ctx, uint64_t out[4]);
  * RK_OPT_BLOCK_STACKING: 1 (default) runs the blocks and block pairs of
  *   rk_rank_blocked (flags 0) as stacks; 0 runs every block and pair ciphertext with
  *   its own launches (the plain per-query form, for comparison).  Same results.
+ * RK_OPT_SERVER_LANES: execution lanes of the next rk_server_start (1 to 16, default 2):
+ *   each runs its own batch on its own stream, so batches overlap on the device.
  * RK_OPT_TRIM_LEVELS: 0 (default) evaluates rk_rank / rk_rank_batch at the input's
  *   level; 1 first brings the input down (scalar products by 1 and rescales, as
  *   rk_level_down) to the lowest level the rank circuit needs, so that every key
@@ -142,6 +144,7 @@ rk_status rk_ctx_counters(const rk_ctx* ctx, uint64_t out[4]);
 #define RK_OPT_KS_GROUP_BYTES 2
 #define RK_OPT_BLOCK_STACKING 3
 #define RK_OPT_TRIM_LEVELS 4
+#define RK_OPT_SERVER_LANES 5
 rk_status rk_ctx_set_option(rk_ctx* ctx, uint32_t option, int64_t value);
 
 /* Autotune the launch shapes on this device (the paper has no counterpart): times
@@ -373,6 +376,22 @@ rk_status rk_sort(rk_ctx* ctx, const rk_ct* in, uint32_t flags, rk_ct** out);
  * Cmp_G = 2C^2 - C or its complement).  Errors: RK_EDEPTH, RK_ENOKEY, RK_EINVAL. */
 rk_status rk_rank_blocked(rk_ctx* ctx, const rk_ct* const* blocks, uint32_t L, uint32_t flags, rk_ct** outs);
 
+/* rk_rank_blocked (flags 0) in two parts, so that the L(L+1)/2 block comparisons (the
+ * parallel loop over block pairs of Sec. 5) can be divided between devices and only
+ * their partial sums exchanged.  Part one evaluates C_{i,j} = Cmp(ReplR(V_i),
+ * ReplC(TransR(V_j))) for the npairs listed pairs (pair_i[p] <= pair_j[p] < L) and
+ * writes, per block i, A[i] = the sum of the listed C_{i,j} and B[i] = the sum of the
+ * listed C_{j,i} with j < i (an encryption of zero with no noise where no listed pair
+ * contributes), all at the comparison's output level.  Part two takes the sums over
+ * all parts (rk_add of the parts' A[i], and of their B[i]) and returns
+ * outs[i] = TransC(SumC(i - B[i])) + SumR(A[i]) + 1/2 (Eq. 3), bit-identical to
+ * rk_rank_blocked when the parts together list every pair once.  Blocks as for
+ * rk_rank_blocked; every output is owned by the caller.
+ * Errors: RK_EINVAL (a pair out of range, mismatched sums), RK_EDEPTH, RK_ENOKEY. */
+rk_status rk_rank_blocked_partial(rk_ctx* ctx, const rk_ct* const* blocks, uint32_t L, const uint32_t* pair_i,
+                                  const uint32_t* pair_j, uint32_t npairs, rk_ct** A, rk_ct** B);
+rk_status rk_rank_blocked_finish(rk_ctx* ctx, const rk_ct* const* A, const rk_ct* const* B, uint32_t L, rk_ct** outs);
+
 /* Order statistic over a multi-ciphertext vector (Alg. 4 on the tie-corrected
  * blocked ranks of rk_rank_blocked): outs[i] marks, in row 0, the element of block i
  * whose stable rank is k (1 <= k <= L*B), one-hot over the whole vector.  The
@@ -397,17 +416,28 @@ rk_status rk_sort_batch(rk_ctx* ctx, const rk_ct* const* in, size_t count, uint3
 
 /* ---- serving loop ------------------------------------------------------------ */
 
-/* A worker thread per context with continuous batching (the paper has no serving
- * layer; this is the batched form of Alg. 3-5 and 7 under a request stream).
- * Requests are queued from any thread; whenever the worker is free it takes the
- * oldest request and every queued request of the same operation, arguments and
- * ciphertext shape (level, N, Q, n_real, layout), up to `max_stack` and to as many
- * as fit `mem_budget_bytes` of working set, and evaluates them as one stacked
- * circuit.  Each result is bit-identical to the result of its request alone.
- * While a server runs, the worker owns the context: other threads may call only
- * rk_server_* and rk_ct_free on collected results until rk_server_stop returns.
- * Inputs are borrowed: keep each submitted ciphertext alive and unchanged until its
- * result has been collected.  Results are owned by the caller once collected. */
+/* Serving loop with continuous batching (the paper has no serving layer; this is the
+ * batched form of Alg. 3-5 and 7 under a request stream).  The server runs
+ * RK_OPT_SERVER_LANES execution lanes, each a worker thread with its own stream,
+ * key-switching scratch (sized for stacks of 16 at start) and plaintext caches over
+ * the context's keys, so that batches on different lanes overlap on the device.
+ * Requests are queued from any thread.  Whenever a lane is free and the running
+ * batches leave room in `mem_budget_bytes` for the oldest queued request (a lane with
+ * nothing else running always takes it), the lane takes that request and every
+ * queued request of the same operation, arguments and ciphertext shape (level, N, Q,
+ * n_real, layout), up to `max_stack` ciphertexts and the room left, and evaluates
+ * them as one stacked circuit.  Single-ciphertext requests of padded length N with
+ * Q = (n/2)/N^2 >= 2 are slot-packed first when the packing rotations' keys exist
+ * (left rotations by +-N^2 2^k, 2^k < Q; rk_keygen makes all of them except +-n/4,
+ * which rk_keygen_rotations adds): up to Q requests share a ciphertext (Sec. 2.3
+ * layout), packed and unpacked by trees of stacked rotations.  Results of unpacked
+ * requests are bit-identical to the request alone; packed results carry the packing
+ * rotations' noise and decrypt to the request's values alone within the circuit's
+ * tolerance (other slots hold other requests' results).
+ * While a server runs, it owns the context: other threads may call only rk_server_*
+ * and rk_ct_free on collected results until rk_server_stop returns.  Inputs are
+ * borrowed: keep each submitted ciphertext alive and unchanged until its result has
+ * been collected.  Results are owned by the caller once collected. */
 #define RK_OP_RANK 1          /* rk_rank(in, flags) */
 #define RK_OP_ORDER_STAT 2    /* rk_order_stat(in, arg = k, flags) */
 #define RK_OP_SORT 3          /* rk_sort(in, flags) */
@@ -430,6 +460,10 @@ rk_status rk_server_poll(rk_ctx* ctx, uint64_t ticket, rk_ct** out);
  * above the level at rk_server_start (bytes; includes other users of the device),
  * requests queued. */
 rk_status rk_server_stats(rk_ctx* ctx, double out[8]);
+/* out[5]: lanes, most lanes busy at once, mean lanes busy (the batches' run times
+ * summed over the span from the first batch's start to the last one's end), requests
+ * served slot-packed, scratch bytes of the lanes. */
+rk_status rk_server_stats_lanes(rk_ctx* ctx, double out[5]);
 /* Latencies (s) of the finished requests in completion order: writes min(cap, count)
  * values; *count receives the number finished. */
 rk_status rk_server_latencies(rk_ctx* ctx, double* out, size_t cap, size_t* count);

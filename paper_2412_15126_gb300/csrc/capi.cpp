@@ -15,6 +15,9 @@ rk_ct* circuit_order_value(rk_ctx* c, const rk_ct* in, uint32_t k);
 rk_ct* circuit_median(rk_ctx* c, const rk_ct* in);
 void indicator_import(rk_ctx* c, uint32_t N, const double* coeffs, size_t count);
 void circuit_rank_blocked(rk_ctx* c, const rk_ct* const* blocks, int L, rk_ct** outs);
+void circuit_rank_blocked_partial(rk_ctx* c, const rk_ct* const* blocks, int L, const std::vector<std::pair<int, int>>& pairs,
+                                  rk_ct** A_out, rk_ct** B_out);
+void circuit_rank_blocked_finish(rk_ctx* c, const rk_ct* const* A_in, const rk_ct* const* B_in, int L, rk_ct** outs);
 void circuit_rank_blocked_tc(rk_ctx* c, const rk_ct* const* blocks, int L, rk_ct** outs);
 void circuit_order_stat_blocked(rk_ctx* c, const rk_ct* const* blocks, int L, uint32_t k, rk_ct** outs);
 void circuit_sort_blocked(rk_ctx* c, const rk_ct* const* blocks, int L, rk_ct** outs);
@@ -27,6 +30,7 @@ void ntt_autotune(rk_ctx* c, std::vector<double>& report);
 void ks_autotune(rk_ctx* c, std::vector<double>& report);
 size_t server_latencies(rk_ctx* c, double* out, size_t cap);
 void server_stop(rk_ctx* c);
+void server_stats_lanes(rk_ctx* c, double out[5]);
 rk_ct* graph_rank_run(rk_graph* g, const rk_ct* in);
 void graph_free(rk_graph* g);
 rk_ctx* graph_context(const rk_graph* g);
@@ -178,6 +182,10 @@ rk_status rk_ctx_set_option(rk_ctx* ctx, uint32_t option, int64_t value) {
             case RK_OPT_KS_GROUP_BYTES: ctx->ks_group_bytes = (double)value; break;
             case RK_OPT_BLOCK_STACKING: ctx->stack_blocks = value != 0; break;
             case RK_OPT_TRIM_LEVELS: ctx->trim_levels = value != 0; break;
+            case RK_OPT_SERVER_LANES:
+                RK_REQUIRE(value >= 1 && value <= 16, RK_EINVAL, "server lanes must be 1 to 16");
+                ctx->server_lanes = (int)value;
+                break;
             default: throw rk_error(RK_EINVAL, "unknown option " + std::to_string(option));
         }
     });
@@ -260,15 +268,16 @@ rk_status rk_encoding_import(rk_ctx* ctx, uint32_t kind, uint32_t N, uint32_t Q,
         const uint32_t nr = mask_nreal(kind, n_real);
         ctx->encodings[std::make_tuple(kind, N, Q, nr)] = std::vector<double>(u, u + n);
         ctx->generation++;
-        for (auto it = ctx->plain_cache.begin(); it != ctx->plain_cache.end();) {
-            if (std::get<0>(it->first) == kind && std::get<1>(it->first) == N && std::get<2>(it->first) == Q &&
-                std::get<3>(it->first) == nr) {
-                cudaFree(it->second);
-                it = ctx->plain_cache.erase(it);
-            } else {
-                ++it;
+        for (auto* cache : {&ctx->plain_cache, &ctx->plain_add_cache})
+            for (auto it = cache->begin(); it != cache->end();) {
+                if (std::get<0>(it->first) == kind && std::get<1>(it->first) == N && std::get<2>(it->first) == Q &&
+                    std::get<3>(it->first) == nr) {
+                    cudaFree(it->second);
+                    it = cache->erase(it);
+                } else {
+                    ++it;
+                }
             }
-        }
     });
 }
 
@@ -680,6 +689,39 @@ rk_status rk_rank_blocked(rk_ctx* ctx, const rk_ct* const* blocks, uint32_t L, u
     });
 }
 
+rk_status rk_rank_blocked_partial(rk_ctx* ctx, const rk_ct* const* blocks, uint32_t L, const uint32_t* pair_i,
+                                  const uint32_t* pair_j, uint32_t npairs, rk_ct** A, rk_ct** B) {
+    return guard([&] {
+        need(ctx, "ctx");
+        need(blocks, "blocks");
+        need(A, "A");
+        need(B, "B");
+        RK_REQUIRE(npairs == 0 || (pair_i && pair_j), RK_EINVAL, "pair lists are NULL");
+        for (uint32_t i = 0; i < L; i++) same_ctx(ctx, blocks[i]);
+        std::vector<std::pair<int, int>> pairs;
+        for (uint32_t p = 0; p < npairs; p++) pairs.push_back({(int)pair_i[p], (int)pair_j[p]});
+        set_device(ctx);
+        circuit_rank_blocked_partial(ctx, blocks, (int)L, pairs, A, B);
+        check_launch();
+    });
+}
+
+rk_status rk_rank_blocked_finish(rk_ctx* ctx, const rk_ct* const* A, const rk_ct* const* B, uint32_t L, rk_ct** outs) {
+    return guard([&] {
+        need(ctx, "ctx");
+        need(A, "A");
+        need(B, "B");
+        need(outs, "outs");
+        for (uint32_t i = 0; i < L; i++) {
+            same_ctx(ctx, A[i]);
+            same_ctx(ctx, B[i]);
+        }
+        set_device(ctx);
+        circuit_rank_blocked_finish(ctx, A, B, (int)L, outs);
+        check_launch();
+    });
+}
+
 rk_status rk_order_stat_blocked(rk_ctx* ctx, const rk_ct* const* blocks, uint32_t L, uint32_t k, uint32_t flags,
                                 rk_ct** outs) {
     return guard([&] {
@@ -740,6 +782,14 @@ rk_status rk_server_stats(rk_ctx* ctx, double out[8]) {
         need(ctx, "ctx");
         need(out, "out");
         server_stats(ctx, out);
+    });
+}
+
+rk_status rk_server_stats_lanes(rk_ctx* ctx, double out[5]) {
+    return guard([&] {
+        need(ctx, "ctx");
+        need(out, "out");
+        server_stats_lanes(ctx, out);
     });
 }
 

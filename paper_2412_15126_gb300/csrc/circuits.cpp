@@ -763,14 +763,20 @@ static void check_blocks(rk_ctx* c, const rk_ct* const* blocks, int L, int need,
     check_square(c, b0, need, what);
 }
 
-// Alg. 7: ranks of a vector split into L blocks (one ciphertext each, same shape;
-// each block may be a stack of Bq members, block i of Bq queries).  The L blocks run
-// as one stack through ReplR/TransR/ReplC, the L(L+1)/2 block comparisons C_{i,j}
-// (j >= i) as one stack through Cmp; then
-// R_i = TransC(SumC(sum_{j<i} (1 - C_{j,i}))) + SumR(sum_{j>=i} C_{i,j}) + 1/2 (Eq. 3).
-void circuit_rank_blocked(rk_ctx* c, const rk_ct* const* blocks, int L, rk_ct** outs) {
+// Alg. 7 in two parts, so that the block comparisons (the parallel loop over block
+// pairs of Sec. 5) can be spread over several devices and their partial sums exchanged.
+// Part one: the comparisons C_{i,j} = Cmp(ReplR(V_i), ReplC(TransR(V_j))) of the listed
+// pairs (j >= i), and per block the partial sums A_i = sum of the listed C_{i,j} and
+// Bs_i = sum of the listed C_{j,i} with j < i (a zero ciphertext where no listed pair
+// contributes), all at the comparison's output level.  The L blocks (one ciphertext
+// each, same shape; each may be a stack of Bq members, block i of Bq queries) run as one
+// stack through ReplR/TransR/ReplC, the listed comparisons as one stack through Cmp.
+void circuit_rank_blocked_partial(rk_ctx* c, const rk_ct* const* blocks, int L, const std::vector<std::pair<int, int>>& pairs,
+                                  rk_ct** A_out, rk_ct** B_out) {
     const int need = 3 + cmp_depth(c);
     check_blocks(c, blocks, L, need, "blocked rank");
+    for (auto& pr : pairs)
+        RK_REQUIRE(pr.first >= 0 && pr.first <= pr.second && pr.second < L, RK_EINVAL, "block pair out of range");
     const int Bq = blocks[0]->B;
     Ev E{c};
     H V(ct_stack(c, blocks, L));
@@ -789,39 +795,55 @@ void circuit_rank_blocked(rk_ctx* c, const rk_ct* const* blocks, int L, rk_ct** 
         }
         rc = std::make_pair(stack_of(c, pr), stack_of(c, pc));
     }
-    std::vector<std::pair<int, int>> pairs;
-    std::map<std::pair<int, int>, int> pidx;
+    const int lvl = rc.second->level - cmp_depth(c);
+    std::vector<H> A(L), Bs(L);
+    if (!pairs.empty()) {
+        std::vector<H> vr_views, vc_views;
+        std::vector<rk_ct*> vr, vc;
+        for (auto& pr : pairs) {
+            vr_views.push_back(range(rc.first, pr.first, Bq));
+            vc_views.push_back(range(rc.second, pr.second, Bq));
+            vr.push_back(vr_views.back().p);
+            vc.push_back(vc_views.back().p);
+        }
+        H Cst = each(c, E, E.sub(stack_of(c, vr), stack_of(c, vc)),
+                     [&](H x) { return cmp(E, std::move(x), (int)c->prm.d_g, (int)c->prm.d_f); });
+        for (size_t p = 0; p < pairs.size(); p++) {
+            const int i = pairs[p].first, j = pairs[p].second;
+            H Cij = range(Cst, (int)p, Bq);
+            A[i] = A[i].p ? E.add(A[i], Cij) : E.copy(Cij);
+            if (j > i) Bs[j] = Bs[j].p ? E.add(Bs[j], Cij) : E.copy(Cij);
+        }
+    }
     for (int i = 0; i < L; i++)
-        for (int j = i; j < L; j++) {
-            pidx[{i, j}] = (int)pairs.size();
-            pairs.push_back({i, j});
-        }
-    std::vector<H> vr_views, vc_views;
-    std::vector<rk_ct*> vr, vc;
-    for (auto& pr : pairs) {
-        vr_views.push_back(range(rc.first, pr.first, Bq));
-        vc_views.push_back(range(rc.second, pr.second, Bq));
-        vr.push_back(vr_views.back().p);
-        vc.push_back(vc_views.back().p);
-    }
-    H Cst = each(c, E, E.sub(stack_of(c, vr), stack_of(c, vc)),
-                 [&](H x) { return cmp(E, std::move(x), (int)c->prm.d_g, (int)c->prm.d_f); });
-    auto Cv = [&](int i, int j) { return range(Cst, pidx[{i, j}], Bq); };
-    // A_i = sum_{j>=i} C_{i,j}, B_i = sum_{j<i} (1 - C_{j,i}) = i - sum_{j<i} C_{j,i}
-    std::vector<H> A, Bm;
+        for (H* h : {&A[i], &Bs[i]})
+            if (!h->p) {   // no listed pair: an encryption of zero with no noise
+                *h = H(ct_alloc_like(rc.second.p, lvl, Bq));
+                RK_CUDA(cudaMemsetAsync((*h)->data, 0, (size_t)Bq * c->ct_words() * 8, c->stream));
+                (*h)->level = lvl;
+            }
     for (int i = 0; i < L; i++) {
-        H a = E.copy(Cv(i, i));
-        for (int j = i + 1; j < L; j++) a = E.add(a, Cv(i, j));
-        A.push_back(std::move(a));
-        if (i > 0) {
-            H s = E.copy(Cv(0, i));
-            for (int j = 1; j < i; j++) s = E.add(s, Cv(j, i));
-            Bm.push_back(E.add_const(E.neg(s), (double)i));
-        }
+        A_out[i] = A[i].release();
+        B_out[i] = Bs[i].release();
     }
-    std::vector<rk_ct*> ap;
-    for (auto& a : A) ap.push_back(a.p);
-    H S = each(c, E, stack_of(c, ap), [&](H x) { return sum_r(E, std::move(x)); });   // stack of L Bq
+}
+
+// Part two, given every pair's contribution summed over the parts:
+// R_i = TransC(SumC(i - Bs_i)) + SumR(A_i) + 1/2 (Eq. 3: B_i = sum_{j<i} (1 - C_{j,i})).
+void circuit_rank_blocked_finish(rk_ctx* c, const rk_ct* const* A_in, const rk_ct* const* B_in, int L, rk_ct** outs) {
+    RK_REQUIRE(L >= 1, RK_EINVAL, "no blocks");
+    const rk_ct* a0 = A_in[0];
+    for (int i = 0; i < L; i++)
+        RK_REQUIRE(A_in[i]->level == a0->level && B_in[i]->level == a0->level && A_in[i]->B == a0->B &&
+                       B_in[i]->B == a0->B && A_in[i]->N == a0->N && B_in[i]->N == a0->N && A_in[i]->Q == a0->Q &&
+                       B_in[i]->Q == a0->Q,
+                   RK_EINVAL, "partial sums must share level, stack size and shape");
+    RK_REQUIRE(a0->level >= 2, RK_EDEPTH, "blocked rank: the partial sums need two levels");
+    const int Bq = a0->B;
+    Ev E{c};
+    std::vector<H> Bm;
+    for (int i = 1; i < L; i++) Bm.push_back(E.add_const(E.neg(H(ct_view_range(B_in[i], 0, Bq))), (double)i));
+    H S = each(c, E, H(ct_stack(c, A_in, L)), [&](H x) { return sum_r(E, std::move(x)); });   // stack of L Bq
     H T;
     if (L > 1) {
         std::vector<rk_ct*> bp;
@@ -843,6 +865,25 @@ void circuit_rank_blocked(rk_ctx* c, const rk_ct* const* blocks, int L, rk_ct** 
         rp.push_back(R.back().p);
     }
     split_blocks(c, stack_of(c, rp), L, outs);
+}
+
+// Alg. 7 on one device: every pair (j >= i), then the assembly.
+void circuit_rank_blocked(rk_ctx* c, const rk_ct* const* blocks, int L, rk_ct** outs) {
+    std::vector<std::pair<int, int>> pairs;
+    for (int i = 0; i < L; i++)
+        for (int j = i; j < L; j++) pairs.push_back({i, j});
+    std::vector<rk_ct*> A(L, nullptr), Bs(L, nullptr);
+    try {
+        circuit_rank_blocked_partial(c, blocks, L, pairs, A.data(), Bs.data());
+        std::vector<const rk_ct*> a(A.begin(), A.end()), b(Bs.begin(), Bs.end());
+        circuit_rank_blocked_finish(c, a.data(), b.data(), L, outs);
+    } catch (...) {
+        for (auto* p : A) ct_free(p);
+        for (auto* p : Bs) ct_free(p);
+        throw;
+    }
+    for (auto* p : A) ct_free(p);
+    for (auto* p : Bs) ct_free(p);
 }
 
 // 2 C^2 - C: 1 where the row-form value exceeds the column-form value, 0 at ties

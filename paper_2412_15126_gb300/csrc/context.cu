@@ -382,12 +382,78 @@ void ctx_build(rk_ctx* c, const rk_params* p, int device, void* stream) {
 
 void server_stop(rk_ctx* c);
 
+// An execution lane of `parent` for the serving loop: the parent's parameters, device
+// tables, keys, encodings and coefficients (shared, read only, never freed through the
+// lane), with a stream, a scratch area, plaintext caches and a profiler of its own, so
+// that circuits on different lanes run concurrently on the device.
+rk_ctx* ctx_lane_create(rk_ctx* parent) {
+    rk_ctx* c = new rk_ctx();
+    c->lane_of = parent;
+    c->prm = parent->prm;
+    c->device = parent->device;
+    c->log_n = parent->log_n;
+    c->n = parent->n;
+    c->L = parent->L;
+    c->alpha = parent->alpha;
+    c->dsize = parent->dsize;
+    c->n_primes = parent->n_primes;
+    c->primes = parent->primes;
+    c->scales = parent->scales;
+    c->ninv = parent->ninv;
+    c->d_tw = parent->d_tw;
+    c->d_conv = parent->d_conv;
+    c->d_pc = parent->d_pc;
+    c->h_pc = parent->h_pc;
+    c->h_pinv = parent->h_pinv;
+    c->d_sk = parent->d_sk;
+    c->h_sk = parent->h_sk;
+    c->d_pk = parent->d_pk;
+    c->rlk = parent->rlk;
+    c->gal = parent->gal;
+    c->seed = parent->seed;
+    c->tune = parent->tune;
+    c->ks_fused = parent->ks_fused;
+    c->stack_blocks = parent->stack_blocks;
+    c->trim_levels = parent->trim_levels;
+    c->ks_group_bytes = parent->ks_group_bytes;
+    c->ind_stack_bytes = parent->ind_stack_bytes;
+    c->cmp_coeffs = parent->cmp_coeffs;
+    c->encodings = parent->encodings;
+    c->indicator = parent->indicator;
+    c->env = parent->env;
+    c->env.prof = &c->prof;
+    c->env.tune = &c->tune;
+    try {
+        RK_CUDA(cudaSetDevice(c->device));
+        RK_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+        c->own_stream = true;
+    } catch (...) {
+        delete c;
+        throw;
+    }
+    return c;
+}
+
+// Frees what the lane owns (stream, scratch, cached plaintexts, events) and the lane.
+void ctx_lane_release(rk_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (auto& kv : c->plain_cache) cudaFree(kv.second);
+    for (auto& kv : c->plain_add_cache) cudaFree(kv.second);
+    if (c->d_scratch) cudaFree(c->d_scratch);
+    for (cudaEvent_t ev : c->prof.ev) cudaEventDestroy(ev);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
 void ctx_release(rk_ctx* c) {
     if (!c) return;
     server_stop(c);
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     for (auto& kv : c->plain_cache) cudaFree(kv.second);
+    for (auto& kv : c->plain_add_cache) cudaFree(kv.second);
     for (auto& kv : c->gal) cudaFree(kv.second.data);
     if (c->rlk.data) cudaFree(c->rlk.data);
     if (c->d_sk) cudaFree(c->d_sk);

@@ -234,6 +234,8 @@ struct rk_ctx {
     size_t scratch_words = 0;
     int batch_cap = 1;            // largest stack B the scratch layout is sized for
     rk_server* server = nullptr;  // serving loop, when one runs (it owns the stream meanwhile)
+    rk_ctx* lane_of = nullptr;    // a serving lane: the context whose tables and keys it shares
+    int server_lanes = 2;         // lanes (concurrent batches) of the next serving loop
     // Bumped whenever a buffer that captured CUDA graphs point into is replaced (scratch
     // growth, switching keys, cached plaintexts, indicator coefficients).
     uint64_t generation = 0;

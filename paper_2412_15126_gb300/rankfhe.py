@@ -31,6 +31,7 @@ TIES_FIRST, TIES_ALL = 0, 2
 MASK_ROW0S, MASK_COL0S, MASK_TIEC, MASK_SORTIDX, MASK_ROWIDX = 6, 7, 8, 9, 10
 OPT_KS_FUSED, OPT_KS_GROUP_BYTES, OPT_BLOCK_STACKING = 1, 2, 3
 OPT_TRIM_LEVELS = 4
+OPT_SERVER_LANES = 5
 OP_RANK, OP_ORDER_STAT, OP_SORT, OP_RANK_BLOCKED, OP_ORDER_STAT_BLOCKED, OP_SORT_BLOCKED = 1, 2, 3, 4, 5, 6
 
 
@@ -93,6 +94,9 @@ _sig("rk_ct_stack", [_vp, ctypes.POINTER(_vp), _u32, ctypes.POINTER(_vp)])
 _sig("rk_rank_blocked", [_vp, ctypes.POINTER(_vp), _u32, _u32, ctypes.POINTER(_vp)])
 _sig("rk_ct_unstack", [_vp, _vp, ctypes.POINTER(_vp)])
 _sig("rk_order_stat_blocked", [_vp, ctypes.POINTER(_vp), _u32, _u32, _u32, ctypes.POINTER(_vp)])
+_sig("rk_rank_blocked_partial", [_vp, ctypes.POINTER(_vp), _u32, ctypes.POINTER(_u32), ctypes.POINTER(_u32), _u32,
+                                 ctypes.POINTER(_vp), ctypes.POINTER(_vp)])
+_sig("rk_rank_blocked_finish", [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _u32, ctypes.POINTER(_vp)])
 _sig("rk_sort_blocked", [_vp, ctypes.POINTER(_vp), _u32, _u32, ctypes.POINTER(_vp)])
 _sig("rk_ct_count", [_vp], _u32)
 _sig("rk_rotate", [_vp, _vp, ctypes.c_int32, ctypes.POINTER(_vp)])
@@ -122,6 +126,7 @@ _sig("rk_server_submit", [_vp, _u32, _u32, _u32, _vp, ctypes.POINTER(ctypes.c_ui
 _sig("rk_server_wait", [_vp, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(_vp)])
 _sig("rk_server_poll", [_vp, ctypes.c_uint64, ctypes.POINTER(_vp)])
 _sig("rk_server_stats", [_vp, _dp])
+_sig("rk_server_stats_lanes", [_vp, _dp])
 _sig("rk_server_stop", [_vp])
 _sig("rk_server_latencies", [_vp, _dp, _sz, ctypes.POINTER(_sz)])
 _sig("rk_graph_rank", [_vp, _vp, _u32, ctypes.POINTER(_vp)])
@@ -374,6 +379,26 @@ class Context:
         _check(_L.rk_rank_blocked(self.handle, ins, len(blocks), flags, outs))
         return [Ciphertext(self, o) for o in outs]
 
+    def rank_blocked_partial(self, blocks, pairs):
+        """Part one of the partitioned blocked rank: the comparisons of the listed block
+        pairs (i <= j) and the per-block partial sums (A, B), L ciphertexts each."""
+        L = len(blocks)
+        ins = (_vp * L)(*[c.handle.value for c in blocks])
+        pi = (_u32 * max(len(pairs), 1))(*[int(p[0]) for p in pairs])
+        pj = (_u32 * max(len(pairs), 1))(*[int(p[1]) for p in pairs])
+        A, B = (_vp * L)(), (_vp * L)()
+        _check(_L.rk_rank_blocked_partial(self.handle, ins, L, pi, pj, len(pairs), A, B))
+        return [Ciphertext(self, a) for a in A], [Ciphertext(self, b) for b in B]
+
+    def rank_blocked_finish(self, A, B):
+        """Part two: the blocked ranks from the partial sums over every pair."""
+        L = len(A)
+        a = (_vp * L)(*[c.handle.value for c in A])
+        b = (_vp * L)(*[c.handle.value for c in B])
+        outs = (_vp * L)()
+        _check(_L.rk_rank_blocked_finish(self.handle, a, b, L, outs))
+        return [Ciphertext(self, o) for o in outs]
+
     def order_stat_blocked(self, blocks, k, flags=0):
         ins = (_vp * len(blocks))(*[c.handle.value for c in blocks])
         outs = (_vp * len(blocks))()
@@ -491,6 +516,12 @@ class Context:
         _check(_L.rk_server_stats(self.handle, out))
         keys = ("finished", "p50_s", "p99_s", "max_s", "batches", "mean_batch", "peak_bytes", "queued")
         return dict(zip(keys, list(out)))
+
+    def server_stats_lanes(self) -> dict:
+        out = (ctypes.c_double * 5)()
+        _check(_L.rk_server_stats_lanes(self.handle, out))
+        return {"lanes": int(out[0]), "max_lanes_busy": int(out[1]), "mean_lanes_busy": out[2],
+                "packed_requests": int(out[3]), "lane_scratch_bytes": out[4]}
 
     def server_latencies(self) -> list:
         cnt = _sz()

@@ -135,3 +135,29 @@ def test_block_stacking_option_changes_nothing(ordb):
         ctx.set_option(rankfhe.OPT_BLOCK_STACKING, 1)
     for a, b in zip(stacked, plain):
         assert np.array_equal(a, b)
+
+
+def test_blocked_rank_in_parts_bit_exact(ordb):
+    """Alg. 7 with the block pairs divided in two parts (rk_rank_blocked_partial), the
+    partial sums added (rk_add) and assembled (rk_rank_blocked_finish): bit for bit the
+    oracle's blocked rank; the distributed helper with one rank gives the same."""
+    from paper_2412_15126_gb300 import blocked_dist
+    P, keys, ctx = ordb
+    v = np.array([0.75, 0.125, 0.5, 0.0, 0.625, 0.25, 0.875, 0.375, 0.3125, 0.5625, 0.1875, 0.9375])
+    cts, g = _encrypt_blocks(P, keys, ctx, v, 70)
+    ref = C.rank_blocked(C.OracleCkks(P, keys), cts, BSZ, 1, 1)
+    parts = blocked_dist.pair_partition(3, 2)
+    A0, B0 = ctx.rank_blocked_partial(g, parts[0])
+    A1, B1 = ctx.rank_blocked_partial(g, parts[1])
+    got = ctx.rank_blocked_finish([ctx.add(a, b) for a, b in zip(A0, A1)], [ctx.add(a, b) for a, b in zip(B0, B1)])
+    for a, b in zip(got, ref):
+        assert a.level == b.level
+        assert np.array_equal(a.export(), b.c)
+    one = blocked_dist.blocked_rank_distributed(blocked_dist.CudaEvaluator(ctx, BSZ), g, 0, 1)
+    for a, b in zip(one, ref):
+        assert np.array_equal(a.export(), b.c)
+    # the exchange form: a part's sums exported and imported again change nothing
+    ev = blocked_dist.CudaEvaluator(ctx, BSZ)
+    back = [ev.import_(ev.export(a), a) for a in A1]
+    for a, b in zip(back, A1):
+        assert np.array_equal(a.export(), b.export())
