@@ -185,6 +185,57 @@ def order_sort_workload(stream, device, reps=3, seed=3):
         ctx.close()
 
 
+def blocked_packing_workload(stream, device, reps=1):
+    """Blocked rank, argmin and sort of 512 values (4 blocks of 128, Alg. 7, Alg. 4 on
+    blocked ranks, Alg. 8) at n = 2^16, 39 + 3 limbs, scale 2^40, Cmp g^4 f^2, values
+    distinct with gap >= 2^-9: latency with the block-pair work packed two to a
+    ciphertext (RK_OPT_PAIR_PACKING, the rotation by n/4 keyed) and without; CUDA events
+    on the library stream, inputs resident."""
+    import numpy as np
+    import torch
+    from paper_2412_15126_gb300 import inputs, rankfhe
+    from oracle.circuits import brute_fractional_rank, brute_tie_corrected_rank   # brute-force definitions only
+    W = SERVE_SORT
+    ctx = rankfhe.Context(W["log_n"], W["n_limbs"], W["n_special"], W["digit_size"], W["log_scale"], W["log_q0"],
+                          W["log_special"], W["d_g"], W["d_f"], device=device, stream=stream.cuda_stream)
+    try:
+        ctx.keygen(4321, 128)
+        ctx.keygen_rotations([ctx.n // 4])
+        v = inputs.gap_vector(512, 2.0 ** -9, 4322)
+        blocks = [ctx.encrypt(v[128 * b:128 * (b + 1)], N=128) for b in range(4)]
+        ops = {
+            "rank": (lambda: ctx.rank_blocked(blocks), brute_fractional_rank(v)),
+            "argmin": (lambda: ctx.order_stat_blocked(blocks, 1), np.eye(512)[int(np.argmin(v))]),
+            "sort": (lambda: ctx.sort_blocked(blocks), np.sort(v)),
+        }
+        out = {"workload": "N=512 as 4 blocks of 128, gap 2^-9, n=2^16, 39+3 limbs, scale 2^40, Cmp g^4 f^2, "
+                           "indicator 4096 coefficients"}
+        for name, (fn, want) in ops.items():
+            res = {}
+            for packed in (1, 0):
+                ctx.set_option(rankfhe.OPT_PAIR_PACKING, packed)
+                for r in fn():
+                    r.free()            # warm-up: masks, scratch
+                ctx.sync()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                with torch.cuda.stream(stream):
+                    e0.record(stream)
+                    for _ in range(reps):
+                        got = fn()
+                    e1.record(stream)
+                e1.synchronize()
+                dec = np.concatenate([ctx.decrypt(g) for g in got])
+                res["packed" if packed else "unpacked"] = {"ms": e0.elapsed_time(e1) / reps,
+                                                           "max_error": float(np.max(np.abs(dec - want)))}
+            res["speedup"] = res["unpacked"]["ms"] / res["packed"]["ms"]
+            out[name] = res
+        ctx.set_option(rankfhe.OPT_PAIR_PACKING, 1)
+        return out
+    finally:
+        ctx.close()
+
+
 # ---------------------------------------------------------------------------
 # serving: Poisson arrivals of mixed rank / argmin / sort requests
 # ---------------------------------------------------------------------------
@@ -1040,6 +1091,10 @@ def run_cuda(args):
         small = small_rank_workload(stream, local)
         cheb = cheb_comparator_workload(stream, local)
 
+    blocked = None
+    if not args.no_order_sort and world == 1:
+        blocked = blocked_packing_workload(stream, local)
+
     serving = None
     if args.serve and world == 1:
         serving = serving_workload(stream, torch.cuda.Stream(), local, count=args.serve)
@@ -1086,6 +1141,7 @@ def run_cuda(args):
             "batched": batched,
             "graph": graph, "trimmed_levels": trimmed,
             "order_sort": order_sort,
+            "blocked_512": blocked,
             "rank8": small,
             "cheb_comparator": cheb,
             "serving": serving,

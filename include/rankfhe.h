@@ -130,6 +130,16 @@ rk_status rk_ctx_counters(const rk_ctx* ctx, uint64_t out[4]);
  * RK_OPT_BLOCK_STACKING: 1 (default) runs the blocks and block pairs of
  *   rk_rank_blocked (flags 0) as stacks; 0 runs every block and pair ciphertext with
  *   its own launches (the plain per-query form, for comparison).  Same results.
+ * RK_OPT_PAIR_PACKING: 1 (default) lets the blocked circuits (rk_rank_blocked,
+ *   rk_order_stat_blocked, rk_sort_blocked and rk_rank_blocked_partial) pack their
+ *   block-pair work into the free tiles of a ciphertext: a block of B values fills
+ *   Q B^2 of the n/2 slots, so up to T = (n/2)/(Q B^2) comparisons (and, for the
+ *   blocked order statistic and sort, indicators) run as one ciphertext, moved in and
+ *   out by trees of rotations by +-Q B^2 2^s.  It applies when T >= 2, block stacking
+ *   is on and the keys of those rotations exist (rk_keygen makes all of them for
+ *   B <= max_len / 2 and all but +-n/4 otherwise); the ciphertexts then carry the
+ *   packing rotations' noise (same decryption within the circuits' tolerance).  0 runs
+ *   every pair on its own ciphertext.
  * RK_OPT_SERVER_LANES: execution lanes of the next rk_server_start (1 to 16, default 2):
  *   each runs its own batch on its own stream, so batches overlap on the device.
  * RK_OPT_TRIM_LEVELS: 0 (default) evaluates rk_rank / rk_rank_batch at the input's
@@ -145,6 +155,7 @@ rk_status rk_ctx_counters(const rk_ctx* ctx, uint64_t out[4]);
 #define RK_OPT_BLOCK_STACKING 3
 #define RK_OPT_TRIM_LEVELS 4
 #define RK_OPT_SERVER_LANES 5
+#define RK_OPT_PAIR_PACKING 6
 rk_status rk_ctx_set_option(rk_ctx* ctx, uint32_t option, int64_t value);
 
 /* Autotune the launch shapes on this device (the paper has no counterpart): times

@@ -393,18 +393,63 @@ def rank(B, V, N, dg, df, Q=1, n_real=None, trim=False):
     return B.add_const(sum_r(B, C, N, Q), 0.5)
 
 
-def rank_blocked(B, Vs, Bsz, dg, df, Q=1):
+def pack_tiles(B, xs, tile, per):
+    """Pack ciphertexts whose slots outside [0, tile) are zero into groups of `per`:
+    member k of a group moves to tile k (slots k tile + [0, tile)) by a tree of
+    rotations (at step s = 1, 2, 4 ..: x_i += x_(i+s) >> s tile for every i whose
+    place in its group is a multiple of 2s).  Returns one ciphertext per group."""
+    xs = list(xs)
+    m = len(xs)
+    s = 1
+    while s < per:
+        for i in range(m):
+            g = i % per
+            if g % (2 * s) == 0 and g + s < per and i + s < m:
+                xs[i] = B.add(xs[i], B.rot(xs[i + s], -tile * s))
+        s *= 2
+    return [xs[g * per] for g in range((m + per - 1) // per)]
+
+
+def unpack_tiles(B, ys, counts, tile):
+    """Inverse of pack_tiles: member k of group g is ys[g] rotated left by k tile (a
+    tree: entry j + s = entry j << s tile), so its tile-0 slots hold what tile k held."""
+    out = []
+    for y, c in zip(ys, counts):
+        part = [None] * c
+        part[0] = y
+        s = 1
+        while s < c:
+            for j in range(s):
+                if j + s < c:
+                    part[j + s] = B.rot(part[j], tile * s)
+            s *= 2
+        out += part
+    return out
+
+
+def packed_apply(B, xs, tile, per, f):
+    """f on every x of xs, with the xs packed `per` to a ciphertext (per = 1: one by
+    one): f must act slot by slot, and the xs must be zero outside [0, tile)."""
+    if per <= 1:
+        return [f(x) for x in xs]
+    packed = pack_tiles(B, xs, tile, per)
+    counts = [min(per, len(xs) - g * per) for g in range(len(packed))]
+    return unpack_tiles(B, [f(p) for p in packed], counts, tile)
+
+
+def rank_blocked(B, Vs, Bsz, dg, df, Q=1, pack=1):
     """Alg. 7, multi-ciphertext ranking of a vector split into L blocks of Bsz values
     (block i in row 0 of Vs[i]).  C_{i,j} = Cmp(ReplR(V_i), ReplC(TransR(V_j))) for
     j >= i only; by Eq. 3 the blocks j < i enter as 1 - C_{j,i}, summed column-wise
     and transposed:  R_i = TransC(SumC(sum_{j<i} (1 - C_{j,i}))) + SumR(sum_{j>=i} C_{i,j}) + 1/2.
-    All R_i leave at the level of the TransC branch (SumR's branch is brought down)."""
+    All R_i leave at the level of the TransC branch (SumR's branch is brought down).
+    pack > 1: the comparisons run `pack` block pairs to a ciphertext (pairs in their
+    listed order, i then j, packed into tiles of Q Bsz^2 slots by pack_tiles)."""
     L = len(Vs)
     forms = [row_col_forms(B, V, Bsz, Q) for V in Vs]
-    Cs = {}
-    for i in range(L):
-        for j in range(i, L):
-            Cs[(i, j)] = cmp(B, B.sub(forms[i][0], forms[j][1]), dg, df)
+    pairs = [(i, j) for i in range(L) for j in range(i, L)]
+    diffs = [B.sub(forms[i][0], forms[j][1]) for i, j in pairs]
+    Cs = dict(zip(pairs, packed_apply(B, diffs, Q * Bsz * Bsz, pack, lambda x: cmp(B, x, dg, df))))
     out = []
     for i in range(L):
         A = Cs[(i, i)]
@@ -429,7 +474,7 @@ def cmp_strict(B, C):
     return B.sub(B.add(C2, C2), B.level_down(C, B.level(C2)))
 
 
-def rank_blocked_tc(B, Vs, Bsz, dg, df, Q=1, scaled=False):
+def rank_blocked_tc(B, Vs, Bsz, dg, df, Q=1, scaled=False, pack=1):
     """Tie-corrected multi-ciphertext ranking (Alg. 7 with Alg. 6): the rank of element
     b of block i counts the smaller elements and the equal ones at or before it in the
     global order (block i, position b).  Per block pair (Eq. 3 for j < i):
@@ -437,16 +482,21 @@ def rank_blocked_tc(B, Vs, Bsz, dg, df, Q=1, scaled=False):
         j > i:  SumR(G_ij)                 G = 2C^2 - C, strictly smaller elements of block j
         j < i:  TransC(SumC(1 - G_ji))     elements of block j not larger (all earlier ties count)
     scaled: every rank leaves divided by the total length D = L Bsz (masks 'row0s' with
-    denominator D), the form the indicator of Alg. 4 and 8 takes.
+    denominator D), the form the indicator of Alg. 4 and 8 takes.  pack > 1: the
+    diagonal comparisons, and the upper ones with their Cmp_G, run `pack` to a
+    ciphertext (pack_tiles).
     Returns the rank blocks (all at one level) and the ReplR forms of the blocks."""
     L = len(Vs)
     D = L * Bsz
     forms = [row_col_forms(B, V, Bsz, Q) for V in Vs]
-    Cs = {}
-    for i in range(L):
-        for j in range(i, L):
-            Cs[(i, j)] = cmp(B, B.sub(forms[i][0], forms[j][1]), dg, df)
-    Gs = {(i, j): cmp_strict(B, Cs[(i, j)]) for i in range(L) for j in range(i + 1, L)}
+    tile = Q * Bsz * Bsz
+    diag = packed_apply(B, [B.sub(forms[i][0], forms[i][1]) for i in range(L)], tile, pack,
+                        lambda x: cmp(B, x, dg, df))
+    Cs = {(i, i): diag[i] for i in range(L)}
+    upper = [(i, j) for i in range(L) for j in range(i + 1, L)]
+    ups = packed_apply(B, [B.sub(forms[i][0], forms[j][1]) for i, j in upper], tile, pack,
+                       lambda x: cmp_strict(B, cmp(B, x, dg, df)))
+    Gs = dict(zip(upper, ups))
     rmask = ("row0s", Bsz, Q, D) if scaled else ("row0", Bsz, Q)
     out = []
     for i in range(L):
@@ -469,30 +519,37 @@ def rank_blocked_tc(B, Vs, Bsz, dg, df, Q=1, scaled=False):
     return out, [f[0] for f in forms]
 
 
-def order_statistic_blocked(B, Vs, Bsz, k, dg, df, Q=1, coeffs=None):
+def order_statistic_blocked(B, Vs, Bsz, k, dg, df, Q=1, coeffs=None, pack=1):
     """Alg. 4 over a multi-ciphertext vector: O_i = Ind_k(R_i) on the tie-corrected
-    block ranks, one-hot at the first element of global rank k."""
+    block ranks, one-hot at the first element of global rank k.  pack > 1: the block
+    ranks (zero outside their tile) are packed before the constant -k/D is added, and
+    the indicators run `pack` to a ciphertext."""
     D = len(Vs) * Bsz
     coeffs = sinc2_window_coeffs(D) if coeffs is None else coeffs
-    Rs, _ = rank_blocked_tc(B, Vs, Bsz, dg, df, Q, scaled=True)
-    return [cheb_ps(B, B.add_const(R, -k / D), coeffs) for R in Rs]
+    Rs, _ = rank_blocked_tc(B, Vs, Bsz, dg, df, Q, scaled=True, pack=pack)
+    return packed_apply(B, Rs, Q * Bsz * Bsz, pack, lambda R: cheb_ps(B, B.add_const(R, -k / D), coeffs))
 
 
-def sort_blocked(B, Vs, Bsz, dg, df, Q=1, coeffs=None):
+def sort_blocked(B, Vs, Bsz, dg, df, Q=1, coeffs=None, pack=1):
     """Alg. 8 (multi-ciphertext sorting) on tie-corrected ranks:
         S_i = TransC(SumC(sum_j Ind_0(ReplR(R_j) - offset_i) . ReplR(V_j)))
     offset_i holds B i + a + 1 in row a (0-based block i): mask 'rowidx' plus the
-    constant -B i / D, with ranks and offsets divided by D = L B."""
+    constant -B i / D, with ranks and offsets divided by D = L B.  pack > 1: the
+    comparisons of the ranking and, per output block, its L indicators run `pack` to
+    a ciphertext."""
     L = len(Vs)
     D = L * Bsz
     coeffs = sinc2_window_coeffs(D) if coeffs is None else coeffs
-    Rs, VRs = rank_blocked_tc(B, Vs, Bsz, dg, df, Q, scaled=True)
+    Rs, VRs = rank_blocked_tc(B, Vs, Bsz, dg, df, Q, scaled=True, pack=pack)
     RR = [B.add_plain(repl_r(B, R, Bsz), ("rowidx", Bsz, Q, D)) for R in Rs]
     out = []
     for i in range(L):
+        # the L indicators of output block i: RR_j (zero outside its tile) packed, then
+        # the constant -B i / D, common to the group, added to every slot
+        Ms = packed_apply(B, RR, Q * Bsz * Bsz, pack, lambda x: cheb_ps(B, B.add_const(x, -Bsz * i / D), coeffs))
         acc = None
         for j in range(L):
-            M = cheb_ps(B, B.add_const(RR[j], -Bsz * i / D), coeffs)
+            M = Ms[j]
             P = B.mul(M, B.level_down(VRs[j], B.level(M)))
             acc = P if acc is None else B.add(acc, P)
         out.append(trans_c(B, sum_c(B, acc, Bsz, Q), Bsz, Q))

@@ -182,6 +182,7 @@ rk_status rk_ctx_set_option(rk_ctx* ctx, uint32_t option, int64_t value) {
             case RK_OPT_KS_GROUP_BYTES: ctx->ks_group_bytes = (double)value; break;
             case RK_OPT_BLOCK_STACKING: ctx->stack_blocks = value != 0; break;
             case RK_OPT_TRIM_LEVELS: ctx->trim_levels = value != 0; break;
+            case RK_OPT_PAIR_PACKING: ctx->pair_packing = value != 0; break;
             case RK_OPT_SERVER_LANES:
                 RK_REQUIRE(value >= 1 && value <= 16, RK_EINVAL, "server lanes must be 1 to 16");
                 ctx->server_lanes = (int)value;

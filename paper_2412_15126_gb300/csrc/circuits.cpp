@@ -763,6 +763,72 @@ static void check_blocks(rk_ctx* c, const rk_ct* const* blocks, int L, int need,
     check_square(c, b0, need, what);
 }
 
+// Tiles of Q B^2 slots a ciphertext of blocks shaped like `like` holds, when block-pair
+// work may be packed into them: stacking on, packing on, at least two tiles, and the
+// packing rotations' keys (left by +-T 2^s, 2^s below the tile count) present; else 1.
+static int pair_tiles(const rk_ctx* c, const rk_ct* like) {
+    if (!c->pair_packing || !c->stack_blocks) return 1;
+    const size_t T = (size_t)like->Q * like->N * like->N;
+    const size_t tiles = (size_t)c->n / 2 / T;
+    if (tiles < 2) return 1;
+    for (size_t s = 1; s < tiles; s <<= 1)
+        for (int64_t r : {-(int64_t)(T * s), (int64_t)(T * s)})
+            if (!c->gal.count(galois_left(c, (int)r))) return 1;
+    return (int)tiles;
+}
+
+// f on each of the m members (Bq ciphertexts each) of the stack X, the members packed
+// `per` to a ciphertext: member k of a group moves to tile k (slots k T + [0, T)) by a
+// tree of stacked rotations (step s: x_i += x_(i+s) >> s T for every i whose place in
+// its group is a multiple of 2s), f runs once on the stack of groups, and the results
+// come back by the mirrored tree (entry j + s = entry j << s T).  f must act slot by
+// slot and the members must be zero outside their first tile.  per = 1: f on X.
+template <class F>
+static H packed_apply(rk_ctx* c, Ev& E, H X, int m, int Bq, int T, int per, F f) {
+    if (per <= 1) return f(std::move(X));
+    std::vector<H> xs;
+    for (int i = 0; i < m; i++) xs.push_back(E.copy(range(X, i, Bq)));
+    X = H();
+    for (int s = 1; s < per; s <<= 1) {
+        std::vector<int> lo, hi;
+        for (int i = 0; i < m; i++) {
+            const int g = i % per;
+            if (g % (2 * s) == 0 && g + s < per && i + s < m) {
+                lo.push_back(i);
+                hi.push_back(i + s);
+            }
+        }
+        if (lo.empty()) continue;
+        std::vector<rk_ct*> hp;
+        for (int h : hi) hp.push_back(xs[h].p);
+        H R = E.rot(stack_of(c, hp), -T * s);
+        for (size_t p = 0; p < lo.size(); p++) xs[lo[p]] = E.add(xs[lo[p]], range(R, (int)p, Bq));
+    }
+    const int G = (m + per - 1) / per;
+    std::vector<rk_ct*> gp;
+    for (int g = 0; g < G; g++) gp.push_back(xs[g * per].p);
+    H P = stack_of(c, gp);
+    xs.clear();
+    H Y = f(std::move(P));
+    std::vector<H> parts(m);
+    for (int g = 0; g < G; g++) parts[g * per] = E.copy(range(Y, g, Bq));
+    for (int s = 1; s < per; s <<= 1) {
+        std::vector<std::pair<int, int>> src;
+        for (int g = 0; g < G; g++) {
+            const int cnt = std::min(per, m - g * per);
+            for (int j = 0; j < s && j + s < cnt; j++) src.push_back({g * per + j, g * per + j + s});
+        }
+        if (src.empty()) continue;
+        std::vector<rk_ct*> sp;
+        for (auto& pr : src) sp.push_back(parts[pr.first].p);
+        H R = E.rot(stack_of(c, sp), T * s);
+        for (size_t p = 0; p < src.size(); p++) parts[src[p].second] = E.copy(range(R, (int)p, Bq));
+    }
+    std::vector<rk_ct*> pp;
+    for (auto& h : parts) pp.push_back(h.p);
+    return stack_of(c, pp);
+}
+
 // Alg. 7 in two parts, so that the block comparisons (the parallel loop over block
 // pairs of Sec. 5) can be spread over several devices and their partial sums exchanged.
 // Part one: the comparisons C_{i,j} = Cmp(ReplR(V_i), ReplC(TransR(V_j))) of the listed
@@ -806,8 +872,12 @@ void circuit_rank_blocked_partial(rk_ctx* c, const rk_ct* const* blocks, int L, 
             vr.push_back(vr_views.back().p);
             vc.push_back(vc_views.back().p);
         }
-        H Cst = each(c, E, E.sub(stack_of(c, vr), stack_of(c, vc)),
-                     [&](H x) { return cmp(E, std::move(x), (int)c->prm.d_g, (int)c->prm.d_f); });
+        const int per = pair_tiles(c, blocks[0]);
+        const int T = (int)(blocks[0]->Q * blocks[0]->N * blocks[0]->N);
+        H Cst = per > 1 ? packed_apply(c, E, E.sub(stack_of(c, vr), stack_of(c, vc)), (int)pairs.size(), Bq, T, per,
+                                       [&](H x) { return cmp(E, std::move(x), (int)c->prm.d_g, (int)c->prm.d_f); })
+                        : each(c, E, E.sub(stack_of(c, vr), stack_of(c, vc)),
+                               [&](H x) { return cmp(E, std::move(x), (int)c->prm.d_g, (int)c->prm.d_f); });
         for (size_t p = 0; p < pairs.size(); p++) {
             const int i = pairs[p].first, j = pairs[p].second;
             H Cij = range(Cst, (int)p, Bq);
@@ -933,10 +1003,15 @@ static std::pair<H, H> blocked_ranks_tc(rk_ctx* c, const rk_ct* const* blocks, i
             ur.push_back(dr[i]);
             uc.push_back(dcol[j]);
         }
-    H F = tie_fold(E, cmp(E, E.sub(stack_of(c, dr), stack_of(c, dcol)), dg, df), RK_MASK_TIE);
+    const int per = pair_tiles(c, blocks[0]);
+    const int tile = (int)(blocks[0]->Q * Bsz * Bsz);
+    H F = tie_fold(E, packed_apply(c, E, E.sub(stack_of(c, dr), stack_of(c, dcol)), L, Bq, tile, per,
+                                   [&](H x) { return cmp(E, std::move(x), dg, df); }),
+                   RK_MASK_TIE);
     H G, Gd;
     if (L > 1) {
-        G = cmp_strict(E, cmp(E, E.sub(stack_of(c, ur), stack_of(c, uc)), dg, df));
+        G = packed_apply(c, E, E.sub(stack_of(c, ur), stack_of(c, uc)), (int)ur.size(), Bq, tile, per,
+                         [&](H x) { return cmp_strict(E, cmp(E, std::move(x), dg, df)); });
         Gd = E.level_down(G, F->level);
     }
     std::vector<H> A, Bm;
@@ -998,7 +1073,8 @@ void circuit_order_stat_blocked(rk_ctx* c, const rk_ct* const* blocks, int L, ui
     check_blocks(c, blocks, L, blocked_rank_tc_depth(c) + cheb_depth((int)co.size()), "blocked order statistic");
     auto rr = blocked_ranks_tc(c, blocks, L, true);
     Ev E{c};
-    H O = cheb_ps(E, E.add_const(rr.first, -(double)k / D), co);
+    H O = packed_apply(c, E, std::move(rr.first), L, blocks[0]->B, (int)(blocks[0]->Q * blocks[0]->N * blocks[0]->N),
+                       pair_tiles(c, blocks[0]), [&](H x) { return cheb_ps(E, E.add_const(x, -(double)k / D), co); });
     split_blocks(c, O, L, outs);
 }
 
@@ -1020,8 +1096,30 @@ void circuit_sort_blocked(rk_ctx* c, const rk_ct* const* blocks, int L, rk_ct** 
     const size_t live = (size_t)baby_steps((int)co.size()) + 2 * (size_t)cheb_depth((int)co.size()) + 8;
     const int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)L * L, c->ind_stack_bytes / (live * ct_bytes)));
     std::vector<H> acc(L);
+    const int per = pair_tiles(c, blocks[0]);
+    if (per > 1) {
+        // per output block i, its L indicators packed `per` to a ciphertext: the RR_j
+        // (zero outside their tile) packed, the constant -B i / D added to every slot
+        const int T = (int)(blocks[0]->Q * Bsz * Bsz);
+        for (int i = 0; i < L; i++) {
+            H M = packed_apply(c, E, E.copy(RR), L, Bq, T, per, [&](H x) {
+                return cheb_ps(E, E.add_const(x, -(double)Bsz * i / D), co);
+            });
+            std::vector<H> vr;
+            std::vector<rk_ct*> vp;
+            for (int j = 0; j < L; j++) {
+                vr.push_back(E.level_down(range(rr.second, j, Bq), M->level));
+                vp.push_back(vr.back().p);
+            }
+            H P = E.mul(M, stack_of(c, vp));
+            for (int j = 0; j < L; j++) {
+                H pm = range(P, j, Bq);
+                acc[i] = acc[i].p ? E.add(acc[i], pm) : E.copy(pm);
+            }
+        }
+    }
     std::vector<std::pair<int, int>> pairs;
-    for (int i = 0; i < L; i++)
+    for (int i = 0; i < L && per <= 1; i++)
         for (int j = 0; j < L; j++) pairs.push_back({i, j});
     for (size_t p0 = 0; p0 < pairs.size(); p0 += chunk) {
         const size_t p1 = std::min(pairs.size(), p0 + chunk);

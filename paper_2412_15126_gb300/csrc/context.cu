@@ -415,6 +415,7 @@ rk_ctx* ctx_lane_create(rk_ctx* parent) {
     c->ks_fused = parent->ks_fused;
     c->stack_blocks = parent->stack_blocks;
     c->trim_levels = parent->trim_levels;
+    c->pair_packing = parent->pair_packing;
     c->ks_group_bytes = parent->ks_group_bytes;
     c->ind_stack_bytes = parent->ind_stack_bytes;
     c->cmp_coeffs = parent->cmp_coeffs;

@@ -243,6 +243,7 @@ struct rk_ctx {
     bool ks_fused = false;        // key switching with conversions fused into the NTT passes
     bool stack_blocks = true;     // blocked rank: blocks and block pairs as stacks (else one by one)
     bool trim_levels = false;     // rank: bring the input down to the level the circuit needs first
+    bool pair_packing = true;     // blocked circuits: pack block-pair work into free tiles when keys allow
     double ks_group_bytes = 48.0 * (1 << 20);   // lifted digits kept in L2 between the fused kernels
     size_t ind_stack_bytes = (size_t)4 << 30;   // working set of one stacked indicator evaluation
     u64* noalloc_scratch = nullptr;             // device address of the allocation-free rescale's array

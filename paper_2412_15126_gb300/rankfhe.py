@@ -32,6 +32,7 @@ MASK_ROW0S, MASK_COL0S, MASK_TIEC, MASK_SORTIDX, MASK_ROWIDX = 6, 7, 8, 9, 10
 OPT_KS_FUSED, OPT_KS_GROUP_BYTES, OPT_BLOCK_STACKING = 1, 2, 3
 OPT_TRIM_LEVELS = 4
 OPT_SERVER_LANES = 5
+OPT_PAIR_PACKING = 6
 OP_RANK, OP_ORDER_STAT, OP_SORT, OP_RANK_BLOCKED, OP_ORDER_STAT_BLOCKED, OP_SORT_BLOCKED = 1, 2, 3, 4, 5, 6
 
 

@@ -161,3 +161,77 @@ def test_blocked_rank_in_parts_bit_exact(ordb):
     back = [ev.import_(ev.export(a), a) for a in A1]
     for a, b in zip(back, A1):
         assert np.array_equal(a.export(), b.export())
+
+
+def _plain_blocks(P, v, f):
+    """Row 0 of every block of f's output in the noiseless slot model."""
+    Bp = C.PlainSlots(P.slots, P.L)
+    out = f(Bp, [Bp.fresh(v[i * BSZ:(i + 1) * BSZ]) for i in range(len(v) // BSZ)])
+    return np.concatenate([Bp.values(x)[:BSZ] for x in out])
+
+
+@pytest.fixture(scope="module")
+def ordb_packed():
+    """The n = 2^11 ring with the keys of the tile-packing rotations too: 64 tiles of
+    16 slots a ciphertext, rotations by +-16 2^s."""
+    P = helpers.oracle_params("ordb")
+    tile = BSZ * BSZ
+    tiles = P.slots // tile
+    rots = list(helpers.rotation_set(BSZ))
+    s = 1
+    while s < tiles:
+        rots += [tile * s, -tile * s]
+        s *= 2
+    keys = ckks.keygen(P, 42, helpers.galois_elts(P, rots))
+    ctx = helpers.gpu_context("ordb")
+    helpers.import_keys(ctx, keys)
+    helpers.import_encodings(ctx, P, BSZ, kinds=("row0", "col0", "tie"))
+    for L in (2, 3):
+        D = L * BSZ
+        for kind in ("row0s", "rowidx"):
+            u = ckks.encode_unscaled(C.mask_slots(kind, BSZ, 1, D, slots=P.slots), P.n)
+            ctx.encoding_import(helpers.MASK_IDS[kind], BSZ, 1, D, u)
+        ctx.indicator_import(D, C.sinc2_window_coeffs(D))
+    yield P, keys, ctx, tiles
+    ctx.close()
+
+
+def test_pair_packed_blocked_circuits_bit_exact(ordb_packed):
+    """With the packing keys present the blocked circuits pack their block-pair
+    comparisons (and the order statistic's and sort's indicators) 64 to a ciphertext:
+    each output block equals the oracle's packed schedule bit for bit and decrypts to
+    the noiseless model of the circuit (for ranks also to brute force; the order
+    statistic and sort carry the g f comparator's own error at gap 1/8); with
+    RK_OPT_PAIR_PACKING = 0 they equal the unpacked schedule."""
+    from paper_2412_15126_gb300 import rankfhe
+    P, keys, ctx, tiles = ordb_packed
+    Bo = C.OracleCkks(P, keys)
+    v3 = np.array([0.75, 0.125, 0.5, 0.0, 0.625, 0.25, 0.875, 0.375, 0.3125, 0.5625, 0.1875, 0.9375])
+    t3 = np.array([3, 1, 3, 0, 2, 1, 3, 2, 0, 1, 2, 3]) / 8.0
+    v2 = np.array([0.75, 0.125, 0.5, 0.0, 0.625, 0.25, 0.875, 0.375])
+    cases = [
+        (v3, lambda g: ctx.rank_blocked(g), lambda c, p: C.rank_blocked(Bo, c, BSZ, 1, 1, pack=p),
+         C.brute_fractional_rank(v3), 0.5),
+        (t3, lambda g: ctx.rank_blocked(g, rankfhe.TIES_CORRECT),
+         lambda c, p: C.rank_blocked_tc(Bo, c, BSZ, 1, 1, pack=p)[0], C.brute_tie_corrected_rank(t3), 0.25),
+        (v2, lambda g: ctx.order_stat_blocked(g, 2), lambda c, p: C.order_statistic_blocked(Bo, c, BSZ, 2, 1, 1, pack=p),
+         _plain_blocks(P, v2, lambda Bp, bl: C.order_statistic_blocked(Bp, bl, BSZ, 2, 1, 1)), 1e-3),
+        (v2, lambda g: ctx.sort_blocked(g), lambda c, p: C.sort_blocked(Bo, c, BSZ, 1, 1, pack=p),
+         _plain_blocks(P, v2, lambda Bp, bl: C.sort_blocked(Bp, bl, BSZ, 1, 1)), 1e-3),
+    ]
+    for idx, (v, gpu, orc, want, tol) in enumerate(cases):
+        cts, g = _encrypt_blocks(P, keys, ctx, v, 80 + 10 * idx)
+        ref = orc(cts, tiles)
+        got = gpu(g)
+        for a, b in zip(got, ref):
+            assert a.level == b.level
+            assert np.array_equal(a.export(), b.c), idx
+        dec = np.concatenate([ctx.decrypt(a) for a in got])
+        assert np.max(np.abs(dec - want)) < tol, idx
+        ctx.set_option(rankfhe.OPT_PAIR_PACKING, 0)
+        try:
+            plain = gpu(g)
+        finally:
+            ctx.set_option(rankfhe.OPT_PAIR_PACKING, 1)
+        for a, b in zip(plain, orc(cts, 1)):
+            assert np.array_equal(a.export(), b.c), idx
