@@ -778,7 +778,7 @@ def batched_workload(ctx, seed=4):
     big = [inputs.gap_vector(512, WORKLOAD["gap"], 20_000 + i) for i in range(8)]
     pq = [ctx.encrypt(v, N=N) for v, N in zip(vecs, lens)]
     pq_blocks = [[ctx.encrypt(v[128 * b:128 * (b + 1)], N=128) for b in range(4)] for v in big]
-    packed, packed_ids = [], []
+    packed, packed_ids, packed_shape = [], [], []
     for N in sorted(set(lens)):
         ids = [i for i, x in enumerate(lens) if x == N]
         qmax = slots // (N * N)
@@ -786,6 +786,7 @@ def batched_workload(ctx, seed=4):
             chunk = ids[s:s + qmax]
             packed.append(ctx.encrypt(np.concatenate([vecs[i] for i in chunk]), N=N, Q=len(chunk), n_real=N))
             packed_ids.append(chunk)
+            packed_shape.append((N, len(chunk)))
     pk_blocks = []
     for a in range(0, 8, 2):
         pk_blocks.append([ctx.encrypt(np.concatenate([big[a][128 * b:128 * (b + 1)], big[a + 1][128 * b:128 * (b + 1)]]),
@@ -821,6 +822,22 @@ def batched_workload(ctx, seed=4):
     t_bb, out_bb = timed(b_blocked)
     t_pq, t_b = t_pqs + t_pqb, t_bs + t_bb
     out_b = (out_bs, out_bb)
+    # the batched form replayed from CUDA graphs: one graph per group of packed
+    # ciphertexts of one shape (stacked, as rk_rank_batch groups them) and one for the
+    # stack of the packed blocked queries
+    groups = {}
+    for ct, shape in zip(packed, packed_shape):
+        groups.setdefault(shape, []).append(ct)
+    g_in = [ctx.stack(g) for g in groups.values()]
+    graphs = [ctx.graph_capture(rankfhe.OP_RANK, x) for x in g_in]
+    b_in = ctx.stack(pk_stacked)
+    gb = ctx.graph_capture(rankfhe.OP_RANK_BLOCKED, b_in, L=4)
+    replay = lambda: [g.run(x) for g, x in zip(graphs, g_in)] + [gb.run(b_in)]
+    timed(replay)
+    t_g, out_g = timed(replay)
+    graph_same = bool(np.array_equal(ctx.unstack(out_g[-1])[0].export(), out_bb[0][0][0].export()))
+    for g in graphs + [gb]:
+        g.free()
     # correctness of the batched outputs
     err = 0.0
     for ct, chunk in zip(out_b[0], packed_ids):
@@ -841,6 +858,8 @@ def batched_workload(ctx, seed=4):
             "speedup_vs_per_query_with_stacked_pairs": (t_pqs + t_pqb_st) / t_b,
             "ranks_per_s": n_q / t_b, "per_query_ranks_per_s": n_q / t_pq, "elements_per_s": elems / t_b,
             "speedup": t_pq / t_b, "ciphertexts_batched": len(packed) + 4 * len(pk_blocks),
+            "batched_graph_s": t_g, "graph_ranks_per_s": n_q / t_g, "speedup_graph": t_pq / t_g,
+            "graphs": len(graphs) + 1, "graph_blocked_bit_identical": graph_same,
             "ciphertexts_per_query": len(pq) + 4 * len(pq_blocks), "max_rank_error": err}
 
 

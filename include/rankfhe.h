@@ -491,6 +491,16 @@ typedef struct rk_graph rk_graph;
  * Must not be called while the context stream is being captured elsewhere.
  * Errors: as rk_rank, RK_ECUDA if capture or instantiation fails. */
 rk_status rk_graph_rank(rk_ctx* ctx, const rk_ct* tmpl, uint32_t flags, rk_graph** out);
+/* Capture any circuit as one CUDA graph for inputs shaped like `tmpl` (level, N, Q,
+ * n_real, stack size), as rk_graph_rank does for the rank.  op is an RK_OP_* code with
+ * the arguments of the serving loop (arg = k for order statistics, flags); for the
+ * blocked operations tmpl is a stack of L blocks, block i being members
+ * [i B/L, (i+1) B/L) of it (B/L queries a block), and a replay returns the stack of
+ * the L output blocks in the same layout.  Errors: as the circuit, RK_EINVAL for an
+ * unknown op or L not dividing the stack, RK_ECUDA if capture or instantiation
+ * fails. */
+rk_status rk_graph_capture(rk_ctx* ctx, uint32_t op, uint32_t arg, uint32_t flags, uint32_t L, const rk_ct* tmpl,
+                           rk_graph** out);
 /* Replay: copy `in` (same shape as the template) into the captured input, launch
  * the graph and return the result in a new handle (owned by the caller). */
 rk_status rk_graph_run(rk_graph* g, const rk_ct* in, rk_ct** out);

@@ -22,6 +22,7 @@ void circuit_rank_blocked_tc(rk_ctx* c, const rk_ct* const* blocks, int L, rk_ct
 void circuit_order_stat_blocked(rk_ctx* c, const rk_ct* const* blocks, int L, uint32_t k, rk_ct** outs);
 void circuit_sort_blocked(rk_ctx* c, const rk_ct* const* blocks, int L, rk_ct** outs);
 rk_graph* graph_rank_capture(rk_ctx* c, const rk_ct* tmpl, uint32_t flags);
+rk_graph* graph_capture(rk_ctx* c, uint32_t op, uint32_t arg, uint32_t flags, int L, const rk_ct* tmpl);
 rk_server* server_start(rk_ctx* c, size_t budget, int max_stack);
 uint64_t server_submit(rk_ctx* c, uint32_t op, uint32_t arg, uint32_t flags, const rk_ct* in);
 rk_ct* server_collect(rk_ctx* c, uint64_t ticket, double timeout_s);
@@ -818,6 +819,17 @@ rk_status rk_graph_rank(rk_ctx* ctx, const rk_ct* tmpl, uint32_t flags, rk_graph
         need(out, "out");
         set_device(ctx);
         *out = graph_rank_capture(ctx, tmpl, flags);
+    });
+}
+
+rk_status rk_graph_capture(rk_ctx* ctx, uint32_t op, uint32_t arg, uint32_t flags, uint32_t L, const rk_ct* tmpl,
+                           rk_graph** out) {
+    return guard([&] {
+        need(ctx, "ctx");
+        same_ctx(ctx, tmpl);
+        need(out, "out");
+        set_device(ctx);
+        *out = graph_capture(ctx, op, arg, flags, (int)L, tmpl);
     });
 }
 

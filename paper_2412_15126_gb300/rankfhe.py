@@ -131,6 +131,7 @@ _sig("rk_server_stats_lanes", [_vp, _dp])
 _sig("rk_server_stop", [_vp])
 _sig("rk_server_latencies", [_vp, _dp, _sz, ctypes.POINTER(_sz)])
 _sig("rk_graph_rank", [_vp, _vp, _u32, ctypes.POINTER(_vp)])
+_sig("rk_graph_capture", [_vp, _u32, _u32, _u32, _u32, _vp, ctypes.POINTER(_vp)])
 _sig("rk_graph_run", [_vp, _vp, ctypes.POINTER(_vp)])
 _sig("rk_graph_free", [_vp], None)
 _sig("rk_ntt_forward", [_vp, _vp, _u32, _u32])
@@ -534,6 +535,13 @@ class Context:
     def server_stop(self):
         _check(_L.rk_server_stop(self.handle))
         self._server_inputs = {}
+
+    def graph_capture(self, op: int, template: Ciphertext, arg: int = 0, flags: int = 0, L: int = 1) -> RankGraph:
+        """Capture the circuit `op` (OP_*) for template-shaped inputs as one CUDA graph;
+        blocked circuits take a stack of L blocks and replay to the stack of L results."""
+        h = _vp()
+        _check(_L.rk_graph_capture(self.handle, op, int(arg), flags, L, template.handle, ctypes.byref(h)))
+        return RankGraph(self, h.value)
 
     def graph_rank(self, template: Ciphertext, flags=0) -> RankGraph:
         """Capture rank(template-shaped input, flags) as one CUDA graph."""

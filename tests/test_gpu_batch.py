@@ -209,3 +209,43 @@ def test_graph_refuses_replay_after_scratch_growth(cfg2):
         assert np.array_equal(g2.run(cts[3]).export(), ctx.rank(cts[3]).export())
     finally:
         g2.free()
+
+
+def test_graph_capture_every_circuit_bit_identical():
+    """rk_graph_capture of the order statistic (a stack of two), the sort, and the
+    blocked rank, order statistic and sort (two blocks of two queries each): every
+    replay equals the direct call bit for bit, on inputs other than the template."""
+    from paper_2412_15126_gb300 import rankfhe
+    ctx = helpers.gpu_context("ord")
+    try:
+        ctx.keygen(404, 8)
+        mk = lambda s: ctx.encrypt(inputs.grid_vector(8, 16, s), N=8)
+        pairs = [(ctx.stack([mk(1), mk(2)]), ctx.stack([mk(3), mk(4)])), (mk(5), mk(6))]
+        cases = [
+            (rankfhe.OP_ORDER_STAT, 1, rankfhe.TIES_FIRST, 1, pairs[0],
+             lambda x: ctx.order_stat(x, 1, rankfhe.TIES_FIRST)),
+            (rankfhe.OP_SORT, 0, 0, 1, pairs[1], lambda x: ctx.sort(x)),
+        ]
+        # blocked: block i of two queries is a stack of two; the template is the stack of
+        # the L = 2 blocks, block-major
+        q = [[ctx.encrypt(inputs.gap_vector(4, 0.05, 40 + 10 * a + b), N=4) for b in range(2)] for a in range(4)]
+        blk = lambda a0, a1: [ctx.stack([q[a0][b], q[a1][b]]) for b in range(2)]
+        tmpl_b, run_b = blk(0, 1), blk(2, 3)
+        for op, direct in ((rankfhe.OP_RANK_BLOCKED, lambda bl: ctx.rank_blocked(bl)),
+                           (rankfhe.OP_ORDER_STAT_BLOCKED, lambda bl: ctx.order_stat_blocked(bl, 3)),
+                           (rankfhe.OP_SORT_BLOCKED, lambda bl: ctx.sort_blocked(bl))):
+            g = ctx.graph_capture(op, ctx.stack(tmpl_b), arg=3 if op == rankfhe.OP_ORDER_STAT_BLOCKED else 0, L=2)
+            got = ctx.unstack(g.run(ctx.stack(run_b)))
+            want = [m for blk_out in direct(run_b) for m in ctx.unstack(blk_out)]
+            assert len(got) == len(want) == 4
+            for a, b in zip(got, want):
+                assert np.array_equal(a.export(), b.export()), op
+            g.free()
+        for op, arg, flags, L, (tmpl, x), direct in cases:
+            g = ctx.graph_capture(op, tmpl, arg=arg, flags=flags, L=L)
+            got, want = g.run(x), direct(x)
+            for a, b in zip(ctx.unstack(got), ctx.unstack(want)):
+                assert np.array_equal(a.export(), b.export()), op
+            g.free()
+    finally:
+        ctx.close()
