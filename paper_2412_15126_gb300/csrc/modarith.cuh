@@ -40,23 +40,6 @@ RK_HD u64 shoup_lazy(u64 a, u64 w, u64 wp, u64 q) {
 }
 RK_HD u64 shoup_mul(u64 a, u64 w, u64 wp, u64 q) { return reduce_2q(shoup_lazy(a, w, wp, q), q); }
 
-// Shoup with an estimated quotient: of the four 32 x 32-bit partial products of a wp
-// only the high x high one and the high words of the two cross terms enter, which
-// leaves out the low x low product and the carries of the low words, so the estimate
-// is the exact quotient less 0, 1 or 2 and the result lies in [0, 4q) (q < 2^62).
-// One wide and two high-word multiplies instead of the four wide ones of the exact
-// high product.
-RK_HD u64 shoup_lazy4(u64 a, u64 w, u64 wp, u64 q) {
-    const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32);
-    const uint32_t p0 = (uint32_t)wp, p1 = (uint32_t)(wp >> 32);
-#ifdef __CUDA_ARCH__
-    const u64 qhat = (u64)a1 * p1 + __umulhi(a1, p0) + __umulhi(a0, p1);
-#else
-    const u64 qhat = (u64)a1 * p1 + (((u64)a1 * p0) >> 32) + (((u64)a0 * p1) >> 32);
-#endif
-    return a * w - qhat * q;
-}
-
 // Montgomery reduction of T = hi 2^64 + lo with hi < q: returns T R^-1 mod q in [0, q).
 // qinv = q^-1 mod 2^64.
 RK_HD u64 mont_redc(u64 lo, u64 hi, u64 q, u64 qinv) {

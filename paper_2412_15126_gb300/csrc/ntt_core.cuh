@@ -15,14 +15,11 @@
 
 namespace nttc {
 
-// Cooley-Tukey butterfly on values in [0, 4q): the product with the estimated Shoup
-// quotient lies in [0, 4q), one conditional subtraction each brings it and the upper
-// input to [0, 2q).
+// Cooley-Tukey butterfly on values in [0, 4q): one conditional subtraction.
 __device__ __forceinline__ void ct_bfly(u64& a, u64& b, u64 w, u64 wsh, u64 q, u64 q2) {
     u64 U = a;
     if (U >= q2) U -= q2;
-    u64 V = shoup_lazy4(b, w, wsh, q);
-    if (V >= q2) V -= q2;
+    const u64 V = shoup_lazy(b, w, wsh, q);   // [0, 2q) for any 64-bit input
     a = U + V;
     b = U + q2 - V;
 }
@@ -32,16 +29,13 @@ __device__ __forceinline__ u64 reduce_4q(u64 x, u64 q, u64 q2) {
     return x >= q ? x - q : x;
 }
 
-// Gentleman-Sande butterfly on values in [0, 2q) (estimated Shoup quotient, the
-// product brought back to [0, 2q) by one conditional subtraction).
+// Gentleman-Sande butterfly on values in [0, 2q).
 __device__ __forceinline__ void gs_bfly(u64& a, u64& b, u64 w, u64 wsh, u64 q, u64 q2) {
     u64 U = a, V = b;
     u64 x = U + V;
     if (x >= q2) x -= q2;
     a = x;
-    u64 y = shoup_lazy4(U + q2 - V, w, wsh, q);
-    if (y >= q2) y -= q2;
-    b = y;
+    b = shoup_lazy(U + q2 - V, w, wsh, q);
 }
 
 template <int LOG>
