@@ -616,13 +616,15 @@ def committed_traffic(kernel: str, algorithmic_per_launch: float):
 # CPU baseline: the oracle on a bounded sample
 # ---------------------------------------------------------------------------
 def rank_rotations(N):
-    """The rotation amounts of a rank circuit (ReplR, TransR, ReplC, SumR; Sec. 3.1)."""
+    """The rotation amounts of a rank circuit (ReplR, TransR, ReplC, SumR; Sec. 3.1),
+    with the sums of the step pairs its chains take two at a time."""
     k = N.bit_length() - 1
+    chains = [[-(N << i) for i in range(k)], [-(1 << i) for i in range(k)], [N << i for i in range(k)],
+              [-((N * (N - 1)) >> i) for i in range(1, k + 1)]]
     rs = set()
-    for i in range(k):
-        rs.update({-(N << i), -(1 << i), N << i})
-    for i in range(1, k + 1):
-        rs.add(-((N * (N - 1)) >> i))
+    for ch in chains:   # every step, and the sums of the step pairs taken two at a time
+        rs.update(ch)
+        rs.update(ch[i] + ch[i + 1] for i in range(0, len(ch) - 1, 2))
     return sorted(rs)
 
 

@@ -85,9 +85,10 @@ class PV:
 class PlainSlots:
     """Noiseless slot model with level accounting (every product costs one level)."""
 
-    def __init__(self, slots: int, top_level: int):
+    def __init__(self, slots: int, top_level: int, radix2: bool = False):
         self.slots = slots
         self.top = top_level
+        self.radix2 = radix2
         self.counts = {"rot": 0, "mul": 0, "mul_scalar": 0, "mul_plain": 0}
 
     def fresh(self, values) -> PV:
@@ -108,6 +109,15 @@ class PlainSlots:
 
     def rot_many(self, x, rs):
         return [self.rot(x, r) for r in rs]
+
+    def has_rot(self, r):
+        """Whether a rotation by r is keyed (the model has every rotation unless told
+        otherwise: `radix2` makes the chains take one doubling at a time)."""
+        return not self.radix2
+
+    def rot_sum(self, x, rs):
+        self.counts["rot"] += len(rs)
+        return PV(x.v + sum(np.roll(x.v, -(r % self.slots)) for r in rs), x.level)
 
     def add(self, x, y):
         assert x.level == y.level
@@ -178,6 +188,13 @@ class OracleCkks:
     def rot_many(self, x, rs):
         return [self.rot(x, r) for r in rs]
 
+    def has_rot(self, r):
+        return ckks.galois_left(r % self.slots, self.P.n) in self.keys.gal
+
+    def rot_sum(self, x, rs):
+        self.counts["rot"] += len(rs)
+        return ckks.rotate_sum(self.P, self.keys, x, rs)
+
     def add(self, x, y):
         return ckks.add(self.P, x, y)
 
@@ -219,51 +236,88 @@ class OracleCkks:
 # --------------------------------------------------------------------------
 # Recursive matrix operations (App. A, Alg. 8-11; transpositions Alg. 1-2)
 # --------------------------------------------------------------------------
+def chain_pairs(B, amounts):
+    """How a chain of doubling steps X <- X + (X << a_i) runs: consecutive steps
+    (a_i, a_(i+1)) are taken two at a time as X + (X << a_i) + (X << a_(i+1)) +
+    (X << a_i + a_(i+1)) with one hoisted ModUp and one ModDown (rot_sum) when the
+    rotation by a_i + a_(i+1) is keyed; otherwise, and for a last odd step, one at a
+    time.  Returns the list of steps, each a tuple of rotation amounts."""
+    steps, i = [], 0
+    while i < len(amounts):
+        if i + 1 < len(amounts) and B.has_rot(amounts[i] + amounts[i + 1]):
+            a, b = amounts[i], amounts[i + 1]
+            steps.append((a, b, a + b))
+            i += 2
+        else:
+            steps.append((amounts[i],))
+            i += 1
+    return steps
+
+
+def steps_taken(step) -> int:
+    """Doubling steps one entry of chain_pairs covers: two for (a, b, a + b), else one."""
+    return 2 if len(step) > 1 else 1
+
+
+def chain(B, x, amounts):
+    """The doubling steps X <- X + (X << a) for a in amounts (left rotations; negative
+    amounts rotate right), grouped as chain_pairs says."""
+    for st in chain_pairs(B, amounts):
+        x = B.rot_sum(x, list(st)) if len(st) > 1 else B.add(x, B.rot(x, st[0]))
+    return x
+
+
+def repl_r_amounts(N):
+    return [-(N << i) for i in range(log2_exact(N))]
+
+
+def trans_r_amounts(N):
+    return [-((N * (N - 1)) >> i) for i in range(1, log2_exact(N) + 1)]
+
+
 def repl_r(B, x, N):
     """Alg. 10: X <- X + (X >> N 2^i), i = 0 .. log N - 1."""
-    for i in range(log2_exact(N)):
-        x = B.add(x, B.rot(x, -(N << i)))
-    return x
+    return chain(B, x, repl_r_amounts(N))
 
 
 def repl_c(B, x, N):
     """Alg. 11: X <- X + (X >> 2^i)."""
-    for i in range(log2_exact(N)):
-        x = B.add(x, B.rot(x, -(1 << i)))
-    return x
+    return chain(B, x, [-(1 << i) for i in range(log2_exact(N))])
 
 
 def sum_r(B, x, N, Q=1):
     """Alg. 8: X <- X + (X << N 2^i), then MaskR(X, 0)."""
-    for i in range(log2_exact(N)):
-        x = B.add(x, B.rot(x, N << i))
+    x = chain(B, x, [N << i for i in range(log2_exact(N))])
     return B.mul_plain(x, ("row0", N, Q))
 
 
 def sum_c(B, x, N, Q=1):
     """Alg. 9: X <- X + (X << 2^i), then MaskC(X, 0)."""
-    for i in range(log2_exact(N)):
-        x = B.add(x, B.rot(x, 1 << i))
+    x = chain(B, x, [1 << i for i in range(log2_exact(N))])
     return B.mul_plain(x, ("col0", N, Q))
 
 
 def trans_r(B, x, N, Q=1, trace=None):
-    """Alg. 1: X <- X + (X >> N(N-1)/2^i), i = 1 .. log N, then MaskC(X, 0)."""
-    for i in range(1, log2_exact(N) + 1):
-        r = (N * (N - 1)) >> i
-        x = B.add(x, B.rot(x, -r))
-        if trace is not None:
-            trace.append((r, x))
+    """Alg. 1: X <- X + (X >> N(N-1)/2^i), i = 1 .. log N, then MaskC(X, 0).  With a
+    trace, one step at a time (the trace records every step)."""
+    if trace is None:
+        x = chain(B, x, trans_r_amounts(N))
+    else:
+        for r in trans_r_amounts(N):
+            x = B.add(x, B.rot(x, r))
+            trace.append((-r, x))
     return B.mul_plain(x, ("col0", N, Q))
 
 
 def trans_c(B, x, N, Q=1, trace=None):
-    """Alg. 2: X <- X + (X << N(N-1)/2^i), i = 1 .. log N, then MaskR(X, 0)."""
-    for i in range(1, log2_exact(N) + 1):
-        r = (N * (N - 1)) >> i
-        x = B.add(x, B.rot(x, r))
-        if trace is not None:
-            trace.append((r, x))
+    """Alg. 2: X <- X + (X << N(N-1)/2^i), i = 1 .. log N, then MaskR(X, 0).  With a
+    trace, one step at a time."""
+    if trace is None:
+        x = chain(B, x, [-r for r in trans_r_amounts(N)])
+    else:
+        for r in trans_r_amounts(N):
+            x = B.add(x, B.rot(x, -r))
+            trace.append((-r, x))
     return B.mul_plain(x, ("row0", N, Q))
 
 
@@ -342,19 +396,23 @@ def comparison_matrix(B, V, N, dg, df, Q=1):
 
 def row_col_forms(B, V, N, Q=1):
     """V_R = ReplR(V) and V_C = ReplC(TransR(V)) (Alg. 3 lines 1-2), V_R brought down to
-    V_C's level.  The first rotations of ReplR and TransR both rotate V and share one
-    ModUp (hoisting)."""
+    V_C's level.  The first steps of ReplR and TransR both rotate V and share one
+    ModUp (hoisting); each chain then runs as chain() groups it."""
     k = log2_exact(N)
     if k == 0:
         VR, VT = V, V
     else:
-        r1, t1 = B.rot_many(V, [-N, -((N * (N - 1)) >> 1)])
-        VR = B.add(V, r1)
-        for i in range(1, k):
-            VR = B.add(VR, B.rot(VR, -(N << i)))
-        VT = B.add(V, t1)
-        for i in range(2, k + 1):
-            VT = B.add(VT, B.rot(VT, -((N * (N - 1)) >> i)))
+        ra, ta = repl_r_amounts(N), trans_r_amounts(N)
+        r0, t0 = chain_pairs(B, ra)[0], chain_pairs(B, ta)[0]
+        # the first step of each chain from V (one hoisted ModUp for both)
+        if len(r0) == 1 and len(t0) == 1:
+            r1, t1 = B.rot_many(V, [r0[0], t0[0]])
+            VR, VT = B.add(V, r1), B.add(V, t1)
+        else:
+            step = lambda x, st: B.rot_sum(x, list(st)) if len(st) > 1 else B.add(x, B.rot(x, st[0]))
+            VR, VT = step(V, r0), step(V, t0)
+        VR = chain(B, VR, ra[steps_taken(r0):])
+        VT = chain(B, VT, ta[steps_taken(t0):])
     T = B.mul_plain(VT, ("col0", N, Q))                     # TransR's MaskC
     VC = repl_c(B, T, N)
     return B.level_down(VR, B.level(VC)), VC
@@ -503,16 +561,14 @@ def rank_blocked_tc(B, Vs, Bsz, dg, df, Q=1, scaled=False, pack=1):
         A = tie_fold(B, Cs[(i, i)], Bsz, Q, "tie")
         for j in range(i + 1, L):
             A = B.add(A, B.level_down(Gs[(i, j)], B.level(A)))
-        for r in range(log2_exact(Bsz)):
-            A = B.add(A, B.rot(A, Bsz << r))
+        A = chain(B, A, [Bsz << r for r in range(log2_exact(Bsz))])
         S = B.mul_plain(A, rmask)
         if i > 0:
             Bs = Gs[(0, i)]
             for j in range(1, i):
                 Bs = B.add(Bs, Gs[(j, i)])
             T = sum_c(B, B.add_const(B.neg(Bs), float(i)), Bsz, Q)
-            for r in range(1, log2_exact(Bsz) + 1):
-                T = B.add(T, B.rot(T, (Bsz * (Bsz - 1)) >> r))
+            T = chain(B, T, [-r for r in trans_r_amounts(Bsz)])
             T = B.mul_plain(T, rmask)
             S = B.add(S, B.level_down(T, B.level(S)))
         out.append(S)
@@ -657,14 +713,12 @@ def cheb_depth(length: int) -> int:
 # Order statistics (Alg. 4) and sorting (Alg. 5, column form)
 # --------------------------------------------------------------------------
 def sum_rows_masked(B, x, N, Q, kind):
-    for i in range(log2_exact(N)):
-        x = B.add(x, B.rot(x, N << i))
+    x = chain(B, x, [N << i for i in range(log2_exact(N))])
     return B.mul_plain(x, (kind, N, Q))
 
 
 def sum_cols_masked(B, x, N, Q, kind):
-    for i in range(log2_exact(N)):
-        x = B.add(x, B.rot(x, 1 << i))
+    x = chain(B, x, [1 << i for i in range(log2_exact(N))])
     return B.mul_plain(x, (kind, N, Q))
 
 

@@ -565,6 +565,28 @@ def rotate(P: Params, keys: Keys, x: Ct, r: int) -> Ct:
     return Ct(np.stack([c0, k1]), x.level)
 
 
+def rotate_sum(P: Params, keys: Keys, x: Ct, rs) -> Ct:
+    """x + sum_k (x << r_k) for nonzero rotations r_k with one ModDown for the sum:
+    the inner products of x's lifted digits (automorphism g_k on the digits, the key
+    of g_k) are added over Q_l P first, then brought down once; c0 takes x's c0 and
+    its automorphic images, c1 takes x's c1.  Equal to adding the separate rotations
+    up to the ModDown's rounding (one rounding instead of one per rotation)."""
+    q = P.q[: x.level + 1]
+    primes = P.qp(x.level)
+    U0 = U1 = None
+    c0 = x.c[0].copy()
+    for r in rs:
+        g = galois_left(r % P.slots, P.n)
+        assert g != 1, "rotate_sum takes nonzero rotations"
+        u0, u1 = key_switch_raw(P, x.c[1], keys.gal[g], x.level, g)
+        U0 = u0 if U0 is None else add_mod(U0, u0, primes)
+        U1 = u1 if U1 is None else add_mod(U1, u1, primes)
+        c0 = add_mod(c0, automorphism(x.c[0], g, q), q)
+    c0 = add_mod(c0, mod_down(P, U0, x.level), q)
+    c1 = add_mod(x.c[1], mod_down(P, U1, x.level), q)
+    return Ct(np.stack([c0, c1]), x.level)
+
+
 def mul(P: Params, keys: Keys, x: Ct, y: Ct) -> Ct:
     assert x.level == y.level, (x.level, y.level)
     lvl = x.level

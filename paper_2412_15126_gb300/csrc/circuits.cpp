@@ -89,6 +89,21 @@ struct Ev {
         ev_rotate_multi(c, x.p, r.data(), true, o.p);
         return o;
     }
+    // x_b + sum_k rot(x_b, r_b[k]) with one ModUp and one ModDown; r_b of one length
+    // K <= 3 for every member b (member_r[b]), or the same list for all (one entry)
+    H rot_sum(const H& x, const std::vector<std::vector<int>>& member_r) {
+        const int B = x->B, K = (int)member_r[0].size();
+        std::vector<int> r((size_t)3 * B, 0);
+        for (int b = 0; b < B; b++) {
+            const std::vector<int>& rb = member_r.size() == 1 ? member_r[0] : member_r[b];
+            RK_REQUIRE((int)rb.size() == K, RK_EINVAL, "rot_sum: one rotation count for every member");
+            for (int k = 0; k < K; k++) r[(size_t)b * 3 + k] = rb[k];
+        }
+        H o = fresh(x, x->level);
+        rk_ct* outs[1] = {o.p};
+        ev_rotate_sums(c, x.p, 1, &K, r.data(), true, outs);
+        return o;
+    }
     std::pair<H, H> rot2(const H& x, int r1, int r2) {
         H a = fresh(x, x->level), b = fresh(x, x->level);
         int r[2] = {r1, r2};
@@ -172,6 +187,50 @@ int log2_exact(uint32_t N) {
     return k;
 }
 
+// Doubling chains X <- X + (X <<< a_i) (Alg. 1, 2, 8-11): consecutive steps are taken
+// two at a time, X + (X <<< a_i) + (X <<< a_(i+1)) + (X <<< a_i + a_(i+1)) with one
+// ModUp and one ModDown, when the rotation by a_i + a_(i+1) is keyed; otherwise, and
+// for a last odd step, one at a time.  Each step is its list of rotation amounts.
+bool has_rot(const rk_ctx* c, int r) {
+    const u64 g = galois_left(c, r);
+    return g != 1 && c->gal.count(g) > 0;
+}
+std::vector<std::vector<int>> chain_pairs(const rk_ctx* c, const std::vector<int>& a) {
+    std::vector<std::vector<int>> steps;
+    size_t i = 0;
+    while (i < a.size()) {
+        if (i + 1 < a.size() && has_rot(c, a[i] + a[i + 1])) {
+            steps.push_back({a[i], a[i + 1], a[i] + a[i + 1]});
+            i += 2;
+        } else {
+            steps.push_back({a[i]});
+            i += 1;
+        }
+    }
+    return steps;
+}
+int steps_taken(const std::vector<int>& step) { return step.size() > 1 ? 2 : 1; }
+
+std::vector<int> repl_r_amounts(int N, int k) {
+    std::vector<int> a;
+    for (int i = 0; i < k; i++) a.push_back(-(N << i));
+    return a;
+}
+std::vector<int> trans_r_amounts(int N, int k) {   // right rotations by N(N-1)/2^i, i = 1 .. k
+    std::vector<int> a;
+    for (int i = 1; i <= k; i++) a.push_back(-((N * (N - 1)) >> i));
+    return a;
+}
+std::vector<int> pow2_amounts(int scale, int k, int sign) {   // sign scale 2^i, i < k
+    std::vector<int> a;
+    for (int i = 0; i < k; i++) a.push_back(sign * (scale << i));
+    return a;
+}
+std::vector<int> negated(std::vector<int> a) {
+    for (int& x : a) x = -x;
+    return a;
+}
+
 // Cheon et al. composite sign polynomials (Sec. 2.2): coefficients of x, x^3, x^5, x^7.
 const double kF[4] = {35.0 / 16, -35.0 / 16, 21.0 / 16, -5.0 / 16};
 const double kG[4] = {4589.0 / 1024, -16577.0 / 1024, 25614.0 / 1024, -12860.0 / 1024};
@@ -228,10 +287,16 @@ H cmp(Ev& E, H x, int dg, int df) {
     return E.add_const(x, 0.5);
 }
 
+// The chain's steps on x (every stack member by the same amounts).
+H chain(Ev& E, H x, const std::vector<int>& amounts) {
+    for (const auto& st : chain_pairs(E.c, amounts)) x = st.size() > 1 ? E.rot_sum(x, {st}) : E.rot_add(x, st[0]);
+    return x;
+}
+
 // SumR (Alg. 8) with the row mask `kind` (RK_MASK_ROW0, or RK_MASK_ROW0S to divide by N)
 H sum_rows(Ev& E, H x, uint32_t kind) {
     const int N = (int)x->N, k = log2_exact(x->N);
-    for (int i = 0; i < k; i++) x = E.rot_add(x, N << i);
+    x = chain(E, std::move(x), pow2_amounts(N, k, 1));
     return E.mul_mask(x, kind);
 }
 H sum_r(Ev& E, H x) { return sum_rows(E, std::move(x), RK_MASK_ROW0); }
@@ -239,21 +304,20 @@ H sum_r(Ev& E, H x) { return sum_rows(E, std::move(x), RK_MASK_ROW0); }
 // SumC (Alg. 9) with the column mask `kind`
 H sum_cols(Ev& E, H x, uint32_t kind) {
     const int k = log2_exact(x->N);
-    for (int i = 0; i < k; i++) x = E.rot_add(x, 1 << i);
+    x = chain(E, std::move(x), pow2_amounts(1, k, 1));
     return E.mul_mask(x, kind);
 }
 
 // TransC (Alg. 2): X <- X + (X << N(N-1)/2^i), i = 1 .. log N, then MaskR(X, 0)
 H trans_c(Ev& E, H x) {
     const int N = (int)x->N, k = log2_exact(x->N);
-    for (int i = 1; i <= k; i++) x = E.rot_add(x, (N * (N - 1)) >> i);
+    x = chain(E, std::move(x), negated(trans_r_amounts(N, k)));
     return E.mul_mask(x, RK_MASK_ROW0);
 }
 // ReplC (Alg. 11)
 H repl_c(Ev& E, H x) {
     const int k = log2_exact(x->N);
-    for (int i = 0; i < k; i++) x = E.rot_add(x, -(1 << i));
-    return x;
+    return chain(E, std::move(x), pow2_amounts(1, k, -1));
 }
 
 // C + E (delta - 1/2), E = 4 K, K = C - C^2 (Alg. 6 before its SumR); the mask holds 4 delta - 2
@@ -493,19 +557,41 @@ std::pair<H, H> row_col_forms(Ev& E, const H& V) {
         VR = E.copy(V);
         VT = E.copy(V);
     } else {
-        auto rt = E.rot2(V, -N, -((N * (N - 1)) >> 1));   // hoisted: one ModUp for both
-        VR = E.add(V, rt.first);
-        VT = E.add(V, rt.second);
-        if (V->B == 1 && k > 1) {
+        const std::vector<int> ra = repl_r_amounts(N, k), ta = trans_r_amounts(N, k);
+        const std::vector<int> r0 = chain_pairs(E.c, ra)[0], t0 = chain_pairs(E.c, ta)[0];
+        if (r0.size() == 1 && t0.size() == 1) {
+            auto rt = E.rot2(V, r0[0], t0[0]);   // hoisted: one ModUp for both
+            VR = E.add(V, rt.first);
+            VT = E.add(V, rt.second);
+        } else {   // both chains' first steps from V: one ModUp, one ModDown
+            VR = E.fresh(V, V->level);
+            VT = E.fresh(V, V->level);
+            const int B = V->B;
+            const int K[2] = {(int)r0.size(), (int)t0.size()};
+            std::vector<int> r((size_t)2 * B * 3, 0);
+            for (int b = 0; b < B; b++)
+                for (int j = 0; j < 3; j++) {
+                    if (j < K[0]) r[(size_t)b * 3 + j] = r0[j];
+                    if (j < K[1]) r[((size_t)B + b) * 3 + j] = t0[j];
+                }
+            rk_ct* outs[2] = {VR.p, VT.p};
+            ev_rotate_sums(E.c, V.p, 2, K, r.data(), true, outs);
+        }
+        const std::vector<int> rrest(ra.begin() + steps_taken(r0), ra.end()), trest(ta.begin() + steps_taken(t0), ta.end());
+        const auto rs = chain_pairs(E.c, rrest), ts = chain_pairs(E.c, trest);
+        bool lockstep = V->B == 1 && !rs.empty() && rs.size() == ts.size();
+        for (size_t i = 0; lockstep && i < rs.size(); i++) lockstep = rs[i].size() == ts[i].size();
+        if (lockstep) {
             // the two chains in step, as one two-member stack with a key per member
             const rk_ct* pair[2] = {VR.p, VT.p};
             H S(ct_stack(E.c, pair, 2));
-            for (int i = 1; i < k; i++) S = E.rot_add_multi(S, {-(N << i), -((N * (N - 1)) >> (i + 1))});
+            for (size_t i = 0; i < rs.size(); i++)
+                S = rs[i].size() > 1 ? E.rot_sum(S, {rs[i], ts[i]}) : E.rot_add_multi(S, {rs[i][0], ts[i][0]});
             VR = E.copy(H(ct_view(S.p, 0)));
             VT = E.copy(H(ct_view(S.p, 1)));
         } else {
-            for (int i = 1; i < k; i++) VR = E.rot_add(VR, -(N << i));
-            for (int i = 2; i <= k; i++) VT = E.rot_add(VT, -((N * (N - 1)) >> i));
+            VR = chain(E, std::move(VR), rrest);
+            VT = chain(E, std::move(VT), trest);
         }
     }
     H VC = E.mul_mask(VT, RK_MASK_COL0);                 // TransR's MaskC
@@ -966,8 +1052,7 @@ static H cmp_strict(Ev& E, const H& C) {
 // ReplR (Alg. 10): X <- X + (X >> N 2^i)
 static H repl_r(Ev& E, H x) {
     const int N = (int)x->N, k = log2_exact(x->N);
-    for (int i = 0; i < k; i++) x = E.rot_add(x, -(N << i));
-    return x;
+    return chain(E, std::move(x), repl_r_amounts(N, k));
 }
 
 static int blocked_rank_tc_depth(const rk_ctx* c) { return 1 + cmp_depth(c) + 3; }
@@ -1030,7 +1115,7 @@ static std::pair<H, H> blocked_ranks_tc(rk_ctx* c, const rk_ct* const* blocks, i
     H S = stack_of(c, ap);
     {
         const int k = log2_exact((uint32_t)Bsz);
-        for (int r = 0; r < k; r++) S = E.rot_add(S, Bsz << r);
+        S = chain(E, std::move(S), pow2_amounts(Bsz, k, 1));
         S = E.mul_mask_d(S, rmask, Dn);
     }
     if (L == 1) return std::make_pair(std::move(S), std::move(rc.first));
@@ -1039,7 +1124,7 @@ static std::pair<H, H> blocked_ranks_tc(rk_ctx* c, const rk_ct* const* blocks, i
     H T = sum_cols(E, stack_of(c, bp), RK_MASK_COL0);   // stack of (L - 1) Bq
     {
         const int k = log2_exact((uint32_t)Bsz);
-        for (int r = 1; r <= k; r++) T = E.rot_add(T, (Bsz * (Bsz - 1)) >> r);
+        T = chain(E, std::move(T), negated(trans_r_amounts(Bsz, k)));
         T = E.mul_mask_d(T, rmask, Dn);
     }
     std::vector<H> R;
@@ -1161,18 +1246,16 @@ rk_ct* circuit_compare_matrix(rk_ctx* c, const rk_ct* in) {
     return comparison_matrix(E, V, (int)c->prm.d_g, (int)c->prm.d_f).release();
 }
 
-// Rotation amounts the circuits use for a vector of length N (Sec. 3.1 and App. A).
+// Rotation amounts the circuits use for a vector of length N (Sec. 3.1 and App. A):
+// every chain's steps (ReplR, SumR, ReplC, SumC, TransR, TransC) and the sums of the
+// step pairs the chains take two at a time (steps 2j and 2j + 1).
 void circuit_rotations(uint32_t N, std::vector<int>& out) {
     const int k = log2_exact(N);
     const int n = (int)N;
-    for (int i = 0; i < k; i++) {
-        out.push_back(-(n << i));   // ReplR
-        out.push_back(n << i);      // SumR
-        out.push_back(-(1 << i));   // ReplC
-        out.push_back(1 << i);      // SumC
-    }
-    for (int i = 1; i <= k; i++) {
-        out.push_back(-((n * (n - 1)) >> i));   // TransR
-        out.push_back((n * (n - 1)) >> i);      // TransC
+    const std::vector<std::vector<int>> chains = {repl_r_amounts(n, k), pow2_amounts(n, k, 1), pow2_amounts(1, k, -1),
+                                                  pow2_amounts(1, k, 1), trans_r_amounts(n, k), negated(trans_r_amounts(n, k))};
+    for (const auto& ch : chains) {
+        for (int a : ch) out.push_back(a);
+        for (size_t i = 0; i + 1 < ch.size(); i += 2) out.push_back(ch[i] + ch[i + 1]);
     }
 }

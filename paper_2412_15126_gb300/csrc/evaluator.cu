@@ -594,6 +594,75 @@ void ev_rotate_multi(rk_ctx* c, const rk_ct* a, const int* r, bool add, rk_ct* o
     copy_meta(out, a);
 }
 
+// Hoisted sums of rotations: for every set s and stack member b,
+//   outs[s]_b = [a_b +] sum_{k < K[s]} (a_b <<< r[(s B + b) 3 + k])
+// with one ModUp of the stack for all of them, the inner products of each sum added
+// over Q_l P (accumulating launches), one ModDown for all the sums and a combine that
+// adds the automorphic images of c0 (K[s] <= 3).  The sums' ModDown rounds once, so a
+// sum equals adding its separate rotations up to that rounding.  Always on the staged
+// kernels (the result does not depend on RK_OPT_KS_FUSED).
+void ev_rotate_sums(rk_ctx* c, const rk_ct* a, int nsets, const int* K, const int* r, bool add, rk_ct** outs) {
+    const int B = a->B, l = a->level;
+    RK_REQUIRE(nsets >= 1, RK_EINVAL, "rotate_sums: no sets");
+    std::vector<std::vector<u64>> gal((size_t)nsets * B);
+    for (int s = 0; s < nsets; s++) {
+        RK_REQUIRE(K[s] >= 1 && K[s] <= 3, RK_EINVAL, "rotate_sums: 1 to 3 rotations a sum");
+        RK_REQUIRE(outs[s] != a && outs[s]->B == B, RK_EINVAL, "rotate_sums: output aliases input or stack mismatch");
+        for (int b = 0; b < B; b++)
+            for (int k = 0; k < K[s]; k++) {
+                const int rr = r[((size_t)s * B + b) * 3 + k];
+                const u64 g = galois_left(c, rr);
+                RK_REQUIRE(g != 1, RK_EINVAL, "rotate_sums: rotation by 0");
+                RK_REQUIRE(c->gal.count(g), RK_ENOKEY, "rotation key missing for r = " + std::to_string(rr));
+                gal[(size_t)s * B + b].push_back(g);
+            }
+    }
+    ensure_batch(c, nsets * B);   // before the lift: growing the scratch would drop it
+    const size_t ps = c->poly_stride(), n = c->n;
+    const u64* d = a->data + ps;
+    ks_lift(c, d, 2 * ps, l, B);
+    ks_lift_ext(c, d, 2 * ps, l, B);
+    Scratch S = scratch_layout(c);
+    const int QP = l + 1 + c->alpha, beta = c->beta(l);
+    const size_t es = (size_t)QP * n;
+    for (int s = 0; s < nsets; s++) {
+        bool uniform = true;   // every member rotated by the same amounts: one launch for the stack
+        for (int b = 1; b < B && uniform; b++) uniform = gal[(size_t)s * B + b] == gal[(size_t)s * B];
+        u64* us = S.u + (size_t)s * B * 2 * es;
+        if (uniform) {
+            for (int k = 0; k < K[s]; k++) {
+                const u64 g = gal[(size_t)s * B][k];
+                launch_ks_inner(c->env, S.ext, es, c->gal[g].ref(), us, l, beta, g, c->stream, B, k > 0);
+            }
+        } else {
+            for (int b = 0; b < B; b++)
+                for (int k = 0; k < K[s]; k++) {
+                    const u64 g = gal[(size_t)s * B + b][k];
+                    launch_ks_inner(c->env, S.ext + (size_t)b * beta * es, es, c->gal[g].ref(), us + (size_t)b * 2 * es, l, beta,
+                                    g, c->stream, 1, k > 0);
+                }
+        }
+    }
+    const int polys = 2 * nsets * B;
+    launch_ntt_inverse(c->env, LimbSet{S.u + (size_t)(l + 1) * n, es, polys, c->alpha, 0, 0, c->L + 1}, c->stream);
+    launch_moddown_conv(c->env, S.u, S.w, l, c->stream, polys);
+    launch_ntt_forward(c->env, ls_q(S.w, (size_t)(l + 1) * n, polys, l + 1), c->stream);
+    for (int s = 0; s < nsets; s++) {
+        for (int b = 0; b < B; b++) {
+            const std::vector<u64>& gs = gal[(size_t)s * B + b];
+            GaloisSet set{(int)gs.size(), {0, 0, 0}};
+            for (size_t k = 0; k < gs.size(); k++) set.g[k] = gs[k];
+            const size_t m = (size_t)s * B + b;
+            launch_ks_combine_sum(c->env, outs[s]->data + (size_t)b * 2 * ps, ps, a->data + (size_t)b * 2 * ps, 2 * ps, set, add,
+                                  S.u + m * 2 * es, S.w + m * 2 * (l + 1) * n, l, c->stream, 1);
+        }
+        outs[s]->level = l;
+        copy_meta(outs[s], a);
+    }
+    c->n_ks += (uint64_t)nsets * B;
+    for (int s = 0; s < nsets; s++) c->n_rot += (uint64_t)K[s] * B;
+}
+
 // The relinearisation and rescale of B tensor products already in S.d ([B][3][l+1][n]),
 // into out ([B] members at level l - 1).
 static void mul_finish(rk_ctx* c, int l, int B, const rk_ct* meta, rk_ct* out) {

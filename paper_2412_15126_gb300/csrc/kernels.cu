@@ -387,7 +387,7 @@ void launch_ks_combine_rs(const KernelEnv& env, u64* out, size_t ps, const u64* 
 template <int CH, bool SEEDED>
 __global__ void __launch_bounds__(TPB, (CH == 1 ? 6 : (CH == 2 ? 4 : 3))) k_ks_inner(const u64* __restrict__ ext, size_t ext_stride, const u64* __restrict__ key,
                                                   u64 seed, u64* __restrict__ u, int level, int L, int alpha, int beta, u64 galois,
-                                                  int logn, int B, const PrimeConst* __restrict__ pc) {
+                                                  int logn, int B, int accumulate, const PrimeConst* __restrict__ pc) {
     RK_KERNEL_PROLOGUE();
     const int n = 1 << logn;
     const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y;
@@ -425,26 +425,32 @@ __global__ void __launch_bounds__(TPB, (CH == 1 ? 6 : (CH == 2 ? 4 : 3))) k_ks_i
     for (int b = 0; b < CH; b++) {
         if (CH == 1 || b < nb) {
             u64* ub = u + (size_t)(b0 + b) * 2 * ul * n;
-            ub[(size_t)t * n + k] = a0[b].redc(P.q, P.qinv);
-            ub[(size_t)ul * n + (size_t)t * n + k] = a1[b].redc(P.q, P.qinv);
+            u64 r0 = a0[b].redc(P.q, P.qinv), r1 = a1[b].redc(P.q, P.qinv);
+            if (accumulate) {   // a further rotation's products added to the sum held in u
+                r0 = add_mod(r0, ub[(size_t)t * n + k], P.q);
+                r1 = add_mod(r1, ub[(size_t)ul * n + (size_t)t * n + k], P.q);
+            }
+            ub[(size_t)t * n + k] = r0;
+            ub[(size_t)ul * n + (size_t)t * n + k] = r1;
         }
     }
 }
 
 void launch_ks_inner(const KernelEnv& env, const u64* ext, size_t ext_stride, KeyRef key, u64* u, int level, int beta,
-                     u64 galois, cudaStream_t st, int B) {
+                     u64 galois, cudaStream_t st, int B, bool accumulate) {
     // algorithmic bytes: B lifted inputs read, the key (b and a, or b alone when
     // seeded) read once per chunk, B outputs written
     const double QP = level + 1 + env.alpha;
     const int ch = B <= 1 ? 1 : B <= 2 ? 2 : 4;
     const int chunks = (B + ch - 1) / ch;
     const double key_parts = key.seeded ? 1.0 : 2.0;
-    ProfScope pf(env, KK_KS_INNER, st, 1, ((double)B * beta + key_parts * beta * chunks + 2.0 * B) * QP * 8.0 * env.n,
+    ProfScope pf(env, KK_KS_INNER, st, 1,
+                 ((double)B * beta + key_parts * beta * chunks + (accumulate ? 4.0 : 2.0) * B) * QP * 8.0 * env.n,
                  2.0 * B * beta * QP * env.n);
     dim3 g(env.n / TPB, level + 1 + env.alpha, chunks);
 #define RK_KSI(C, SD)                                                                                                \
     rk_launch(k_ks_inner<C, SD>, g, TPB, 0, st, ext, ext_stride, key.data, key.seed, u, level, env.L, env.alpha, beta, \
-              galois, env.logn, B, env.pc)
+              galois, env.logn, B, accumulate ? 1 : 0, env.pc)
     if (key.seeded) {
         switch (ch) {
             case 1: RK_KSI(1, true); break;
@@ -492,6 +498,38 @@ void launch_ks_combine(const KernelEnv& env, u64* out, size_t ps, const u64* bas
     ProfScope pf(env, KK_KS_COMBINE, st, 1, (addend ? 9.0 : 7.0) * B * (level + 1) * 8.0 * env.n, 2.0 * B * (level + 1) * env.n);
     dim3 g(env.n / TPB, level + 1, 2 * B);
     rk_launch(k_ks_combine, g, TPB, 0, st, out, ps, base0, galois0, base1, bstride, u, w, addend, level, env.alpha, env.conv,
+              env.logn, env.pc);
+}
+
+// A hoisted sum of K rotations of x (K <= 3), z = 2b + p over B stacked ciphertexts:
+//   out_b.c0 = x_b.c0 + sum_k sigma_k(x_b.c0) + (u0_b - w0_b) P^-1,
+//   out_b.c1 = x_b.c1 + (u1_b - w1_b) P^-1
+// (x_b at x + b * bstride, poly stride ps; u the summed inner products, w ModDown's
+// conversion of their P part); without `add`, x_b itself is left out.
+__global__ void k_ks_combine_sum(u64* out, size_t ps, const u64* __restrict__ x, size_t bstride, GaloisSet gs, int add,
+                                 const u64* __restrict__ u, const u64* __restrict__ w, int level, int alpha, ConvTables cv,
+                                 int logn, const PrimeConst* __restrict__ pc) {
+    RK_KERNEL_PROLOGUE();
+    const int n = 1 << logn;
+    const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y, c = blockIdx.z;
+    const int b = c >> 1, p = c & 1;
+    const u64 q = pc[t].q;
+    const int ul = level + 1 + alpha;
+    u64 v = sub_mod(u[(size_t)c * ul * n + (size_t)t * n + k], w[(size_t)c * (level + 1) * n + (size_t)t * n + k], q);
+    v = shoup_mul(v, cv.pinv[2 * t], cv.pinv[2 * t + 1], q);
+    const u64* xb = x + (size_t)b * bstride + (size_t)p * ps + (size_t)t * n;
+    if (p == 0)
+        for (int r = 0; r < gs.K; r++) v = add_mod(v, xb[galois_src(k, gs.g[r], logn)], q);
+    if (add) v = add_mod(v, xb[k], q);
+    out[(size_t)b * bstride + (size_t)p * ps + (size_t)t * n + k] = v;
+}
+
+void launch_ks_combine_sum(const KernelEnv& env, u64* out, size_t ps, const u64* x, size_t bstride, const GaloisSet& gs,
+                           bool add, const u64* u, const u64* w, int level, cudaStream_t st, int B) {
+    ProfScope pf(env, KK_KS_COMBINE, st, 1, (7.0 + gs.K + (add ? 2.0 : 0.0)) * B * (level + 1) * 8.0 * env.n,
+                 2.0 * B * (level + 1) * env.n);
+    dim3 g(env.n / TPB, level + 1, 2 * B);
+    rk_launch(k_ks_combine_sum, g, TPB, 0, st, out, ps, x, bstride, gs, add ? 1 : 0, u, w, level, env.alpha, env.conv,
               env.logn, env.pc);
 }
 

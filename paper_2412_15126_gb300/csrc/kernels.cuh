@@ -103,8 +103,16 @@ void launch_ks_add_pd(const KernelEnv& env, u64* u, const u64* d, int level, u64
 void launch_ks_combine_rs(const KernelEnv& env, u64* out, size_t ps, const u64* u, const u64* w, const u64* d, int level,
                           cudaStream_t st, int B);
 
+// accumulate: add the products to the sums already in u (a hoisted sum of rotations)
 void launch_ks_inner(const KernelEnv& env, const u64* ext, size_t ext_stride, KeyRef key, u64* u, int level, int beta,
-                     u64 galois, cudaStream_t st, int B = 1);
+                     u64 galois, cudaStream_t st, int B = 1, bool accumulate = false);
+// Galois elements of a hoisted sum of up to three rotations
+struct GaloisSet {
+    int K;
+    u64 g[3];
+};
+void launch_ks_combine_sum(const KernelEnv& env, u64* out, size_t ps, const u64* x, size_t bstride, const GaloisSet& gs,
+                           bool add, const u64* u, const u64* w, int level, cudaStream_t st, int B);
 void launch_ks_combine(const KernelEnv& env, u64* out, size_t ps, const u64* base0, u64 galois0, const u64* base1, size_t bstride,
                        const u64* u, const u64* w, int level, cudaStream_t st, int B = 1, const u64* addend = nullptr);
 // fused key switching (ks_fused.cu)

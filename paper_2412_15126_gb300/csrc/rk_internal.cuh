@@ -303,6 +303,8 @@ void ev_mul_plain(rk_ctx* c, const rk_ct* a, uint32_t kind, uint32_t N, uint32_t
 void ev_rotate_many(rk_ctx* c, const rk_ct* a, const int* r, int k, rk_ct** outs);  // left rotations
 void ev_rotate_add(rk_ctx* c, const rk_ct* a, int r, rk_ct* out);               // a + (a <<< r)
 void ev_rotate_multi(rk_ctx* c, const rk_ct* a, const int* r, bool add, rk_ct* out);  // member b by r[b]
+// outs[s]_b = [a_b +] sum_k a_b <<< r[(s B + b) 3 + k], k < K[s] <= 3: one ModUp, one ModDown
+void ev_rotate_sums(rk_ctx* c, const rk_ct* a, int nsets, const int* K, const int* r, bool add, rk_ct** outs);
 void ev_add_plain(rk_ctx* c, const rk_ct* a, uint32_t kind, uint32_t N, uint32_t Q, uint32_t n_real, rk_ct* out);
 void ev_lincomb(rk_ctx* c, const std::vector<const rk_ct*>& xs, const std::vector<double>& cs, rk_ct* out,
                 bool rescale = true);   // sum c_i x_i, then a rescale unless told not to  // out at level-1

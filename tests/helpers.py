@@ -61,13 +61,19 @@ def import_encodings(ctx, P, N, Q=1, n_real=None, kinds=("row0", "col0", "tie", 
         ctx.encoding_import(MASK_IDS["valid"], N, Q, n_real, u)
 
 
-def rotation_set(N):
+def rotation_set(N, radix4=True):
+    """Rotations of every circuit's chains for length N (ReplR, ReplC, SumR, SumC,
+    TransR, TransC), and with radix4 the sums a_i + a_(i+1) of the step pairs the
+    chains take two at a time (i = 0, 2, 4 ..)."""
     k = int(np.log2(N))
     rs = set()
-    for i in range(k):
-        rs.update({-(N << i), N << i, -(1 << i), 1 << i})
-    for i in range(1, k + 1):
-        rs.update({-((N * (N - 1)) >> i), (N * (N - 1)) >> i})
+    chains = [[-(N << i) for i in range(k)], [-(1 << i) for i in range(k)],
+              [N << i for i in range(k)], [1 << i for i in range(k)],
+              [-((N * (N - 1)) >> i) for i in range(1, k + 1)], [(N * (N - 1)) >> i for i in range(1, k + 1)]]
+    for ch in chains:
+        rs.update(ch)
+        if radix4:
+            rs.update(ch[i] + ch[i + 1] for i in range(0, len(ch) - 1, 2))
     return sorted(rs)
 
 

@@ -30,13 +30,15 @@ pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 
 def rank_rotations(N):
-    """The rotation amounts of a rank (ReplR, TransR, ReplC, SumR)."""
+    """The rotation amounts of a rank (ReplR, TransR, ReplC, SumR), with the sums of
+    the step pairs its chains take two at a time."""
     k = int(np.log2(N))
+    chains = [[-(N << i) for i in range(k)], [-(1 << i) for i in range(k)], [N << i for i in range(k)],
+              [-((N * (N - 1)) >> i) for i in range(1, k + 1)]]
     rs = set()
-    for i in range(k):
-        rs.update({-(N << i), -(1 << i), N << i})
-    for i in range(1, k + 1):
-        rs.add(-((N * (N - 1)) >> i))
+    for ch in chains:   # every step, and the sums of the step pairs taken two at a time
+        rs.update(ch)
+        rs.update(ch[i] + ch[i + 1] for i in range(0, len(ch) - 1, 2))
     return sorted(rs)
 
 

@@ -94,7 +94,7 @@ def test_fig4_tie_offset(golden):
 def test_rotation_count_rank(golden):
     # Sec. 3.1: 4 ceil(log N) rotations for ranking; 28 at N = 128 (Sec. 6 argmin count).
     for N in (2, 8, 32, 128):
-        B = C.PlainSlots(max(2 * N * N, 64), 40)
+        B = C.PlainSlots(max(2 * N * N, 64), 40, radix2=True)   # one doubling a step, as printed
         C.rank(B, B.fresh(np.linspace(0, 0.9, N)), N, 4, 2)
         assert B.counts["rot"] == 4 * int(np.log2(N))
     assert golden["argmin_counts"]["rotations"] == 4 * 7
