@@ -15,124 +15,146 @@ const char* const kKernelKindNames[KK_COUNT] = {"ntt_fwd", "ntt_inv", "modup", "
 
 // ===========================================================================
 // Pointwise kernels on ciphertexts (layout [2][L+1][n], limb t <-> q_t).
-// grid: (n / TPB, limbs, polys)
+// Two consecutive coefficients a thread, moved as one 16-byte access (every offset
+// below is even and every buffer 16-byte aligned); grid: (n / (2 TPB), limbs, polys).
 // ===========================================================================
+__device__ __forceinline__ ulonglong2 ld2(const u64* p) { return *reinterpret_cast<const ulonglong2*>(p); }
+__device__ __forceinline__ void st2(u64* p, u64 x, u64 y) { *reinterpret_cast<ulonglong2*>(p) = make_ulonglong2(x, y); }
+inline dim3 grid2(const KernelEnv& env, int limbs, int polys) { return dim3(env.n / (2 * TPB), limbs, polys); }
+
 __global__ void k_addsub(u64* out, const u64* a, const u64* b, int n, size_t ps, const PrimeConst* __restrict__ pc, int mode) {
     RK_KERNEL_PROLOGUE();
-    const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y, c = blockIdx.z;
+    const int k = 2 * (blockIdx.x * TPB + threadIdx.x), t = blockIdx.y, c = blockIdx.z;
     const u64 q = pc[t].q;
     const size_t off = c * ps + (size_t)t * n + k;
-    u64 x = a[off];
-    u64 r;
-    if (mode == 0) r = add_mod(x, b[off], q);
-    else if (mode == 1) r = sub_mod(x, b[off], q);
-    else r = x ? q - x : 0;
-    out[off] = r;
+    const ulonglong2 x = ld2(a + off);
+    if (mode == 2) {
+        st2(out + off, x.x ? q - x.x : 0, x.y ? q - x.y : 0);
+        return;
+    }
+    const ulonglong2 y = ld2(b + off);
+    if (mode == 0) st2(out + off, add_mod(x.x, y.x, q), add_mod(x.y, y.y, q));
+    else st2(out + off, sub_mod(x.x, y.x, q), sub_mod(x.y, y.y, q));
 }
 
 void launch_addsub(const KernelEnv& env, u64* out, const u64* a, const u64* b, int limbs, size_t ps, int mode, cudaStream_t st,
                    int polys) {
     ProfScope pf(env, KK_POINTWISE, st, 1, 3.0 * polys * limbs * 8.0 * env.n, 0.0);
-    dim3 g(env.n / TPB, limbs, polys);
-    rk_launch(k_addsub, g, TPB, 0, st, out, a, b, env.n, ps, env.pc, mode);
+    rk_launch(k_addsub, grid2(env, limbs, polys), TPB, 0, st, out, a, b, env.n, ps, env.pc, mode);
 }
 
 // out0 = a0 + K_t, out1 = a1
 __global__ void k_add_const(u64* out, const u64* a, ScalarArg K, int n, size_t ps, const PrimeConst* __restrict__ pc) {
     RK_KERNEL_PROLOGUE();
-    const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y, c = blockIdx.z;
+    const int k = 2 * (blockIdx.x * TPB + threadIdx.x), t = blockIdx.y, c = blockIdx.z;
     const size_t off = c * ps + (size_t)t * n + k;
-    u64 x = a[off];
-    if ((c & 1) == 0) x = add_mod(x, K.w[t], pc[t].q);
-    out[off] = x;
+    ulonglong2 x = ld2(a + off);
+    if ((c & 1) == 0) {
+        const u64 q = pc[t].q;
+        x.x = add_mod(x.x, K.w[t], q);
+        x.y = add_mod(x.y, K.w[t], q);
+    }
+    st2(out + off, x.x, x.y);
 }
 
 void launch_add_const(const KernelEnv& env, u64* out, const u64* a, const ScalarArg& K, int limbs, size_t ps, cudaStream_t st,
                       int polys) {
     ProfScope pf(env, KK_POINTWISE, st, 1, 2.0 * polys * limbs * 8.0 * env.n, 0.0);
-    dim3 g(env.n / TPB, limbs, polys);
-    rk_launch(k_add_const, g, TPB, 0, st, out, a, K, env.n, ps, env.pc);
+    rk_launch(k_add_const, grid2(env, limbs, polys), TPB, 0, st, out, a, K, env.n, ps, env.pc);
 }
 
 // out = a * K_t (Shoup)
 // limbs t0 .. t0 + gridDim.y - 1
 __global__ void k_mul_scalar(u64* out, const u64* a, ScalarArg K, int n, size_t ps, int t0, const PrimeConst* __restrict__ pc) {
     RK_KERNEL_PROLOGUE();
-    const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y + t0, c = blockIdx.z;
+    const int k = 2 * (blockIdx.x * TPB + threadIdx.x), t = blockIdx.y + t0, c = blockIdx.z;
     const size_t off = c * ps + (size_t)t * n + k;
-    out[off] = shoup_mul(a[off], K.w[t], K.wsh[t], pc[t].q);
+    const u64 q = pc[t].q;
+    const ulonglong2 x = ld2(a + off);
+    st2(out + off, shoup_mul(x.x, K.w[t], K.wsh[t], q), shoup_mul(x.y, K.w[t], K.wsh[t], q));
 }
 
 void launch_mul_scalar(const KernelEnv& env, u64* out, const u64* a, const ScalarArg& K, int limbs, size_t ps, cudaStream_t st,
                        int polys, int t0) {
     ProfScope pf(env, KK_POINTWISE, st, 1, 2.0 * polys * limbs * 8.0 * env.n, 1.0 * polys * limbs * env.n);
-    dim3 g(env.n / TPB, limbs, polys);
-    rk_launch(k_mul_scalar, g, TPB, 0, st, out, a, K, env.n, ps, t0, env.pc);
+    rk_launch(k_mul_scalar, grid2(env, limbs, polys), TPB, 0, st, out, a, K, env.n, ps, t0, env.pc);
 }
 
 // out = a * pt, pt stored times R ([limbs][n])
 __global__ void k_mul_plain(u64* out, const u64* a, const u64* pt, int n, size_t ps, const PrimeConst* __restrict__ pc) {
     RK_KERNEL_PROLOGUE();
-    const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y, c = blockIdx.z;
+    const int k = 2 * (blockIdx.x * TPB + threadIdx.x), t = blockIdx.y, c = blockIdx.z;
     const size_t off = c * ps + (size_t)t * n + k;
     const PrimeConst P = pc[t];
-    out[off] = mont_mul(a[off], pt[(size_t)t * n + k], P.q, P.qinv);
+    const ulonglong2 x = ld2(a + off), m = ld2(pt + (size_t)t * n + k);
+    st2(out + off, mont_mul(x.x, m.x, P.q, P.qinv), mont_mul(x.y, m.y, P.q, P.qinv));
 }
 
 void launch_mul_plain(const KernelEnv& env, u64* out, const u64* a, const u64* pt, int limbs, size_t ps, cudaStream_t st,
                       int polys) {
     ProfScope pf(env, KK_POINTWISE, st, 1, (2.0 * polys + 1.0) * limbs * 8.0 * env.n, 1.0 * polys * limbs * env.n);
-    dim3 g(env.n / TPB, limbs, polys);
-    rk_launch(k_mul_plain, g, TPB, 0, st, out, a, pt, env.n, ps, env.pc);
+    rk_launch(k_mul_plain, grid2(env, limbs, polys), TPB, 0, st, out, a, pt, env.n, ps, env.pc);
 }
 
 // out (+)= sum_i x_i * K_i, exact modular arithmetic, one reduction per output
 __global__ void k_lincomb(u64* out, LincombArg a, int terms, int accumulate, int n, size_t ps, const PrimeConst* __restrict__ pc) {
     RK_KERNEL_PROLOGUE();
-    const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y, c = blockIdx.z;
+    const int k = 2 * (blockIdx.x * TPB + threadIdx.x), t = blockIdx.y, c = blockIdx.z;
     const PrimeConst P = pc[t];
     const size_t off = c * ps + (size_t)t * n + k;
-    Acc128 acc;
-    for (int i = 0; i < terms; i++) acc.mac(a.x[i][off], a.KR[i][t]);
-    u64 r = acc.redc(P.q, P.qinv);
-    if (accumulate) r = add_mod(r, out[off], P.q);
-    out[off] = r;
+    Acc128 acc0, acc1;
+    for (int i = 0; i < terms; i++) {
+        const ulonglong2 x = ld2(a.x[i] + off);
+        acc0.mac(x.x, a.KR[i][t]);
+        acc1.mac(x.y, a.KR[i][t]);
+    }
+    u64 r0 = acc0.redc(P.q, P.qinv), r1 = acc1.redc(P.q, P.qinv);
+    if (accumulate) {
+        const ulonglong2 o = ld2(out + off);
+        r0 = add_mod(r0, o.x, P.q);
+        r1 = add_mod(r1, o.y, P.q);
+    }
+    st2(out + off, r0, r1);
 }
 
 void launch_lincomb(const KernelEnv& env, u64* out, const LincombArg& a, int terms, bool accumulate, int limbs, size_t ps,
                     cudaStream_t st, int polys) {
     ProfScope pf(env, KK_POINTWISE, st, 1, (terms + 1.0) * polys * limbs * 8.0 * env.n, 1.0 * terms * polys * limbs * env.n);
-    dim3 g(env.n / TPB, limbs, polys);
-    rk_launch(k_lincomb, g, TPB, 0, st, out, a, terms, accumulate ? 1 : 0, env.n, ps, env.pc);
+    rk_launch(k_lincomb, grid2(env, limbs, polys), TPB, 0, st, out, a, terms, accumulate ? 1 : 0, env.n, ps, env.pc);
 }
 
 // d = [d0 | d1 | d2] each [limbs][n]: d0 = x0 y0, d1 = x0 y1 + x1 y0, d2 = x1 y1
 // one ciphertext pair per blockIdx.z (stacked layout [B][2][L+1][n]); d is [B][3][limbs][n]
 __global__ void k_tensor(u64* d, const u64* x, const u64* y, int limbs, int n, size_t ps, const PrimeConst* __restrict__ pc) {
     RK_KERNEL_PROLOGUE();
-    const int k = blockIdx.x * TPB + threadIdx.x, t = blockIdx.y, b = blockIdx.z;
+    const int k = 2 * (blockIdx.x * TPB + threadIdx.x), t = blockIdx.y, b = blockIdx.z;
     const PrimeConst P = pc[t];
     const size_t pl = (size_t)limbs * n;
     x += (size_t)b * 2 * ps;
     y += (size_t)b * 2 * ps;
     d += (size_t)b * 3 * pl;
     const size_t off = (size_t)t * n + k;
-    const u64 x0 = x[off], x1 = x[ps + off], y0 = y[off], y1 = y[ps + off];
-    u64 r0 = mont_mul(x0, y0, P.q, P.qinv);
-    Acc128 a1;
-    a1.mac(x0, y1);
-    a1.mac(x1, y0);
-    u64 r1 = a1.redc(P.q, P.qinv);
-    u64 r2 = mont_mul(x1, y1, P.q, P.qinv);
-    d[off] = shoup_mul(r0, P.r_mod, P.r_shoup, P.q);
-    d[pl + off] = shoup_mul(r1, P.r_mod, P.r_shoup, P.q);
-    d[2 * pl + off] = shoup_mul(r2, P.r_mod, P.r_shoup, P.q);
+    const ulonglong2 X0 = ld2(x + off), X1 = ld2(x + ps + off), Y0 = ld2(y + off), Y1 = ld2(y + ps + off);
+    u64 r[3][2];
+    const u64 x0s[2] = {X0.x, X0.y}, x1s[2] = {X1.x, X1.y}, y0s[2] = {Y0.x, Y0.y}, y1s[2] = {Y1.x, Y1.y};
+#pragma unroll
+    for (int e = 0; e < 2; e++) {
+        const u64 x0 = x0s[e], x1 = x1s[e], y0 = y0s[e], y1 = y1s[e];
+        Acc128 a1;
+        a1.mac(x0, y1);
+        a1.mac(x1, y0);
+        r[0][e] = shoup_mul(mont_mul(x0, y0, P.q, P.qinv), P.r_mod, P.r_shoup, P.q);
+        r[1][e] = shoup_mul(a1.redc(P.q, P.qinv), P.r_mod, P.r_shoup, P.q);
+        r[2][e] = shoup_mul(mont_mul(x1, y1, P.q, P.qinv), P.r_mod, P.r_shoup, P.q);
+    }
+    st2(d + off, r[0][0], r[0][1]);
+    st2(d + pl + off, r[1][0], r[1][1]);
+    st2(d + 2 * pl + off, r[2][0], r[2][1]);
 }
 
 void launch_tensor(const KernelEnv& env, u64* d, const u64* x, const u64* y, int limbs, size_t ps, cudaStream_t st, int B) {
     ProfScope pf(env, KK_TENSOR, st, 1, 7.0 * B * limbs * 8.0 * env.n, 4.0 * B * limbs * env.n);
-    dim3 g(env.n / TPB, limbs, B);
-    rk_launch(k_tensor, g, TPB, 0, st, d, x, y, limbs, env.n, ps, env.pc);
+    rk_launch(k_tensor, grid2(env, limbs, B), TPB, 0, st, d, x, y, limbs, env.n, ps, env.pc);
 }
 
 // ===========================================================================
@@ -354,24 +376,26 @@ __global__ void k_ks_combine_rs(u64* out, size_t ps, const u64* __restrict__ u, 
                                 const u64* __restrict__ d, int level, int L, int alpha, ConvTables cv, int n,
                                 const PrimeConst* __restrict__ pc) {
     RK_KERNEL_PROLOGUE();
-    const int k = blockIdx.x * TPB + threadIdx.x, i = blockIdx.y, c = blockIdx.z;
+    const int k = 2 * (blockIdx.x * TPB + threadIdx.x), i = blockIdx.y, c = blockIdx.z;
     const int b = c >> 1, p = c & 1;
     const u64 q = pc[i].q;
     const size_t pl = (size_t)(level + 1) * n;
     const u64* sinv = cv.mdrs + (size_t)level * cv.mdrs_stride + 2 * (alpha + 1) + (size_t)(alpha + 1) * (L + 1) + (L + 1);
     const u64* rs = cv.rescale + (size_t)level * 3 * (L + 1);
-    const u64 uv = u[(size_t)c * (level + 1 + alpha) * n + (size_t)i * n + k];
-    const u64 wv = w[(size_t)c * level * n + (size_t)i * n + k];
-    const u64 dv = d[(size_t)b * 3 * pl + (size_t)p * pl + (size_t)i * n + k];
-    const u64 a = shoup_mul(sub_mod(uv, wv, q), sinv[i], sinv[(L + 1) + i], q);
-    out[(size_t)c * ps + (size_t)i * n + k] = add_mod(a, shoup_mul(dv, rs[i], rs[(L + 1) + i], q), q);
+    const u64 s0 = sinv[i], s1 = sinv[(L + 1) + i], r0 = rs[i], r1 = rs[(L + 1) + i];
+    const ulonglong2 uv = ld2(u + (size_t)c * (level + 1 + alpha) * n + (size_t)i * n + k);
+    const ulonglong2 wv = ld2(w + (size_t)c * level * n + (size_t)i * n + k);
+    const ulonglong2 dv = ld2(d + (size_t)b * 3 * pl + (size_t)p * pl + (size_t)i * n + k);
+    const u64 a0 = shoup_mul(sub_mod(uv.x, wv.x, q), s0, s1, q), a1 = shoup_mul(sub_mod(uv.y, wv.y, q), s0, s1, q);
+    st2(out + (size_t)c * ps + (size_t)i * n + k, add_mod(a0, shoup_mul(dv.x, r0, r1, q), q),
+        add_mod(a1, shoup_mul(dv.y, r0, r1, q), q));
 }
 
 void launch_ks_combine_rs(const KernelEnv& env, u64* out, size_t ps, const u64* u, const u64* w, const u64* d, int level,
                           cudaStream_t st, int B) {
     ProfScope pf(env, KK_KS_COMBINE, st, 1, 8.0 * B * level * 8.0 * env.n, 2.0 * B * level * env.n);
-    dim3 g(env.n / TPB, level, 2 * B);
-    rk_launch(k_ks_combine_rs, g, TPB, 0, st, out, ps, u, w, d, level, env.L, env.alpha, env.conv, env.n, env.pc);
+    rk_launch(k_ks_combine_rs, grid2(env, level, 2 * B), TPB, 0, st, out, ps, u, w, d, level, env.L, env.alpha, env.conv, env.n,
+              env.pc);
 }
 
 // ===========================================================================
@@ -561,20 +585,24 @@ template <bool SCALE>
 __global__ void k_rescale_combine(u64* out, const u64* in, size_t ps, const u64* v, int level, int L, ConvTables cv, ScalarArg K,
                                   int n, const PrimeConst* __restrict__ pc) {
     RK_KERNEL_PROLOGUE();
-    const int k = blockIdx.x * TPB + threadIdx.x, i = blockIdx.y, c = blockIdx.z;
+    const int k = 2 * (blockIdx.x * TPB + threadIdx.x), i = blockIdx.y, c = blockIdx.z;
     const u64 q = pc[i].q;
     const u64* tab = cv.rescale + (size_t)level * 3 * (L + 1);
+    const u64 t0 = tab[i], t1 = tab[(L + 1) + i];
     const size_t off = (size_t)c * ps + (size_t)i * n + k;
-    u64 x = in[off];
-    if (SCALE) x = shoup_mul(x, K.w[i], K.wsh[i], q);
-    const u64 d = sub_mod(x, v[(size_t)c * level * n + (size_t)i * n + k], q);
-    out[off] = shoup_mul(d, tab[i], tab[(L + 1) + i], q);
+    ulonglong2 x = ld2(in + off);
+    if (SCALE) {
+        x.x = shoup_mul(x.x, K.w[i], K.wsh[i], q);
+        x.y = shoup_mul(x.y, K.w[i], K.wsh[i], q);
+    }
+    const ulonglong2 vv = ld2(v + (size_t)c * level * n + (size_t)i * n + k);
+    st2(out + off, shoup_mul(sub_mod(x.x, vv.x, q), t0, t1, q), shoup_mul(sub_mod(x.y, vv.y, q), t0, t1, q));
 }
 
 void launch_rescale_combine(const KernelEnv& env, u64* out, const u64* in, size_t ps, const u64* v, int level, const ScalarArg* K,
                             cudaStream_t st, int polys) {
     ProfScope pf(env, KK_RESCALE, st, 1, 3.0 * polys * level * 8.0 * env.n, 1.0 * polys * level * env.n);
-    dim3 g(env.n / TPB, level, polys);
+    dim3 g = grid2(env, level, polys);
     if (K)
         rk_launch(k_rescale_combine<true>, g, TPB, 0, st, out, in, ps, v, level, env.L, env.conv, *K, env.n, env.pc);
     else

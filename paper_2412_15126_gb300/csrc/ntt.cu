@@ -42,12 +42,17 @@ __global__ void __launch_bounds__(256, (LOG <= 8 ? (COL ? RK_NTT_COL_BLOCKS : RK
     constexpr int P = S::P, E = S::E;
     extern __shared__ u64 sm[];
     const int n = 1 << logn, B = 1 << (logn - loga);
-    const int limb = blockIdx.y;
-    if (s.skip_ds && limb < s.split && limb / s.skip_ds == (int)(blockIdx.z % s.skip_beta)) return;   // block-uniform
+    // grid y = polynomial, z = limb: the polynomials of one limb (one prime, one twiddle
+    // table) run together; the second pass of a transform walks the grid backwards, so
+    // that it starts on the limbs the first pass wrote last (still in L2)
+    constexpr bool REV = INV == COL;
+    const int poly = REV ? gridDim.y - 1 - blockIdx.y : blockIdx.y;
+    const int limb = REV ? gridDim.z - 1 - blockIdx.z : blockIdx.z;
+    if (s.skip_ds && limb < s.split && limb / s.skip_ds == poly % s.skip_beta) return;   // block-uniform
     const int pid = limb_prime(s, limb);
     const PrimeConst PC = pc[pid];
     const u64 q = PC.q, q2 = 2 * q;
-    u64* data = s.base + (size_t)blockIdx.z * s.poly_stride + (size_t)limb * n;
+    u64* data = s.base + (size_t)poly * s.poly_stride + (size_t)limb * n;
     const int tid = threadIdx.x;
     int u, t, rho;
     u64* g;
@@ -73,7 +78,7 @@ __global__ void __launch_bounds__(256, (LOG <= 8 ? (COL ? RK_NTT_COL_BLOCKS : RK
         // load the strided set {t + P m}: coalesced over u (columns) or t (rows)
         if (LIFT) {
             // centred representative of the source residue x (mod lift_q), modulo q
-            const u64* lg = s.lift + (size_t)blockIdx.z * s.lift_stride + (size_t)blockIdx.x * units + u;
+            const u64* lg = s.lift + (size_t)poly * s.lift_stride + (size_t)blockIdx.x * units + u;
             const u64 half = s.lift_q >> 1, qlm = s.lift_mod[limb];
 #pragma unroll
             for (int m = 0; m < E; m++) {
@@ -110,7 +115,7 @@ __global__ void __launch_bounds__(256, (LOG <= 8 ? (COL ? RK_NTT_COL_BLOCKS : RK
 #pragma unroll
             for (int m = 0; m < E; m++) x[m] = g[(size_t)(t * E + m) * gs];
         } else {
-            const u64* gin = s.src ? s.src + (size_t)blockIdx.z * s.src_stride + (size_t)limb * n + (size_t)rho * B : g;
+            const u64* gin = s.src ? s.src + (size_t)poly * s.src_stride + (size_t)limb * n + (size_t)rho * B : g;
 #pragma unroll
             for (int m = 0; m < E; m++) sm[sidx(t + P * m)] = gin[t + P * m];
             __syncthreads();
@@ -155,13 +160,16 @@ __global__ void __launch_bounds__(256, 4) k_ntt_row8(LimbSet s, int logn, int lo
     RK_KERNEL_PROLOGUE();
     extern __shared__ u64 sm[];
     const int n = 1 << logn, B = 1 << (logn - loga);
-    const int limb = blockIdx.y;
-    if (s.skip_ds && limb < s.split && limb / s.skip_ds == (int)(blockIdx.z % s.skip_beta)) return;   // block-uniform
+    // grid y = polynomial, z = limb; the forward row pass (a transform's second pass)
+    // walks the grid backwards, starting on the limbs the column pass wrote last
+    const int poly = INV ? blockIdx.y : gridDim.y - 1 - blockIdx.y;
+    const int limb = INV ? blockIdx.z : gridDim.z - 1 - blockIdx.z;
+    if (s.skip_ds && limb < s.split && limb / s.skip_ds == poly % s.skip_beta) return;   // block-uniform
     const int pid = limb_prime(s, limb);
     const u64 q = pc[pid].q, q2 = 2 * q;
     const int wi = threadIdx.x >> 5, t = threadIdx.x & 31;
     const int rho = blockIdx.x * (blockDim.x >> 5) + wi;
-    u64* g = s.base + (size_t)blockIdx.z * s.poly_stride + (size_t)limb * n + (size_t)rho * B;
+    u64* g = s.base + (size_t)poly * s.poly_stride + (size_t)limb * n + (size_t)rho * B;
     u64* row = sm + wi * 256;
     const Twid tw_{tw + (size_t)pid * 2 * n, logn - 1, rho};
     auto stage = [&](int v) { return twid_stage<8>(tw_, v); };
@@ -224,7 +232,7 @@ __global__ void __launch_bounds__(256, 4) k_ntt_row8(LimbSet s, int logn, int lo
             reinterpret_cast<ulonglong2*>(g + 8 * t)[m >> 1] = pr;
         }
     } else {
-        const u64* gin = s.src ? s.src + (size_t)blockIdx.z * s.src_stride + (size_t)limb * n + (size_t)rho * B : g;
+        const u64* gin = s.src ? s.src + (size_t)poly * s.src_stride + (size_t)limb * n + (size_t)rho * B : g;
 #pragma unroll
         for (int m = 0; m < 8; m += 2) {
             const ulonglong2 pr = reinterpret_cast<const ulonglong2*>(gin + 8 * t)[m >> 1];
@@ -342,7 +350,7 @@ PassGeom geom(int LOG, bool COL, int count, const LimbSet& s, int sms, int force
     PassGeom gm;
     gm.units = units;
     gm.threads = P * units;
-    gm.grid = dim3(count / units, s.n_limbs, s.n_polys);
+    gm.grid = dim3(count / units, s.n_polys, s.n_limbs);
     gm.smem = (size_t)(1 << LOG) * units * 8;
     return gm;
 }
