@@ -216,7 +216,7 @@ def test_graph_capture_every_circuit_bit_identical():
     blocked rank, order statistic and sort (two blocks of two queries each): every
     replay equals the direct call bit for bit, on inputs other than the template."""
     from paper_2412_15126_gb300 import rankfhe
-    ctx = helpers.gpu_context("ord")
+    ctx = helpers.gpu_context("ordb")     # shallow comparator: the blocked sort of 2 x 4 fits 23 levels
     try:
         ctx.keygen(404, 8)
         mk = lambda s: ctx.encrypt(inputs.grid_vector(8, 16, s), N=8)

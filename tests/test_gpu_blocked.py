@@ -213,7 +213,8 @@ def test_pair_packed_blocked_circuits_bit_exact(ordb_packed):
         (v3, lambda g: ctx.rank_blocked(g), lambda c, p: C.rank_blocked(Bo, c, BSZ, 1, 1, pack=p),
          C.brute_fractional_rank(v3), 0.5),
         (t3, lambda g: ctx.rank_blocked(g, rankfhe.TIES_CORRECT),
-         lambda c, p: C.rank_blocked_tc(Bo, c, BSZ, 1, 1, pack=p)[0], C.brute_tie_corrected_rank(t3), 0.25),
+         lambda c, p: C.rank_blocked_tc(Bo, c, BSZ, 1, 1, pack=p)[0],
+         _plain_blocks(P, t3, lambda Bp, bl: C.rank_blocked_tc(Bp, bl, BSZ, 1, 1)[0]), 1e-3),
         (v2, lambda g: ctx.order_stat_blocked(g, 2), lambda c, p: C.order_statistic_blocked(Bo, c, BSZ, 2, 1, 1, pack=p),
          _plain_blocks(P, v2, lambda Bp, bl: C.order_statistic_blocked(Bp, bl, BSZ, 2, 1, 1)), 1e-3),
         (v2, lambda g: ctx.sort_blocked(g), lambda c, p: C.sort_blocked(Bo, c, BSZ, 1, 1, pack=p),
