@@ -367,6 +367,16 @@ rk_status rk_order_stat(rk_ctx* ctx, const rk_ct* in, uint32_t k, uint32_t flags
  * row 0); the other slots of row 0 are zero.  Errors as rk_order_stat. */
 rk_status rk_order_value(rk_ctx* ctx, const rk_ct* in, uint32_t k, rk_ct** out);
 
+/* Value of the k-th order statistic from the all-ties mask (Sec. 3.2): O = the
+ * rk_order_stat mask with RK_TIES_ALL (k = 1: every minimum, k = N: every maximum,
+ * other k: the elements of fractional rank k), and the value <O, V> / |O|_1 =
+ * SumC(O . V) / SumC(O), the division by Goldschmidt's iteration on SumC(O) / N
+ * (d iterations, d the smallest with (1 - 1/N)^(2^(d+1)) <= 2^-10: 5 at N = 8, 9 at
+ * N = 128).  The value is in slot 0 of each query block, zero if no element has rank
+ * k.  Takes the order statistic's levels plus d + 4.
+ * Errors: RK_EDEPTH, RK_ENOKEY, RK_EINVAL. */
+rk_status rk_order_value_all(rk_ctx* ctx, const rk_ct* in, uint32_t k, rk_ct** out);
+
 /* Median (Alg. 4's particular case): the (N+1)/2-th smallest value for odd N, the mean
  * of the N/2-th and (N/2+1)-th for even N, from one tie-corrected rank; in slot 0 as
  * for rk_order_value.  Errors as rk_order_stat. */

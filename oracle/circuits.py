@@ -763,6 +763,50 @@ def order_value(B, V, N, k, dg, df, Q=1, coeffs=None):
     return sum_c(B, B.mul(O, B.level_down(V, B.level(O))), N, Q)
 
 
+def goldschmidt_iterations(N: int) -> int:
+    """Iterations d of the inverse below for a mask weight m in [1, N]: the product
+    prod_{i<=d} (1 + y^(2^i)) equals (1 - y^(2^(d+1))) / x for y = 1 - x, x = m / N, so its
+    relative error is y^(2^(d+1)) <= (1 - 1/N)^(2^(d+1)); d is the smallest with that
+    at most 2^-10."""
+    d = 0
+    while (1.0 - 1.0 / N) ** (2 ** (d + 1)) > 2.0 ** -10:
+        d += 1
+    return d
+
+
+def inverse_goldschmidt(B, x, d):
+    """1/x for slots x in (0, 1] by Goldschmidt's iteration: y = 1 - x, a = 1 + y,
+    b = y^2, then d times a <- a (1 + b), b <- b^2 (one level each, the two products
+    in parallel)."""
+    y = B.add_const(B.neg(x), 1.0)
+    a = B.add_const(y, 1.0)
+    b = B.mul(y, y)
+    a = B.level_down(a, B.level(b))
+    for _ in range(d):
+        a2 = B.mul(a, B.add_const(b, 1.0))
+        b = B.mul(b, b)
+        a = a2
+    return a
+
+
+def order_value_all(B, V, N, k, dg, df, Q=1, coeffs=None):
+    """Value of the k-th order statistic from the all-ties mask (Sec. 3.2): O marks
+    every element of rank k (k = 1: every minimum, Cmp_G; k = N: every maximum,
+    Cmp_GE; other k: fractional ranks), and the value is <O, V> / |O|_1 =
+    SumC(O . V) / SumC(O), the division by Goldschmidt's iteration on
+    x = SumC(O) / N (goldschmidt_iterations(N) steps) with the 1/N folded into the
+    numerator.  The value sits in slot 0 of each query; zero if no element has
+    rank k."""
+    O = order_statistic(B, V, N, k, dg, df, Q, "all", coeffs)
+    num = sum_c(B, B.mul(O, B.level_down(V, B.level(O))), N, Q)
+    den = sum_c(B, O, N, Q)
+    x = B.mul_scalar(den, 1.0 / N)
+    inv = inverse_goldschmidt(B, x, goldschmidt_iterations(N))
+    numN = B.mul_scalar(num, 1.0 / N)
+    lo = min(B.level(numN), B.level(inv))
+    return B.mul(B.level_down(numN, lo), B.level_down(inv, lo))
+
+
 def median(B, V, N, dg, df, Q=1, coeffs=None):
     """Median (Alg. 4's particular case): the (N+1)/2-th statistic for odd N, the mean of
     the N/2-th and (N/2+1)-th for even N, as SumC((O_a + O_b) . V/2) on one shared rank."""

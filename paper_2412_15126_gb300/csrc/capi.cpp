@@ -10,6 +10,7 @@ rk_ct* circuit_rank(rk_ctx* c, const rk_ct* in, uint32_t flags);
 rk_ct* circuit_compare_matrix(rk_ctx* c, const rk_ct* in);
 void rescale_noalloc(rk_ctx* c, const u64* in, u64* out, int l);
 rk_ct* circuit_order_stat(rk_ctx* c, const rk_ct* in, uint32_t k, uint32_t flags);
+rk_ct* circuit_order_value_all(rk_ctx* c, const rk_ct* in, uint32_t k);
 rk_ct* circuit_sort(rk_ctx* c, const rk_ct* in, uint32_t flags);
 rk_ct* circuit_order_value(rk_ctx* c, const rk_ct* in, uint32_t k);
 rk_ct* circuit_median(rk_ctx* c, const rk_ct* in);
@@ -513,6 +514,18 @@ rk_status rk_indicator_import(rk_ctx* ctx, uint32_t N, const double* coeffs, siz
         need(ctx, "ctx");
         need(coeffs, "coeffs");
         indicator_import(ctx, N, coeffs, count);
+    });
+}
+
+rk_status rk_order_value_all(rk_ctx* ctx, const rk_ct* in, uint32_t k, rk_ct** out) {
+    return guard([&] {
+        need(ctx, "ctx");
+        same_ctx(ctx, in);
+        need(out, "out");
+        RK_REQUIRE(k >= 1 && k <= in->N, RK_EINVAL, "k must be in [1, N]");
+        set_device(ctx);
+        *out = circuit_order_value_all(ctx, in, k);
+        check_launch();
     });
 }
 

@@ -750,6 +750,47 @@ rk_ct* circuit_order_value(rk_ctx* c, const rk_ct* in, uint32_t k) {
     return sum_cols(E, E.mul(O, E.level_down(V, O->level)), RK_MASK_COL0).release();
 }
 
+// Iterations of the Goldschmidt inverse for a mask weight in [1, N]: the smallest d with
+// (1 - 1/N)^(2^(d+1)) <= 2^-10 (the relative error of prod_{i<=d} (1 + y^(2^i)) as 1/x).
+static int goldschmidt_iterations(uint32_t N) {
+    int d = 0;
+    while (std::pow(1.0 - 1.0 / (double)N, std::pow(2.0, d + 1)) > std::pow(2.0, -10)) d++;
+    return d;
+}
+
+int order_value_all_depth(rk_ctx* c, const rk_ct* in, uint32_t k) {
+    // O, then SumC (mask), the 1/N scalar, y^2, d iterations and the final product
+    return order_stat_depth(c, in, k, RK_TIES_ALL) + 4 + goldschmidt_iterations(in->N);
+}
+
+// The value of the k-th statistic from the all-ties mask (Sec. 3.2): <O, V> / |O|_1 =
+// SumC(O . V) / SumC(O), the inverse by Goldschmidt's iteration on x = SumC(O) / N
+// (y = 1 - x, a = 1 + y, b = y^2, then a <- a (1 + b), b <- b^2), the 1/N folded into
+// the numerator; slot 0 of each query, zero if no element has rank k.
+rk_ct* circuit_order_value_all(rk_ctx* c, const rk_ct* in, uint32_t k) {
+    check_square(c, in, order_value_all_depth(c, in, k), "order value (all ties)");
+    const double Nd = (double)in->N;
+    Ev E{c};
+    H O(circuit_order_stat(c, in, k, RK_TIES_ALL));
+    H V(ct_clone_meta(in, in->level));
+    ev_copy(c, in, V.p);
+    H num = sum_cols(E, E.mul(O, E.level_down(V, O->level)), RK_MASK_COL0);
+    H den = sum_cols(E, E.copy(O), RK_MASK_COL0);
+    H x = E.mul_scalar(den, 1.0 / Nd);
+    H y = E.add_const(E.neg(x), 1.0);
+    H a = E.add_const(y, 1.0);
+    H b = E.mul(y, y);
+    a = E.level_down(a, b->level);
+    for (int i = goldschmidt_iterations(in->N); i > 0; i--) {
+        H a2 = E.mul(a, E.add_const(b, 1.0));
+        b = E.mul(b, b);
+        a = std::move(a2);
+    }
+    H numN = E.mul_scalar(num, 1.0 / Nd);
+    const int lo = std::min(numN->level, a->level);
+    return E.mul(E.level_down(numN, lo), E.level_down(a, lo)).release();
+}
+
 // Median (Alg. 4's particular case): the (N+1)/2-th statistic for odd N, else the mean
 // of the N/2-th and (N/2+1)-th, as SumC((O_a + O_b) . V/2) on one shared rank; the two
 // indicators run as one stack.

@@ -115,6 +115,7 @@ _sig("rk_order_stat", [_vp, _vp, _u32, _u32, ctypes.POINTER(_vp)])
 _sig("rk_sort", [_vp, _vp, _u32, ctypes.POINTER(_vp)])
 _sig("rk_order_value", [_vp, _vp, _u32, ctypes.POINTER(_vp)])
 _sig("rk_median", [_vp, _vp, ctypes.POINTER(_vp)])
+_sig("rk_order_value_all", [_vp, _vp, _u32, ctypes.POINTER(_vp)])
 _sig("rk_indicator_import", [_vp, _u32, _dp, _sz])
 _sig("rk_comparator_import", [_vp, _dp, _sz])
 _sig("rk_rank_batch", [_vp, ctypes.POINTER(_vp), _sz, _u32, ctypes.POINTER(_vp)])
@@ -466,6 +467,11 @@ class Context:
 
     def order_value(self, ct, k):
         return self._out(_L.rk_order_value, ct.handle, int(k))
+
+    def order_value_all(self, ct, k):
+        """Value of the k-th statistic from the all-ties mask, divided by its weight
+        (Goldschmidt); slot 0 of each query."""
+        return self._out(_L.rk_order_value_all, ct.handle, int(k))
 
     def median(self, ct):
         return self._out(_L.rk_median, ct.handle)

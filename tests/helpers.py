@@ -17,6 +17,8 @@ CONFIGS = {
     # the smallest ring holding a 128 x 128 matrix, with the 34-limb chain of the tie
     # workload (not 128-bit secure at n = 2^15: a parity set only)
     "big15": (15, 34, 60, 45, 3, 61, 3, 3, 2),
+    # a deeper n = 2^11 ring (test only): order statistics with the division of Sec. 3.2
+    "deep": (11, 36, 60, 40, 2, 61, 2, 2, 1),
 }
 
 MASK_IDS = {"row0": 1, "col0": 2, "tie": 3, "tri": 4, "valid": 5, "row0s": 6, "col0s": 7, "tiec": 8, "sortidx": 9,
