@@ -140,6 +140,12 @@ rk_status rk_ctx_counters(const rk_ctx* ctx, uint64_t out[4]);
  *   B <= max_len / 2 and all but +-n/4 otherwise); the ciphertexts then carry the
  *   packing rotations' noise (same decryption within the circuits' tolerance).  0 runs
  *   every pair on its own ciphertext.
+ * RK_OPT_STACK_BUDGET: bytes of device memory one stacked step of the blocked circuits
+ *   may take (default 16 GiB): the forms of the blocks and the block-pair comparisons
+ *   run in chunks of whole packing groups that fit it, so L is bounded by memory for
+ *   the L output blocks only.  RK_OPT_INDICATOR_BUDGET: the same for the blocked order
+ *   statistic's and sort's indicator evaluations (default 4 GiB).  Results never
+ *   depend on either.
  * RK_OPT_SERVER_LANES: execution lanes of the next rk_server_start (1 to 16, default 2):
  *   each runs its own batch on its own stream, so batches overlap on the device.
  * RK_OPT_TRIM_LEVELS: 0 (default) evaluates rk_rank / rk_rank_batch at the input's
@@ -156,6 +162,8 @@ rk_status rk_ctx_counters(const rk_ctx* ctx, uint64_t out[4]);
 #define RK_OPT_TRIM_LEVELS 4
 #define RK_OPT_SERVER_LANES 5
 #define RK_OPT_PAIR_PACKING 6
+#define RK_OPT_STACK_BUDGET 7
+#define RK_OPT_INDICATOR_BUDGET 8
 rk_status rk_ctx_set_option(rk_ctx* ctx, uint32_t option, int64_t value);
 
 /* Autotune the launch shapes on this device (the paper has no counterpart): times

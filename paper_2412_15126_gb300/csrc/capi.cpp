@@ -185,6 +185,14 @@ rk_status rk_ctx_set_option(rk_ctx* ctx, uint32_t option, int64_t value) {
             case RK_OPT_BLOCK_STACKING: ctx->stack_blocks = value != 0; break;
             case RK_OPT_TRIM_LEVELS: ctx->trim_levels = value != 0; break;
             case RK_OPT_PAIR_PACKING: ctx->pair_packing = value != 0; break;
+            case RK_OPT_STACK_BUDGET:
+                RK_REQUIRE(value >= 1, RK_EINVAL, "stack budget must be positive");
+                ctx->stack_budget_bytes = (size_t)value;
+                break;
+            case RK_OPT_INDICATOR_BUDGET:
+                RK_REQUIRE(value >= 1, RK_EINVAL, "indicator budget must be positive");
+                ctx->ind_stack_bytes = (size_t)value;
+                break;
             case RK_OPT_SERVER_LANES:
                 RK_REQUIRE(value >= 1 && value <= 16, RK_EINVAL, "server lanes must be 1 to 16");
                 ctx->server_lanes = (int)value;

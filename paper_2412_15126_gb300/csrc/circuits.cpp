@@ -964,6 +964,46 @@ static H packed_apply(rk_ctx* c, Ev& E, H X, int m, int Bq, int T, int per, F f)
 // contributes), all at the comparison's output level.  The L blocks (one ciphertext
 // each, same shape; each may be a stack of Bq members, block i of Bq queries) run as one
 // stack through ReplR/TransR/ReplC, the listed comparisons as one stack through Cmp.
+// Stack members of a step at `level` that fit the context's stacking budget: a member
+// holds the key-switching scratch of one ciphertext and about a dozen live ciphertexts.
+static int stack_chunk(const rk_ctx* c, int level) {
+    const size_t l1 = (size_t)level + 1, QP = l1 + c->alpha;
+    const size_t words = (l1 + (size_t)c->beta(level) * QP + 2 * QP + 7 * l1) + 24 * l1;
+    return (int)std::max<size_t>(1, c->stack_budget_bytes / (words * c->n * 8));
+}
+
+// ReplR and ReplC(TransR) forms of L blocks (stacks of Bq each) as two stacks of L Bq,
+// evaluated in chunks of blocks that fit the stacking budget (the same values as one
+// stack: members are independent).
+static std::pair<H, H> blocked_forms(rk_ctx* c, Ev& E, const rk_ct* const* blocks, int L) {
+    const int Bq = blocks[0]->B;
+    const int fc = std::max(1, stack_chunk(c, blocks[0]->level) / Bq);
+    if (c->stack_blocks && fc >= L) {
+        H V(ct_stack(c, blocks, L));
+        return row_col_forms(E, V);
+    }
+    std::vector<H> fr, fcol;
+    std::vector<rk_ct*> pr, pc;
+    if (!c->stack_blocks) {   // the plain per-query form: every member on its own
+        H V(ct_stack(c, blocks, L));
+        for (int b = 0; b < V->B; b++) {
+            auto f = row_col_forms(E, E.copy(H(ct_view(V.p, b))));
+            fr.push_back(std::move(f.first));
+            fcol.push_back(std::move(f.second));
+        }
+    } else {
+        for (int b0 = 0; b0 < L; b0 += fc) {
+            H V(ct_stack(c, blocks + b0, std::min(fc, L - b0)));
+            auto f = row_col_forms(E, V);
+            fr.push_back(std::move(f.first));
+            fcol.push_back(std::move(f.second));
+        }
+    }
+    for (auto& h : fr) pr.push_back(h.p);
+    for (auto& h : fcol) pc.push_back(h.p);
+    return std::make_pair(stack_of(c, pr), stack_of(c, pc));
+}
+
 void circuit_rank_blocked_partial(rk_ctx* c, const rk_ct* const* blocks, int L, const std::vector<std::pair<int, int>>& pairs,
                                   rk_ct** A_out, rk_ct** B_out) {
     const int need = 3 + cmp_depth(c);
@@ -972,42 +1012,30 @@ void circuit_rank_blocked_partial(rk_ctx* c, const rk_ct* const* blocks, int L, 
         RK_REQUIRE(pr.first >= 0 && pr.first <= pr.second && pr.second < L, RK_EINVAL, "block pair out of range");
     const int Bq = blocks[0]->B;
     Ev E{c};
-    H V(ct_stack(c, blocks, L));
-    std::pair<H, H> rc;   // stacks of L Bq
-    if (c->stack_blocks || V->B == 1) {
-        rc = row_col_forms(E, V);
-    } else {
-        std::vector<H> fr, fc;
-        std::vector<rk_ct*> pr, pc;
-        for (int b = 0; b < V->B; b++) {
-            auto f = row_col_forms(E, E.copy(H(ct_view(V.p, b))));
-            fr.push_back(std::move(f.first));
-            fc.push_back(std::move(f.second));
-            pr.push_back(fr.back().p);
-            pc.push_back(fc.back().p);
-        }
-        rc = std::make_pair(stack_of(c, pr), stack_of(c, pc));
-    }
+    std::pair<H, H> rc = blocked_forms(c, E, blocks, L);   // stacks of L Bq
     const int lvl = rc.second->level - cmp_depth(c);
     std::vector<H> A(L), Bs(L);
-    if (!pairs.empty()) {
+    const int per = pair_tiles(c, blocks[0]);
+    const int T = (int)(blocks[0]->Q * blocks[0]->N * blocks[0]->N);
+    // the listed pairs in chunks that fit the stacking budget (whole packing groups)
+    const size_t chunk = (size_t)std::max(1, stack_chunk(c, rc.second->level) / Bq) * per;
+    for (size_t p0 = 0; p0 < pairs.size(); p0 += chunk) {
+        const size_t p1 = std::min(pairs.size(), p0 + chunk);
         std::vector<H> vr_views, vc_views;
         std::vector<rk_ct*> vr, vc;
-        for (auto& pr : pairs) {
-            vr_views.push_back(range(rc.first, pr.first, Bq));
-            vc_views.push_back(range(rc.second, pr.second, Bq));
+        for (size_t p = p0; p < p1; p++) {
+            vr_views.push_back(range(rc.first, pairs[p].first, Bq));
+            vc_views.push_back(range(rc.second, pairs[p].second, Bq));
             vr.push_back(vr_views.back().p);
             vc.push_back(vc_views.back().p);
         }
-        const int per = pair_tiles(c, blocks[0]);
-        const int T = (int)(blocks[0]->Q * blocks[0]->N * blocks[0]->N);
-        H Cst = per > 1 ? packed_apply(c, E, E.sub(stack_of(c, vr), stack_of(c, vc)), (int)pairs.size(), Bq, T, per,
+        H Cst = per > 1 ? packed_apply(c, E, E.sub(stack_of(c, vr), stack_of(c, vc)), (int)(p1 - p0), Bq, T, per,
                                        [&](H x) { return cmp(E, std::move(x), (int)c->prm.d_g, (int)c->prm.d_f); })
                         : each(c, E, E.sub(stack_of(c, vr), stack_of(c, vc)),
                                [&](H x) { return cmp(E, std::move(x), (int)c->prm.d_g, (int)c->prm.d_f); });
-        for (size_t p = 0; p < pairs.size(); p++) {
+        for (size_t p = p0; p < p1; p++) {
             const int i = pairs[p].first, j = pairs[p].second;
-            H Cij = range(Cst, (int)p, Bq);
+            H Cij = range(Cst, (int)(p - p0), Bq);
             A[i] = A[i].p ? E.add(A[i], Cij) : E.copy(Cij);
             if (j > i) Bs[j] = Bs[j].p ? E.add(Bs[j], Cij) : E.copy(Cij);
         }
@@ -1112,11 +1140,10 @@ static std::pair<H, H> blocked_ranks_tc(rk_ctx* c, const rk_ct* const* blocks, i
     const int Bsz = (int)blocks[0]->N, Bq = blocks[0]->B, dg = (int)c->prm.d_g, df = (int)c->prm.d_f;
     const uint32_t Dn = scaled ? (uint32_t)(L * Bsz) : 0u;
     const uint32_t rmask = scaled ? RK_MASK_ROW0S : RK_MASK_ROW0;
-    H V(ct_stack(c, blocks, L));
-    auto rc = row_col_forms(E, V);   // stacks of L Bq
+    auto rc = blocked_forms(c, E, blocks, L);   // stacks of L Bq
     std::vector<H> views;
-    std::vector<rk_ct*> dr, dcol, ur, uc;
-    std::map<std::pair<int, int>, int> uidx;
+    std::vector<rk_ct*> dr, dcol;
+    std::vector<std::pair<int, int>> up;
     for (int i = 0; i < L; i++) {
         views.push_back(range(rc.first, i, Bq));
         dr.push_back(views.back().p);
@@ -1124,33 +1151,45 @@ static std::pair<H, H> blocked_ranks_tc(rk_ctx* c, const rk_ct* const* blocks, i
         dcol.push_back(views.back().p);
     }
     for (int i = 0; i < L; i++)
-        for (int j = i + 1; j < L; j++) {
-            uidx[{i, j}] = (int)ur.size();
-            ur.push_back(dr[i]);
-            uc.push_back(dcol[j]);
-        }
+        for (int j = i + 1; j < L; j++) up.push_back({i, j});
     const int per = pair_tiles(c, blocks[0]);
     const int tile = (int)(blocks[0]->Q * Bsz * Bsz);
-    H F = tie_fold(E, packed_apply(c, E, E.sub(stack_of(c, dr), stack_of(c, dcol)), L, Bq, tile, per,
-                                   [&](H x) { return cmp(E, std::move(x), dg, df); }),
-                   RK_MASK_TIE);
-    H G, Gd;
-    if (L > 1) {
-        G = packed_apply(c, E, E.sub(stack_of(c, ur), stack_of(c, uc)), (int)ur.size(), Bq, tile, per,
-                         [&](H x) { return cmp_strict(E, cmp(E, std::move(x), dg, df)); });
-        Gd = E.level_down(G, F->level);
+    // members in chunks that fit the stacking budget (whole packing groups)
+    const size_t chunk = (size_t)std::max(1, stack_chunk(c, rc.second->level) / Bq) * per;
+    std::vector<H> Fparts;
+    std::vector<rk_ct*> fp;
+    for (size_t i0 = 0; i0 < (size_t)L; i0 += chunk) {
+        const size_t i1 = std::min((size_t)L, i0 + chunk);
+        std::vector<rk_ct*> r(dr.begin() + i0, dr.begin() + i1), cl(dcol.begin() + i0, dcol.begin() + i1);
+        Fparts.push_back(tie_fold(E, packed_apply(c, E, E.sub(stack_of(c, r), stack_of(c, cl)), (int)(i1 - i0), Bq, tile, per,
+                                                  [&](H x) { return cmp(E, std::move(x), dg, df); }),
+                                  RK_MASK_TIE));
+        fp.push_back(Fparts.back().p);
     }
-    std::vector<H> A, Bm;
-    for (int i = 0; i < L; i++) {
-        H a = E.copy(range(F, i, Bq));
-        for (int j = i + 1; j < L; j++) a = E.add(a, range(Gd, uidx[{i, j}], Bq));
-        A.push_back(std::move(a));
-        if (i > 0) {
-            H s = E.copy(range(G, uidx[{0, i}], Bq));
-            for (int j = 1; j < i; j++) s = E.add(s, range(G, uidx[{j, i}], Bq));
-            Bm.push_back(E.add_const(E.neg(s), (double)i));
+    H F = Fparts.size() == 1 ? std::move(Fparts[0]) : stack_of(c, fp);
+    Fparts.clear();
+    // A_i = F_i + sum_{j > i} G_ij (at F's level), Bs_i = sum_{j < i} G_ji, in pair order
+    std::vector<H> A(L), Bsum(L);
+    for (int i = 0; i < L; i++) A[i] = E.copy(range(F, i, Bq));
+    for (size_t p0 = 0; p0 < up.size(); p0 += chunk) {
+        const size_t p1 = std::min(up.size(), p0 + chunk);
+        std::vector<rk_ct*> r, cl;
+        for (size_t p = p0; p < p1; p++) {
+            r.push_back(dr[up[p].first]);
+            cl.push_back(dcol[up[p].second]);
+        }
+        H G = packed_apply(c, E, E.sub(stack_of(c, r), stack_of(c, cl)), (int)(p1 - p0), Bq, tile, per,
+                           [&](H x) { return cmp_strict(E, cmp(E, std::move(x), dg, df)); });
+        H Gd = E.level_down(G, F->level);
+        for (size_t p = p0; p < p1; p++) {
+            const int i = up[p].first, j = up[p].second;
+            A[i] = E.add(A[i], range(Gd, (int)(p - p0), Bq));
+            H gji = range(G, (int)(p - p0), Bq);
+            Bsum[j] = Bsum[j].p ? E.add(Bsum[j], gji) : E.copy(gji);
         }
     }
+    std::vector<H> Bm;
+    for (int i = 1; i < L; i++) Bm.push_back(E.add_const(E.neg(Bsum[i]), (double)i));
     std::vector<rk_ct*> ap;
     for (auto& a : A) ap.push_back(a.p);
     H S = stack_of(c, ap);
@@ -1199,8 +1238,21 @@ void circuit_order_stat_blocked(rk_ctx* c, const rk_ct* const* blocks, int L, ui
     check_blocks(c, blocks, L, blocked_rank_tc_depth(c) + cheb_depth((int)co.size()), "blocked order statistic");
     auto rr = blocked_ranks_tc(c, blocks, L, true);
     Ev E{c};
-    H O = packed_apply(c, E, std::move(rr.first), L, blocks[0]->B, (int)(blocks[0]->Q * blocks[0]->N * blocks[0]->N),
-                       pair_tiles(c, blocks[0]), [&](H x) { return cheb_ps(E, E.add_const(x, -(double)k / D), co); });
+    const int Bq = blocks[0]->B, per = pair_tiles(c, blocks[0]);
+    const int T = (int)(blocks[0]->Q * blocks[0]->N * blocks[0]->N);
+    // the L indicators in chunks of whole packing groups that fit the indicator budget
+    const size_t ct_bytes = (size_t)2 * (rr.first->level + 1) * c->n * 8 * Bq;
+    const size_t live = (size_t)baby_steps((int)co.size()) + 2 * (size_t)cheb_depth((int)co.size()) + 8;
+    const int chunk = (int)std::max<size_t>(1, c->ind_stack_bytes / (live * ct_bytes)) * per;
+    std::vector<H> parts;
+    std::vector<rk_ct*> pp;
+    for (int i0 = 0; i0 < L; i0 += chunk) {
+        const int i1 = std::min(L, i0 + chunk);
+        parts.push_back(packed_apply(c, E, H(ct_view_range(rr.first.p, i0 * Bq, (i1 - i0) * Bq)), i1 - i0, Bq, T, per,
+                                     [&](H x) { return cheb_ps(E, E.add_const(x, -(double)k / D), co); }));
+        pp.push_back(parts.back().p);
+    }
+    H O = parts.size() == 1 ? std::move(parts[0]) : stack_of(c, pp);
     split_blocks(c, O, L, outs);
 }
 
@@ -1227,20 +1279,23 @@ void circuit_sort_blocked(rk_ctx* c, const rk_ct* const* blocks, int L, rk_ct** 
         // per output block i, its L indicators packed `per` to a ciphertext: the RR_j
         // (zero outside their tile) packed, the constant -B i / D added to every slot
         const int T = (int)(blocks[0]->Q * Bsz * Bsz);
+        const int jc = std::max(1, chunk) * per;   // whole packing groups a chunk
         for (int i = 0; i < L; i++) {
-            H M = packed_apply(c, E, E.copy(RR), L, Bq, T, per, [&](H x) {
-                return cheb_ps(E, E.add_const(x, -(double)Bsz * i / D), co);
-            });
-            std::vector<H> vr;
-            std::vector<rk_ct*> vp;
-            for (int j = 0; j < L; j++) {
-                vr.push_back(E.level_down(range(rr.second, j, Bq), M->level));
-                vp.push_back(vr.back().p);
-            }
-            H P = E.mul(M, stack_of(c, vp));
-            for (int j = 0; j < L; j++) {
-                H pm = range(P, j, Bq);
-                acc[i] = acc[i].p ? E.add(acc[i], pm) : E.copy(pm);
+            for (int j0 = 0; j0 < L; j0 += jc) {
+                const int j1 = std::min(L, j0 + jc);
+                H M = packed_apply(c, E, E.copy(H(ct_view_range(RR.p, j0 * Bq, (j1 - j0) * Bq))), j1 - j0, Bq, T, per,
+                                   [&](H x) { return cheb_ps(E, E.add_const(x, -(double)Bsz * i / D), co); });
+                std::vector<H> vr;
+                std::vector<rk_ct*> vp;
+                for (int j = j0; j < j1; j++) {
+                    vr.push_back(E.level_down(range(rr.second, j, Bq), M->level));
+                    vp.push_back(vr.back().p);
+                }
+                H P = E.mul(M, stack_of(c, vp));
+                for (int j = j0; j < j1; j++) {
+                    H pm = range(P, j - j0, Bq);
+                    acc[i] = acc[i].p ? E.add(acc[i], pm) : E.copy(pm);
+                }
             }
         }
     }

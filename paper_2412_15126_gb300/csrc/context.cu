@@ -418,6 +418,7 @@ rk_ctx* ctx_lane_create(rk_ctx* parent) {
     c->pair_packing = parent->pair_packing;
     c->ks_group_bytes = parent->ks_group_bytes;
     c->ind_stack_bytes = parent->ind_stack_bytes;
+    c->stack_budget_bytes = parent->stack_budget_bytes;
     c->cmp_coeffs = parent->cmp_coeffs;
     c->encodings = parent->encodings;
     c->indicator = parent->indicator;

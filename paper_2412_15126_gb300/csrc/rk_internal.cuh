@@ -246,6 +246,7 @@ struct rk_ctx {
     bool pair_packing = true;     // blocked circuits: pack block-pair work into free tiles when keys allow
     double ks_group_bytes = 48.0 * (1 << 20);   // lifted digits kept in L2 between the fused kernels
     size_t ind_stack_bytes = (size_t)4 << 30;   // working set of one stacked indicator evaluation
+    size_t stack_budget_bytes = (size_t)16 << 30;   // working set of one stacked step of the blocked circuits
     u64* noalloc_scratch = nullptr;             // device address of the allocation-free rescale's array
     std::vector<double> cmp_coeffs;             // Chebyshev comparator coefficients (computed or imported)
     // plaintext caches: key = (kind, N, Q, n_real, level)

@@ -33,6 +33,7 @@ OPT_KS_FUSED, OPT_KS_GROUP_BYTES, OPT_BLOCK_STACKING = 1, 2, 3
 OPT_TRIM_LEVELS = 4
 OPT_SERVER_LANES = 5
 OPT_PAIR_PACKING = 6
+OPT_STACK_BUDGET, OPT_INDICATOR_BUDGET = 7, 8
 OP_RANK, OP_ORDER_STAT, OP_SORT, OP_RANK_BLOCKED, OP_ORDER_STAT_BLOCKED, OP_SORT_BLOCKED = 1, 2, 3, 4, 5, 6
 
 

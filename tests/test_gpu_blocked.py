@@ -236,3 +236,29 @@ def test_pair_packed_blocked_circuits_bit_exact(ordb_packed):
             ctx.set_option(rankfhe.OPT_PAIR_PACKING, 1)
         for a, b in zip(plain, orc(cts, 1)):
             assert np.array_equal(a.export(), b.c), idx
+
+
+def test_chunked_blocked_circuits_identical(ordb_packed):
+    """Stacking budgets of one byte (every step of the blocked circuits in chunks of
+    one packing group, every indicator group on its own) leave every output block
+    unchanged, bit for bit: rank, tie-corrected rank, order statistic, sort."""
+    from paper_2412_15126_gb300 import rankfhe
+    P, keys, ctx, tiles = ordb_packed
+    v = np.array([0.75, 0.125, 0.5, 0.0, 0.625, 0.25, 0.875, 0.375, 0.3125, 0.5625, 0.1875, 0.9375])
+    _, g = _encrypt_blocks(P, keys, ctx, v, 95)
+    runs = [lambda: ctx.rank_blocked(g), lambda: ctx.rank_blocked(g, rankfhe.TIES_CORRECT),
+            lambda: ctx.order_stat_blocked(g, 5), lambda: ctx.sort_blocked(g)]
+    for packing in (1, 0):
+        ctx.set_option(rankfhe.OPT_PAIR_PACKING, packing)
+        try:
+            full = [[b.export() for b in run()] for run in runs]
+            ctx.set_option(rankfhe.OPT_STACK_BUDGET, 1)
+            ctx.set_option(rankfhe.OPT_INDICATOR_BUDGET, 1)
+            small = [[b.export() for b in run()] for run in runs]
+        finally:
+            ctx.set_option(rankfhe.OPT_STACK_BUDGET, 16 << 30)
+            ctx.set_option(rankfhe.OPT_INDICATOR_BUDGET, 4 << 30)
+            ctx.set_option(rankfhe.OPT_PAIR_PACKING, 1)
+        for a, b in zip(full, small):
+            for x, y in zip(a, b):
+                assert np.array_equal(x, y)
