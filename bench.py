@@ -236,6 +236,77 @@ def blocked_packing_workload(stream, device, reps=1):
         ctx.close()
 
 
+RING17 = dict(log_n=17, n_limbs=44, n_special=3, digit_size=3, log_scale=40, log_q0=60, log_special=61, d_g=5, d_f=2)
+
+
+def blocked_scaling_workload(stream, device, sizes=(512, 2048, 8192, 16384), n17=2048):
+    """Blocked ranks (Alg. 7) of N = 512 .. 16384 uniform values on the 128-element
+    rank's parameter set (n = 2^16, 28 + 3 limbs, blocks of 128, two block pairs a
+    ciphertext), and the blocked argmin and sort (Alg. 4 on the blocked tie-corrected
+    ranks, Alg. 8) of N = 2048 values on a 2048-level grid on an n = 2^17 ring (44 + 3
+    limbs at 2^40, comparator g^5 f^2, blocks of 128, four block pairs a ciphertext,
+    indicator of 16384 coefficients): one run each, CUDA events on the library stream,
+    inputs resident; errors against brute force (mean and max for the ranks of
+    uniform values, where pairs closer than the comparator resolves swap)."""
+    import numpy as np
+    import torch
+    from paper_2412_15126_gb300 import inputs, rankfhe
+    from oracle.circuits import brute_fractional_rank   # brute-force definition only
+
+    def run(fn):
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+            out = fn()
+            ev1.record(stream)
+        ev1.synchronize()
+        return ev0.elapsed_time(ev1), out
+
+    out = {"workload": "blocked rank of N uniform values at n=2^16 28+3 limbs (blocks of 128); blocked argmin "
+                       "and sort of %d grid values at n=2^17 44+3 limbs 2^40, Cmp g^5 f^2" % n17}
+    W = WORKLOAD
+    ctx = rankfhe.Context(W["log_n"], W["n_limbs"], W["n_special"], W["digit_size"], W["log_scale"], W["log_q0"],
+                          W["log_special"], W["d_g"], W["d_f"], device=device, stream=stream.cuda_stream)
+    try:
+        ctx.keygen(7001, 128)
+        ctx.keygen_rotations([ctx.n // 4])       # two block pairs a ciphertext
+        rng = np.random.default_rng(7002)
+        ranks = {}
+        for N in sizes:
+            v = rng.uniform(0, 1, N)
+            blocks = [ctx.encrypt(v[128 * b:128 * (b + 1)], N=128) for b in range(N // 128)]
+            ctx.sync()
+            ms, res = run(lambda: ctx.rank_blocked(blocks))
+            err = np.abs(np.concatenate([ctx.decrypt(r) for r in res]) - brute_fractional_rank(v))
+            ranks[str(N)] = {"s": ms / 1000.0, "mean_rank_error": float(err.mean()), "max_rank_error": float(err.max())}
+            for x in res + blocks:
+                x.free()
+        out["rank_n2^16"] = ranks
+    finally:
+        ctx.close()
+    W = RING17
+    ctx = rankfhe.Context(W["log_n"], W["n_limbs"], W["n_special"], W["digit_size"], W["log_scale"], W["log_q0"],
+                          W["log_special"], W["d_g"], W["d_f"], device=device, stream=stream.cuda_stream)
+    try:
+        ctx.keygen(7003, 128)
+        ctx.keygen_rotations([16384, 32768])     # four block pairs a ciphertext
+        v = inputs.grid_vector(n17, n17, 7004)
+        blocks = [ctx.encrypt(v[128 * b:128 * (b + 1)], N=128) for b in range(n17 // 128)]
+        ctx.sync()
+        ms, res = run(lambda: ctx.order_stat_blocked(blocks, 1))
+        first = np.zeros(n17)
+        first[int(np.argmin(v))] = 1
+        e_min = float(np.max(np.abs(np.concatenate([ctx.decrypt(r) for r in res]) - first)))
+        ms2, res2 = run(lambda: ctx.sort_blocked(blocks))
+        e_sort = float(np.max(np.abs(np.concatenate([ctx.decrypt(r) for r in res2]) - np.sort(v))))
+        out["n2^17_%d" % n17] = {"argmin_s": ms / 1000.0, "argmin_max_error": e_min,
+                                 "sort_s": ms2 / 1000.0, "sort_max_error": e_sort}
+    finally:
+        ctx.close()
+    return out
+
+
 # ---------------------------------------------------------------------------
 # serving: Poisson arrivals of mixed rank / argmin / sort requests
 # ---------------------------------------------------------------------------
@@ -1112,9 +1183,10 @@ def run_cuda(args):
         small = small_rank_workload(stream, local)
         cheb = cheb_comparator_workload(stream, local)
 
-    blocked = None
+    blocked = scaling = None
     if not args.no_order_sort and world == 1:
         blocked = blocked_packing_workload(stream, local)
+        scaling = blocked_scaling_workload(stream, local)
 
     serving = None
     if args.serve and world == 1:
@@ -1163,6 +1235,7 @@ def run_cuda(args):
             "graph": graph, "trimmed_levels": trimmed,
             "order_sort": order_sort,
             "blocked_512": blocked,
+            "blocked_scaling": scaling,
             "rank8": small,
             "cheb_comparator": cheb,
             "serving": serving,

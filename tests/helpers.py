@@ -19,6 +19,8 @@ CONFIGS = {
     "big15": (15, 34, 60, 45, 3, 61, 3, 3, 2),
     # a deeper n = 2^11 ring (test only): order statistics with the division of Sec. 3.2
     "deep": (11, 36, 60, 40, 2, 61, 2, 2, 1),
+    # the n = 2^17 ring of the larger blocked order statistics and sorts, few limbs
+    "ring17": (17, 8, 60, 40, 2, 61, 2, 1, 1),
 }
 
 MASK_IDS = {"row0": 1, "col0": 2, "tie": 3, "tri": 4, "valid": 5, "row0s": 6, "col0s": 7, "tiec": 8, "sortidx": 9,

@@ -31,7 +31,7 @@ def _horner(coeffs, x, q):
     return acc
 
 
-@pytest.mark.parametrize("name", ["small", "cfg1", "cfg2"])
+@pytest.mark.parametrize("name", ["small", "cfg1", "cfg2", "ring17"])
 def test_ntt_forward_inverse(name):
     ctx = helpers.gpu_context(name)
     primes = ctx.moduli()
@@ -58,3 +58,21 @@ def test_ntt_forward_inverse(name):
     ctx.sync()
     assert np.array_equal(dev.cpu().numpy().view(np.uint64), x)
     ctx.close()
+
+
+def test_ring17_rotation_and_product_bit_exact():
+    """n = 2^17 (2^9-point row passes): one rotation and one product equal the
+    oracle's bit for bit."""
+    from oracle import ckks
+    from paper_2412_15126_gb300 import inputs
+    P = helpers.oracle_params("ring17")
+    keys = ckks.keygen(P, 17, helpers.galois_elts(P, [-256]))
+    ctx = helpers.gpu_context("ring17")
+    try:
+        helpers.import_keys(ctx, keys)
+        ct = ckks.encrypt(P, keys, inputs.gap_vector(256, 2.0 ** -9, 17), 17)
+        g = ctx.ct_import(ct.c, ct.level, N=256)
+        assert np.array_equal(ctx.rotate(g, -256).export(), ckks.rotate(P, keys, ct, -256).c)
+        assert np.array_equal(ctx.mul(g, g).export(), ckks.mul(P, keys, ct, ct).c)
+    finally:
+        ctx.close()
