@@ -236,7 +236,7 @@ def blocked_packing_workload(stream, device, reps=1):
         ctx.close()
 
 
-RING17 = dict(log_n=17, n_limbs=44, n_special=3, digit_size=3, log_scale=40, log_q0=60, log_special=61, d_g=5, d_f=2)
+RING17 = dict(log_n=17, n_limbs=44, n_special=3, digit_size=3, log_scale=50, log_q0=60, log_special=61, d_g=5, d_f=2)
 
 
 def blocked_scaling_workload(stream, device, sizes=(512, 2048, 8192, 16384), n17=2048):
@@ -244,10 +244,13 @@ def blocked_scaling_workload(stream, device, sizes=(512, 2048, 8192, 16384), n17
     rank's parameter set (n = 2^16, 28 + 3 limbs, blocks of 128, two block pairs a
     ciphertext), and the blocked argmin and sort (Alg. 4 on the blocked tie-corrected
     ranks, Alg. 8) of N = 2048 values on a 2048-level grid on an n = 2^17 ring (44 + 3
-    limbs at 2^40, comparator g^5 f^2, blocks of 128, four block pairs a ciphertext,
+    limbs at 2^50, comparator g^5 f^2, blocks of 128, four block pairs a ciphertext,
     indicator of 16384 coefficients): one run each, CUDA events on the library stream,
     inputs resident; errors against brute force (mean and max for the ranks of
-    uniform values, where pairs closer than the comparator resolves swap)."""
+    uniform values, where pairs closer than the comparator resolves swap: the noiseless
+    slot model gives the same errors).  The n = 2^17 ring takes the scale 2^50: its
+    16384-coefficient indicator squares its Chebyshev terms 13 times, which multiplies
+    the rescaling noise by about 4^13, too much at 2^40."""
     import numpy as np
     import torch
     from paper_2412_15126_gb300 import inputs, rankfhe
@@ -264,7 +267,7 @@ def blocked_scaling_workload(stream, device, sizes=(512, 2048, 8192, 16384), n17
         return ev0.elapsed_time(ev1), out
 
     out = {"workload": "blocked rank of N uniform values at n=2^16 28+3 limbs (blocks of 128); blocked argmin "
-                       "and sort of %d grid values at n=2^17 44+3 limbs 2^40, Cmp g^5 f^2" % n17}
+                       "and sort of %d grid values at n=2^17 44+3 limbs 2^50, Cmp g^5 f^2" % n17}
     W = WORKLOAD
     ctx = rankfhe.Context(W["log_n"], W["n_limbs"], W["n_special"], W["digit_size"], W["log_scale"], W["log_q0"],
                           W["log_special"], W["d_g"], W["d_f"], device=device, stream=stream.cuda_stream)

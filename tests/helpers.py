@@ -18,7 +18,7 @@ CONFIGS = {
     # workload (not 128-bit secure at n = 2^15: a parity set only)
     "big15": (15, 34, 60, 45, 3, 61, 3, 3, 2),
     # a deeper n = 2^11 ring (test only): order statistics with the division of Sec. 3.2
-    "deep": (11, 36, 60, 40, 2, 61, 2, 2, 1),
+    "deep": (11, 36, 60, 40, 3, 61, 3, 2, 1),
     # the n = 2^17 ring of the larger blocked order statistics and sorts, few limbs
     "ring17": (17, 8, 60, 40, 2, 61, 2, 1, 1),
 }
