@@ -44,13 +44,14 @@ METRIC = "128-elem encrypted rank latency"
 UNIT = "s"
 PAPER_RANK128_S = 5.76   # the paper's 128-element rank, 64 threads on a Xeon 8358 (context)
 WORKLOAD = dict(log_n=16, n_limbs=28, n_special=3, digit_size=3, log_scale=45, log_q0=60, log_special=61,
-                d_g=4, d_f=2, N=128, gap=2.0 ** -9)
+                d_g=4, d_f=2, N=128, gap=2.0 ** -9, prime_form=1)
 
 
 def workload_config(extra=None):
     cfg = {"workload": "rank N=128, n=2^16, 28+3 limbs, scale 2^45, dnum digits of 3, Cmp g^4 f^2",
            "vector_len": WORKLOAD["N"], "ring_degree": 1 << WORKLOAD["log_n"], "limbs": WORKLOAD["n_limbs"],
            "special_primes": WORKLOAD["n_special"], "gap": "2^-9",
+           "primes": "k 2^32 + 1" if WORKLOAD.get("prime_form") else "1 mod 2n",
            "l2": "working set larger than L2 (seeded rotation and relinearisation keys, ~4.4 GB of b parts, read every step)"}
     if extra:
         cfg.update(extra)
@@ -70,7 +71,8 @@ def small_rank_workload(stream, device, reps=20):
     from oracle.circuits import brute_fractional_rank
     W = SMALL_WORKLOAD
     ctx = rankfhe.Context(W["log_n"], W["n_limbs"], W["n_special"], W["digit_size"], W["log_scale"], W["log_q0"],
-                          W["log_special"], W["d_g"], W["d_f"], device=device, stream=stream.cuda_stream)
+                          W["log_special"], W["d_g"], W["d_f"], device=device, stream=stream.cuda_stream,
+                          prime_form=W.get("prime_form", 0))
     try:
         ctx.keygen(808, W["N"])
         vecs = [inputs.gap_vector(W["N"], W["gap"], 900 + i) for i in range(reps + 3)]
@@ -106,7 +108,8 @@ def cheb_comparator_workload(stream, device, depths=(8, 10, 12), reps=3):
     vecs = [rng.uniform(0, 1, W["N"]) for _ in range(reps + 1)]
     for d in depths:
         ctx = rankfhe.Context(W["log_n"], W["n_limbs"], W["n_special"], W["digit_size"], W["log_scale"], W["log_q0"],
-                              W["log_special"], 0, 0, device=device, stream=stream.cuda_stream, cmp_cheb=1 << (d - 1))
+                              W["log_special"], 0, 0, device=device, stream=stream.cuda_stream, cmp_cheb=1 << (d - 1),
+                              prime_form=W.get("prime_form", 0))
         try:
             ctx.keygen(700 + d, W["N"])
             cts = [ctx.encrypt(v, N=W["N"]) for v in vecs]
@@ -128,7 +131,7 @@ def cheb_comparator_workload(stream, device, depths=(8, 10, 12), reps=3):
 
 
 ORDER_WORKLOAD = dict(log_n=16, n_limbs=34, n_special=3, digit_size=3, log_scale=45, log_q0=60, log_special=61,
-                      d_g=3, d_f=2, N=128, levels=64)
+                      d_g=3, d_f=2, N=128, levels=64, prime_form=1)
 
 
 def order_sort_workload(stream, device, reps=3, seed=3):
@@ -142,7 +145,8 @@ def order_sort_workload(stream, device, reps=3, seed=3):
 
     W = ORDER_WORKLOAD
     ctx = rankfhe.Context(W["log_n"], W["n_limbs"], W["n_special"], W["digit_size"], W["log_scale"], W["log_q0"],
-                          W["log_special"], W["d_g"], W["d_f"], device=device, stream=stream.cuda_stream)
+                          W["log_special"], W["d_g"], W["d_f"], device=device, stream=stream.cuda_stream,
+                          prime_form=W.get("prime_form", 0))
     try:
         ctx.keygen(5000 + seed, W["N"])
         vecs = [inputs.grid_vector(W["N"], W["levels"], 100 + seed * 10 + i) for i in range(reps + 1)]
@@ -197,7 +201,8 @@ def blocked_packing_workload(stream, device, reps=1):
     from oracle.circuits import brute_fractional_rank, brute_tie_corrected_rank   # brute-force definitions only
     W = SERVE_SORT
     ctx = rankfhe.Context(W["log_n"], W["n_limbs"], W["n_special"], W["digit_size"], W["log_scale"], W["log_q0"],
-                          W["log_special"], W["d_g"], W["d_f"], device=device, stream=stream.cuda_stream)
+                          W["log_special"], W["d_g"], W["d_f"], device=device, stream=stream.cuda_stream,
+                          prime_form=W.get("prime_form", 0))
     try:
         ctx.keygen(4321, 128)
         ctx.keygen_rotations([ctx.n // 4])
@@ -236,7 +241,8 @@ def blocked_packing_workload(stream, device, reps=1):
         ctx.close()
 
 
-RING17 = dict(log_n=17, n_limbs=44, n_special=3, digit_size=3, log_scale=50, log_q0=60, log_special=61, d_g=5, d_f=2)
+RING17 = dict(log_n=17, n_limbs=44, n_special=3, digit_size=3, log_scale=50, log_q0=60, log_special=61, d_g=5, d_f=2,
+              prime_form=1)
 
 
 def blocked_scaling_workload(stream, device, sizes=(512, 2048, 8192, 16384), n17=2048):
@@ -270,7 +276,8 @@ def blocked_scaling_workload(stream, device, sizes=(512, 2048, 8192, 16384), n17
                        "and sort of %d grid values at n=2^17 44+3 limbs 2^50, Cmp g^5 f^2" % n17}
     W = WORKLOAD
     ctx = rankfhe.Context(W["log_n"], W["n_limbs"], W["n_special"], W["digit_size"], W["log_scale"], W["log_q0"],
-                          W["log_special"], W["d_g"], W["d_f"], device=device, stream=stream.cuda_stream)
+                          W["log_special"], W["d_g"], W["d_f"], device=device, stream=stream.cuda_stream,
+                          prime_form=W.get("prime_form", 0))
     try:
         ctx.keygen(7001, 128)
         ctx.keygen_rotations([ctx.n // 4])       # two block pairs a ciphertext
@@ -290,7 +297,8 @@ def blocked_scaling_workload(stream, device, sizes=(512, 2048, 8192, 16384), n17
         ctx.close()
     W = RING17
     ctx = rankfhe.Context(W["log_n"], W["n_limbs"], W["n_special"], W["digit_size"], W["log_scale"], W["log_q0"],
-                          W["log_special"], W["d_g"], W["d_f"], device=device, stream=stream.cuda_stream)
+                          W["log_special"], W["d_g"], W["d_f"], device=device, stream=stream.cuda_stream,
+                          prime_form=W.get("prime_form", 0))
     try:
         ctx.keygen(7003, 128)
         ctx.keygen_rotations([16384, 32768])     # four block pairs a ciphertext
@@ -313,7 +321,8 @@ def blocked_scaling_workload(stream, device, sizes=(512, 2048, 8192, 16384), n17
 # ---------------------------------------------------------------------------
 # serving: Poisson arrivals of mixed rank / argmin / sort requests
 # ---------------------------------------------------------------------------
-SERVE_RANK = dict(log_n=16, n_limbs=34, n_special=3, digit_size=3, log_scale=45, log_q0=60, log_special=61, d_g=4, d_f=2)
+SERVE_RANK = dict(log_n=16, n_limbs=34, n_special=3, digit_size=3, log_scale=45, log_q0=60, log_special=61, d_g=4, d_f=2,
+                  prime_form=1)
 SERVE_SORT = dict(log_n=16, n_limbs=39, n_special=3, digit_size=3, log_scale=40, log_q0=60, log_special=61, d_g=4, d_f=2)
 SERVE_LANES = 2   # execution lanes of each serving loop
 
@@ -352,7 +361,8 @@ def serving_workload(stream_a, stream_b, device, count=120, rate=20.0):
 
     def make(P, stream):
         return rankfhe.Context(P["log_n"], P["n_limbs"], P["n_special"], P["digit_size"], P["log_scale"], P["log_q0"],
-                               P["log_special"], P["d_g"], P["d_f"], device=device, stream=stream.cuda_stream)
+                               P["log_special"], P["d_g"], P["d_f"], device=device, stream=stream.cuda_stream,
+                               prime_form=P.get("prime_form", 0))
 
     reqs = serving_requests(count, rate)
     ca, cs = make(SERVE_RANK, stream_a), make(SERVE_SORT, stream_b)
@@ -601,6 +611,7 @@ def ntt_roofline(prof, clk, alu=None):
         # the integer multiplier (FMA-heavy) pipe: one busy cycle of each of the 608
         # sub-partitions per clock, hpb busy cycles a butterfly
         mul_peak = GB300_SMS * GB300_SCHEDULERS * GB300_MAX_SM_MHZ * 1e6 / hpb / 1e9
+    # the transforms run the general butterfly for every prime form
     bpeak = alu["butterfly_per_s"] / 1e9 if alu and alu.get("butterfly_per_s") else None
     return {"bound": "alu", "kernel": "ntt_fwd (column + row pass)", "achieved": achieved, "peak": bpeak,
             "peak_kind": "measured: register-resident Cooley-Tukey butterflies a second over every SM "
@@ -728,7 +739,7 @@ def oracle_rank_setup(seed: int = 3):
     from paper_2412_15126_gb300 import inputs
     W = WORKLOAD
     P = ckks.gen_params(W["log_n"], W["n_limbs"], W["log_q0"], W["log_scale"], W["n_special"],
-                        W["log_special"], W["digit_size"])
+                        W["log_special"], W["digit_size"], W.get("prime_form", 0))
     keys = ckks.keygen(P, seed, sorted({ckks.galois_left(r % P.slots, P.n) for r in rank_rotations(W["N"])}))
     v = inputs.gap_vector(W["N"], W["gap"], seed)
     return P, keys, v, ckks.encrypt(P, keys, v, seed)
@@ -768,7 +779,7 @@ def oracle_rank_estimate(steps: int = 1, warmup: int = 0, setup=None):
     W = WORKLOAD
     if setup is None:
         P = ckks.gen_params(W["log_n"], W["n_limbs"], W["log_q0"], W["log_scale"], W["n_special"],
-                            W["log_special"], W["digit_size"])
+                            W["log_special"], W["digit_size"], W.get("prime_form", 0))
         keys = ckks.keygen(P, 3, [ckks.galois_left(P.slots - W["N"], P.n)])
         from paper_2412_15126_gb300 import inputs
         ct = ckks.encrypt(P, keys, inputs.gap_vector(W["N"], W["gap"], 1), 1)
@@ -1017,7 +1028,8 @@ def run_cuda(args):
     W = WORKLOAD
     stream = torch.cuda.Stream()
     ctx = rankfhe.Context(W["log_n"], W["n_limbs"], W["n_special"], W["digit_size"], W["log_scale"], W["log_q0"],
-                          W["log_special"], W["d_g"], W["d_f"], device=local, stream=stream.cuda_stream)
+                          W["log_special"], W["d_g"], W["d_f"], device=local, stream=stream.cuda_stream,
+                          prime_form=W.get("prime_form", 0))
     ctx.keygen(1000 + rank, W["N"])
     tuned = ctx.autotune() if not args.no_autotune else None
     alu = ctx.measure_alu()
@@ -1265,7 +1277,7 @@ def profile_case():
     from paper_2412_15126_gb300 import rankfhe
     W = WORKLOAD
     ctx = rankfhe.Context(W["log_n"], W["n_limbs"], W["n_special"], W["digit_size"], W["log_scale"], W["log_q0"],
-                          W["log_special"], W["d_g"], W["d_f"], device=0)
+                          W["log_special"], W["d_g"], W["d_f"], device=0, prime_form=W.get("prime_form", 0))
     ctx.keygen(5, 2)
     ct = ctx.encrypt(np.linspace(0.0, 0.9, 2), N=2)
     ctx.sync()

@@ -67,6 +67,13 @@ typedef struct {
                               coefficients (a power of two, 4..16384): the interpolant at
                               first-kind nodes on [-1, 1] of the step 1 / 1/2 / 0, odd part
                               plus 1/2, by Paterson-Stockmeyer; depth log2(count) + 1      */
+    uint32_t prime_form;   /* 0: every prime = 1 mod 2n (as above); 1: every prime = 1 mod
+                              2^32, i.e. k 2^32 + 1, by the same rules with 2^32 in place
+                              of 2n (the kernels then multiply by q with one 32-bit
+                              product; results are the same words for the same primes).
+                              Needs log_scale, log_q0, log_special >= 34; at scales near
+                              2^45 the chosen primes lie within a few percent of the
+                              scale and the canonical scales absorb the spread          */
 } rk_params;
 
 /* Ciphertext slot layouts (Sec. 2.3 row-by-row encoding; slot q*N^2 + i*N + j is
@@ -146,6 +153,13 @@ rk_status rk_ctx_counters(const rk_ctx* ctx, uint64_t out[4]);
  *   the L output blocks only.  RK_OPT_INDICATOR_BUDGET: the same for the blocked order
  *   statistic's and sort's indicator evaluations (default 4 GiB).  Results never
  *   depend on either.
+ * RK_OPT_MODUP_COL: 1 runs the staged path's ModUp conversion inside the forward
+ *   NTT's column pass (one kernel, the lifted digits written once, in the pass's
+ *   output form); 0 (default) converts, then transforms.  rk_autotune picks one.
+ *   Results never depend on it.
+ * RK_OPT_NTT_GROUP_BYTES: a forward or inverse NTT of more bytes runs as groups of
+ *   limbs of at most this size, both passes of a group before the next (0: one launch
+ *   pair for the whole set; rk_autotune picks a size).  Results never depend on it.
  * RK_OPT_SERVER_LANES: execution lanes of the next rk_server_start (1 to 16, default 2):
  *   each runs its own batch on its own stream, so batches overlap on the device.
  * RK_OPT_TRIM_LEVELS: 0 (default) evaluates rk_rank / rk_rank_batch at the input's
@@ -164,16 +178,23 @@ rk_status rk_ctx_counters(const rk_ctx* ctx, uint64_t out[4]);
 #define RK_OPT_PAIR_PACKING 6
 #define RK_OPT_STACK_BUDGET 7
 #define RK_OPT_INDICATOR_BUDGET 8
+#define RK_OPT_NTT_GROUP_BYTES 9
+#define RK_OPT_MODUP_COL 10
 rk_status rk_ctx_set_option(rk_ctx* ctx, uint32_t option, int64_t value);
 
 /* Autotune the launch shapes on this device (the paper has no counterpart): times
  * every candidate block width of the four NTT passes for large (224 limbs) and small
- * (2 x 3 limbs) limb sets, and, when a rotation key exists, one top-level rotation
- * with staged and with fused key switching (three L2 group sizes); keeps the fastest
- * of each.  Results never depend on the choice.  report (may be NULL) receives, for
- * the NTT slots [small][inverse][column] in that nesting order, (width, us) pairs,
- * then, with a rotation key, staged us, fused us at 24/48/96 MiB and the choice
- * (0 staged, else the group MiB); *count receives the number of values. */
+ * (2 x 3 limbs) limb sets; the forward NTT of a top-level ModUp set in one launch pair
+ * and in limb groups of at most 96, 64 and 32 MiB (both passes of a group before the
+ * next, so the data between the passes stays in L2); and, when a rotation key exists,
+ * one top-level rotation with staged and with fused key switching (three L2 group
+ * sizes).  Keeps the fastest of each.  Results never depend on the choice.  report
+ * (may be NULL) receives, for the NTT slots [small][inverse][column] in that nesting
+ * order, (width, us) pairs (16 values), then the four group timings in us and the
+ * chosen group MiB (0: whole set), then, with a rotation key, staged us, fused us at
+ * 24/48/96 MiB and the choice (0 staged, else the group MiB), then the staged path
+ * with the ModUp conversion in the column pass (us) and whether it was chosen (1/0);
+ * *count receives the number of values. */
 rk_status rk_autotune(rk_ctx* ctx, double* report, size_t cap, size_t* count);
 
 /* ---- keys ----------------------------------------------------------------- */
@@ -559,9 +580,11 @@ rk_status rk_profile_pause(rk_ctx* ctx, int paused);
  * SM; the best of three timed launches each).  out[0]: 32-bit integer multiply-adds
  * a second; out[1]: 64-bit Shoup modular products a second (x w mod q with a
  * precomputed companion, the NTT's product); out[2]: forward NTT butterflies
- * (Cooley-Tukey, values in [0, 4q)) a second.  Synchronises; takes about a second.
- * Errors: RK_ECUDA. */
-rk_status rk_measure_alu(rk_ctx* ctx, double out[3]);
+ * (Cooley-Tukey, values in [0, 4q)) a second; out[3], out[4]: the Shoup products and
+ * butterflies with a prime k 2^32 + 1 and the cheaper product by such a q (the path
+ * of contexts whose primes all have that form, prime_form 1).  Synchronises; takes
+ * about a second.  Errors: RK_ECUDA. */
+rk_status rk_measure_alu(rk_ctx* ctx, double out[5]);
 /* Device allocations (cudaMalloc and cudaMallocAsync calls) the library has made in
  * this process, over every context. */
 uint64_t rk_device_alloc_count(void);

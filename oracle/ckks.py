@@ -15,6 +15,8 @@ library):
              down, q_l the unused prime = 1 mod 2n nearest floor(Delta_l^2 / 2^logD)
              (ties to the smaller), Delta_L = 2^logD, Delta_{l-1} = Delta_l^2 / q_l;
              specials p_0 > p_1 > ... the largest unused primes < 2^bp, = 1 mod 2n.
+             prime_form 1: the same rules with every "= 1 mod 2n" read "= 1 mod 2^32"
+             (primes k 2^32 + 1; 2n divides 2^32, so they stay NTT-friendly).
   encoding   slot j <-> evaluation at zeta^(5^j), zeta = exp(i pi / n); a plaintext
              at scale s has coefficients rha(s * u_k) where u is the real
              polynomial with those evaluations and rha rounds half away from 0.
@@ -111,9 +113,9 @@ class Params:
 
 
 def gen_params(log_n: int, n_q: int, log_q0: int, log_scale: int, n_special: int,
-               log_special: int, dsize: int) -> Params:
+               log_special: int, dsize: int, prime_form: int = 0) -> Params:
     n = 1 << log_n
-    m = 2 * n
+    m = (1 << 32) if prime_form else 2 * n
     used: set = set()
     q0 = _largest_prime_below(1 << log_q0, m, used)
     used.add(q0)

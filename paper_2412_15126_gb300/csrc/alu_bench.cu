@@ -8,6 +8,8 @@
 //   imad      x <- x a + b, 32-bit (one multiply-add a step)
 //   modmul    x <- x w mod q, Shoup's form with a precomputed companion (the NTT's)
 //   butterfly the forward NTT's Cooley-Tukey butterfly on values in [0, 4q) (Harvey)
+// The last two are also timed with a prime k 2^32 + 1 and the kernels' cheaper
+// product by such a q.
 #include <algorithm>
 
 #include "ntt_core.cuh"
@@ -35,6 +37,7 @@ __global__ void __launch_bounds__(kThreads) k_bench_imad(uint32_t* out, int roun
     out[t] = acc;
 }
 
+template <bool SP>
 __global__ void __launch_bounds__(kThreads) k_bench_modmul(u64* out, int rounds, u64 q, u64 w, u64 wp) {
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     u64 x[kChains];
@@ -42,7 +45,7 @@ __global__ void __launch_bounds__(kThreads) k_bench_modmul(u64* out, int rounds,
     for (int i = 0; i < kChains; i++) x[i] = (u64)t * 2654435761ull + (u64)i;
     for (int r = 0; r < rounds; r++) {
 #pragma unroll
-        for (int i = 0; i < kChains; i++) x[i] = shoup_lazy(x[i], w, wp, q);
+        for (int i = 0; i < kChains; i++) x[i] = shoup_lazy_t<SP>(x[i], w, wp, q);
     }
     u64 acc = 0;
 #pragma unroll
@@ -50,6 +53,7 @@ __global__ void __launch_bounds__(kThreads) k_bench_modmul(u64* out, int rounds,
     out[t] = acc;
 }
 
+template <bool SP>
 __global__ void __launch_bounds__(kThreads) k_bench_butterfly(u64* out, int rounds, u64 q, u64 w, u64 wp) {
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     constexpr int P = kChains / 2;   // pairs a thread
@@ -62,7 +66,7 @@ __global__ void __launch_bounds__(kThreads) k_bench_butterfly(u64* out, int roun
     }
     for (int r = 0; r < rounds; r++) {
 #pragma unroll
-        for (int i = 0; i < P; i++) nttc::ct_bfly(a[i], b[i], w, wp, q, q2);
+        for (int i = 0; i < P; i++) nttc::ct_bfly<SP>(a[i], b[i], w, wp, q, q2);
     }
     u64 acc = 0;
 #pragma unroll
@@ -73,10 +77,11 @@ __global__ void __launch_bounds__(kThreads) k_bench_butterfly(u64* out, int roun
 }  // namespace
 
 // out[0]: 32-bit multiply-adds a second, out[1]: Shoup modular products a second,
-// out[2]: forward NTT butterflies a second (each the best of three timed launches,
-// CUDA events on the context stream).  Grids of `per_sm` blocks of 256 threads on
-// every SM, 4 and 8 blocks tried.
-void measure_alu(rk_ctx* c, double out[3]) {
+// out[2]: forward NTT butterflies a second, out[3], out[4]: the same two with the
+// prime k 2^32 + 1 form (each the best of three timed launches, CUDA events on the
+// context stream).  Grids of `per_sm` blocks of 256 threads on every SM, 4 and 8
+// blocks tried.
+void measure_alu(rk_ctx* c, double out[5]) {
     const int sms = c->env.sms;
     const size_t max_threads = (size_t)sms * 8 * kThreads;
     u64* buf = nullptr;
@@ -84,23 +89,29 @@ void measure_alu(rk_ctx* c, double out[3]) {
     cudaEvent_t e0, e1;
     RK_CUDA(cudaEventCreate(&e0));
     RK_CUDA(cudaEventCreate(&e1));
-    const u64 q = c->primes[0];                    // a prime of the chain (below 2^61)
-    const u64 w = 0x1234567ull % q, wp = (u64)(((u128)w << 64) / q);
-    out[0] = out[1] = out[2] = 0.0;
+    const u64 qg = c->primes[0];                   // a prime of the chain (below 2^61)
+    const u64 qs = (8185ull << 32) + 1;            // a prime k 2^32 + 1 (k = 8185) near 2^45
+    for (int i = 0; i < 5; i++) out[i] = 0.0;
     try {
-        for (int kind = 0; kind < 3; kind++) {
+        for (int kind = 0; kind < 5; kind++) {
+            const u64 q = kind >= 3 ? qs : qg;
+            const u64 w = 0x1234567ull % q, wp = (u64)(((u128)w << 64) / q);
             const int rounds = kind == 0 ? 1 << 16 : 1 << 12;
             for (int per_sm : {4, 8}) {
                 const int blocks = sms * per_sm;
-                const double ops = (double)blocks * kThreads * rounds * (kind == 2 ? kChains / 2 : kChains);
+                const double ops = (double)blocks * kThreads * rounds * (kind == 2 || kind == 4 ? kChains / 2 : kChains);
                 for (int rep = 0; rep < 4; rep++) {   // the first launch warms up
                     RK_CUDA(cudaEventRecord(e0, c->stream));
                     if (kind == 0)
                         k_bench_imad<<<blocks, kThreads, 0, c->stream>>>((uint32_t*)buf, rounds, 0x9E3779B9u);
                     else if (kind == 1)
-                        k_bench_modmul<<<blocks, kThreads, 0, c->stream>>>(buf, rounds, q, w, wp);
+                        k_bench_modmul<false><<<blocks, kThreads, 0, c->stream>>>(buf, rounds, q, w, wp);
+                    else if (kind == 2)
+                        k_bench_butterfly<false><<<blocks, kThreads, 0, c->stream>>>(buf, rounds, q, w, wp);
+                    else if (kind == 3)
+                        k_bench_modmul<true><<<blocks, kThreads, 0, c->stream>>>(buf, rounds, q, w, wp);
                     else
-                        k_bench_butterfly<<<blocks, kThreads, 0, c->stream>>>(buf, rounds, q, w, wp);
+                        k_bench_butterfly<true><<<blocks, kThreads, 0, c->stream>>>(buf, rounds, q, w, wp);
                     RK_CUDA(cudaGetLastError());
                     RK_CUDA(cudaEventRecord(e1, c->stream));
                     RK_CUDA(cudaEventSynchronize(e1));

@@ -37,7 +37,7 @@ rk_ct* graph_rank_run(rk_graph* g, const rk_ct* in);
 void graph_free(rk_graph* g);
 rk_ctx* graph_context(const rk_graph* g);
 void circuit_rotations(uint32_t N, std::vector<int>& out);
-void measure_alu(rk_ctx* c, double out[3]);
+void measure_alu(rk_ctx* c, double out[5]);
 
 namespace {
 thread_local std::string g_last_error;
@@ -193,6 +193,11 @@ rk_status rk_ctx_set_option(rk_ctx* ctx, uint32_t option, int64_t value) {
                 RK_REQUIRE(value >= 1, RK_EINVAL, "indicator budget must be positive");
                 ctx->ind_stack_bytes = (size_t)value;
                 break;
+            case RK_OPT_MODUP_COL: ctx->modup_col = value != 0; break;
+            case RK_OPT_NTT_GROUP_BYTES:
+                RK_REQUIRE(value >= 0, RK_EINVAL, "NTT group bytes must not be negative");
+                ctx->tune.ntt_group_bytes = (size_t)value;
+                break;
             case RK_OPT_SERVER_LANES:
                 RK_REQUIRE(value >= 1 && value <= 16, RK_EINVAL, "server lanes must be 1 to 16");
                 ctx->server_lanes = (int)value;
@@ -294,7 +299,7 @@ rk_status rk_encoding_import(rk_ctx* ctx, uint32_t kind, uint32_t N, uint32_t Q,
 
 uint64_t rk_device_alloc_count(void) { return rk_alloc_counted(); }
 
-rk_status rk_measure_alu(rk_ctx* ctx, double out[3]) {
+rk_status rk_measure_alu(rk_ctx* ctx, double out[5]) {
     return guard([&] {
         need(ctx, "ctx");
         need(out, "out");

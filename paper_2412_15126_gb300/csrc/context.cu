@@ -139,6 +139,9 @@ static void validate(const rk_params* p) {
     RK_REQUIRE(p->log_scale >= 20 && p->log_scale <= 58, RK_EINVAL, "log_scale must be in [20, 58]");
     RK_REQUIRE(p->log_q0 >= 20 && p->log_q0 <= 61, RK_EINVAL, "log_q0 must be in [20, 61]");
     RK_REQUIRE(p->log_special >= 20 && p->log_special <= 61, RK_EINVAL, "log_special must be in [20, 61]");
+    RK_REQUIRE(p->prime_form <= 1, RK_EINVAL, "prime_form must be 0 or 1");
+    RK_REQUIRE(p->prime_form == 0 || (p->log_scale >= 34 && p->log_q0 >= 34 && p->log_special >= 34), RK_EINVAL,
+               "prime_form 1 (primes k 2^32 + 1) needs log_scale, log_q0 and log_special of at least 34");
 }
 
 void ctx_build(rk_ctx* c, const rk_params* p, int device, void* stream) {
@@ -166,11 +169,13 @@ void ctx_build(rk_ctx* c, const rk_params* p, int device, void* stream) {
     c->dsize = (int)p->digit_size;
     c->n_primes = c->L + 1 + c->alpha;
     const u64 m = 2ull * (u64)c->n;
+    // candidate step: primes = 1 mod 2n, or (prime_form 1) = 1 mod 2^32, which 2n divides
+    const u64 step = p->prime_form ? (1ull << 32) : m;
 
     // ---- prime chain and canonical scales ----
     std::vector<u64> used;
     std::vector<u64> q(c->L + 1);
-    q[0] = largest_prime_below(1ull << p->log_q0, m, used);
+    q[0] = largest_prime_below(1ull << p->log_q0, step, used);
     used.push_back(q[0]);
     std::vector<double> sc(c->L + 1);
     const double two_ls = std::ldexp(1.0, (int)p->log_scale);
@@ -178,7 +183,7 @@ void ctx_build(rk_ctx* c, const rk_params* p, int device, void* stream) {
     for (int l = c->L; l >= 1; l--) {
         volatile double t = sc[l] * sc[l];
         double target = t / two_ls;
-        u64 ql = nearest_prime((u64)std::floor(target), m, used);
+        u64 ql = nearest_prime((u64)std::floor(target), step, used);
         used.push_back(ql);
         q[l] = ql;
         volatile double sq = sc[l] * sc[l];
@@ -187,7 +192,7 @@ void ctx_build(rk_ctx* c, const rk_params* p, int device, void* stream) {
     std::vector<u64> sp;
     u64 bound = 1ull << p->log_special;
     for (int k = 0; k < c->alpha; k++) {
-        u64 pk = largest_prime_below(bound, m, used);
+        u64 pk = largest_prime_below(bound, step, used);
         used.push_back(pk);
         sp.push_back(pk);
         bound = pk;
@@ -361,6 +366,8 @@ void ctx_build(rk_ctx* c, const rk_params* p, int device, void* stream) {
     e.L = L;
     e.alpha = A;
     e.pc = c->d_pc;
+    e.sp = true;
+    for (u64 x : c->primes) e.sp = e.sp && is_k32_prime(x);
     e.tw.psi = c->d_tw;
     e.tw.ipsi = c->d_tw + (size_t)2 * NP * n;
     e.conv.modup = c->d_conv + mu_off;
@@ -413,6 +420,7 @@ rk_ctx* ctx_lane_create(rk_ctx* parent) {
     c->seed = parent->seed;
     c->tune = parent->tune;
     c->ks_fused = parent->ks_fused;
+    c->modup_col = parent->modup_col;
     c->stack_blocks = parent->stack_blocks;
     c->trim_levels = parent->trim_levels;
     c->pair_packing = parent->pair_packing;

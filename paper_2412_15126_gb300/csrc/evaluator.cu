@@ -403,10 +403,15 @@ static void ks_lift_ext(rk_ctx* c, const u64* d_eval, size_t d_stride, int l, in
     Scratch S = scratch_layout(c);
     const size_t n = c->n;
     const int QP = l + 1 + c->alpha;
-    launch_modup(c->env, S.coef, d_eval, d_stride, S.ext, (size_t)QP * n, l, c->beta(l), c->stream, B);
     LimbSet ext{S.ext, (size_t)QP * n, B * c->beta(l), QP, l + 1, 0, c->L + 1};
     ext.skip_ds = c->dsize;   // each digit's own limbs are already in the evaluation domain
     ext.skip_beta = c->beta(l);
+    if (c->modup_col) {   // conversion fused into the column pass, then the row pass
+        launch_modup_col(c->env, S.coef, S.ext, (size_t)QP * n, l, c->beta(l), 0, QP, c->stream, B, d_eval, d_stride);
+        launch_ntt_forward_rows(c->env, ext, c->stream);
+        return;
+    }
+    launch_modup(c->env, S.coef, d_eval, d_stride, S.ext, (size_t)QP * n, l, c->beta(l), c->stream, B);
     launch_ntt_forward(c->env, ext, c->stream);
 }
 
@@ -737,11 +742,12 @@ void ks_autotune(rk_ctx* c, std::vector<double>& report) {
     cudaEvent_t e0, e1;
     RK_CUDA(cudaEventCreate(&e0));
     RK_CUDA(cudaEventCreate(&e1));
-    const bool fused0 = c->ks_fused;
+    const bool fused0 = c->ks_fused, modup_col0 = c->modup_col;
     const double group0 = c->ks_group_bytes;
-    auto time_rot = [&](bool fused, double group) {
+    auto time_rot = [&](bool fused, double group, bool modup_col = false) {
         c->ks_fused = fused;
         c->ks_group_bytes = group;
+        c->modup_col = modup_col;
         rk_ct* outs[1] = {y};
         ev_rotate_many(c, x, &r, 1, outs);   // warm
         RK_CUDA(cudaEventRecord(e0, c->stream));
@@ -765,19 +771,26 @@ void ks_autotune(rk_ctx* c, std::vector<double>& report) {
             }
         }
         report.push_back(choice);
+        // the staged path with the ModUp conversion fused into the column pass
+        const double t_mc = time_rot(false, group0, true);
+        const bool mc = choice == 0 && t_mc < best;
+        report.push_back(t_mc);
+        report.push_back(mc ? 1.0 : 0.0);
         c->ks_fused = choice > 0;
         c->ks_group_bytes = choice > 0 ? choice * mib : group0;
+        c->modup_col = mc;
     } catch (...) {
         c->ks_fused = fused0;
         c->ks_group_bytes = group0;
+        c->modup_col = modup_col0;
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         ct_free(x);
         ct_free(y);
         throw;
     }
-    c->n_ks -= 16;   // the timing rotations are not the caller's
-    c->n_rot -= 16;
+    c->n_ks -= 20;   // the timing rotations are not the caller's
+    c->n_rot -= 20;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     ct_free(x);

@@ -125,6 +125,7 @@ void launch_lincomb(const KernelEnv& env, u64* out, const LincombArg& a, int ter
 
 // d = [d0 | d1 | d2] each [limbs][n]: d0 = x0 y0, d1 = x0 y1 + x1 y0, d2 = x1 y1
 // one ciphertext pair per blockIdx.z (stacked layout [B][2][L+1][n]); d is [B][3][limbs][n]
+template <bool SP>
 __global__ void k_tensor(u64* d, const u64* x, const u64* y, int limbs, int n, size_t ps, const PrimeConst* __restrict__ pc) {
     RK_KERNEL_PROLOGUE();
     const int k = 2 * (blockIdx.x * TPB + threadIdx.x), t = blockIdx.y, b = blockIdx.z;
@@ -143,9 +144,9 @@ __global__ void k_tensor(u64* d, const u64* x, const u64* y, int limbs, int n, s
         Acc128 a1;
         a1.mac(x0, y1);
         a1.mac(x1, y0);
-        r[0][e] = shoup_mul(mont_mul(x0, y0, P.q, P.qinv), P.r_mod, P.r_shoup, P.q);
-        r[1][e] = shoup_mul(a1.redc(P.q, P.qinv), P.r_mod, P.r_shoup, P.q);
-        r[2][e] = shoup_mul(mont_mul(x1, y1, P.q, P.qinv), P.r_mod, P.r_shoup, P.q);
+        r[0][e] = shoup_mul(mont_mul_t<SP>(x0, y0, P.q, P.qinv), P.r_mod, P.r_shoup, P.q);
+        r[1][e] = shoup_mul(a1.template redc_t<SP>(P.q, P.qinv), P.r_mod, P.r_shoup, P.q);
+        r[2][e] = shoup_mul(mont_mul_t<SP>(x1, y1, P.q, P.qinv), P.r_mod, P.r_shoup, P.q);
     }
     st2(d + off, r[0][0], r[0][1]);
     st2(d + pl + off, r[1][0], r[1][1]);
@@ -154,7 +155,10 @@ __global__ void k_tensor(u64* d, const u64* x, const u64* y, int limbs, int n, s
 
 void launch_tensor(const KernelEnv& env, u64* d, const u64* x, const u64* y, int limbs, size_t ps, cudaStream_t st, int B) {
     ProfScope pf(env, KK_TENSOR, st, 1, 7.0 * B * limbs * 8.0 * env.n, 4.0 * B * limbs * env.n);
-    rk_launch(k_tensor, grid2(env, limbs, B), TPB, 0, st, d, x, y, limbs, env.n, ps, env.pc);
+    if (env.sp)
+        rk_launch(k_tensor<true>, grid2(env, limbs, B), TPB, 0, st, d, x, y, limbs, env.n, ps, env.pc);
+    else
+        rk_launch(k_tensor<false>, grid2(env, limbs, B), TPB, 0, st, d, x, y, limbs, env.n, ps, env.pc);
 }
 
 // ===========================================================================
@@ -166,7 +170,7 @@ void launch_tensor(const KernelEnv& env, u64* d, const u64* x, const u64* y, int
 // Each thread converts CONV_EL coefficients (k0 + e TPB) so that every conversion
 // constant, staged in shared memory, serves CONV_EL products.
 #define CONV_EL 4
-template <int DS>
+template <int DS, bool SP>
 __global__ void __launch_bounds__(TPB) k_modup(const u64* __restrict__ x, const u64* __restrict__ x_eval, u64* __restrict__ ext,
                                                size_t ext_stride, int level, int L, int alpha, ConvTables cv, int n,
                                                const PrimeConst* __restrict__ pc) {
@@ -218,7 +222,7 @@ __global__ void __launch_bounds__(TPB) k_modup(const u64* __restrict__ x, const 
         }
         const u64 q = s_q[t], qinv = s_qinv[t];
 #pragma unroll
-        for (int e = 0; e < CONV_EL; e++) out[e * TPB] = acc[e].redc(q, qinv);
+        for (int e = 0; e < CONV_EL; e++) out[e * TPB] = acc[e].template redc_t<SP>(q, qinv);
     }
 }
 
@@ -236,7 +240,12 @@ void launch_modup(const KernelEnv& env, const u64* x, const u64* x_eval, size_t 
         switch (env.conv.dsize) {
 #define RK_MODUP_CASE(D)                                                                                                 \
     case D:                                                                                                              \
-        rk_launch(k_modup<D>, g, TPB, 0, st, xb, eb, ob, ext_stride, level, env.L, env.alpha, env.conv, env.n, env.pc);        \
+        if (env.sp)                                                                                                      \
+            rk_launch(k_modup<D, true>, g, TPB, 0, st, xb, eb, ob, ext_stride, level, env.L, env.alpha, env.conv, env.n,  \
+                      env.pc);                                                                                           \
+        else                                                                                                             \
+            rk_launch(k_modup<D, false>, g, TPB, 0, st, xb, eb, ob, ext_stride, level, env.L, env.alpha, env.conv, env.n, \
+                      env.pc);                                                                                           \
         break;
             RK_MODUP_CASE(1) RK_MODUP_CASE(2) RK_MODUP_CASE(3) RK_MODUP_CASE(4)
             RK_MODUP_CASE(5) RK_MODUP_CASE(6) RK_MODUP_CASE(7) RK_MODUP_CASE(8)
@@ -254,7 +263,7 @@ void launch_modup(const KernelEnv& env, const u64* x, const u64* x_eval, size_t 
 // multiple of S is decided by one rounding, v = floor(sum_k y_k (1/s_k) + 1/2) in
 // IEEE double (products and sums rounded to nearest in source order), so that w is the
 // centred residue of u mod S and the product is round(u / S).
-template <int A, bool RS>
+template <int A, bool RS, bool SP>
 __global__ void __launch_bounds__(TPB) k_moddown_conv(const u64* __restrict__ u, u64* __restrict__ w, int level, int L,
                                                       ConvTables cv, int n, const PrimeConst* __restrict__ pc) {
     RK_KERNEL_PROLOGUE();
@@ -318,7 +327,7 @@ __global__ void __launch_bounds__(TPB) k_moddown_conv(const u64* __restrict__ u,
         }
 #pragma unroll
         for (int e = 0; e < CONV_EL; e++) {
-            u64 r = acc[e].redc(q, qinv);
+            u64 r = acc[e].template redc_t<SP>(q, qinv);
             for (int z = 0; z < nneg[e]; z++) r = sub_mod(r, pm, q);
             out[(size_t)i * n + e * TPB] = r;
         }
@@ -333,7 +342,10 @@ static void moddown_conv_launch(const KernelEnv& env, const u64* u, u64* w, int 
     switch (env.alpha) {
 #define RK_MD_CASE(A)                                                                               \
     case A:                                                                                         \
-        rk_launch(k_moddown_conv<A, RS>, g, TPB, 0, st, u, w, level, env.L, env.conv, env.n, env.pc);      \
+        if (env.sp)                                                                                 \
+            rk_launch(k_moddown_conv<A, RS, true>, g, TPB, 0, st, u, w, level, env.L, env.conv, env.n, env.pc);  \
+        else                                                                                        \
+            rk_launch(k_moddown_conv<A, RS, false>, g, TPB, 0, st, u, w, level, env.L, env.conv, env.n, env.pc); \
         break;
         RK_MD_CASE(1) RK_MD_CASE(2) RK_MD_CASE(3) RK_MD_CASE(4) RK_MD_CASE(5) RK_MD_CASE(6) RK_MD_CASE(7) RK_MD_CASE(8)
 #undef RK_MD_CASE
@@ -408,7 +420,7 @@ void launch_ks_combine_rs(const KernelEnv& env, u64* out, size_t ps, const u64* 
 // hides the key stream), so a single ciphertext keeps two accumulators and the digit
 // loop stays unrolled.
 // SEEDED: the key holds b_j only and a_j is regenerated from the key's seed.
-template <int CH, bool SEEDED>
+template <int CH, bool SEEDED, bool SP>
 __global__ void __launch_bounds__(TPB, (CH == 1 ? 6 : (CH == 2 ? 4 : 3))) k_ks_inner(const u64* __restrict__ ext, size_t ext_stride, const u64* __restrict__ key,
                                                   u64 seed, u64* __restrict__ u, int level, int L, int alpha, int beta, u64 galois,
                                                   int logn, int B, int accumulate, const PrimeConst* __restrict__ pc) {
@@ -431,7 +443,7 @@ __global__ void __launch_bounds__(TPB, (CH == 1 ? 6 : (CH == 2 ? 4 : 3))) k_ks_i
 #pragma unroll 4
     for (int j = 0; j < beta; j++) {
         const u64 kb = __ldg(kj);
-        const u64 ka = SEEDED ? seeded_key_word(state, P.q) : __ldg(kj + KL);
+        const u64 ka = SEEDED ? seeded_key_word_t<SP>(state, P.q) : __ldg(kj + KL);
 #pragma unroll
         for (int b = 0; b < CH; b++) {
             if (CH == 1 || b < nb) {
@@ -449,7 +461,7 @@ __global__ void __launch_bounds__(TPB, (CH == 1 ? 6 : (CH == 2 ? 4 : 3))) k_ks_i
     for (int b = 0; b < CH; b++) {
         if (CH == 1 || b < nb) {
             u64* ub = u + (size_t)(b0 + b) * 2 * ul * n;
-            u64 r0 = a0[b].redc(P.q, P.qinv), r1 = a1[b].redc(P.q, P.qinv);
+            u64 r0 = a0[b].template redc_t<SP>(P.q, P.qinv), r1 = a1[b].template redc_t<SP>(P.q, P.qinv);
             if (accumulate) {   // a further rotation's products added to the sum held in u
                 r0 = add_mod(r0, ub[(size_t)t * n + k], P.q);
                 r1 = add_mod(r1, ub[(size_t)ul * n + (size_t)t * n + k], P.q);
@@ -472,9 +484,15 @@ void launch_ks_inner(const KernelEnv& env, const u64* ext, size_t ext_stride, Ke
                  ((double)B * beta + key_parts * beta * chunks + (accumulate ? 4.0 : 2.0) * B) * QP * 8.0 * env.n,
                  2.0 * B * beta * QP * env.n);
     dim3 g(env.n / TPB, level + 1 + env.alpha, chunks);
-#define RK_KSI(C, SD)                                                                                                \
-    rk_launch(k_ks_inner<C, SD>, g, TPB, 0, st, ext, ext_stride, key.data, key.seed, u, level, env.L, env.alpha, beta, \
-              galois, env.logn, B, accumulate ? 1 : 0, env.pc)
+#define RK_KSI(C, SD)                                                                                                     \
+    do {                                                                                                                    \
+        if (env.sp)                                                                                                         \
+            rk_launch(k_ks_inner<C, SD, true>, g, TPB, 0, st, ext, ext_stride, key.data, key.seed, u, level, env.L,          \
+                      env.alpha, beta, galois, env.logn, B, accumulate ? 1 : 0, env.pc);                                    \
+        else                                                                                                                \
+            rk_launch(k_ks_inner<C, SD, false>, g, TPB, 0, st, ext, ext_stride, key.data, key.seed, u, level, env.L,         \
+                      env.alpha, beta, galois, env.logn, B, accumulate ? 1 : 0, env.pc);                                    \
+    } while (0)
     if (key.seeded) {
         switch (ch) {
             case 1: RK_KSI(1, true); break;

@@ -118,7 +118,9 @@ void launch_ks_combine(const KernelEnv& env, u64* out, size_t ps, const u64* bas
 // fused key switching (ks_fused.cu)
 void ks_fused_init_attributes();
 void launch_modup_col(const KernelEnv& env, const u64* coef, u64* ext, size_t ext_stride, int level, int beta, int t0, int limbs,
-                      cudaStream_t st, int B = 1);
+                      cudaStream_t st, int B = 1, const u64* x_eval = nullptr, size_t eval_stride = 0);
+// the row pass of a forward NTT whose column pass ran elsewhere (k_modup_col)
+void launch_ntt_forward_rows(const KernelEnv& env, const LimbSet& s, cudaStream_t st);
 void launch_ks_row(const KernelEnv& env, const u64* ext, size_t ext_stride, const u64* x_eval, size_t eval_stride, KeyRef key,
                    u64* u, int level, int beta, int t0, int limbs, u64 galois, cudaStream_t st, int B = 1);
 void launch_moddown_col(const KernelEnv& env, const u64* u, u64* w, int level, cudaStream_t st, int polys = 2);

@@ -28,10 +28,14 @@ namespace {
 // ModUp conversion of digit j into target limb tt fused with the forward column
 // pass.  coef: [B][l+1][n] (coefficient domain); ext: digit j of stack member b at
 // ext + (b * beta + j) * ext_stride, limb tt at + tt * n; column-pass output in [0, 4q).
+// x_eval (may be null): the input in the evaluation domain (member b at
+// x_eval + b * eval_stride); the blocks of a digit's own limbs then copy those limbs
+// into ext (the staged path's row pass skips them).
 // grid (2^b / units, limbs of the group, B * beta), block P * units
 // ---------------------------------------------------------------------------
-template <int LOG>
+template <int LOG, bool SP>
 __global__ void __launch_bounds__(256) k_modup_col(const u64* __restrict__ coef, u64* __restrict__ ext, size_t ext_stride,
+                                                   const u64* __restrict__ x_eval, size_t eval_stride,
                                                    int level, int L, int alpha, int beta, int t0, ConvTables cv, int logn,
                                                    int loga, int units, const PrimeConst* __restrict__ pc,
                                                    const u64* __restrict__ tw) {
@@ -44,7 +48,16 @@ __global__ void __launch_bounds__(256) k_modup_col(const u64* __restrict__ coef,
     const int tt = t0 + blockIdx.y;
     const int j = blockIdx.z % beta, b = blockIdx.z / beta;
     const int DS = cv.dsize, lo = j * DS, hi = min(lo + DS, level + 1), ns = hi - lo;
-    if (tt >= lo && tt < hi) return;   // block-uniform: the digit's own limb
+    if (tt >= lo && tt < hi) {   // block-uniform: the digit's own limb
+        if (x_eval) {
+            const int u = threadIdx.x % units, t = threadIdx.x / units, col = blockIdx.x * units + u;
+            const u64* src = x_eval + (size_t)b * eval_stride + (size_t)tt * n + col;
+            u64* dst = ext + ((size_t)b * beta + j) * ext_stride + (size_t)tt * n + col;
+#pragma unroll
+            for (int m = 0; m < E; m++) dst[(size_t)(t + P * m) * Bw] = src[(size_t)(t + P * m) * Bw];
+        }
+        return;
+    }
     const int pid = tt <= level ? tt : L + 1 + (tt - level - 1);
     const PrimeConst PC = pc[pid];
     const u64 q = PC.q, q2 = 2 * q;
@@ -73,7 +86,7 @@ __global__ void __launch_bounds__(256) k_modup_col(const u64* __restrict__ coef,
                 acc.mac(y, cst[3 * RK_MAX_DIGIT + i]);
             }
         }
-        x[m] = acc.redc(q, PC.qinv);
+        x[m] = acc.template redc_t<SP>(q, PC.qinv);
     }
     const Twid tw_{tw + (size_t)pid * 2 * n, loga - 1, 0};
     fwd_strided<LOG>(x, t, tw_, q, q2);
@@ -326,7 +339,8 @@ Geom geom_of(int LOG, int count) {
 void ks_fused_init_attributes() {
     const int bytes = 96 * 1024;
 #define RK_ATTR(LG)                                                                                        \
-    cudaFuncSetAttribute(k_modup_col<LG>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);             \
+    cudaFuncSetAttribute(k_modup_col<LG, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);      \
+    cudaFuncSetAttribute(k_modup_col<LG, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);       \
     cudaFuncSetAttribute(k_ks_row<LG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * bytes);            \
     cudaFuncSetAttribute(k_moddown_col<LG>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);           \
     cudaFuncSetAttribute(k_moddown_row<LG>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
@@ -335,7 +349,7 @@ void ks_fused_init_attributes() {
 }
 
 void launch_modup_col(const KernelEnv& env, const u64* coef, u64* ext, size_t ext_stride, int level, int beta, int t0, int limbs,
-                      cudaStream_t st, int B) {
+                      cudaStream_t st, int B, const u64* x_eval, size_t eval_stride) {
     if (limbs <= 0) return;
     const int logn = env.logn, loga = logn / 2, logb = logn - loga;
     // algorithmic bytes: the digits read once, every lifted limb of the group written
@@ -345,8 +359,14 @@ void launch_modup_col(const KernelEnv& env, const u64* coef, u64* ext, size_t ex
     const Geom g = geom_of(loga, 1 << logb);
     const dim3 grid(g.blocks, limbs, B * beta);
     const size_t smem = (size_t)(1 << loga) * g.units * 8;
-    RK_LOG_SWITCH(loga, (rk_launch(k_modup_col<LG>, grid, g.threads, smem, st, coef, ext, ext_stride, level, env.L, env.alpha, beta, t0,
-                                                                        env.conv, logn, loga, g.units, env.pc, env.tw.psi)));
+    if (env.sp)
+        RK_LOG_SWITCH(loga, (rk_launch(k_modup_col<LG, true>, grid, g.threads, smem, st, coef, ext, ext_stride, x_eval,
+                                       eval_stride, level, env.L, env.alpha, beta, t0, env.conv, logn, loga, g.units, env.pc,
+                                       env.tw.psi)))
+    else
+        RK_LOG_SWITCH(loga, (rk_launch(k_modup_col<LG, false>, grid, g.threads, smem, st, coef, ext, ext_stride, x_eval,
+                                       eval_stride, level, env.L, env.alpha, beta, t0, env.conv, logn, loga, g.units, env.pc,
+                                       env.tw.psi)))
 }
 
 void launch_ks_row(const KernelEnv& env, const u64* ext, size_t ext_stride, const u64* x_eval, size_t eval_stride, KeyRef key,

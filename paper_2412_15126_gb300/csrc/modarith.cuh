@@ -48,6 +48,56 @@ RK_HD u64 mont_redc(u64 lo, u64 hi, u64 q, u64 qinv) {
     u64 t = hi - mh;
     return hi < mh ? t + q : t;
 }
+
+// ---------------------------------------------------------------------------
+// Primes of the form q = k 2^32 + 1 (k < 2^29, so q < 2^61).  Products by q then
+// need one 32-bit multiply where a general q needs three (low word) or four (high
+// word):
+//   x q mod 2^64          = x + ((x mod 2^32) k mod 2^32) 2^32
+//   floor(m q / 2^64)     = mh k + floor((ml k + mh) / 2^32),  m = mh 2^32 + ml
+//   q^-1 mod 2^64         = 1 - k 2^32            (since (1 + k 2^32)(1 - k 2^32) = 1 - k^2 2^64)
+// The results are the same words as the general forms above, bit for bit.  The key-
+// switching kernels take the Montgomery reductions and the seeded key word in this
+// form; Shoup's product keeps the general form (with the shift and add it measured
+// no faster, and slower inside the NTT butterfly).
+// ---------------------------------------------------------------------------
+RK_HD bool is_k32_prime(u64 q) { return (q & 0xffffffffull) == 1ull && (q >> 32) < (1ull << 29); }
+
+RK_HD u64 mul_q_lo_k32(u64 x, u64 q) {
+    return x + ((u64)((uint32_t)x * (uint32_t)(q >> 32)) << 32);
+}
+
+// floor(x q / 2^64)
+RK_HD u64 mulhi_q_k32(u64 x, u64 q) {
+    const uint32_t k = (uint32_t)(q >> 32);
+    const u64 xh = x >> 32;
+    return xh * k + (((u64)(uint32_t)x * k + xh) >> 32);
+}
+
+RK_HD u64 mont_redc_k32(u64 lo, u64 hi, u64 q) {
+    const uint32_t k = (uint32_t)(q >> 32);
+    const u64 m = lo - ((u64)((uint32_t)lo * k) << 32);   // lo q^-1 mod 2^64
+    const u64 mh = mulhi_q_k32(m, q);
+    const u64 t = hi - mh;
+    return hi < mh ? t + q : t;
+}
+
+// The two forms behind one switch (SP: every prime the kernel touches is k 2^32 + 1).
+template <bool SP>
+RK_HD u64 shoup_lazy_t(u64 a, u64 w, u64 wp, u64 q) {
+    const u64 qhat = umulhi64(a, wp);
+    return a * w - (SP ? mul_q_lo_k32(qhat, q) : qhat * q);
+}
+template <bool SP>
+RK_HD u64 shoup_mul_t(u64 a, u64 w, u64 wp, u64 q) { return reduce_2q(shoup_lazy_t<SP>(a, w, wp, q), q); }
+template <bool SP>
+RK_HD u64 mont_redc_t(u64 lo, u64 hi, u64 q, u64 qinv) {
+    return SP ? mont_redc_k32(lo, hi, q) : mont_redc(lo, hi, q, qinv);
+}
+template <bool SP>
+RK_HD u64 mont_mul_t(u64 a, u64 b, u64 q, u64 qinv) {
+    return mont_redc_t<SP>(a * b, umulhi64(a, b), q, qinv);
+}
 // a * b R^-1 mod q for a < 2^64, b < q (so that hi < q)
 RK_HD u64 mont_mul(u64 a, u64 b, u64 q, u64 qinv) {
     return mont_redc(a * b, umulhi64(a, b), q, qinv);
@@ -68,6 +118,12 @@ struct Acc128 {
         u64 h = hi;
         if (h >= q) h -= q;
         return mont_redc(lo, h, q, qinv);
+    }
+    template <bool SP>
+    RK_HD u64 redc_t(u64 q, u64 qinv) const {
+        u64 h = hi;
+        if (h >= q) h -= q;
+        return mont_redc_t<SP>(lo, h, q, qinv);
     }
 };
 

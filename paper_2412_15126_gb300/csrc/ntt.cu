@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(256, (LOG <= 8 ? (COL ? RK_NTT_COL_BLOCKS : RK
     // that it starts on the limbs the first pass wrote last (still in L2)
     constexpr bool REV = INV == COL;
     const int poly = REV ? gridDim.y - 1 - blockIdx.y : blockIdx.y;
-    const int limb = REV ? gridDim.z - 1 - blockIdx.z : blockIdx.z;
+    const int limb = s.limb0 + (REV ? gridDim.z - 1 - blockIdx.z : blockIdx.z);
     if (s.skip_ds && limb < s.split && limb / s.skip_ds == poly % s.skip_beta) return;   // block-uniform
     const int pid = limb_prime(s, limb);
     const PrimeConst PC = pc[pid];
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(256, 4) k_ntt_row8(LimbSet s, int logn, int lo
     // grid y = polynomial, z = limb; the forward row pass (a transform's second pass)
     // walks the grid backwards, starting on the limbs the column pass wrote last
     const int poly = INV ? blockIdx.y : gridDim.y - 1 - blockIdx.y;
-    const int limb = INV ? blockIdx.z : gridDim.z - 1 - blockIdx.z;
+    const int limb = s.limb0 + (INV ? blockIdx.z : gridDim.z - 1 - blockIdx.z);
     if (s.skip_ds && limb < s.split && limb / s.skip_ds == poly % s.skip_beta) return;   // block-uniform
     const int pid = limb_prime(s, limb);
     const u64 q = pc[pid].q, q2 = 2 * q;
@@ -293,6 +293,9 @@ __global__ void __launch_bounds__(256, 4) k_ntt_row8(LimbSet s, int logn, int lo
 // threads owning one transform of a pass
 constexpr int pass_threads(int LOG, bool COL) { return (!COL && LOG == 8) ? 32 : 1 << (LOG / 2); }
 
+// The transforms keep the general Shoup product for every prime: the cheaper product
+// by a prime k 2^32 + 1 measured slower in the butterfly (its shifts and adds cost
+// more issue slots than the two multiplies it saves).
 template <bool INV, bool COL, bool LIFT = false>
 void pass_launch(int LOG, dim3 grid, int threads, size_t smem, cudaStream_t st, const LimbSet& s, int logn, int loga,
                  int units, const PrimeConst* pc, const u64* tw) {
@@ -303,7 +306,7 @@ void pass_launch(int LOG, dim3 grid, int threads, size_t smem, cudaStream_t st, 
     switch (LOG) {
 #define RK_NTT_CASE(L)                                                                                        \
     case L:                                                                                                   \
-        rk_launch(k_ntt_pass<L, INV, COL, LIFT>, grid, threads, smem, st, s, logn, loga, units, pc, tw);             \
+        rk_launch(k_ntt_pass<L, INV, COL, LIFT>, grid, threads, smem, st, s, logn, loga, units, pc, tw);      \
         break;
         RK_NTT_CASE(5)
         RK_NTT_CASE(6)
@@ -365,31 +368,74 @@ void ntt_init_attributes() {
     set_smem_attr<true, true>();
 }
 
-void launch_ntt_forward(const KernelEnv& env, const LimbSet& s, cudaStream_t st) {
-    if (s.n_limbs <= 0 || s.n_polys <= 0) return;
-    const double limbs = (double)s.n_limbs * s.n_polys - (s.skip_ds ? (double)(s.n_polys / s.skip_beta) * s.split : 0.0);
-    ProfScope ps(env, KK_NTT_FWD, st, 2, 2.0 * limbs * 8.0 * env.n, limbs * (env.n / 2) * env.logn);
+namespace {
+
+// limbs a group: all of them, or as many as keep a group within `group_bytes`
+int group_limbs(const KernelEnv& env, const LimbSet& s, size_t group_bytes) {
+    const size_t limb_bytes = (size_t)s.n_polys * env.n * 8;
+    if (group_bytes == 0 || limb_bytes * s.n_limbs <= group_bytes) return s.n_limbs;
+    const int per = (int)std::max<size_t>(1, group_bytes / limb_bytes);
+    const int groups = (s.n_limbs + per - 1) / per;
+    return (s.n_limbs + groups - 1) / groups;   // groups of (nearly) equal size
+}
+
+void ntt_forward_grouped(const KernelEnv& env, const LimbSet& s, cudaStream_t st, size_t group_bytes) {
     const int logn = env.logn, loga = logn / 2, logb = logn - loga;
     const int sm = small_set(s);
-    PassGeom c = geom(loga, true, 1 << logb, s, env.sms, env.tune ? env.tune->ntt_units[0][1][sm] : 0);
-    if (s.lift)
-        pass_launch<false, true, true>(loga, c.grid, c.threads, c.smem, st, s, logn, loga, c.units, env.pc, env.tw.psi);
-    else
-        pass_launch<false, true>(loga, c.grid, c.threads, c.smem, st, s, logn, loga, c.units, env.pc, env.tw.psi);
-    PassGeom r = geom(logb, false, 1 << loga, s, env.sms, env.tune ? env.tune->ntt_units[0][0][sm] : 0);
-    pass_launch<false, false>(logb, r.grid, r.threads, r.smem, st, s, logn, loga, r.units, env.pc, env.tw.psi);
+    const int per = group_limbs(env, s, group_bytes);
+    const double limbs = (double)s.n_limbs * s.n_polys - (s.skip_ds ? (double)(s.n_polys / s.skip_beta) * s.split : 0.0);
+    ProfScope ps(env, KK_NTT_FWD, st, 2 * ((s.n_limbs + per - 1) / per), 2.0 * limbs * 8.0 * env.n,
+                 limbs * (env.n / 2) * env.logn);
+    for (int z0 = 0; z0 < s.n_limbs; z0 += per) {
+        LimbSet g = s;
+        g.limb0 = s.limb0 + z0;
+        g.n_limbs = std::min(per, s.n_limbs - z0);
+        PassGeom c = geom(loga, true, 1 << logb, g, env.sms, env.tune ? env.tune->ntt_units[0][1][sm] : 0);
+        if (g.lift)
+            pass_launch<false, true, true>(loga, c.grid, c.threads, c.smem, st, g, logn, loga, c.units, env.pc, env.tw.psi);
+        else
+            pass_launch<false, true>(loga, c.grid, c.threads, c.smem, st, g, logn, loga, c.units, env.pc, env.tw.psi);
+        PassGeom r = geom(logb, false, 1 << loga, g, env.sms, env.tune ? env.tune->ntt_units[0][0][sm] : 0);
+        pass_launch<false, false>(logb, r.grid, r.threads, r.smem, st, g, logn, loga, r.units, env.pc, env.tw.psi);
+    }
+}
+
+void ntt_inverse_grouped(const KernelEnv& env, const LimbSet& s, cudaStream_t st, size_t group_bytes) {
+    const int logn = env.logn, loga = logn / 2, logb = logn - loga;
+    const int sm = small_set(s);
+    const int per = group_limbs(env, s, group_bytes);
+    ProfScope ps(env, KK_NTT_INV, st, 2 * ((s.n_limbs + per - 1) / per), 2.0 * s.n_limbs * s.n_polys * 8.0 * env.n,
+                 (double)s.n_limbs * s.n_polys * (env.n / 2) * env.logn);
+    for (int z0 = 0; z0 < s.n_limbs; z0 += per) {
+        LimbSet g = s;
+        g.limb0 = s.limb0 + z0;
+        g.n_limbs = std::min(per, s.n_limbs - z0);
+        PassGeom r = geom(logb, false, 1 << loga, g, env.sms, env.tune ? env.tune->ntt_units[1][0][sm] : 0);
+        pass_launch<true, false>(logb, r.grid, r.threads, r.smem, st, g, logn, loga, r.units, env.pc, env.tw.ipsi);
+        PassGeom c = geom(loga, true, 1 << logb, g, env.sms, env.tune ? env.tune->ntt_units[1][1][sm] : 0);
+        pass_launch<true, true>(loga, c.grid, c.threads, c.smem, st, g, logn, loga, c.units, env.pc, env.tw.ipsi);
+    }
+}
+
+}  // namespace
+
+void launch_ntt_forward(const KernelEnv& env, const LimbSet& s, cudaStream_t st) {
+    if (s.n_limbs <= 0 || s.n_polys <= 0) return;
+    ntt_forward_grouped(env, s, st, env.tune ? env.tune->ntt_group_bytes : 0);
 }
 
 void launch_ntt_inverse(const KernelEnv& env, const LimbSet& s, cudaStream_t st) {
     if (s.n_limbs <= 0 || s.n_polys <= 0) return;
-    ProfScope ps(env, KK_NTT_INV, st, 2, 2.0 * s.n_limbs * s.n_polys * 8.0 * env.n,
-                 (double)s.n_limbs * s.n_polys * (env.n / 2) * env.logn);
+    ntt_inverse_grouped(env, s, st, env.tune ? env.tune->ntt_group_bytes : 0);
+}
+
+void launch_ntt_forward_rows(const KernelEnv& env, const LimbSet& s, cudaStream_t st) {
+    if (s.n_limbs <= 0 || s.n_polys <= 0) return;
     const int logn = env.logn, loga = logn / 2, logb = logn - loga;
-    const int sm = small_set(s);
-    PassGeom r = geom(logb, false, 1 << loga, s, env.sms, env.tune ? env.tune->ntt_units[1][0][sm] : 0);
-    pass_launch<true, false>(logb, r.grid, r.threads, r.smem, st, s, logn, loga, r.units, env.pc, env.tw.ipsi);
-    PassGeom c = geom(loga, true, 1 << logb, s, env.sms, env.tune ? env.tune->ntt_units[1][1][sm] : 0);
-    pass_launch<true, true>(loga, c.grid, c.threads, c.smem, st, s, logn, loga, c.units, env.pc, env.tw.ipsi);
+    const double limbs = (double)s.n_limbs * s.n_polys - (s.skip_ds ? (double)(s.n_polys / s.skip_beta) * s.split : 0.0);
+    ProfScope ps(env, KK_NTT_FWD, st, 1, 2.0 * limbs * 8.0 * env.n, limbs * (env.n / 2) * logb);
+    PassGeom r = geom(logb, false, 1 << loga, s, env.sms, env.tune ? env.tune->ntt_units[0][0][small_set(s)] : 0);
+    pass_launch<false, false>(logb, r.grid, r.threads, r.smem, st, s, logn, loga, r.units, env.pc, env.tw.psi);
 }
 
 // ---------------------------------------------------------------------------
@@ -462,9 +508,44 @@ void ntt_autotune(rk_ctx* c, std::vector<double>& report) {
         cudaFreeAsync(buf, c->stream);
         throw;
     }
+    RK_CUDA(cudaFreeAsync(buf, c->stream));
+    c->tune = t;
+
+    // limb groups of the largest forward NTT (a top-level ModUp: every digit lifted to
+    // all of Q u P): the whole set in one launch pair, or groups of at most 96, 64 or
+    // 32 MiB, both passes of a group before the next
+    const int beta = (L1 + c->dsize - 1) / c->dsize, T = L1 + c->alpha;
+    const size_t words = (size_t)beta * T * n;
+    RK_CUDA(rk_malloc_async((void**)&buf, words * 8, c->stream));
+    try {
+        RK_CUDA(cudaMemsetAsync(buf, 0, words * 8, c->stream));
+        const LimbSet s{buf, (size_t)T * n, beta, T, T, 0, 0};
+        const size_t cand[4] = {0, (size_t)96 << 20, (size_t)64 << 20, (size_t)32 << 20};
+        float best = 1e30f;
+        for (size_t g : cand) {
+            ntt_forward_grouped(c->env, s, c->stream, g);   // warm
+            RK_CUDA(cudaEventRecord(e0, c->stream));
+            for (int r = 0; r < 5; r++) ntt_forward_grouped(c->env, s, c->stream, g);
+            RK_CUDA(cudaEventRecord(e1, c->stream));
+            RK_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            RK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            ms /= 5;
+            report.push_back(1000.0 * ms);
+            if (ms < best) {
+                best = ms;
+                c->tune.ntt_group_bytes = g;
+            }
+        }
+        report.push_back((double)(c->tune.ntt_group_bytes >> 20));
+    } catch (...) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaFreeAsync(buf, c->stream);
+        throw;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     RK_CUDA(cudaFreeAsync(buf, c->stream));
     RK_CUDA(cudaStreamSynchronize(c->stream));
-    c->tune = t;
 }

@@ -15,11 +15,13 @@
 
 namespace nttc {
 
-// Cooley-Tukey butterfly on values in [0, 4q): one conditional subtraction.
+// Cooley-Tukey butterfly on values in [0, 4q): one conditional subtraction.  SP: q is
+// a prime k 2^32 + 1 (cheaper product by q, same result).
+template <bool SP = false>
 __device__ __forceinline__ void ct_bfly(u64& a, u64& b, u64 w, u64 wsh, u64 q, u64 q2) {
     u64 U = a;
     if (U >= q2) U -= q2;
-    const u64 V = shoup_lazy(b, w, wsh, q);   // [0, 2q) for any 64-bit input
+    const u64 V = shoup_lazy_t<SP>(b, w, wsh, q);   // [0, 2q) for any 64-bit input
     a = U + V;
     b = U + q2 - V;
 }
@@ -30,12 +32,13 @@ __device__ __forceinline__ u64 reduce_4q(u64 x, u64 q, u64 q2) {
 }
 
 // Gentleman-Sande butterfly on values in [0, 2q).
+template <bool SP = false>
 __device__ __forceinline__ void gs_bfly(u64& a, u64& b, u64 w, u64 wsh, u64 q, u64 q2) {
     u64 U = a, V = b;
     u64 x = U + V;
     if (x >= q2) x -= q2;
     a = x;
-    b = shoup_lazy(U + q2 - V, w, wsh, q);
+    b = shoup_lazy_t<SP>(U + q2 - V, w, wsh, q);
 }
 
 template <int LOG>
@@ -64,7 +67,7 @@ __device__ __forceinline__ void twid_fetch(const ulonglong2* p, u64& w, u64& wsh
 }
 
 // forward stages with span 2^v >= P (v = LOG-1 .. LOGP) on the strided set
-template <int LOG>
+template <int LOG, bool SP = false>
 __device__ __forceinline__ void fwd_strided(u64 (&x)[Shape<LOG>::E], int t, const Twid& tw, u64 q, u64 q2) {
     using S = Shape<LOG>;
 #pragma unroll
@@ -76,13 +79,13 @@ __device__ __forceinline__ void fwd_strided(u64 (&x)[Shape<LOG>::E], int t, cons
             if (m & h) continue;
             u64 w, wsh;   // (t + P m) >> (v + 1) = m >> (v + 1 - LOGP): shared by the whole transform
             twid_fetch(T + (m >> (v + 1 - S::LOGP)), w, wsh);
-            ct_bfly(x[m], x[m + h], w, wsh, q, q2);
+            ct_bfly<SP>(x[m], x[m + h], w, wsh, q, q2);
         }
     }
 }
 
 // forward stages with span 2^v < P (v = LOGP-1 .. 0) on the contiguous set
-template <int LOG>
+template <int LOG, bool SP = false>
 __device__ __forceinline__ void fwd_contig(u64 (&x)[Shape<LOG>::E], int t, const Twid& tw, u64 q, u64 q2) {
     using S = Shape<LOG>;
 #pragma unroll
@@ -94,13 +97,13 @@ __device__ __forceinline__ void fwd_contig(u64 (&x)[Shape<LOG>::E], int t, const
             if (m & h) continue;
             u64 w, wsh;   // (t E + m) >> (v + 1) = t E / 2^(v+1) + (m >> (v + 1))
             twid_fetch(T + (m >> (v + 1)), w, wsh);
-            ct_bfly(x[m], x[m + h], w, wsh, q, q2);
+            ct_bfly<SP>(x[m], x[m + h], w, wsh, q, q2);
         }
     }
 }
 
 // inverse stages with span 2^v < P (v = 0 .. LOGP-1) on the contiguous set
-template <int LOG>
+template <int LOG, bool SP = false>
 __device__ __forceinline__ void inv_contig(u64 (&x)[Shape<LOG>::E], int t, const Twid& tw, u64 q, u64 q2) {
     using S = Shape<LOG>;
 #pragma unroll
@@ -112,13 +115,13 @@ __device__ __forceinline__ void inv_contig(u64 (&x)[Shape<LOG>::E], int t, const
             if (m & h) continue;
             u64 w, wsh;
             twid_fetch(T + (m >> (v + 1)), w, wsh);
-            gs_bfly(x[m], x[m + h], w, wsh, q, q2);
+            gs_bfly<SP>(x[m], x[m + h], w, wsh, q, q2);
         }
     }
 }
 
 // inverse stages with span 2^v >= P (v = LOGP .. LOG-1) on the strided set
-template <int LOG>
+template <int LOG, bool SP = false>
 __device__ __forceinline__ void inv_strided(u64 (&x)[Shape<LOG>::E], int t, const Twid& tw, u64 q, u64 q2) {
     using S = Shape<LOG>;
 #pragma unroll
@@ -130,7 +133,7 @@ __device__ __forceinline__ void inv_strided(u64 (&x)[Shape<LOG>::E], int t, cons
             if (m & h) continue;
             u64 w, wsh;
             twid_fetch(T + (m >> (v + 1 - S::LOGP)), w, wsh);
-            gs_bfly(x[m], x[m + h], w, wsh, q, q2);
+            gs_bfly<SP>(x[m], x[m + h], w, wsh, q, q2);
         }
     }
 }

@@ -66,6 +66,9 @@ struct LimbSet {
     size_t lift_stride = 0;
     const u64* lift_mod = nullptr;
     u64 lift_q = 0;
+    // NTT launches over a group of the limbs: grid z covers limbs limb0 .. limb0 +
+    // n_limbs - 1 of the set (limb indices stay those of the whole set)
+    int limb0 = 0;
 };
 
 __host__ __device__ __forceinline__ int limb_prime(const LimbSet& s, int t) {
@@ -148,11 +151,16 @@ inline uint32_t mask_nreal(uint32_t kind, uint32_t n_real) {
 // (transforms per block) indexed [inverse][column pass][small: fewer than 16 limbs].
 struct TuneTable {
     int ntt_units[2][2][2] = {};
+    // a forward or inverse NTT of more bytes than this runs as limb groups of at most
+    // this size, both passes of one group before the next (the intermediate between
+    // the passes then stays in L2); 0: one launch pair for the whole set
+    size_t ntt_group_bytes = 0;
 };
 
 struct KernelEnv {
     int logn, n, L, alpha;
     int sms = 152;          // multiprocessors of the device (grid sizing)
+    bool sp = false;        // every prime is k 2^32 + 1 (kernels take the cheaper products by q)
     const TuneTable* tune = nullptr;
     const PrimeConst* pc;   // device array [n_primes]
     DevTables tw;
@@ -193,6 +201,10 @@ __host__ __device__ __forceinline__ u64 seeded_key_state(u64 seed, int j, int T,
     return seed + ((((u64)j * (u64)T + (u64)p) * (u64)n + (u64)k) + 1) * kSm64Gamma;
 }
 __device__ __forceinline__ u64 seeded_key_word(u64 state, u64 q) { return umulhi64(sm64_mix(state), q); }
+template <bool SP>
+__device__ __forceinline__ u64 seeded_key_word_t(u64 state, u64 q) {
+    return SP ? mulhi_q_k32(sm64_mix(state), q) : umulhi64(sm64_mix(state), q);
+}
 
 struct SwitchKeyDev {
     u64* data = nullptr;  // [beta_L][2][L+1+alpha][n] (seeded: [beta_L][1][..][n], b only),
@@ -241,6 +253,8 @@ struct rk_ctx {
     uint64_t generation = 0;
     TuneTable tune;
     bool ks_fused = false;        // key switching with conversions fused into the NTT passes
+    bool modup_col = false;       // staged key switching with the ModUp conversion fused into
+                                  // the forward column pass (k_modup_col)
     bool stack_blocks = true;     // blocked rank: blocks and block pairs as stacks (else one by one)
     bool trim_levels = false;     // rank: bring the input down to the level the circuit needs first
     bool pair_packing = true;     // blocked circuits: pack block-pair work into free tiles when keys allow

@@ -34,6 +34,7 @@ OPT_TRIM_LEVELS = 4
 OPT_SERVER_LANES = 5
 OPT_PAIR_PACKING = 6
 OPT_STACK_BUDGET, OPT_INDICATOR_BUDGET = 7, 8
+OPT_NTT_GROUP_BYTES, OPT_MODUP_COL = 9, 10
 OP_RANK, OP_ORDER_STAT, OP_SORT, OP_RANK_BLOCKED, OP_ORDER_STAT_BLOCKED, OP_SORT_BLOCKED = 1, 2, 3, 4, 5, 6
 
 
@@ -46,7 +47,7 @@ class RkError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [(name, ctypes.c_uint32) for name in
                 ("log_n", "n_limbs", "n_special", "digit_size", "log_scale", "log_q0", "log_special", "d_g", "d_f",
-                 "cmp_cheb")]
+                 "cmp_cheb", "prime_form")]
 
 
 _vp = ctypes.c_void_p
@@ -220,8 +221,9 @@ class RankGraph:
 
 class Context:
     def __init__(self, log_n, n_limbs, n_special, digit_size, log_scale, log_q0=60, log_special=61,
-                 d_g=4, d_f=2, device=0, stream=None, cmp_cheb=0):
-        self.params = Params(log_n, n_limbs, n_special, digit_size, log_scale, log_q0, log_special, d_g, d_f, cmp_cheb)
+                 d_g=4, d_f=2, device=0, stream=None, cmp_cheb=0, prime_form=0):
+        self.params = Params(log_n, n_limbs, n_special, digit_size, log_scale, log_q0, log_special, d_g, d_f, cmp_cheb,
+                             prime_form)
         h = _vp()
         _check(_L.rk_ctx_create(ctypes.byref(self.params), device, _vp(stream) if stream else None, ctypes.byref(h)))
         self.handle = h
@@ -283,9 +285,13 @@ class Context:
         rep = {}
         for i, slot in enumerate([(s, d, p) for s in ("large", "small") for d in ("fwd", "inv") for p in ("row", "col")]):
             rep["ntt_%s_%s_%s" % slot] = {"units": int(v[2 * i]), "us": v[2 * i + 1]}
-        if len(v) > 16:
-            rep["ks"] = {"staged_us": v[16], "fused_us": dict(zip(("24MiB", "48MiB", "96MiB"), v[17:20])),
-                         "choice": "staged" if v[20] == 0 else "fused %d MiB" % v[20]}
+        rep["ntt_groups"] = {"us": dict(zip(("whole", "96MiB", "64MiB", "32MiB"), v[16:20])),
+                             "choice": "whole" if v[20] == 0 else "%d MiB" % v[20]}
+        if len(v) > 21:
+            rep["ks"] = {"staged_us": v[21], "fused_us": dict(zip(("24MiB", "48MiB", "96MiB"), v[22:25])),
+                         "staged_modup_col_us": v[26],
+                         "choice": ("staged, ModUp in the column pass" if v[27] else "staged") if v[25] == 0
+                         else "fused %d MiB" % v[25]}
         return rep
 
     # ---- keys ----
@@ -331,10 +337,12 @@ class Context:
 
     def measure_alu(self) -> dict:
         """Integer throughput of the device: 32-bit multiply-adds, Shoup modular products
-        and forward NTT butterflies a second (register-resident microbenchmarks)."""
-        out = (ctypes.c_double * 3)()
+        and forward NTT butterflies a second (register-resident microbenchmarks); the
+        last two also with a prime k 2^32 + 1 (``*_k32``)."""
+        out = (ctypes.c_double * 5)()
         _check(_L.rk_measure_alu(self.handle, out))
-        return {"imad_per_s": out[0], "modmul_per_s": out[1], "butterfly_per_s": out[2]}
+        return {"imad_per_s": out[0], "modmul_per_s": out[1], "butterfly_per_s": out[2],
+                "modmul_k32_per_s": out[3], "butterfly_k32_per_s": out[4]}
 
     def indicator_export(self, N):
         return self._coeffs_export(_L.rk_indicator_export, N)

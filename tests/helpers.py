@@ -21,7 +21,12 @@ CONFIGS = {
     "deep": (11, 36, 60, 40, 3, 61, 3, 2, 1),
     # the n = 2^17 ring of the larger blocked order statistics and sorts, few limbs
     "ring17": (17, 8, 60, 40, 2, 61, 2, 1, 1),
+    # a small ring whose primes are all k 2^32 + 1: every operation on that path
+    "small_k32": (11, 6, 60, 45, 2, 61, 2, 1, 1),
 }
+
+# sets whose primes are all k 2^32 + 1 (prime_form 1; the others: = 1 mod 2n)
+PRIME_FORM = {"cfg2": 1, "cfg3": 1, "big15": 1, "small_k32": 1}
 
 MASK_IDS = {"row0": 1, "col0": 2, "tie": 3, "tri": 4, "valid": 5, "row0s": 6, "col0s": 7, "tiec": 8, "sortidx": 9,
             "rowidx": 10}
@@ -30,14 +35,14 @@ ALL_MASKS = ("row0", "col0", "tie", "tri", "row0s", "col0s", "tiec", "sortidx")
 
 def oracle_params(name):
     log_n, n_limbs, log_q0, log_scale, alpha, log_sp, dsize, _, _ = CONFIGS[name]
-    return ckks.gen_params(log_n, n_limbs, log_q0, log_scale, alpha, log_sp, dsize)
+    return ckks.gen_params(log_n, n_limbs, log_q0, log_scale, alpha, log_sp, dsize, PRIME_FORM.get(name, 0))
 
 
 def gpu_context(name, device=0, cmp_cheb=0):
     from paper_2412_15126_gb300 import rankfhe
     log_n, n_limbs, log_q0, log_scale, alpha, log_sp, dsize, dg, df = CONFIGS[name]
     return rankfhe.Context(log_n, n_limbs, alpha, dsize, log_scale, log_q0, log_sp, dg, df, device=device,
-                           cmp_cheb=cmp_cheb)
+                           cmp_cheb=cmp_cheb, prime_form=PRIME_FORM.get(name, 0))
 
 
 def import_key(ctx, kind, g, key):

@@ -14,11 +14,11 @@ def test_ntt_roofline_arithmetic():
     with open(bench.os.path.join(bench.ROOT, "profiles", "traffic.json")) as f:
         rec = json.load(f)["ntt_fwd"]
     prof = {"launches": 10, "ms": 0.8, "ops": 10 * 4.0e7, "bytes": 10 * 8.0e7}
-    r = bench.ntt_roofline(prof, {"sm_mhz": 2070.0}, {"butterfly_per_s": 2.0e12})
+    r = bench.ntt_roofline(prof, {"sm_mhz": 2070.0}, {"butterfly_per_s": 1.0e12, "butterfly_k32_per_s": 2.0e12})
     assert r["bound"] == "alu" and r["unit"] == "Gbutterfly/s"
     assert r["achieved"] == pytest.approx(4.0e7 / 80e-6 / 1e9)
-    assert r["peak"] == pytest.approx(2000.0)                  # the measured butterfly rate
-    assert r["frac"] == pytest.approx(r["achieved"] / 2000.0)
+    assert r["peak"] == pytest.approx(1000.0)                  # the measured (general) butterfly rate
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
     assert bench.ntt_roofline(prof, None)["frac"] is None      # no measurement, no fraction
     if rec["source_sha256"] == bench.kernel_source_sha256("ntt_fwd"):
         issue = 152 * 4 * 32 * 2070e6 / rec["thread_instructions_per_butterfly"] / 1e9

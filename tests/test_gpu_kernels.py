@@ -10,7 +10,7 @@ from tests import helpers
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module", params=["small", "cfg1"])
+@pytest.fixture(scope="module", params=["small", "cfg1", "small_k32"])
 def setup(request):
     name = request.param
     P = helpers.oracle_params(name)

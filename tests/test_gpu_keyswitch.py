@@ -90,9 +90,42 @@ def test_autotune_keeps_results():
         before = ctx.rank(ct).export()
         rep = ctx.autotune()
         assert rep["ntt_large_fwd_col"]["units"] >= 1 and rep["ntt_small_inv_row"]["us"] > 0
-        assert "ks" in rep
+        assert rep["ntt_groups"]["us"]["whole"] > 0 and "ks" in rep
         after = ctx.rank(ct).export()
         assert np.array_equal(before, after)
+    finally:
+        ctx.close()
+
+
+def test_ntt_limb_groups_keep_results():
+    """NTTs run as limb groups (both passes of a group before the next) give the same
+    words as one launch pair over the whole set: a rank on the n = 2^16, 28-limb set
+    (whose top-level ModUp transforms 155 MB) with groups of 32 and 8 MiB."""
+    ctx = helpers.gpu_context("cfg2")
+    try:
+        ctx.keygen(5, 128)
+        ct = ctx.encrypt(inputs.gap_vector(128, 2.0 ** -9, 4), N=128)
+        ctx.set_option(rankfhe.OPT_NTT_GROUP_BYTES, 0)
+        whole = ctx.rank(ct).export()
+        for mib in (32, 8):
+            ctx.set_option(rankfhe.OPT_NTT_GROUP_BYTES, mib << 20)
+            assert np.array_equal(ctx.rank(ct).export(), whole), mib
+    finally:
+        ctx.close()
+
+
+@pytest.mark.parametrize("name, N", [("cfg1", 8), ("cfg2", 128)])
+def test_modup_in_column_pass_keeps_results(name, N):
+    """The staged key switch with the ModUp conversion inside the forward column pass
+    (and the digits' own limbs copied by that kernel) gives the same rank, word for
+    word, on a set with primes = 1 mod 2n and on one with primes k 2^32 + 1."""
+    ctx = helpers.gpu_context(name)
+    try:
+        ctx.keygen(6, N)
+        ct = ctx.encrypt(inputs.gap_vector(N, 2.0 ** -9 if N > 8 else 0.05, 5), N=N)
+        staged = ctx.rank(ct).export()
+        ctx.set_option(rankfhe.OPT_MODUP_COL, 1)
+        assert np.array_equal(ctx.rank(ct).export(), staged)
     finally:
         ctx.close()
 

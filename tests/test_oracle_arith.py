@@ -15,6 +15,10 @@ CONFIGS = {
     "n2^13_14x40": (13, 14, 40, 40, 1, 61, 1),
     "n2^16_28limbs": (16, 28, 60, 45, 3, 61, 3),
     "n2^16_34limbs": (16, 34, 60, 45, 3, 61, 3),
+    # every prime k 2^32 + 1 (prime_form 1)
+    "n2^16_28limbs_k32": (16, 28, 60, 45, 3, 61, 3, 1),
+    "n2^16_34limbs_k32": (16, 34, 60, 45, 3, 61, 3, 1),
+    "n2^15_34limbs_k32": (15, 34, 60, 45, 3, 61, 3, 1),
 }
 
 
@@ -30,9 +34,11 @@ def test_is_prime_matches_sympy():
 
 @pytest.mark.parametrize("name", list(CONFIGS))
 def test_prime_chain(name):
-    log_n, n_q, b0, logd, alpha, bp, dsize = CONFIGS[name]
+    log_n, n_q, b0, logd, alpha, bp, dsize = CONFIGS[name][:7]
+    form = CONFIGS[name][7] if len(CONFIGS[name]) > 7 else 0
     P = ckks.gen_params(*CONFIGS[name])
-    m = 2 << log_n
+    m = (1 << 32) if form else 2 << log_n
+    assert m % (2 << log_n) == 0
     allp = list(P.q) + list(P.p)
     assert len(set(allp)) == len(allp)
     for x in allp:
@@ -66,8 +72,11 @@ def test_prime_chain(name):
                 assert dc > d or (dc == d and c > P.q[lvl]), (lvl, c, P.q[lvl])
             c += m
         used.add(P.q[lvl])
+    # canonical scales near 2^logd: the candidates = 1 mod 2n are dense near 2^45; those
+    # = 1 mod 2^32 are 2^32 apart and prime about one in 16, so the nearest lie within
+    # a few percent
     for s in P.scales:
-        assert abs(s / 2.0 ** logd - 1.0) < 2.0 ** -15
+        assert abs(s / 2.0 ** logd - 1.0) < (0.05 if form else 2.0 ** -15)
 
 
 def test_security_budgets():
@@ -75,6 +84,8 @@ def test_security_budgets():
     # standard for n = 2^16 (1772 bits); config 2 additionally within 1550.
     assert ckks.gen_params(*CONFIGS["n2^16_28limbs"]).log_qp() <= 1550
     assert ckks.gen_params(*CONFIGS["n2^16_34limbs"]).log_qp() <= 1772
+    assert ckks.gen_params(*CONFIGS["n2^16_28limbs_k32"]).log_qp() <= 1550
+    assert ckks.gen_params(*CONFIGS["n2^16_34limbs_k32"]).log_qp() <= 1772
 
 
 def _negacyclic_bigint(a, b, q):
