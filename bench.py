@@ -1268,16 +1268,19 @@ def run_cuda(args):
     return 0
 
 
-def profile_case():
+def profile_case(ntt_group_mib=0, modup_col=False):
     """Small case for ncu captures: the rank workload's parameters (n = 2^16, 28 + 3
     limbs) but only the keys of one rotation (about 1.3 GB on the device); two top-level
-    rotations and one product inside the NVTX range "prof"."""
+    rotations and one product inside the NVTX range "prof".  ntt_group_mib and
+    modup_col set the launch options the autotuner chose in the timed run."""
     import numpy as np
     import torch
     from paper_2412_15126_gb300 import rankfhe
     W = WORKLOAD
     ctx = rankfhe.Context(W["log_n"], W["n_limbs"], W["n_special"], W["digit_size"], W["log_scale"], W["log_q0"],
                           W["log_special"], W["d_g"], W["d_f"], device=0, prime_form=W.get("prime_form", 0))
+    ctx.set_option(rankfhe.OPT_NTT_GROUP_BYTES, ntt_group_mib << 20)
+    ctx.set_option(rankfhe.OPT_MODUP_COL, 1 if modup_col else 0)
     ctx.keygen(5, 2)
     ct = ctx.encrypt(np.linspace(0.0, 0.9, 2), N=2)
     ctx.sync()
@@ -1305,10 +1308,14 @@ def main():
     ap.add_argument("--no-order-sort", action="store_true", help="skip the 34-limb argmin/argmax/sort latencies")
     ap.add_argument("--serve", type=int, default=40, help="requests of the serving sample (0: skip)")
     ap.add_argument("--profile-case", action="store_true", help="run the small ncu capture case and exit")
+    ap.add_argument("--profile-ntt-group-mib", type=int, default=0,
+                    help="profile case: NTT limb groups of at most this many MiB (0: whole sets)")
+    ap.add_argument("--profile-modup-col", action="store_true",
+                    help="profile case: the ModUp conversion inside the forward column pass")
     ap.add_argument("--no-autotune", action="store_true", help="keep the built-in launch shapes")
     args = ap.parse_args()
     if args.profile_case:
-        return profile_case()
+        return profile_case(args.profile_ntt_group_mib, args.profile_modup_col)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
