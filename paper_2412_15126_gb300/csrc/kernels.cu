@@ -182,11 +182,14 @@ __global__ void __launch_bounds__(TPB) k_modup(const u64* __restrict__ x, const 
     const u64* tab = cv.modup + ((size_t)level * cv.beta_max + j) * cv.modup_stride;
     const int T = L + 1 + alpha;
     const int limbs = level + 1 + alpha;
+    // grid z splits the target limbs into groups (more blocks for the same work)
+    const int chunk = (limbs + gridDim.z - 1) / gridDim.z;
+    const int t0 = blockIdx.z * chunk, t1 = min(limbs, t0 + chunk);
     for (int idx = threadIdx.x; idx < ns * limbs; idx += TPB) {
         const int i = idx / limbs, t = idx - i * limbs;
-        s_c[i * RK_MAX_PRIMES + t] = tab[2 * DS + (size_t)i * T + t];
+        if (t >= t0 && t < t1) s_c[i * RK_MAX_PRIMES + t] = tab[2 * DS + (size_t)i * T + t];
     }
-    for (int t = threadIdx.x; t < limbs; t += TPB) {
+    for (int t = t0 + threadIdx.x; t < t1; t += TPB) {
         const int pid = t <= level ? t : L + 1 + (t - level - 1);
         s_q[t] = pc[pid].q;
         s_qinv[t] = pc[pid].qinv;
@@ -203,7 +206,7 @@ __global__ void __launch_bounds__(TPB) k_modup(const u64* __restrict__ x, const 
             for (int e = 0; e < CONV_EL; e++) y[e][i] = shoup_mul(xi[e * TPB], w, wsh, qi);
         }
     }
-    for (int t = 0; t < limbs; t++) {
+    for (int t = t0; t < t1; t++) {
         u64* out = ext + (size_t)j * ext_stride + (size_t)t * n + k0;
         if (t >= lo && t < hi) {
             const u64* xe = x_eval + (size_t)t * n + k0;
@@ -232,7 +235,11 @@ void launch_modup(const KernelEnv& env, const u64* x, const u64* x_eval, size_t 
                   int level, int beta, cudaStream_t st, int B) {
     ProfScope pf(env, KK_MODUP, st, B, B * (2.0 * (level + 1) + (double)beta * (level + 1 + env.alpha)) * 8.0 * env.n,
                  (double)B * (level + 1 + env.alpha) * (level + 1) * env.n);
-    dim3 g(env.n / (TPB * CONV_EL), beta);
+    // about eight blocks an SM: the target limbs split over grid z when the digits'
+    // coefficient blocks alone would leave a ragged last wave
+    const int bxy = env.n / (TPB * CONV_EL) * beta, limbs = level + 1 + env.alpha;
+    const int nz = std::max(1, std::min(limbs, (8 * env.sms + bxy - 1) / bxy));
+    dim3 g(env.n / (TPB * CONV_EL), beta, nz);
     for (int b = 0; b < B; b++) {
         const u64* xb = x + (size_t)b * (level + 1) * env.n;
         const u64* eb = x_eval + (size_t)b * eval_stride;
@@ -272,14 +279,18 @@ __global__ void __launch_bounds__(TPB) k_moddown_conv(const u64* __restrict__ u,
     __shared__ u64 s_q[RK_MAX_PRIMES], s_qinv[RK_MAX_PRIMES], s_pm[RK_MAX_PRIMES];
     const int c = blockIdx.y;
     const int nt = RS ? level : level + 1;   // target limbs
+    // grid z splits the target limbs into groups of `chunk` (each block recomputes the
+    // few centred source terms, so that small sets still fill the device)
+    const int chunk = (nt + gridDim.z - 1) / gridDim.z;
+    const int i0 = blockIdx.z * chunk, i1 = min(nt, i0 + chunk);
     const u64* blk = RS ? cv.mdrs + (size_t)level * cv.mdrs_stride : cv.moddown;
     const u64* cm = blk + 2 * NS;
     const u64* pmod = cm + (size_t)NS * (L + 1);
     for (int idx = threadIdx.x; idx < NS * nt; idx += TPB) {
         const int kk = idx / nt, i = idx - kk * nt;
-        s_c[kk * RK_MAX_PRIMES + i] = cm[(size_t)kk * (L + 1) + i];
+        if (i >= i0 && i < i1) s_c[kk * RK_MAX_PRIMES + i] = cm[(size_t)kk * (L + 1) + i];
     }
-    for (int i = threadIdx.x; i < nt; i += TPB) {
+    for (int i = i0 + threadIdx.x; i < i1; i += TPB) {
         s_q[i] = pc[i].q;
         s_qinv[i] = pc[i].qinv;
         s_pm[i] = pmod[i];
@@ -316,7 +327,7 @@ __global__ void __launch_bounds__(TPB) k_moddown_conv(const u64* __restrict__ u,
         for (int e = 0; e < CONV_EL; e++) nneg[e] = (int)floor(__dadd_rn(f[e], 0.5));
     }
     u64* out = w + (size_t)c * nt * n + k0;
-    for (int i = 0; i < nt; i++) {
+    for (int i = i0; i < i1; i++) {
         const u64 q = s_q[i], qinv = s_qinv[i], pm = s_pm[i];
         Acc128 acc[CONV_EL];
 #pragma unroll
@@ -338,7 +349,11 @@ template <bool RS>
 static void moddown_conv_launch(const KernelEnv& env, const u64* u, u64* w, int level, cudaStream_t st, int polys) {
     const int nt = RS ? level : level + 1, ns = env.alpha + (RS ? 1 : 0);
     ProfScope pf(env, KK_MODDOWN, st, 1, polys * (1.0 * ns + nt) * 8.0 * env.n, 1.0 * polys * nt * ns * env.n);
-    dim3 g(env.n / (TPB * CONV_EL), polys);
+    // enough blocks for two waves: the target limbs split over grid z when the
+    // coefficient blocks of the polynomials alone would leave SMs idle
+    const int bxy = env.n / (TPB * CONV_EL) * polys;
+    const int nz = std::max(1, std::min(nt, (2 * env.sms + bxy - 1) / bxy));
+    dim3 g(env.n / (TPB * CONV_EL), polys, nz);
     switch (env.alpha) {
 #define RK_MD_CASE(A)                                                                               \
     case A:                                                                                         \
