@@ -318,6 +318,51 @@ def blocked_scaling_workload(stream, device, sizes=(512, 2048, 8192, 16384), n17
     return out
 
 
+def large_argmin(N: int, levels: int = 2048):
+    """The blocked argmin (Alg. 4 on the blocked tie-corrected ranks, Alg. 7) of N
+    values on a `levels`-level grid (ties) on the n = 2^17 ring (44 + 3 limbs at 2^50,
+    comparator g^5 f^2, blocks of 128, four block pairs a ciphertext, indicator of
+    8N coefficients): one run, CUDA events on the library stream, inputs resident;
+    the one-hot mask against brute force.  Not part of the default run (minutes at
+    N = 16384); prints one JSON line."""
+    import numpy as np
+    import torch
+    from paper_2412_15126_gb300 import inputs, rankfhe
+    W = RING17
+    stream = torch.cuda.Stream()
+    ctx = rankfhe.Context(W["log_n"], W["n_limbs"], W["n_special"], W["digit_size"], W["log_scale"], W["log_q0"],
+                          W["log_special"], W["d_g"], W["d_f"], device=0, stream=stream.cuda_stream,
+                          prime_form=W.get("prime_form", 0))
+    try:
+        ctx.keygen(7003, 128)
+        ctx.keygen_rotations([16384, 32768])     # four block pairs a ciphertext
+        v = inputs.grid_vector(N, levels, 7005)
+        blocks = [ctx.encrypt(v[128 * b:128 * (b + 1)], N=128) for b in range(N // 128)]
+        t0 = time.perf_counter()
+        ncoef = len(ctx.indicator_export(N))     # the host computes and caches them: not timed
+        coef_s = time.perf_counter() - t0
+        ctx.sync()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+            res = ctx.order_stat_blocked(blocks, 1)
+            ev1.record(stream)
+        ev1.synchronize()
+        first = np.zeros(N)
+        first[int(np.argmin(v))] = 1
+        got = np.concatenate([ctx.decrypt(r) for r in res])
+        out = {"large_argmin": {"N": N, "grid_levels": levels, "blocks": N // 128, "s": ev0.elapsed_time(ev1) / 1000.0,
+                                "indicator_coefficients": ncoef, "indicator_host_s": coef_s,
+                                "max_error": float(np.max(np.abs(got - first))),
+                                "argmax_of_mask_is_first_minimum": int(np.argmax(got)) == int(np.argmin(v)),
+                                "workload": "n=2^17 44+3 limbs 2^50, primes k 2^32 + 1, Cmp g^5 f^2, blocks of 128"}}
+        print(json.dumps(out))
+    finally:
+        ctx.close()
+    return 0
+
+
 # ---------------------------------------------------------------------------
 # serving: Poisson arrivals of mixed rank / argmin / sort requests
 # ---------------------------------------------------------------------------
@@ -1313,7 +1358,11 @@ def main():
     ap.add_argument("--profile-modup-col", action="store_true",
                     help="profile case: the ModUp conversion inside the forward column pass")
     ap.add_argument("--no-autotune", action="store_true", help="keep the built-in launch shapes")
+    ap.add_argument("--large-argmin", type=int, default=0,
+                    help="run only the blocked argmin of this many values on the n = 2^17 ring and exit")
     args = ap.parse_args()
+    if args.large_argmin:
+        return large_argmin(args.large_argmin)
     if args.profile_case:
         return profile_case(args.profile_ntt_group_mib, args.profile_modup_col)
     if args.warmup < 3:

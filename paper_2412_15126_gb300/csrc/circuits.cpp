@@ -417,8 +417,9 @@ struct ChebPS {
         H Pm = E.mul(E.level_down(Qc, lo), E.level_down(G[m], lo));
         return E.add(Pm, E.level_down(Rc, Pm->level));
     }
-    // value of every node, deepest first: a node is Q T_m + R over its children; all
-    // leaves are held at once, so this form is for stacks of at most two members
+    // value of every node, deepest first: a node is Q T_m + R over its children (which
+    // are released once used); all leaves are held at once, so this form is for stacks
+    // of at most two members
     H eval(const std::vector<double>& c) {
         nodes.clear();
         build(c, 0);
@@ -469,6 +470,15 @@ struct ChebPS {
                 const H& Rc = val[nodes[ids[i]].r];
                 val[ids[i]] = E.add(prods[i], E.level_down(Rc, prods[i]->level));
             }
+            // this depth's operands and products are no longer needed
+            for (int id : ids) {
+                val[nodes[id].q] = H();
+                val[nodes[id].r] = H();
+            }
+            prods.clear();
+            qs.clear();
+            gs.clear();
+            hold.clear();
         }
         return std::move(val[0]);
     }
@@ -510,6 +520,7 @@ H cheb_ps(Ev& E, const H& t, const std::vector<double>& c) {
     int leaf_level = 1 << 30;
     for (int i = 1; i < k; i++) leaf_level = std::min(leaf_level, ps.T[i]->level);
     for (int i = 1; i < k; i++) ps.TL.push_back(E.level_down(ps.T[i], leaf_level));
+    ps.T.clear();   // the leaves and the giant steps hold everything the evaluation reads
     return t->B <= 2 ? ps.eval(c) : ps.rec(c);
 }
 
@@ -846,15 +857,21 @@ static H stack_of(rk_ctx* c, const std::vector<rk_ct*>& xs) {
     return H(ct_stack(c, p.data(), (int)p.size()));
 }
 
-// f on the whole stack, or, when the context runs blocked circuits one ciphertext at
-// a time (the plain per-query form), on each member with its own launches.
+static int stack_chunk(const rk_ctx* c, int level);
+
+// f on the whole stack, in chunks of members that fit the stacking budget (members are
+// independent, so the results are the same), or, when the context runs blocked
+// circuits one ciphertext at a time (the plain per-query form), on each member with
+// its own launches.
 template <class F>
 static H each(rk_ctx* c, Ev& E, H x, F f) {
-    if (c->stack_blocks || x->B == 1) return f(std::move(x));
+    const int chunk = c->stack_blocks ? stack_chunk(c, x->level) : 1;
+    if (x->B <= chunk) return f(std::move(x));
     std::vector<H> parts;
     std::vector<rk_ct*> ps;
-    for (int b = 0; b < x->B; b++) {
-        parts.push_back(f(E.copy(H(ct_view(x.p, b)))));
+    for (int b0 = 0; b0 < x->B; b0 += chunk) {
+        const int g = std::min(chunk, x->B - b0);
+        parts.push_back(f(E.copy(H(ct_view_range(x.p, b0, g)))));
         ps.push_back(parts.back().p);
     }
     return stack_of(c, ps);
@@ -1192,21 +1209,18 @@ static std::pair<H, H> blocked_ranks_tc(rk_ctx* c, const rk_ct* const* blocks, i
     for (int i = 1; i < L; i++) Bm.push_back(E.add_const(E.neg(Bsum[i]), (double)i));
     std::vector<rk_ct*> ap;
     for (auto& a : A) ap.push_back(a.p);
-    H S = stack_of(c, ap);
-    {
-        const int k = log2_exact((uint32_t)Bsz);
-        S = chain(E, std::move(S), pow2_amounts(Bsz, k, 1));
-        S = E.mul_mask_d(S, rmask, Dn);
-    }
+    const int kB = log2_exact((uint32_t)Bsz);
+    H S = each(c, E, stack_of(c, ap), [&](H x) {
+        return E.mul_mask_d(chain(E, std::move(x), pow2_amounts(Bsz, kB, 1)), rmask, Dn);
+    });
+    A.clear();
     if (L == 1) return std::make_pair(std::move(S), std::move(rc.first));
     std::vector<rk_ct*> bp;
     for (auto& b : Bm) bp.push_back(b.p);
-    H T = sum_cols(E, stack_of(c, bp), RK_MASK_COL0);   // stack of (L - 1) Bq
-    {
-        const int k = log2_exact((uint32_t)Bsz);
-        T = chain(E, std::move(T), negated(trans_r_amounts(Bsz, k)));
-        T = E.mul_mask_d(T, rmask, Dn);
-    }
+    H T = each(c, E, stack_of(c, bp), [&](H x) {   // stack of (L - 1) Bq
+        return E.mul_mask_d(chain(E, sum_cols(E, std::move(x), RK_MASK_COL0), negated(trans_r_amounts(Bsz, kB))), rmask, Dn);
+    });
+    Bm.clear();
     std::vector<H> R;
     std::vector<rk_ct*> rp;
     for (int i = 0; i < L; i++) {
@@ -1269,7 +1283,9 @@ void circuit_sort_blocked(rk_ctx* c, const rk_ct* const* blocks, int L, rk_ct** 
     check_blocks(c, blocks, L, blocked_rank_tc_depth(c) + cheb_depth((int)co.size()) + 3, "blocked sort");
     auto rr = blocked_ranks_tc(c, blocks, L, true);
     Ev E{c};
-    H RR = E.add_mask_d(repl_r(E, std::move(rr.first)), RK_MASK_ROWIDX, D);   // stack of L Bq
+    H RR = each(c, E, std::move(rr.first), [&](H x) {   // stack of L Bq
+        return E.add_mask_d(repl_r(E, std::move(x)), RK_MASK_ROWIDX, D);
+    });
     const size_t ct_bytes = (size_t)2 * (RR->level + 1) * c->n * 8 * Bq;
     const size_t live = (size_t)baby_steps((int)co.size()) + 2 * (size_t)cheb_depth((int)co.size()) + 8;
     const int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)L * L, c->ind_stack_bytes / (live * ct_bytes)));

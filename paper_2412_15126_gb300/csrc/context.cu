@@ -106,13 +106,35 @@ static int bitrev(int x, int bits) {
 
 static std::atomic<uint64_t> g_device_allocs{0};
 uint64_t rk_alloc_counted() { return g_device_allocs.load(); }
+// Freed stream-ordered allocations stay reserved in the device's default pool (its
+// release threshold is raised at context creation), and blocks of other sizes do not
+// serve a request; so when an allocation fails, the unused reserve is returned to the
+// device and the allocation is tried once more.
+static cudaError_t trim_and_retry(cudaError_t e, cudaStream_t st) {
+    if (e != cudaErrorMemoryAllocation) return e;
+    cudaGetLastError();   // clear the failed allocation's error
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return e;
+    if (st) {   // not while a graph is being captured on the stream
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return e;
+        cudaStreamSynchronize(st);
+    }
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess || cudaMemPoolTrimTo(pool, 0) != cudaSuccess) return e;
+    return cudaSuccess;
+}
 cudaError_t rk_malloc(void** p, size_t bytes) {
     g_device_allocs++;
-    return cudaMalloc(p, bytes);
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaErrorMemoryAllocation && trim_and_retry(e, nullptr) == cudaSuccess) e = cudaMalloc(p, bytes);
+    return e;
 }
 cudaError_t rk_malloc_async(void** p, size_t bytes, cudaStream_t st) {
     g_device_allocs++;
-    return cudaMallocAsync(p, bytes, st);
+    cudaError_t e = cudaMallocAsync(p, bytes, st);
+    if (e == cudaErrorMemoryAllocation && trim_and_retry(e, st) == cudaSuccess) e = cudaMallocAsync(p, bytes, st);
+    return e;
 }
 
 u64* rk_ctx::scratch(size_t words) {
