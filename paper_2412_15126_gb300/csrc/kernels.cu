@@ -169,7 +169,9 @@ void launch_tensor(const KernelEnv& env, u64* d, const u64* x, const u64* y, int
 // conversion reproduces them exactly), so the following NTT can skip them.
 // Each thread converts CONV_EL coefficients (k0 + e TPB) so that every conversion
 // constant, staged in shared memory, serves CONV_EL products.
+#ifndef CONV_EL   // a build may set another width
 #define CONV_EL 4
+#endif
 template <int DS, bool SP>
 __global__ void __launch_bounds__(TPB) k_modup(const u64* __restrict__ x, const u64* __restrict__ x_eval, u64* __restrict__ ext,
                                                size_t ext_stride, int level, int L, int alpha, ConvTables cv, int n,
