@@ -114,6 +114,15 @@ typedef struct {
 rk_status rk_ctx_create(const rk_params* params, int device, void* cuda_stream, rk_ctx** out);
 void rk_ctx_destroy(rk_ctx* ctx);
 
+/* The prime chain and canonical scales a parameter set gives (the rules above), on
+ * the host, without a device or a context: moduli (may be NULL) receives min(cap,
+ * L+1+alpha) words, q_0..q_L then p_0..p_{alpha-1}; *count (may be NULL) the number
+ * of moduli; scales (may be NULL) min(scales_cap, L+1) doubles Delta_0..Delta_L.
+ * The same values rk_ctx_moduli and rk_ctx_scales return for a context of these
+ * parameters.  Errors: RK_EINVAL on NULL params or parameters rk_ctx_create rejects. */
+rk_status rk_params_chain(const rk_params* params, uint64_t* moduli, size_t cap, size_t* count, double* scales,
+                          size_t scales_cap);
+
 /* The moduli q_0..q_L followed by p_0..p_{alpha-1}; *count receives L+1+alpha.
  * Writes min(cap, count) words.  Errors: RK_EINVAL on NULL. */
 rk_status rk_ctx_moduli(const rk_ctx* ctx, uint64_t* out, size_t cap, size_t* count);

@@ -38,6 +38,7 @@ void graph_free(rk_graph* g);
 rk_ctx* graph_context(const rk_graph* g);
 void circuit_rotations(uint32_t N, std::vector<int>& out);
 void measure_alu(rk_ctx* c, double out[5]);
+void params_chain(const rk_params* p, std::vector<u64>& primes, std::vector<double>& scales);
 
 namespace {
 thread_local std::string g_last_error;
@@ -145,6 +146,21 @@ rk_status rk_ctx_moduli(const rk_ctx* ctx, uint64_t* out, size_t cap, size_t* co
         if (count) *count = ctx->primes.size();
         if (out)
             for (size_t i = 0; i < ctx->primes.size() && i < cap; i++) out[i] = ctx->primes[i];
+    });
+}
+
+rk_status rk_params_chain(const rk_params* params, uint64_t* moduli, size_t cap, size_t* count, double* scales,
+                          size_t scales_cap) {
+    return guard([&] {
+        need(params, "params");
+        std::vector<u64> q;
+        std::vector<double> sc;
+        params_chain(params, q, sc);
+        if (count) *count = q.size();
+        if (moduli)
+            for (size_t i = 0; i < q.size() && i < cap; i++) moduli[i] = q[i];
+        if (scales)
+            for (size_t i = 0; i < sc.size() && i < scales_cap; i++) scales[i] = sc[i];
     });
 }
 

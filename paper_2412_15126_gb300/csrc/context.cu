@@ -166,6 +166,42 @@ static void validate(const rk_params* p) {
                "prime_form 1 (primes k 2^32 + 1) needs log_scale, log_q0 and log_special of at least 34");
 }
 
+// The prime chain and canonical scales of a parameter set (host only, no device):
+// q_0..q_L then the special primes, and Delta_0..Delta_L.
+void params_chain(const rk_params* p, std::vector<u64>& primes, std::vector<double>& scales) {
+    validate(p);
+    const int n = 1 << p->log_n, L = (int)p->n_limbs - 1, alpha = (int)p->n_special;
+    const u64 m = 2ull * (u64)n;
+    // candidate step: primes = 1 mod 2n, or (prime_form 1) = 1 mod 2^32, which 2n divides
+    const u64 step = p->prime_form ? (1ull << 32) : m;
+    std::vector<u64> used;
+    std::vector<u64> q(L + 1);
+    q[0] = largest_prime_below(1ull << p->log_q0, step, used);
+    used.push_back(q[0]);
+    std::vector<double> sc(L + 1);
+    const double two_ls = std::ldexp(1.0, (int)p->log_scale);
+    sc[L] = two_ls;
+    for (int l = L; l >= 1; l--) {
+        volatile double t = sc[l] * sc[l];
+        double target = t / two_ls;
+        u64 ql = nearest_prime((u64)std::floor(target), step, used);
+        used.push_back(ql);
+        q[l] = ql;
+        volatile double sq = sc[l] * sc[l];
+        sc[l - 1] = sq / (double)ql;
+    }
+    u64 bound = 1ull << p->log_special;
+    primes = q;
+    for (int k = 0; k < alpha; k++) {
+        u64 pk = largest_prime_below(bound, step, used);
+        used.push_back(pk);
+        primes.push_back(pk);
+        bound = pk;
+    }
+    scales = sc;
+    for (u64 x : primes) RK_REQUIRE(x < (1ull << 61), RK_EINVAL, "prime above 2^61");
+}
+
 void ctx_build(rk_ctx* c, const rk_params* p, int device, void* stream) {
     validate(p);
     c->prm = *p;
@@ -191,38 +227,11 @@ void ctx_build(rk_ctx* c, const rk_params* p, int device, void* stream) {
     c->dsize = (int)p->digit_size;
     c->n_primes = c->L + 1 + c->alpha;
     const u64 m = 2ull * (u64)c->n;
-    // candidate step: primes = 1 mod 2n, or (prime_form 1) = 1 mod 2^32, which 2n divides
-    const u64 step = p->prime_form ? (1ull << 32) : m;
 
     // ---- prime chain and canonical scales ----
-    std::vector<u64> used;
-    std::vector<u64> q(c->L + 1);
-    q[0] = largest_prime_below(1ull << p->log_q0, step, used);
-    used.push_back(q[0]);
-    std::vector<double> sc(c->L + 1);
-    const double two_ls = std::ldexp(1.0, (int)p->log_scale);
-    sc[c->L] = two_ls;
-    for (int l = c->L; l >= 1; l--) {
-        volatile double t = sc[l] * sc[l];
-        double target = t / two_ls;
-        u64 ql = nearest_prime((u64)std::floor(target), step, used);
-        used.push_back(ql);
-        q[l] = ql;
-        volatile double sq = sc[l] * sc[l];
-        sc[l - 1] = sq / (double)ql;
-    }
-    std::vector<u64> sp;
-    u64 bound = 1ull << p->log_special;
-    for (int k = 0; k < c->alpha; k++) {
-        u64 pk = largest_prime_below(bound, step, used);
-        used.push_back(pk);
-        sp.push_back(pk);
-        bound = pk;
-    }
-    c->primes = q;
-    c->primes.insert(c->primes.end(), sp.begin(), sp.end());
-    c->scales = sc;
-    for (u64 x : c->primes) RK_REQUIRE(x < (1ull << 61), RK_EINVAL, "prime above 2^61");
+    params_chain(p, c->primes, c->scales);
+    const std::vector<u64> q(c->primes.begin(), c->primes.begin() + c->L + 1);
+    const std::vector<u64> sp(c->primes.begin() + c->L + 1, c->primes.end());
 
     // ---- per-prime constants ----
     const int NP = c->n_primes, n = c->n;

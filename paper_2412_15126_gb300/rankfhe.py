@@ -85,6 +85,7 @@ _sig("rk_encoding_export", [_vp, _u32, _u32, _u32, _u32, _dp, _sz])
 _sig("rk_indicator_export", [_vp, _u32, _dp, _sz, ctypes.POINTER(_sz)])
 _sig("rk_comparator_export", [_vp, _dp, _sz, ctypes.POINTER(_sz)])
 _sig("rk_measure_alu", [_vp, _dp])
+_sig("rk_params_chain", [ctypes.POINTER(Params), _u64p, _sz, ctypes.POINTER(_sz), _dp, _sz])
 _sig("rk_device_alloc_count", [], ctypes.c_uint64)
 _sig("rk_encrypt", [_vp, _dp, _u32, _u32, _u32, _u32, ctypes.POINTER(_vp)])
 _sig("rk_decrypt_slots", [_vp, _vp, _dp, _sz])
@@ -155,6 +156,17 @@ def _check(status):
 def device_alloc_count() -> int:
     """Device allocations the library has made in this process (every context)."""
     return int(_L.rk_device_alloc_count())
+
+
+def params_chain(log_n, n_limbs, n_special, digit_size, log_scale, log_q0=60, log_special=61, prime_form=0):
+    """The moduli (q_0..q_L, then the special primes) and canonical scales of a
+    parameter set, computed on the host by the library (no device needed)."""
+    prm = Params(log_n, n_limbs, n_special, digit_size, log_scale, log_q0, log_special, 0, 0, 0, prime_form)
+    cnt = _sz()
+    q = (ctypes.c_uint64 * (n_limbs + n_special))()
+    sc = (ctypes.c_double * n_limbs)()
+    _check(_L.rk_params_chain(ctypes.byref(prm), q, len(q), ctypes.byref(cnt), sc, len(sc)))
+    return [int(x) for x in q[:cnt.value]], [float(x) for x in sc]
 
 
 def raw(name):
