@@ -1,6 +1,6 @@
 """The library's 64-bit modular arithmetic (csrc/modarith.cuh), compiled for the host
 with g++, against Python's integers: Shoup's product, Montgomery's reduction, and
-their forms for primes k 2^32 + 1 (the products by q of reading 18), which must give
+their forms for primes k 2^32 + 1 (one or two 32-bit products by q), which must give
 the same words as the general forms."""
 import os
 import random
